@@ -1,0 +1,775 @@
+/*
+ * FP64 CPU oracle for GP reconstruction + level-crossing probability (LCP).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may call this file:
+ * only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline leg load it.
+ * It shares no code, header, table or constant with the CUDA library.
+ *
+ * Plain, slow, obviously-correct definitions, in the paper's order:
+ *   - kernel k(x1,x2): RBF sigma^2 exp(-|x1-x2|^2/(2 l^2)) (Sec. 3, Sec. 4.2);
+ *     anisotropic lengths divide each axis; Matern-5/2 is the textbook
+ *     (1+sqrt5 r+5r^2/3)exp(-sqrt5 r) (Rasmussen & Williams eq. 4.17).
+ *   - posterior, Eq. (1): for plain GPR the stored inducing distribution is the
+ *     latent posterior at the observations, and Eq. (1) reduces to
+ *     mu(x) = k_x^T Kt^-1 y, Sigma(a,b) = k(a,b) - k_a^T Kt^-1 k_b,
+ *     Kt = K(X,X) + sn2 I.  Both forms are implemented (or_posterior,
+ *     or_posterior_sgpr) so a test can check the reduction.
+ *   - cell LCP (Sec. 3): 1 - P(all 8 corners < theta) - P(all 8 > theta),
+ *     estimated either by the Genz sequential-conditioning (SOV) rule over a
+ *     shifted rank-1 lattice or by Monte Carlo (the paper's estimator, 1600
+ *     samples, Sec. 5.4) with Philox-4x32-10 + Box-Muller normals.
+ *   - regional bound, Eq. (upper_bound) with Slepian's inequality (Sec. 4.1):
+ *     1 - B_l^d - B_u^d, B = min over the node of Phi(+-(theta-mu)/sigma).
+ *   - octree adaptive query, Algorithm 1 (Sec. 4.3), one level per call.
+ *
+ * Readings where the paper is silent are fixed by the caller-visible options
+ * (jitter tau, skip epsilon, minimiser steps T) and documented at each site.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define OR_SE 0
+#define OR_MATERN52 1
+
+typedef struct {
+    int64_t m;
+    int kernel;
+    double ell[3];
+    double sf2, sn2;
+    double *X;      /* m x 3 */
+    double *y;      /* m */
+    double *L;      /* m x m row-major, lower Cholesky factor of Kt */
+    double *Linv;   /* m x m row-major, L^-1 (lower) */
+    double *vy;     /* L^-1 y */
+    double *alpha;  /* Kt^-1 y */
+    double *mu_obs; /* latent posterior mean at the observations */
+    double *var_obs;/* latent posterior variance at the observations */
+} or_model;
+
+/* ------------------------------------------------------------------ kernel */
+
+double or_kernel_eval(int kernel, const double *ell, double sf2, const double *a, const double *b)
+{
+    double r2 = 0.0;
+    for (int d = 0; d < 3; ++d) {
+        double t = (a[d] - b[d]) / ell[d];
+        r2 += t * t;
+    }
+    if (kernel == OR_SE) return sf2 * exp(-0.5 * r2);
+    double r = sqrt(r2), s5r = sqrt(5.0) * r;
+    return sf2 * (1.0 + s5r + 5.0 * r2 / 3.0) * exp(-s5r);
+}
+
+/* d k(x, b) / d x_d for the kernel above (gradient in the first argument). */
+static void kernel_grad(int kernel, const double *ell, double sf2, const double *x, const double *b,
+                        double *k_out, double g[3])
+{
+    double r2 = 0.0, dd[3];
+    for (int d = 0; d < 3; ++d) {
+        dd[d] = x[d] - b[d];
+        double t = dd[d] / ell[d];
+        r2 += t * t;
+    }
+    if (kernel == OR_SE) {
+        double k = sf2 * exp(-0.5 * r2);
+        *k_out = k;
+        for (int d = 0; d < 3; ++d) g[d] = -k * dd[d] / (ell[d] * ell[d]);
+    } else {
+        double r = sqrt(r2), s5r = sqrt(5.0) * r, e = exp(-s5r);
+        *k_out = sf2 * (1.0 + s5r + 5.0 * r2 / 3.0) * e;
+        /* dk/dr = -(5/3) sf2 r (1 + sqrt5 r) e^{-sqrt5 r};  dr/dx_d = dd/(l^2 r) */
+        double c = -(5.0 / 3.0) * sf2 * (1.0 + s5r) * e;
+        for (int d = 0; d < 3; ++d) g[d] = c * dd[d] / (ell[d] * ell[d]);
+    }
+}
+
+/* --------------------------------------------------------- dense algebra */
+
+/* In-place Cholesky of an n x n row-major SPD matrix (lower). 0 on success. */
+int or_cholesky(double *A, int64_t n)
+{
+    for (int64_t j = 0; j < n; ++j) {
+        double s = A[j * n + j];
+        for (int64_t k = 0; k < j; ++k) s -= A[j * n + k] * A[j * n + k];
+        if (!(s > 0.0)) return -1;
+        double ljj = sqrt(s);
+        A[j * n + j] = ljj;
+        for (int64_t i = j + 1; i < n; ++i) {
+            double t = A[i * n + j];
+            for (int64_t k = 0; k < j; ++k) t -= A[i * n + k] * A[j * n + k];
+            A[i * n + j] = t / ljj;
+        }
+        for (int64_t k = j + 1; k < n; ++k) A[j * n + k] = 0.0;
+    }
+    return 0;
+}
+
+/* Solve L x = b (forward substitution), L lower n x n row-major. */
+static void fwd_sub(const double *L, int64_t n, const double *b, double *x)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        double s = b[i];
+        const double *row = L + i * n;
+        for (int64_t k = 0; k < i; ++k) s -= row[k] * x[k];
+        x[i] = s / row[i];
+    }
+}
+
+/* Solve L^T x = b (back substitution). */
+static void back_sub_T(const double *L, int64_t n, const double *b, double *x)
+{
+    for (int64_t i = n - 1; i >= 0; --i) {
+        double s = b[i];
+        for (int64_t k = i + 1; k < n; ++k) s -= L[k * n + i] * x[k];
+        x[i] = s / L[i * n + i];
+    }
+}
+
+static double dot(const double *a, const double *b, int64_t n)
+{
+    double s = 0.0;
+    for (int64_t i = 0; i < n; ++i) s += a[i] * b[i];
+    return s;
+}
+
+/* ------------------------------------------------------------------ model */
+
+void or_model_destroy(or_model *M)
+{
+    if (!M) return;
+    free(M->X); free(M->y); free(M->L); free(M->Linv); free(M->vy); free(M->alpha);
+    free(M->mu_obs); free(M->var_obs);
+    free(M);
+}
+
+/* Builds Kt = K(X,X) + sn2 I, its Cholesky factor, L^-1, L^-1 y, Kt^-1 y and the
+ * latent posterior at the observations (Sec. 4.3's p1/p2 test needs it).  With
+ * the observations as inducing set, mu_M = K Kt^-1 y = y - sn2 Kt^-1 y and
+ * A_M = K - K Kt^-1 K = sn2 I - sn2^2 Kt^-1 (because K = Kt - sn2 I).
+ * Variance floor: 1e-12 sf2 (reading; the paper is silent).
+ * Returns NULL when Kt is not positive definite. */
+or_model *or_model_create(const double *X, const double *y, int64_t m, int kernel,
+                          const double *ell, double sf2, double sn2)
+{
+    or_model *M = (or_model *)calloc(1, sizeof(or_model));
+    M->m = m; M->kernel = kernel; M->sf2 = sf2; M->sn2 = sn2;
+    for (int d = 0; d < 3; ++d) M->ell[d] = ell[d];
+    M->X = (double *)malloc(sizeof(double) * 3 * m);
+    M->y = (double *)malloc(sizeof(double) * m);
+    memcpy(M->X, X, sizeof(double) * 3 * m);
+    memcpy(M->y, y, sizeof(double) * m);
+    M->L = (double *)malloc(sizeof(double) * m * m);
+    for (int64_t i = 0; i < m; ++i)
+        for (int64_t j = 0; j < m; ++j)
+            M->L[i * m + j] = or_kernel_eval(kernel, ell, sf2, X + 3 * i, X + 3 * j) + (i == j ? sn2 : 0.0);
+    if (or_cholesky(M->L, m) != 0) { or_model_destroy(M); return NULL; }
+    /* L^-1 column by column: L x = e_j */
+    M->Linv = (double *)calloc((size_t)(m * m), sizeof(double));
+    double *e = (double *)calloc((size_t)m, sizeof(double));
+    double *col = (double *)malloc(sizeof(double) * m);
+    for (int64_t j = 0; j < m; ++j) {
+        e[j] = 1.0;
+        fwd_sub(M->L, m, e, col);
+        e[j] = 0.0;
+        for (int64_t i = 0; i < m; ++i) M->Linv[i * m + j] = col[i];
+    }
+    free(e); free(col);
+    M->vy = (double *)malloc(sizeof(double) * m);
+    M->alpha = (double *)malloc(sizeof(double) * m);
+    fwd_sub(M->L, m, y, M->vy);
+    back_sub_T(M->L, m, M->vy, M->alpha);
+    M->mu_obs = (double *)malloc(sizeof(double) * m);
+    M->var_obs = (double *)malloc(sizeof(double) * m);
+    for (int64_t i = 0; i < m; ++i) {
+        double qii = 0.0; /* [Kt^-1]_ii = sum_k (L^-1)_{ki}^2 */
+        for (int64_t k = i; k < m; ++k) qii += M->Linv[k * m + i] * M->Linv[k * m + i];
+        M->mu_obs[i] = y[i] - sn2 * M->alpha[i];
+        double v = sn2 - sn2 * sn2 * qii;
+        double fl = 1e-12 * sf2;
+        M->var_obs[i] = v > fl ? v : fl;
+    }
+    return M;
+}
+
+void or_model_get(const or_model *M, double *L, double *alpha, double *vy, double *mu_obs, double *var_obs)
+{
+    int64_t m = M->m;
+    if (L) memcpy(L, M->L, sizeof(double) * m * m);
+    if (alpha) memcpy(alpha, M->alpha, sizeof(double) * m);
+    if (vy) memcpy(vy, M->vy, sizeof(double) * m);
+    if (mu_obs) memcpy(mu_obs, M->mu_obs, sizeof(double) * m);
+    if (var_obs) memcpy(var_obs, M->var_obs, sizeof(double) * m);
+}
+
+/* v = L^-1 k_x for one point (whitened kernel row). */
+static void whiten_row(const or_model *M, const double *x, double *kbuf, double *v)
+{
+    for (int64_t j = 0; j < M->m; ++j) kbuf[j] = or_kernel_eval(M->kernel, M->ell, M->sf2, x, M->X + 3 * j);
+    fwd_sub(M->L, M->m, kbuf, v);
+}
+
+/* Posterior of plain GPR at n points: mean (n) and, if cov != NULL, the full
+ * n x n covariance; var (n) always.  Sigma(a,b) = k(a,b) - v_a . v_b. */
+void or_posterior(const or_model *M, const double *P, int64_t n, double *mu, double *var, double *cov)
+{
+    int64_t m = M->m;
+    double *V = (double *)malloc(sizeof(double) * n * m);
+#pragma omp parallel
+    {
+        double *kb = (double *)malloc(sizeof(double) * m);
+#pragma omp for schedule(static)
+        for (int64_t a = 0; a < n; ++a) {
+            whiten_row(M, P + 3 * a, kb, V + a * m);
+            mu[a] = dot(V + a * m, M->vy, m);
+            var[a] = or_kernel_eval(M->kernel, M->ell, M->sf2, P + 3 * a, P + 3 * a) - dot(V + a * m, V + a * m, m);
+        }
+        free(kb);
+    }
+    if (cov) {
+#pragma omp parallel for schedule(static)
+        for (int64_t a = 0; a < n; ++a)
+            for (int64_t b = 0; b < n; ++b)
+                cov[a * n + b] = or_kernel_eval(M->kernel, M->ell, M->sf2, P + 3 * a, P + 3 * b) - dot(V + a * m, V + b * m, m);
+    }
+    free(V);
+}
+
+/* Eq. (1) as printed (SGPR form): mu = K_IM K_MM^-1 mu_M,
+ * Sigma = K_II - K_IM K_MM^-1 K_MI + K_IM K_MM^-1 A_M K_MM^-1 K_MI,
+ * with K_MM = K(X,X) (no noise).  Returns 0, or -1 if K_MM is not PD. */
+int or_posterior_sgpr(const or_model *M, const double *muM, const double *AM, const double *P, int64_t n,
+                      double *mu, double *cov)
+{
+    int64_t m = M->m;
+    double *Kmm = (double *)malloc(sizeof(double) * m * m);
+    for (int64_t i = 0; i < m; ++i)
+        for (int64_t j = 0; j < m; ++j)
+            Kmm[i * m + j] = or_kernel_eval(M->kernel, M->ell, M->sf2, M->X + 3 * i, M->X + 3 * j);
+    if (or_cholesky(Kmm, m) != 0) { free(Kmm); return -1; }
+    /* B = K_MM^-1 K_MI  (m x n), column a solves K_MM b = k_a */
+    double *B = (double *)malloc(sizeof(double) * m * n);
+    double *kb = (double *)malloc(sizeof(double) * m), *t = (double *)malloc(sizeof(double) * m);
+    double *Kim = (double *)malloc(sizeof(double) * n * m);
+    for (int64_t a = 0; a < n; ++a) {
+        for (int64_t j = 0; j < m; ++j) {
+            kb[j] = or_kernel_eval(M->kernel, M->ell, M->sf2, P + 3 * a, M->X + 3 * j);
+            Kim[a * m + j] = kb[j];
+        }
+        fwd_sub(Kmm, m, kb, t);
+        back_sub_T(Kmm, m, t, kb);
+        for (int64_t j = 0; j < m; ++j) B[j * n + a] = kb[j];
+    }
+    for (int64_t a = 0; a < n; ++a) {
+        double s = 0.0;
+        for (int64_t j = 0; j < m; ++j) s += B[j * n + a] * muM[j];
+        mu[a] = s;
+    }
+    for (int64_t a = 0; a < n; ++a)
+        for (int64_t b = 0; b < n; ++b) {
+            double kab = or_kernel_eval(M->kernel, M->ell, M->sf2, P + 3 * a, P + 3 * b);
+            double s1 = 0.0, s2 = 0.0;
+            for (int64_t j = 0; j < m; ++j) s1 += Kim[a * m + j] * B[j * n + b];
+            for (int64_t i = 0; i < m; ++i) {
+                double ai = 0.0;
+                for (int64_t j = 0; j < m; ++j) ai += AM[i * m + j] * B[j * n + b];
+                s2 += B[i * n + a] * ai;
+            }
+            cov[a * n + b] = kab - s1 + s2;
+        }
+    free(Kmm); free(B); free(kb); free(t); free(Kim);
+    return 0;
+}
+
+/* ---------------------------------------------------- normal distribution */
+
+double or_norm_cdf(double x) { return 0.5 * erfc(-x / sqrt(2.0)); }
+
+/* Inverse standard normal CDF.  Start from Abramowitz & Stegun 26.2.23
+ * (|error| < 4.5e-4) and polish with three Halley steps on Phi(x) - p, which
+ * converge cubically to full double precision for p >= 1e-300. */
+double or_norm_ppf(double p)
+{
+    if (!(p > 0.0)) return -INFINITY;
+    if (!(p < 1.0)) return INFINITY;
+    int upper = p > 0.5;
+    double q = upper ? 1.0 - p : p; /* exact for p in (0.5,1) */
+    double t = sqrt(-2.0 * log(q));
+    double x = -(t - (2.515517 + 0.802853 * t + 0.010328 * t * t) /
+                     (1.0 + 1.432788 * t + 0.189269 * t * t + 0.001308 * t * t * t));
+    for (int it = 0; it < 3; ++it) {
+        double f = or_norm_cdf(x) - q;
+        double phi = exp(-0.5 * x * x) / sqrt(2.0 * M_PI);
+        if (!(phi > 0.0)) break;
+        double dx = f / phi;
+        x = x - dx / (1.0 + 0.5 * x * dx);
+    }
+    return upper ? -x : x;
+}
+
+/* ln Phi(g), accurate in both tails. */
+static double log_norm_cdf(double g)
+{
+    if (g >= 0.0) return log1p(-0.5 * erfc(g / sqrt(2.0)));
+    double c = 0.5 * erfc(-g / sqrt(2.0));
+    if (c > 0.0) return log(c);
+    /* far lower tail: ln Phi(g) ~ -g^2/2 - ln(-g sqrt(2 pi)) */
+    return -0.5 * g * g - log(-g * sqrt(2.0 * M_PI));
+}
+
+/* --------------------------------------------- counter-based generators */
+
+/* SplitMix64 (Steele, Lea & Flood 2014): the k-th output (k >= 1) of the stream
+ * started at state `seed` is mix(seed + k * 0x9E3779B97F4A7C15). */
+uint64_t or_splitmix64(uint64_t seed, uint64_t k)
+{
+    uint64_t z = seed + k * 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+/* Philox-4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11). */
+void or_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4])
+{
+    uint32_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
+    uint32_t k0 = key_in[0], k1 = key_in[1];
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+        uint64_t p0 = (uint64_t)0xD2511F53u * c0;
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c1 ^ k0, n1 = lo1, n2 = hi0 ^ c3 ^ k1, n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* Uniform in (0,1) from 32 random bits: odd multiples of 2^-24, exact in binary32. */
+static double u01(uint32_t x) { return (double)(((x >> 9) << 1) | 1u) * (1.0 / 16777216.0); }
+
+/* ------------------------------------------------------ orthant estimators */
+
+/* Rank-1 lattice generators: frac(sqrt(p)) for the first primes, as 32-bit
+ * fixed-point fractions (Richtmyer lattice, Genz 1992). */
+static const int PRIMES[15] = {2, 3, 5, 7, 11, 13, 17, 19, 23, 29, 31, 37, 41, 43, 47};
+static uint32_t lattice_gen(int i)
+{
+    double s = sqrt((double)PRIMES[i]);
+    double f = s - floor(s);
+    return (uint32_t)floor(f * 4294967296.0);
+}
+
+/* P(X_i <= b_i for all i), X ~ N(0, L L^T), by Genz's sequential conditioning
+ * over N points of the shifted lattice (point k, dimension i:
+ * U = k*G_i + D_i mod 2^32, u = u01(U), w = |2u - 1|).  shift[] holds D_i. */
+double or_sov_orthant(int d, const double *L, const double *b, int64_t N, const uint32_t *shift)
+{
+    uint32_t G[16];
+    for (int i = 0; i < d - 1; ++i) G[i] = lattice_gen(i);
+    double acc = 0.0;
+    double z[16];
+    for (int64_t k = 0; k < N; ++k) {
+        double f = 1.0;
+        for (int i = 0; i < d; ++i) {
+            double s = 0.0;
+            for (int j = 0; j < i; ++j) s += L[i * d + j] * z[j];
+            double e = or_norm_cdf((b[i] - s) / L[i * d + i]);
+            f *= e;
+            if (!(f > 0.0)) { f = 0.0; break; } /* the sample contributes nothing further */
+            if (i < d - 1) {
+                uint32_t U = (uint32_t)((uint64_t)k * G[i]) + shift[i];
+                double w = fabs(2.0 * u01(U) - 1.0);
+                z[i] = or_norm_ppf(w * e);
+            }
+        }
+        acc += f;
+    }
+    return acc / (double)N;
+}
+
+/* Cholesky of a d x d covariance with the pivot floor used by the cell rule:
+ * a pivot below `floor_` is replaced by floor_ (reading; the paper is silent). */
+static void chol_floor(const double *S, int d, double floor_, double *L)
+{
+    for (int i = 0; i < d * d; ++i) L[i] = 0.0;
+    for (int j = 0; j < d; ++j) {
+        double s = S[j * d + j];
+        for (int k = 0; k < j; ++k) s -= L[j * d + k] * L[j * d + k];
+        if (!(s > floor_)) s = floor_;
+        double ljj = sqrt(s);
+        L[j * d + j] = ljj;
+        for (int i = j + 1; i < d; ++i) {
+            double t = S[i * d + j];
+            for (int k = 0; k < j; ++k) t -= L[i * d + k] * L[j * d + k];
+            L[i * d + j] = t / ljj;
+        }
+    }
+}
+
+#define EST_SOV 0
+#define EST_MC 1
+
+/* Cell level-crossing probability for d corner variables (d = 8 for a cell):
+ * LCP = 1 - P(all < theta) - P(all > theta)  (Sec. 3).
+ * Readings (paper silent): Sigma += tau * max diag * I; pivot floor
+ * 1e-3 * tau * max diag; if sum_c P(Y_c > theta) or sum_c P(Y_c < theta) is below
+ * skip_eps, Boole's inequality bounds the LCP by it and the result is 0; a
+ * cell whose largest variance is below 1e-30 is deterministic.
+ * est = EST_SOV: shifts of cell `cell` are SplitMix64 outputs 8*cell+i+1, top
+ * 32 bits.  est = EST_MC: Philox-4x32-10 with key (seed lo, seed hi) and counter
+ * (sample, cell lo, cell hi, r), r = 0,1 giving 8 normals by Box-Muller. */
+double or_cell_lcp(int d, const double *mu, const double *S, double theta, int est, int64_t N,
+                   uint64_t seed, uint64_t cell, double tau, double skip_eps)
+{
+    double Sj[256], L[256];
+    double maxdiag = 0.0;
+    for (int i = 0; i < d; ++i) if (S[i * d + i] > maxdiag) maxdiag = S[i * d + i];
+    if (!(maxdiag > 1e-30)) {
+        int lo = 1, hi = 1;
+        for (int i = 0; i < d; ++i) { if (!(mu[i] < theta)) lo = 0; if (!(mu[i] > theta)) hi = 0; }
+        return (lo || hi) ? 0.0 : 1.0;
+    }
+    double jit = tau * maxdiag;
+    for (int i = 0; i < d * d; ++i) Sj[i] = S[i];
+    for (int i = 0; i < d; ++i) Sj[i * d + i] += jit;
+    double s_above = 0.0, s_below = 0.0;
+    for (int i = 0; i < d; ++i) {
+        double sd = sqrt(Sj[i * d + i]);
+        s_above += or_norm_cdf((mu[i] - theta) / sd);
+        s_below += or_norm_cdf((theta - mu[i]) / sd);
+    }
+    if (s_above < skip_eps || s_below < skip_eps) return 0.0;
+    chol_floor(Sj, d, 1e-3 * jit, L);
+    double p_lo, p_hi;
+    if (est == EST_SOV) {
+        uint32_t sh[16];
+        for (int i = 0; i < d - 1; ++i) sh[i] = (uint32_t)(or_splitmix64(seed, (uint64_t)cell * 8 + i + 1) >> 32);
+        double b[16];
+        for (int i = 0; i < d; ++i) b[i] = theta - mu[i];
+        p_lo = or_sov_orthant(d, L, b, N, sh);
+        for (int i = 0; i < d; ++i) b[i] = mu[i] - theta;
+        p_hi = or_sov_orthant(d, L, b, N, sh);
+        double v = 1.0 - p_lo - p_hi;
+        return v < 0.0 ? 0.0 : (v > 1.0 ? 1.0 : v);
+    }
+    /* Monte Carlo: fraction of samples whose corners are not all on one side. */
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    int64_t crossed = 0;
+    double z[16], yv[16];
+    for (int64_t k = 0; k < N; ++k) {
+        for (int r = 0; r < (d + 3) / 4; ++r) {
+            uint32_t ctr[4] = {(uint32_t)k, (uint32_t)cell, (uint32_t)(cell >> 32), (uint32_t)r}, o[4];
+            or_philox4x32_10(ctr, key, o);
+            for (int p = 0; p < 2; ++p) {
+                double u1 = u01(o[2 * p]), u2 = u01(o[2 * p + 1]);
+                double rr = sqrt(-2.0 * log(u1));
+                int i0 = 4 * r + 2 * p;
+                if (i0 < 16) z[i0] = rr * cos(2.0 * M_PI * u2);
+                if (i0 + 1 < 16) z[i0 + 1] = rr * sin(2.0 * M_PI * u2);
+            }
+        }
+        int all_lo = 1, all_hi = 1;
+        for (int i = 0; i < d; ++i) {
+            double s = mu[i];
+            for (int j = 0; j <= i; ++j) s += L[i * d + j] * z[j];
+            yv[i] = s;
+            if (!(s < theta)) all_lo = 0;
+            if (!(s > theta)) all_hi = 0;
+        }
+        if (!(all_lo || all_hi)) ++crossed;
+    }
+    (void)p_lo; (void)p_hi;
+    return (double)crossed / (double)N;
+}
+
+/* ------------------------------------------------------------------ grid */
+
+typedef struct {
+    double lo[3], hi[3];
+    int64_t n[3];
+} or_grid;
+
+static double grid_h(const or_grid *g, int d) { return (g->hi[d] - g->lo[d]) / (double)(g->n[d] - 1); }
+static double grid_x(const or_grid *g, int d, int64_t i) { return g->lo[d] + (double)i * grid_h(g, d); }
+
+/* Forward neighbour offsets: the lexicographically positive half of
+ * {-1,0,1}^3 \ 0, in this order; stats slot 2+e holds cov(p, p+off[e]). */
+static const int OFF13[13][3] = {
+    {1, -1, -1}, {1, -1, 0}, {1, -1, 1}, {1, 0, -1}, {1, 0, 0}, {1, 0, 1}, {1, 1, -1}, {1, 1, 0}, {1, 1, 1},
+    {0, 1, -1}, {0, 1, 0}, {0, 1, 1}, {0, 0, 1}};
+
+/* Posterior stats for the grid points in the index box [i0, i1):
+ * out[p*15 + 0] = mu, [1] = var, [2+e] = cov(p, p+OFF13[e]) (NaN off-grid).
+ * Points are ordered x-fastest inside the box.  Whitened rows are computed for
+ * the box grown by one point on each side. */
+void or_stats15_block(const or_model *M, const or_grid *g, const int64_t *i0, const int64_t *i1, double *out)
+{
+    int64_t m = M->m;
+    int64_t e0[3], e1[3], en[3];
+    for (int d = 0; d < 3; ++d) {
+        e0[d] = i0[d] > 0 ? i0[d] - 1 : 0;
+        e1[d] = i1[d] < g->n[d] ? i1[d] + 1 : g->n[d];
+        en[d] = e1[d] - e0[d];
+    }
+    int64_t ne = en[0] * en[1] * en[2];
+    double *V = (double *)malloc(sizeof(double) * ne * m);
+#pragma omp parallel
+    {
+        double *kb = (double *)malloc(sizeof(double) * m);
+#pragma omp for schedule(static)
+        for (int64_t q = 0; q < ne; ++q) {
+            int64_t a = e0[0] + q % en[0], b = e0[1] + (q / en[0]) % en[1], c = e0[2] + q / (en[0] * en[1]);
+            double x[3] = {grid_x(g, 0, a), grid_x(g, 1, b), grid_x(g, 2, c)};
+            whiten_row(M, x, kb, V + q * m);
+        }
+        free(kb);
+    }
+    int64_t bn[3] = {i1[0] - i0[0], i1[1] - i0[1], i1[2] - i0[2]};
+    int64_t nb = bn[0] * bn[1] * bn[2];
+#pragma omp parallel for schedule(static)
+    for (int64_t p = 0; p < nb; ++p) {
+        int64_t a = i0[0] + p % bn[0], b = i0[1] + (p / bn[0]) % bn[1], c = i0[2] + p / (bn[0] * bn[1]);
+        int64_t q = (a - e0[0]) + en[0] * ((b - e0[1]) + en[1] * (c - e0[2]));
+        double x[3] = {grid_x(g, 0, a), grid_x(g, 1, b), grid_x(g, 2, c)};
+        double *o = out + p * 15;
+        o[0] = dot(V + q * m, M->vy, m);
+        o[1] = or_kernel_eval(M->kernel, M->ell, M->sf2, x, x) - dot(V + q * m, V + q * m, m);
+        for (int e = 0; e < 13; ++e) {
+            int64_t a2 = a + OFF13[e][0], b2 = b + OFF13[e][1], c2 = c + OFF13[e][2];
+            if (a2 < 0 || b2 < 0 || c2 < 0 || a2 >= g->n[0] || b2 >= g->n[1] || c2 >= g->n[2]) { o[2 + e] = NAN; continue; }
+            int64_t q2 = (a2 - e0[0]) + en[0] * ((b2 - e0[1]) + en[1] * (c2 - e0[2]));
+            double x2[3] = {grid_x(g, 0, a2), grid_x(g, 1, b2), grid_x(g, 2, c2)};
+            o[2 + e] = or_kernel_eval(M->kernel, M->ell, M->sf2, x, x2) - dot(V + q * m, V + q2 * m, m);
+        }
+    }
+    free(V);
+}
+
+/* LCP of the cells whose min-corner index lies in the box [c0, c1), written
+ * x-fastest inside the box.  The 8x8 corner covariance of each cell is formed
+ * directly as K_88 - V_8 V_8^T from the corners' whitened rows (Sec. 3, the
+ * baseline dense method).  Corner c = bx + 2 by + 4 bz.  The cell index used
+ * to key the estimator is the linear index of the cell in the whole grid. */
+void or_lcp_block(const or_model *M, const or_grid *g, double theta, int est, int64_t N, uint64_t seed,
+                  double tau, double skip_eps, const int64_t *c0, const int64_t *c1, double *out)
+{
+    int64_t m = M->m;
+    int64_t pn[3];
+    for (int d = 0; d < 3; ++d) pn[d] = c1[d] - c0[d] + 1;
+    int64_t np = pn[0] * pn[1] * pn[2];
+    double *V = (double *)malloc(sizeof(double) * np * m);
+#pragma omp parallel
+    {
+        double *kb = (double *)malloc(sizeof(double) * m);
+#pragma omp for schedule(static)
+        for (int64_t q = 0; q < np; ++q) {
+            int64_t a = c0[0] + q % pn[0], b = c0[1] + (q / pn[0]) % pn[1], c = c0[2] + q / (pn[0] * pn[1]);
+            double x[3] = {grid_x(g, 0, a), grid_x(g, 1, b), grid_x(g, 2, c)};
+            whiten_row(M, x, kb, V + q * m);
+        }
+        free(kb);
+    }
+    int64_t cn[3] = {c1[0] - c0[0], c1[1] - c0[1], c1[2] - c0[2]};
+    int64_t nc = cn[0] * cn[1] * cn[2];
+    int64_t gc[3] = {g->n[0] - 1, g->n[1] - 1, g->n[2] - 1};
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t p = 0; p < nc; ++p) {
+        int64_t a = c0[0] + p % cn[0], b = c0[1] + (p / cn[0]) % cn[1], c = c0[2] + p / (cn[0] * cn[1]);
+        int64_t q[8];
+        double x[8][3], mu[8], S[64];
+        for (int cc = 0; cc < 8; ++cc) {
+            int bx = cc & 1, by = (cc >> 1) & 1, bz = (cc >> 2) & 1;
+            q[cc] = (a + bx - c0[0]) + pn[0] * ((b + by - c0[1]) + pn[1] * (c + bz - c0[2]));
+            x[cc][0] = grid_x(g, 0, a + bx); x[cc][1] = grid_x(g, 1, b + by); x[cc][2] = grid_x(g, 2, c + bz);
+            mu[cc] = dot(V + q[cc] * m, M->vy, m);
+        }
+        for (int i = 0; i < 8; ++i)
+            for (int j = 0; j <= i; ++j) {
+                double s = or_kernel_eval(M->kernel, M->ell, M->sf2, x[i], x[j]) - dot(V + q[i] * m, V + q[j] * m, m);
+                S[i * 8 + j] = s; S[j * 8 + i] = s;
+            }
+        uint64_t cell = (uint64_t)(a + gc[0] * (b + gc[1] * c));
+        out[p] = or_cell_lcp(8, mu, S, theta, est, N, seed, cell, tau, skip_eps);
+    }
+    free(V);
+}
+
+/* ---------------------------------------------------- regional bound, octree */
+
+/* g(x) = side * (theta - mu(x)) / sigma(x) and its gradient; side = +1 gives
+ * F = Phi(g) = P(Y < theta), side = -1 gives 1 - F = P(Y > theta) (Sec. 4.1). */
+static double eval_g(const or_model *M, const double *x, double theta, int side, double grad[3],
+                     double *kb, double *dk, double *v, double *P)
+{
+    int64_t m = M->m;
+    for (int64_t j = 0; j < m; ++j) kernel_grad(M->kernel, M->ell, M->sf2, x, M->X + 3 * j, kb + j, dk + 3 * j);
+    fwd_sub(M->L, m, kb, v);
+    double mu = dot(v, M->vy, m);
+    double var = or_kernel_eval(M->kernel, M->ell, M->sf2, x, x) - dot(v, v, m);
+    double fl = 1e-12 * M->sf2;
+    if (!(var > fl)) var = fl;
+    double sd = sqrt(var);
+    back_sub_T(M->L, m, v, P); /* P = Kt^-1 k */
+    double gmu[3] = {0, 0, 0}, gvar[3] = {0, 0, 0};
+    for (int64_t j = 0; j < m; ++j)
+        for (int d = 0; d < 3; ++d) {
+            gmu[d] += dk[3 * j + d] * M->alpha[j];
+            gvar[d] += -2.0 * dk[3 * j + d] * P[j];
+        }
+    double gl = (theta - mu) / sd;
+    for (int d = 0; d < 3; ++d) {
+        double gd = -gmu[d] / sd - gl * gvar[d] / (2.0 * var);
+        grad[d] = side * gd;
+    }
+    return side * gl;
+}
+
+/* Node geometry at level l of a depth-D octree over the cell grid: node (i,j,k)
+ * spans cells [i s, (i+1) s) per axis, s = 2^(D-l), i.e. grid points
+ * [i s, min((i+1) s, n-1)]; its box is the span of those points. */
+static void node_geom(const or_grid *g, int D, int l, const int64_t ijk[3], int64_t p0[3], int64_t p1[3],
+                      double blo[3], double bhi[3])
+{
+    int64_t s = (int64_t)1 << (D - l);
+    for (int d = 0; d < 3; ++d) {
+        p0[d] = ijk[d] * s;
+        p1[d] = (ijk[d] + 1) * s;
+        if (p1[d] > g->n[d] - 1) p1[d] = g->n[d] - 1;
+        blo[d] = grid_x(g, d, p0[d]);
+        bhi[d] = grid_x(g, d, p1[d]);
+    }
+}
+
+/* min over the node of g(x) for one side.  Reading of the paper's L-BFGS-B
+ * step (the minimiser is not specified beyond "quasi-Newton"): when the node
+ * has at most 3 grid points per axis, the minimum is taken exactly over its
+ * grid points; otherwise over the continuous box, starting from the best of the
+ * 3x3x3 lattice (corners, edge/face midpoints, centre; first in x-fastest order
+ * on ties) and taking T projected steps x' = clamp(x + eta_t * w * u/|u|_inf),
+ * u = -grad g * w (w = box widths), eta_t = 0.25 * 2^-t, each kept only if it
+ * lowers g. */
+static double node_min_g(const or_model *M, const or_grid *g, const int64_t p0[3], const int64_t p1[3],
+                         const double blo[3], const double bhi[3], double theta, int side, int T,
+                         double *kb, double *dk, double *v, double *P)
+{
+    double grad[3];
+    int small = 1;
+    for (int d = 0; d < 3; ++d) if (p1[d] - p0[d] + 1 > 3) small = 0;
+    if (small) {
+        double best = INFINITY;
+        for (int64_t c = p0[2]; c <= p1[2]; ++c)
+            for (int64_t b = p0[1]; b <= p1[1]; ++b)
+                for (int64_t a = p0[0]; a <= p1[0]; ++a) {
+                    double x[3] = {grid_x(g, 0, a), grid_x(g, 1, b), grid_x(g, 2, c)};
+                    double val = eval_g(M, x, theta, side, grad, kb, dk, v, P);
+                    if (val < best) best = val;
+                }
+        return best;
+    }
+    double bx[3], bestg = INFINITY, bestgrad[3] = {0, 0, 0};
+    for (int t = 0; t < 27; ++t) {
+        int ia = t % 3, ib = (t / 3) % 3, ic = t / 9;
+        int id[3] = {ia, ib, ic};
+        double x[3];
+        for (int d = 0; d < 3; ++d) x[d] = blo[d] + 0.5 * (double)id[d] * (bhi[d] - blo[d]);
+        double val = eval_g(M, x, theta, side, grad, kb, dk, v, P);
+        if (val < bestg) { bestg = val; for (int d = 0; d < 3; ++d) { bx[d] = x[d]; bestgrad[d] = grad[d]; } }
+    }
+    for (int t = 0; t < T; ++t) {
+        double w[3], u[3], un = 0.0;
+        for (int d = 0; d < 3; ++d) {
+            w[d] = bhi[d] - blo[d];
+            u[d] = -bestgrad[d] * w[d];
+            if (fabs(u[d]) > un) un = fabs(u[d]);
+        }
+        if (!(un > 0.0)) break;
+        double eta = 0.25 * ldexp(1.0, -t), xc[3];
+        for (int d = 0; d < 3; ++d) {
+            double xn = bx[d] + eta * w[d] * u[d] / un;
+            xc[d] = xn < blo[d] ? blo[d] : (xn > bhi[d] ? bhi[d] : xn);
+        }
+        double val = eval_g(M, xc, theta, side, grad, kb, dk, v, P);
+        if (val < bestg) { bestg = val; for (int d = 0; d < 3; ++d) { bx[d] = xc[d]; bestgrad[d] = grad[d]; } }
+    }
+    return bestg;
+}
+
+/* One level of Algorithm 1 for `count` nodes (packed i | j<<21 | k<<42).
+ * Per node: decision[q] = 0 (drop), 1 (subdivide: p1 > alpha and p2 > alpha),
+ * 2 (subdivide: bound > alpha); bound[q] = the upper bound used (NaN for 1);
+ * side[q] = 0 both sides, 1 lower only (p2 <= alpha), 2 upper only (p1 <= alpha).
+ * The p-test uses the observations inside the closed node box with the latent
+ * posterior at the observations.  d = number of grid points in the node. */
+void or_octree_level(const or_model *M, const or_grid *g, int D, int l, double theta, double alpha, int T,
+                     const int64_t *nodes, int64_t count, int8_t *decision, double *bound, int8_t *side_out)
+{
+    int64_t m = M->m;
+    int8_t *flo = (int8_t *)malloc((size_t)m), *fhi = (int8_t *)malloc((size_t)m);
+    for (int64_t i = 0; i < m; ++i) {
+        double sd = sqrt(M->var_obs[i]);
+        flo[i] = or_norm_cdf((theta - M->mu_obs[i]) / sd) > alpha;
+        fhi[i] = or_norm_cdf((M->mu_obs[i] - theta) / sd) > alpha;
+    }
+#pragma omp parallel
+    {
+        double *kb = (double *)malloc(sizeof(double) * m), *dk = (double *)malloc(sizeof(double) * 3 * m);
+        double *v = (double *)malloc(sizeof(double) * m), *P = (double *)malloc(sizeof(double) * m);
+#pragma omp for schedule(dynamic, 1)
+        for (int64_t q = 0; q < count; ++q) {
+            int64_t ijk[3] = {nodes[q] & 0x1FFFFF, (nodes[q] >> 21) & 0x1FFFFF, (nodes[q] >> 42) & 0x1FFFFF};
+            int64_t p0[3], p1[3];
+            double blo[3], bhi[3];
+            node_geom(g, D, l, ijk, p0, p1, blo, bhi);
+            int any = 0, anylo = 0, anyhi = 0;
+            for (int64_t i = 0; i < m; ++i) {
+                const double *x = M->X + 3 * i;
+                if (x[0] >= blo[0] && x[0] <= bhi[0] && x[1] >= blo[1] && x[1] <= bhi[1] && x[2] >= blo[2] && x[2] <= bhi[2]) {
+                    any = 1; anylo |= flo[i]; anyhi |= fhi[i];
+                }
+            }
+            if (any && anylo && anyhi) { decision[q] = 1; bound[q] = NAN; side_out[q] = 0; continue; }
+            int do_lo, do_hi;
+            if (!any || (!anylo && !anyhi)) { do_lo = 1; do_hi = 1; }
+            else if (!anyhi) { do_lo = 1; do_hi = 0; }
+            else { do_lo = 0; do_hi = 1; }
+            double dcount = (double)((p1[0] - p0[0] + 1) * (p1[1] - p0[1] + 1) * (p1[2] - p0[2] + 1));
+            double lB_lo = -INFINITY, lB_hi = -INFINITY; /* ln B; B = 0 when the side is not used */
+            if (do_lo) lB_lo = log_norm_cdf(node_min_g(M, g, p0, p1, blo, bhi, theta, +1, T, kb, dk, v, P));
+            if (do_hi) lB_hi = log_norm_cdf(node_min_g(M, g, p0, p1, blo, bhi, theta, -1, T, kb, dk, v, P));
+            double bnd;
+            if (do_lo && do_hi) bnd = -expm1(dcount * lB_lo) - exp(dcount * lB_hi);
+            else if (do_lo) bnd = -expm1(dcount * lB_lo);
+            else bnd = -expm1(dcount * lB_hi);
+            bound[q] = bnd;
+            side_out[q] = (int8_t)((do_lo && do_hi) ? 0 : (do_lo ? 1 : 2));
+            decision[q] = bnd > alpha ? 2 : 0;
+        }
+        free(kb); free(dk); free(v); free(P);
+    }
+    free(flo); free(fhi);
+}
+
+/* g at arbitrary points (test hook for the minimiser pins). */
+void or_eval_g(const or_model *M, const double *x, int64_t n, double theta, int side, double *g_out, double *grad_out)
+{
+    int64_t m = M->m;
+    double *kb = (double *)malloc(sizeof(double) * m), *dk = (double *)malloc(sizeof(double) * 3 * m);
+    double *v = (double *)malloc(sizeof(double) * m), *P = (double *)malloc(sizeof(double) * m);
+    for (int64_t q = 0; q < n; ++q) g_out[q] = eval_g(M, x + 3 * q, theta, side, grad_out + 3 * q, kb, dk, v, P);
+    free(kb); free(dk); free(v); free(P);
+}
+
+int or_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
