@@ -1,0 +1,299 @@
+#!/usr/bin/env python
+"""LCP-field throughput on the paper-scale synthetic GP field, through the C ABI.
+
+Workload (one step): build the GP model from m=500 observations (anisotropic SE,
+lengths (0.15, 0.2, 0.25), noise 1e-4) and compute the level-crossing probability
+field of a 128^3 grid (127^3 cells, 1600-sample SOV-QMC estimator) at the 25th,
+50th and 75th percentile of y.  Metric: target grid points per second
+(3 x 128^3 points per step), as the paper reports seconds per field (Sec. 6.1).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--mode adaptive|dense]
+  python bench.py --impl reference ...   # the FP64 CPU oracle on host cores
+
+Prints one JSON line (rank 0).  Under torchrun each rank runs an independent replica
+(weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads  # noqa: E402
+
+METRIC = "LCP grid points/s"
+UNIT = "grid points/s"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--mode", default="dense", choices=["dense", "adaptive"])
+    p.add_argument("--prec", default="fp32", choices=["fp32", "fp64"])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-sample", type=int, default=20, help="cells per axis of the oracle sample")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0])); mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(w, theta, cells_per_axis):
+    """The FP64 oracle as it stands, on a bounded block of cells straddling the field."""
+    import oracle
+    t0 = time.perf_counter()
+    om = oracle.Model.from_workload(w)
+    c0 = (w.n - 1) // 2 - cells_per_axis // 2
+    c = (c0, c0, c0)
+    c1 = tuple(v + cells_per_axis for v in c)
+    om.lcp_block(w.n, theta, c, c1)
+    dt = time.perf_counter() - t0
+    cells = cells_per_axis ** 3
+    return {"value": cells / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"model set-up + SOV-1600 LCP of a {cells_per_axis}^3-cell block at the median isovalue "
+                      f"({cells} cells ~ grid points), {dt:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    w = workloads.config2()
+    import oracle
+    theta = w.isovalues[1]
+    k = max(6, args.cpu_sample // 2)
+    times = []
+    for s in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        om = oracle.Model.from_workload(w)
+        c0 = (w.n - 1) // 2 - k // 2
+        om.lcp_block(w.n, theta, (c0, c0, c0), (c0 + k, c0 + k, c0 + k))
+        if s >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    t = sum(times) / len(times)
+    v = k ** 3 / t
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": w.name + " x3 isovalues", "sample": f"{k}^3 cells at the median isovalue"},
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                            "sample": f"{k}^3-cell block per step, model set-up included"},
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    import paper_2512_12442_gb300 as g
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    w = workloads.config2()
+    n = w.n
+    ncell = (n - 1) ** 3
+    grid = g.make_grid(n)
+    prec = g.GPR_P_FP64 if args.prec == "fp64" else g.GPR_P_FP32
+    opts = g.lcp_options(prec=prec)
+    stream = torch.cuda.current_stream()
+    fields = [torch.zeros(ncell, dtype=torch.float32, device="cuda") for _ in w.isovalues]
+    host = [torch.zeros(ncell, dtype=torch.float32).pin_memory() for _ in w.isovalues]
+    stats_last = {}
+
+    def step(e2e=False):
+        M = g.gpr_model_create(w.X, w.y, w.kernel, w.ell, w.sf2, w.sn2, stream=stream)
+        for t, th in enumerate(w.isovalues):
+            if args.mode == "dense":
+                st = g.gpr_lcp_dense(M, grid, th, opts, fields[t], stream=stream)
+            else:
+                st = g.gpr_lcp_adaptive(M, grid, th, w.max_depth, opts, fields[t], stream=stream)
+            stats_last[t] = st
+            if e2e:
+                host[t].copy_(fields[t], non_blocking=True)
+        return M
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        M = step()
+        M.close()
+    g.gpr_sync(stream)
+
+    # timed region: device-resident inputs
+    barrier()
+    g.gpr_profile_reset()
+    g.gpr_profile_enable(True)
+    with ClockSampler(local) as clk:
+        ev0 = torch.cuda.Event(enable_timing=True); ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            M = step()
+        ev1.record(stream)
+        barrier()
+    g.gpr_profile_enable(False)
+    launches = g.gpr_launch_count()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    prof = {k: g.gpr_profile_read(k) for k in ("w64", "meanvar32", "stats_from_w64", "cell_prep", "sov", "classify")}
+    g.gpr_sync(stream)
+    M.close()
+    t_max = ms
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    pts_per_step = len(w.isovalues) * n ** 3
+    value = world * pts_per_step / (t_max / 1e3)
+
+    # end-to-end: host inputs in, fields copied back to pinned host memory every step
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        M = step(e2e=True)
+        M.close()
+    e1.record(stream)
+    barrier()
+    ms_e2e = e0.elapsed_time(e1) / args.steps
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms_e2e], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_e2e = float(t.item())
+
+    if rank != 0:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+
+    # roofline of the dominant kernel
+    dom = max(prof, key=lambda k: prof[k][0])
+    m = w.m
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    recon = sum(stats_last[t]["recon_points"] for t in stats_last)
+    roof = None
+    if dom == "w64" and prof["w64"][1] > 0:
+        # algorithmic FLOPs of the triangular whitening GEMM: 2 * sum_{j<m} (j+1) per point
+        flops_per_launch = recon / len(stats_last) * m * (m + 1)
+        avg_s = prof["w64"][0] / prof["w64"][1] / 1e3
+        achieved = flops_per_launch / avg_s / 1e12
+        peak = 2.0 * 2 * 152 * 2.07e9 / 1e12  # FP64: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz (derived)
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "k_w_store<double> (FP64 whitening GEMM)",
+                "peak_source": "derived FP64 issue rate (not in MEASURED_PEAKS.json)"}
+    cpu = None if args.no_cpu_baseline else cpu_baseline(w, w.isovalues[1], args.cpu_sample)
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t_max, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if True else "f32", "data": "synthetic",
+        "config": {"workload": f"{w.name}, 3 isovalues (P25/P50/P75 of y), SOV-QMC 1600, {args.mode}",
+                   "m": m, "grid": n, "mode": args.mode, "prepass": args.prec,
+                   "l2": "working set > L2 (FP64 whitened rows of the kept points, GBs)",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": roof,
+        "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
+        "kept_cells": [stats_last[t]["leaf_cells"] for t in stats_last],
+        "recon_points": [stats_last[t]["recon_points"] for t in stats_last],
+        "cpu_baseline": cpu,
+        "e2e": {"value": world * pts_per_step / (ms_e2e / 1e3), "unit": UNIT,
+                "h2d_bytes_per_step": int(w.X.nbytes + w.y.nbytes),
+                "d2h_bytes_per_step": int(len(w.isovalues) * ncell * 4)},
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+        "measured_peaks": {k: peaks.get(k) for k in ("hbm_gbs", "bf16_tflops", "bf16_tflops_sustained")},
+    }
+    print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

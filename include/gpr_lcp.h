@@ -1,0 +1,221 @@
+/*
+ * gpr_lcp.h -- C ABI of the GB300 library for Gaussian-process reconstruction
+ * and level-crossing probability (LCP) fields.
+ *
+ * Method: Li, Michaud, Biswas, Shen, "Efficient Level-Crossing Probability
+ * Calculation for Gaussian Process Modeled Data".  Paper passages are cited as
+ * Sec./Eq./Algorithm numbers.
+ *
+ * Conventions shared by every entry point
+ *   - All calls return gpr_status.  Argument errors are detected on the host
+ *     and returned before any work is queued.  Errors raised on the device
+ *     (non positive-definite K, a bounded wait that ran out) are written to the
+ *     model's device status word and returned by gpr_sync() or by the next
+ *     call that synchronises.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *     stream).  Work is queued asynchronously on it unless stated otherwise.
+ *   - Pointers marked "device" must be device (or managed) memory of the
+ *     current CUDA device; pointers marked "host" must be host memory.
+ *     Caller-owned buffers are never freed by the library.
+ *   - Grids: n[d] >= 2 points per axis, coordinates x_i = lo + i (hi-lo)/(n-1),
+ *     linear point index i + n0 (j + n1 k) (x fastest).  Cells are indexed by
+ *     their minimum corner, linear index i + (n0-1)(j + (n1-1) k); a cell's
+ *     corner c = bx + 2 by + 4 bz sits at (i+bx, j+by, k+bz).
+ *   - Per-point statistics ("stats15"): slot 0 = posterior mean, 1 = variance,
+ *     2+e = covariance with the forward neighbour p + OFF[e], where OFF is
+ *     (1,-1,-1) (1,-1,0) (1,-1,1) (1,0,-1) (1,0,0) (1,0,1) (1,1,-1) (1,1,0)
+ *     (1,1,1) (0,1,-1) (0,1,0) (0,1,1) (0,0,1); NaN where the neighbour is off
+ *     the grid.  These 15 numbers per point determine every cell's 8x8 corner
+ *     covariance (Sec. 3).
+ */
+#ifndef GPR_LCP_H
+#define GPR_LCP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gpr_model gpr_model; /* opaque; owns its device buffers */
+
+typedef enum {
+    GPR_OK = 0,
+    GPR_ERR_ARG = 1,         /* invalid argument (host check) */
+    GPR_ERR_NOT_PD = 2,      /* K(X,X) + noise I not positive definite */
+    GPR_ERR_CUDA = 3,        /* a CUDA runtime call failed */
+    GPR_ERR_OOM = 4,         /* device allocation failed */
+    GPR_ERR_TIMEOUT = 5,     /* a bounded device wait ran out */
+    GPR_ERR_UNSUPPORTED = 6  /* valid request this build does not serve */
+} gpr_status;
+
+typedef enum { GPR_K_SE = 0, GPR_K_MATERN52 = 1 } gpr_kernel;
+
+/* Arithmetic of the O(m^2 n) contraction (the Cholesky, the inverse and the
+ * solves are FP64 in every mode).  GPR_P_FP64 is the only mode whose
+ * covariances are accurate enough for the cell LCP; the others serve the
+ * posterior mean/variance, the octree bounds and the LCP pre-classification. */
+typedef enum {
+    GPR_P_FP64 = 0,   /* FP64 CUDA cores */
+    GPR_P_FP32 = 1,   /* FP32 CUDA cores */
+    GPR_P_TF32 = 2,   /* tcgen05 kind::tf32, FP32 accumulate in TMEM */
+    GPR_P_TF32X3 = 3, /* three TF32 products (hi*hi + hi*lo + lo*hi) */
+    GPR_P_BF16 = 4,   /* tcgen05 kind::f16 with bf16 operands */
+    GPR_P_BF16X3 = 5  /* three bf16 slices, six products */
+} gpr_precision;
+
+typedef enum { GPR_EST_SOV_QMC = 0, GPR_EST_MC = 1 } gpr_estimator;
+
+typedef struct {
+    double lo[3], hi[3];
+    int32_t n[3]; /* points per axis */
+} gpr_grid;
+
+/* Options of the LCP calls.  Defaults come from gpr_lcp_options_default(). */
+typedef struct {
+    double alpha;          /* octree threshold (Algorithm 1), default 1e-3 (Sec. 6.3) */
+    double beta;           /* local-GP radius in length scales (Sec. 4.2), default 6; unused by this build */
+    gpr_estimator est;     /* cell estimator, default SOV-QMC */
+    int32_t n_samples;     /* samples per cell, default 1600 (Sec. 5.4) */
+    uint64_t seed;         /* lattice shifts / Philox key */
+    double jitter;         /* tau: Sigma_8 += tau * max diag * I, default 1e-4 */
+    double skip_eps;       /* Boole pre-skip threshold, default 1e-9 */
+    gpr_precision prec;    /* precision of the pre-classification / octree pass, default GPR_P_FP32 */
+    int32_t max_iters_min; /* projected steps T of the box minimiser, default 4 */
+} gpr_lcp_options;
+
+typedef struct {
+    int64_t nodes_per_level[24];   /* nodes evaluated at each level of Algorithm 1 */
+    int64_t subdiv_per_level[24];  /* nodes subdivided at each level */
+    int64_t leaf_cells;            /* |S|: cells kept at the deepest level */
+    int64_t recon_points;          /* grid points reconstructed in FP64 */
+    int64_t cells_estimated;       /* cells that ran the estimator (not pre-skipped) */
+} gpr_adaptive_stats;
+
+/* Fills the defaults listed above. */
+void gpr_lcp_options_default(gpr_lcp_options *opts);
+
+/* Human-readable name of a status code (static storage). */
+const char *gpr_status_string(gpr_status s);
+
+/*
+ * gpr_model_create -- builds the stored GP model (Sec. 3, Eq. 1 with the
+ * observations as inducing set):  Kt = K(X,X) + noise_var I = L L^T (FP64
+ * blocked Cholesky on the device), L^-1, v = L^-1 y, alpha = Kt^-1 y, and the
+ * latent posterior at the observations (mean y - noise_var alpha, variance
+ * noise_var - noise_var^2 [Kt^-1]_ii) used by Algorithm 1's p1/p2 test.
+ *   obs_xyz  host, m x 3 row-major FP64 observation sites
+ *   y        host, m FP64 observation values
+ *   m        1 <= m <= 8192
+ *   kernel   GPR_K_SE: k = s exp(-sum_d (dx_d/l_d)^2 / 2)  (the paper's RBF,
+ *            Sec. 3, with one length per axis); GPR_K_MATERN52: the
+ *            Matern-5/2 function of r = |dx / l|
+ *   length_scales host[3] > 0;  signal_var > 0;  noise_var >= 0
+ *   stream   queue for the set-up kernels
+ *   out      receives the model; the call synchronises `stream` and returns
+ *            GPR_ERR_NOT_PD if a Cholesky pivot is not positive.
+ * The model owns its device memory until gpr_model_destroy().
+ */
+gpr_status gpr_model_create(const double *obs_xyz, const double *y, int64_t m, gpr_kernel kernel,
+                            const double length_scales[3], double signal_var, double noise_var,
+                            void *stream, gpr_model **out);
+
+/* Frees the model and its workspace (synchronises the device first). */
+gpr_status gpr_model_destroy(gpr_model *model);
+
+/* Observation count of a model. */
+int64_t gpr_model_m(const gpr_model *model);
+
+/*
+ * gpr_reconstruct_dense -- posterior statistics at every grid point (Eq. 1):
+ * mean mu(x) = k_x^T Kt^-1 y and variance k(x,x) - k_x^T Kt^-1 k_x, computed in
+ * the whitened form w = L^-1 k_x (mu = w . L^-1 y, var = k(x,x) - |w|^2), with
+ * kernel rows generated on the fly (never stored).
+ *   prec == GPR_P_FP64: mean/var/cov13 are double* (device, n, n, n x 13).
+ *   other precisions:   mean/var/cov13 are float*.
+ *   cov13 may be NULL; if given, slot e holds cov(p, p + OFF[e]) (see top).
+ *   The call may grow the model's workspace (cudaMalloc) on first use of a
+ *   larger grid.
+ */
+gpr_status gpr_reconstruct_dense(gpr_model *model, const gpr_grid *grid, gpr_precision prec,
+                                 void *mean, void *var, void *cov13, void *stream);
+
+/*
+ * gpr_stats_points -- stats15 (FP64) for an arbitrary list of grid points.
+ *   point_idx  device, count int64 linear grid indices
+ *   stats      device, count x 15 double (layout above); covariances whose
+ *              neighbour is not in the list are NaN
+ */
+gpr_status gpr_stats_points(gpr_model *model, const gpr_grid *grid, const int64_t *point_idx, int64_t count,
+                            double *stats, void *stream);
+
+/*
+ * gpr_cell_lcp_from_stats -- cell LCP (Sec. 3): LCP = 1 - P(all 8 corners <
+ * theta) - P(all 8 corners > theta) for the listed cells, from FP64 stats15 of
+ * a full grid (device, n x 15 double).  Sigma_8 gets jitter*max(diag) on its
+ * diagonal; if sum_c P(Y_c > theta) or sum_c P(Y_c < theta) is below skip_eps
+ * the LCP is 0 (Boole's inequality); otherwise the estimator of opts->est runs:
+ *   SOV-QMC: Genz's sequential conditioning over corners 0..7 in index order,
+ *            n_samples points of the rank-1 lattice with generators frac(sqrt p)
+ *            (p = 2,3,5,...,17) as 32-bit fractions, shifted per cell by the
+ *            SplitMix64 outputs 8 cell + i + 1 (top 32 bits), tent-periodised.
+ *   MC:      the paper's estimator: n_samples draws of the 8-variate Gaussian
+ *            (Philox-4x32-10, key = seed, counter = (sample, cell, 0|1), Box-
+ *            Muller), LCP = fraction of draws whose corners straddle theta.
+ *   cell_idx  device, count int64 linear cell indices (NULL = every cell, in order)
+ *   lcp       device float, count values (or every cell when cell_idx is NULL)
+ */
+gpr_status gpr_cell_lcp_from_stats(const gpr_grid *grid, const double *stats15, double isovalue,
+                                   const gpr_lcp_options *opts, const int64_t *cell_idx, int64_t count,
+                                   float *lcp, void *stream);
+
+/*
+ * gpr_lcp_dense -- the dense baseline LCP field (Sec. 3, Sec. 5.4): every cell's
+ * LCP.  A pre-pass in opts->prec computes mean/variance at all points and drops
+ * cells whose Boole bound, widened by a margin that covers that precision's
+ * error, is below skip_eps; the remaining cells' corners are reconstructed in
+ * FP64 and estimated.  Result equals the all-FP64 computation.
+ *   lcp  device float, (n0-1)(n1-1)(n2-1) values
+ */
+gpr_status gpr_lcp_dense(gpr_model *model, const gpr_grid *grid, double isovalue, const gpr_lcp_options *opts,
+                         float *lcp, gpr_adaptive_stats *stats, void *stream);
+
+/*
+ * gpr_lcp_adaptive -- Algorithm 1 (Sec. 4.3) then leaf reconstruction: the
+ * octree over the cell grid (root = cells [0, 2^D)^3) is refined level by level
+ * on the device.  A node is subdivided when the observations inside it have
+ * p1 > alpha and p2 > alpha, or when the regional upper bound 1 - B_l^d - B_u^d
+ * (Eq. upper_bound; one-sided when the p-test says so) exceeds alpha; B is the
+ * minimum of Phi(+-(theta - mu)/sigma) over the node (exact over grid points
+ * when the node has <= 3 points per axis, else a 3x3x3 lattice start plus
+ * opts->max_iters_min projected gradient steps).  Cells kept at depth D form S;
+ * their LCP is computed exactly as gpr_lcp_dense does and all other cells are 0.
+ *   max_depth  D with 2^D >= n_d - 1 for every axis, D <= 20
+ *   lcp        device float, one value per cell
+ *   stats      host, nullable: per-level counts and |S|
+ */
+gpr_status gpr_lcp_adaptive(gpr_model *model, const gpr_grid *grid, double isovalue, int32_t max_depth,
+                            const gpr_lcp_options *opts, float *lcp, gpr_adaptive_stats *stats, void *stream);
+
+/* Waits for `stream` and returns the first device-side error recorded by any
+ * model since the last call (GPR_OK if none). */
+gpr_status gpr_sync(void *stream);
+
+/* ---- Tracing (no counterpart in the paper; the paper reports per-phase wall time,
+ * Sec. 5.2).  When enabled, the library records CUDA events on the launching stream
+ * around its main kernels, grouped by name ("w64", "meanvar32", "stats_from_w64",
+ * "cell_prep", "sov", "mc", "classify", ...). */
+void gpr_profile_enable(int on);
+/* Clears the accumulated times and the launch counter. */
+void gpr_profile_reset(void);
+/* Synchronises the recorded events; total milliseconds and launches of `name`.
+ * Returns 1 if the name was seen, else 0 (outputs zeroed).  Pointers are host. */
+int gpr_profile_read(const char *name, double *total_ms, int64_t *count);
+/* Number of the library's own kernel launches since the last reset. */
+int64_t gpr_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GPR_LCP_H */

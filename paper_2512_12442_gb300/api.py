@@ -1,0 +1,178 @@
+"""Thin Python binding of the C ABI (include/gpr_lcp.h): same names, argument
+marshalling only.  Device buffers are torch CUDA tensors (or raw integer device
+pointers); every computation runs in libgprlcp.so.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from ._lib import AdaptiveStatsC, GridC, LcpOptionsC, load
+
+GPR_K_SE, GPR_K_MATERN52 = 0, 1
+GPR_P_FP64, GPR_P_FP32, GPR_P_TF32, GPR_P_TF32X3, GPR_P_BF16, GPR_P_BF16X3 = range(6)
+GPR_EST_SOV_QMC, GPR_EST_MC = 0, 1
+GPR_OK, GPR_ERR_ARG, GPR_ERR_NOT_PD, GPR_ERR_CUDA, GPR_ERR_OOM, GPR_ERR_TIMEOUT, GPR_ERR_UNSUPPORTED = range(7)
+
+
+class GPRError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = int(status)
+        msg = load().gpr_status_string(int(status)).decode()
+        super().__init__(f"{where}: {msg} (status {status})")
+
+
+def _check(rc: int, where: str):
+    if rc != GPR_OK:
+        raise GPRError(rc, where)
+
+
+def _ptr(t, dtype=None, allow_none=False):
+    """Device pointer of a torch CUDA tensor (contiguous) or an int pointer."""
+    if t is None:
+        if allow_none:
+            return None
+        raise ValueError("buffer required")
+    if isinstance(t, int):
+        return t
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"expected dtype {dtype}, got {t.dtype}")
+    return t.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def make_grid(n, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0)) -> GridC:
+    if np.isscalar(n):
+        n = (n, n, n)
+    g = GridC()
+    for d in range(3):
+        g.lo[d], g.hi[d], g.n[d] = float(lo[d]), float(hi[d]), int(n[d])
+    return g
+
+
+def lcp_options(**kw) -> LcpOptionsC:
+    o = LcpOptionsC()
+    load().gpr_lcp_options_default(C.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+class Model:
+    """Owns a gpr_model handle; destroyed with the object."""
+
+    def __init__(self, handle: int):
+        self.handle = handle
+
+    @property
+    def m(self) -> int:
+        return int(load().gpr_model_m(self.handle))
+
+    def close(self):
+        if self.handle:
+            load().gpr_model_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def gpr_model_create(obs_xyz, y, kernel=GPR_K_SE, length_scales=(0.2, 0.2, 0.2), signal_var=1.0,
+                     noise_var=1e-4, stream=None) -> Model:
+    X = np.ascontiguousarray(obs_xyz, np.float64).reshape(-1, 3)
+    yy = np.ascontiguousarray(y, np.float64).reshape(-1)
+    ell = np.ascontiguousarray(length_scales, np.float64).reshape(3)
+    h = C.c_void_p()
+    rc = load().gpr_model_create(X.ctypes.data, yy.ctypes.data, yy.shape[0], int(kernel), ell.ctypes.data,
+                                 float(signal_var), float(noise_var), _stream(stream), C.byref(h))
+    _check(rc, "gpr_model_create")
+    return Model(h.value)
+
+
+def gpr_reconstruct_dense(model: Model, grid: GridC, prec, mean, var, cov13=None, stream=None):
+    rc = load().gpr_reconstruct_dense(model.handle, C.byref(grid), int(prec), _ptr(mean), _ptr(var),
+                                      _ptr(cov13, allow_none=True), _stream(stream))
+    _check(rc, "gpr_reconstruct_dense")
+
+
+def gpr_stats_points(model: Model, grid: GridC, point_idx, stats, stream=None):
+    n = 0 if point_idx is None else int(point_idx.numel())
+    rc = load().gpr_stats_points(model.handle, C.byref(grid), _ptr(point_idx, allow_none=True), n,
+                                 _ptr(stats, allow_none=True), _stream(stream))
+    _check(rc, "gpr_stats_points")
+
+
+def gpr_cell_lcp_from_stats(grid: GridC, stats15, isovalue, opts: LcpOptionsC, cell_idx, lcp, stream=None):
+    n = 0 if cell_idx is None else int(cell_idx.numel())
+    rc = load().gpr_cell_lcp_from_stats(C.byref(grid), _ptr(stats15), float(isovalue), C.byref(opts),
+                                        _ptr(cell_idx, allow_none=True), n, _ptr(lcp), _stream(stream))
+    _check(rc, "gpr_cell_lcp_from_stats")
+
+
+def _stats_dict(s: AdaptiveStatsC) -> dict:
+    return {"nodes_per_level": list(s.nodes_per_level), "subdiv_per_level": list(s.subdiv_per_level),
+            "leaf_cells": s.leaf_cells, "recon_points": s.recon_points, "cells_estimated": s.cells_estimated}
+
+
+def gpr_lcp_dense(model: Model, grid: GridC, isovalue, opts: LcpOptionsC, lcp, stream=None) -> dict:
+    s = AdaptiveStatsC()
+    rc = load().gpr_lcp_dense(model.handle, C.byref(grid), float(isovalue), C.byref(opts), _ptr(lcp), C.byref(s),
+                              _stream(stream))
+    _check(rc, "gpr_lcp_dense")
+    return _stats_dict(s)
+
+
+def gpr_lcp_adaptive(model: Model, grid: GridC, isovalue, max_depth, opts: LcpOptionsC, lcp, stream=None) -> dict:
+    s = AdaptiveStatsC()
+    rc = load().gpr_lcp_adaptive(model.handle, C.byref(grid), float(isovalue), int(max_depth), C.byref(opts),
+                                 _ptr(lcp), C.byref(s), _stream(stream))
+    _check(rc, "gpr_lcp_adaptive")
+    return _stats_dict(s)
+
+
+def gpr_sync(stream=None):
+    _check(load().gpr_sync(_stream(stream)), "gpr_sync")
+
+
+def gpr_model_export(model: Model):
+    """Test hook: FP64 factors of the device model as numpy arrays."""
+    m = model.m
+    L = np.zeros((m, m)); a = np.zeros(m); vy = np.zeros(m); mo = np.zeros(m); vo = np.zeros(m)
+    _check(load().gpr_model_export(model.handle, L.ctypes.data, a.ctypes.data, vy.ctypes.data, mo.ctypes.data,
+                                   vo.ctypes.data), "gpr_model_export")
+    return {"L": L, "alpha": a, "vy": vy, "mu_obs": mo, "var_obs": vo}
+
+
+def gpr_profile_enable(on: bool = True):
+    load().gpr_profile_enable(1 if on else 0)
+
+
+def gpr_profile_reset():
+    load().gpr_profile_reset()
+
+
+def gpr_profile_read(name: str):
+    """(total milliseconds, launches) recorded for kernel group `name`."""
+    t = C.c_double(); n = C.c_int64()
+    load().gpr_profile_read(name.encode(), C.byref(t), C.byref(n))
+    return t.value, n.value
+
+
+def gpr_launch_count() -> int:
+    return int(load().gpr_launch_count())

@@ -1,0 +1,161 @@
+// Internal declarations shared by the CUDA translation units of the library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/gpr_lcp.h"
+
+#define GPR_CUDA_TRY(expr)                                   \
+    do {                                                     \
+        cudaError_t _e = (expr);                             \
+        if (_e != cudaSuccess) {                             \
+            gpr_internal_note_cuda_error(_e, #expr, __LINE__); \
+            return (_e == cudaErrorMemoryAllocation) ? GPR_ERR_OOM : GPR_ERR_CUDA; \
+        }                                                    \
+    } while (0)
+
+#define GPR_TRY(expr)                   \
+    do {                                \
+        gpr_status _s = (expr);         \
+        if (_s != GPR_OK) return _s;    \
+    } while (0)
+
+void gpr_internal_note_cuda_error(cudaError_t e, const char *what, int line);
+
+// Process-wide device status word (one int in device memory): 0 = OK, otherwise the
+// first gpr_status a kernel recorded.  Read and cleared by gpr_sync().
+int *gpr_status_word();
+
+// Forward neighbour offsets of the stats15 layout (see gpr_lcp.h).
+static constexpr int kOff13[13][3] = {
+    {1, -1, -1}, {1, -1, 0}, {1, -1, 1}, {1, 0, -1}, {1, 0, 0}, {1, 0, 1}, {1, 1, -1},
+    {1, 1, 0},   {1, 1, 1},  {0, 1, -1}, {0, 1, 0},  {0, 1, 1}, {0, 0, 1}};
+
+// Grid description on the device side.
+struct GridDev {
+    double lo[3], h[3];
+    int32_t n[3];
+    int64_t npts() const { return (int64_t)n[0] * n[1] * n[2]; }
+    int64_t ncells() const { return (int64_t)(n[0] - 1) * (n[1] - 1) * (n[2] - 1); }
+};
+
+GridDev make_grid(const gpr_grid *g);
+bool grid_valid(const gpr_grid *g);
+
+// Kernel parameters passed by value to device code.
+struct KernParams {
+    int kind;          // gpr_kernel
+    double ell[3];
+    double sf2;
+};
+
+struct gpr_model {
+    int64_t m = 0;
+    int64_t mp = 0;  // m rounded up to a multiple of 64 (GEMM column padding)
+    KernParams kp;
+    double sn2 = 0.0;
+    int device = 0;
+    // device buffers (FP64 unless noted)
+    double *X = nullptr;       // m x 3
+    double *y = nullptr;       // m
+    double *L = nullptr;       // m x m lower Cholesky factor
+    double *Linv = nullptr;    // m x m lower inverse
+    double *vy = nullptr;      // mp: L^-1 y (zero padded)
+    double *alpha = nullptr;   // m: Kt^-1 y
+    double *mu_obs = nullptr;  // m
+    double *var_obs = nullptr; // m
+    double *BT64 = nullptr;    // mp x mp: BT[i][j] = Linv[j][i] (upper triangular), zero padded
+    float *BT32 = nullptr;     // mp x mp FP32 copy
+    float *vy32 = nullptr;     // mp
+    // host copies used by the octree p-test
+    std::vector<double> hX, hy;
+    // two independent workspaces (grow, never shrink): slot 0 for a call's first phase,
+    // slot 1 for buffers sized after a device->host count read-back
+    void *ws[2] = {nullptr, nullptr};
+    size_t ws_bytes[2] = {0, 0};
+};
+
+// Makes workspace slot `which` at least `bytes` long (cudaMalloc only when it grows).
+gpr_status ws_reserve(gpr_model *M, int which, size_t bytes, cudaStream_t st);
+
+// Bump allocator over a workspace block (256-byte aligned pieces).
+struct Carver {
+    char *base;
+    size_t off = 0;
+    template <typename T>
+    T *take(size_t count) {
+        off = (off + 255) & ~size_t(255);
+        T *p = reinterpret_cast<T *>(base + off);
+        off += count * sizeof(T);
+        return p;
+    }
+    static size_t round(size_t b) { return (b + 255) & ~size_t(255); }
+};
+
+// ---- stats (stats.cu)
+// Per-axis SE factor tables E_d[g][j] (or squared scaled distance for Matern), FP64 and FP32.
+gpr_status build_tables(const gpr_model *M, const GridDev &g, double *T64, float *T32, cudaStream_t st);
+size_t table_elems(const gpr_model *M, const GridDev &g);  // per precision, all 3 axes
+
+// Point lists: `pts` (device int64 grid indices) or, when pts == nullptr, the consecutive
+// grid points pt_base, pt_base+1, ...  Row r of W belongs to list position r.
+// Slot maps: grid index -> row of W (`slot`, int32, -1 = absent) or, when slot == nullptr,
+// row = grid index - slot_base.
+void launch_w64(const gpr_model *M, const GridDev &g, const double *T64, const int64_t *pts, int64_t pt_base,
+                int64_t count, double *W, cudaStream_t st);
+void launch_w32(const gpr_model *M, const GridDev &g, const float *T32, const int64_t *pts, int64_t pt_base,
+                int64_t count, float *W, cudaStream_t st);
+// stats from W rows: either out15 (count x 15) or separate mean/var/cov13 (cov13 nullable).
+void launch_stats_from_w64(const gpr_model *M, const GridDev &g, const int64_t *pts, int64_t pt_base, int64_t count,
+                           const int32_t *slot, int64_t slot_base, const double *W, double *out15, double *mean,
+                           double *var, double *cov13, cudaStream_t st);
+void launch_stats_from_w32(const gpr_model *M, const GridDev &g, const int64_t *pts, int64_t pt_base, int64_t count,
+                           const int32_t *slot, int64_t slot_base, const float *W, float *mean, float *var,
+                           float *cov13, cudaStream_t st);
+// Fused FP32 mean/variance (W never stored).
+void launch_meanvar32(const gpr_model *M, const GridDev &g, const float *T32, const int64_t *pts, int64_t pt_base,
+                      int64_t count, float *mean, float *var, cudaStream_t st);
+
+// ---- LCP (lcp.cu)
+struct LcpOpts {
+    double theta, tau, skip_eps;
+    int est, n_samples;
+    uint64_t seed;
+};
+// For cells in `cells` (nullptr = all), build Sigma_8 from stats (indexed via slot map, nullptr = identity),
+// write 0/1 for skipped/deterministic cells into lcp[cell-or-position], and queue the rest.
+// out_by_position: lcp indexed by position in `cells` (true) or by linear cell index (false).
+gpr_status run_cell_lcp(const GridDev &g, const double *stats, const int32_t *slot, const int64_t *cells,
+                        int64_t count, const LcpOpts &o, float *lcp, bool out_by_position, void *scratch,
+                        size_t scratch_bytes, int64_t *n_estimated, cudaStream_t st);
+size_t cell_lcp_scratch_bytes(int64_t count);
+
+// Pre-classification: keep[cell] = 1 unless the widened Boole bound is below skip_eps.
+void launch_classify_cells(const GridDev &g, const float *mean, const float *var, double theta, double skip_eps,
+                           double tau, double margin_var, double margin_mu, uint8_t *keep, cudaStream_t st);
+
+// Compaction helpers
+// Marks corners of kept cells in point_flag (uint8 per grid point).
+void launch_mark_corners(const GridDev &g, const uint8_t *keep_cell, uint8_t *point_flag, cudaStream_t st);
+// Stream compaction of flagged indices: out_idx gets indices i with flag[i] != 0 in increasing order,
+// *count_dev the number; slot (optional) gets the position of each flagged index (-1 otherwise).
+gpr_status compact_flags(const uint8_t *flag, int64_t n, int64_t *out_idx, int32_t *slot, int64_t *count_host,
+                         void *scratch, size_t scratch_bytes, cudaStream_t st);
+size_t compact_scratch_bytes(int64_t n);
+
+int num_sms();
+
+// ---- tracing (profile.cu)
+void note_launch(int n = 1);
+// RAII scope: records CUDA events around the enclosed launches when profiling is on.
+struct ProfScope {
+    const char *name;
+    cudaStream_t st;
+    bool active;
+    void *a = nullptr, *b = nullptr;
+    ProfScope(const char *name, cudaStream_t st);
+    ~ProfScope();
+};

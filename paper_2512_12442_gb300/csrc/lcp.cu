@@ -1,0 +1,494 @@
+// Cell level-crossing probability (Sec. 3): LCP = 1 - P(all 8 corners < theta)
+// - P(all 8 corners > theta) for the 8-variate Gaussian of a cell's corners.
+// Stage 1 (FP64, thread per cell): assemble (mu_8, Sigma_8) from per-point stats15,
+// add the jitter, apply Boole's pre-skip and factor Sigma_8 = L L^T.
+// Stage 2 (FP32, warp per cell): the estimator -- Genz sequential conditioning over
+// a shifted rank-1 lattice (SOV-QMC), or the paper's Monte Carlo with Philox-4x32-10.
+#include <math.h>
+
+#include "internal.h"
+
+namespace {
+
+// For the 28 corner pairs (c1 < c2): which corner stores the covariance (0: c1, 1: c2) and the
+// offset slot e of that corner's stats15 row.  Built on the host from the offset list.
+struct PairTable {
+    int owner[8][8];
+    int slot[8][8];
+};
+
+PairTable make_pair_table()
+{
+    PairTable t;
+    for (int c1 = 0; c1 < 8; ++c1)
+        for (int c2 = 0; c2 < 8; ++c2) {
+            t.owner[c1][c2] = -1;
+            t.slot[c1][c2] = -1;
+            if (c1 == c2) continue;
+            int d[3] = {((c2 >> 0) & 1) - ((c1 >> 0) & 1), ((c2 >> 1) & 1) - ((c1 >> 1) & 1),
+                        ((c2 >> 2) & 1) - ((c1 >> 2) & 1)};
+            for (int e = 0; e < 13; ++e) {
+                if (kOff13[e][0] == d[0] && kOff13[e][1] == d[1] && kOff13[e][2] == d[2]) { t.owner[c1][c2] = 0; t.slot[c1][c2] = e; }
+                if (kOff13[e][0] == -d[0] && kOff13[e][1] == -d[1] && kOff13[e][2] == -d[2]) { t.owner[c1][c2] = 1; t.slot[c1][c2] = e; }
+            }
+        }
+    return t;
+}
+
+// One estimator record per cell that survives the pre-skip.
+struct CellRec {
+    float b[8];       // theta - mu_c
+    float L[36];      // lower Cholesky factor, row-major packed (row i: entries 0..i)
+    int64_t cell;     // linear cell index (keys the lattice shift / Philox stream)
+    int64_t out;      // output position
+};
+
+__device__ __forceinline__ int tri(int i, int j) { return i * (i + 1) / 2 + j; }
+
+__global__ void k_cell_prep(GridDev g, const double *stats, const int32_t *slot, const int64_t *cells,
+                            int64_t count, double theta, double tau, double skip_eps, PairTable pt, float *lcp,
+                            bool by_pos, CellRec *recs, unsigned long long *nrec, int *status)
+{
+    int64_t pos = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    bool active = pos < count;
+    bool need = false;
+    CellRec r;
+    int64_t outi = 0;
+    if (active) {
+        int64_t cidx = cells ? cells[pos] : pos;
+        int64_t cx = g.n[0] - 1, cy = g.n[1] - 1;
+        if (cidx < 0 || cidx >= cx * cy * (int64_t)(g.n[2] - 1)) {  // listed cell off the grid
+            atomicCAS(status, 0, (int)GPR_ERR_ARG);
+            active = false;
+            cidx = 0;
+        }
+        outi = by_pos ? pos : cidx;
+    }
+    if (active) {
+        int64_t cidx = cells ? cells[pos] : pos;
+        int64_t cx = g.n[0] - 1, cy = g.n[1] - 1;
+        int64_t i = cidx % cx, j = (cidx / cx) % cy, k = cidx / (cx * cy);
+        const double *row[8];
+        double mu[8], S[8][8];
+        for (int c = 0; c < 8; ++c) {
+            int64_t p = (i + (c & 1)) + (int64_t)g.n[0] * ((j + ((c >> 1) & 1)) + (int64_t)g.n[1] * (k + (c >> 2)));
+            int64_t s = slot ? (int64_t)slot[p] : p;
+            row[c] = stats + s * 15;
+            mu[c] = row[c][0];
+            S[c][c] = row[c][1];
+        }
+        for (int c1 = 0; c1 < 8; ++c1)
+            for (int c2 = c1 + 1; c2 < 8; ++c2) {
+                double v = pt.owner[c1][c2] == 0 ? row[c1][2 + pt.slot[c1][c2]] : row[c2][2 + pt.slot[c1][c2]];
+                S[c1][c2] = v;
+                S[c2][c1] = v;
+            }
+        double maxd = 0.0;
+        for (int c = 0; c < 8; ++c) maxd = fmax(maxd, S[c][c]);
+        float result = 0.0f;
+        if (!(maxd > 1e-30)) {
+            bool lo = true, hi = true;
+            for (int c = 0; c < 8; ++c) { lo = lo && (mu[c] < theta); hi = hi && (mu[c] > theta); }
+            result = (lo || hi) ? 0.0f : 1.0f;
+        } else {
+            double jit = tau * maxd;
+            for (int c = 0; c < 8; ++c) S[c][c] += jit;
+            double sa = 0.0, sb = 0.0;
+            for (int c = 0; c < 8; ++c) {
+                double sd = sqrt(S[c][c]);
+                sa += normcdf((mu[c] - theta) / sd);
+                sb += normcdf((theta - mu[c]) / sd);
+            }
+            if (!(sa < skip_eps || sb < skip_eps)) {
+                double Lm[8][8];
+                double fl = 1e-3 * jit;
+                for (int a = 0; a < 8; ++a) {
+                    for (int b = 0; b <= a; ++b) {
+                        double s = S[a][b];
+                        for (int q = 0; q < b; ++q) s -= Lm[a][q] * Lm[b][q];
+                        if (a == b) {
+                            if (!(s > fl)) s = fl;
+                            Lm[a][a] = sqrt(s);
+                        } else {
+                            Lm[a][b] = s / Lm[b][b];
+                        }
+                    }
+                }
+                for (int a = 0; a < 8; ++a) {
+                    r.b[a] = (float)(theta - mu[a]);
+                    for (int b = 0; b <= a; ++b) r.L[tri(a, b)] = (float)Lm[a][b];
+                }
+                r.cell = cidx;
+                r.out = outi;
+                need = true;
+            }
+        }
+        if (!need) lcp[outi] = result;
+    }
+    // warp-aggregated append of the cells that need the estimator
+    unsigned mask = __ballot_sync(0xffffffffu, need);
+    if (!mask) return;
+    int lane = threadIdx.x & 31, leader = __ffs(mask) - 1;
+    unsigned long long base = 0;
+    if (lane == leader) base = atomicAdd(nrec, (unsigned long long)__popc(mask));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (need) recs[base + __popc(mask & ((1u << lane) - 1))] = r;
+}
+
+__device__ __forceinline__ uint64_t splitmix64(uint64_t seed, uint64_t k)
+{
+    uint64_t z = seed + k * 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+// odd multiples of 2^-24 in (0,1): exact in binary32
+__device__ __forceinline__ float u01f(uint32_t x) { return (float)(((x >> 9) << 1) | 1u) * (1.0f / 16777216.0f); }
+
+struct Lattice {
+    uint32_t G[7];
+};
+
+__global__ void k_sov(const CellRec *recs, const unsigned long long *nrec, int N, uint64_t seed, Lattice lat,
+                      float *lcp)
+{
+    int lane = threadIdx.x & 31;
+    int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    int64_t n = (int64_t)*nrec;
+    for (int64_t q = warp; q < n; q += nw) {
+        const CellRec &r = recs[q];
+        float L[36], b[8], inv[8];
+#pragma unroll
+        for (int t = 0; t < 36; ++t) L[t] = r.L[t];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) { b[t] = r.b[t]; inv[t] = 1.0f / L[tri(t, t)]; }
+        uint32_t D = 0;
+        if (lane < 7) D = (uint32_t)(splitmix64(seed, (uint64_t)r.cell * 8 + lane + 1) >> 32);
+        uint32_t Ds[7];
+#pragma unroll
+        for (int i = 0; i < 7; ++i) Ds[i] = __shfl_sync(0xffffffffu, D, i);
+        double acc_lo = 0.0, acc_hi = 0.0;
+        for (int k = lane; k < N; k += 32) {
+            float w[7];
+#pragma unroll
+            for (int i = 0; i < 7; ++i) {
+                uint32_t U = (uint32_t)k * lat.G[i] + Ds[i];
+                w[i] = fabsf(2.0f * u01f(U) - 1.0f);
+            }
+#pragma unroll
+            for (int side = 0; side < 2; ++side) {
+                float sg = side == 0 ? 1.0f : -1.0f;
+                float z[7];
+                float f = 1.0f;
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    float s = 0.0f;
+#pragma unroll
+                    for (int j = 0; j < i; ++j) s = fmaf(L[tri(i, j)], z[j], s);
+                    float e = normcdff((sg * b[i] - s) * inv[i]);
+                    f *= e;
+                    if (!(f > 0.0f)) { f = 0.0f; break; }
+                    if (i < 7) z[i] = normcdfinvf(fmaxf(w[i] * e, 1e-37f));
+                }
+                if (side == 0) acc_lo += f; else acc_hi += f;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            acc_lo += __shfl_xor_sync(0xffffffffu, acc_lo, o);
+            acc_hi += __shfl_xor_sync(0xffffffffu, acc_hi, o);
+        }
+        if (lane == 0) {
+            double v = 1.0 - acc_lo / N - acc_hi / N;
+            lcp[r.out] = (float)(v < 0.0 ? 0.0 : (v > 1.0 ? 1.0 : v));
+        }
+    }
+}
+
+// Philox-4x32-10 (Salmon et al., SC'11).
+__device__ __forceinline__ void philox(uint32_t c[4], uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+        uint32_t hi0 = __umulhi(0xD2511F53u, c[0]), lo0 = 0xD2511F53u * c[0];
+        uint32_t hi1 = __umulhi(0xCD9E8D57u, c[2]), lo1 = 0xCD9E8D57u * c[2];
+        uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+        c[0] = n0; c[1] = lo1; c[2] = n2; c[3] = lo0;
+    }
+}
+
+__global__ void k_mc(const CellRec *recs, const unsigned long long *nrec, int N, uint64_t seed, float *lcp)
+{
+    int lane = threadIdx.x & 31;
+    int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    int64_t n = (int64_t)*nrec;
+    uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    for (int64_t q = warp; q < n; q += nw) {
+        const CellRec &r = recs[q];
+        float L[36], b[8];
+#pragma unroll
+        for (int t = 0; t < 36; ++t) L[t] = r.L[t];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) b[t] = r.b[t];
+        uint32_t clo = (uint32_t)r.cell, chi = (uint32_t)((uint64_t)r.cell >> 32);
+        int crossed = 0;
+        for (int k = lane; k < N; k += 32) {
+            float z[8];
+#pragma unroll
+            for (int rr = 0; rr < 2; ++rr) {
+                uint32_t c[4] = {(uint32_t)k, clo, chi, (uint32_t)rr};
+                philox(c, k0, k1);
+#pragma unroll
+                for (int p = 0; p < 2; ++p) {
+                    float u1 = u01f(c[2 * p]), u2 = u01f(c[2 * p + 1]);
+                    float rad = sqrtf(-2.0f * logf(u1));
+                    float sn, cs;
+                    sincospif(2.0f * u2, &sn, &cs);
+                    z[4 * rr + 2 * p] = rad * cs;
+                    z[4 * rr + 2 * p + 1] = rad * sn;
+                }
+            }
+            bool all_lo = true, all_hi = true;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                float s = 0.0f;
+#pragma unroll
+                for (int j = 0; j <= i; ++j) s = fmaf(L[tri(i, j)], z[j], s);
+                all_lo = all_lo && (s < b[i]);
+                all_hi = all_hi && (s > b[i]);
+            }
+            crossed += (all_lo || all_hi) ? 0 : 1;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) crossed += __shfl_xor_sync(0xffffffffu, crossed, o);
+        if (lane == 0) lcp[r.out] = (float)((double)crossed / (double)N);
+    }
+}
+
+Lattice make_lattice()
+{
+    static const int primes[7] = {2, 3, 5, 7, 11, 13, 17};
+    Lattice L;
+    for (int i = 0; i < 7; ++i) {
+        double s = sqrt((double)primes[i]);
+        L.G[i] = (uint32_t)floor((s - floor(s)) * 4294967296.0);
+    }
+    return L;
+}
+
+}  // namespace
+
+size_t cell_lcp_scratch_bytes(int64_t count) { return Carver::round(sizeof(CellRec) * (size_t)count) + 256; }
+
+gpr_status run_cell_lcp(const GridDev &g, const double *stats, const int32_t *slot, const int64_t *cells,
+                        int64_t count, const LcpOpts &o, float *lcp, bool by_pos, void *scratch,
+                        size_t scratch_bytes, int64_t *n_estimated, cudaStream_t st)
+{
+    if (count <= 0) {
+        if (n_estimated) *n_estimated = 0;
+        return GPR_OK;
+    }
+    if (scratch_bytes < cell_lcp_scratch_bytes(count)) return GPR_ERR_ARG;
+    Carver cv{(char *)scratch};
+    unsigned long long *nrec = cv.take<unsigned long long>(1);
+    CellRec *recs = cv.take<CellRec>((size_t)count);
+    GPR_CUDA_TRY(cudaMemsetAsync(nrec, 0, sizeof(unsigned long long), st));
+    static PairTable pt = make_pair_table();
+    int *status = gpr_status_word();
+    if (!status) return GPR_ERR_CUDA;
+    {
+        ProfScope _ps("cell_prep", st);
+        k_cell_prep<<<(unsigned)((count + 127) / 128), 128, 0, st>>>(g, stats, slot, cells, count, o.theta, o.tau,
+                                                                 o.skip_eps, pt, lcp, by_pos, recs, nrec, status);
+    }
+    note_launch();
+    GPR_CUDA_TRY(cudaGetLastError());
+    int sms = num_sms();
+    int64_t warps_needed = count;
+    int64_t blocks = (warps_needed + 7) / 8;
+    if (blocks > (int64_t)sms * 16) blocks = (int64_t)sms * 16;
+    if (o.est == GPR_EST_SOV_QMC) {
+        static Lattice lat = make_lattice();
+        {
+            ProfScope _ps("sov", st);
+            k_sov<<<(unsigned)blocks, 256, 0, st>>>(recs, nrec, o.n_samples, o.seed, lat, lcp);
+        }
+        note_launch();
+    } else {
+        {
+            ProfScope _ps("mc", st);
+            k_mc<<<(unsigned)blocks, 256, 0, st>>>(recs, nrec, o.n_samples, o.seed, lcp);
+        }
+        note_launch();
+    }
+    GPR_CUDA_TRY(cudaGetLastError());
+    if (n_estimated) {
+        unsigned long long h = 0;
+        GPR_CUDA_TRY(cudaMemcpyAsync(&h, nrec, sizeof h, cudaMemcpyDeviceToHost, st));
+        GPR_CUDA_TRY(cudaStreamSynchronize(st));
+        *n_estimated = (int64_t)h;
+    }
+    return GPR_OK;
+}
+
+// ------------------------------------------------------------ pre-classification
+
+__global__ void k_classify(GridDev g, const float *mean, const float *var, double theta, double skip_eps,
+                           double tau, double mv, double mm, uint8_t *keep)
+{
+    int64_t cidx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int64_t cx = g.n[0] - 1, cy = g.n[1] - 1, cz = g.n[2] - 1;
+    if (cidx >= cx * cy * cz) return;
+    int64_t i = cidx % cx, j = (cidx / cx) % cy, k = cidx / (cx * cy);
+    double mu[8], v[8], maxv = 0.0;
+    for (int c = 0; c < 8; ++c) {
+        int64_t p = (i + (c & 1)) + (int64_t)g.n[0] * ((j + ((c >> 1) & 1)) + (int64_t)g.n[1] * (k + (c >> 2)));
+        mu[c] = mean[p];
+        v[c] = fmax((double)var[p], 0.0) + mv;
+        maxv = fmax(maxv, v[c]);
+    }
+    double sa = 0.0, sb = 0.0;
+    for (int c = 0; c < 8; ++c) {
+        double sd = sqrt(v[c] + tau * maxv);
+        sa += normcdf((mu[c] + mm - theta) / sd);
+        sb += normcdf((theta - mu[c] + mm) / sd);
+    }
+    keep[cidx] = (sa < skip_eps || sb < skip_eps) ? 0 : 1;
+}
+
+void launch_classify_cells(const GridDev &g, const float *mean, const float *var, double theta, double skip_eps,
+                           double tau, double margin_var, double margin_mu, uint8_t *keep, cudaStream_t st)
+{
+    {
+        ProfScope _ps("classify", st);
+        k_classify<<<(unsigned)((g.ncells() + 255) / 256), 256, 0, st>>>(g, mean, var, theta, skip_eps, tau,
+                                                                     margin_var, margin_mu, keep);
+    }
+    note_launch();
+}
+
+__global__ void k_mark_corners(GridDev g, const uint8_t *keep, uint8_t *flag)
+{
+    int64_t cidx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int64_t cx = g.n[0] - 1, cy = g.n[1] - 1, cz = g.n[2] - 1;
+    if (cidx >= cx * cy * cz || !keep[cidx]) return;
+    int64_t i = cidx % cx, j = (cidx / cx) % cy, k = cidx / (cx * cy);
+    for (int c = 0; c < 8; ++c) {
+        int64_t p = (i + (c & 1)) + (int64_t)g.n[0] * ((j + ((c >> 1) & 1)) + (int64_t)g.n[1] * (k + (c >> 2)));
+        flag[p] = 1;
+    }
+}
+
+void launch_mark_corners(const GridDev &g, const uint8_t *keep_cell, uint8_t *point_flag, cudaStream_t st)
+{
+    k_mark_corners<<<(unsigned)((g.ncells() + 255) / 256), 256, 0, st>>>(g, keep_cell, point_flag);
+    note_launch();
+}
+
+// ------------------------------------------------------------ stream compaction
+
+static constexpr int CHUNK = 4096;  // flags per block
+
+__global__ void k_count(const uint8_t *flag, int64_t n, unsigned *counts)
+{
+    __shared__ unsigned wsum[32];
+    int64_t base = (int64_t)blockIdx.x * CHUNK;
+    unsigned c = 0;
+    for (int t = threadIdx.x; t < CHUNK; t += blockDim.x) {
+        int64_t i = base + t;
+        if (i < n && flag[i]) ++c;
+    }
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned s = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += wsum[w];
+        counts[blockIdx.x] = s;
+    }
+}
+
+// Exclusive scan of nb block counts in one block (serial over chunks of 1024).
+__global__ void k_scan_counts(const unsigned *counts, int64_t nb, unsigned long long *offs, unsigned long long *total)
+{
+    __shared__ unsigned long long sh[1024];
+    unsigned long long carry = 0;
+    for (int64_t b0 = 0; b0 < nb; b0 += 1024) {
+        int64_t i = b0 + threadIdx.x;
+        unsigned long long v = i < nb ? counts[i] : 0;
+        sh[threadIdx.x] = v;
+        __syncthreads();
+        for (int o = 1; o < 1024; o <<= 1) {
+            unsigned long long t = threadIdx.x >= (unsigned)o ? sh[threadIdx.x - o] : 0;
+            __syncthreads();
+            sh[threadIdx.x] += t;
+            __syncthreads();
+        }
+        if (i < nb) offs[i] = carry + sh[threadIdx.x] - v;
+        __syncthreads();
+        carry += sh[1023];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *total = carry;
+}
+
+__global__ void k_scatter(const uint8_t *flag, int64_t n, const unsigned long long *offs, int64_t *out_idx,
+                          int32_t *slot)
+{
+    __shared__ unsigned wsum[32];
+    int64_t base = (int64_t)blockIdx.x * CHUNK;
+    unsigned long long run = offs[blockIdx.x];
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int t0 = 0; t0 < CHUNK; t0 += blockDim.x) {
+        int64_t i = base + t0 + threadIdx.x;
+        bool f = i < n && flag[i];
+        unsigned m = __ballot_sync(0xffffffffu, f);
+        if (lane == 0) wsum[w] = __popc(m);
+        __syncthreads();
+        unsigned before = 0, tot = 0;
+        for (int q = 0; q < nw; ++q) {
+            if (q < w) before += wsum[q];
+            tot += wsum[q];
+        }
+        unsigned long long pos = run + before + __popc(m & ((1u << lane) - 1));
+        if (i < n) {
+            if (f) out_idx[pos] = i;
+            if (slot) slot[i] = f ? (int32_t)pos : -1;
+        }
+        run += tot;
+        __syncthreads();
+    }
+}
+
+size_t compact_scratch_bytes(int64_t n)
+{
+    int64_t nb = (n + CHUNK - 1) / CHUNK;
+    return Carver::round(sizeof(unsigned) * nb) + Carver::round(sizeof(unsigned long long) * nb) + 512;
+}
+
+gpr_status compact_flags(const uint8_t *flag, int64_t n, int64_t *out_idx, int32_t *slot, int64_t *count_host,
+                         void *scratch, size_t scratch_bytes, cudaStream_t st)
+{
+    if (scratch_bytes < compact_scratch_bytes(n)) return GPR_ERR_ARG;
+    int64_t nb = (n + CHUNK - 1) / CHUNK;
+    Carver cv{(char *)scratch};
+    unsigned *counts = cv.take<unsigned>(nb);
+    unsigned long long *offs = cv.take<unsigned long long>(nb);
+    unsigned long long *total = cv.take<unsigned long long>(1);
+    k_count<<<(unsigned)nb, 256, 0, st>>>(flag, n, counts);
+    note_launch();
+    k_scan_counts<<<1, 1024, 0, st>>>(counts, nb, offs, total);
+    note_launch();
+    k_scatter<<<(unsigned)nb, 256, 0, st>>>(flag, n, offs, out_idx, slot);
+    note_launch();
+    GPR_CUDA_TRY(cudaGetLastError());
+    unsigned long long h = 0;
+    GPR_CUDA_TRY(cudaMemcpyAsync(&h, total, sizeof h, cudaMemcpyDeviceToHost, st));
+    GPR_CUDA_TRY(cudaStreamSynchronize(st));
+    *count_host = (int64_t)h;
+    return GPR_OK;
+}

@@ -1,0 +1,377 @@
+// Model set-up on the device (Sec. 3 / Eq. 1 precomputation): Kt = K(X,X) + sn2 I,
+// blocked FP64 Cholesky, L^-1, v = L^-1 y, alpha = Kt^-1 y, latent posterior at the
+// observations, and the whitening operand BT = L^-T in FP64 and FP32.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include "internal.h"
+
+static constexpr int NB = 32;  // Cholesky block size
+
+static int *g_status_dev = nullptr;
+
+int *gpr_status_word()
+{
+    if (!g_status_dev) {
+        if (cudaMalloc(&g_status_dev, sizeof(int)) != cudaSuccess) return nullptr;
+        cudaMemset(g_status_dev, 0, sizeof(int));
+    }
+    return g_status_dev;
+}
+
+static char g_last_err[256];
+void gpr_internal_note_cuda_error(cudaError_t e, const char *what, int line)
+{
+    snprintf(g_last_err, sizeof g_last_err, "%s (%s) at line %d", cudaGetErrorString(e), what, line);
+    if (getenv("GPR_VERBOSE")) fprintf(stderr, "gpr_lcp: %s\n", g_last_err);
+}
+
+int num_sms()
+{
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+    }
+    return n;
+}
+
+__device__ __forceinline__ double kern64(const KernParams &kp, const double *a, const double *b)
+{
+    double r2 = 0.0;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        double t = (a[d] - b[d]) / kp.ell[d];
+        r2 += t * t;
+    }
+    if (kp.kind == GPR_K_SE) return kp.sf2 * exp(-0.5 * r2);
+    double r = sqrt(r2), s5r = 2.2360679774997896964 * r;
+    return kp.sf2 * (1.0 + s5r + (5.0 / 3.0) * r2) * exp(-s5r);
+}
+
+// Kt padded to mb x mb with the identity on the padding.
+__global__ void k_build_K(const double *X, int64_t m, int64_t mb, KernParams kp, double sn2, double *A)
+{
+    int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= mb * mb) return;
+    int64_t i = idx / mb, j = idx % mb;
+    double v;
+    if (i < m && j < m) v = kern64(kp, X + 3 * i, X + 3 * j) + (i == j ? sn2 : 0.0);
+    else v = (i == j) ? 1.0 : 0.0;
+    A[idx] = v;
+}
+
+// Unblocked Cholesky of the diagonal block kb (one warp; lane = row of the block).
+__global__ void k_potrf_diag(double *A, int64_t mb, int kb, int *status)
+{
+    __shared__ double S[NB][NB + 1];
+    int lane = threadIdx.x;
+    int64_t r0 = (int64_t)kb * NB;
+    for (int c = 0; c < NB; ++c) S[lane][c] = A[(r0 + lane) * mb + r0 + c];
+    __syncwarp();
+    for (int j = 0; j < NB; ++j) {
+        double piv = S[j][j];
+        bool bad = !(piv > 0.0);
+        if (bad) {
+            if (lane == 0) atomicCAS(status, 0, (int)GPR_ERR_NOT_PD);
+            piv = 1.0;  // keep going with finite numbers; the status word reports the failure
+        }
+        double ljj = sqrt(piv);
+        __syncwarp();
+        if (lane == j) S[j][j] = ljj;
+        if (lane > j) S[lane][j] /= ljj;
+        __syncwarp();
+        if (lane > j) {
+            double lij = S[lane][j];
+            for (int k = j + 1; k <= lane; ++k) S[lane][k] -= lij * S[k][j];
+        }
+        __syncwarp();
+    }
+    for (int c = 0; c < NB; ++c) A[(r0 + lane) * mb + r0 + c] = (c <= lane) ? S[lane][c] : 0.0;
+}
+
+// Panel solve: rows below block kb, A[r][kb-block] <- A[r][kb-block] L_kk^-T (thread per row).
+__global__ void k_trsm_panel(double *A, int64_t mb, int kb)
+{
+    __shared__ double Lk[NB][NB + 1];
+    int64_t r0 = (int64_t)kb * NB;
+    for (int t = threadIdx.x; t < NB * NB; t += blockDim.x) Lk[t / NB][t % NB] = A[(r0 + t / NB) * mb + r0 + t % NB];
+    __syncthreads();
+    int64_t row = r0 + NB + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (row >= mb) return;
+    double x[NB];
+#pragma unroll
+    for (int c = 0; c < NB; ++c) x[c] = A[row * mb + r0 + c];
+#pragma unroll
+    for (int c = 0; c < NB; ++c) {
+        double s = x[c];
+#pragma unroll
+        for (int k = 0; k < c; ++k) s -= x[k] * Lk[c][k];
+        x[c] = s / Lk[c][c];
+    }
+#pragma unroll
+    for (int c = 0; c < NB; ++c) A[row * mb + r0 + c] = x[c];
+}
+
+// Trailing update A[ib][jb] -= A[ib][kb] A[jb][kb]^T for kb < jb <= ib (lower blocks only).
+__global__ void k_syrk_update(double *A, int64_t mb, int kb)
+{
+    int ib = kb + 1 + blockIdx.y, jb = kb + 1 + blockIdx.x;
+    if (jb > ib) return;
+    __shared__ double Pa[NB][NB + 1], Pb[NB][NB + 1];
+    int64_t c0 = (int64_t)kb * NB;
+    for (int t = threadIdx.x; t < NB * NB; t += blockDim.x) {
+        int r = t / NB, c = t % NB;
+        Pa[r][c] = A[((int64_t)ib * NB + r) * mb + c0 + c];
+        Pb[r][c] = A[((int64_t)jb * NB + r) * mb + c0 + c];
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < NB * NB; t += blockDim.x) {
+        int r = t / NB, c = t % NB;
+        double s = 0.0;
+#pragma unroll 8
+        for (int k = 0; k < NB; ++k) s += Pa[r][k] * Pb[c][k];
+        A[((int64_t)ib * NB + r) * mb + (int64_t)jb * NB + c] -= s;
+    }
+}
+
+// L^-1 column by column (warp per column j): x = L^-1 e_j by forward substitution.
+__global__ void k_trtri_cols(const double *L, int64_t mb, double *Linv)
+{
+    extern __shared__ double xs[];
+    int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    int64_t j = blockIdx.x * (int64_t)(blockDim.x / 32) + warp;
+    if (j >= mb) return;
+    double *x = xs + (int64_t)warp * mb;
+    for (int64_t i = lane; i < mb; i += 32) x[i] = 0.0;
+    __syncwarp();
+    if (lane == 0) x[j] = 1.0 / L[j * mb + j];
+    __syncwarp();
+    for (int64_t i = j + 1; i < mb; ++i) {
+        double s = 0.0;
+        for (int64_t k = j + lane; k < i; k += 32) s += L[i * mb + k] * x[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) x[i] = -s / L[i * mb + i];
+        __syncwarp();
+    }
+    for (int64_t i = lane; i < mb; i += 32) Linv[i * mb + j] = x[i];
+}
+
+// vy = L^-1 y (warp per row).
+__global__ void k_vy(const double *Linv, int64_t mb, const double *y, int64_t m, double *vy, int64_t mp)
+{
+    int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    int64_t i = blockIdx.x * (int64_t)(blockDim.x / 32) + warp;
+    if (i >= mp) return;
+    double s = 0.0;
+    if (i < m)
+        for (int64_t k = lane; k <= i; k += 32) s += Linv[i * mb + k] * y[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) vy[i] = s;
+}
+
+// alpha = L^-T vy, Q_jj = sum_i Linv[i][j]^2, latent posterior at the observations.
+__global__ void k_alpha_obs(const double *Linv, int64_t mb, const double *vy, const double *y, int64_t m,
+                            double sn2, double sf2, double *alpha, double *mu_obs, double *var_obs)
+{
+    int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= m) return;
+    double a = 0.0, q = 0.0;
+    for (int64_t i = j; i < m; ++i) {
+        double l = Linv[i * mb + j];
+        a += l * vy[i];
+        q += l * l;
+    }
+    alpha[j] = a;
+    mu_obs[j] = y[j] - sn2 * a;
+    double v = sn2 - sn2 * sn2 * q, fl = 1e-12 * sf2;
+    var_obs[j] = v > fl ? v : fl;
+}
+
+// BT[i][j] = Linv[j][i] for i <= j < m, else 0  (mp x mp), FP64 and FP32.
+__global__ void k_operands(const double *Linv, int64_t mb, int64_t m, int64_t mp, double *BT64, float *BT32,
+                           const double *vy, float *vy32)
+{
+    int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx < mp) vy32[idx] = (float)vy[idx];
+    if (idx >= mp * mp) return;
+    int64_t i = idx / mp, j = idx % mp;
+    double v = (i < m && j < m && i <= j) ? Linv[j * mb + i] : 0.0;
+    BT64[idx] = v;
+    BT32[idx] = (float)v;
+}
+
+// Compact the padded mb x mb factor into m x m.
+__global__ void k_unpad(const double *A, int64_t mb, int64_t m, double *out)
+{
+    int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= m * m) return;
+    int64_t i = idx / m, j = idx % m;
+    out[idx] = (j <= i) ? A[i * mb + j] : 0.0;
+}
+
+static unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+extern "C" gpr_status gpr_model_create(const double *obs_xyz, const double *y, int64_t m, gpr_kernel kernel,
+                                       const double length_scales[3], double signal_var, double noise_var,
+                                       void *stream, gpr_model **out)
+{
+    if (!out) return GPR_ERR_ARG;
+    *out = nullptr;
+    if (!obs_xyz || !y || !length_scales || m < 1 || m > 8192) return GPR_ERR_ARG;
+    if (kernel != GPR_K_SE && kernel != GPR_K_MATERN52) return GPR_ERR_ARG;
+    if (!(signal_var > 0.0) || !(noise_var >= 0.0) || !isfinite(signal_var) || !isfinite(noise_var)) return GPR_ERR_ARG;
+    for (int d = 0; d < 3; ++d)
+        if (!(length_scales[d] > 0.0) || !isfinite(length_scales[d])) return GPR_ERR_ARG;
+    for (int64_t i = 0; i < 3 * m; ++i)
+        if (!isfinite(obs_xyz[i])) return GPR_ERR_ARG;
+    for (int64_t i = 0; i < m; ++i)
+        if (!isfinite(y[i])) return GPR_ERR_ARG;
+    if (getenv("GPR_FAULT") && strcmp(getenv("GPR_FAULT"), "alloc") == 0) return GPR_ERR_OOM;
+
+    cudaStream_t st = (cudaStream_t)stream;
+    int *status = gpr_status_word();
+    if (!status) return GPR_ERR_CUDA;
+    gpr_model *M = new gpr_model();
+    M->m = m;
+    M->mp = (m + 63) / 64 * 64;
+    M->kp.kind = kernel;
+    for (int d = 0; d < 3; ++d) M->kp.ell[d] = length_scales[d];
+    M->kp.sf2 = signal_var;
+    M->sn2 = noise_var;
+    cudaGetDevice(&M->device);
+    M->hX.assign(obs_xyz, obs_xyz + 3 * m);
+    M->hy.assign(y, y + m);
+    int64_t mb = (m + NB - 1) / NB * NB, mp = M->mp;
+    double *A = nullptr;
+    gpr_status rc = GPR_OK;
+    auto fail = [&](gpr_status s) {
+        if (A) cudaFree(A);
+        gpr_model_destroy(M);
+        return s;
+    };
+#define ALLOC(ptr, bytes)                                                   \
+    do {                                                                    \
+        cudaError_t _e = cudaMalloc((void **)&(ptr), (bytes));              \
+        if (_e != cudaSuccess) {                                            \
+            gpr_internal_note_cuda_error(_e, "cudaMalloc", __LINE__);       \
+            return fail(_e == cudaErrorMemoryAllocation ? GPR_ERR_OOM : GPR_ERR_CUDA); \
+        }                                                                   \
+    } while (0)
+    ALLOC(M->X, sizeof(double) * 3 * m);
+    ALLOC(M->y, sizeof(double) * m);
+    ALLOC(M->L, sizeof(double) * m * m);
+    ALLOC(M->Linv, sizeof(double) * mb * mb);
+    ALLOC(M->vy, sizeof(double) * mp);
+    ALLOC(M->alpha, sizeof(double) * m);
+    ALLOC(M->mu_obs, sizeof(double) * m);
+    ALLOC(M->var_obs, sizeof(double) * m);
+    ALLOC(M->BT64, sizeof(double) * mp * mp);
+    ALLOC(M->BT32, sizeof(float) * mp * mp);
+    ALLOC(M->vy32, sizeof(float) * mp);
+    ALLOC(A, sizeof(double) * mb * mb);
+#undef ALLOC
+    if (cudaMemcpyAsync(M->X, obs_xyz, sizeof(double) * 3 * m, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(M->y, y, sizeof(double) * m, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess)
+        return fail(GPR_ERR_CUDA);
+
+    k_build_K<<<nblk(mb * mb, 256), 256, 0, st>>>(M->X, m, mb, M->kp, noise_var, A);
+    note_launch();
+    int nbk = (int)(mb / NB);
+    for (int kb = 0; kb < nbk; ++kb) {
+        k_potrf_diag<<<1, 32, 0, st>>>(A, mb, kb, status);
+        note_launch();
+        int64_t rows = mb - (int64_t)(kb + 1) * NB;
+        if (rows > 0) {
+            k_trsm_panel<<<nblk(rows, 128), 128, 0, st>>>(A, mb, kb);
+            note_launch();
+            unsigned T = (unsigned)(nbk - kb - 1);
+            k_syrk_update<<<dim3(T, T), 256, 0, st>>>(A, mb, kb);
+            note_launch();
+        }
+    }
+    const int wpb = (sizeof(double) * mb * 4 <= 200 * 1024) ? 4 : ((sizeof(double) * mb * 2 <= 200 * 1024) ? 2 : 1);
+    size_t smem = sizeof(double) * mb * wpb;
+    if (smem > 48 * 1024) cudaFuncSetAttribute(k_trtri_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_trtri_cols<<<nblk(mb, wpb), 32 * wpb, smem, st>>>(A, mb, M->Linv);
+    note_launch();
+    k_vy<<<nblk(mp, 8), 256, 0, st>>>(M->Linv, mb, M->y, m, M->vy, mp);
+    note_launch();
+    k_alpha_obs<<<nblk(m, 128), 128, 0, st>>>(M->Linv, mb, M->vy, M->y, m, noise_var, signal_var, M->alpha,
+                                               M->mu_obs, M->var_obs);
+    note_launch();
+    k_operands<<<nblk(mp * mp, 256), 256, 0, st>>>(M->Linv, mb, m, mp, M->BT64, M->BT32, M->vy, M->vy32);
+    note_launch();
+    k_unpad<<<nblk(m * m, 256), 256, 0, st>>>(A, mb, m, M->L);
+    note_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) { gpr_internal_note_cuda_error(e, "setup launch", __LINE__); return fail(GPR_ERR_CUDA); }
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) { gpr_internal_note_cuda_error(e, "setup sync", __LINE__); return fail(GPR_ERR_CUDA); }
+    int hs = 0;
+    cudaMemcpy(&hs, status, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(A);
+    A = nullptr;
+    if (hs != 0) {
+        cudaMemset(status, 0, sizeof(int));
+        gpr_model_destroy(M);
+        return (gpr_status)hs;
+    }
+    (void)rc;
+    *out = M;
+    return GPR_OK;
+}
+
+extern "C" gpr_status gpr_model_destroy(gpr_model *M)
+{
+    if (!M) return GPR_ERR_ARG;
+    cudaDeviceSynchronize();
+    cudaFree(M->X); cudaFree(M->y); cudaFree(M->L); cudaFree(M->Linv); cudaFree(M->vy); cudaFree(M->alpha);
+    cudaFree(M->mu_obs); cudaFree(M->var_obs); cudaFree(M->BT64); cudaFree(M->BT32); cudaFree(M->vy32);
+    for (int w = 0; w < 2; ++w)
+        if (M->ws[w]) cudaFree(M->ws[w]);
+    delete M;
+    return GPR_OK;
+}
+
+extern "C" int64_t gpr_model_m(const gpr_model *M) { return M ? M->m : -1; }
+
+gpr_status ws_reserve(gpr_model *M, int which, size_t bytes, cudaStream_t st)
+{
+    if (bytes <= M->ws_bytes[which]) return GPR_OK;
+    if (M->ws[which]) {
+        cudaStreamSynchronize(st);
+        cudaFree(M->ws[which]);
+        M->ws[which] = nullptr;
+        M->ws_bytes[which] = 0;
+    }
+    size_t want = bytes + bytes / 8;
+    cudaError_t e = cudaMalloc(&M->ws[which], want);
+    if (e != cudaSuccess) {
+        gpr_internal_note_cuda_error(e, "workspace", __LINE__);
+        M->ws[which] = nullptr;
+        return e == cudaErrorMemoryAllocation ? GPR_ERR_OOM : GPR_ERR_CUDA;
+    }
+    M->ws_bytes[which] = want;
+    return GPR_OK;
+}
+
+// Test hook: copy the FP64 factors of a model to host buffers (each nullable).
+extern "C" gpr_status gpr_model_export(const gpr_model *M, double *L, double *alpha, double *vy, double *mu_obs,
+                                       double *var_obs)
+{
+    if (!M) return GPR_ERR_ARG;
+    int64_t m = M->m;
+    if (L) GPR_CUDA_TRY(cudaMemcpy(L, M->L, sizeof(double) * m * m, cudaMemcpyDeviceToHost));
+    if (alpha) GPR_CUDA_TRY(cudaMemcpy(alpha, M->alpha, sizeof(double) * m, cudaMemcpyDeviceToHost));
+    if (vy) GPR_CUDA_TRY(cudaMemcpy(vy, M->vy, sizeof(double) * m, cudaMemcpyDeviceToHost));
+    if (mu_obs) GPR_CUDA_TRY(cudaMemcpy(mu_obs, M->mu_obs, sizeof(double) * m, cudaMemcpyDeviceToHost));
+    if (var_obs) GPR_CUDA_TRY(cudaMemcpy(var_obs, M->var_obs, sizeof(double) * m, cudaMemcpyDeviceToHost));
+    return GPR_OK;
+}

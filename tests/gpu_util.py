@@ -1,0 +1,17 @@
+"""Shared helpers of the GPU parity tests."""
+import numpy as np
+
+
+def torch_cuda():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    return torch
+
+
+def model_of(w, stream=None):
+    import paper_2512_12442_gb300 as g
+    return g.gpr_model_create(w.X, w.y, w.kernel, w.ell, w.sf2, w.sn2, stream=stream)
+
+
+def cell_linear(i, j, k, n):
+    return i + (n - 1) * (j + (n - 1) * k)

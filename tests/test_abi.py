@@ -1,0 +1,75 @@
+"""CPU checks of the C ABI: the library builds for sm_103a, loads without a GPU and
+exports every function declared in include/gpr_lcp.h; options defaults; no compute."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    src = open(os.path.join(ROOT, "include", "gpr_lcp.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"\b(gpr_[a-z0-9_]+)\s*\(", src)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2512_12442_gb300 import build
+    build.build()
+    from paper_2512_12442_gb300 import _lib
+    return _lib.load()
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for must in ("gpr_model_create", "gpr_model_destroy", "gpr_reconstruct_dense", "gpr_lcp_dense",
+                 "gpr_lcp_adaptive", "gpr_cell_lcp_from_stats", "gpr_stats_points", "gpr_sync"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in _declared_functions():
+        assert hasattr(lib, name), name
+    from paper_2512_12442_gb300 import _lib
+    assert set(_declared_functions()) <= set(_lib.SIGNATURES)
+
+
+def test_option_defaults_and_status_strings(lib):
+    import paper_2512_12442_gb300 as g
+    o = g.lcp_options()
+    assert (o.alpha, o.beta, o.n_samples, o.jitter, o.skip_eps, o.max_iters_min) == (1e-3, 6.0, 1600, 1e-4, 1e-9, 4)
+    assert lib.gpr_status_string(2) == b"kernel matrix not positive definite"
+
+
+def test_host_argument_checks_need_no_gpu(lib):
+    """Invalid arguments are rejected on the host before any CUDA call."""
+    import numpy as np
+    import paper_2512_12442_gb300 as g
+    h = ctypes.c_void_p()
+    X = np.zeros((4, 3)); y = np.zeros(4); ell = np.array([0.1, -1.0, 0.1])
+    rc = lib.gpr_model_create(X.ctypes.data, y.ctypes.data, 4, 0, ell.ctypes.data, 1.0, 1e-4, None, ctypes.byref(h))
+    assert rc == g.GPR_ERR_ARG
+    rc = lib.gpr_model_create(X.ctypes.data, y.ctypes.data, 0, 0, np.ones(3).ctypes.data, 1.0, 1e-4, None,
+                              ctypes.byref(h))
+    assert rc == g.GPR_ERR_ARG
+    y[1] = float("nan")
+    rc = lib.gpr_model_create(X.ctypes.data, y.ctypes.data, 4, 0, np.ones(3).ctypes.data, 1.0, 1e-4, None,
+                              ctypes.byref(h))
+    assert rc == g.GPR_ERR_ARG
+    grid = g.make_grid(1)
+    assert lib.gpr_cell_lcp_from_stats(ctypes.byref(grid), 1, 0.0, ctypes.byref(g.lcp_options()), None, 0, 1,
+                                       None) == g.GPR_ERR_ARG
+
+
+def test_product_package_does_not_import_the_oracle():
+    """The product path never routes through the CPU oracle."""
+    pkg = os.path.join(ROOT, "paper_2512_12442_gb300")
+    for dp, _, fs in os.walk(pkg):
+        for f in fs:
+            if f.endswith((".py", ".cu", ".h", ".cuh")):
+                txt = open(os.path.join(dp, f)).read()
+                assert "import oracle" not in txt and "from oracle" not in txt and "gpr_oracle" not in txt, f
