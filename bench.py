@@ -44,7 +44,9 @@ def parse():
     p.add_argument("--mode", default="dense", choices=["dense", "adaptive"])
     p.add_argument("--prec", default="fp32", choices=["fp32", "fp64"])
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--cpu-sample", type=int, default=20, help="cells per axis of the oracle sample")
+    p.add_argument("--cpu-sample", type=int, default=64, help="cells per axis of the oracle sample")
+    p.add_argument("--case", default="full", choices=["full", "small"],
+                   help="small: one dense LCP field of the same field on a 64^3 grid (for ncu captures)")
     return p.parse_args()
 
 
@@ -168,6 +170,15 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl")
     w = workloads.config2()
+    if args.case == "small":
+        n = 64
+        grid = g.make_grid(n)
+        out = torch.zeros((n - 1) ** 3, dtype=torch.float32, device="cuda")
+        M = g.gpr_model_create(w.X, w.y, w.kernel, w.ell, w.sf2, w.sn2)
+        st = g.gpr_lcp_dense(M, grid, w.isovalues[1], g.lcp_options(), out)
+        g.gpr_sync()
+        print(json.dumps({"case": "small", "grid": n, "m": w.m, **{k: st[k] for k in ("recon_points", "leaf_cells")}}))
+        return
     n = w.n
     ncell = (n - 1) ** 3
     grid = g.make_grid(n)
@@ -265,9 +276,12 @@ def main():
         avg_s = prof["w64"][0] / prof["w64"][1] / 1e3
         achieved = flops_per_launch / avg_s / 1e12
         peak = 2.0 * 2 * 152 * 2.07e9 / 1e12  # FP64: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz (derived)
+        # DRAM bytes per W row from the ncu capture of the small case (bench.py --case small:
+        # 609.7 MB for 161,920 rows); traffic grows with the rows, so scale to this launch.
+        traffic = 609.7e6 / 161920 * recon / len(stats_last)
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "k_w_store<double> (FP64 whitening GEMM)",
-                "peak_source": "derived FP64 issue rate (not in MEASURED_PEAKS.json)"}
+                "traffic": traffic, "kernel": "k_w_store<double> (FP64 whitening GEMM)",
+                "peak_source": "derived FP64 issue rate 2 DFMA/clk/SM x 152 x 2.07 GHz (probe measured 1.202)"}
     cpu = None if args.no_cpu_baseline else cpu_baseline(w, w.isovalues[1], args.cpu_sample)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,

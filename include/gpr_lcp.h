@@ -132,7 +132,9 @@ int64_t gpr_model_m(const gpr_model *model);
  * the whitened form w = L^-1 k_x (mu = w . L^-1 y, var = k(x,x) - |w|^2), with
  * kernel rows generated on the fly (never stored).
  *   prec == GPR_P_FP64: mean/var/cov13 are double* (device, n, n, n x 13).
- *   other precisions:   mean/var/cov13 are float*.
+ *   other precisions:   mean/var/cov13 are float*; the O(m^2) part runs in that
+ *   precision, while the mean k_x . Kt^-1 y (O(m) per point, but a sum of terms
+ *   ~1e3 times larger than the result) is summed in float-float arithmetic.
  *   cov13 may be NULL; if given, slot e holds cov(p, p + OFF[e]) (see top).
  *   The call may grow the model's workspace (cudaMalloc) on first use of a
  *   larger grid.

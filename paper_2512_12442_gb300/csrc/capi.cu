@@ -132,24 +132,35 @@ extern "C" gpr_status gpr_reconstruct_dense(gpr_model *M, const gpr_grid *grid, 
         return dense_stats64(M, g, T64, W, rows, nullptr, (double *)mean, (double *)var, (double *)cov13, st);
     }
     float *T32;
+    float2 *Tff;
     if (!cov13) {
-        size_t bytes = Carver::round(te * sizeof(float)) + 1024;
+        size_t bytes = Carver::round(te * sizeof(float)) + Carver::round(te * sizeof(float2)) +
+                       Carver::round(te * sizeof(double)) + 1024;
         GPR_TRY(ws_reserve(M, 0, bytes, st));
         Carver cv{(char *)M->ws[0]};
         T32 = cv.take<float>(te);
-        GPR_TRY(build_tables(M, g, nullptr, T32, st));
+        Tff = cv.take<float2>(te);
+        double *T64 = cv.take<double>(te);
+        GPR_TRY(build_tables(M, g, T64, T32, st, Tff));
         launch_meanvar32(M, g, T32, nullptr, 0, g.npts(), (float *)mean, (float *)var, st);
+        launch_mean_compensated(M, g, Tff, T64, nullptr, 0, g.npts(), (float *)mean, st);
         GPR_CUDA_TRY(cudaGetLastError());
         return GPR_OK;
     }
     size_t rows = slab_rows(g, M->mp, sizeof(float), kWBudget);
-    size_t bytes = Carver::round(te * sizeof(float)) + Carver::round(rows * M->mp * sizeof(float)) + 1024;
+    size_t bytes = Carver::round(te * sizeof(float)) + Carver::round(te * sizeof(float2)) +
+                   Carver::round(te * sizeof(double)) + Carver::round(rows * M->mp * sizeof(float)) + 1024;
     GPR_TRY(ws_reserve(M, 0, bytes, st));
     Carver cv{(char *)M->ws[0]};
     T32 = cv.take<float>(te);
+    Tff = cv.take<float2>(te);
+    double *T64 = cv.take<double>(te);
     float *W = cv.take<float>(rows * M->mp);
-    GPR_TRY(build_tables(M, g, nullptr, T32, st));
-    return dense_stats32(M, g, T32, W, rows, (float *)mean, (float *)var, (float *)cov13, st);
+    GPR_TRY(build_tables(M, g, T64, T32, st, Tff));
+    GPR_TRY(dense_stats32(M, g, T32, W, rows, (float *)mean, (float *)var, (float *)cov13, st));
+    launch_mean_compensated(M, g, Tff, T64, nullptr, 0, g.npts(), (float *)mean, st);
+    GPR_CUDA_TRY(cudaGetLastError());
+    return GPR_OK;
 }
 
 __global__ void k_fill_slot(const int64_t *idx, int64_t count, int64_t npts, int32_t *slot, int *status)

@@ -70,6 +70,7 @@ struct gpr_model {
     double *BT64 = nullptr;    // mp x mp: BT[i][j] = Linv[j][i] (upper triangular), zero padded
     float *BT32 = nullptr;     // mp x mp FP32 copy
     float *vy32 = nullptr;     // mp
+    float2 *alpha_ff = nullptr; // mp: alpha as float-float (hi, lo)
     // host copies used by the octree p-test
     std::vector<double> hX, hy;
     // two independent workspaces (grow, never shrink): slot 0 for a call's first phase,
@@ -97,7 +98,8 @@ struct Carver {
 
 // ---- stats (stats.cu)
 // Per-axis SE factor tables E_d[g][j] (or squared scaled distance for Matern), FP64 and FP32.
-gpr_status build_tables(const gpr_model *M, const GridDev &g, double *T64, float *T32, cudaStream_t st);
+gpr_status build_tables(const gpr_model *M, const GridDev &g, double *T64, float *T32, cudaStream_t st,
+                        float2 *Tff = nullptr);
 size_t table_elems(const gpr_model *M, const GridDev &g);  // per precision, all 3 axes
 
 // Point lists: `pts` (device int64 grid indices) or, when pts == nullptr, the consecutive
@@ -115,6 +117,9 @@ void launch_stats_from_w64(const gpr_model *M, const GridDev &g, const int64_t *
 void launch_stats_from_w32(const gpr_model *M, const GridDev &g, const int64_t *pts, int64_t pt_base, int64_t count,
                            const int32_t *slot, int64_t slot_base, const float *W, float *mean, float *var,
                            float *cov13, cudaStream_t st);
+// Posterior mean k . alpha in float-float (SE) or FP64 (Matern); Tff / T64 tables as built.
+void launch_mean_compensated(const gpr_model *M, const GridDev &g, const float2 *Tff, const double *T64,
+                             const int64_t *pts, int64_t pt_base, int64_t count, float *mean, cudaStream_t st);
 // Fused FP32 mean/variance (W never stored).
 void launch_meanvar32(const gpr_model *M, const GridDev &g, const float *T32, const int64_t *pts, int64_t pt_base,
                       int64_t count, float *mean, float *var, cudaStream_t st);

@@ -31,7 +31,9 @@ size_t table_elems(const gpr_model *M, const GridDev &g) { return (size_t)(g.n[0
 
 // SE: T_d[g][j] = exp(-(x_g - X_jd)^2 / (2 l_d^2)), sf2 folded into axis 0.
 // Matern-5/2: T_d[g][j] = ((x_g - X_jd)/l_d)^2.  Columns j >= m are 0.
-__global__ void k_tables(const double *X, int64_t m, int64_t mp, KernParams kp, GridDev g, double *T64, float *T32)
+// Optional float-float copy (hi, lo) of the FP64 table for the compensated mean.
+__global__ void k_tables(const double *X, int64_t m, int64_t mp, KernParams kp, GridDev g, double *T64, float *T32,
+                         float2 *Tff)
 {
     int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     int64_t total = (int64_t)(g.n[0] + g.n[1] + g.n[2]) * mp;
@@ -53,12 +55,17 @@ __global__ void k_tables(const double *X, int64_t m, int64_t mp, KernParams kp, 
     }
     if (T64) T64[idx] = v;
     if (T32) T32[idx] = (float)v;
+    if (Tff) {
+        float hi = (float)v;
+        Tff[idx] = make_float2(hi, (float)(v - (double)hi));
+    }
 }
 
-gpr_status build_tables(const gpr_model *M, const GridDev &g, double *T64, float *T32, cudaStream_t st)
+gpr_status build_tables(const gpr_model *M, const GridDev &g, double *T64, float *T32, cudaStream_t st,
+                        float2 *Tff)
 {
     int64_t total = (int64_t)table_elems(M, g);
-    k_tables<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(M->X, M->m, M->mp, M->kp, g, T64, T32);
+    k_tables<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(M->X, M->m, M->mp, M->kp, g, T64, T32, Tff);
     note_launch();
     GPR_CUDA_TRY(cudaGetLastError());
     return GPR_OK;
@@ -397,5 +404,94 @@ void launch_stats_from_w32(const gpr_model *M, const GridDev &g, const int64_t *
         k_stats_from_w<float, float><<<(unsigned)((count + 7) / 8), 256, 0, st>>>(
         g, pts, pt_base, count, slot, slot_base, W, M->mp, M->vy32, M->kp.sf2, pr, nullptr, mean, var, cov13);
     }
+    note_launch();
+}
+
+// ---------------------------------------------------------------- compensated mean
+// mu_p = sum_j k(x_p, X_j) alpha_j evaluated in float-float arithmetic (pairs of FP32
+// carrying ~48 bits): the terms k_j alpha_j reach ~1e3 while mu is O(1), so a plain
+// FP32 sum loses ~1e-4 of the field scale.  SE kernels: k = E_x E_y E_z from the
+// float-float tables; Matern: FP64 arithmetic.
+struct FF {
+    float h, l;
+};
+__device__ __forceinline__ FF ff_mul(FF a, FF b)
+{
+    float p = a.h * b.h;
+    float e = fmaf(a.h, b.h, -p);
+    e = fmaf(a.h, b.l, e);
+    e = fmaf(a.l, b.h, e);
+    float s = p + e;
+    return {s, e - (s - p)};
+}
+__device__ __forceinline__ FF ff_add(FF a, FF b)
+{
+    float s = a.h + b.h;
+    float bv = s - a.h;
+    float err = (a.h - (s - bv)) + (b.h - bv);
+    err += a.l + b.l;
+    float r = s + err;
+    return {r, err - (r - s)};
+}
+
+__global__ void k_mean_ff(const float2 *Tff, int64_t off1, int64_t off2, int64_t mp, int64_t m, const float2 *aff,
+                          GridDev g, const int64_t *pts, int64_t pt_base, int64_t count, float *mean)
+{
+    int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    int64_t pos = blockIdx.x * (int64_t)(blockDim.x / 32) + warp;
+    if (pos >= count) return;
+    int64_t p = pts ? pts[pos] : pt_base + pos;
+    int64_t nx = g.n[0], ny = g.n[1];
+    if (p < 0 || p >= nx * ny * (int64_t)g.n[2]) return;
+    int64_t gx = p % nx, gy = (p / nx) % ny, gz = p / (nx * ny);
+    const float2 *tx = Tff + gx * mp, *ty = Tff + off1 + gy * mp, *tz = Tff + off2 + gz * mp;
+    FF acc = {0.f, 0.f};
+    for (int64_t j = lane; j < m; j += 32) {
+        float2 a = tx[j], b = ty[j], c = tz[j], al = aff[j];
+        FF k = ff_mul(ff_mul(FF{a.x, a.y}, FF{b.x, b.y}), FF{c.x, c.y});
+        acc = ff_add(acc, ff_mul(k, FF{al.x, al.y}));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        FF t = {__shfl_xor_sync(0xffffffffu, acc.h, o), __shfl_xor_sync(0xffffffffu, acc.l, o)};
+        acc = ff_add(acc, t);
+    }
+    if (lane == 0) mean[pos] = acc.h + acc.l;
+}
+
+__global__ void k_mean_f64(const double *T64, int64_t off1, int64_t off2, int64_t mp, int64_t m, double sf2,
+                           const double *alpha, GridDev g, const int64_t *pts, int64_t pt_base, int64_t count,
+                           float *mean)
+{
+    int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    int64_t pos = blockIdx.x * (int64_t)(blockDim.x / 32) + warp;
+    if (pos >= count) return;
+    int64_t p = pts ? pts[pos] : pt_base + pos;
+    int64_t nx = g.n[0], ny = g.n[1];
+    if (p < 0 || p >= nx * ny * (int64_t)g.n[2]) return;
+    int64_t gx = p % nx, gy = (p / nx) % ny, gz = p / (nx * ny);
+    double acc = 0.0;
+    for (int64_t j = lane; j < m; j += 32) {
+        double r2 = T64[gx * mp + j] + T64[off1 + gy * mp + j] + T64[off2 + gz * mp + j];
+        acc += KFun<double>::matern(r2, sf2) * alpha[j];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) mean[pos] = (float)acc;
+}
+
+void launch_mean_compensated(const gpr_model *M, const GridDev &g, const float2 *Tff, const double *T64,
+                             const int64_t *pts, int64_t pt_base, int64_t count, float *mean, cudaStream_t st)
+{
+    if (count <= 0) return;
+    int64_t o1, o2;
+    table_offsets(M, g, o1, o2);
+    ProfScope _ps("mean_ff", st);
+    if (M->kp.kind == GPR_K_SE)
+        k_mean_ff<<<(unsigned)((count + 7) / 8), 256, 0, st>>>(Tff, o1, o2, M->mp, M->m, M->alpha_ff, g, pts, pt_base,
+                                                             count, mean);
+    else
+        k_mean_f64<<<(unsigned)((count + 7) / 8), 256, 0, st>>>(T64, o1, o2, M->mp, M->m, M->kp.sf2, M->alpha, g,
+                                                              pts, pt_base, count, mean);
     note_launch();
 }
