@@ -199,6 +199,29 @@ gpr_status gpr_lcp_dense(gpr_model *model, const gpr_grid *grid, double isovalue
 gpr_status gpr_lcp_adaptive(gpr_model *model, const gpr_grid *grid, double isovalue, int32_t max_depth,
                             const gpr_lcp_options *opts, float *lcp, gpr_adaptive_stats *stats, void *stream);
 
+/*
+ * gpr_cell_lcp_from_stats_noalloc -- no counterpart in the paper.  The same cell
+ * LCP as gpr_cell_lcp_from_stats (same arguments, same results), for callers that
+ * may not allocate device memory when they call: a plug-in inside an application
+ * or framework that owns the device memory through its own pool allocator, or a
+ * latency-critical loop (cudaFree synchronises the whole device).
+ *   - Allocates nothing: the estimator's scratch is a static device array of the
+ *     library holding GPR_NOALLOC_MAX_CELLS cell records (~3 MB), kept by every
+ *     GPU that loads the library until the process exits.
+ *   - count (or, with cell_idx == NULL, the grid's cell count) must be at most
+ *     GPR_NOALLOC_MAX_CELLS, else GPR_ERR_ARG; split larger requests.
+ *   - The first call on a device resolves the array's device address on that
+ *     device (cudaGetSymbolAddress, with the device current); make that first call
+ *     before any stream capture on the device.
+ *   - All calls share the array and it keeps the last call's contents; calls that
+ *     overlap on the GPU race on it, so order them (one stream, or events).
+ *   - Cell indices off the grid are skipped (their output is left unchanged).
+ */
+#define GPR_NOALLOC_MAX_CELLS 16384
+gpr_status gpr_cell_lcp_from_stats_noalloc(const gpr_grid *grid, const double *stats15, double isovalue,
+                                           const gpr_lcp_options *opts, const int64_t *cell_idx, int64_t count,
+                                           float *lcp, void *stream);
+
 /* Waits for `stream` and returns the first device-side error recorded by any
  * model since the last call (GPR_OK if none). */
 gpr_status gpr_sync(void *stream);

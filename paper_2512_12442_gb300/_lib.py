@@ -39,6 +39,9 @@ SIGNATURES = {
     "gpr_stats_points": (C.c_int, [C.c_void_p, C.POINTER(GridC), C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
     "gpr_cell_lcp_from_stats": (C.c_int, [C.POINTER(GridC), C.c_void_p, C.c_double, C.POINTER(LcpOptionsC),
                                           C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
+    "gpr_cell_lcp_from_stats_noalloc": (C.c_int, [C.POINTER(GridC), C.c_void_p, C.c_double,
+                                                  C.POINTER(LcpOptionsC), C.c_void_p, C.c_int64, C.c_void_p,
+                                                  C.c_void_p]),
     "gpr_lcp_dense": (C.c_int, [C.c_void_p, C.POINTER(GridC), C.c_double, C.POINTER(LcpOptionsC), C.c_void_p,
                                 C.POINTER(AdaptiveStatsC), C.c_void_p]),
     "gpr_lcp_adaptive": (C.c_int, [C.c_void_p, C.POINTER(GridC), C.c_double, C.c_int32, C.POINTER(LcpOptionsC),

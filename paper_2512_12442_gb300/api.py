@@ -125,6 +125,18 @@ def gpr_cell_lcp_from_stats(grid: GridC, stats15, isovalue, opts: LcpOptionsC, c
     _check(rc, "gpr_cell_lcp_from_stats")
 
 
+GPR_NOALLOC_MAX_CELLS = 16384
+
+
+def gpr_cell_lcp_from_stats_noalloc(grid: GridC, stats15, isovalue, opts: LcpOptionsC, cell_idx, lcp, stream=None):
+    """As gpr_cell_lcp_from_stats, for callers that may not allocate device memory
+    (the library's static scratch serves at most GPR_NOALLOC_MAX_CELLS cells per call)."""
+    n = 0 if cell_idx is None else int(cell_idx.numel())
+    rc = load().gpr_cell_lcp_from_stats_noalloc(C.byref(grid), _ptr(stats15), float(isovalue), C.byref(opts),
+                                                _ptr(cell_idx, allow_none=True), n, _ptr(lcp), _stream(stream))
+    _check(rc, "gpr_cell_lcp_from_stats_noalloc")
+
+
 def _stats_dict(s: AdaptiveStatsC) -> dict:
     return {"nodes_per_level": list(s.nodes_per_level), "subdiv_per_level": list(s.subdiv_per_level),
             "leaf_cells": s.leaf_cells, "recon_points": s.recon_points, "cells_estimated": s.cells_estimated}

@@ -137,6 +137,10 @@ gpr_status run_cell_lcp(const GridDev &g, const double *stats, const int32_t *sl
                         int64_t count, const LcpOpts &o, float *lcp, bool out_by_position, void *scratch,
                         size_t scratch_bytes, int64_t *n_estimated, cudaStream_t st);
 size_t cell_lcp_scratch_bytes(int64_t count);
+size_t cell_rec_bytes();
+gpr_status run_cell_lcp_on_scratch(const GridDev &g, const double *stats, const int64_t *cells, int64_t count,
+                                   const LcpOpts &o, float *lcp, bool by_pos, void *scratch, int64_t max_records,
+                                   int *status, cudaStream_t st);
 
 // Pre-classification: keep[cell] = 1 unless the widened Boole bound is below skip_eps.
 void launch_classify_cells(const GridDev &g, const float *mean, const float *var, double theta, double skip_eps,

@@ -492,3 +492,35 @@ gpr_status compact_flags(const uint8_t *flag, int64_t n, int64_t *out_idx, int32
     *count_host = (int64_t)h;
     return GPR_OK;
 }
+
+// Same two stages as run_cell_lcp, on caller-provided scratch: `scratch` holds the record
+// counter (first 256 bytes) and then `max_records` CellRec records; `status` receives
+// GPR_ERR_ARG for listed cells off the grid.  Queues work only (no allocation, no sync).
+size_t cell_rec_bytes() { return sizeof(CellRec); }
+
+gpr_status run_cell_lcp_on_scratch(const GridDev &g, const double *stats, const int64_t *cells, int64_t count,
+                                   const LcpOpts &o, float *lcp, bool by_pos, void *scratch, int64_t max_records,
+                                   int *status, cudaStream_t st)
+{
+    if (count <= 0) return GPR_OK;
+    if (count > max_records) return GPR_ERR_ARG;
+    unsigned long long *nrec = (unsigned long long *)scratch;
+    CellRec *recs = (CellRec *)((char *)scratch + 256);
+    GPR_CUDA_TRY(cudaMemsetAsync(nrec, 0, sizeof(unsigned long long), st));
+    static PairTable pt = make_pair_table();
+    k_cell_prep<<<(unsigned)((count + 127) / 128), 128, 0, st>>>(g, stats, nullptr, cells, count, o.theta, o.tau,
+                                                                 o.skip_eps, pt, lcp, by_pos, recs, nrec, status);
+    note_launch();
+    GPR_CUDA_TRY(cudaGetLastError());
+    int64_t blocks = (count + 7) / 8;
+    if (blocks > (int64_t)num_sms() * 16) blocks = (int64_t)num_sms() * 16;
+    if (o.est == GPR_EST_SOV_QMC) {
+        static Lattice lat = make_lattice();
+        k_sov<<<(unsigned)blocks, 256, 0, st>>>(recs, nrec, o.n_samples, o.seed, lat, lcp);
+    } else {
+        k_mc<<<(unsigned)blocks, 256, 0, st>>>(recs, nrec, o.n_samples, o.seed, lcp);
+    }
+    note_launch();
+    GPR_CUDA_TRY(cudaGetLastError());
+    return GPR_OK;
+}
