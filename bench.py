@@ -226,7 +226,8 @@ def main():
     g.gpr_profile_enable(False)
     launches = g.gpr_launch_count()
     ms = ev0.elapsed_time(ev1) / args.steps
-    prof = {k: g.gpr_profile_read(k) for k in ("w64", "meanvar32", "stats_from_w64", "cell_prep", "sov", "classify")}
+    prof = {k: g.gpr_profile_read(k) for k in ("w64", "meanvar32", "mean_ff", "stats_from_w64", "cell_prep", "sov",
+                                                "classify", "oct_eval_w")}
     g.gpr_sync(stream)
     M.close()
     t_max = ms

@@ -51,8 +51,11 @@ SIGNATURES = {
     "gpr_profile_reset": (None, []),
     "gpr_profile_read": (C.c_int, [C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     "gpr_launch_count": (C.c_int64, []),
-    # test hook (not in the public header)
+    # test hooks (not in the public header)
     "gpr_model_export": (C.c_int, [C.c_void_p] + [C.c_void_p] * 5),
+    "gpr_octree_trace": (C.c_int, [C.c_void_p, C.POINTER(GridC), C.c_double, C.c_int32, C.POINTER(LcpOptionsC),
+                                   C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
+                                   C.POINTER(C.c_int64), C.c_void_p]),
 }
 
 _lib = None

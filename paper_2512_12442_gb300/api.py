@@ -162,6 +162,18 @@ def gpr_sync(stream=None):
     _check(load().gpr_sync(_stream(stream)), "gpr_sync")
 
 
+def gpr_octree_trace(model: Model, grid: GridC, isovalue, max_depth, opts: LcpOptionsC, level, capacity=1 << 22,
+                     stream=None):
+    """Test hook: (node codes, decisions, bounds) of one level of the device octree."""
+    nodes = np.zeros(capacity, np.int64); dec = np.zeros(capacity, np.int8); bnd = np.zeros(capacity)
+    cnt = C.c_int64()
+    _check(load().gpr_octree_trace(model.handle, C.byref(grid), float(isovalue), int(max_depth), C.byref(opts),
+                                   int(level), nodes.ctypes.data, dec.ctypes.data, bnd.ctypes.data, capacity,
+                                   C.byref(cnt), _stream(stream)), "gpr_octree_trace")
+    c = min(cnt.value, capacity)
+    return nodes[:c], dec[:c], bnd[:c]
+
+
 def gpr_model_export(model: Model):
     """Test hook: FP64 factors of the device model as numpy arrays."""
     m = model.m

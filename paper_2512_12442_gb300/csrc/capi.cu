@@ -44,7 +44,7 @@ extern "C" gpr_status gpr_sync(void *stream)
     return (gpr_status)h;
 }
 
-static bool opts_valid(const gpr_lcp_options *o)
+bool opts_valid(const gpr_lcp_options *o)
 {
     if (!o) return false;
     if (o->est != GPR_EST_SOV_QMC && o->est != GPR_EST_MC) return false;
@@ -220,7 +220,7 @@ static gpr_status scratch_reserve(size_t bytes, cudaStream_t st)
     return GPR_OK;
 }
 
-static LcpOpts lcp_opts(const gpr_lcp_options *o, double theta)
+LcpOpts lcp_opts(const gpr_lcp_options *o, double theta)
 {
     LcpOpts l;
     l.theta = theta;
@@ -251,7 +251,7 @@ extern "C" gpr_status gpr_cell_lcp_from_stats(const gpr_grid *grid, const double
 // Widening of the pre-pass Boole test so that it never drops a cell the FP64 test keeps:
 // the FP32 whitened mean/variance errors measured on the configurations are below 1e-5 of
 // the field scale; the margins are 100x that.
-static void prepass_margins(const gpr_model *M, double &mv, double &mm)
+void prepass_margins(const gpr_model *M, double &mv, double &mm)
 {
     double ymax = 0.0;
     for (double v : M->hy) ymax = fmax(ymax, fabs(v));
@@ -316,6 +316,14 @@ extern "C" gpr_status gpr_lcp_dense(gpr_model *M, const gpr_grid *grid, double i
     double mv, mm;
     prepass_margins(M, mv, mm);
     launch_classify_cells(g, mean, var, isovalue, opts->skip_eps, opts->jitter, mv, mm, keep, st);
+    return lcp_from_kept_cells(M, g, T64, keep, pflag, plist, slot, clist, cscr, csb, lo, lcp, stats, st);
+}
+
+gpr_status lcp_from_kept_cells(gpr_model *M, const GridDev &g, const double *T64, const uint8_t *keep, uint8_t *pflag,
+                               int64_t *plist, int32_t *slot, int64_t *clist, void *cscr, size_t csb, const LcpOpts &lo,
+                               float *lcp, gpr_adaptive_stats *stats, cudaStream_t st)
+{
+    int64_t n = g.npts(), nc = g.ncells();
     GPR_CUDA_TRY(cudaMemsetAsync(pflag, 0, (size_t)n, st));
     launch_mark_corners(g, keep, pflag, st);
     GPR_CUDA_TRY(cudaGetLastError());
@@ -328,7 +336,7 @@ extern "C" gpr_status gpr_lcp_dense(gpr_model *M, const gpr_grid *grid, double i
         stats->leaf_cells = ncell;
     }
     if (ncell == 0) return GPR_OK;
-    // Phase 2: FP64 W rows and stats15 for the kept cells' corners, then the estimator.
+    // FP64 W rows and stats15 for the kept cells' corners, then the estimator.
     size_t b2 = Carver::round((size_t)npts * M->mp * sizeof(double)) + Carver::round((size_t)npts * 15 * sizeof(double)) +
                 cell_lcp_scratch_bytes(ncell) + 1024;
     GPR_TRY(ws_reserve(M, 1, b2, st));
@@ -346,10 +354,3 @@ extern "C" gpr_status gpr_lcp_dense(gpr_model *M, const gpr_grid *grid, double i
     return GPR_OK;
 }
 
-extern "C" gpr_status gpr_lcp_adaptive(gpr_model *M, const gpr_grid *grid, double isovalue, int32_t max_depth,
-                                       const gpr_lcp_options *opts, float *lcp, gpr_adaptive_stats *stats,
-                                       void *stream)
-{
-    (void)M; (void)grid; (void)isovalue; (void)max_depth; (void)opts; (void)lcp; (void)stats; (void)stream;
-    return GPR_ERR_UNSUPPORTED;
-}

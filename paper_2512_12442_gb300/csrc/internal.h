@@ -71,6 +71,9 @@ struct gpr_model {
     float *BT32 = nullptr;     // mp x mp FP32 copy
     float *vy32 = nullptr;     // mp
     float2 *alpha_ff = nullptr; // mp: alpha as float-float (hi, lo)
+    float *Linv32 = nullptr;   // mp x mp FP32 copy of L^-1 (lower), zero padded
+    float *X32 = nullptr;      // m x 3 FP32 observation sites
+    float *alpha32 = nullptr;  // mp FP32 alpha
     // host copies used by the octree p-test
     std::vector<double> hX, hy;
     // two independent workspaces (grow, never shrink): slot 0 for a call's first phase,
@@ -156,6 +159,15 @@ gpr_status compact_flags(const uint8_t *flag, int64_t n, int64_t *out_idx, int32
 size_t compact_scratch_bytes(int64_t n);
 
 int num_sms();
+
+// ---- shared by the LCP entry points (capi.cu)
+bool opts_valid(const gpr_lcp_options *o);
+LcpOpts lcp_opts(const gpr_lcp_options *o, double theta);
+void prepass_margins(const gpr_model *M, double &mv, double &mm);
+// keep[cell] != 0 cells: FP64 stats of their corners, estimator, field (zeroed elsewhere).
+gpr_status lcp_from_kept_cells(gpr_model *M, const GridDev &g, const double *T64, const uint8_t *keep, uint8_t *pflag,
+                               int64_t *plist, int32_t *slot, int64_t *clist, void *cscr, size_t csb, const LcpOpts &lo,
+                               float *lcp, gpr_adaptive_stats *stats, cudaStream_t st);
 
 // ---- tracing (profile.cu)
 void note_launch(int n = 1);

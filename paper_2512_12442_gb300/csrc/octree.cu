@@ -1,0 +1,732 @@
+// Algorithm 1 (octree adaptive query, Sec. 4.3) on the device, level by level, followed by
+// the leaf reconstruction of Sec. 4.3's last paragraph: the cells of S get the dense
+// method's LCP, every other cell 0.
+//
+// Per level: (1) p-test on the observations inside each node (Sec. 4.3: p1 = max P(Y_i<t),
+// p2 = max P(Y_i>t) over the node's observations, with the latent posterior at the
+// observations); (2) the regional upper bound 1 - B_l^d - B_u^d (Eq. upper_bound, Sec. 4.1)
+// for the remaining nodes, B = min over the node of Phi(+-(t - mu)/sigma): exact over the
+// grid points when a node has <= 3 points per axis, otherwise a 3x3x3 lattice start plus T
+// projected gradient steps (our reading of the paper's L-BFGS-B minimiser); (3) compaction
+// of the subdivided nodes into the next frontier (or into S at the last level).
+// Evaluations of mu, sigma and their gradients run in FP32 on the whitened form.
+#include <math.h>
+#include <string.h>
+
+#include <vector>
+
+#include "internal.h"
+
+namespace {
+
+constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
+constexpr int64_t kEvalChunk = 131072;  // evaluation points per pipeline pass
+
+struct EvalModel {
+    const float *X32, *BT32, *Linv32, *alpha32;
+    int64_t m, mp;
+    int kind;
+    float ell[3];
+    float sf2;
+};
+
+__device__ __forceinline__ float kdirect(const EvalModel &E, float x, float y, float z, int64_t j)
+{
+    float a = (x - E.X32[3 * j]) / E.ell[0], b = (y - E.X32[3 * j + 1]) / E.ell[1], c = (z - E.X32[3 * j + 2]) / E.ell[2];
+    float r2 = a * a + b * b + c * c;
+    if (E.kind == GPR_K_SE) return E.sf2 * __expf(-0.5f * r2);
+    float r = sqrtf(r2), s5r = 2.23606797749979f * r;
+    return E.sf2 * (1.0f + s5r + (5.0f / 3.0f) * r2) * __expf(-s5r);
+}
+
+// W rows (FP32) of arbitrary evaluation points: W = K(x, X) L^-T.
+__global__ void __launch_bounds__(NT) k_eval_w(EvalModel E, const double *xyz, int64_t count, float *W)
+{
+    __shared__ float As[BK][BM + 4], Bs[BK][BN + 4];
+    __shared__ float px[BM], py[BM], pz[BM];
+    __shared__ bool valid[BM];
+    int64_t row0 = (int64_t)blockIdx.y * BM, j0 = (int64_t)blockIdx.x * BN;
+    for (int r = threadIdx.x; r < BM; r += NT) {
+        int64_t row = row0 + r;
+        bool ok = row < count;
+        valid[r] = ok;
+        px[r] = ok ? (float)xyz[3 * row] : 0.f;
+        py[r] = ok ? (float)xyz[3 * row + 1] : 0.f;
+        pz[r] = ok ? (float)xyz[3 * row + 2] : 0.f;
+    }
+    __syncthreads();
+    int t = threadIdx.x, tx = t % 16, ty = t / 16;
+    float acc[4][4] = {};
+    int64_t kend = j0 + BN < E.m ? j0 + BN : E.m;
+    for (int64_t k0 = 0; k0 < kend; k0 += BK) {
+#pragma unroll
+        for (int e = 0; e < (BM * BK) / NT; ++e) {
+            int idx = t + NT * e, r = idx % BM, kk = idx / BM;
+            int64_t j = k0 + kk;
+            As[kk][r] = (j < E.m && valid[r]) ? kdirect(E, px[r], py[r], pz[r], j) : 0.f;
+        }
+#pragma unroll
+        for (int e = 0; e < (BK * BN) / NT; ++e) {
+            int idx = t + NT * e, kk = idx / BN, c = idx % BN;
+            Bs[kk][c] = E.BT32[(k0 + kk) * E.mp + j0 + c];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            float a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) b[c] = Bs[kk][tx * 4 + c];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) acc[i][c] = fmaf(a[i], b[c], acc[i][c]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        int64_t row = row0 + ty * 4 + i;
+        if (row >= count) continue;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) W[row * E.mp + j0 + tx * 4 + c] = acc[i][c];
+    }
+}
+
+// P rows = W L^-1, i.e. P = Kt^-1 k (P_i = sum_{j >= i} w_j [L^-1]_{ji}); feeds grad sigma^2.
+__global__ void __launch_bounds__(NT) k_eval_p(EvalModel E, const float *W, int64_t count, float *P)
+{
+    __shared__ float As[BK][BM + 4], Bs[BK][BN + 4];
+    int64_t row0 = (int64_t)blockIdx.y * BM, i0 = (int64_t)blockIdx.x * BN;
+    int t = threadIdx.x, tx = t % 16, ty = t / 16;
+    float acc[4][4] = {};
+    for (int64_t k0 = i0; k0 < E.m; k0 += BK) {
+#pragma unroll
+        for (int e = 0; e < (BM * BK) / NT; ++e) {
+            int idx = t + NT * e, r = idx % BM, kk = idx / BM;
+            int64_t row = row0 + r;
+            As[kk][r] = row < count ? W[row * E.mp + k0 + kk] : 0.f;
+        }
+#pragma unroll
+        for (int e = 0; e < (BK * BN) / NT; ++e) {
+            int idx = t + NT * e, kk = idx / BN, c = idx % BN;
+            Bs[kk][c] = E.Linv32[(k0 + kk) * E.mp + i0 + c];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            float a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) b[c] = Bs[kk][tx * 4 + c];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) acc[i][c] = fmaf(a[i], b[c], acc[i][c]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        int64_t row = row0 + ty * 4 + i;
+        if (row >= count) continue;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) P[row * E.mp + i0 + tx * 4 + c] = acc[i][c];
+    }
+}
+
+// g = (theta - mu)/sigma and grad g at each evaluation point (warp per point).
+// grad mu = sum_j dk_j alpha_j, grad sigma^2 = -2 sum_j dk_j P_j.
+__global__ void k_eval_reduce(EvalModel E, const double *xyz, const float *W, const float *P, int64_t count,
+                              double theta, float4 *out)
+{
+    int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    int64_t q = blockIdx.x * (int64_t)(blockDim.x / 32) + warp;
+    if (q >= count) return;
+    float x = (float)xyz[3 * q], y = (float)xyz[3 * q + 1], z = (float)xyz[3 * q + 2];
+    float wsq = 0.f, mu_h = 0.f, mu_l = 0.f, gm[3] = {0, 0, 0}, gv[3] = {0, 0, 0};
+    const float *wr = W + q * E.mp, *pr = P + q * E.mp;
+    float il2[3] = {1.f / (E.ell[0] * E.ell[0]), 1.f / (E.ell[1] * E.ell[1]), 1.f / (E.ell[2] * E.ell[2])};
+    for (int64_t j = lane; j < E.m; j += 32) {
+        float w = wr[j];
+        wsq = fmaf(w, w, wsq);
+        float d0 = x - E.X32[3 * j], d1 = y - E.X32[3 * j + 1], d2 = z - E.X32[3 * j + 2];
+        float r2 = d0 * d0 * il2[0] + d1 * d1 * il2[1] + d2 * d2 * il2[2];
+        float k, c;
+        if (E.kind == GPR_K_SE) {
+            k = E.sf2 * __expf(-0.5f * r2);
+            c = -k;
+        } else {
+            float r = sqrtf(r2), s5r = 2.23606797749979f * r, e = __expf(-s5r);
+            k = E.sf2 * (1.0f + s5r + (5.0f / 3.0f) * r2) * e;
+            c = -(5.0f / 3.0f) * E.sf2 * (1.0f + s5r) * e;
+        }
+        float a = E.alpha32[j], pj = pr[j];
+        // compensated accumulation of mu (terms k*alpha reach ~1e3 for an O(1) result)
+        float term = k * a, s = mu_h + term, bv = s - mu_h;
+        mu_l += (mu_h - (s - bv)) + (term - bv);
+        mu_h = s;
+        float dd[3] = {d0, d1, d2};
+#pragma unroll
+        for (int dI = 0; dI < 3; ++dI) {
+            float dk = c * dd[dI] * il2[dI];
+            gm[dI] = fmaf(dk, a, gm[dI]);
+            gv[dI] = fmaf(-2.f * dk, pj, gv[dI]);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        wsq += __shfl_xor_sync(0xffffffffu, wsq, o);
+        mu_h += __shfl_xor_sync(0xffffffffu, mu_h, o);
+        mu_l += __shfl_xor_sync(0xffffffffu, mu_l, o);
+#pragma unroll
+        for (int dI = 0; dI < 3; ++dI) {
+            gm[dI] += __shfl_xor_sync(0xffffffffu, gm[dI], o);
+            gv[dI] += __shfl_xor_sync(0xffffffffu, gv[dI], o);
+        }
+    }
+    if (lane == 0) {
+        float var = E.sf2 - wsq;
+        float fl = 1e-12f * E.sf2;
+        if (!(var > fl)) var = fl;
+        float sd = sqrtf(var), mu = mu_h + mu_l;
+        float gg = (float)(theta - (double)mu) / sd;
+        float4 o;
+        o.x = gg;
+        o.y = -gm[0] / sd - gg * gv[0] / (2.f * var);
+        o.z = -gm[1] / sd - gg * gv[1] / (2.f * var);
+        o.w = -gm[2] / sd - gg * gv[2] / (2.f * var);
+        out[q] = o;
+    }
+}
+
+struct Geom {
+    int64_t p0[3], p1[3];
+    double blo[3], bhi[3];
+};
+
+__device__ __forceinline__ Geom node_geom(const GridDev &g, int D, int l, int64_t code)
+{
+    Geom G;
+    int64_t s = (int64_t)1 << (D - l);
+    int64_t ijk[3] = {code & 0x1FFFFF, (code >> 21) & 0x1FFFFF, (code >> 42) & 0x1FFFFF};
+    for (int d = 0; d < 3; ++d) {
+        G.p0[d] = ijk[d] * s;
+        G.p1[d] = (ijk[d] + 1) * s;
+        if (G.p1[d] > g.n[d] - 1) G.p1[d] = g.n[d] - 1;
+        G.blo[d] = g.lo[d] + (double)G.p0[d] * g.h[d];
+        G.bhi[d] = g.lo[d] + (double)G.p1[d] * g.h[d];
+    }
+    return G;
+}
+
+__device__ __forceinline__ bool is_small(const Geom &G)
+{
+    return G.p1[0] - G.p0[0] <= 2 && G.p1[1] - G.p0[1] <= 2 && G.p1[2] - G.p0[2] <= 2;
+}
+
+__device__ __forceinline__ double log_norm_cdf(double gg)
+{
+    if (gg >= 0.0) return log1p(-0.5 * erfc(gg * 0.70710678118654752440));
+    double c = 0.5 * erfc(-gg * 0.70710678118654752440);
+    if (c > 0.0) return log(c);
+    return -0.5 * gg * gg - log(-gg * 2.5066282746310005024);
+}
+
+__device__ __forceinline__ double bound_of(int sides, double dcount, double glo, double ghi)
+{
+    double lBlo = (sides & 1) ? log_norm_cdf(glo) : -INFINITY;
+    double lBhi = (sides & 2) ? log_norm_cdf(ghi) : -INFINITY;
+    if (sides == 3) return -expm1(dcount * lBlo) - exp(dcount * lBhi);
+    if (sides == 1) return -expm1(dcount * lBlo);
+    return -expm1(dcount * lBhi);
+}
+
+// Observation flags for the p-test: bit0 = P(Y_i < theta) > alpha, bit1 = P(Y_i > theta) > alpha.
+__global__ void k_obs_flags(const double *mu_obs, const double *var_obs, int64_t m, double theta, double alpha,
+                            uint8_t *flags)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    double sd = sqrt(var_obs[i]);
+    bool lo = normcdf((theta - mu_obs[i]) / sd) > alpha;
+    bool hi = normcdf((mu_obs[i] - theta) / sd) > alpha;
+    flags[i] = (uint8_t)((lo ? 1 : 0) | (hi ? 2 : 0));
+}
+
+// p-test (warp per node).  decision: 1 = subdivide (p1 > alpha and p2 > alpha), 0 = bound needed;
+// sides: bit0 lower bound B_l, bit1 upper bound B_u.
+__global__ void k_ptest(GridDev g, int D, int l, const int64_t *nodes, int64_t count, const double *X, int64_t m,
+                        const uint8_t *flags, int8_t *decision, int8_t *sides)
+{
+    int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    int64_t q = blockIdx.x * (int64_t)(blockDim.x / 32) + warp;
+    if (q >= count) return;
+    Geom G = node_geom(g, D, l, nodes[q]);
+    bool any = false, lo = false, hi = false;
+    for (int64_t i = lane; i < m; i += 32) {
+        const double *x = X + 3 * i;
+        bool in = x[0] >= G.blo[0] && x[0] <= G.bhi[0] && x[1] >= G.blo[1] && x[1] <= G.bhi[1] && x[2] >= G.blo[2] &&
+                  x[2] <= G.bhi[2];
+        if (in) {
+            any = true;
+            lo = lo || (flags[i] & 1);
+            hi = hi || (flags[i] & 2);
+        }
+    }
+    any = __any_sync(0xffffffffu, any);
+    lo = __any_sync(0xffffffffu, lo);
+    hi = __any_sync(0xffffffffu, hi);
+    if (lane == 0) {
+        if (any && lo && hi) {
+            decision[q] = 1;
+            sides[q] = 0;
+        } else {
+            decision[q] = 0;
+            sides[q] = (!any || (!lo && !hi)) ? 3 : (!hi ? 1 : 2);
+        }
+    }
+}
+
+// Flags the grid points of pending small nodes whose mean/variance is not yet in the table.
+__global__ void k_mark_small_points(GridDev g, int D, int l, const int64_t *nodes, int64_t count,
+                                    const int8_t *decision, const uint8_t *have, uint8_t *need)
+{
+    int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= count || decision[q] != 0) return;
+    Geom G = node_geom(g, D, l, nodes[q]);
+    if (!is_small(G)) return;
+    for (int64_t c = G.p0[2]; c <= G.p1[2]; ++c)
+        for (int64_t b = G.p0[1]; b <= G.p1[1]; ++b)
+            for (int64_t a = G.p0[0]; a <= G.p1[0]; ++a) {
+                int64_t p = a + (int64_t)g.n[0] * (b + (int64_t)g.n[1] * c);
+                if (!have[p]) need[p] = 1;
+            }
+}
+
+__global__ void k_scatter_mv(const int64_t *pts, int64_t count, const float *mean, const float *var, float2 *mv,
+                             uint8_t *have)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    int64_t p = pts[i];
+    mv[p] = make_float2(mean[i], var[i]);
+    have[p] = 1;
+}
+
+// Exact minimum over the grid points of small pending nodes -> bound -> decision.
+__global__ void k_small_bound(GridDev g, int D, int l, const int64_t *nodes, int64_t count, const float2 *mv,
+                              double theta, double alpha, double sf2, int8_t *decision, const int8_t *sides,
+                              double *bound)
+{
+    int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= count || decision[q] != 0) return;
+    Geom G = node_geom(g, D, l, nodes[q]);
+    if (!is_small(G)) return;
+    double glo = INFINITY, ghi = INFINITY;
+    for (int64_t c = G.p0[2]; c <= G.p1[2]; ++c)
+        for (int64_t b = G.p0[1]; b <= G.p1[1]; ++b)
+            for (int64_t a = G.p0[0]; a <= G.p1[0]; ++a) {
+                float2 v = mv[a + (int64_t)g.n[0] * (b + (int64_t)g.n[1] * c)];
+                double var = fmax((double)v.y, 1e-12 * sf2);
+                double gg = (theta - (double)v.x) / sqrt(var);
+                glo = fmin(glo, gg);
+                ghi = fmin(ghi, -gg);
+            }
+    double dcount = (double)((G.p1[0] - G.p0[0] + 1) * (G.p1[1] - G.p0[1] + 1) * (G.p1[2] - G.p0[2] + 1));
+    double bnd = bound_of(sides[q], dcount, glo, ghi);
+    bound[q] = bnd;
+    decision[q] = bnd > alpha ? 2 : 0;
+}
+
+// Pending large nodes -> compact list (positions in the frontier).
+__global__ void k_flag_large(GridDev g, int D, int l, const int64_t *nodes, int64_t count, const int8_t *decision,
+                             uint8_t *flag)
+{
+    int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= count) return;
+    bool f = false;
+    if (decision[q] == 0) f = !is_small(node_geom(g, D, l, nodes[q]));
+    flag[q] = f ? 1 : 0;
+}
+
+// Lattice points (3x3x3 per node; corners, edge/face midpoints, centre, x fastest).
+__global__ void k_lattice_points(GridDev g, int D, int l, const int64_t *nodes, const int64_t *pend, int64_t npend,
+                                 int64_t first, int64_t cnt, double *xyz)
+{
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= cnt) return;
+    int64_t gi = first + e, q = gi / 27;
+    int t = (int)(gi % 27);
+    Geom G = node_geom(g, D, l, nodes[pend[q]]);
+    int id[3] = {t % 3, (t / 3) % 3, t / 9};
+    for (int d = 0; d < 3; ++d) xyz[3 * e + d] = G.blo[d] + 0.5 * (double)id[d] * (G.bhi[d] - G.blo[d]);
+}
+
+// Best lattice point per node and side (lowest g; first in x-fastest order on ties).
+struct MinState {
+    double x[2][3];
+    float g[2];
+    float grad[2][3];
+};
+
+__global__ void k_lattice_best(const float4 *ev, int64_t npend, MinState *ms)
+{
+    int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= npend) return;
+    MinState s;
+    for (int side = 0; side < 2; ++side) {
+        float sg = side == 0 ? 1.f : -1.f;
+        int best = 0;
+        float bg = sg * ev[q * 27].x;
+        for (int t = 1; t < 27; ++t) {
+            float v = sg * ev[q * 27 + t].x;
+            if (v < bg) { bg = v; best = t; }
+        }
+        float4 e = ev[q * 27 + best];
+        s.g[side] = bg;
+        s.grad[side][0] = sg * e.y;
+        s.grad[side][1] = sg * e.z;
+        s.grad[side][2] = sg * e.w;
+        s.x[side][0] = best % 3;  // lattice indices; converted to coordinates by the caller kernel
+        s.x[side][1] = (best / 3) % 3;
+        s.x[side][2] = best / 9;
+    }
+    ms[q] = s;
+}
+
+__global__ void k_lattice_coords(GridDev g, int D, int l, const int64_t *nodes, const int64_t *pend, int64_t npend,
+                                 MinState *ms)
+{
+    int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= npend) return;
+    Geom G = node_geom(g, D, l, nodes[pend[q]]);
+    for (int side = 0; side < 2; ++side)
+        for (int d = 0; d < 3; ++d) ms[q].x[side][d] = G.blo[d] + 0.5 * ms[q].x[side][d] * (G.bhi[d] - G.blo[d]);
+}
+
+// Candidate of projected step t for every (node, side): x' = clamp(x + eta_t w u/|u|_inf), u = -grad g * w.
+__global__ void k_candidates(GridDev g, int D, int l, const int64_t *nodes, const int64_t *pend, int64_t npend,
+                             const MinState *ms, int step, int64_t first, int64_t cnt, double *xyz, uint8_t *valid)
+{
+    int64_t le = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (le >= cnt) return;
+    int64_t e = first + le;
+    int64_t q = e / 2;
+    int side = (int)(e % 2);
+    Geom G = node_geom(g, D, l, nodes[pend[q]]);
+    double w[3], u[3], un = 0.0;
+    for (int d = 0; d < 3; ++d) {
+        w[d] = G.bhi[d] - G.blo[d];
+        u[d] = -(double)ms[q].grad[side][d] * w[d];
+        un = fmax(un, fabs(u[d]));
+    }
+    double eta = 0.25 * ldexp(1.0, -step);
+    for (int d = 0; d < 3; ++d) {
+        double xn = un > 0.0 ? ms[q].x[side][d] + eta * w[d] * u[d] / un : ms[q].x[side][d];
+        xyz[3 * le + d] = xn < G.blo[d] ? G.blo[d] : (xn > G.bhi[d] ? G.bhi[d] : xn);
+    }
+    valid[le] = un > 0.0 ? 1 : 0;
+}
+
+__global__ void k_accept(const double *xyz, const uint8_t *valid, const float4 *ev, int64_t first, int64_t cnt,
+                         MinState *ms)
+{
+    int64_t le = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (le >= cnt) return;
+    int64_t e = first + le;
+    int64_t q = e / 2;
+    int side = (int)(e % 2);
+    if (!valid[le]) return;
+    float sg = side == 0 ? 1.f : -1.f;
+    float v = sg * ev[le].x;
+    if (v < ms[q].g[side]) {
+        ms[q].g[side] = v;
+        ms[q].grad[side][0] = sg * ev[le].y;
+        ms[q].grad[side][1] = sg * ev[le].z;
+        ms[q].grad[side][2] = sg * ev[le].w;
+        for (int d = 0; d < 3; ++d) ms[q].x[side][d] = xyz[3 * le + d];
+    }
+}
+
+__global__ void k_large_bound(GridDev g, int D, int l, const int64_t *nodes, const int64_t *pend, int64_t npend,
+                              const MinState *ms, double alpha, int8_t *decision, const int8_t *sides, double *bound)
+{
+    int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= npend) return;
+    int64_t node = pend[q];
+    Geom G = node_geom(g, D, l, nodes[node]);
+    double dcount = (double)((G.p1[0] - G.p0[0] + 1) * (G.p1[1] - G.p0[1] + 1) * (G.p1[2] - G.p0[2] + 1));
+    double bnd = bound_of(sides[node], dcount, (double)ms[q].g[0], (double)ms[q].g[1]);
+    bound[node] = bnd;
+    decision[node] = bnd > alpha ? 2 : 0;
+}
+
+// Subdivided nodes -> children (next frontier) or, at the last level, cells of S.
+__global__ void k_children(GridDev g, int D, int l, const int64_t *nodes, int64_t count, const int8_t *decision,
+                           int64_t *next, unsigned long long *nnext, uint8_t *leaf, unsigned long long *nsub)
+{
+    int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    bool sub = q < count && decision[q] > 0;
+    unsigned mask = __ballot_sync(0xffffffffu, sub);
+    if ((threadIdx.x & 31) == 0 && mask) atomicAdd(nsub, (unsigned long long)__popc(mask));
+    if (!sub) return;
+    int64_t code = nodes[q];
+    int64_t i = code & 0x1FFFFF, j = (code >> 21) & 0x1FFFFF, k = (code >> 42) & 0x1FFFFF;
+    if (l == D) {
+        leaf[i + (int64_t)(g.n[0] - 1) * (j + (int64_t)(g.n[1] - 1) * k)] = 1;
+        return;
+    }
+    int64_t sc = (int64_t)1 << (D - l - 1);
+    int64_t out[8];
+    int c = 0;
+    for (int b = 0; b < 8; ++b) {
+        int64_t ci = 2 * i + (b & 1), cj = 2 * j + ((b >> 1) & 1), ck = 2 * k + ((b >> 2) & 1);
+        if (ci * sc < g.n[0] - 1 && cj * sc < g.n[1] - 1 && ck * sc < g.n[2] - 1) out[c++] = ci | (cj << 21) | (ck << 42);
+    }
+    unsigned long long base = atomicAdd(nnext, (unsigned long long)c);
+    for (int t = 0; t < c; ++t) next[base + t] = out[t];
+}
+
+unsigned nb(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+struct OctBuffers {
+    int64_t *front[2];
+    int8_t *decision, *sides;
+    double *bound;
+    uint8_t *obs_flags, *have, *need, *lflag, *leaf;
+    float2 *mv;
+    int64_t *plist, *pend;
+    float *tmp_mean, *tmp_var;
+    double *xyz;
+    float *W, *P;
+    float4 *ev, *lat;
+    uint8_t *cvalid;
+    MinState *ms;
+    unsigned long long *counters;  // [0] nnext, [1] nsub
+    void *cscr;
+    size_t csb;
+};
+
+}  // namespace
+
+// Trace hook for tests: records one level's frontier, decisions and bounds on the host.
+struct OctTrace {
+    int level;
+    int64_t *nodes;
+    int8_t *decision;
+    double *bound;
+    int64_t capacity;
+    int64_t count;
+};
+
+static gpr_status run_eval(const gpr_model *M, const EvalModel &E, OctBuffers &B, int64_t cnt, double theta,
+                           cudaStream_t st)
+{
+    dim3 grid((unsigned)(M->mp / BN), nb(cnt, BM));
+    {
+        ProfScope ps("oct_eval_w", st);
+        k_eval_w<<<grid, NT, 0, st>>>(E, B.xyz, cnt, B.W);
+    }
+    note_launch();
+    k_eval_p<<<grid, NT, 0, st>>>(E, B.W, cnt, B.P);
+    note_launch();
+    k_eval_reduce<<<nb(cnt, 8), 256, 0, st>>>(E, B.xyz, B.W, B.P, cnt, theta, B.ev);
+    note_launch();
+    GPR_CUDA_TRY(cudaGetLastError());
+    return GPR_OK;
+}
+
+gpr_status octree_lcp(gpr_model *M, const gpr_grid *grid, double theta, int D, const gpr_lcp_options *opts,
+                      float *lcp, gpr_adaptive_stats *stats, cudaStream_t st, OctTrace *trace)
+{
+    GridDev g = make_grid(grid);
+    int64_t n = g.npts(), nc = g.ncells(), m = M->m;
+    size_t te = table_elems(M, g);
+    int T = opts->max_iters_min;
+    // nodes with >= 4 cells per side: at most prod ceil((n_d - 1) / 4) of them in any level
+    int64_t max_large = 1;
+    for (int d = 0; d < 3; ++d) max_large *= (int64_t)(g.n[d] - 1 + 3) / 4;
+    // workspace (slot 0): tables, frontier, per-point mean/var table, evaluation chunk
+    size_t csb = compact_scratch_bytes(nc > n ? nc : n);
+    size_t bytes = Carver::round(te * sizeof(float)) + Carver::round(te * sizeof(double)) +
+                   Carver::round(te * sizeof(float2)) + 2 * Carver::round((size_t)nc * 8) + 2 * Carver::round((size_t)nc) +
+                   Carver::round((size_t)nc * 8) + Carver::round((size_t)m) + 3 * Carver::round((size_t)n) +
+                   Carver::round((size_t)nc) + Carver::round((size_t)nc) + Carver::round((size_t)n * sizeof(float2)) +
+                   Carver::round((size_t)n * 8) + Carver::round((size_t)nc * 8) + 2 * Carver::round((size_t)n * 4) +
+                   Carver::round((size_t)kEvalChunk * 24) + 2 * Carver::round((size_t)kEvalChunk * M->mp * 4) +
+                   Carver::round((size_t)kEvalChunk * 16) + Carver::round((size_t)kEvalChunk) +
+                   Carver::round((size_t)nc * sizeof(MinState)) + Carver::round((size_t)max_large * 27 * 16) + 512 +
+                   csb + 8192;
+    GPR_TRY(ws_reserve(M, 0, bytes, st));
+    Carver cv{(char *)M->ws[0]};
+    float *T32 = cv.take<float>(te);
+    double *T64 = cv.take<double>(te);
+    float2 *Tff = cv.take<float2>(te);
+    OctBuffers B;
+    B.front[0] = cv.take<int64_t>((size_t)nc);
+    B.front[1] = cv.take<int64_t>((size_t)nc);
+    B.decision = cv.take<int8_t>((size_t)nc);
+    B.sides = cv.take<int8_t>((size_t)nc);
+    B.bound = cv.take<double>((size_t)nc);
+    B.obs_flags = cv.take<uint8_t>((size_t)m);
+    B.have = cv.take<uint8_t>((size_t)n);
+    B.need = cv.take<uint8_t>((size_t)n);
+    uint8_t *pflag = cv.take<uint8_t>((size_t)n);
+    B.lflag = cv.take<uint8_t>((size_t)nc);
+    B.leaf = cv.take<uint8_t>((size_t)nc);
+    B.mv = cv.take<float2>((size_t)n);
+    B.plist = cv.take<int64_t>((size_t)n);
+    B.pend = cv.take<int64_t>((size_t)nc);
+    B.tmp_mean = cv.take<float>((size_t)n);
+    B.tmp_var = cv.take<float>((size_t)n);
+    B.xyz = cv.take<double>((size_t)kEvalChunk * 3);
+    B.W = cv.take<float>((size_t)kEvalChunk * M->mp);
+    B.P = cv.take<float>((size_t)kEvalChunk * M->mp);
+    B.ev = cv.take<float4>((size_t)kEvalChunk);
+    B.lat = cv.take<float4>((size_t)max_large * 27);
+    B.cvalid = cv.take<uint8_t>((size_t)kEvalChunk);
+    B.ms = cv.take<MinState>((size_t)nc);
+    B.counters = cv.take<unsigned long long>(4);
+    B.csb = csb;
+    B.cscr = cv.take<char>(csb);
+    int32_t *slot = (int32_t *)B.tmp_mean;  // reused by the leaf phase (n int32 fits in n floats)
+    int64_t *clist = B.pend;                 // reused by the leaf phase (nc int64)
+
+    EvalModel E;
+    E.X32 = M->X32; E.BT32 = M->BT32; E.Linv32 = M->Linv32; E.alpha32 = M->alpha32;
+    E.m = M->m; E.mp = M->mp; E.kind = M->kp.kind; E.sf2 = (float)M->kp.sf2;
+    for (int d = 0; d < 3; ++d) E.ell[d] = (float)M->kp.ell[d];
+
+    GPR_TRY(build_tables(M, g, T64, T32, st, Tff));
+    GPR_CUDA_TRY(cudaMemsetAsync(B.have, 0, (size_t)n, st));
+    GPR_CUDA_TRY(cudaMemsetAsync(B.leaf, 0, (size_t)nc, st));
+    k_obs_flags<<<nb(m, 128), 128, 0, st>>>(M->mu_obs, M->var_obs, m, theta, opts->alpha, B.obs_flags);
+    note_launch();
+    int64_t root = 0;
+    GPR_CUDA_TRY(cudaMemcpyAsync(B.front[0], &root, sizeof root, cudaMemcpyHostToDevice, st));
+    int64_t count = 1;
+    int cur = 0;
+    if (stats) memset(stats, 0, sizeof *stats);
+    for (int l = 0; l <= D && count > 0; ++l) {
+        const int64_t *nodes = B.front[cur];
+        int64_t s = (int64_t)1 << (D - l);
+        ProfScope lvl("oct_level", st);
+        k_ptest<<<nb(count, 8), 256, 0, st>>>(g, D, l, nodes, count, M->X, m, B.obs_flags, B.decision, B.sides);
+        note_launch();
+        // small nodes: exact minimum over grid points from the per-point table
+        {
+            GPR_CUDA_TRY(cudaMemsetAsync(B.need, 0, (size_t)n, st));
+            k_mark_small_points<<<nb(count, 128), 128, 0, st>>>(g, D, l, nodes, count, B.decision, B.have, B.need);
+            note_launch();
+            int64_t nneed = 0;
+            GPR_TRY(compact_flags(B.need, n, B.plist, nullptr, &nneed, B.cscr, B.csb, st));
+            if (nneed > 0) {
+                launch_meanvar32(M, g, T32, B.plist, 0, nneed, B.tmp_mean, B.tmp_var, st);
+                launch_mean_compensated(M, g, Tff, T64, B.plist, 0, nneed, B.tmp_mean, st);
+                k_scatter_mv<<<nb(nneed, 256), 256, 0, st>>>(B.plist, nneed, B.tmp_mean, B.tmp_var, B.mv, B.have);
+                note_launch();
+            }
+        }
+        k_small_bound<<<nb(count, 128), 128, 0, st>>>(g, D, l, nodes, count, B.mv, theta, opts->alpha, M->kp.sf2,
+                                                      B.decision, B.sides, B.bound);
+        note_launch();
+        // large nodes: lattice start + projected gradient steps
+        if (s > 2) {
+            k_flag_large<<<nb(count, 256), 256, 0, st>>>(g, D, l, nodes, count, B.decision, B.lflag);
+            note_launch();
+            int64_t npend = 0;
+            GPR_TRY(compact_flags(B.lflag, count, B.pend, nullptr, &npend, B.cscr, B.csb, st));
+            if (npend > 0) {
+                for (int64_t first = 0; first < npend * 27; first += kEvalChunk) {
+                    int64_t cnt = npend * 27 - first < kEvalChunk ? npend * 27 - first : kEvalChunk;
+                    k_lattice_points<<<nb(cnt, 256), 256, 0, st>>>(g, D, l, nodes, B.pend, npend, first, cnt, B.xyz);
+                    note_launch();
+                    GPR_TRY(run_eval(M, E, B, cnt, theta, st));
+                    GPR_CUDA_TRY(cudaMemcpyAsync(B.lat + first, B.ev, sizeof(float4) * cnt, cudaMemcpyDeviceToDevice,
+                                                 st));
+                }
+                k_lattice_best<<<nb(npend, 128), 128, 0, st>>>(B.lat, npend, B.ms);
+                note_launch();
+                k_lattice_coords<<<nb(npend, 128), 128, 0, st>>>(g, D, l, nodes, B.pend, npend, B.ms);
+                note_launch();
+                for (int t = 0; t < T; ++t) {
+                    for (int64_t first = 0; first < 2 * npend; first += kEvalChunk) {
+                        int64_t cnt = 2 * npend - first < kEvalChunk ? 2 * npend - first : kEvalChunk;
+                        k_candidates<<<nb(cnt, 256), 256, 0, st>>>(g, D, l, nodes, B.pend, npend, B.ms, t, first, cnt,
+                                                                   B.xyz, B.cvalid);
+                        note_launch();
+                        GPR_TRY(run_eval(M, E, B, cnt, theta, st));
+                        k_accept<<<nb(cnt, 256), 256, 0, st>>>(B.xyz, B.cvalid, B.ev, first, cnt, B.ms);
+                        note_launch();
+                    }
+                }
+                k_large_bound<<<nb(npend, 128), 128, 0, st>>>(g, D, l, nodes, B.pend, npend, B.ms, opts->alpha,
+                                                             B.decision, B.sides, B.bound);
+                note_launch();
+            }
+        }
+        GPR_CUDA_TRY(cudaMemsetAsync(B.counters, 0, 2 * sizeof(unsigned long long), st));
+        k_children<<<nb(count, 256), 256, 0, st>>>(g, D, l, nodes, count, B.decision, B.front[1 - cur], B.counters,
+                                                   B.leaf, B.counters + 1);
+        note_launch();
+        GPR_CUDA_TRY(cudaGetLastError());
+        unsigned long long hc[2] = {0, 0};
+        GPR_CUDA_TRY(cudaMemcpyAsync(hc, B.counters, sizeof hc, cudaMemcpyDeviceToHost, st));
+        if (trace && trace->level == l) {
+            int64_t c = count < trace->capacity ? count : trace->capacity;
+            GPR_CUDA_TRY(cudaMemcpyAsync(trace->nodes, nodes, sizeof(int64_t) * c, cudaMemcpyDeviceToHost, st));
+            GPR_CUDA_TRY(cudaMemcpyAsync(trace->decision, B.decision, c, cudaMemcpyDeviceToHost, st));
+            GPR_CUDA_TRY(cudaMemcpyAsync(trace->bound, B.bound, sizeof(double) * c, cudaMemcpyDeviceToHost, st));
+            trace->count = count;
+        }
+        GPR_CUDA_TRY(cudaStreamSynchronize(st));
+        if (stats && l < 24) {
+            stats->nodes_per_level[l] = count;
+            stats->subdiv_per_level[l] = (int64_t)hc[1];
+        }
+        count = (int64_t)hc[0];
+        cur = 1 - cur;
+    }
+    if (trace) return GPR_OK;
+    int64_t leaf_cells = 0, rp = 0, est = 0;
+    gpr_adaptive_stats tmp;
+    memset(&tmp, 0, sizeof tmp);
+    GPR_TRY(lcp_from_kept_cells(M, g, T64, B.leaf, pflag, B.plist, slot, clist, B.cscr, B.csb, lcp_opts(opts, theta),
+                                lcp, &tmp, st));
+    leaf_cells = tmp.leaf_cells;
+    rp = tmp.recon_points;
+    est = tmp.cells_estimated;
+    if (stats) {
+        stats->leaf_cells = leaf_cells;
+        stats->recon_points = rp;
+        stats->cells_estimated = est;
+    }
+    return GPR_OK;
+}
+
+extern "C" gpr_status gpr_lcp_adaptive(gpr_model *M, const gpr_grid *grid, double isovalue, int32_t max_depth,
+                                       const gpr_lcp_options *opts, float *lcp, gpr_adaptive_stats *stats,
+                                       void *stream)
+{
+    if (!M || !grid_valid(grid) || !lcp || !opts_valid(opts) || !isfinite(isovalue)) return GPR_ERR_ARG;
+    if (max_depth < 0 || max_depth > 20) return GPR_ERR_ARG;
+    for (int d = 0; d < 3; ++d)
+        if (((int64_t)1 << max_depth) < (int64_t)grid->n[d] - 1) return GPR_ERR_ARG;
+    return octree_lcp(M, grid, isovalue, max_depth, opts, lcp, stats, (cudaStream_t)stream, nullptr);
+}
+
+// Test hook (not in the public header): the frontier, decisions and bounds of one level.
+extern "C" gpr_status gpr_octree_trace(gpr_model *M, const gpr_grid *grid, double isovalue, int32_t max_depth,
+                                       const gpr_lcp_options *opts, int32_t level, int64_t *nodes, int8_t *decision,
+                                       double *bound, int64_t capacity, int64_t *count, void *stream)
+{
+    if (!M || !grid_valid(grid) || !opts_valid(opts) || !nodes || !decision || !bound || !count) return GPR_ERR_ARG;
+    if (max_depth < 0 || max_depth > 20 || level < 0 || level > max_depth) return GPR_ERR_ARG;
+    OctTrace tr{level, nodes, decision, bound, capacity, 0};
+    gpr_status s = octree_lcp(M, grid, isovalue, max_depth, opts, nullptr, nullptr, (cudaStream_t)stream, &tr);
+    *count = tr.count;
+    return s;
+}

@@ -195,7 +195,8 @@ __global__ void k_alpha_obs(const double *Linv, int64_t mb, const double *vy, co
 
 // BT[i][j] = Linv[j][i] for i <= j < m, else 0  (mp x mp), FP64 and FP32.
 __global__ void k_operands(const double *Linv, int64_t mb, int64_t m, int64_t mp, double *BT64, float *BT32,
-                           const double *vy, float *vy32, const double *alpha, float2 *alpha_ff)
+                           const double *vy, float *vy32, const double *alpha, float2 *alpha_ff, float *Linv32,
+                           const double *X, float *X32, float *alpha32)
 {
     int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (idx < mp) {
@@ -203,12 +204,15 @@ __global__ void k_operands(const double *Linv, int64_t mb, int64_t m, int64_t mp
         double a = idx < m ? alpha[idx] : 0.0;
         float h = (float)a;
         alpha_ff[idx] = make_float2(h, (float)(a - (double)h));
+        alpha32[idx] = h;
     }
+    if (idx < 3 * m) X32[idx] = (float)X[idx];
     if (idx >= mp * mp) return;
     int64_t i = idx / mp, j = idx % mp;
     double v = (i < m && j < m && i <= j) ? Linv[j * mb + i] : 0.0;
     BT64[idx] = v;
     BT32[idx] = (float)v;
+    Linv32[idx] = (i < m && j < m && j <= i) ? (float)Linv[i * mb + j] : 0.0f;
 }
 
 // Compact the padded mb x mb factor into m x m.
@@ -280,6 +284,9 @@ extern "C" gpr_status gpr_model_create(const double *obs_xyz, const double *y, i
     ALLOC(M->BT32, sizeof(float) * mp * mp);
     ALLOC(M->vy32, sizeof(float) * mp);
     ALLOC(M->alpha_ff, sizeof(float2) * mp);
+    ALLOC(M->Linv32, sizeof(float) * mp * mp);
+    ALLOC(M->X32, sizeof(float) * 3 * m);
+    ALLOC(M->alpha32, sizeof(float) * mp);
     ALLOC(A, sizeof(double) * mb * mb);
 #undef ALLOC
     if (cudaMemcpyAsync(M->X, obs_xyz, sizeof(double) * 3 * m, cudaMemcpyHostToDevice, st) != cudaSuccess ||
@@ -312,7 +319,7 @@ extern "C" gpr_status gpr_model_create(const double *obs_xyz, const double *y, i
     k_alpha_obs<<<nblk(m, 128), 128, 0, st>>>(M->Linv, mb, M->vy, M->y, m, noise_var, signal_var, M->alpha,
                                                M->mu_obs, M->var_obs);
     note_launch();
-    k_operands<<<nblk(mp * mp, 256), 256, 0, st>>>(M->Linv, mb, m, mp, M->BT64, M->BT32, M->vy, M->vy32, M->alpha, M->alpha_ff);
+    k_operands<<<nblk(mp * mp, 256), 256, 0, st>>>(M->Linv, mb, m, mp, M->BT64, M->BT32, M->vy, M->vy32, M->alpha, M->alpha_ff, M->Linv32, M->X, M->X32, M->alpha32);
     note_launch();
     k_unpad<<<nblk(m * m, 256), 256, 0, st>>>(A, mb, m, M->L);
     note_launch();
@@ -339,7 +346,7 @@ extern "C" gpr_status gpr_model_destroy(gpr_model *M)
     if (!M) return GPR_ERR_ARG;
     cudaDeviceSynchronize();
     cudaFree(M->X); cudaFree(M->y); cudaFree(M->L); cudaFree(M->Linv); cudaFree(M->vy); cudaFree(M->alpha);
-    cudaFree(M->mu_obs); cudaFree(M->var_obs); cudaFree(M->BT64); cudaFree(M->BT32); cudaFree(M->vy32); cudaFree(M->alpha_ff);
+    cudaFree(M->mu_obs); cudaFree(M->var_obs); cudaFree(M->BT64); cudaFree(M->BT32); cudaFree(M->vy32); cudaFree(M->alpha_ff); cudaFree(M->Linv32); cudaFree(M->X32); cudaFree(M->alpha32);
     for (int w = 0; w < 2; ++w)
         if (M->ws[w]) cudaFree(M->ws[w]);
     delete M;

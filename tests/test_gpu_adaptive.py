@@ -1,0 +1,135 @@
+"""GPU parity of the adaptive path (Algorithm 1 + leaf reconstruction) against the oracle
+and against the GPU dense field.
+
+Node decisions: the p-test decisions (FP64 on both sides) must agree exactly; bound decisions
+may differ only where the oracle's bound lies within a factor 3 of alpha (the device evaluates
+mu, sigma and their gradients in FP32 and its minimiser path can differ near the threshold).
+Fields: equal to the dense field on S (same FP64 statistics, bit for bit) and 0 elsewhere.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from gpu_util import model_of, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    return torch_cuda()
+
+
+@pytest.fixture(scope="module")
+def g():
+    import paper_2512_12442_gb300 as g
+    return g
+
+
+def _compare_level(om, n, D, l, th, nodes, dec, bnd, alpha=1e-3, sample=None, seed=0):
+    idx = np.arange(len(nodes))
+    if sample is not None and len(idx) > sample:
+        idx = np.sort(np.random.default_rng(seed).choice(len(idx), sample, replace=False))
+    odec, obnd, _ = om.octree_level(n, D, l, th, nodes[idx], alpha=alpha)
+    gd = dec[idx]
+    # p-test decisions agree exactly
+    assert np.array_equal(odec == 1, gd == 1), (l, np.sum((odec == 1) != (gd == 1)))
+    keep_o = odec > 0
+    keep_g = gd > 0
+    mism = keep_o != keep_g
+    near = (obnd >= alpha / 3) & (obnd <= 3 * alpha)
+    assert np.all(near[mism]), (l, obnd[mism & ~near][:10], bnd[idx][mism & ~near][:10])
+    return int(mism.sum()), len(idx)
+
+
+@pytest.mark.parametrize("case", ["small", "config1"])
+def test_octree_levels_match_oracle(torch, g, case):
+    if case == "small":
+        w = workloads.small(5, 60, 17, ell=(0.2, 0.2, 0.2))
+    else:
+        w = workloads.config1()
+    M = model_of(w)
+    om = oracle.Model.from_workload(w)
+    n, D, th = w.n, w.max_depth, w.isovalues[0]
+    grid = g.make_grid(n)
+    total_mism = 0
+    for l in range(D + 1):
+        nodes, dec, bnd = g.gpr_octree_trace(M, grid, th, D, g.lcp_options(), l)
+        if len(nodes) == 0:
+            break
+        mm, cnt = _compare_level(om, n, D, l, th, nodes, dec, bnd)
+        total_mism += mm
+    assert total_mism <= 0.01 * (n - 1) ** 3 + 2
+
+
+def _fields(g, torch, M, n, D, th, **kw):
+    grid = g.make_grid(n)
+    a = torch.zeros((n - 1) ** 3, dtype=torch.float32, device="cuda")
+    d = torch.zeros_like(a)
+    sa = g.gpr_lcp_adaptive(M, grid, th, D, g.lcp_options(**kw), a)
+    sd = g.gpr_lcp_dense(M, grid, th, g.lcp_options(**kw), d)
+    g.gpr_sync()
+    return a.cpu().numpy().astype(np.float64), d.cpu().numpy().astype(np.float64), sa, sd
+
+
+@pytest.mark.parametrize("case", ["small", "config1"])
+def test_adaptive_field_vs_dense_and_oracle(torch, g, case):
+    """Adaptive = dense on S and 0 elsewhere; against the oracle's adaptive field within 1e-4
+    except on cells whose membership of S differs near alpha (their LCP is below ~alpha)."""
+    w = workloads.small(5, 60, 17, ell=(0.2, 0.2, 0.2)) if case == "small" else workloads.config1()
+    M = model_of(w)
+    n, D, th = w.n, w.max_depth, w.isovalues[0]
+    a, d, sa, sd = _fields(g, torch, M, n, D, th)
+    nz = a != 0
+    assert np.array_equal(a[nz], d[nz])
+    assert sa["leaf_cells"] <= (n - 1) ** 3 and sa["leaf_cells"] > 0
+    om = oracle.Model.from_workload(w)
+    fo, leaves, _ = om.lcp_adaptive(n, D, th)
+    lin = (leaves & 0x1FFFFF) + (n - 1) * (((leaves >> 21) & 0x1FFFFF) + (n - 1) * ((leaves >> 42) & 0x1FFFFF))
+    in_o = np.zeros(a.size, bool); in_o[lin] = True
+    diff = np.abs(a - fo)
+    # cells the oracle kept and the GPU dropped (or vice versa) carry an LCP below a few alpha
+    assert diff.max() <= 5e-3, diff.max()
+    assert np.sum(diff > 1e-4) <= 0.01 * a.size + 2
+    # RMSE adaptive vs dense (the paper's accuracy metric, Sec. 5.2): small
+    assert np.sqrt(np.mean((a - d) ** 2)) < 2e-3
+
+
+def test_adaptive_config2_full_size_sampled_nodes(torch, g):
+    """Paper-scale field (m=500, 128^3, D=7): sampled nodes of the deepest four levels against the
+    oracle's per-node decision (each node's decision depends only on the node)."""
+    w = workloads.config2()
+    M = model_of(w)
+    om = oracle.Model.from_workload(w)
+    th = w.isovalues[1]
+    grid = g.make_grid(w.n)
+    for l in (2, 4, 5, 6, 7):
+        nodes, dec, bnd = g.gpr_octree_trace(M, grid, th, w.max_depth, g.lcp_options(), l)
+        assert len(nodes) > 0
+        mm, cnt = _compare_level(om, w.n, w.max_depth, l, th, nodes, dec, bnd, sample=150 if l >= 5 else None,
+                                 seed=l)
+        assert mm <= max(3, 0.03 * cnt)
+
+
+def test_adaptive_config2_full_field(torch, g):
+    """Full adaptive field at the three isovalues, launched as the bench does: equal to the dense
+    field on S, zero elsewhere, RMSE vs dense small, and fewer reconstructed points."""
+    w = workloads.config2()
+    M = model_of(w)
+    for th in w.isovalues:
+        a, d, sa, sd = _fields(g, torch, M, w.n, w.max_depth, th)
+        nz = a != 0
+        assert np.array_equal(a[nz], d[nz])
+        assert np.sqrt(np.mean((a - d) ** 2)) < 1e-3
+        assert sa["recon_points"] <= sd["recon_points"]
+        assert sum(sa["nodes_per_level"]) > 0
+
+
+def test_adaptive_argument_checks(torch, g):
+    w = workloads.small(1, 10, 9)
+    M = model_of(w)
+    out = torch.zeros(512, dtype=torch.float32, device="cuda")
+    with pytest.raises(g.GPRError) as e:
+        g.gpr_lcp_adaptive(M, g.make_grid(9), 0.0, 2, g.lcp_options(), out)  # 2^2 < 8 cells
+    assert e.value.status == g.GPR_ERR_ARG
