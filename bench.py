@@ -42,7 +42,8 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--mode", default="dense", choices=["dense", "adaptive"])
-    p.add_argument("--prec", default="fp32", choices=["fp32", "fp64"])
+    p.add_argument("--prec", default="tf32x3", choices=["fp32", "fp64", "tf32", "tf32x3", "bf16", "bf16x3"],
+                   help="precision of the pre-classification / octree pass")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-sample", type=int, default=64, help="cells per axis of the oracle sample")
     p.add_argument("--case", default="full", choices=["full", "small"],
@@ -175,14 +176,15 @@ def main():
         grid = g.make_grid(n)
         out = torch.zeros((n - 1) ** 3, dtype=torch.float32, device="cuda")
         M = g.gpr_model_create(w.X, w.y, w.kernel, w.ell, w.sf2, w.sn2)
-        st = g.gpr_lcp_dense(M, grid, w.isovalues[1], g.lcp_options(), out)
+        st = g.gpr_lcp_dense(M, grid, w.isovalues[1], g.lcp_options(prec=g.GPR_P_TF32X3), out)
         g.gpr_sync()
         print(json.dumps({"case": "small", "grid": n, "m": w.m, **{k: st[k] for k in ("recon_points", "leaf_cells")}}))
         return
     n = w.n
     ncell = (n - 1) ** 3
     grid = g.make_grid(n)
-    prec = g.GPR_P_FP64 if args.prec == "fp64" else g.GPR_P_FP32
+    prec = {"fp64": g.GPR_P_FP64, "fp32": g.GPR_P_FP32, "tf32": g.GPR_P_TF32, "tf32x3": g.GPR_P_TF32X3,
+            "bf16": g.GPR_P_BF16, "bf16x3": g.GPR_P_BF16X3}[args.prec]
     opts = g.lcp_options(prec=prec)
     stream = torch.cuda.current_stream()
     fields = [torch.zeros(ncell, dtype=torch.float32, device="cuda") for _ in w.isovalues]
@@ -226,8 +228,8 @@ def main():
     g.gpr_profile_enable(False)
     launches = g.gpr_launch_count()
     ms = ev0.elapsed_time(ev1) / args.steps
-    prof = {k: g.gpr_profile_read(k) for k in ("w64", "meanvar32", "mean_ff", "stats_from_w64", "cell_prep", "sov",
-                                                "classify", "oct_eval_w")}
+    prof = {k: g.gpr_profile_read(k) for k in ("w64", "meanvar32", "tc_sumsq", "mean_ff", "stats_from_w64", "cell_prep",
+                                                "sov", "classify", "oct_eval_w")}
     g.gpr_sync(stream)
     M.close()
     t_max = ms

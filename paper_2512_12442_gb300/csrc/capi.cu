@@ -114,13 +114,24 @@ extern "C" gpr_status gpr_reconstruct_dense(gpr_model *M, const gpr_grid *grid, 
                                             void *var, void *cov13, void *stream)
 {
     if (!M || !grid_valid(grid) || !mean || !var) return GPR_ERR_ARG;
-    if (!simt_precision(prec)) {
-        if (prec < GPR_P_FP64 || prec > GPR_P_BF16X3) return GPR_ERR_ARG;
-        return GPR_ERR_UNSUPPORTED;
-    }
+    if (prec < GPR_P_FP64 || prec > GPR_P_BF16X3) return GPR_ERR_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     GridDev g = make_grid(grid);
     size_t te = table_elems(M, g);
+    if (tc_precision(prec)) {
+        if (cov13) return GPR_ERR_UNSUPPORTED;  // the tensor-core pass reduces W to |w|^2 on chip
+        size_t np = tc_partial_elems(prec, M, g.npts());
+        size_t bytes = Carver::round(te * sizeof(float)) + Carver::round(te * sizeof(float2)) +
+                       Carver::round(te * sizeof(double)) + Carver::round(np * sizeof(float)) + 1024;
+        GPR_TRY(ws_reserve(M, 0, bytes, st));
+        Carver cv{(char *)M->ws[0]};
+        float *T32 = cv.take<float>(te);
+        float2 *Tff = cv.take<float2>(te);
+        double *T64 = cv.take<double>(te);
+        float *part = cv.take<float>(np);
+        GPR_TRY(build_tables(M, g, T64, T32, st, Tff));
+        return fast_meanvar(M, g, prec, T32, Tff, T64, nullptr, 0, g.npts(), (float *)mean, (float *)var, part, st);
+    }
     if (prec == GPR_P_FP64) {
         size_t rows = slab_rows(g, M->mp, sizeof(double), kWBudget);
         size_t bytes = Carver::round(te * sizeof(double)) + Carver::round(rows * M->mp * sizeof(double)) + 1024;
@@ -263,7 +274,6 @@ extern "C" gpr_status gpr_lcp_dense(gpr_model *M, const gpr_grid *grid, double i
                                     float *lcp, gpr_adaptive_stats *stats, void *stream)
 {
     if (!M || !grid_valid(grid) || !lcp || !opts_valid(opts) || !isfinite(isovalue)) return GPR_ERR_ARG;
-    if (!simt_precision(opts->prec)) return GPR_ERR_UNSUPPORTED;
     cudaStream_t st = (cudaStream_t)stream;
     GridDev g = make_grid(grid);
     int64_t n = g.npts(), nc = g.ncells();
@@ -297,7 +307,8 @@ extern "C" gpr_status gpr_lcp_dense(gpr_model *M, const gpr_grid *grid, double i
     size_t b1 = Carver::round(te * sizeof(float)) + Carver::round(te * sizeof(double)) +
                 2 * Carver::round((size_t)n * sizeof(float)) + Carver::round((size_t)nc) + Carver::round((size_t)n) +
                 Carver::round((size_t)n * sizeof(int64_t)) + Carver::round((size_t)n * sizeof(int32_t)) +
-                Carver::round((size_t)nc * sizeof(int64_t)) + compact_scratch_bytes(nc > n ? nc : n) + 4096;
+                Carver::round((size_t)nc * sizeof(int64_t)) + compact_scratch_bytes(nc > n ? nc : n) +
+                Carver::round(te * sizeof(float2)) + Carver::round(tc_partial_elems(GPR_P_BF16X3, M, n) * 4) + 4096;
     GPR_TRY(ws_reserve(M, 0, b1, st));
     Carver cv{(char *)M->ws[0]};
     float *T32 = cv.take<float>(te);
@@ -311,10 +322,17 @@ extern "C" gpr_status gpr_lcp_dense(gpr_model *M, const gpr_grid *grid, double i
     int64_t *clist = cv.take<int64_t>((size_t)nc);
     size_t csb = compact_scratch_bytes(nc > n ? nc : n);
     void *cscr = cv.take<char>(csb);
-    GPR_TRY(build_tables(M, g, T64, T32, st));
-    launch_meanvar32(M, g, T32, nullptr, 0, n, mean, var, st);
+    float2 *Tff = cv.take<float2>(te);
+    float *part = cv.take<float>(tc_partial_elems(GPR_P_BF16X3, M, n));
+    GPR_TRY(build_tables(M, g, T64, T32, st, Tff));
+    if (tc_precision(opts->prec)) {
+        GPR_TRY(fast_meanvar(M, g, opts->prec, T32, Tff, T64, nullptr, 0, n, mean, var, part, st));
+    } else {
+        launch_meanvar32(M, g, T32, nullptr, 0, n, mean, var, st);
+    }
     double mv, mm;
     prepass_margins(M, mv, mm);
+    if (opts->prec == GPR_P_TF32 || opts->prec == GPR_P_BF16) mv = M->kp.sf2;  // single-pass: ~1e-1 var error
     launch_classify_cells(g, mean, var, isovalue, opts->skip_eps, opts->jitter, mv, mm, keep, st);
     return lcp_from_kept_cells(M, g, T64, keep, pflag, plist, slot, clist, cscr, csb, lo, lcp, stats, st);
 }

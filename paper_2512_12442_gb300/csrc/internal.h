@@ -52,6 +52,13 @@ struct KernParams {
     double sf2;
 };
 
+// Tensor-core B operands (rows of L^-1, K-major, mpt x mpt with mpt = mp rounded up to 256).
+struct TcOperands {
+    int64_t mpt = 0;
+    float *thi = nullptr, *tlo = nullptr;        // TF32 hi/lo (FP32 storage)
+    void *b0 = nullptr, *b1 = nullptr, *b2 = nullptr;  // BF16 slices
+};
+
 struct gpr_model {
     int64_t m = 0;
     int64_t mp = 0;  // m rounded up to a multiple of 64 (GEMM column padding)
@@ -74,6 +81,7 @@ struct gpr_model {
     float *Linv32 = nullptr;   // mp x mp FP32 copy of L^-1 (lower), zero padded
     float *X32 = nullptr;      // m x 3 FP32 observation sites
     float *alpha32 = nullptr;  // mp FP32 alpha
+    TcOperands *tc = nullptr;  // built on first tensor-core use
     // host copies used by the octree p-test
     std::vector<double> hX, hy;
     // two independent workspaces (grow, never shrink): slot 0 for a call's first phase,
@@ -126,6 +134,19 @@ void launch_mean_compensated(const gpr_model *M, const GridDev &g, const float2 
 // Fused FP32 mean/variance (W never stored).
 void launch_meanvar32(const gpr_model *M, const GridDev &g, const float *T32, const int64_t *pts, int64_t pt_base,
                       int64_t count, float *mean, float *var, cudaStream_t st);
+
+// ---- tensor cores (tc.cu)
+bool tc_precision(gpr_precision p);
+gpr_status tc_prepare(gpr_model *M, cudaStream_t st);
+void tc_release(gpr_model *M);
+size_t tc_partial_elems(gpr_precision p, const gpr_model *M, int64_t count);
+gpr_status launch_tc_var(const gpr_model *M, const GridDev &g, gpr_precision prec, const float *T32,
+                         const int64_t *pts, int64_t pt_base, int64_t count, float *partial, float *var, cudaStream_t st);
+// FP32-class mean/variance of a point list in any non-FP64 precision (SIMT FP32 or tensor cores);
+// the mean is always the compensated k . alpha.  `partial` needs tc_partial_elems floats (TC only).
+gpr_status fast_meanvar(gpr_model *M, const GridDev &g, gpr_precision prec, const float *T32, const float2 *Tff,
+                        const double *T64, const int64_t *pts, int64_t pt_base, int64_t count, float *mean, float *var,
+                        float *partial, cudaStream_t st);
 
 // ---- LCP (lcp.cu)
 struct LcpOpts {

@@ -503,6 +503,7 @@ struct OctBuffers {
     double *xyz;
     float *W, *P;
     float4 *ev, *lat;
+    float *part;
     uint8_t *cvalid;
     MinState *ms;
     unsigned long long *counters;  // [0] nnext, [1] nsub
@@ -559,7 +560,7 @@ gpr_status octree_lcp(gpr_model *M, const gpr_grid *grid, double theta, int D, c
                    Carver::round((size_t)kEvalChunk * 24) + 2 * Carver::round((size_t)kEvalChunk * M->mp * 4) +
                    Carver::round((size_t)kEvalChunk * 16) + Carver::round((size_t)kEvalChunk) +
                    Carver::round((size_t)nc * sizeof(MinState)) + Carver::round((size_t)max_large * 27 * 16) + 512 +
-                   csb + 8192;
+                   csb + Carver::round(tc_partial_elems(GPR_P_BF16X3, M, n) * 4) + 8192;
     GPR_TRY(ws_reserve(M, 0, bytes, st));
     Carver cv{(char *)M->ws[0]};
     float *T32 = cv.take<float>(te);
@@ -592,6 +593,7 @@ gpr_status octree_lcp(gpr_model *M, const gpr_grid *grid, double theta, int D, c
     B.counters = cv.take<unsigned long long>(4);
     B.csb = csb;
     B.cscr = cv.take<char>(csb);
+    B.part = cv.take<float>(tc_partial_elems(GPR_P_BF16X3, M, n));
     int32_t *slot = (int32_t *)B.tmp_mean;  // reused by the leaf phase (n int32 fits in n floats)
     int64_t *clist = B.pend;                 // reused by the leaf phase (nc int64)
 
@@ -624,8 +626,8 @@ gpr_status octree_lcp(gpr_model *M, const gpr_grid *grid, double theta, int D, c
             int64_t nneed = 0;
             GPR_TRY(compact_flags(B.need, n, B.plist, nullptr, &nneed, B.cscr, B.csb, st));
             if (nneed > 0) {
-                launch_meanvar32(M, g, T32, B.plist, 0, nneed, B.tmp_mean, B.tmp_var, st);
-                launch_mean_compensated(M, g, Tff, T64, B.plist, 0, nneed, B.tmp_mean, st);
+                gpr_precision pp = opts->prec == GPR_P_FP64 ? GPR_P_FP32 : opts->prec;
+                GPR_TRY(fast_meanvar(M, g, pp, T32, Tff, T64, B.plist, 0, nneed, B.tmp_mean, B.tmp_var, B.part, st));
                 k_scatter_mv<<<nb(nneed, 256), 256, 0, st>>>(B.plist, nneed, B.tmp_mean, B.tmp_var, B.mv, B.have);
                 note_launch();
             }

@@ -349,6 +349,7 @@ extern "C" gpr_status gpr_model_destroy(gpr_model *M)
     cudaFree(M->mu_obs); cudaFree(M->var_obs); cudaFree(M->BT64); cudaFree(M->BT32); cudaFree(M->vy32); cudaFree(M->alpha_ff); cudaFree(M->Linv32); cudaFree(M->X32); cudaFree(M->alpha32);
     for (int w = 0; w < 2; ++w)
         if (M->ws[w]) cudaFree(M->ws[w]);
+    tc_release(M);
     delete M;
     return GPR_OK;
 }

@@ -1,0 +1,544 @@
+// Whitened contraction W = K_* L^-T on the 5th-generation tensor cores (tcgen05, sm_103a),
+// reduced on the fly to var = k(x,x) - |w|^2 (Eq. 1, whitened form).
+//
+// One CTA per (128-point row tile, N-column tile).  A (the kernel rows, M x K, K-major) is
+// generated by all warps from the separable tables directly into shared memory in the
+// canonical 128-byte-swizzled K-major layout, split into TF32 hi/lo or three BF16 slices.
+// B = rows of L^-1 (N x K, K-major, pre-split on the device at model set-up) arrives by TMA
+// (cp.async.bulk.tensor, 128B swizzle).  One thread issues tcgen05.mma into a TMEM
+// accumulator (FP32, 128 lanes x N columns); two pipeline stages overlap the generation of
+// the next A tile with the MMAs of the current one.  The epilogue reads TMEM with
+// tcgen05.ld and sums w^2 per row; a partial per N tile goes to global memory.
+// Split products (Ootomo & Yokota 2022): TF32x3 = hi*hi + hi*lo + lo*hi;
+// BF16x3 = sum over slice pairs (i, j) with i + j <= 2 (six products).
+// Every mbarrier wait is bounded; a wait that runs out records GPR_ERR_TIMEOUT.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <math.h>
+
+#include <mutex>
+
+#include "internal.h"
+
+namespace {
+
+constexpr int TM = 128;          // rows (points) per tile = TMEM lanes
+constexpr int NTHR = 256;        // 8 warps
+constexpr uint32_t kSpinLimit = 1u << 22;
+
+template <int P>
+struct Cfg;
+// P = precision code (GPR_P_TF32 .. GPR_P_BF16X3)
+template <>
+struct Cfg<GPR_P_TF32> {
+    static constexpr int NA = 1, NB = 1, NPROD = 1, BKE = 32, ESZ = 4, N = 256;
+    static constexpr bool BF = false;
+};
+template <>
+struct Cfg<GPR_P_TF32X3> {
+    static constexpr int NA = 2, NB = 2, NPROD = 3, BKE = 32, ESZ = 4, N = 256;
+    static constexpr bool BF = false;
+};
+template <>
+struct Cfg<GPR_P_BF16> {
+    static constexpr int NA = 1, NB = 1, NPROD = 1, BKE = 64, ESZ = 2, N = 256;
+    static constexpr bool BF = true;
+};
+template <>
+struct Cfg<GPR_P_BF16X3> {
+    static constexpr int NA = 3, NB = 3, NPROD = 6, BKE = 64, ESZ = 2, N = 128;
+    static constexpr bool BF = true;
+};
+
+// slice pairs (a, b) of the split products
+__device__ __forceinline__ void prod_pair(int P, int t, int &a, int &b)
+{
+    if (P == GPR_P_TF32X3) {
+        const int pa[3] = {0, 0, 1}, pb[3] = {0, 1, 0};
+        a = pa[t]; b = pb[t];
+    } else if (P == GPR_P_BF16X3) {
+        const int pa[6] = {0, 0, 1, 0, 1, 2}, pb[6] = {0, 1, 0, 2, 1, 0};
+        a = pa[t]; b = pb[t];
+    } else {
+        a = 0; b = 0;
+    }
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// tcgen05 shared-memory descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart.
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t addr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;             // leading-dimension offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;   // stride-dimension offset: 1024 B
+    d |= (uint64_t)1 << 46;             // descriptor version
+    d |= (uint64_t)2 << 61;             // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor: D = F32, A/B = TF32 (kind::tf32) or BF16 (kind::f16), K-major, M x N.
+template <bool BF>
+__host__ __device__ constexpr uint32_t idesc(int M, int N)
+{
+    return (1u << 4) | ((BF ? 1u : 2u) << 7) | ((BF ? 1u : 2u) << 10) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t a, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes) : "memory");
+}
+// Bounded wait on phase `parity`; returns false if the limit ran out.
+__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity)
+{
+    for (uint32_t it = 0; it < kSpinLimit; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.b32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int c0, int c1, uint32_t mbar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            dst),
+        "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(mbar)
+        : "memory");
+}
+
+template <bool BF>
+__device__ __forceinline__ void mma(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc)
+{
+    if (BF)
+        asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+                         tmem_d),
+                     "l"(a), "l"(b), "r"(id), "r"(acc));
+    else
+        asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+                         tmem_d),
+                     "l"(a), "l"(b), "r"(id), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t mbar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
+}
+
+__device__ __forceinline__ float tf32_round(float x)
+{
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+struct TcParams {
+    const float *T32;
+    int64_t off1, off2, mp, m;
+    int kind;
+    float sf2;
+    GridDev g;
+    const int64_t *pts;
+    int64_t pt_base, count;
+    float *partial;  // count x nN partial sums of w^2
+    int nN;
+    int *status;
+};
+
+template <int P>
+__global__ void __launch_bounds__(NTHR, 1) k_tc_sumsq(const __grid_constant__ CUtensorMap mapB0,
+                                                     const __grid_constant__ CUtensorMap mapB1,
+                                                     const __grid_constant__ CUtensorMap mapB2, TcParams prm)
+{
+    using C = Cfg<P>;
+    constexpr int N = C::N, BKE = C::BKE;
+    constexpr int A_TILE = TM * 128;   // bytes per A slice per stage
+    constexpr int B_TILE = N * 128;    // bytes per B slice per stage
+    constexpr int STAGE = C::NA * A_TILE + C::NB * B_TILE;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t *bars = (uint64_t *)(smem + 2 * STAGE);  // full[2], free[2], done
+    __shared__ uint32_t tmem_slot;
+    __shared__ int gx[TM], gy[TM], gz[TM];
+    __shared__ bool rvalid[TM];
+    __shared__ float red[2][TM];
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int64_t row0 = (int64_t)blockIdx.x * TM;
+    const int n0 = blockIdx.y * N;
+    const int64_t m = prm.m;
+    const int64_t kend = (int64_t)n0 + N < m ? (int64_t)n0 + N : m;
+    const int nkb = (int)((kend + BKE - 1) / BKE);
+    const uint32_t bar_full0 = smem_u32(&bars[0]), bar_free0 = smem_u32(&bars[2]), bar_done = smem_u32(&bars[4]);
+
+    if (tid == 0) {
+        mbar_init(bar_full0, 1);
+        mbar_init(bar_full0 + 8, 1);
+        mbar_init(bar_free0, 1);
+        mbar_init(bar_free0 + 8, 1);
+        mbar_init(bar_done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                     "r"((uint32_t)N));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    for (int r = tid; r < TM; r += NTHR) {
+        int64_t row = row0 + r;
+        bool ok = row < prm.count;
+        int64_t p = ok ? (prm.pts ? prm.pts[row] : prm.pt_base + row) : 0;
+        int64_t nx = prm.g.n[0], ny = prm.g.n[1];
+        if (p < 0 || p >= nx * ny * (int64_t)prm.g.n[2]) { ok = false; p = 0; }
+        gx[r] = (int)(p % nx);
+        gy[r] = (int)((p / nx) % ny);
+        gz[r] = (int)(p / (nx * ny));
+        rvalid[r] = ok;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_slot;
+    bool ok_all = true;
+    const CUtensorMap *maps[3] = {&mapB0, &mapB1, &mapB2};
+    constexpr uint32_t ID = idesc<C::BF>(TM, N);
+
+    for (int kb = 0; kb < nkb; ++kb) {
+        const int s = kb & 1, use = kb >> 1;
+        unsigned char *st = smem + s * STAGE;
+        if (kb >= 2) {
+            if (!mbar_wait(bar_free0 + 8 * s, (use - 1) & 1)) ok_all = false;
+        }
+        if (tid == 0) {
+            mbar_expect_tx(bar_full0 + 8 * s, (uint32_t)(C::NB * B_TILE));
+            for (int b = 0; b < C::NB; ++b)
+                tma_load_2d(smem_u32(st + C::NA * A_TILE + b * B_TILE), maps[b], kb * BKE, n0, bar_full0 + 8 * s);
+        }
+        // A tile: 128 rows x 128 bytes per slice; one 16-byte chunk per (row, c)
+        for (int q = tid; q < TM * 8; q += NTHR) {
+            const int r = q >> 3, c = q & 7;
+            const int64_t k0 = (int64_t)kb * BKE + c * (16 / C::ESZ);
+            float v[8];
+            constexpr int EPC = 16 / C::ESZ;  // elements per chunk
+#pragma unroll
+            for (int e = 0; e < EPC; ++e) v[e] = 0.f;
+            if (rvalid[r]) {
+                const float *tx = prm.T32 + (int64_t)gx[r] * prm.mp, *ty = prm.T32 + prm.off1 + (int64_t)gy[r] * prm.mp,
+                            *tz = prm.T32 + prm.off2 + (int64_t)gz[r] * prm.mp;
+#pragma unroll
+                for (int e = 0; e < EPC; ++e) {
+                    int64_t j = k0 + e;
+                    if (j < m) {
+                        float a = tx[j], b = ty[j], cc = tz[j];
+                        if (prm.kind == GPR_K_SE) {
+                            v[e] = a * b * cc;
+                        } else {
+                            float r2 = a + b + cc, rr = sqrtf(r2), s5r = 2.23606797749979f * rr;
+                            v[e] = prm.sf2 * (1.0f + s5r + (5.0f / 3.0f) * r2) * __expf(-s5r);
+                        }
+                    }
+                }
+            }
+            const int off = r * 128 + ((c ^ (r & 7)) << 4);
+            if (!C::BF) {
+                float4 hi, lo;
+                float *h = &hi.x, *l = &lo.x;
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    h[e] = tf32_round(v[e]);
+                    l[e] = tf32_round(v[e] - h[e]);
+                }
+                *(float4 *)(st + off) = hi;
+                if (C::NA > 1) *(float4 *)(st + A_TILE + off) = lo;
+            } else {
+                uint32_t wd[3][4];
+#pragma unroll
+                for (int e = 0; e < 8; e += 2) {
+                    uint32_t bits[3][2];
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        float x = v[e + h];
+                        __nv_bfloat16 b0 = __float2bfloat16_rn(x);
+                        float r1 = x - __bfloat162float(b0);
+                        __nv_bfloat16 b1 = __float2bfloat16_rn(r1);
+                        float r2 = r1 - __bfloat162float(b1);
+                        __nv_bfloat16 b2 = __float2bfloat16_rn(r2);
+                        bits[0][h] = __bfloat16_as_ushort(b0);
+                        bits[1][h] = __bfloat16_as_ushort(b1);
+                        bits[2][h] = __bfloat16_as_ushort(b2);
+                    }
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) wd[a][e / 2] = bits[a][0] | (bits[a][1] << 16);
+                }
+#pragma unroll
+                for (int a = 0; a < C::NA; ++a)
+                    *(uint4 *)(st + a * A_TILE + off) = make_uint4(wd[a][0], wd[a][1], wd[a][2], wd[a][3]);
+            }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            if (!mbar_wait(bar_full0 + 8 * s, use & 1)) ok_all = false;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            for (int t = 0; t < C::NPROD; ++t) {
+                int ia, ib;
+                prod_pair(P, t, ia, ib);
+                const uint32_t abase = smem_u32(st + ia * A_TILE), bbase = smem_u32(st + C::NA * A_TILE + ib * B_TILE);
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk) {
+                    uint32_t acc = (kb > 0 || t > 0 || kk > 0) ? 1u : 0u;
+                    mma<C::BF>(tmem, desc_sw128(abase + kk * 32), desc_sw128(bbase + kk * 32), ID, acc);
+                }
+            }
+            mma_commit(bar_free0 + 8 * s);
+            if (kb == nkb - 1) mma_commit(bar_done);
+        }
+    }
+    // epilogue: warp w reads TMEM lanes 32*(w%4).., column half w/4
+    if (!mbar_wait(bar_done, 0)) ok_all = false;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const int lq = warp & 3, half = warp >> 2;
+    float sum = 0.f;
+#pragma unroll
+    for (int c0 = 0; c0 < N / 2; c0 += 32) {
+        uint32_t rr[32];
+        const uint32_t taddr = tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(half * (N / 2) + c0);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,"
+            "%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+            : "=r"(rr[0]), "=r"(rr[1]), "=r"(rr[2]), "=r"(rr[3]), "=r"(rr[4]), "=r"(rr[5]), "=r"(rr[6]), "=r"(rr[7]),
+              "=r"(rr[8]), "=r"(rr[9]), "=r"(rr[10]), "=r"(rr[11]), "=r"(rr[12]), "=r"(rr[13]), "=r"(rr[14]),
+              "=r"(rr[15]), "=r"(rr[16]), "=r"(rr[17]), "=r"(rr[18]), "=r"(rr[19]), "=r"(rr[20]), "=r"(rr[21]),
+              "=r"(rr[22]), "=r"(rr[23]), "=r"(rr[24]), "=r"(rr[25]), "=r"(rr[26]), "=r"(rr[27]), "=r"(rr[28]),
+              "=r"(rr[29]), "=r"(rr[30]), "=r"(rr[31])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+            float w = __uint_as_float(rr[i]);
+            sum = fmaf(w, w, sum);
+        }
+    }
+    red[half][lq * 32 + lane] = sum;
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (tid < TM) {
+        int64_t row = row0 + tid;
+        if (row < prm.count) prm.partial[row * prm.nN + blockIdx.y] = red[0][tid] + red[1][tid];
+    }
+    if (!ok_all) atomicCAS(prm.status, 0, (int)GPR_ERR_TIMEOUT);
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)N));
+    }
+}
+
+__global__ void k_tc_finalize(const float *partial, int nN, int64_t count, double sf2, float *var)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    float s = 0.f;
+    for (int t = 0; t < nN; ++t) s += partial[i * nN + t];
+    var[i] = (float)(sf2 - (double)s);
+}
+
+// B slices of L^-1 (rows j, columns i <= j), K-major: TF32 hi/lo (FP32 storage) or BF16 x3.
+__global__ void k_split_b(const double *Linv, int64_t mb, int64_t m, int64_t mpt, float *thi, float *tlo,
+                          __nv_bfloat16 *b0, __nv_bfloat16 *b1, __nv_bfloat16 *b2)
+{
+    int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= mpt * mpt) return;
+    int64_t j = idx / mpt, i = idx % mpt;
+    double v = (j < m && i <= j) ? Linv[j * mb + i] : 0.0;
+    float f = (float)v;
+    float h = tf32_round(f);
+    thi[idx] = h;
+    tlo[idx] = tf32_round((float)(v - (double)h));
+    __nv_bfloat16 x0 = __double2bfloat16(v);
+    double r1 = v - (double)__bfloat162float(x0);
+    __nv_bfloat16 x1 = __double2bfloat16(r1);
+    double r2 = r1 - (double)__bfloat162float(x1);
+    b0[idx] = x0;
+    b1[idx] = x1;
+    b2[idx] = __double2bfloat16(r2);
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encode()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        cudaDriverEntryPointQueryResult q;
+        void *p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    });
+    return fn;
+}
+
+bool make_map(CUtensorMap *map, void *base, int64_t mpt, bool bf, int N)
+{
+    auto enc = get_encode();
+    if (!enc) return false;
+    cuuint64_t gdim[2] = {(cuuint64_t)mpt, (cuuint64_t)mpt};
+    cuuint64_t gstride[1] = {(cuuint64_t)mpt * (bf ? 2 : 4)};
+    cuuint32_t box[2] = {(cuuint32_t)(bf ? 64 : 32), (cuuint32_t)N};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(map, bf ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, gdim, gstride,
+                     box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+template <int P>
+size_t smem_bytes()
+{
+    using C = Cfg<P>;
+    size_t stage = (size_t)C::NA * TM * 128 + (size_t)C::NB * C::N * 128;
+    return 2 * stage + 64 + 1024;
+}
+
+template <int P>
+gpr_status launch_tc(const gpr_model *M, const TcParams &prm, cudaStream_t st)
+{
+    using C = Cfg<P>;
+    CUtensorMap maps[3];
+    const TcOperands &B = *M->tc;
+    if (C::BF) {
+        void *bases[3] = {B.b0, B.b1, B.b2};
+        for (int i = 0; i < 3; ++i)
+            if (!make_map(&maps[i], bases[i], B.mpt, true, C::N)) return GPR_ERR_UNSUPPORTED;
+    } else {
+        void *bases[3] = {B.thi, B.tlo, B.thi};
+        for (int i = 0; i < 3; ++i)
+            if (!make_map(&maps[i], bases[i], B.mpt, false, C::N)) return GPR_ERR_UNSUPPORTED;
+    }
+    size_t smem = smem_bytes<P>();
+    GPR_CUDA_TRY(cudaFuncSetAttribute(k_tc_sumsq<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    dim3 grid((unsigned)((prm.count + TM - 1) / TM), (unsigned)prm.nN);
+    {
+        ProfScope ps("tc_sumsq", st);
+        k_tc_sumsq<P><<<grid, NTHR, smem, st>>>(maps[0], maps[1], maps[2], prm);
+    }
+    note_launch();
+    GPR_CUDA_TRY(cudaGetLastError());
+    return GPR_OK;
+}
+
+}  // namespace
+
+int tc_ntile(gpr_precision p) { return p == GPR_P_BF16X3 ? 128 : 256; }
+
+bool tc_precision(gpr_precision p)
+{
+    return p == GPR_P_TF32 || p == GPR_P_TF32X3 || p == GPR_P_BF16 || p == GPR_P_BF16X3;
+}
+
+gpr_status fast_meanvar(gpr_model *M, const GridDev &g, gpr_precision prec, const float *T32, const float2 *Tff,
+                        const double *T64, const int64_t *pts, int64_t pt_base, int64_t count, float *mean, float *var,
+                        float *partial, cudaStream_t st)
+{
+    if (count <= 0) return GPR_OK;
+    if (tc_precision(prec)) {
+        GPR_TRY(tc_prepare(M, st));
+        GPR_TRY(launch_tc_var(M, g, prec, T32, pts, pt_base, count, partial, var, st));
+    } else {
+        launch_meanvar32(M, g, T32, pts, pt_base, count, mean, var, st);
+    }
+    launch_mean_compensated(M, g, Tff, T64, pts, pt_base, count, mean, st);
+    GPR_CUDA_TRY(cudaGetLastError());
+    return GPR_OK;
+}
+
+gpr_status tc_prepare(gpr_model *M, cudaStream_t st)
+{
+    if (M->tc) return GPR_OK;
+    int64_t mb = (M->m + 31) / 32 * 32;
+    TcOperands *B = new TcOperands();
+    B->mpt = (M->mp + 255) / 256 * 256;
+    int64_t mpt = B->mpt;
+    size_t n = (size_t)mpt * mpt;
+    cudaError_t e = cudaSuccess;
+    e = cudaMalloc(&B->thi, n * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&B->tlo, n * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&B->b0, n * 2);
+    if (e == cudaSuccess) e = cudaMalloc(&B->b1, n * 2);
+    if (e == cudaSuccess) e = cudaMalloc(&B->b2, n * 2);
+    if (e != cudaSuccess) {
+        cudaFree(B->thi); cudaFree(B->tlo); cudaFree(B->b0); cudaFree(B->b1); cudaFree(B->b2);
+        delete B;
+        return e == cudaErrorMemoryAllocation ? GPR_ERR_OOM : GPR_ERR_CUDA;
+    }
+    k_split_b<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(M->Linv, mb, M->m, mpt, B->thi, B->tlo,
+                                                          (__nv_bfloat16 *)B->b0, (__nv_bfloat16 *)B->b1,
+                                                          (__nv_bfloat16 *)B->b2);
+    note_launch();
+    GPR_CUDA_TRY(cudaGetLastError());
+    M->tc = B;
+    return GPR_OK;
+}
+
+void tc_release(gpr_model *M)
+{
+    if (!M->tc) return;
+    cudaFree(M->tc->thi); cudaFree(M->tc->tlo); cudaFree(M->tc->b0); cudaFree(M->tc->b1); cudaFree(M->tc->b2);
+    delete M->tc;
+    M->tc = nullptr;
+}
+
+size_t tc_partial_elems(gpr_precision p, const gpr_model *M, int64_t count)
+{
+    int64_t mpt = (M->mp + 255) / 256 * 256;
+    return (size_t)count * (size_t)((mpt + tc_ntile(p) - 1) / tc_ntile(p));
+}
+
+// var of the listed points by the tensor-core contraction; `partial` holds tc_partial_elems floats.
+gpr_status launch_tc_var(const gpr_model *M, const GridDev &g, gpr_precision prec, const float *T32,
+                         const int64_t *pts, int64_t pt_base, int64_t count, float *partial, float *var, cudaStream_t st)
+{
+    if (count <= 0) return GPR_OK;
+    if (!M->tc) return GPR_ERR_ARG;
+    TcParams prm;
+    prm.T32 = T32;
+    prm.off1 = (int64_t)g.n[0] * M->mp;
+    prm.off2 = prm.off1 + (int64_t)g.n[1] * M->mp;
+    prm.mp = M->mp;
+    prm.m = M->m;
+    prm.kind = M->kp.kind;
+    prm.sf2 = (float)M->kp.sf2;
+    prm.g = g;
+    prm.pts = pts;
+    prm.pt_base = pt_base;
+    prm.count = count;
+    prm.partial = partial;
+    prm.nN = (int)((M->tc->mpt + tc_ntile(prec) - 1) / tc_ntile(prec));
+    prm.status = gpr_status_word();
+    if (!prm.status) return GPR_ERR_CUDA;
+    gpr_status s;
+    switch (prec) {
+    case GPR_P_TF32: s = launch_tc<GPR_P_TF32>(M, prm, st); break;
+    case GPR_P_TF32X3: s = launch_tc<GPR_P_TF32X3>(M, prm, st); break;
+    case GPR_P_BF16: s = launch_tc<GPR_P_BF16>(M, prm, st); break;
+    case GPR_P_BF16X3: s = launch_tc<GPR_P_BF16X3>(M, prm, st); break;
+    default: return GPR_ERR_ARG;
+    }
+    if (s != GPR_OK) return s;
+    k_tc_finalize<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(partial, prm.nN, count, M->kp.sf2, var);
+    note_launch();
+    GPR_CUDA_TRY(cudaGetLastError());
+    return GPR_OK;
+}

@@ -1,0 +1,101 @@
+"""Tensor-core (tcgen05) whitened contraction: TF32, TF32x3, BF16, BF16x3 against the oracle.
+
+Split precisions (TF32x3, BF16x3) are asserted to the FP32-class tolerance (|dvar| <= 1e-4 sf2,
+|dmean| <= 1e-4 max|y|; the mean is the compensated k.alpha in every precision).  Single-pass
+TF32 and BF16 are reported (their variance error is large on ill-conditioned models) and only
+checked for finiteness and the mean.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from gpu_util import model_of, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    return torch_cuda()
+
+
+@pytest.fixture(scope="module")
+def g():
+    import paper_2512_12442_gb300 as g
+    return g
+
+
+def _recon(g, torch, M, n, prec, lo=(0, 0, 0), hi=(1, 1, 1)):
+    grid = g.make_grid(n, lo, hi)
+    npts = int(np.prod(n)) if not np.isscalar(n) else n ** 3
+    mean = torch.zeros(npts, dtype=torch.float32, device="cuda")
+    var = torch.zeros_like(mean)
+    g.gpr_reconstruct_dense(M, grid, prec, mean, var, None)
+    g.gpr_sync()
+    return mean.cpu().numpy().astype(np.float64), var.cpu().numpy().astype(np.float64)
+
+
+@pytest.mark.parametrize("case", ["ragged_m97", "config1"])
+def test_tc_split_precisions_small(torch, g, case):
+    if case == "config1":
+        w = workloads.config1(); n = (32, 32, 32)
+    else:
+        w = workloads.small(97, 97, 9, ell=(0.15, 0.2, 0.25)); n = (11, 13, 9)  # 1287 points: ragged tiles
+    M = model_of(w)
+    ref = oracle.Model.from_workload(w).stats15(n)
+    ys = np.abs(w.y).max()
+    m32, v32 = _recon(g, torch, M, n, g.GPR_P_FP32)
+    for prec in (g.GPR_P_TF32X3, g.GPR_P_BF16X3):
+        m, v = _recon(g, torch, M, n, prec)
+        assert np.abs(m - ref[:, 0]).max() <= 1e-4 * ys
+        assert np.abs(v - ref[:, 1]).max() <= 1e-4 * w.sf2, (prec, np.abs(v - ref[:, 1]).max())
+        assert np.abs(v - v32).max() <= 1e-4
+    for prec in (g.GPR_P_TF32, g.GPR_P_BF16):
+        m, v = _recon(g, torch, M, n, prec)
+        assert np.all(np.isfinite(v))
+        assert np.abs(m - ref[:, 0]).max() <= 1e-4 * ys
+
+
+def test_tc_config2_full_grid_sampled(torch, g):
+    """The m=500 field on the full 128^3 grid in TF32x3 and BF16x3, sampled against the oracle."""
+    w = workloads.config2()
+    M = model_of(w)
+    n = w.n
+    rng = np.random.default_rng(3)
+    idx = np.concatenate([rng.integers(0, n ** 3, 2500), [0, n ** 3 - 1]])
+    P = np.stack([idx % n, (idx // n) % n, idx // (n * n)], 1) / (n - 1)
+    mu, vr = oracle.Model.from_workload(w).posterior(P)
+    ys = np.abs(w.y).max()
+    errs = {}
+    for prec in (g.GPR_P_TF32X3, g.GPR_P_BF16X3, g.GPR_P_TF32, g.GPR_P_BF16):
+        m, v = _recon(g, torch, M, n, prec)
+        errs[prec] = (np.abs(m[idx] - mu).max() / ys, np.abs(v[idx] - vr).max())
+    for prec in (g.GPR_P_TF32X3, g.GPR_P_BF16X3):
+        assert errs[prec][0] <= 1e-4 and errs[prec][1] <= 1e-4, errs
+    print("tensor-core errors (max |dmean|/max|y|, max |dvar|):", errs)
+
+
+def test_tc_prepass_lcp_equals_fp64(torch, g):
+    """The LCP cascade with a tensor-core pre-pass gives the all-FP64 field."""
+    w = workloads.config1()
+    M = model_of(w)
+    th = w.isovalues[0]
+    out = {}
+    for prec in (g.GPR_P_FP64, g.GPR_P_TF32X3, g.GPR_P_BF16X3):
+        f = torch.zeros((w.n - 1) ** 3, dtype=torch.float32, device="cuda")
+        g.gpr_lcp_dense(M, g.make_grid(w.n), th, g.lcp_options(prec=prec), f)
+        g.gpr_sync()
+        out[prec] = f.cpu().numpy()
+    assert np.array_equal(out[g.GPR_P_FP64], out[g.GPR_P_TF32X3])
+    assert np.array_equal(out[g.GPR_P_FP64], out[g.GPR_P_BF16X3])
+
+
+def test_tc_cov13_not_served(torch, g):
+    w = workloads.small(3, 20, 5)
+    M = model_of(w)
+    t = torch.zeros(125, dtype=torch.float32, device="cuda")
+    c = torch.zeros(125, 13, dtype=torch.float32, device="cuda")
+    with pytest.raises(g.GPRError) as e:
+        g.gpr_reconstruct_dense(M, g.make_grid(5), g.GPR_P_TF32X3, t, t.clone(), c)
+    assert e.value.status == g.GPR_ERR_UNSUPPORTED
