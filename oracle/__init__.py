@@ -68,6 +68,12 @@ def lib():
                                       C.c_double, C.c_int, _i64p, C.c_int64, _i8p, _dp, _i8p]
         L.or_eval_g.argtypes = [C.c_void_p, _dp, C.c_int64, C.c_double, C.c_int, _dp, _dp]
         L.or_num_threads.restype = C.c_int
+        L.or_cell_lcp_adj.restype = C.c_double
+        L.or_cell_lcp_adj.argtypes = [C.c_int, _dp, _dp, C.c_double, C.c_int64, C.c_uint64, C.c_uint64, C.c_double,
+                                      C.c_double, C.c_double, _dp, _dp]
+        L.or_lcp_grad_block.restype = C.c_double
+        L.or_lcp_grad_block.argtypes = [C.c_void_p, C.POINTER(_Grid), C.c_double, C.c_int64, C.c_uint64, C.c_double,
+                                        C.c_double, _dp, _i64p, _i64p, _dp, _dp]
         _lib = L
     return _lib
 
@@ -237,11 +243,34 @@ class Model:
             field[lin] = dense[lin]
         return field, leaves, levels
 
+    def lcp_grad(self, n, theta, weights, c0=(0, 0, 0), c1=None, n_samples=1600, seed=0, tau=1e-4, skip_eps=1e-9):
+        """Gradient of sum_c weights[c] LCP_c over cells [c0, c1) wrt y and log length scales.
+        Returns (loss, dL/dy, dL/dlog l)."""
+        g = grid(n)
+        if c1 is None:
+            c1 = tuple(int(v) - 1 for v in g.n)
+        c0 = np.asarray(c0, np.int64); c1 = np.asarray(c1, np.int64)
+        dy = np.zeros(self.m); dl = np.zeros(3)
+        loss = lib().or_lcp_grad_block(self._h, C.byref(g), float(theta), int(n_samples), C.c_uint64(seed), float(tau),
+                                       float(skip_eps), np.ascontiguousarray(weights, np.float64), c0, c1, dy, dl)
+        return loss, dy, dl
+
     def eval_g(self, x, theta, side):
         x = np.ascontiguousarray(x, np.float64).reshape(-1, 3)
         g = np.zeros(x.shape[0]); gr = np.zeros((x.shape[0], 3))
         lib().or_eval_g(self._h, x, x.shape[0], float(theta), int(side), g, gr.reshape(-1))
         return g, gr
+
+
+def cell_lcp_adj(mu, S, theta, wbar=1.0, n_samples=1600, seed=0, cell=0, tau=1e-4, skip_eps=1e-9):
+    """Adjoint of the SOV cell rule: (LCP, dLCP/dmu * wbar, dLCP/dSigma * wbar)."""
+    mu = np.ascontiguousarray(mu, np.float64)
+    S = np.ascontiguousarray(S, np.float64)
+    d = mu.shape[0]
+    mb = np.zeros(d); Sb = np.zeros(d * d)
+    v = lib().or_cell_lcp_adj(d, mu, S.reshape(-1), float(theta), int(n_samples), C.c_uint64(seed), C.c_uint64(cell),
+                              float(tau), float(skip_eps), float(wbar), mb, Sb)
+    return v, mb, Sb.reshape(d, d)
 
 
 def cell_lcp(mu, S, theta, est=EST_SOV, n_samples=1600, seed=0, cell=0, tau=1e-4, skip_eps=1e-9):

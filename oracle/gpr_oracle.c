@@ -773,3 +773,261 @@ int or_num_threads(void)
     return 1;
 #endif
 }
+
+/* ----------------------------------------------------------------- adjoint
+ * Gradient of loss = sum_c w_c LCP_c (SOV estimator) with respect to y and the
+ * log length scales.  Parity unpinned against the paper (it has no gradient):
+ * pinned by central finite differences of this oracle's own forward.
+ *
+ * Reverse sweep of the sequential-conditioning rule, per sample:
+ *   u_i = (b_i - sum_{j<i} L_ij z_j) / L_ii, e_i = Phi(u_i), f = prod e_i,
+ *   z_i = Phi^-1(w_i e_i)  =>  dz_i/de_i = w_i / phi(z_i). */
+static double npdf(double x) { return exp(-0.5 * x * x) / sqrt(2.0 * M_PI); }
+
+static void sov_orthant_adj(int d, const double *L, const double *b, int64_t N, const uint32_t *shift, double Pbar,
+                            double *bbar, double *Lbar)
+{
+    uint32_t G[16];
+    for (int i = 0; i < d - 1; ++i) G[i] = lattice_gen(i);
+    double z[16], u[16], e[16], w[16], zbar[16];
+    for (int64_t k = 0; k < N; ++k) {
+        double f = 1.0;
+        int ok = 1;
+        for (int i = 0; i < d; ++i) {
+            double s = 0.0;
+            for (int j = 0; j < i; ++j) s += L[i * d + j] * z[j];
+            u[i] = (b[i] - s) / L[i * d + i];
+            e[i] = or_norm_cdf(u[i]);
+            f *= e[i];
+            if (!(f > 0.0)) { ok = 0; break; }
+            if (i < d - 1) {
+                uint32_t U = (uint32_t)((uint64_t)k * G[i]) + shift[i];
+                w[i] = fabs(2.0 * u01(U) - 1.0);
+                z[i] = or_norm_ppf(w[i] * e[i]);
+            }
+        }
+        if (!ok) continue;
+        double fbar = Pbar / (double)N;
+        for (int i = 0; i < d; ++i) zbar[i] = 0.0;
+        for (int i = d - 1; i >= 0; --i) {
+            double ebar = fbar * (f / e[i]);
+            if (i < d - 1) ebar += zbar[i] * w[i] / npdf(z[i]);
+            double ubar = ebar * npdf(u[i]);
+            double lii = L[i * d + i];
+            bbar[i] += ubar / lii;
+            double sbar = -ubar / lii;
+            Lbar[i * d + i] += -ubar * u[i] / lii;
+            for (int j = 0; j < i; ++j) {
+                Lbar[i * d + j] += sbar * z[j];
+                zbar[j] += sbar * L[i * d + j];
+            }
+        }
+    }
+}
+
+/* Sbar = L^-T sym(Phi(L^T Lbar)) L^-1, Phi = lower triangle with the diagonal halved:
+ * the adjoint of Sigma = L L^T for a symmetric perturbation, dloss = sum_ij Sbar_ij dSigma_ij. */
+static void chol_adj(int d, const double *L, const double *Lbar, double *Sbar)
+{
+    double Pm[256], T[256], Li[256];
+    for (int i = 0; i < d; ++i)
+        for (int j = 0; j < d; ++j) {
+            double s = 0.0;
+            for (int k = 0; k < d; ++k) s += L[k * d + i] * Lbar[k * d + j]; /* (L^T Lbar)_ij */
+            Pm[i * d + j] = s;
+        }
+    for (int i = 0; i < d; ++i)
+        for (int j = 0; j < d; ++j) {
+            double v = j < i ? Pm[i * d + j] : (j == i ? 0.5 * Pm[i * d + i] : 0.0);
+            T[i * d + j] = v;
+        }
+    for (int i = 0; i < d; ++i)
+        for (int j = 0; j < d; ++j) Pm[i * d + j] = 0.5 * (T[i * d + j] + T[j * d + i]);
+    /* Li = L^-1 (lower) */
+    for (int i = 0; i < d * d; ++i) Li[i] = 0.0;
+    for (int c = 0; c < d; ++c) {
+        for (int i = 0; i < d; ++i) {
+            double s = (i == c) ? 1.0 : 0.0;
+            for (int k = 0; k < i; ++k) s -= L[i * d + k] * Li[k * d + c];
+            Li[i * d + c] = s / L[i * d + i];
+        }
+    }
+    /* Sbar = Li^T Pm Li */
+    for (int i = 0; i < d; ++i)
+        for (int j = 0; j < d; ++j) {
+            double s = 0.0;
+            for (int k = 0; k < d; ++k) s += Pm[i * d + k] * Li[k * d + j];
+            T[i * d + j] = s;
+        }
+    for (int i = 0; i < d; ++i)
+        for (int j = 0; j < d; ++j) {
+            double s = 0.0;
+            for (int k = 0; k < d; ++k) s += Li[k * d + i] * T[k * d + j];
+            Sbar[i * d + j] = s;
+        }
+}
+
+/* Adjoint of the SOV cell rule: given wbar = dloss/dLCP, fills mubar[d] and the
+ * symmetric Sbar[d*d] with dloss = sum mubar_i dmu_i + sum_ij Sbar_ij dSigma_ij.
+ * Returns the LCP.  Cells that the rule makes constant (Boole pre-skip, deterministic,
+ * clamped) have zero gradient. */
+double or_cell_lcp_adj(int d, const double *mu, const double *S, double theta, int64_t N, uint64_t seed, uint64_t cell,
+                       double tau, double skip_eps, double wbar, double *mubar, double *Sbar)
+{
+    for (int i = 0; i < d; ++i) mubar[i] = 0.0;
+    for (int i = 0; i < d * d; ++i) Sbar[i] = 0.0;
+    double Sj[256], L[256], Lbar[256], b[16], bbar_lo[16], bbar_hi[16];
+    double maxdiag = 0.0;
+    int amax = 0;
+    for (int i = 0; i < d; ++i) if (S[i * d + i] > maxdiag) { maxdiag = S[i * d + i]; amax = i; }
+    if (!(maxdiag > 1e-30)) return or_cell_lcp(d, mu, S, theta, EST_SOV, N, seed, cell, tau, skip_eps);
+    double jit = tau * maxdiag;
+    for (int i = 0; i < d * d; ++i) Sj[i] = S[i];
+    for (int i = 0; i < d; ++i) Sj[i * d + i] += jit;
+    double s_above = 0.0, s_below = 0.0;
+    for (int i = 0; i < d; ++i) {
+        double sd = sqrt(Sj[i * d + i]);
+        s_above += or_norm_cdf((mu[i] - theta) / sd);
+        s_below += or_norm_cdf((theta - mu[i]) / sd);
+    }
+    if (s_above < skip_eps || s_below < skip_eps) return 0.0;
+    chol_floor(Sj, d, 1e-3 * jit, L);
+    uint32_t sh[16];
+    for (int i = 0; i < d - 1; ++i) sh[i] = (uint32_t)(or_splitmix64(seed, (uint64_t)cell * 8 + i + 1) >> 32);
+    for (int i = 0; i < d; ++i) b[i] = theta - mu[i];
+    double p_lo = or_sov_orthant(d, L, b, N, sh);
+    for (int i = 0; i < d; ++i) b[i] = mu[i] - theta;
+    double p_hi = or_sov_orthant(d, L, b, N, sh);
+    double v = 1.0 - p_lo - p_hi;
+    if (v < 0.0 || v > 1.0) return v < 0.0 ? 0.0 : 1.0;
+    for (int i = 0; i < d * d; ++i) Lbar[i] = 0.0;
+    for (int i = 0; i < d; ++i) { bbar_lo[i] = 0.0; bbar_hi[i] = 0.0; }
+    for (int i = 0; i < d; ++i) b[i] = theta - mu[i];
+    sov_orthant_adj(d, L, b, N, sh, -wbar, bbar_lo, Lbar);
+    for (int i = 0; i < d; ++i) b[i] = mu[i] - theta;
+    sov_orthant_adj(d, L, b, N, sh, -wbar, bbar_hi, Lbar);
+    for (int i = 0; i < d; ++i) mubar[i] = -bbar_lo[i] + bbar_hi[i];
+    chol_adj(d, L, Lbar, Sbar);
+    double tr = 0.0;
+    for (int i = 0; i < d; ++i) tr += Sbar[i * d + i];
+    Sbar[amax * d + amax] += tau * tr;
+    return v;
+}
+
+/* d k(a, b) / d log l_d for the kernel (a, b fixed). */
+static double kernel_dlogl(int kernel, const double *ell, double sf2, const double *a, const double *b, int dd)
+{
+    double r2 = 0.0;
+    for (int d = 0; d < 3; ++d) {
+        double t = (a[d] - b[d]) / ell[d];
+        r2 += t * t;
+    }
+    double t = (a[dd] - b[dd]) / ell[dd], t2 = t * t;
+    if (kernel == OR_SE) return sf2 * exp(-0.5 * r2) * t2;
+    double r = sqrt(r2), s5r = sqrt(5.0) * r;
+    return (5.0 / 3.0) * sf2 * (1.0 + s5r) * exp(-s5r) * t2;
+}
+
+/* Gradient of loss = sum_c w[c] LCP_c over the cells with min corner in [c0, c1) (weights
+ * indexed by the linear cell index of the whole grid).  dy[m], dlogl[3]; returns the loss.
+ * Chain rule through Eq. (1) for plain GPR, per cell: with P_i = Kt^-1 k_i, alpha = Kt^-1 y,
+ * Kd = dK(X,X)/dlog l_d, kd_i = dk(x_i, X)/dlog l_d:
+ *   dmu_i/dy = P_i,   dmu_i/dlog l_d = kd_i . alpha - P_i^T Kd alpha,
+ *   dSigma_ij/dlog l_d = dk(x_i,x_j) - kd_i . P_j - P_i . kd_j + P_i^T Kd P_j. */
+double or_lcp_grad_block(const or_model *M, const or_grid *g, double theta, int64_t N, uint64_t seed, double tau,
+                         double skip_eps, const double *weights, const int64_t *c0, const int64_t *c1, double *dy,
+                         double *dlogl)
+{
+    int64_t m = M->m;
+    int64_t pn[3];
+    for (int d = 0; d < 3; ++d) pn[d] = c1[d] - c0[d] + 1;
+    int64_t np = pn[0] * pn[1] * pn[2];
+    double *V = (double *)malloc(sizeof(double) * np * m);
+    double *Pr = (double *)malloc(sizeof(double) * np * m);
+    double *Kd = (double *)malloc(sizeof(double) * np * m * 3);   /* kd rows */
+    double *KdP = (double *)malloc(sizeof(double) * np * m * 3);  /* Kd_d P_p */
+    double *Kda = (double *)malloc(sizeof(double) * m * 3);       /* Kd_d alpha */
+    double *Kdm = (double *)malloc(sizeof(double) * m * m * 3);   /* Kd_d matrices */
+    for (int d = 0; d < 3; ++d)
+        for (int64_t i = 0; i < m; ++i)
+            for (int64_t j = 0; j < m; ++j)
+                Kdm[(d * m + i) * m + j] = kernel_dlogl(M->kernel, M->ell, M->sf2, M->X + 3 * i, M->X + 3 * j, d);
+    for (int d = 0; d < 3; ++d)
+        for (int64_t i = 0; i < m; ++i) Kda[d * m + i] = dot(Kdm + (d * m + i) * m, M->alpha, m);
+#pragma omp parallel
+    {
+        double *kb = (double *)malloc(sizeof(double) * m);
+#pragma omp for schedule(static)
+        for (int64_t q = 0; q < np; ++q) {
+            int64_t a = c0[0] + q % pn[0], b = c0[1] + (q / pn[0]) % pn[1], c = c0[2] + q / (pn[0] * pn[1]);
+            double x[3] = {grid_x(g, 0, a), grid_x(g, 1, b), grid_x(g, 2, c)};
+            whiten_row(M, x, kb, V + q * m);
+            back_sub_T(M->L, m, V + q * m, Pr + q * m);
+            for (int d = 0; d < 3; ++d) {
+                for (int64_t j = 0; j < m; ++j)
+                    Kd[(q * 3 + d) * m + j] = kernel_dlogl(M->kernel, M->ell, M->sf2, x, M->X + 3 * j, d);
+                for (int64_t i = 0; i < m; ++i)
+                    KdP[(q * 3 + d) * m + i] = dot(Kdm + (d * m + i) * m, Pr + q * m, m);
+            }
+        }
+        free(kb);
+    }
+    int64_t cn[3] = {c1[0] - c0[0], c1[1] - c0[1], c1[2] - c0[2]};
+    int64_t nc = cn[0] * cn[1] * cn[2];
+    int64_t gc[3] = {g->n[0] - 1, g->n[1] - 1, g->n[2] - 1};
+    double loss = 0.0, gl[3] = {0, 0, 0};
+    for (int64_t i = 0; i < m; ++i) dy[i] = 0.0;
+#pragma omp parallel
+    {
+        double *dyl = (double *)calloc((size_t)m, sizeof(double));
+        double gll[3] = {0, 0, 0}, lossl = 0.0;
+#pragma omp for schedule(dynamic, 16)
+        for (int64_t p = 0; p < nc; ++p) {
+            int64_t a = c0[0] + p % cn[0], b = c0[1] + (p / cn[0]) % cn[1], c = c0[2] + p / (cn[0] * cn[1]);
+            uint64_t cell = (uint64_t)(a + gc[0] * (b + gc[1] * c));
+            double wc = weights[cell];
+            int64_t q[8];
+            double x[8][3], mu[8], S[64], mubar[8], Sbar[64];
+            for (int cc = 0; cc < 8; ++cc) {
+                int bx = cc & 1, by = (cc >> 1) & 1, bz = (cc >> 2) & 1;
+                q[cc] = (a + bx - c0[0]) + pn[0] * ((b + by - c0[1]) + pn[1] * (c + bz - c0[2]));
+                x[cc][0] = grid_x(g, 0, a + bx); x[cc][1] = grid_x(g, 1, b + by); x[cc][2] = grid_x(g, 2, c + bz);
+                mu[cc] = dot(V + q[cc] * m, M->vy, m);
+            }
+            for (int i = 0; i < 8; ++i)
+                for (int j = 0; j <= i; ++j) {
+                    double s = or_kernel_eval(M->kernel, M->ell, M->sf2, x[i], x[j]) - dot(V + q[i] * m, V + q[j] * m, m);
+                    S[i * 8 + j] = s; S[j * 8 + i] = s;
+                }
+            lossl += wc * or_cell_lcp_adj(8, mu, S, theta, N, seed, cell, tau, skip_eps, wc, mubar, Sbar);
+            for (int i = 0; i < 8; ++i) {
+                if (mubar[i] != 0.0)
+                    for (int64_t j = 0; j < m; ++j) dyl[j] += mubar[i] * Pr[q[i] * m + j];
+                for (int d = 0; d < 3; ++d)
+                    gll[d] += mubar[i] * (dot(Kd + (q[i] * 3 + d) * m, M->alpha, m) - dot(Pr + q[i] * m, Kda + d * m, m));
+            }
+            for (int i = 0; i < 8; ++i)
+                for (int j = 0; j < 8; ++j) {
+                    double sb = Sbar[i * 8 + j];
+                    if (sb == 0.0) continue;
+                    for (int d = 0; d < 3; ++d) {
+                        double dS = kernel_dlogl(M->kernel, M->ell, M->sf2, x[i], x[j], d) -
+                                    dot(Kd + (q[i] * 3 + d) * m, Pr + q[j] * m, m) -
+                                    dot(Pr + q[i] * m, Kd + (q[j] * 3 + d) * m, m) +
+                                    dot(Pr + q[i] * m, KdP + (q[j] * 3 + d) * m, m);
+                        gll[d] += sb * dS;
+                    }
+                }
+        }
+#pragma omp critical
+        {
+            for (int64_t j = 0; j < m; ++j) dy[j] += dyl[j];
+            for (int d = 0; d < 3; ++d) gl[d] += gll[d];
+            loss += lossl;
+        }
+        free(dyl);
+    }
+    for (int d = 0; d < 3; ++d) dlogl[d] = gl[d];
+    free(V); free(Pr); free(Kd); free(KdP); free(Kda); free(Kdm);
+    return loss;
+}

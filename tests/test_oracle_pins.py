@@ -358,3 +358,50 @@ def test_octree_alpha_zero_keeps_nonzero_cells_and_adaptive_equals_dense():
     assert np.all(field3[mask] == 0)
     # RMSE against dense is small, as the paper reports (Sec. 6.2): a sanity range, not a pin
     assert math.sqrt(np.mean((field3 - dense) ** 2)) < 5e-3
+
+
+# ------------------------------------------------------------ adjoint (no paper counterpart)
+
+def test_cell_adjoint_matches_finite_differences():
+    """Reverse sweep through the sequential-conditioning rule and the 8x8 Cholesky: dLCP/dmu and
+    dLCP/dSigma against central differences of the same estimator (fixed lattice: smooth)."""
+    rng = np.random.default_rng(3)
+    A = rng.normal(size=(8, 8)); S = A @ A.T / 8 + 0.05 * np.ones((8, 8)) + 0.02 * np.eye(8)
+    mu = rng.normal(0, 0.2, 8)
+    v, mb, Sb = oracle.cell_lcp_adj(mu, S, 0.05)
+    assert v == pytest.approx(oracle.cell_lcp(mu, S, 0.05), abs=1e-15)
+    h = 1e-5
+    for i in range(8):
+        e = np.zeros(8); e[i] = h
+        fd = (oracle.cell_lcp(mu + e, S, 0.05) - oracle.cell_lcp(mu - e, S, 0.05)) / (2 * h)
+        assert mb[i] == pytest.approx(fd, rel=1e-6, abs=1e-10)
+    for (i, j) in ((0, 0), (2, 5), (7, 7), (1, 6), (3, 4)):
+        E = np.zeros((8, 8)); E[i, j] += h
+        if i != j:
+            E[j, i] += h
+        fd = (oracle.cell_lcp(mu, S + E, 0.05) - oracle.cell_lcp(mu, S - E, 0.05)) / (2 * h)
+        an = Sb[i, j] + (Sb[j, i] if i != j else 0.0)
+        assert an == pytest.approx(fd, rel=1e-5, abs=1e-9)
+
+
+def test_field_gradient_matches_finite_differences():
+    """loss = sum_c w_c LCP_c on a small field: dloss/dy_i and dloss/dlog l_d (analytic, chain rule
+    through Eq. 1) against central differences with h = 1e-3."""
+    w = workloads.small(5, 30, 9, ell=(0.2, 0.25, 0.3))
+    M = oracle.Model.from_workload(w)
+    th = w.isovalues[0]
+    wts = np.random.default_rng(5).random(512)
+    loss, dy, dl = M.lcp_grad(9, th, wts)
+    assert loss == pytest.approx(float(np.dot(wts, M.lcp_dense(9, th))), rel=1e-12)
+    h = 1e-3
+    for i in (0, 7, 21):
+        y2 = w.y.copy(); y2[i] += h
+        lp = oracle.Model(w.X, y2, w.kernel, w.ell, w.sf2, w.sn2).lcp_grad(9, th, wts)[0]
+        y2[i] -= 2 * h
+        lm = oracle.Model(w.X, y2, w.kernel, w.ell, w.sf2, w.sn2).lcp_grad(9, th, wts)[0]
+        assert dy[i] == pytest.approx((lp - lm) / (2 * h), rel=2e-4, abs=1e-6)
+    for d in range(3):
+        e = np.zeros(3); e[d] = h
+        lp = oracle.Model(w.X, w.y, w.kernel, tuple(np.array(w.ell) * np.exp(e)), w.sf2, w.sn2).lcp_grad(9, th, wts)[0]
+        lm = oracle.Model(w.X, w.y, w.kernel, tuple(np.array(w.ell) * np.exp(-e)), w.sf2, w.sn2).lcp_grad(9, th, wts)[0]
+        assert dl[d] == pytest.approx((lp - lm) / (2 * h), rel=2e-4, abs=1e-6)
