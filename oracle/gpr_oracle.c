@@ -806,12 +806,17 @@ static void sov_orthant_adj(int d, const double *L, const double *b, int64_t N, 
                 z[i] = or_norm_ppf(w[i] * e[i]);
             }
         }
-        if (!ok) continue;
+        /* samples whose product is below 1e-200 carry a negligible share of the value and of
+         * the gradient (both are proportional to f); skipping them keeps 1/phi(z) finite */
+        if (!ok || !(f > 1e-200)) continue;
         double fbar = Pbar / (double)N;
         for (int i = 0; i < d; ++i) zbar[i] = 0.0;
         for (int i = d - 1; i >= 0; --i) {
             double ebar = fbar * (f / e[i]);
-            if (i < d - 1) ebar += zbar[i] * w[i] / npdf(z[i]);
+            if (i < d - 1) {
+                double ph = npdf(z[i]);
+                if (ph > 0.0) ebar += zbar[i] * w[i] / ph;
+            }
             double ubar = ebar * npdf(u[i]);
             double lii = L[i * d + i];
             bbar[i] += ubar / lii;
