@@ -41,7 +41,9 @@ def parse():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--mode", default="dense", choices=["dense", "adaptive"])
+    p.add_argument("--mode", default="adaptive", choices=["dense", "adaptive", "backward"],
+                   help="backward: the differentiation workload (m=500 SE, 128^3, median isovalue, U(0,1) "
+                        "cell weights): forward field + hand-written adjoint per step")
     p.add_argument("--prec", default="tf32x3", choices=["fp32", "fp64", "tf32", "tf32x3", "bf16", "bf16x3"],
                    help="precision of the pre-classification / octree pass")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -157,6 +159,51 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def run_backward(args, g, torch, rank, world, local):
+    """Forward LCP field + gpr_lcp_backward on the differentiation workload; metric: grid points/s
+    of (forward + backward) steps."""
+    w = workloads.config5()
+    n = w.n
+    grid = g.make_grid(n)
+    th = w.isovalues[0]
+    opts = g.lcp_options(prec=g.GPR_P_TF32X3)
+    wts = torch.tensor(w.extra["cell_weights"], dtype=torch.float32, device="cuda")
+    field = torch.zeros((n - 1) ** 3, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        M = g.gpr_model_create(w.X, w.y, w.kernel, w.ell, w.sf2, w.sn2, stream=stream)
+        g.gpr_lcp_dense(M, grid, th, opts, field, stream=stream)
+        dy, dl = g.gpr_lcp_backward(M, grid, th, opts, wts, stream=stream)
+        M.close()
+        return dy, dl
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    g.gpr_profile_reset(); g.gpr_profile_enable(True)
+    with ClockSampler(local) as clk:
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            dy, dl = step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    g.gpr_profile_enable(False)
+    ms = e0.elapsed_time(e1) / args.steps
+    prof = {k: g.gpr_profile_read(k) for k in ("w64", "tc_sumsq", "stats_from_w64", "sov", "adj_cell", "adj_R", "adj_Z")}
+    if rank != 0:
+        return
+    out = {"metric": METRIC + " (forward + backward)", "value": world * n ** 3 / (ms / 1e3), "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": f"{w.name}: loss = sum_c U(0,1)_c LCP_c, d/dy (500) and d/dlog l (3)"},
+           "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
+           "grad_norm_y": float(np.linalg.norm(dy)), "grad_loglen": [float(v) for v in dl],
+           "clocks": clk.summary(), "gpu_launches": g.gpr_launch_count()}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -179,6 +226,9 @@ def main():
         st = g.gpr_lcp_dense(M, grid, w.isovalues[1], g.lcp_options(prec=g.GPR_P_TF32X3), out)
         g.gpr_sync()
         print(json.dumps({"case": "small", "grid": n, "m": w.m, **{k: st[k] for k in ("recon_points", "leaf_cells")}}))
+        return
+    if args.mode == "backward":
+        run_backward(args, g, torch, rank, world, local)
         return
     n = w.n
     ncell = (n - 1) ** 3

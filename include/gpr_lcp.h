@@ -222,6 +222,22 @@ gpr_status gpr_cell_lcp_from_stats_noalloc(const gpr_grid *grid, const double *s
                                            const gpr_lcp_options *opts, const int64_t *cell_idx, int64_t count,
                                            float *lcp, void *stream);
 
+/*
+ * gpr_lcp_backward -- hand-written adjoint (no counterpart in the paper) of
+ * loss = sum_c dL_dlcp[c] * LCP_c, the SOV-QMC cell LCP of gpr_lcp_dense, with
+ * respect to the observation values y and the log length scales.  The forward
+ * quantities are recomputed (kernel rows regenerated, never stored): FP64
+ * whitened rows of the kept cells' corners, the reverse sweep of the estimator
+ * per cell (FP32 samples, FP64 8x8 Cholesky adjoint), then through Eq. 1 in
+ * FP64.  Cells with dL_dlcp[c] == 0 or dropped by the Boole test contribute 0.
+ *   dL_dlcp     device float, one weight per cell
+ *   dL_dy       host double[m];  dL_dloglen host double[3]
+ * Synchronises `stream`.  opts->est must be GPR_EST_SOV_QMC (the indicator
+ * MC estimator is piecewise constant), else GPR_ERR_UNSUPPORTED.
+ */
+gpr_status gpr_lcp_backward(gpr_model *model, const gpr_grid *grid, double isovalue, const gpr_lcp_options *opts,
+                            const float *dL_dlcp, double *dL_dy, double *dL_dloglen, void *stream);
+
 /* Waits for `stream` and returns the first device-side error recorded by any
  * model since the last call (GPR_OK if none). */
 gpr_status gpr_sync(void *stream);

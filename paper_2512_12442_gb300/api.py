@@ -158,6 +158,15 @@ def gpr_lcp_adaptive(model: Model, grid: GridC, isovalue, max_depth, opts: LcpOp
     return _stats_dict(s)
 
 
+def gpr_lcp_backward(model: Model, grid: GridC, isovalue, opts: LcpOptionsC, dL_dlcp, stream=None):
+    """Adjoint of sum_c dL_dlcp[c] LCP_c: returns (dL/dy (m,), dL/dlog l (3,)) as numpy float64."""
+    dy = np.zeros(model.m); dl = np.zeros(3)
+    rc = load().gpr_lcp_backward(model.handle, C.byref(grid), float(isovalue), C.byref(opts), _ptr(dL_dlcp),
+                                 dy.ctypes.data, dl.ctypes.data, _stream(stream))
+    _check(rc, "gpr_lcp_backward")
+    return dy, dl
+
+
 def gpr_sync(stream=None):
     _check(load().gpr_sync(_stream(stream)), "gpr_sync")
 

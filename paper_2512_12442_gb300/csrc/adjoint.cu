@@ -1,0 +1,653 @@
+// Hand-written adjoint of the LCP field (no counterpart in the paper):
+//   loss = sum_c dL_dlcp[c] * LCP_c   ->   dloss/dy, dloss/dlog l_d.
+//
+// Per cell (K9): reverse sweep of the sequential-conditioning estimator (FP32, lanes over
+// samples) and the 8x8 Cholesky / jitter adjoint (FP64) give dloss/dmu_8 and dloss/dSigma_8,
+// scattered onto the per-point statistics: g_mu[p], G_var[p], G_cov[p][e].
+// Through Eq. (1) in the whitened form (K10/K11), with W rows w_p = L^-1 k_p,
+// G_pq the symmetric pair weights, Zh_p = sum_q G_pq w_q, Z_p = L^-T Zh_p, t = W^T g_mu:
+//   dloss/dy        = L^-T t
+//   dloss/dlog l_d  = sum_p g_p kd_p.alpha + sum_(p,e) G_cov[p][e] kd_e - 2 sum_p kd_p.Z_p
+//                     + tr(Kd_d L^-T (Zh^T W - v t^T) L^-1)
+// with kd = dk/dlog l_d, Kd_d = dK(X,X)/dlog l_d and v = L^-1 y.  The kernel rows K_* are
+// regenerated from the tables, never stored; the m x m parts are FP64.
+#include <math.h>
+#include <string.h>
+
+#include "internal.h"
+
+namespace {
+
+__constant__ int c_off[13][3] = {{1, -1, -1}, {1, -1, 0}, {1, -1, 1}, {1, 0, -1}, {1, 0, 0}, {1, 0, 1}, {1, 1, -1},
+                                 {1, 1, 0},   {1, 1, 1},  {0, 1, -1}, {0, 1, 0},  {0, 1, 1}, {0, 0, 1}};
+
+struct Pairs {
+    int owner[8][8];
+    int slot[8][8];
+};
+
+Pairs make_pairs()
+{
+    Pairs t;
+    for (int c1 = 0; c1 < 8; ++c1)
+        for (int c2 = 0; c2 < 8; ++c2) {
+            t.owner[c1][c2] = -1;
+            t.slot[c1][c2] = -1;
+            if (c1 == c2) continue;
+            int d[3] = {(c2 & 1) - (c1 & 1), ((c2 >> 1) & 1) - ((c1 >> 1) & 1), ((c2 >> 2) & 1) - ((c1 >> 2) & 1)};
+            for (int e = 0; e < 13; ++e) {
+                if (kOff13[e][0] == d[0] && kOff13[e][1] == d[1] && kOff13[e][2] == d[2]) { t.owner[c1][c2] = 0; t.slot[c1][c2] = e; }
+                if (kOff13[e][0] == -d[0] && kOff13[e][1] == -d[1] && kOff13[e][2] == -d[2]) { t.owner[c1][c2] = 1; t.slot[c1][c2] = e; }
+            }
+        }
+    return t;
+}
+
+__device__ __forceinline__ int tri(int i, int j) { return i * (i + 1) / 2 + j; }
+
+__device__ __forceinline__ uint64_t splitmix64(uint64_t seed, uint64_t k)
+{
+    uint64_t z = seed + k * 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+__device__ __forceinline__ float u01f(uint32_t x) { return (float)(((x >> 9) << 1) | 1u) * (1.0f / 16777216.0f); }
+__device__ __forceinline__ float npdf(float x) { return 0.3989422804014327f * __expf(-0.5f * x * x); }
+
+struct Lat {
+    uint32_t G[7];
+};
+
+struct WarpCell {
+    double L64[36];
+    float L[36];
+    float inv[8];
+    float b[8];
+    int slot[8];
+    int active;
+    int amax;
+};
+
+// K9: one warp per kept cell.
+__global__ void k_adj_cell(GridDev g, const double *stats, const int32_t *slot, const int64_t *cells, int64_t count,
+                           const float *dldlcp, double theta, double tau, double skip_eps, int N, uint64_t seed,
+                           Lat lat, Pairs pt, double *G16)
+{
+    __shared__ WarpCell wc[8];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int64_t q = blockIdx.x * (int64_t)(blockDim.x >> 5) + warp;
+    if (q >= count) return;
+    WarpCell &W = wc[warp];
+    const int64_t cidx = cells[q];
+    const float wbar = dldlcp[cidx];
+    if (lane == 0) {
+        W.active = 0;
+        int64_t cx = g.n[0] - 1, cy = g.n[1] - 1;
+        int64_t i = cidx % cx, j = (cidx / cx) % cy, k = cidx / (cx * cy);
+        const double *row[8];
+        double mu[8], S[8][8];
+        for (int c = 0; c < 8; ++c) {
+            int64_t p = (i + (c & 1)) + (int64_t)g.n[0] * ((j + ((c >> 1) & 1)) + (int64_t)g.n[1] * (k + (c >> 2)));
+            int s = slot[p];
+            W.slot[c] = s;
+            row[c] = stats + (int64_t)s * 15;
+            mu[c] = row[c][0];
+            S[c][c] = row[c][1];
+        }
+        for (int a = 0; a < 8; ++a)
+            for (int b = a + 1; b < 8; ++b) {
+                double v = pt.owner[a][b] == 0 ? row[a][2 + pt.slot[a][b]] : row[b][2 + pt.slot[a][b]];
+                S[a][b] = v;
+                S[b][a] = v;
+            }
+        double maxd = 0.0;
+        int am = 0;
+        for (int c = 0; c < 8; ++c)
+            if (S[c][c] > maxd) { maxd = S[c][c]; am = c; }
+        if (wbar != 0.0f && maxd > 1e-30) {
+            double jit = tau * maxd;
+            for (int c = 0; c < 8; ++c) S[c][c] += jit;
+            double sa = 0.0, sb = 0.0;
+            for (int c = 0; c < 8; ++c) {
+                double sd = sqrt(S[c][c]);
+                sa += normcdf((mu[c] - theta) / sd);
+                sb += normcdf((theta - mu[c]) / sd);
+            }
+            if (!(sa < skip_eps || sb < skip_eps)) {
+                double Lm[8][8];
+                double fl = 1e-3 * jit;
+                for (int a = 0; a < 8; ++a)
+                    for (int b = 0; b <= a; ++b) {
+                        double s = S[a][b];
+                        for (int r = 0; r < b; ++r) s -= Lm[a][r] * Lm[b][r];
+                        if (a == b) {
+                            if (!(s > fl)) s = fl;
+                            Lm[a][a] = sqrt(s);
+                        } else {
+                            Lm[a][b] = s / Lm[b][b];
+                        }
+                    }
+                for (int a = 0; a < 8; ++a) {
+                    W.b[a] = (float)(theta - mu[a]);
+                    W.inv[a] = (float)(1.0 / Lm[a][a]);
+                    for (int b = 0; b <= a; ++b) {
+                        W.L64[tri(a, b)] = Lm[a][b];
+                        W.L[tri(a, b)] = (float)Lm[a][b];
+                    }
+                }
+                W.amax = am;
+                W.active = 1;
+            }
+        }
+    }
+    __syncwarp();
+    if (!W.active) return;
+    uint32_t D = 0;
+    if (lane < 7) D = (uint32_t)(splitmix64(seed, (uint64_t)cidx * 8 + lane + 1) >> 32);
+    uint32_t Ds[7];
+#pragma unroll
+    for (int i = 0; i < 7; ++i) Ds[i] = __shfl_sync(0xffffffffu, D, i);
+    float bbar[2][8], Lbar[36];
+    double P[2] = {0.0, 0.0};
+#pragma unroll
+    for (int i = 0; i < 8; ++i) { bbar[0][i] = 0.f; bbar[1][i] = 0.f; }
+#pragma unroll
+    for (int t = 0; t < 36; ++t) Lbar[t] = 0.f;
+    const float fbar = -wbar / (float)N;
+    for (int k = lane; k < N; k += 32) {
+        float w[7];
+#pragma unroll
+        for (int i = 0; i < 7; ++i) {
+            uint32_t U = (uint32_t)k * lat.G[i] + Ds[i];
+            w[i] = fabsf(2.0f * u01f(U) - 1.0f);
+        }
+#pragma unroll
+        for (int side = 0; side < 2; ++side) {
+            float sg = side == 0 ? 1.f : -1.f;
+            float u[8], e[8], z[7];
+            float f = 1.f;
+            bool ok = true;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                float s = 0.f;
+#pragma unroll
+                for (int j = 0; j < i; ++j) s = fmaf(W.L[tri(i, j)], z[j], s);
+                u[i] = (sg * W.b[i] - s) * W.inv[i];
+                e[i] = normcdff(u[i]);
+                f *= e[i];
+                if (!(f > 0.f)) { ok = false; break; }
+                if (i < 7) z[i] = normcdfinvf(fmaxf(w[i] * e[i], 1e-37f));
+            }
+            if (!ok) continue;
+            P[side] += f;
+            if (!(f > 1e-30f)) continue;  // negligible share of value and gradient (both scale with f)
+            float zbar[7];
+#pragma unroll
+            for (int i = 0; i < 7; ++i) zbar[i] = 0.f;
+#pragma unroll
+            for (int i = 7; i >= 0; --i) {
+                float ebar = fbar * (f / e[i]);
+                if (i < 7) {
+                    float ph = npdf(z[i]);
+                    if (ph > 0.f) ebar += zbar[i] * w[i] / ph;
+                }
+                float ubar = ebar * npdf(u[i]);
+                bbar[side][i] += ubar * W.inv[i];
+                float sbar = -ubar * W.inv[i];
+                Lbar[tri(i, i)] += -ubar * u[i] * W.inv[i];
+#pragma unroll
+                for (int j = 0; j < i; ++j) {
+                    Lbar[tri(i, j)] = fmaf(sbar, z[j], Lbar[tri(i, j)]);
+                    zbar[j] = fmaf(sbar, W.L[tri(i, j)], zbar[j]);
+                }
+            }
+        }
+    }
+    // warp reductions (sample partial sums: FP64 for the probabilities, FP32 for the adjoints)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        P[0] += __shfl_xor_sync(0xffffffffu, P[0], o);
+        P[1] += __shfl_xor_sync(0xffffffffu, P[1], o);
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            bbar[0][i] += __shfl_xor_sync(0xffffffffu, bbar[0][i], o);
+            bbar[1][i] += __shfl_xor_sync(0xffffffffu, bbar[1][i], o);
+        }
+#pragma unroll
+    for (int t = 0; t < 36; ++t)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) Lbar[t] += __shfl_xor_sync(0xffffffffu, Lbar[t], o);
+    if (lane != 0) return;
+    double red[2 + 16 + 36];
+    red[0] = P[0];
+    red[1] = P[1];
+    for (int i = 0; i < 8; ++i) { red[2 + i] = bbar[0][i]; red[10 + i] = bbar[1][i]; }
+    for (int t = 0; t < 36; ++t) red[18 + t] = Lbar[t];
+    double lcp = 1.0 - red[0] / N - red[1] / N;
+    if (lcp < 0.0 || lcp > 1.0) return;  // clamped: constant in a neighbourhood
+    // mu adjoint: b_lo = theta - mu, b_hi = mu - theta
+    double mubar[8];
+    for (int i = 0; i < 8; ++i) mubar[i] = -red[2 + i] + red[10 + i];
+    // Cholesky adjoint: Sbar = L^-T sym(Phi(L^T Lbar)) L^-1
+    double L[8][8], Lb[8][8], Pm[8][8], T[8][8], Li[8][8], Sb[8][8];
+    for (int i = 0; i < 8; ++i)
+        for (int j = 0; j < 8; ++j) {
+            L[i][j] = j <= i ? W.L64[tri(i, j)] : 0.0;
+            Lb[i][j] = j <= i ? red[18 + tri(i, j)] : 0.0;
+        }
+    for (int i = 0; i < 8; ++i)
+        for (int j = 0; j < 8; ++j) {
+            double s = 0.0;
+            for (int k = 0; k < 8; ++k) s += L[k][i] * Lb[k][j];
+            Pm[i][j] = s;
+        }
+    for (int i = 0; i < 8; ++i)
+        for (int j = 0; j < 8; ++j) T[i][j] = j < i ? Pm[i][j] : (j == i ? 0.5 * Pm[i][i] : 0.0);
+    for (int i = 0; i < 8; ++i)
+        for (int j = 0; j < 8; ++j) Pm[i][j] = 0.5 * (T[i][j] + T[j][i]);
+    for (int c = 0; c < 8; ++c)
+        for (int i = 0; i < 8; ++i) {
+            double s = (i == c) ? 1.0 : 0.0;
+            for (int k = 0; k < i; ++k) s -= L[i][k] * Li[k][c];
+            Li[i][c] = i < c ? 0.0 : s / L[i][i];
+        }
+    for (int i = 0; i < 8; ++i)
+        for (int j = 0; j < 8; ++j) {
+            double s = 0.0;
+            for (int k = 0; k < 8; ++k) s += Pm[i][k] * Li[k][j];
+            T[i][j] = s;
+        }
+    for (int i = 0; i < 8; ++i)
+        for (int j = 0; j < 8; ++j) {
+            double s = 0.0;
+            for (int k = 0; k < 8; ++k) s += Li[k][i] * T[k][j];
+            Sb[i][j] = s;
+        }
+    double tr = 0.0;
+    for (int i = 0; i < 8; ++i) tr += Sb[i][i];
+    Sb[W.amax][W.amax] += tau * tr;
+    for (int i = 0; i < 8; ++i) {
+        double *gp = G16 + (int64_t)W.slot[i] * 16;
+        atomicAdd(gp + 0, mubar[i]);
+        atomicAdd(gp + 1, Sb[i][i]);
+    }
+    for (int a = 0; a < 8; ++a)
+        for (int b = a + 1; b < 8; ++b) {
+            int own = pt.owner[a][b] == 0 ? a : b;
+            atomicAdd(G16 + (int64_t)W.slot[own] * 16 + 2 + pt.slot[a][b], 2.0 * Sb[a][b]);
+        }
+}
+
+// t partial sums: tp[chunk][j] = sum_{p in chunk} g_mu[p] W[p][j].
+__global__ void k_wt_vec(const double *W, const double *G16, int64_t np, int64_t mp, int64_t chunk, double *tp)
+{
+    int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int64_t c = blockIdx.y;
+    if (j >= mp) return;
+    int64_t p0 = c * chunk, p1 = p0 + chunk < np ? p0 + chunk : np;
+    double s = 0.0;
+    for (int64_t p = p0; p < p1; ++p) s += G16[p * 16] * W[p * mp + j];
+    tp[c * mp + j] = s;
+}
+
+__global__ void k_sum_rows(const double *part, int64_t nrow, int64_t len, double *out)
+{
+    int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= len) return;
+    double s = 0.0;
+    for (int64_t r = 0; r < nrow; ++r) s += part[r * len + j];
+    out[j] = s;
+}
+
+// Zh_p = G_pp w_p + sum_e (G_cov[p][e]/2) w_{p+e} + sum_e (G_cov[p-e][e]/2) w_{p-e}  (warp per point).
+__global__ void k_zhat(GridDev g, const int64_t *pts, int64_t np, const int32_t *slot, const double *W,
+                       const double *G16, int64_t mp, double *Zh)
+{
+    int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    int64_t pos = blockIdx.x * (int64_t)(blockDim.x / 32) + warp;
+    if (pos >= np) return;
+    int64_t p = pts[pos];
+    int64_t nx = g.n[0], ny = g.n[1], nz = g.n[2];
+    int ix = (int)(p % nx), iy = (int)((p / nx) % ny), iz = (int)(p / (nx * ny));
+    int64_t rows[27];
+    double wts[27];
+    int cnt = 0;
+    rows[cnt] = pos;
+    wts[cnt++] = G16[pos * 16 + 1];
+    for (int e = 0; e < 13; ++e) {
+        int a = ix + c_off[e][0], b = iy + c_off[e][1], c = iz + c_off[e][2];
+        if (a >= 0 && b >= 0 && c >= 0 && a < nx && b < ny && c < nz) {
+            int s = slot[a + nx * (b + ny * (int64_t)c)];
+            double gv = G16[pos * 16 + 2 + e];
+            if (s >= 0 && gv != 0.0) { rows[cnt] = s; wts[cnt++] = 0.5 * gv; }
+        }
+        a = ix - c_off[e][0]; b = iy - c_off[e][1]; c = iz - c_off[e][2];
+        if (a >= 0 && b >= 0 && c >= 0 && a < nx && b < ny && c < nz) {
+            int s = slot[a + nx * (b + ny * (int64_t)c)];
+            if (s >= 0) {
+                double gv = G16[(int64_t)s * 16 + 2 + e];
+                if (gv != 0.0) { rows[cnt] = s; wts[cnt++] = 0.5 * gv; }
+            }
+        }
+    }
+    for (int64_t j = lane; j < mp; j += 32) {
+        double acc = 0.0;
+        for (int t = 0; t < cnt; ++t) acc += wts[t] * W[rows[t] * mp + j];
+        Zh[pos * mp + j] = acc;
+    }
+}
+
+// Generic FP64 tiled GEMM: C_z = opA(A) B over the K range of split z (partials stacked by z).
+// opA(i,k) = TA ? A[k*lda + i] : A[i*lda + k];  LOWERB: B[k][j] = 0 for k < j (skip those k).
+constexpr int GB = 64, GK = 16;
+template <bool TA, bool LOWERB>
+__global__ void __launch_bounds__(256) k_gemm64(int64_t M, int64_t N, int64_t K, const double *A, int64_t lda,
+                                                const double *B, int64_t ldb, double *C, int64_t ldc, int64_t kchunk)
+{
+    __shared__ double As[GK][GB + 2], Bs[GK][GB + 2];
+    int t = threadIdx.x, tx = t % 16, ty = t / 16;
+    int64_t i0 = (int64_t)blockIdx.x * GB, j0 = (int64_t)blockIdx.y * GB;
+    int64_t kb = (int64_t)blockIdx.z * kchunk, ke = kb + kchunk < K ? kb + kchunk : K;
+    if (LOWERB && kb < j0) kb = j0 / GK * GK;
+    double acc[4][4] = {};
+    for (int64_t k0 = kb; k0 < ke; k0 += GK) {
+        for (int e = t; e < GK * GB; e += 256) {
+            int kk = e / GB, ii = e % GB;
+            int64_t k = k0 + kk, i = i0 + ii;
+            double v = 0.0;
+            if (k < ke && i < M) v = TA ? A[k * lda + i] : A[i * lda + k];
+            As[kk][ii] = v;
+            int64_t j = j0 + ii;
+            Bs[kk][ii] = (k < ke && j < N) ? B[k * ldb + j] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < GK; ++kk) {
+            double a[4], b[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) a[r] = As[kk][ty * 4 + r];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) b[c] = Bs[kk][tx * 4 + c];
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) acc[r][c] = fma(a[r], b[c], acc[r][c]);
+        }
+        __syncthreads();
+    }
+    double *Cz = C + (int64_t)blockIdx.z * M * ldc;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        int64_t i = i0 + ty * 4 + r;
+        if (i >= M) continue;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            int64_t j = j0 + tx * 4 + c;
+            if (j < N) Cz[i * ldc + j] = acc[r][c];
+        }
+    }
+}
+
+template <bool TA, bool LOWERB>
+void gemm64(int64_t M, int64_t N, int64_t K, const double *A, int64_t lda, const double *B, int64_t ldb, double *C,
+            int64_t ldc, int splits, cudaStream_t st)
+{
+    int64_t kchunk = (K + splits - 1) / splits;
+    kchunk = (kchunk + GK - 1) / GK * GK;
+    dim3 grid((unsigned)((M + GB - 1) / GB), (unsigned)((N + GB - 1) / GB), (unsigned)splits);
+    k_gemm64<TA, LOWERB><<<grid, 256, 0, st>>>(M, N, K, A, lda, B, ldb, C, ldc, kchunk);
+    note_launch();
+}
+
+// M = R - v t^T over the m x m block (zero padding elsewhere kept).
+__global__ void k_form_m(double *R, const double *vy, const double *t, int64_t m, int64_t mp)
+{
+    int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= mp * mp) return;
+    int64_t i = idx / mp, j = idx % mp;
+    if (i < m && j < m) R[idx] -= vy[i] * t[j];
+    else R[idx] = 0.0;
+}
+
+__device__ __forceinline__ double kdot(int kind, const double *ell, double sf2, const double *a, const double *b, int d)
+{
+    double r2 = 0.0;
+    for (int q = 0; q < 3; ++q) {
+        double t = (a[q] - b[q]) / ell[q];
+        r2 += t * t;
+    }
+    double t = (a[d] - b[d]) / ell[d], t2 = t * t;
+    if (kind == GPR_K_SE) return sf2 * exp(-0.5 * r2) * t2;
+    double r = sqrt(r2), s5r = 2.2360679774997896964 * r;
+    return (5.0 / 3.0) * sf2 * (1.0 + s5r) * exp(-s5r) * t2;
+}
+
+// out[d] += sum_ij Kd_d[i][j] N[j][i]  (block reduction, FP64 atomics).
+__global__ void k_trace(const double *X, int64_t m, KernParams kp, const double *Nm, int64_t mp, double *out)
+{
+    __shared__ double red[3][256];
+    double acc[3] = {0, 0, 0};
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < m * m;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = idx / m, j = idx % m;
+        double nji = Nm[j * mp + i];
+        for (int d = 0; d < 3; ++d) acc[d] += kdot(kp.kind, kp.ell, kp.sf2, X + 3 * i, X + 3 * j, d) * nji;
+    }
+    for (int d = 0; d < 3; ++d) red[d][threadIdx.x] = acc[d];
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s)
+            for (int d = 0; d < 3; ++d) red[d][threadIdx.x] += red[d][threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int d = 0; d < 3; ++d) atomicAdd(out + d, red[d][0]);
+}
+
+struct KdPrior {
+    double k[13][3];
+};
+
+// Per-point terms: g_p kd_p.alpha - 2 kd_p.Z_p + sum_e G_cov[p][e] kd_e  (warp per point).
+__global__ void k_point_terms(GridDev g, const int64_t *pts, int64_t np, const double *X, int64_t m, KernParams kp,
+                              const double *alpha, const double *Z, int64_t mp, const double *G16, KdPrior kdp,
+                              double *out)
+{
+    int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    int64_t pos = blockIdx.x * (int64_t)(blockDim.x / 32) + warp;
+    double acc[3] = {0, 0, 0};
+    if (pos < np) {
+        int64_t p = pts[pos];
+        int64_t nx = g.n[0], ny = g.n[1];
+        double x[3] = {g.lo[0] + (double)(p % nx) * g.h[0], g.lo[1] + (double)((p / nx) % ny) * g.h[1],
+                       g.lo[2] + (double)(p / (nx * ny)) * g.h[2]};
+        double gm = G16[pos * 16];
+        const double *zr = Z + pos * mp;
+        for (int64_t j = lane; j < m; j += 32) {
+            double coef = gm * alpha[j] - 2.0 * zr[j];
+            for (int d = 0; d < 3; ++d) acc[d] += kdot(kp.kind, kp.ell, kp.sf2, x, X + 3 * j, d) * coef;
+        }
+        if (lane == 0)
+            for (int e = 0; e < 13; ++e) {
+                double gc = G16[pos * 16 + 2 + e];
+                if (gc != 0.0)
+                    for (int d = 0; d < 3; ++d) acc[d] += gc * kdp.k[e][d];
+            }
+    }
+    for (int d = 0; d < 3; ++d)
+        for (int o = 16; o > 0; o >>= 1) acc[d] += __shfl_xor_sync(0xffffffffu, acc[d], o);
+    if (lane == 0 && pos < np)
+        for (int d = 0; d < 3; ++d) atomicAdd(out + d, acc[d]);
+}
+
+// dy_i = sum_{j >= i} Linv[j][i] t_j.
+__global__ void k_dy(const double *Linv, int64_t mb, const double *t, int64_t m, double *dy)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    double s = 0.0;
+    for (int64_t j = i; j < m; ++j) s += Linv[j * mb + i] * t[j];
+    dy[i] = s;
+}
+
+__global__ void k_mask_keep(uint8_t *keep, const float *dl, int64_t nc)
+{
+    int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c < nc && dl[c] == 0.0f) keep[c] = 0;
+}
+
+}  // namespace
+
+extern "C" gpr_status gpr_lcp_backward(gpr_model *M, const gpr_grid *grid, double isovalue,
+                                       const gpr_lcp_options *opts, const float *dL_dlcp, double *dL_dy,
+                                       double *dL_dloglen, void *stream)
+{
+    if (!M || !grid_valid(grid) || !opts_valid(opts) || !dL_dlcp || !dL_dy || !dL_dloglen || !isfinite(isovalue))
+        return GPR_ERR_ARG;
+    if (opts->est != GPR_EST_SOV_QMC) return GPR_ERR_UNSUPPORTED;  // the indicator MC has no useful gradient
+    cudaStream_t st = (cudaStream_t)stream;
+    GridDev g = make_grid(grid);
+    int64_t n = g.npts(), nc = g.ncells(), m = M->m, mp = M->mp, mb = (m + 31) / 32 * 32;
+    size_t te = table_elems(M, g);
+    size_t csb = compact_scratch_bytes(nc > n ? nc : n);
+    size_t b1 = Carver::round(te * 4) + Carver::round(te * 8) + Carver::round(te * 8) + 2 * Carver::round((size_t)n * 4) +
+                Carver::round((size_t)nc) + Carver::round((size_t)n) + Carver::round((size_t)n * 8) +
+                Carver::round((size_t)n * 4) + Carver::round((size_t)nc * 8) + csb +
+                Carver::round(tc_partial_elems(GPR_P_BF16X3, M, n) * 4) + 8192;
+    GPR_TRY(ws_reserve(M, 0, b1, st));
+    Carver cv{(char *)M->ws[0]};
+    float *T32 = cv.take<float>(te);
+    double *T64 = cv.take<double>(te);
+    float2 *Tff = cv.take<float2>(te);
+    float *mean = cv.take<float>((size_t)n);
+    float *var = cv.take<float>((size_t)n);
+    uint8_t *keep = cv.take<uint8_t>((size_t)nc);
+    uint8_t *pflag = cv.take<uint8_t>((size_t)n);
+    int64_t *plist = cv.take<int64_t>((size_t)n);
+    int32_t *slot = cv.take<int32_t>((size_t)n);
+    int64_t *clist = cv.take<int64_t>((size_t)nc);
+    void *cscr = cv.take<char>(csb);
+    float *part = cv.take<float>(tc_partial_elems(GPR_P_BF16X3, M, n));
+    GPR_TRY(build_tables(M, g, T64, T32, st, Tff));
+    // cells whose LCP is not identically 0 near the current parameters (same cascade as the forward)
+    if (opts->prec == GPR_P_FP64) {
+        GPR_CUDA_TRY(cudaMemsetAsync(keep, 1, (size_t)nc, st));
+    } else {
+        GPR_TRY(fast_meanvar(M, g, opts->prec, T32, Tff, T64, nullptr, 0, n, mean, var, part, st));
+        double mv, mm;
+        prepass_margins(M, mv, mm);
+        if (opts->prec == GPR_P_TF32 || opts->prec == GPR_P_BF16) mv = M->kp.sf2;
+        launch_classify_cells(g, mean, var, isovalue, opts->skip_eps, opts->jitter, mv, mm, keep, st);
+    }
+    k_mask_keep<<<(unsigned)((nc + 255) / 256), 256, 0, st>>>(keep, dL_dlcp, nc);
+    note_launch();
+    GPR_CUDA_TRY(cudaMemsetAsync(pflag, 0, (size_t)n, st));
+    launch_mark_corners(g, keep, pflag, st);
+    int64_t npts = 0, ncell = 0;
+    GPR_TRY(compact_flags(pflag, n, plist, slot, &npts, cscr, csb, st));
+    GPR_TRY(compact_flags(keep, nc, clist, nullptr, &ncell, cscr, csb, st));
+    double h_out[3] = {0, 0, 0};
+    if (ncell == 0) {
+        memset(dL_dy, 0, sizeof(double) * m);
+        memcpy(dL_dloglen, h_out, sizeof h_out);
+        return GPR_OK;
+    }
+    const int splits = 32;
+    const int64_t chunk = 4096;
+    int64_t nchunks = (npts + chunk - 1) / chunk;
+    size_t b2 = 2 * Carver::round((size_t)npts * mp * 8) + Carver::round((size_t)npts * 15 * 8) +
+                Carver::round((size_t)npts * 16 * 8) + Carver::round((size_t)nchunks * mp * 8) +
+                Carver::round((size_t)splits * mp * mp * 8) + 3 * Carver::round((size_t)mp * mp * 8) +
+                4 * Carver::round((size_t)mp * 8) + 4096;
+    GPR_TRY(ws_reserve(M, 1, b2, st));
+    Carver cv2{(char *)M->ws[1]};
+    double *W = cv2.take<double>((size_t)npts * mp);
+    double *Zh = cv2.take<double>((size_t)npts * mp);
+    double *S15 = cv2.take<double>((size_t)npts * 15);
+    double *G16 = cv2.take<double>((size_t)npts * 16);
+    double *tp = cv2.take<double>((size_t)nchunks * mp);
+    double *Rp = cv2.take<double>((size_t)splits * mp * mp);
+    double *R = cv2.take<double>((size_t)mp * mp);
+    double *T1 = cv2.take<double>((size_t)mp * mp);
+    double *Nm = cv2.take<double>((size_t)mp * mp);
+    double *t = cv2.take<double>((size_t)mp);
+    double *dy = cv2.take<double>((size_t)mp);
+    double *acc = cv2.take<double>(4);
+    launch_w64(M, g, T64, plist, 0, npts, W, st);
+    launch_stats_from_w64(M, g, plist, 0, npts, slot, 0, W, S15, nullptr, nullptr, nullptr, st);
+    GPR_CUDA_TRY(cudaMemsetAsync(G16, 0, sizeof(double) * (size_t)npts * 16, st));
+    GPR_CUDA_TRY(cudaMemsetAsync(acc, 0, sizeof(double) * 4, st));
+    static Pairs pt = make_pairs();
+    Lat lat;
+    {
+        static const int primes[7] = {2, 3, 5, 7, 11, 13, 17};
+        for (int i = 0; i < 7; ++i) {
+            double s = sqrt((double)primes[i]);
+            lat.G[i] = (uint32_t)floor((s - floor(s)) * 4294967296.0);
+        }
+    }
+    {
+        ProfScope ps("adj_cell", st);
+        k_adj_cell<<<(unsigned)((ncell + 7) / 8), 256, 0, st>>>(g, S15, slot, clist, ncell, dL_dlcp, isovalue,
+                                                               opts->jitter, opts->skip_eps, opts->n_samples, opts->seed,
+                                                               lat, pt, G16);
+    }
+    note_launch();
+    // t = W^T g_mu
+    k_wt_vec<<<dim3((unsigned)((mp + 255) / 256), (unsigned)nchunks), 256, 0, st>>>(W, G16, npts, mp, chunk, tp);
+    note_launch();
+    k_sum_rows<<<(unsigned)((mp + 255) / 256), 256, 0, st>>>(tp, nchunks, mp, t);
+    note_launch();
+    // Zh rows, R = Zh^T W (split over points), M = R - v t^T, N = L^-T M L^-1
+    k_zhat<<<(unsigned)((npts + 7) / 8), 256, 0, st>>>(g, plist, npts, slot, W, G16, mp, Zh);
+    note_launch();
+    {
+        ProfScope ps("adj_R", st);
+        gemm64<true, false>(mp, mp, npts, Zh, mp, W, mp, Rp, mp, splits, st);
+    }
+    k_sum_rows<<<(unsigned)((mp * mp + 255) / 256), 256, 0, st>>>(Rp, splits, mp * mp, R);
+    note_launch();
+    k_form_m<<<(unsigned)((mp * mp + 255) / 256), 256, 0, st>>>(R, M->vy, t, m, mp);
+    note_launch();
+    // Linv (mb x mb) viewed with leading dimension mb; products restricted to the m x m block
+    gemm64<false, true>(m, m, m, R, mp, M->Linv, mb, T1, mp, 1, st);     // T1 = M L^-1
+    gemm64<true, false>(m, m, m, M->Linv, mb, T1, mp, Nm, mp, 1, st);    // N = L^-T T1
+    k_trace<<<(unsigned)num_sms() * 2, 256, 0, st>>>(M->X, m, M->kp, Nm, mp, acc);
+    note_launch();
+    // Z = Zh L^-1 into the W buffer (W no longer needed), then the per-point terms
+    {
+        ProfScope ps("adj_Z", st);
+        gemm64<false, true>(npts, m, m, Zh, mp, M->Linv, mb, W, mp, 1, st);
+    }
+    KdPrior kdp;
+    for (int e = 0; e < 13; ++e) {
+        double a[3] = {0, 0, 0}, b[3];
+        for (int d = 0; d < 3; ++d) b[d] = kOff13[e][d] * g.h[d];
+        double r2 = 0.0;
+        for (int d = 0; d < 3; ++d) r2 += (b[d] / M->kp.ell[d]) * (b[d] / M->kp.ell[d]);
+        for (int d = 0; d < 3; ++d) {
+            double t2 = (b[d] / M->kp.ell[d]) * (b[d] / M->kp.ell[d]);
+            if (M->kp.kind == GPR_K_SE) kdp.k[e][d] = M->kp.sf2 * exp(-0.5 * r2) * t2;
+            else {
+                double r = sqrt(r2), s5r = sqrt(5.0) * r;
+                kdp.k[e][d] = (5.0 / 3.0) * M->kp.sf2 * (1.0 + s5r) * exp(-s5r) * t2;
+            }
+        }
+        (void)a;
+    }
+    k_point_terms<<<(unsigned)((npts + 7) / 8), 256, 0, st>>>(g, plist, npts, M->X, m, M->kp, M->alpha, W, mp, G16,
+                                                              kdp, acc);
+    note_launch();
+    k_dy<<<(unsigned)((m + 127) / 128), 128, 0, st>>>(M->Linv, mb, t, m, dy);
+    note_launch();
+    GPR_CUDA_TRY(cudaGetLastError());
+    GPR_CUDA_TRY(cudaMemcpyAsync(dL_dy, dy, sizeof(double) * m, cudaMemcpyDeviceToHost, st));
+    GPR_CUDA_TRY(cudaMemcpyAsync(h_out, acc, sizeof(double) * 3, cudaMemcpyDeviceToHost, st));
+    GPR_CUDA_TRY(cudaStreamSynchronize(st));
+    memcpy(dL_dloglen, h_out, sizeof h_out);
+    return GPR_OK;
+}
