@@ -32,6 +32,9 @@ import numpy as np  # noqa: E402
 import workloads  # noqa: E402
 
 METRIC = "LCP grid points/s"
+# FP32 FLOPs executed by k_sov per estimated cell (1600 samples x 2 orthants), from the ncu
+# instruction counters of the small case; see the k_sov profile summary under profiles/.
+SOV_FP32_FLOPS_PER_CELL = 2.1255e6
 UNIT = "grid points/s"
 
 
@@ -225,7 +228,7 @@ def main():
         M = g.gpr_model_create(w.X, w.y, w.kernel, w.ell, w.sf2, w.sn2)
         st = g.gpr_lcp_dense(M, grid, w.isovalues[1], g.lcp_options(prec=g.GPR_P_TF32X3), out)
         g.gpr_sync()
-        print(json.dumps({"case": "small", "grid": n, "m": w.m, **{k: st[k] for k in ("recon_points", "leaf_cells")}}))
+        print(json.dumps({"case": "small", "grid": n, "m": w.m, **{k: st[k] for k in ("recon_points", "leaf_cells", "cells_estimated")}}))
         return
     if args.mode == "backward":
         run_backward(args, g, torch, rank, world, local)
@@ -278,8 +281,9 @@ def main():
     g.gpr_profile_enable(False)
     launches = g.gpr_launch_count()
     ms = ev0.elapsed_time(ev1) / args.steps
-    prof = {k: g.gpr_profile_read(k) for k in ("w64", "meanvar32", "tc_sumsq", "mean_ff", "stats_from_w64", "cell_prep",
-                                                "sov", "classify", "oct_eval_w")}
+    prof = {k: g.gpr_profile_read(k) for k in ("w64", "oz_w", "stats_ff", "meanvar32", "tc_sumsq", "mean_ff",
+                                                "stats_from_w64", "cell_prep", "sov", "classify", "oct_eval_w",
+                                                "oct_level")}
     g.gpr_sync(stream)
     M.close()
     t_max = ms
@@ -313,28 +317,46 @@ def main():
             dist.destroy_process_group()
         return
 
-    # roofline of the dominant kernel
-    dom = max(prof, key=lambda k: prof[k][0])
+    # roofline of the dominant kernel (oct_level spans whole octree levels, not one kernel)
+    kern = {k: v for k, v in prof.items() if k != "oct_level"}
+    dom = max(kern, key=lambda k: kern[k][0])
     m = w.m
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         pass
+    nfield = len(stats_last)
     recon = sum(stats_last[t]["recon_points"] for t in stats_last)
+    est_cells = sum(stats_last[t]["cells_estimated"] for t in stats_last)
     roof = None
-    if dom == "w64" and prof["w64"][1] > 0:
-        # algorithmic FLOPs of the triangular whitening GEMM: 2 * sum_{j<m} (j+1) per point
-        flops_per_launch = recon / len(stats_last) * m * (m + 1)
-        avg_s = prof["w64"][0] / prof["w64"][1] / 1e3
-        achieved = flops_per_launch / avg_s / 1e12
-        peak = 2.0 * 2 * 152 * 2.07e9 / 1e12  # FP64: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz (derived)
-        # DRAM bytes per W row from the ncu capture of the small case (bench.py --case small:
-        # 609.7 MB for 161,920 rows); traffic grows with the rows, so scale to this launch.
-        traffic = 609.7e6 / 161920 * recon / len(stats_last)
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": traffic, "kernel": "k_w_store<double> (FP64 whitening GEMM)",
-                "peak_source": "derived FP64 issue rate 2 DFMA/clk/SM x 152 x 2.07 GHz (probe measured 1.202)"}
+    if kern[dom][1] > 0:
+        avg_s = kern[dom][0] / kern[dom][1] / 1e3
+        if dom == "w64":
+            flops = recon / nfield * m * (m + 1)  # triangular whitening GEMM, per launch
+            peak = 2.0 * 2 * 152 * 2.07e9 / 1e12
+            roof = {"bound": "alu", "achieved": flops / avg_s / 1e12, "peak": peak, "unit": "TFLOP/s",
+                    "traffic": 609.7e6 / 161920 * recon / nfield, "kernel": "k_w_store<double> (FP64 whitening GEMM)",
+                    "peak_source": "derived FP64 issue rate 2 DFMA/clk/SM x 152 x 2.07 GHz (probe measured 1.202)"}
+        elif dom == "oz_w":
+            # BF16 tensor work actually issued: 28 digit products x 2 x rows x sum over 64-column tiles of
+            # 64 x ceil(min(n0+64, m)/32)*32 (the K range of each tile)
+            mp = (m + 63) // 64 * 64
+            kk = sum(64 * ((min(n0 + 64, m) + 31) // 32 * 32) for n0 in range(0, mp, 64))
+            flops = 28 * 2 * (recon / nfield) * kk
+            peak = float(peaks.get("bf16_tflops_sustained") or 1733.1)
+            roof = {"bound": "tensor", "achieved": flops / avg_s / 1e12, "peak": peak, "unit": "TFLOP/s",
+                    "traffic": None, "kernel": "k_oz_w (FP64-class whitening GEMM, BF16 digit split)",
+                    "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained"}
+        elif dom == "sov":
+            # FP32-pipe FLOPs executed per estimated cell (ncu instruction counters of k_sov on the small case:
+            # 2 x ffma + fadd + fmul thread-instructions per cell); MUFU and integer work are not counted
+            flops = SOV_FP32_FLOPS_PER_CELL * est_cells / nfield
+            roof = {"bound": "alu", "achieved": flops / avg_s / 1e12, "peak": 73.07, "unit": "TFLOP/s",
+                    "traffic": None, "kernel": "k_sov (SOV-QMC estimator, FP32)",
+                    "peak_source": "FP32 FMA probe (73.07 TFLOP/s measured on this GB300 model)"}
+        if roof:
+            roof["frac"] = roof["achieved"] / roof["peak"]
     cpu = None if args.no_cpu_baseline else cpu_baseline(w, w.isovalues[1], args.cpu_sample)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,

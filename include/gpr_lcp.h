@@ -66,6 +66,13 @@ typedef enum {
 
 typedef enum { GPR_EST_SOV_QMC = 0, GPR_EST_MC = 1 } gpr_estimator;
 
+/* Arithmetic of the FP64-class reconstruction of the LCP cells' corners.
+ * GPR_EXACT_AUTO: BF16 tensor cores with an error-free split of both operands into
+ * seven 6-bit digit slices (28 products, exact FP32 accumulation for m <= 1024, SE
+ * kernels) and float-float statistics; FP64 CUDA cores otherwise.
+ * GPR_EXACT_FP64: always FP64 CUDA cores. */
+typedef enum { GPR_EXACT_AUTO = 0, GPR_EXACT_FP64 = 1 } gpr_exact_mode;
+
 typedef struct {
     double lo[3], hi[3];
     int32_t n[3]; /* points per axis */
@@ -82,6 +89,7 @@ typedef struct {
     double skip_eps;       /* Boole pre-skip threshold, default 1e-9 */
     gpr_precision prec;    /* precision of the pre-classification / octree pass, default GPR_P_FP32 */
     int32_t max_iters_min; /* projected steps T of the box minimiser, default 4 */
+    gpr_exact_mode exact;  /* FP64-class corner statistics: tensor-core digit split or FP64, default AUTO */
 } gpr_lcp_options;
 
 typedef struct {

@@ -18,7 +18,7 @@ class GridC(C.Structure):
 class LcpOptionsC(C.Structure):
     _fields_ = [("alpha", C.c_double), ("beta", C.c_double), ("est", C.c_int), ("n_samples", C.c_int32),
                 ("seed", C.c_uint64), ("jitter", C.c_double), ("skip_eps", C.c_double), ("prec", C.c_int),
-                ("max_iters_min", C.c_int32)]
+                ("max_iters_min", C.c_int32), ("exact", C.c_int)]
 
 
 class AdaptiveStatsC(C.Structure):
@@ -55,6 +55,8 @@ SIGNATURES = {
     "gpr_launch_count": (C.c_int64, []),
     # test hooks (not in the public header)
     "gpr_model_export": (C.c_int, [C.c_void_p] + [C.c_void_p] * 5),
+    "gpr_stats_points_split": (C.c_int, [C.c_void_p, C.POINTER(GridC), C.c_void_p, C.c_int64, C.c_void_p,
+                                         C.c_void_p]),
     "gpr_octree_trace": (C.c_int, [C.c_void_p, C.POINTER(GridC), C.c_double, C.c_int32, C.POINTER(LcpOptionsC),
                                    C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
                                    C.POINTER(C.c_int64), C.c_void_p]),

@@ -13,6 +13,7 @@ from ._lib import AdaptiveStatsC, GridC, LcpOptionsC, load
 GPR_K_SE, GPR_K_MATERN52 = 0, 1
 GPR_P_FP64, GPR_P_FP32, GPR_P_TF32, GPR_P_TF32X3, GPR_P_BF16, GPR_P_BF16X3 = range(6)
 GPR_EST_SOV_QMC, GPR_EST_MC = 0, 1
+GPR_EXACT_AUTO, GPR_EXACT_FP64 = 0, 1
 GPR_OK, GPR_ERR_ARG, GPR_ERR_NOT_PD, GPR_ERR_CUDA, GPR_ERR_OOM, GPR_ERR_TIMEOUT, GPR_ERR_UNSUPPORTED = range(7)
 
 
@@ -181,6 +182,13 @@ def gpr_octree_trace(model: Model, grid: GridC, isovalue, max_depth, opts: LcpOp
                                    C.byref(cnt), _stream(stream)), "gpr_octree_trace")
     c = min(cnt.value, capacity)
     return nodes[:c], dec[:c], bnd[:c]
+
+
+def gpr_stats_points_split(model: Model, grid: GridC, point_idx, stats, stream=None):
+    """Test hook: stats15 through the tensor-core digit-split path."""
+    rc = load().gpr_stats_points_split(model.handle, C.byref(grid), _ptr(point_idx), int(point_idx.numel()),
+                                       _ptr(stats), _stream(stream))
+    _check(rc, "gpr_stats_points_split")
 
 
 def gpr_model_export(model: Model):

@@ -17,6 +17,7 @@ extern "C" void gpr_lcp_options_default(gpr_lcp_options *o)
     o->skip_eps = 1e-9;
     o->prec = GPR_P_FP32;
     o->max_iters_min = 4;
+    o->exact = GPR_EXACT_AUTO;
 }
 
 extern "C" const char *gpr_status_string(gpr_status s)
@@ -53,6 +54,7 @@ bool opts_valid(const gpr_lcp_options *o)
     if (!(o->alpha >= 0.0) || !isfinite(o->alpha)) return false;
     if (o->prec < GPR_P_FP64 || o->prec > GPR_P_BF16X3) return false;
     if (o->max_iters_min < 0 || o->max_iters_min > 64) return false;
+    if (o->exact != GPR_EXACT_AUTO && o->exact != GPR_EXACT_FP64) return false;
     return true;
 }
 
@@ -240,6 +242,7 @@ LcpOpts lcp_opts(const gpr_lcp_options *o, double theta)
     l.est = o->est;
     l.n_samples = o->n_samples;
     l.seed = o->seed;
+    l.exact_mode = o->exact;
     return l;
 }
 
@@ -354,16 +357,28 @@ gpr_status lcp_from_kept_cells(gpr_model *M, const GridDev &g, const double *T64
         stats->leaf_cells = ncell;
     }
     if (ncell == 0) return GPR_OK;
-    // FP64 W rows and stats15 for the kept cells' corners, then the estimator.
+    // FP64-class W rows and stats15 for the kept cells' corners, then the estimator.  Default:
+    // the tensor-core digit-split GEMM with float-float statistics; FP64 CUDA cores on request
+    // or where the split's exactness bound does not hold (m > 1024, Matern).
+    const bool use_oz = lo.exact_mode == GPR_EXACT_AUTO && oz_supported(M);
+    size_t te = table_elems(M, g);
     size_t b2 = Carver::round((size_t)npts * M->mp * sizeof(double)) + Carver::round((size_t)npts * 15 * sizeof(double)) +
-                cell_lcp_scratch_bytes(ncell) + 1024;
+                cell_lcp_scratch_bytes(ncell) + Carver::round(te * sizeof(float2)) + 2048;
     GPR_TRY(ws_reserve(M, 1, b2, st));
     Carver cv2{(char *)M->ws[1]};
     double *W = cv2.take<double>((size_t)npts * M->mp);
     double *S15 = cv2.take<double>((size_t)npts * 15);
     void *scr = cv2.take<char>(cell_lcp_scratch_bytes(ncell));
-    launch_w64(M, g, T64, plist, 0, npts, W, st);
-    launch_stats_from_w64(M, g, plist, 0, npts, slot, 0, W, S15, nullptr, nullptr, nullptr, st);
+    float2 *Tu = cv2.take<float2>(te);
+    if (use_oz) {
+        GPR_TRY(oz_prepare(M, st));
+        GPR_TRY(oz_unit_tables(M, g, Tu, st));
+        GPR_TRY(launch_oz_w(M, g, Tu, plist, 0, npts, (float2 *)W, st));
+        GPR_TRY(launch_stats_ff(M, g, plist, npts, slot, (const float2 *)W, S15, st));
+    } else {
+        launch_w64(M, g, T64, plist, 0, npts, W, st);
+        launch_stats_from_w64(M, g, plist, 0, npts, slot, 0, W, S15, nullptr, nullptr, nullptr, st);
+    }
     GPR_CUDA_TRY(cudaGetLastError());
     int64_t nest = 0;
     GPR_TRY(run_cell_lcp(g, S15, slot, clist, ncell, lo, lcp, false, scr, cell_lcp_scratch_bytes(ncell),

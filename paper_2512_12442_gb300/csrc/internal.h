@@ -59,6 +59,8 @@ struct TcOperands {
     void *b0 = nullptr, *b1 = nullptr, *b2 = nullptr;  // BF16 slices
 };
 
+struct OzOperands;  // tensor-core FP64-class operands (ozaki.cu)
+
 struct gpr_model {
     int64_t m = 0;
     int64_t mp = 0;  // m rounded up to a multiple of 64 (GEMM column padding)
@@ -82,6 +84,7 @@ struct gpr_model {
     float *X32 = nullptr;      // m x 3 FP32 observation sites
     float *alpha32 = nullptr;  // mp FP32 alpha
     TcOperands *tc = nullptr;  // built on first tensor-core use
+    OzOperands *oz = nullptr;  // built on first FP64-class tensor-core use
     // host copies used by the octree p-test
     std::vector<double> hX, hy;
     // two independent workspaces (grow, never shrink): slot 0 for a call's first phase,
@@ -148,11 +151,22 @@ gpr_status fast_meanvar(gpr_model *M, const GridDev &g, gpr_precision prec, cons
                         const double *T64, const int64_t *pts, int64_t pt_base, int64_t count, float *mean, float *var,
                         float *partial, cudaStream_t st);
 
+// ---- FP64-class whitened rows on the tensor cores (ozaki.cu)
+bool oz_supported(const gpr_model *M);
+gpr_status oz_prepare(gpr_model *M, cudaStream_t st);
+void oz_release(gpr_model *M);
+gpr_status oz_unit_tables(const gpr_model *M, const GridDev &g, float2 *Tu, cudaStream_t st);
+gpr_status launch_oz_w(const gpr_model *M, const GridDev &g, const float2 *Tu, const int64_t *pts, int64_t pt_base,
+                       int64_t count, float2 *W, cudaStream_t st);
+gpr_status launch_stats_ff(const gpr_model *M, const GridDev &g, const int64_t *pts, int64_t count, const int32_t *slot,
+                           const float2 *W, double *out15, cudaStream_t st);
+
 // ---- LCP (lcp.cu)
 struct LcpOpts {
     double theta, tau, skip_eps;
     int est, n_samples;
     uint64_t seed;
+    int exact_mode;  // gpr_lcp_options.exact
 };
 // For cells in `cells` (nullptr = all), build Sigma_8 from stats (indexed via slot map, nullptr = identity),
 // write 0/1 for skipped/deterministic cells into lcp[cell-or-position], and queue the rest.

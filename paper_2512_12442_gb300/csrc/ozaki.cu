@@ -1,0 +1,570 @@
+// FP64-class whitened rows W = K_* L^-T on the BF16 tensor cores by an error-free digit split
+// (Ozaki scheme): both operands are written as sums of S slices of signed 6-bit integer digits
+// times powers of two,
+//   a' = k / sf2 in [0,1]:        a' = sum_s i_s 2^(-6(s+1)),   |i_0| <= 64, |i_s| <= 32,
+//   b' = [L^-1]_ji / 2^F_j:       b' = sum_t l_t 2^(-6(t+1)),   per output column j,
+// so every digit is exact in BF16 and every product i_s * l_t is exact.  Products of the same
+// level d = s + t share one power-of-two weight and are accumulated in one TMEM accumulator;
+// for K <= 1024 the integer sums stay below 2^24 and the FP32 accumulation is exact.  The
+// epilogue combines the levels (smallest first) in float-float arithmetic and writes W as
+// (hi, lo) float pairs.  Products with s + t < S are kept; S = 7 -> 28 products.
+//
+// Tiles: M = 128 points, N = 64 columns, K blocks of 32 digits (64-byte rows, 64B swizzle),
+// two stages; the S accumulators use S x 64 of the 512 TMEM columns.  B digit slices arrive by
+// TMA (one 3-D tensor map: slice, row j, column i); A digits are generated from float-float
+// separable tables by all warps.  Mbarrier waits are bounded.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <math.h>
+
+#include <mutex>
+
+#include "internal.h"
+
+namespace {
+
+constexpr int TM = 128, TN = 64, BKE = 32, NTHR = 256, BETA = 6;
+constexpr uint32_t kSpin = 1u << 22;
+constexpr int A_SLICE = TM * 64;   // bytes of one A digit slice per K block
+constexpr int B_SLICE = TN * 64;   // bytes of one B digit slice per K block
+
+__device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// K-major, 64-byte swizzle (8-row groups 512 B apart).
+__device__ __forceinline__ uint64_t desc_sw64(uint32_t addr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(512 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)4 << 61;  // 64-byte swizzle
+    return d;
+}
+
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+
+__device__ __forceinline__ bool wait_bar(uint32_t a, uint32_t par)
+{
+    for (uint32_t it = 0; it < kSpin; ++it) {
+        uint32_t done;
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.b32 %0, 1, 0, p;\n}\n"
+                     : "=r"(done)
+                     : "r"(a), "r"(par)
+                     : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+struct FF {
+    float h, l;
+};
+__device__ __forceinline__ FF ff_mul(FF a, FF b)
+{
+    float p = a.h * b.h;
+    float e = fmaf(a.h, b.h, -p);
+    e = fmaf(a.h, b.l, e);
+    e = fmaf(a.l, b.h, e);
+    float s = p + e;
+    return {s, e - (s - p)};
+}
+__device__ __forceinline__ FF ff_add(FF a, FF b)
+{
+    float s = a.h + b.h;
+    float bv = s - a.h;
+    float err = (a.h - (s - bv)) + (b.h - bv);
+    err += a.l + b.l;
+    float r = s + err;
+    return {r, err - (r - s)};
+}
+__device__ __forceinline__ FF ff_add_f(FF a, float b)
+{
+    float s = a.h + b;
+    float bv = s - a.h;
+    float err = (a.h - (s - bv)) + (b - bv) + a.l;
+    float r = s + err;
+    return {r, err - (r - s)};
+}
+
+struct OzParams {
+    const float2 *Tu;  // unit (no sf2) float-float SE tables, 3 axes
+    int64_t off1, off2, mp, m;
+    GridDev g;
+    const int64_t *pts;
+    int64_t pt_base, count;
+    const float *colscale;  // 2^F_j
+    float sf2;
+    float2 *W;  // count x mp float-float
+    int *status;
+};
+
+template <int S>
+__global__ void __launch_bounds__(NTHR, 1) k_oz_w(const __grid_constant__ CUtensorMap mapB, OzParams prm)
+{
+    constexpr int STAGE = S * A_SLICE + S * B_SLICE;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t *bars = (uint64_t *)(smem + 2 * STAGE);
+    __shared__ uint32_t tmem_slot;
+    __shared__ int gx[TM], gy[TM], gz[TM];
+    __shared__ bool rvalid[TM];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int64_t row0 = (int64_t)blockIdx.x * TM;
+    const int n0 = blockIdx.y * TN;
+    const int64_t m = prm.m;
+    const int64_t kend = (int64_t)n0 + TN < m ? (int64_t)n0 + TN : m;
+    const int nkb = (int)((kend + BKE - 1) / BKE);
+    const uint32_t full0 = su32(&bars[0]), free0 = su32(&bars[2]), done = su32(&bars[4]);
+    if (tid == 0) {
+        for (int b = 0; b < 5; ++b) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&bars[b])));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(su32(&tmem_slot)));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    for (int r = tid; r < TM; r += NTHR) {
+        int64_t row = row0 + r;
+        bool ok = row < prm.count;
+        int64_t p = ok ? (prm.pts ? prm.pts[row] : prm.pt_base + row) : 0;
+        int64_t nx = prm.g.n[0], ny = prm.g.n[1];
+        if (p < 0 || p >= nx * ny * (int64_t)prm.g.n[2]) { ok = false; p = 0; }
+        gx[r] = (int)(p % nx);
+        gy[r] = (int)((p / nx) % ny);
+        gz[r] = (int)(p / (nx * ny));
+        rvalid[r] = ok;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_slot;
+    bool ok_all = true;
+
+    for (int kb = 0; kb < nkb; ++kb) {
+        const int s = kb & 1, use = kb >> 1;
+        unsigned char *st = smem + s * STAGE;
+        if (kb >= 2 && !wait_bar(free0 + 8 * s, (use - 1) & 1)) ok_all = false;
+        if (tid == 0) {
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(full0 + 8 * s),
+                         "r"((uint32_t)(S * B_SLICE))
+                         : "memory");
+            for (int t = 0; t < S; ++t)
+                asm volatile(
+                    "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
+                    "%4}], [%5];" ::"r"(su32(st + S * A_SLICE + t * B_SLICE)),
+                    "l"((uint64_t)&mapB), "r"(kb * BKE), "r"(n0), "r"(t), "r"(full0 + 8 * s)
+                    : "memory");
+        }
+        // A digits: thread -> (row r, 16 consecutive k)
+        {
+            const int r = tid >> 1, half = tid & 1;
+            float dig[S][16];
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+                const int64_t j = (int64_t)kb * BKE + half * 16 + e;
+                FF a = {0.f, 0.f};
+                if (rvalid[r] && j < m) {
+                    float2 x = prm.Tu[(int64_t)gx[r] * prm.mp + j], y = prm.Tu[prm.off1 + (int64_t)gy[r] * prm.mp + j],
+                           z = prm.Tu[prm.off2 + (int64_t)gz[r] * prm.mp + j];
+                    a = ff_mul(ff_mul(FF{x.x, x.y}, FF{y.x, y.y}), FF{z.x, z.y});
+                }
+                // signed 6-bit digits of a in [0,1]; the low part joins once the high part is consumed
+                float rr = a.h;
+#pragma unroll
+                for (int d = 0; d < S; ++d) {
+                    if (d == 3) rr += a.l;
+                    const float i = rintf(ldexpf(rr, BETA * (d + 1)));
+                    dig[d][e] = i;
+                    rr = fmaf(-i, ldexpf(1.0f, -BETA * (d + 1)), rr);
+                }
+            }
+#pragma unroll
+            for (int d = 0; d < S; ++d) {
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    uint32_t wd[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        uint32_t lo = __bfloat16_as_ushort(__float2bfloat16_rn(dig[d][c * 8 + 2 * q]));
+                        uint32_t hi = __bfloat16_as_ushort(__float2bfloat16_rn(dig[d][c * 8 + 2 * q + 1]));
+                        wd[q] = lo | (hi << 16);
+                    }
+                    const int chunk = half * 2 + c;  // 16-byte chunk in the 64-byte row
+                    const int off = r * 64 + ((chunk ^ ((r >> 1) & 3)) << 4);
+                    *(uint4 *)(st + d * A_SLICE + off) = make_uint4(wd[0], wd[1], wd[2], wd[3]);
+                }
+            }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            if (!wait_bar(full0 + 8 * s, use & 1)) ok_all = false;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+            for (int sa = 0; sa < S; ++sa)
+#pragma unroll
+                for (int tb = 0; tb < S - sa; ++tb) {
+                    const int lvl = sa + tb;
+                    const uint32_t ab = su32(st + sa * A_SLICE), bb = su32(st + S * A_SLICE + tb * B_SLICE);
+#pragma unroll
+                    for (int kk = 0; kk < 2; ++kk) {
+                        uint32_t acc = (kb == 0 && sa == 0 && kk == 0) ? 0u : 1u;
+                        asm volatile(
+                            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+                                tmem + (uint32_t)(lvl * TN)),
+                            "l"(desc_sw64(ab + kk * 32)), "l"(desc_sw64(bb + kk * 32)), "r"(kIdesc), "r"(acc));
+                    }
+                }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(free0 + 8 * s)
+                         : "memory");
+            if (kb == nkb - 1)
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(done)
+                             : "memory");
+        }
+    }
+    if (!wait_bar(done, 0)) ok_all = false;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // epilogue: warp -> lanes 32*(w%4), columns 32*(w/4) of every level accumulator
+    const int lq = warp & 3, half = warp >> 2;
+    FF acc[32];
+#pragma unroll
+    for (int c = 0; c < 32; ++c) acc[c] = FF{0.f, 0.f};
+#pragma unroll
+    for (int lvl = S - 1; lvl >= 0; --lvl) {
+        uint32_t rr[32];
+        const uint32_t taddr = tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(lvl * TN + half * 32);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,"
+            "%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+            : "=r"(rr[0]), "=r"(rr[1]), "=r"(rr[2]), "=r"(rr[3]), "=r"(rr[4]), "=r"(rr[5]), "=r"(rr[6]), "=r"(rr[7]),
+              "=r"(rr[8]), "=r"(rr[9]), "=r"(rr[10]), "=r"(rr[11]), "=r"(rr[12]), "=r"(rr[13]), "=r"(rr[14]),
+              "=r"(rr[15]), "=r"(rr[16]), "=r"(rr[17]), "=r"(rr[18]), "=r"(rr[19]), "=r"(rr[20]), "=r"(rr[21]),
+              "=r"(rr[22]), "=r"(rr[23]), "=r"(rr[24]), "=r"(rr[25]), "=r"(rr[26]), "=r"(rr[27]), "=r"(rr[28]),
+              "=r"(rr[29]), "=r"(rr[30]), "=r"(rr[31])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        const float wgt = ldexpf(1.0f, -BETA * (lvl + 2));
+#pragma unroll
+        for (int c = 0; c < 32; ++c) acc[c] = ff_add_f(acc[c], __uint_as_float(rr[c]) * wgt);
+    }
+    const int64_t row = row0 + lq * 32 + lane;
+    if (row < prm.count) {
+        float2 *out = prm.W + row * prm.mp + n0 + half * 32;
+#pragma unroll
+        for (int c = 0; c < 32; ++c) {
+            const int64_t j = n0 + half * 32 + c;
+            float cs = (j < prm.mp) ? prm.colscale[j] : 0.f;
+            FF v = {acc[c].h * cs, acc[c].l * cs};  // power-of-two scale: exact
+            if (prm.sf2 != 1.0f) v = ff_mul(v, FF{prm.sf2, 0.f});
+            if (j < prm.mp) out[c] = make_float2(v.h, v.l);
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (!ok_all) atomicCAS(prm.status, 0, (int)GPR_ERR_TIMEOUT);
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem));
+    }
+}
+
+// Digit slices of b' = [L^-1]_ji / 2^F_j, layout [S][mpt rows j][mpt cols i] (K-major), BF16.
+__global__ void k_oz_split_b(const double *Linv, int64_t mb, int64_t m, int64_t mpt, int S, const float *colscale,
+                             __nv_bfloat16 *B)
+{
+    int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= mpt * mpt) return;
+    int64_t j = idx / mpt, i = idx % mpt;
+    double v = (j < m && i <= j) ? Linv[j * mb + i] / (double)colscale[j] : 0.0;
+    double r = v;
+    for (int t = 0; t < S; ++t) {
+        double sc = ldexp(1.0, BETA * (t + 1));
+        double d = rint(r * sc);
+        r -= d / sc;
+        B[(int64_t)t * mpt * mpt + idx] = __double2bfloat16(d);
+    }
+}
+
+// Column scales 2^F_j with max_i |[L^-1]_ji| <= 2^F_j (one warp per column).
+__global__ void k_oz_colscale(const double *Linv, int64_t mb, int64_t m, int64_t mpt, float *cs)
+{
+    int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    int64_t j = blockIdx.x * (int64_t)(blockDim.x / 32) + warp;
+    if (j >= mpt) return;
+    double mx = 0.0;
+    if (j < m)
+        for (int64_t i = lane; i <= j; i += 32) mx = fmax(mx, fabs(Linv[j * mb + i]));
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) {
+        int e = 0;
+        if (mx > 0.0) {
+            frexp(mx, &e);  // mx = f 2^e, f in [0.5, 1)
+        }
+        cs[j] = ldexpf(1.0f, e);
+    }
+}
+
+// Unit float-float SE tables exp(-(x_g - X_jd)^2 / (2 l_d^2)) (no signal variance).
+__global__ void k_unit_tables(const double *X, int64_t m, int64_t mp, KernParams kp, GridDev g, float2 *Tu)
+{
+    int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int64_t total = (int64_t)(g.n[0] + g.n[1] + g.n[2]) * mp;
+    if (idx >= total) return;
+    int64_t row = idx / mp, j = idx % mp;
+    int d = 0;
+    int64_t gi = row;
+    if (gi >= g.n[0]) { gi -= g.n[0]; d = 1; if (gi >= g.n[1]) { gi -= g.n[1]; d = 2; } }
+    double v = 0.0;
+    if (j < m) {
+        double x = g.lo[d] + (double)gi * g.h[d];
+        double t = (x - X[3 * j + d]) / kp.ell[d];
+        v = exp(-0.5 * t * t);
+    }
+    float h = (float)v;
+    Tu[idx] = make_float2(h, (float)(v - (double)h));
+}
+
+// stats15 from float-float W rows (warp per listed point).
+__constant__ int c_off[13][3] = {{1, -1, -1}, {1, -1, 0}, {1, -1, 1}, {1, 0, -1}, {1, 0, 0}, {1, 0, 1}, {1, 1, -1},
+                                 {1, 1, 0},   {1, 1, 1},  {0, 1, -1}, {0, 1, 0},  {0, 1, 1}, {0, 0, 1}};
+struct Prior13 {
+    double k[13];
+};
+
+__global__ void k_stats_ff(GridDev g, const int64_t *pts, int64_t count, const int32_t *slot, const float2 *W,
+                           int64_t mp, int64_t m, const float2 *vyff, double sf2, Prior13 pr, double *out15)
+{
+    int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    int64_t pos = blockIdx.x * (int64_t)(blockDim.x / 32) + warp;
+    if (pos >= count) return;
+    int64_t p = pts[pos];
+    int64_t nx = g.n[0], ny = g.n[1], nz = g.n[2];
+    int ix = (int)(p % nx), iy = (int)((p / nx) % ny), iz = (int)(p / (nx * ny));
+    int64_t self = slot[p];
+    int64_t nb[13];
+#pragma unroll
+    for (int e = 0; e < 13; ++e) {
+        int a = ix + c_off[e][0], b = iy + c_off[e][1], c = iz + c_off[e][2];
+        int64_t r = -1;
+        if (a >= 0 && b >= 0 && c >= 0 && a < nx && b < ny && c < nz) r = slot[a + nx * (b + ny * (int64_t)c)];
+        nb[e] = r;
+    }
+    FF acc[15];
+#pragma unroll
+    for (int s = 0; s < 15; ++s) acc[s] = FF{0.f, 0.f};
+    const float2 *wp = W + self * mp;
+    for (int64_t j = lane; j < m; j += 32) {
+        float2 w = wp[j];
+        FF a = {w.x, w.y};
+        float2 v = vyff[j];
+        acc[0] = ff_add(acc[0], ff_mul(a, FF{v.x, v.y}));
+        acc[1] = ff_add(acc[1], ff_mul(a, a));
+#pragma unroll
+        for (int e = 0; e < 13; ++e)
+            if (nb[e] >= 0) {
+                float2 q = W[nb[e] * mp + j];
+                acc[2 + e] = ff_add(acc[2 + e], ff_mul(a, FF{q.x, q.y}));
+            }
+    }
+#pragma unroll
+    for (int s = 0; s < 15; ++s)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            FF t = {__shfl_xor_sync(0xffffffffu, acc[s].h, o), __shfl_xor_sync(0xffffffffu, acc[s].l, o)};
+            acc[s] = ff_add(acc[s], t);
+        }
+    if (lane == 0) {
+        double *o = out15 + pos * 15;
+        o[0] = (double)acc[0].h + (double)acc[0].l;
+        o[1] = sf2 - ((double)acc[1].h + (double)acc[1].l);
+#pragma unroll
+        for (int e = 0; e < 13; ++e)
+            o[2 + e] = nb[e] >= 0 ? pr.k[e] - ((double)acc[2 + e].h + (double)acc[2 + e].l) : (double)NAN;
+    }
+}
+
+__global__ void k_vyff(const double *vy, int64_t mp, float2 *out)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= mp) return;
+    double v = vy[i];
+    float h = (float)v;
+    out[i] = make_float2(h, (float)(v - (double)h));
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        cudaDriverEntryPointQueryResult q;
+        void *p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    });
+    return fn;
+}
+
+}  // namespace
+
+struct OzOperands {
+    int S = 7;
+    int64_t mpt = 0;
+    void *B = nullptr;        // S x mpt x mpt BF16 digits
+    float *colscale = nullptr;
+    float2 *vyff = nullptr;
+    CUtensorMap map;
+};
+
+bool oz_supported(const gpr_model *M) { return M->kp.kind == GPR_K_SE && M->m <= 1024; }
+
+gpr_status oz_prepare(gpr_model *M, cudaStream_t st)
+{
+    if (M->oz) return GPR_OK;
+    OzOperands *O = new OzOperands();
+    O->mpt = (M->mp + 63) / 64 * 64;
+    int64_t mpt = O->mpt, mb = (M->m + 31) / 32 * 32;
+    size_t n = (size_t)mpt * mpt;
+    cudaError_t e = cudaMalloc(&O->B, n * 2 * (size_t)O->S);
+    if (e == cudaSuccess) e = cudaMalloc(&O->colscale, sizeof(float) * mpt);
+    if (e == cudaSuccess) e = cudaMalloc(&O->vyff, sizeof(float2) * mpt);
+    if (e != cudaSuccess) {
+        cudaFree(O->B); cudaFree(O->colscale); cudaFree(O->vyff);
+        delete O;
+        return e == cudaErrorMemoryAllocation ? GPR_ERR_OOM : GPR_ERR_CUDA;
+    }
+    GPR_CUDA_TRY(cudaMemsetAsync(O->vyff, 0, sizeof(float2) * mpt, st));
+    k_oz_colscale<<<(unsigned)((mpt + 7) / 8), 256, 0, st>>>(M->Linv, mb, M->m, mpt, O->colscale);
+    note_launch();
+    k_oz_split_b<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(M->Linv, mb, M->m, mpt, O->S, O->colscale,
+                                                              (__nv_bfloat16 *)O->B);
+    note_launch();
+    k_vyff<<<(unsigned)((M->mp + 255) / 256), 256, 0, st>>>(M->vy, M->mp, O->vyff);
+    note_launch();
+    GPR_CUDA_TRY(cudaGetLastError());
+    auto enc = encoder();
+    if (!enc) { M->oz = O; return GPR_ERR_UNSUPPORTED; }
+    cuuint64_t gdim[3] = {(cuuint64_t)mpt, (cuuint64_t)mpt, (cuuint64_t)O->S};
+    cuuint64_t gstride[2] = {(cuuint64_t)mpt * 2, (cuuint64_t)mpt * mpt * 2};
+    cuuint32_t box[3] = {BKE, TN, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = enc(&O->map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, O->B, gdim, gstride, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    M->oz = O;
+    return r == CUDA_SUCCESS ? GPR_OK : GPR_ERR_UNSUPPORTED;
+}
+
+void oz_release(gpr_model *M)
+{
+    if (!M->oz) return;
+    cudaFree(M->oz->B); cudaFree(M->oz->colscale); cudaFree(M->oz->vyff);
+    delete M->oz;
+    M->oz = nullptr;
+}
+
+size_t oz_unit_table_elems(const gpr_model *M, const GridDev &g) { return table_elems(M, g); }
+
+gpr_status oz_unit_tables(const gpr_model *M, const GridDev &g, float2 *Tu, cudaStream_t st)
+{
+    int64_t total = (int64_t)table_elems(M, g);
+    k_unit_tables<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(M->X, M->m, M->mp, M->kp, g, Tu);
+    note_launch();
+    GPR_CUDA_TRY(cudaGetLastError());
+    return GPR_OK;
+}
+
+// Float-float W rows of the listed points (count x mp float2) on the tensor cores.
+gpr_status launch_oz_w(const gpr_model *M, const GridDev &g, const float2 *Tu, const int64_t *pts, int64_t pt_base,
+                       int64_t count, float2 *W, cudaStream_t st)
+{
+    if (count <= 0) return GPR_OK;
+    const OzOperands *O = M->oz;
+    if (!O) return GPR_ERR_ARG;
+    OzParams prm;
+    prm.Tu = Tu;
+    prm.off1 = (int64_t)g.n[0] * M->mp;
+    prm.off2 = prm.off1 + (int64_t)g.n[1] * M->mp;
+    prm.mp = M->mp;
+    prm.m = M->m;
+    prm.g = g;
+    prm.pts = pts;
+    prm.pt_base = pt_base;
+    prm.count = count;
+    prm.colscale = O->colscale;
+    prm.sf2 = (float)M->kp.sf2;
+    prm.W = W;
+    prm.status = gpr_status_word();
+    if (!prm.status) return GPR_ERR_CUDA;
+    constexpr int S = 7;
+    size_t smem = 2 * (size_t)(S * A_SLICE + S * B_SLICE) + 64 + 1024;
+    GPR_CUDA_TRY(cudaFuncSetAttribute(k_oz_w<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    dim3 grid((unsigned)((count + TM - 1) / TM), (unsigned)(M->mp / TN));
+    {
+        ProfScope ps("oz_w", st);
+        k_oz_w<S><<<grid, NTHR, smem, st>>>(O->map, prm);
+    }
+    note_launch();
+    GPR_CUDA_TRY(cudaGetLastError());
+    return GPR_OK;
+}
+
+gpr_status launch_stats_ff(const gpr_model *M, const GridDev &g, const int64_t *pts, int64_t count, const int32_t *slot,
+                           const float2 *W, double *out15, cudaStream_t st)
+{
+    if (count <= 0) return GPR_OK;
+    Prior13 pr;
+    for (int e = 0; e < 13; ++e) {
+        double r2 = 0.0;
+        for (int d = 0; d < 3; ++d) {
+            double t = kOff13[e][d] * g.h[d] / M->kp.ell[d];
+            r2 += t * t;
+        }
+        pr.k[e] = M->kp.sf2 * exp(-0.5 * r2);
+    }
+    {
+        ProfScope ps("stats_ff", st);
+        k_stats_ff<<<(unsigned)((count + 7) / 8), 256, 0, st>>>(g, pts, count, slot, W, M->mp, M->m, M->oz->vyff,
+                                                              M->kp.sf2, pr, out15);
+    }
+    note_launch();
+    GPR_CUDA_TRY(cudaGetLastError());
+    return GPR_OK;
+}
+
+__global__ void k_fill_slot_oz(const int64_t *idx, int64_t count, int64_t npts, int32_t *slot)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < count && idx[i] >= 0 && idx[i] < npts) slot[idx[i]] = (int32_t)i;
+}
+
+// Test hook (not in the public header): stats15 of listed points through the tensor-core
+// digit-split path, for parity tests against the FP64 path and the oracle.
+extern "C" gpr_status gpr_stats_points_split(gpr_model *M, const gpr_grid *grid, const int64_t *point_idx,
+                                             int64_t count, double *stats, void *stream)
+{
+    if (!M || !grid_valid(grid) || count <= 0 || !point_idx || !stats) return GPR_ERR_ARG;
+    if (!oz_supported(M)) return GPR_ERR_UNSUPPORTED;
+    cudaStream_t st = (cudaStream_t)stream;
+    GridDev g = make_grid(grid);
+    size_t te = table_elems(M, g);
+    size_t bytes = Carver::round(te * sizeof(float2)) + Carver::round((size_t)g.npts() * 4) +
+                   Carver::round((size_t)count * M->mp * 8) + 1024;
+    GPR_TRY(ws_reserve(M, 0, bytes, st));
+    Carver cv{(char *)M->ws[0]};
+    float2 *Tu = cv.take<float2>(te);
+    int32_t *slot = cv.take<int32_t>((size_t)g.npts());
+    float2 *W = cv.take<float2>((size_t)count * M->mp);
+    GPR_TRY(oz_prepare(M, st));
+    GPR_TRY(oz_unit_tables(M, g, Tu, st));
+    GPR_CUDA_TRY(cudaMemsetAsync(slot, 0xff, sizeof(int32_t) * (size_t)g.npts(), st));
+    k_fill_slot_oz<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(point_idx, count, g.npts(), slot);
+    note_launch();
+    GPR_TRY(launch_oz_w(M, g, Tu, point_idx, 0, count, W, st));
+    GPR_TRY(launch_stats_ff(M, g, point_idx, count, slot, W, stats, st));
+    return GPR_OK;
+}

@@ -350,6 +350,7 @@ extern "C" gpr_status gpr_model_destroy(gpr_model *M)
     for (int w = 0; w < 2; ++w)
         if (M->ws[w]) cudaFree(M->ws[w]);
     tc_release(M);
+    oz_release(M);
     delete M;
     return GPR_OK;
 }

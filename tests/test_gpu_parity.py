@@ -164,14 +164,17 @@ def test_lcp_dense_config1_sov_full(torch, g):
 
 
 def test_lcp_prepass_equals_all_fp64(torch, g):
-    """The FP32 pre-classification changes nothing: the field equals the all-FP64 one bit for bit."""
+    """The FP32 pre-classification changes nothing: with FP64 corner statistics the field equals the
+    all-FP64 one bit for bit; with the tensor-core digit split it agrees within 1e-6."""
     w = workloads.config1()
     M = model_of(w)
     th = w.isovalues[0]
     a, sa = _lcp_dense_gpu(g, torch, M, w.n, th, prec=g.GPR_P_FP64)
-    b, sb = _lcp_dense_gpu(g, torch, M, w.n, th, prec=g.GPR_P_FP32)
+    b, sb = _lcp_dense_gpu(g, torch, M, w.n, th, prec=g.GPR_P_FP32, exact=g.GPR_EXACT_FP64)
     assert np.array_equal(a, b)
     assert sb["recon_points"] <= w.n ** 3
+    c, sc = _lcp_dense_gpu(g, torch, M, w.n, th, prec=g.GPR_P_FP32)
+    assert np.abs(a - c).max() <= 1e-6
 
 
 def test_lcp_dense_config1_mc(torch, g):

@@ -84,7 +84,7 @@ def test_tc_prepass_lcp_equals_fp64(torch, g):
     out = {}
     for prec in (g.GPR_P_FP64, g.GPR_P_TF32X3, g.GPR_P_BF16X3):
         f = torch.zeros((w.n - 1) ** 3, dtype=torch.float32, device="cuda")
-        g.gpr_lcp_dense(M, g.make_grid(w.n), th, g.lcp_options(prec=prec), f)
+        g.gpr_lcp_dense(M, g.make_grid(w.n), th, g.lcp_options(prec=prec, exact=g.GPR_EXACT_FP64), f)
         g.gpr_sync()
         out[prec] = f.cpu().numpy()
     assert np.array_equal(out[g.GPR_P_FP64], out[g.GPR_P_TF32X3])
@@ -99,3 +99,48 @@ def test_tc_cov13_not_served(torch, g):
     with pytest.raises(g.GPRError) as e:
         g.gpr_reconstruct_dense(M, g.make_grid(5), g.GPR_P_TF32X3, t, t.clone(), c)
     assert e.value.status == g.GPR_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("case", ["config2", "small_m97"])
+def test_digit_split_stats_vs_fp64_and_oracle(torch, g, case):
+    """FP64-class statistics on the BF16 tensor cores (seven 6-bit digit slices, exact FP32
+    accumulation, float-float epilogue) against the FP64 CUDA-core path and the oracle."""
+    if case == "config2":
+        w = workloads.config2(); n = w.n
+    else:
+        w = workloads.small(97, 97, 9, ell=(0.15, 0.2, 0.25)); n = 11
+    M = model_of(w)
+    grid = g.make_grid(n)
+    rng = np.random.default_rng(4)
+    base = np.unique(rng.integers(0, n ** 3, 600))
+    # include full cells so neighbour covariances are exercised
+    pts = np.unique(np.concatenate([base, base + 1, base + n, base + n * n]))
+    pts = pts[pts < n ** 3]
+    t = torch.tensor(pts, dtype=torch.int64, device="cuda")
+    a = torch.zeros(len(pts), 15, dtype=torch.float64, device="cuda")
+    b = torch.zeros_like(a)
+    g.gpr_stats_points(M, grid, t, a)
+    g.gpr_stats_points_split(M, grid, t, b)
+    g.gpr_sync()
+    a = a.cpu().numpy(); b = b.cpu().numpy()
+    assert np.array_equal(np.isnan(a), np.isnan(b))
+    ok = ~np.isnan(a)
+    d = np.abs(a - b)[ok].max()
+    assert d <= 1e-8, d
+    ref = oracle.Model.from_workload(w).stats15(n)[pts]
+    assert np.abs(b[ok] - ref[ok]).max() <= 1e-8
+
+
+def test_digit_split_lcp_vs_fp64_config2(torch, g):
+    """LCP field of the m=500 field at its median isovalue: digit-split corner statistics vs FP64."""
+    w = workloads.config2()
+    M = model_of(w)
+    th = w.isovalues[1]
+    out = {}
+    for ex in (g.GPR_EXACT_AUTO, g.GPR_EXACT_FP64):
+        f = torch.zeros((w.n - 1) ** 3, dtype=torch.float32, device="cuda")
+        g.gpr_lcp_dense(M, g.make_grid(w.n), th, g.lcp_options(prec=g.GPR_P_TF32X3, exact=ex), f)
+        g.gpr_sync()
+        out[ex] = f.cpu().numpy().astype(np.float64)
+    d = np.abs(out[g.GPR_EXACT_AUTO] - out[g.GPR_EXACT_FP64])
+    assert d.max() <= 1e-6, d.max()
