@@ -353,16 +353,62 @@ __global__ void k_flag_large(GridDev g, int D, int l, const int64_t *nodes, int6
 }
 
 // Lattice points (3x3x3 per node; corners, edge/face midpoints, centre, x fastest).
-__global__ void k_lattice_points(GridDev g, int D, int l, const int64_t *nodes, const int64_t *pend, int64_t npend,
-                                 int64_t first, int64_t cnt, double *xyz)
+__global__ void k_lattice_points(GridDev g, int D, int l, const int64_t *nodes, const int64_t *pend,
+                                 const int64_t *ulist, int64_t first, int64_t cnt, double *xyz)
 {
     int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= cnt) return;
-    int64_t gi = first + e, q = gi / 27;
+    int64_t gi = first + e, q = ulist[gi / 27];
     int t = (int)(gi % 27);
     Geom G = node_geom(g, D, l, nodes[pend[q]]);
     int id[3] = {t % 3, (t / 3) % 3, t / 9};
     for (int d = 0; d < 3; ++d) xyz[3 * e + d] = G.blo[d] + 0.5 * (double)id[d] * (G.bhi[d] - G.blo[d]);
+}
+
+// A node is grid-aligned when its 3x3x3 lattice lies on grid points (even extent per axis).
+__device__ __forceinline__ bool lattice_aligned(const Geom &G)
+{
+    return ((G.p1[0] - G.p0[0]) % 2 == 0) && ((G.p1[1] - G.p0[1]) % 2 == 0) && ((G.p1[2] - G.p0[2]) % 2 == 0);
+}
+
+__device__ __forceinline__ int64_t lattice_point(const GridDev &g, const Geom &G, int t)
+{
+    int id[3] = {t % 3, (t / 3) % 3, t / 9};
+    int64_t q[3];
+    for (int d = 0; d < 3; ++d) q[d] = G.p0[d] + id[d] * ((G.p1[d] - G.p0[d]) / 2);
+    return q[0] + (int64_t)g.n[0] * (q[1] + (int64_t)g.n[1] * q[2]);
+}
+
+// Marks the lattice grid points of aligned pending large nodes that the table lacks; flags the
+// unaligned nodes (their lattice is evaluated point by point).
+__global__ void k_mark_lattice(GridDev g, int D, int l, const int64_t *nodes, const int64_t *pend, int64_t npend,
+                               const uint8_t *have, uint8_t *need, uint8_t *unaligned)
+{
+    int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= npend) return;
+    Geom G = node_geom(g, D, l, nodes[pend[q]]);
+    bool al = lattice_aligned(G);
+    unaligned[q] = al ? 0 : 1;
+    if (!al) return;
+    for (int t = 0; t < 27; ++t) {
+        int64_t p = lattice_point(g, G, t);
+        if (!have[p]) need[p] = 1;
+    }
+}
+
+// g = (theta - mu)/sigma at the 27 lattice points of aligned nodes, from the table.
+__global__ void k_lattice_from_table(GridDev g, int D, int l, const int64_t *nodes, const int64_t *pend,
+                                     int64_t npend, const uint8_t *unaligned, const float2 *mv, double theta,
+                                     double sf2, float4 *lat)
+{
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= npend * 27) return;
+    int64_t q = e / 27;
+    if (unaligned[q]) return;
+    Geom G = node_geom(g, D, l, nodes[pend[q]]);
+    float2 v = mv[lattice_point(g, G, (int)(e % 27))];
+    double var = fmax((double)v.y, 1e-12 * sf2);
+    lat[e] = make_float4((float)((theta - (double)v.x) / sqrt(var)), 0.f, 0.f, 0.f);
 }
 
 // Best lattice point per node and side (lowest g; first in x-fastest order on ties).
@@ -371,6 +417,37 @@ struct MinState {
     float g[2];
     float grad[2][3];
 };
+
+__global__ void k_scatter_lattice(const float4 *ev, const int64_t *ulist, int64_t first, int64_t cnt, float4 *lat)
+{
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= cnt) return;
+    int64_t gi = first + e;
+    lat[ulist[gi / 27] * 27 + gi % 27] = ev[e];
+}
+
+// Start points (best lattice point per side) as evaluation points, for their gradients.
+__global__ void k_start_points(const MinState *ms, int64_t npend, int64_t first, int64_t cnt, double *xyz)
+{
+    int64_t le = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (le >= cnt) return;
+    int64_t e = first + le, q = e / 2;
+    int side = (int)(e % 2);
+    for (int d = 0; d < 3; ++d) xyz[3 * le + d] = ms[q].x[side][d];
+}
+
+__global__ void k_start_grad(const float4 *ev, int64_t first, int64_t cnt, MinState *ms)
+{
+    int64_t le = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (le >= cnt) return;
+    int64_t e = first + le, q = e / 2;
+    int side = (int)(e % 2);
+    float sg = side == 0 ? 1.f : -1.f;
+    ms[q].g[side] = sg * ev[le].x;
+    ms[q].grad[side][0] = sg * ev[le].y;
+    ms[q].grad[side][1] = sg * ev[le].z;
+    ms[q].grad[side][2] = sg * ev[le].w;
+}
 
 __global__ void k_lattice_best(const float4 *ev, int64_t npend, MinState *ms)
 {
@@ -504,6 +581,8 @@ struct OctBuffers {
     float *W, *P;
     float4 *ev, *lat;
     float *part;
+    uint8_t *unal;
+    int64_t *ulist;
     uint8_t *cvalid;
     MinState *ms;
     unsigned long long *counters;  // [0] nnext, [1] nsub
@@ -560,7 +639,8 @@ gpr_status octree_lcp(gpr_model *M, const gpr_grid *grid, double theta, int D, c
                    Carver::round((size_t)kEvalChunk * 24) + 2 * Carver::round((size_t)kEvalChunk * M->mp * 4) +
                    Carver::round((size_t)kEvalChunk * 16) + Carver::round((size_t)kEvalChunk) +
                    Carver::round((size_t)nc * sizeof(MinState)) + Carver::round((size_t)max_large * 27 * 16) + 512 +
-                   csb + Carver::round(tc_partial_elems(GPR_P_BF16X3, M, n) * 4) + 8192;
+                   csb + Carver::round(tc_partial_elems(GPR_P_BF16X3, M, n) * 4) + Carver::round((size_t)max_large) +
+                   Carver::round((size_t)max_large * 8) + 8192;
     GPR_TRY(ws_reserve(M, 0, bytes, st));
     Carver cv{(char *)M->ws[0]};
     float *T32 = cv.take<float>(te);
@@ -594,6 +674,8 @@ gpr_status octree_lcp(gpr_model *M, const gpr_grid *grid, double theta, int D, c
     B.csb = csb;
     B.cscr = cv.take<char>(csb);
     B.part = cv.take<float>(tc_partial_elems(GPR_P_BF16X3, M, n));
+    B.unal = cv.take<uint8_t>((size_t)max_large);
+    B.ulist = cv.take<int64_t>((size_t)max_large);
     int32_t *slot = (int32_t *)B.tmp_mean;  // reused by the leaf phase (n int32 fits in n floats)
     int64_t *clist = B.pend;                 // reused by the leaf phase (nc int64)
 
@@ -642,18 +724,44 @@ gpr_status octree_lcp(gpr_model *M, const gpr_grid *grid, double theta, int D, c
             int64_t npend = 0;
             GPR_TRY(compact_flags(B.lflag, count, B.pend, nullptr, &npend, B.cscr, B.csb, st));
             if (npend > 0) {
-                for (int64_t first = 0; first < npend * 27; first += kEvalChunk) {
-                    int64_t cnt = npend * 27 - first < kEvalChunk ? npend * 27 - first : kEvalChunk;
-                    k_lattice_points<<<nb(cnt, 256), 256, 0, st>>>(g, D, l, nodes, B.pend, npend, first, cnt, B.xyz);
+                // lattice values: aligned nodes from the per-point table, unaligned ones evaluated
+                GPR_CUDA_TRY(cudaMemsetAsync(B.need, 0, (size_t)n, st));
+                k_mark_lattice<<<nb(npend, 128), 128, 0, st>>>(g, D, l, nodes, B.pend, npend, B.have, B.need, B.unal);
+                note_launch();
+                int64_t nneed = 0;
+                GPR_TRY(compact_flags(B.need, n, B.plist, nullptr, &nneed, B.cscr, B.csb, st));
+                if (nneed > 0) {
+                    gpr_precision pp = opts->prec == GPR_P_FP64 ? GPR_P_FP32 : opts->prec;
+                    GPR_TRY(fast_meanvar(M, g, pp, T32, Tff, T64, B.plist, 0, nneed, B.tmp_mean, B.tmp_var, B.part, st));
+                    k_scatter_mv<<<nb(nneed, 256), 256, 0, st>>>(B.plist, nneed, B.tmp_mean, B.tmp_var, B.mv, B.have);
+                    note_launch();
+                }
+                k_lattice_from_table<<<nb(npend * 27, 256), 256, 0, st>>>(g, D, l, nodes, B.pend, npend, B.unal, B.mv,
+                                                                          theta, M->kp.sf2, B.lat);
+                note_launch();
+                int64_t nun = 0;
+                GPR_TRY(compact_flags(B.unal, npend, B.ulist, nullptr, &nun, B.cscr, B.csb, st));
+                for (int64_t first = 0; first < nun * 27; first += kEvalChunk) {
+                    int64_t cnt = nun * 27 - first < kEvalChunk ? nun * 27 - first : kEvalChunk;
+                    k_lattice_points<<<nb(cnt, 256), 256, 0, st>>>(g, D, l, nodes, B.pend, B.ulist, first, cnt, B.xyz);
                     note_launch();
                     GPR_TRY(run_eval(M, E, B, cnt, theta, st));
-                    GPR_CUDA_TRY(cudaMemcpyAsync(B.lat + first, B.ev, sizeof(float4) * cnt, cudaMemcpyDeviceToDevice,
-                                                 st));
+                    k_scatter_lattice<<<nb(cnt, 256), 256, 0, st>>>(B.ev, B.ulist, first, cnt, B.lat);
+                    note_launch();
                 }
                 k_lattice_best<<<nb(npend, 128), 128, 0, st>>>(B.lat, npend, B.ms);
                 note_launch();
                 k_lattice_coords<<<nb(npend, 128), 128, 0, st>>>(g, D, l, nodes, B.pend, npend, B.ms);
                 note_launch();
+                // g and its gradient at the start point of each side
+                for (int64_t first = 0; first < 2 * npend; first += kEvalChunk) {
+                    int64_t cnt = 2 * npend - first < kEvalChunk ? 2 * npend - first : kEvalChunk;
+                    k_start_points<<<nb(cnt, 256), 256, 0, st>>>(B.ms, npend, first, cnt, B.xyz);
+                    note_launch();
+                    GPR_TRY(run_eval(M, E, B, cnt, theta, st));
+                    k_start_grad<<<nb(cnt, 256), 256, 0, st>>>(B.ev, first, cnt, B.ms);
+                    note_launch();
+                }
                 for (int t = 0; t < T; ++t) {
                     for (int64_t first = 0; first < 2 * npend; first += kEvalChunk) {
                         int64_t cnt = 2 * npend - first < kEvalChunk ? 2 * npend - first : kEvalChunk;

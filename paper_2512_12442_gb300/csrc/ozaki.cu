@@ -24,7 +24,7 @@
 
 namespace {
 
-constexpr int TM = 128, TN = 64, BKE = 32, NTHR = 256, BETA = 6;
+constexpr int TM = 128, TN = 64, BKE = 32, NTHR = 512, BETA = 6;
 constexpr uint32_t kSpin = 1u << 22;
 constexpr int A_SLICE = TM * 64;   // bytes of one A digit slice per K block
 constexpr int B_SLICE = TN * 64;   // bytes of one B digit slice per K block
@@ -157,19 +157,27 @@ __global__ void __launch_bounds__(NTHR, 1) k_oz_w(const __grid_constant__ CUtens
                     "l"((uint64_t)&mapB), "r"(kb * BKE), "r"(n0), "r"(t), "r"(full0 + 8 * s)
                     : "memory");
         }
-        // A digits: thread -> (row r, 16 consecutive k)
+        // A digits: thread -> (row r, 16-byte chunk c of 8 consecutive k); all 24 table loads
+        // are issued before the digit arithmetic
         {
-            const int r = tid >> 1, half = tid & 1;
-            float dig[S][16];
+            const int r = tid >> 2, c = tid & 3;
+            const int64_t j0 = (int64_t)kb * BKE + c * 8;
+            const bool rv = rvalid[r];
+            const float2 *px = prm.Tu + (int64_t)gx[r] * prm.mp, *py = prm.Tu + prm.off1 + (int64_t)gy[r] * prm.mp,
+                         *pz = prm.Tu + prm.off2 + (int64_t)gz[r] * prm.mp;
+            float2 tx[8], ty[8], tz[8];
 #pragma unroll
-            for (int e = 0; e < 16; ++e) {
-                const int64_t j = (int64_t)kb * BKE + half * 16 + e;
-                FF a = {0.f, 0.f};
-                if (rvalid[r] && j < m) {
-                    float2 x = prm.Tu[(int64_t)gx[r] * prm.mp + j], y = prm.Tu[prm.off1 + (int64_t)gy[r] * prm.mp + j],
-                           z = prm.Tu[prm.off2 + (int64_t)gz[r] * prm.mp + j];
-                    a = ff_mul(ff_mul(FF{x.x, x.y}, FF{y.x, y.y}), FF{z.x, z.y});
-                }
+            for (int e = 0; e < 8; ++e) {
+                const int64_t j = j0 + e < m ? j0 + e : 0;
+                tx[e] = px[j];
+                ty[e] = py[j];
+                tz[e] = pz[j];
+            }
+            float dig[S][8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                FF a = ff_mul(ff_mul(FF{tx[e].x, tx[e].y}, FF{ty[e].x, ty[e].y}), FF{tz[e].x, tz[e].y});
+                if (!rv || j0 + e >= m) a = FF{0.f, 0.f};
                 // signed 6-bit digits of a in [0,1]; the low part joins once the high part is consumed
                 float rr = a.h;
 #pragma unroll
@@ -180,21 +188,17 @@ __global__ void __launch_bounds__(NTHR, 1) k_oz_w(const __grid_constant__ CUtens
                     rr = fmaf(-i, ldexpf(1.0f, -BETA * (d + 1)), rr);
                 }
             }
+            const int off = r * 64 + ((c ^ ((r >> 1) & 3)) << 4);
 #pragma unroll
             for (int d = 0; d < S; ++d) {
+                uint32_t wd[4];
 #pragma unroll
-                for (int c = 0; c < 2; ++c) {
-                    uint32_t wd[4];
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        uint32_t lo = __bfloat16_as_ushort(__float2bfloat16_rn(dig[d][c * 8 + 2 * q]));
-                        uint32_t hi = __bfloat16_as_ushort(__float2bfloat16_rn(dig[d][c * 8 + 2 * q + 1]));
-                        wd[q] = lo | (hi << 16);
-                    }
-                    const int chunk = half * 2 + c;  // 16-byte chunk in the 64-byte row
-                    const int off = r * 64 + ((chunk ^ ((r >> 1) & 3)) << 4);
-                    *(uint4 *)(st + d * A_SLICE + off) = make_uint4(wd[0], wd[1], wd[2], wd[3]);
+                for (int q = 0; q < 4; ++q) {
+                    uint32_t lo = __bfloat16_as_ushort(__float2bfloat16_rn(dig[d][2 * q]));
+                    uint32_t hi = __bfloat16_as_ushort(__float2bfloat16_rn(dig[d][2 * q + 1]));
+                    wd[q] = lo | (hi << 16);
                 }
+                *(uint4 *)(st + d * A_SLICE + off) = make_uint4(wd[0], wd[1], wd[2], wd[3]);
             }
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -226,35 +230,32 @@ __global__ void __launch_bounds__(NTHR, 1) k_oz_w(const __grid_constant__ CUtens
     }
     if (!wait_bar(done, 0)) ok_all = false;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    // epilogue: warp -> lanes 32*(w%4), columns 32*(w/4) of every level accumulator
-    const int lq = warp & 3, half = warp >> 2;
-    FF acc[32];
+    // epilogue: warp -> lanes 32*(w%4), columns 16*(w/4) of every level accumulator
+    const int lq = warp & 3, quarter = warp >> 2;
+    FF acc[16];
 #pragma unroll
-    for (int c = 0; c < 32; ++c) acc[c] = FF{0.f, 0.f};
+    for (int c = 0; c < 16; ++c) acc[c] = FF{0.f, 0.f};
 #pragma unroll
     for (int lvl = S - 1; lvl >= 0; --lvl) {
-        uint32_t rr[32];
-        const uint32_t taddr = tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(lvl * TN + half * 32);
+        uint32_t rr[16];
+        const uint32_t taddr = tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(lvl * TN + quarter * 16);
         asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,"
-            "%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
             : "=r"(rr[0]), "=r"(rr[1]), "=r"(rr[2]), "=r"(rr[3]), "=r"(rr[4]), "=r"(rr[5]), "=r"(rr[6]), "=r"(rr[7]),
               "=r"(rr[8]), "=r"(rr[9]), "=r"(rr[10]), "=r"(rr[11]), "=r"(rr[12]), "=r"(rr[13]), "=r"(rr[14]),
-              "=r"(rr[15]), "=r"(rr[16]), "=r"(rr[17]), "=r"(rr[18]), "=r"(rr[19]), "=r"(rr[20]), "=r"(rr[21]),
-              "=r"(rr[22]), "=r"(rr[23]), "=r"(rr[24]), "=r"(rr[25]), "=r"(rr[26]), "=r"(rr[27]), "=r"(rr[28]),
-              "=r"(rr[29]), "=r"(rr[30]), "=r"(rr[31])
+              "=r"(rr[15])
             : "r"(taddr));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         const float wgt = ldexpf(1.0f, -BETA * (lvl + 2));
 #pragma unroll
-        for (int c = 0; c < 32; ++c) acc[c] = ff_add_f(acc[c], __uint_as_float(rr[c]) * wgt);
+        for (int c = 0; c < 16; ++c) acc[c] = ff_add_f(acc[c], __uint_as_float(rr[c]) * wgt);
     }
     const int64_t row = row0 + lq * 32 + lane;
     if (row < prm.count) {
-        float2 *out = prm.W + row * prm.mp + n0 + half * 32;
+        float2 *out = prm.W + row * prm.mp + n0 + quarter * 16;
 #pragma unroll
-        for (int c = 0; c < 32; ++c) {
-            const int64_t j = n0 + half * 32 + c;
+        for (int c = 0; c < 16; ++c) {
+            const int64_t j = n0 + quarter * 16 + c;
             float cs = (j < prm.mp) ? prm.colscale[j] : 0.f;
             FF v = {acc[c].h * cs, acc[c].l * cs};  // power-of-two scale: exact
             if (prm.sf2 != 1.0f) v = ff_mul(v, FF{prm.sf2, 0.f});

@@ -43,8 +43,9 @@ def _compare_level(om, n, D, l, th, nodes, dec, bnd, alpha=1e-3, sample=None, se
     return int(mism.sum()), len(idx)
 
 
-@pytest.mark.parametrize("case", ["small", "config1"])
-def test_octree_levels_match_oracle(torch, g, case):
+@pytest.mark.parametrize("case,prec", [("small", "fp32"), ("config1", "fp32"), ("small", "tf32x3"),
+                                       ("config1", "tf32x3")])
+def test_octree_levels_match_oracle(torch, g, case, prec):
     if case == "small":
         w = workloads.small(5, 60, 17, ell=(0.2, 0.2, 0.2))
     else:
@@ -53,9 +54,10 @@ def test_octree_levels_match_oracle(torch, g, case):
     om = oracle.Model.from_workload(w)
     n, D, th = w.n, w.max_depth, w.isovalues[0]
     grid = g.make_grid(n)
+    p = g.GPR_P_FP32 if prec == "fp32" else g.GPR_P_TF32X3
     total_mism = 0
     for l in range(D + 1):
-        nodes, dec, bnd = g.gpr_octree_trace(M, grid, th, D, g.lcp_options(), l)
+        nodes, dec, bnd = g.gpr_octree_trace(M, grid, th, D, g.lcp_options(prec=p), l)
         if len(nodes) == 0:
             break
         mm, cnt = _compare_level(om, n, D, l, th, nodes, dec, bnd)
@@ -105,7 +107,7 @@ def test_adaptive_config2_full_size_sampled_nodes(torch, g):
     th = w.isovalues[1]
     grid = g.make_grid(w.n)
     for l in (2, 4, 5, 6, 7):
-        nodes, dec, bnd = g.gpr_octree_trace(M, grid, th, w.max_depth, g.lcp_options(), l)
+        nodes, dec, bnd = g.gpr_octree_trace(M, grid, th, w.max_depth, g.lcp_options(prec=g.GPR_P_TF32X3), l)
         assert len(nodes) > 0
         mm, cnt = _compare_level(om, w.n, w.max_depth, l, th, nodes, dec, bnd, sample=150 if l >= 5 else None,
                                  seed=l)
