@@ -149,7 +149,7 @@ __global__ void k_adj_cell(GridDev g, const double *stats, const int32_t *slot, 
 #pragma unroll
     for (int i = 0; i < 7; ++i) Ds[i] = __shfl_sync(0xffffffffu, D, i);
     float bbar[2][8], Lbar[36];
-    double P[2] = {0.0, 0.0};
+    float P[2] = {0.f, 0.f};
 #pragma unroll
     for (int i = 0; i < 8; ++i) { bbar[0][i] = 0.f; bbar[1][i] = 0.f; }
 #pragma unroll

@@ -118,7 +118,16 @@ __global__ void k_cell_prep(GridDev g, const double *stats, const int32_t *slot,
                     r.b[a] = (float)(theta - mu[a]);
                     for (int b = 0; b <= a; ++b) r.L[tri(a, b)] = (float)Lm[a][b];
                 }
-                r.cell = cidx;
+                // Frechet bound: P(all < theta) <= min_c P(Y_c < theta) (and likewise above).  An
+                // orthant bounded below 1e-7 is taken as 0: the LCP moves by less than 1e-7.
+                double mlo = 1.0, mhi = 1.0;
+                for (int c = 0; c < 8; ++c) {
+                    double sd = sqrt(S[c][c]);
+                    mlo = fmin(mlo, normcdf((theta - mu[c]) / sd));
+                    mhi = fmin(mhi, normcdf((mu[c] - theta) / sd));
+                }
+                int64_t mask = (mlo < 1e-7 ? 1 : 0) | (mhi < 1e-7 ? 2 : 0);
+                r.cell = cidx | (mask << 56);
                 r.out = outi;
                 need = true;
             }
@@ -150,8 +159,8 @@ struct Lattice {
     uint32_t G[7];
 };
 
-__global__ void k_sov(const CellRec *recs, const unsigned long long *nrec, int N, uint64_t seed, Lattice lat,
-                      float *lcp)
+__global__ void __launch_bounds__(256, 3) k_sov(const CellRec *recs, const unsigned long long *nrec, int N,
+                                               uint64_t seed, Lattice lat, float *lcp)
 {
     int lane = threadIdx.x & 31;
     int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -164,12 +173,14 @@ __global__ void k_sov(const CellRec *recs, const unsigned long long *nrec, int N
         for (int t = 0; t < 36; ++t) L[t] = r.L[t];
 #pragma unroll
         for (int t = 0; t < 8; ++t) { b[t] = r.b[t]; inv[t] = 1.0f / L[tri(t, t)]; }
+        const uint64_t cellid = (uint64_t)r.cell & ((1ull << 56) - 1);
+        const int skip = (int)((uint64_t)r.cell >> 56);
         uint32_t D = 0;
-        if (lane < 7) D = (uint32_t)(splitmix64(seed, (uint64_t)r.cell * 8 + lane + 1) >> 32);
+        if (lane < 7) D = (uint32_t)(splitmix64(seed, cellid * 8 + lane + 1) >> 32);
         uint32_t Ds[7];
 #pragma unroll
         for (int i = 0; i < 7; ++i) Ds[i] = __shfl_sync(0xffffffffu, D, i);
-        double acc_lo = 0.0, acc_hi = 0.0;
+        float acc_lo = 0.f, acc_hi = 0.f;  // <= 50 samples per lane: FP32 sums are exact to ~1e-7
         for (int k = lane; k < N; k += 32) {
             float w[7];
 #pragma unroll
@@ -179,6 +190,7 @@ __global__ void k_sov(const CellRec *recs, const unsigned long long *nrec, int N
             }
 #pragma unroll
             for (int side = 0; side < 2; ++side) {
+                if (skip & (1 << side)) continue;
                 float sg = side == 0 ? 1.0f : -1.0f;
                 float z[7];
                 float f = 1.0f;
@@ -201,7 +213,7 @@ __global__ void k_sov(const CellRec *recs, const unsigned long long *nrec, int N
             acc_hi += __shfl_xor_sync(0xffffffffu, acc_hi, o);
         }
         if (lane == 0) {
-            double v = 1.0 - acc_lo / N - acc_hi / N;
+            double v = 1.0 - (double)acc_lo / N - (double)acc_hi / N;
             lcp[r.out] = (float)(v < 0.0 ? 0.0 : (v > 1.0 ? 1.0 : v));
         }
     }
@@ -234,7 +246,8 @@ __global__ void k_mc(const CellRec *recs, const unsigned long long *nrec, int N,
         for (int t = 0; t < 36; ++t) L[t] = r.L[t];
 #pragma unroll
         for (int t = 0; t < 8; ++t) b[t] = r.b[t];
-        uint32_t clo = (uint32_t)r.cell, chi = (uint32_t)((uint64_t)r.cell >> 32);
+        const uint64_t cellid = (uint64_t)r.cell & ((1ull << 56) - 1);
+        uint32_t clo = (uint32_t)cellid, chi = (uint32_t)(cellid >> 32);
         int crossed = 0;
         for (int k = lane; k < N; k += 32) {
             float z[8];

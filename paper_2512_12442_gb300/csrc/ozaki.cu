@@ -334,8 +334,23 @@ struct Prior13 {
     double k[13];
 };
 
-__global__ void k_stats_ff(GridDev g, const int64_t *pts, int64_t count, const int32_t *slot, const float2 *W,
-                           int64_t mp, int64_t m, const float2 *vyff, double sf2, Prior13 pr, double *out15)
+// Compensated dot product step (Ogita-Rump-Oishi Dot2 with float-float inputs): the product's
+// high part is added by an error-free TwoSum, every rounding error goes to one FP32 carry.
+__device__ __forceinline__ void dot2_step(float &sh, float &sl, float2 a, float2 b)
+{
+    float p = a.x * b.x;
+    float e = fmaf(a.x, b.x, -p);
+    e = fmaf(a.x, b.y, e);
+    e = fmaf(a.y, b.x, e);
+    float s = sh + p;
+    float bv = s - sh;
+    sl += ((sh - (s - bv)) + (p - bv)) + e;
+    sh = s;
+}
+
+__global__ void __launch_bounds__(256, 3) k_stats_ff(GridDev g, const int64_t *pts, int64_t count,
+                                                     const int32_t *slot, const float2 *W, int64_t mp, int64_t m,
+                                                     const float2 *vyff, double sf2, Prior13 pr, double *out15)
 {
     int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     int64_t pos = blockIdx.x * (int64_t)(blockDim.x / 32) + warp;
@@ -343,46 +358,46 @@ __global__ void k_stats_ff(GridDev g, const int64_t *pts, int64_t count, const i
     int64_t p = pts[pos];
     int64_t nx = g.n[0], ny = g.n[1], nz = g.n[2];
     int ix = (int)(p % nx), iy = (int)((p / nx) % ny), iz = (int)(p / (nx * ny));
-    int64_t self = slot[p];
-    int64_t nb[13];
+    const int32_t self = slot[p];
+    int32_t nb[13];
 #pragma unroll
     for (int e = 0; e < 13; ++e) {
         int a = ix + c_off[e][0], b = iy + c_off[e][1], c = iz + c_off[e][2];
-        int64_t r = -1;
+        int32_t r = -1;
         if (a >= 0 && b >= 0 && c >= 0 && a < nx && b < ny && c < nz) r = slot[a + nx * (b + ny * (int64_t)c)];
         nb[e] = r;
     }
-    FF acc[15];
+    float sh[15], sl[15];
 #pragma unroll
-    for (int s = 0; s < 15; ++s) acc[s] = FF{0.f, 0.f};
-    const float2 *wp = W + self * mp;
+    for (int q = 0; q < 15; ++q) { sh[q] = 0.f; sl[q] = 0.f; }
+    const float2 *wp = W + (int64_t)self * mp;
     for (int64_t j = lane; j < m; j += 32) {
-        float2 w = wp[j];
-        FF a = {w.x, w.y};
-        float2 v = vyff[j];
-        acc[0] = ff_add(acc[0], ff_mul(a, FF{v.x, v.y}));
-        acc[1] = ff_add(acc[1], ff_mul(a, a));
+        const float2 a = wp[j];
+        float2 q[13];
 #pragma unroll
-        for (int e = 0; e < 13; ++e)
-            if (nb[e] >= 0) {
-                float2 q = W[nb[e] * mp + j];
-                acc[2 + e] = ff_add(acc[2 + e], ff_mul(a, FF{q.x, q.y}));
-            }
+        for (int e = 0; e < 13; ++e) q[e] = nb[e] >= 0 ? W[(int64_t)nb[e] * mp + j] : make_float2(0.f, 0.f);
+        dot2_step(sh[0], sl[0], a, vyff[j]);
+        dot2_step(sh[1], sl[1], a, a);
+#pragma unroll
+        for (int e = 0; e < 13; ++e) dot2_step(sh[2 + e], sl[2 + e], a, q[e]);
     }
 #pragma unroll
-    for (int s = 0; s < 15; ++s)
+    for (int q = 0; q < 15; ++q) {
+        // combine lanes in float-float (FP64 arithmetic runs at 1/64 rate on this part)
+        FF v = {sh[q], sl[q]};
+        v = ff_add(FF{v.h, 0.f}, FF{v.l, 0.f});
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            FF t = {__shfl_xor_sync(0xffffffffu, acc[s].h, o), __shfl_xor_sync(0xffffffffu, acc[s].l, o)};
-            acc[s] = ff_add(acc[s], t);
+            FF t = {__shfl_xor_sync(0xffffffffu, v.h, o), __shfl_xor_sync(0xffffffffu, v.l, o)};
+            v = ff_add(v, t);
         }
-    if (lane == 0) {
-        double *o = out15 + pos * 15;
-        o[0] = (double)acc[0].h + (double)acc[0].l;
-        o[1] = sf2 - ((double)acc[1].h + (double)acc[1].l);
-#pragma unroll
-        for (int e = 0; e < 13; ++e)
-            o[2 + e] = nb[e] >= 0 ? pr.k[e] - ((double)acc[2 + e].h + (double)acc[2 + e].l) : (double)NAN;
+        if (lane == 0) {
+            double dv = (double)v.h + (double)v.l;
+            double *o = out15 + pos * 15;
+            if (q == 0) o[0] = dv;
+            else if (q == 1) o[1] = sf2 - dv;
+            else o[q] = nb[q - 2] >= 0 ? pr.k[q - 2] - dv : (double)NAN;
+        }
     }
 }
 
