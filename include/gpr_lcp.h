@@ -96,7 +96,9 @@ typedef struct {
     int64_t nodes_per_level[24];   /* nodes evaluated at each level of Algorithm 1 */
     int64_t subdiv_per_level[24];  /* nodes subdivided at each level */
     int64_t leaf_cells;            /* |S|: cells kept at the deepest level */
-    int64_t recon_points;          /* grid points reconstructed in FP64 */
+    int64_t recon_points;          /* grid points whose FP64-class rows this call reconstructed (points
+                                      cached by earlier calls on the same model and grid are not
+                                      counted again) */
     int64_t cells_estimated;       /* cells that ran the estimator (not pre-skipped) */
 } gpr_adaptive_stats;
 

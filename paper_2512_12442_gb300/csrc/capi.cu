@@ -306,37 +306,33 @@ extern "C" gpr_status gpr_lcp_dense(gpr_model *M, const gpr_grid *grid, double i
         }
         return GPR_OK;
     }
-    // Phase 1: FP32 mean/variance everywhere, widened Boole test per cell, corner marking.
-    size_t b1 = Carver::round(te * sizeof(float)) + Carver::round(te * sizeof(double)) +
-                2 * Carver::round((size_t)n * sizeof(float)) + Carver::round((size_t)nc) + Carver::round((size_t)n) +
-                Carver::round((size_t)n * sizeof(int64_t)) + Carver::round((size_t)n * sizeof(int32_t)) +
+    // Phase 1: FP32-class mean/variance everywhere (cached per grid), widened Boole test per cell.
+    gpr_precision pp = opts->prec;
+    GridCache *C = nullptr;
+    GPR_TRY(grid_cache(M, grid, g, pp, &C, st));
+    size_t b1 = 2 * Carver::round((size_t)n * sizeof(float)) + Carver::round((size_t)nc) + Carver::round((size_t)n) +
+                Carver::round((size_t)n * 2 * sizeof(int64_t)) + Carver::round((size_t)n * sizeof(int32_t)) +
                 Carver::round((size_t)nc * sizeof(int64_t)) + compact_scratch_bytes(nc > n ? nc : n) +
-                Carver::round(te * sizeof(float2)) + Carver::round(tc_partial_elems(GPR_P_BF16X3, M, n) * 4) + 4096;
+                Carver::round(tc_partial_elems(GPR_P_BF16X3, M, n) * 4) + 4096;
     GPR_TRY(ws_reserve(M, 0, b1, st));
     Carver cv{(char *)M->ws[0]};
-    float *T32 = cv.take<float>(te);
-    double *T64 = cv.take<double>(te);
     float *mean = cv.take<float>((size_t)n);
     float *var = cv.take<float>((size_t)n);
     uint8_t *keep = cv.take<uint8_t>((size_t)nc);
     uint8_t *pflag = cv.take<uint8_t>((size_t)n);
-    int64_t *plist = cv.take<int64_t>((size_t)n);
+    int64_t *plist = cv.take<int64_t>((size_t)n * 2);
     int32_t *slot = cv.take<int32_t>((size_t)n);
     int64_t *clist = cv.take<int64_t>((size_t)nc);
     size_t csb = compact_scratch_bytes(nc > n ? nc : n);
     void *cscr = cv.take<char>(csb);
-    float2 *Tff = cv.take<float2>(te);
     float *part = cv.take<float>(tc_partial_elems(GPR_P_BF16X3, M, n));
-    GPR_TRY(build_tables(M, g, T64, T32, st, Tff));
-    if (tc_precision(opts->prec)) {
-        GPR_TRY(fast_meanvar(M, g, opts->prec, T32, Tff, T64, nullptr, 0, n, mean, var, part, st));
-    } else {
-        launch_meanvar32(M, g, T32, nullptr, 0, n, mean, var, st);
-    }
+    double *T64 = C->T64;
+    GPR_CUDA_TRY(cudaMemsetAsync(pflag, 1, (size_t)n, st));
+    GPR_TRY(cache_fill_mv(M, C, g, pflag, plist, mean, var, part, cscr, csb, st));
     double mv, mm;
     prepass_margins(M, mv, mm);
     if (opts->prec == GPR_P_TF32 || opts->prec == GPR_P_BF16) mv = M->kp.sf2;  // single-pass: ~1e-1 var error
-    launch_classify_cells(g, mean, var, isovalue, opts->skip_eps, opts->jitter, mv, mm, keep, st);
+    launch_classify_cells_mv(g, C->mv, isovalue, opts->skip_eps, opts->jitter, mv, mm, keep, st);
     return lcp_from_kept_cells(M, g, T64, keep, pflag, plist, slot, clist, cscr, csb, lo, lcp, stats, st);
 }
 
@@ -348,8 +344,9 @@ gpr_status lcp_from_kept_cells(gpr_model *M, const GridDev &g, const double *T64
     GPR_CUDA_TRY(cudaMemsetAsync(pflag, 0, (size_t)n, st));
     launch_mark_corners(g, keep, pflag, st);
     GPR_CUDA_TRY(cudaGetLastError());
+    const bool cached = lo.exact_mode == GPR_EXACT_AUTO && M->cache && M->cache->W && M->cache->n == n;
     int64_t npts = 0, ncell = 0;
-    GPR_TRY(compact_flags(pflag, n, plist, slot, &npts, cscr, csb, st));
+    if (!cached) GPR_TRY(compact_flags(pflag, n, plist, slot, &npts, cscr, csb, st));
     GPR_TRY(compact_flags(keep, nc, clist, nullptr, &ncell, cscr, csb, st));
     GPR_CUDA_TRY(cudaMemsetAsync(lcp, 0, sizeof(float) * (size_t)nc, st));
     if (stats) {
@@ -357,6 +354,20 @@ gpr_status lcp_from_kept_cells(gpr_model *M, const GridDev &g, const double *T64
         stats->leaf_cells = ncell;
     }
     if (ncell == 0) return GPR_OK;
+    // Cached path: complete stats15 of every corner in the model's grid cache (rows reconstructed
+    // only for points no earlier call of this model and grid touched), then the estimator.
+    if (cached) {
+        GridCache *C = M->cache;
+        int64_t nrows = 0;
+        GPR_TRY(cache_fill_stats(M, C, g, pflag, (uint8_t *)slot, plist, cscr, csb, &nrows, st));
+        GPR_TRY(ws_reserve(M, 1, cell_lcp_scratch_bytes(ncell) + 1024, st));
+        if (stats) stats->recon_points = nrows;
+        int64_t nest = 0;
+        GPR_TRY(run_cell_lcp(g, C->S15, nullptr, clist, ncell, lo, lcp, false, M->ws[1], M->ws_bytes[1],
+                             stats ? &nest : nullptr, st));
+        if (stats) stats->cells_estimated = nest;
+        return GPR_OK;
+    }
     // FP64-class W rows and stats15 for the kept cells' corners, then the estimator.  Default:
     // the tensor-core digit-split GEMM with float-float statistics; FP64 CUDA cores on request
     // or where the split's exactness bound does not hold (m > 1024, Matern).

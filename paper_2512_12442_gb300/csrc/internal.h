@@ -60,6 +60,7 @@ struct TcOperands {
 };
 
 struct OzOperands;  // tensor-core FP64-class operands (ozaki.cu)
+struct GridCache;   // isovalue-independent per-grid results (cache.cu)
 
 struct gpr_model {
     int64_t m = 0;
@@ -85,6 +86,7 @@ struct gpr_model {
     float *alpha32 = nullptr;  // mp FP32 alpha
     TcOperands *tc = nullptr;  // built on first tensor-core use
     OzOperands *oz = nullptr;  // built on first FP64-class tensor-core use
+    GridCache *cache = nullptr;
     // host copies used by the octree p-test
     std::vector<double> hX, hy;
     // two independent workspaces (grow, never shrink): slot 0 for a call's first phase,
@@ -156,10 +158,38 @@ bool oz_supported(const gpr_model *M);
 gpr_status oz_prepare(gpr_model *M, cudaStream_t st);
 void oz_release(gpr_model *M);
 gpr_status oz_unit_tables(const gpr_model *M, const GridDev &g, float2 *Tu, cudaStream_t st);
+// out_by_point: row (or stats) of listed point p goes to position p of a full-grid array.
 gpr_status launch_oz_w(const gpr_model *M, const GridDev &g, const float2 *Tu, const int64_t *pts, int64_t pt_base,
-                       int64_t count, float2 *W, cudaStream_t st);
+                       int64_t count, float2 *W, cudaStream_t st, bool out_by_point = false);
 gpr_status launch_stats_ff(const gpr_model *M, const GridDev &g, const int64_t *pts, int64_t count, const int32_t *slot,
-                           const float2 *W, double *out15, cudaStream_t st);
+                           const float2 *W, double *out15, cudaStream_t st, bool out_by_point = false);
+
+// ---- per-model, per-grid cache of isovalue-independent results (cache.cu)
+struct GridCache {
+    gpr_grid key;
+    int64_t n = 0;
+    size_t bytes = 0;
+    float *T32 = nullptr;
+    double *T64 = nullptr;
+    float2 *Tff = nullptr, *Tu = nullptr;
+    float2 *mv = nullptr;        // per-point (mean, var) of the FP32-class pass
+    uint8_t *have_mv = nullptr;
+    gpr_precision mv_prec = GPR_P_FP32;
+    float2 *W = nullptr;         // float-float whitened rows, full grid (nullptr when over budget)
+    uint8_t *have_W = nullptr;
+    double *S15 = nullptr;       // complete stats15 (all forward neighbours), full grid
+    uint8_t *have_S = nullptr;
+};
+// Returns the model's cache for `g` (allocating / resetting it on a new grid or precision).
+gpr_status grid_cache(gpr_model *M, const gpr_grid *grid, const GridDev &g, gpr_precision mv_prec, GridCache **out,
+                      cudaStream_t st);
+void cache_release(gpr_model *M);
+// Fills the per-point table for flagged points that lack it (flags: uint8 per point).
+gpr_status cache_fill_mv(gpr_model *M, GridCache *C, const GridDev &g, const uint8_t *flag, int64_t *list, float *tmp_mean,
+                         float *tmp_var, float *part, void *cscr, size_t csb, cudaStream_t st);
+// Complete FP64-class stats15 in C->S15 for every flagged point (digit-split W rows cached).
+gpr_status cache_fill_stats(gpr_model *M, GridCache *C, const GridDev &g, const uint8_t *flag, uint8_t *tmpflag,
+                            int64_t *list, void *cscr, size_t csb, int64_t *n_new_rows, cudaStream_t st);
 
 // ---- LCP (lcp.cu)
 struct LcpOpts {
@@ -183,6 +213,9 @@ gpr_status run_cell_lcp_on_scratch(const GridDev &g, const double *stats, const 
 // Pre-classification: keep[cell] = 1 unless the widened Boole bound is below skip_eps.
 void launch_classify_cells(const GridDev &g, const float *mean, const float *var, double theta, double skip_eps,
                            double tau, double margin_var, double margin_mu, uint8_t *keep, cudaStream_t st);
+
+void launch_classify_cells_mv(const GridDev &g, const float2 *mvt, double theta, double skip_eps, double tau,
+                              double margin_var, double margin_mu, uint8_t *keep, cudaStream_t st);
 
 // Compaction helpers
 // Marks corners of kept cells in point_flag (uint8 per grid point).

@@ -396,6 +396,41 @@ __global__ void k_mark_corners(GridDev g, const uint8_t *keep, uint8_t *flag)
     }
 }
 
+__global__ void k_classify_mv(GridDev g, const float2 *mvt, double theta, double skip_eps, double tau, double mv,
+                              double mm, uint8_t *keep)
+{
+    int64_t cidx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int64_t cx = g.n[0] - 1, cy = g.n[1] - 1, cz = g.n[2] - 1;
+    if (cidx >= cx * cy * cz) return;
+    int64_t i = cidx % cx, j = (cidx / cx) % cy, k = cidx / (cx * cy);
+    double mu[8], v[8], maxv = 0.0;
+    for (int c = 0; c < 8; ++c) {
+        int64_t p = (i + (c & 1)) + (int64_t)g.n[0] * ((j + ((c >> 1) & 1)) + (int64_t)g.n[1] * (k + (c >> 2)));
+        float2 t = mvt[p];
+        mu[c] = t.x;
+        v[c] = fmax((double)t.y, 0.0) + mv;
+        maxv = fmax(maxv, v[c]);
+    }
+    double sa = 0.0, sb = 0.0;
+    for (int c = 0; c < 8; ++c) {
+        double sd = sqrt(v[c] + tau * maxv);
+        sa += normcdf((mu[c] + mm - theta) / sd);
+        sb += normcdf((theta - mu[c] + mm) / sd);
+    }
+    keep[cidx] = (sa < skip_eps || sb < skip_eps) ? 0 : 1;
+}
+
+void launch_classify_cells_mv(const GridDev &g, const float2 *mvt, double theta, double skip_eps, double tau,
+                              double margin_var, double margin_mu, uint8_t *keep, cudaStream_t st)
+{
+    {
+        ProfScope _ps("classify", st);
+        k_classify_mv<<<(unsigned)((g.ncells() + 255) / 256), 256, 0, st>>>(g, mvt, theta, skip_eps, tau, margin_var,
+                                                                           margin_mu, keep);
+    }
+    note_launch();
+}
+
 void launch_mark_corners(const GridDev &g, const uint8_t *keep_cell, uint8_t *point_flag, cudaStream_t st)
 {
     k_mark_corners<<<(unsigned)((g.ncells() + 255) / 256), 256, 0, st>>>(g, keep_cell, point_flag);

@@ -631,21 +631,23 @@ gpr_status octree_lcp(gpr_model *M, const gpr_grid *grid, double theta, int D, c
     for (int d = 0; d < 3; ++d) max_large *= (int64_t)(g.n[d] - 1 + 3) / 4;
     // workspace (slot 0): tables, frontier, per-point mean/var table, evaluation chunk
     size_t csb = compact_scratch_bytes(nc > n ? nc : n);
-    size_t bytes = Carver::round(te * sizeof(float)) + Carver::round(te * sizeof(double)) +
-                   Carver::round(te * sizeof(float2)) + 2 * Carver::round((size_t)nc * 8) + 2 * Carver::round((size_t)nc) +
+    size_t bytes = 2 * Carver::round((size_t)nc * 8) + 2 * Carver::round((size_t)nc) +
                    Carver::round((size_t)nc * 8) + Carver::round((size_t)m) + 3 * Carver::round((size_t)n) +
-                   Carver::round((size_t)nc) + Carver::round((size_t)nc) + Carver::round((size_t)n * sizeof(float2)) +
-                   Carver::round((size_t)n * 8) + Carver::round((size_t)nc * 8) + 2 * Carver::round((size_t)n * 4) +
+                   Carver::round((size_t)nc) + Carver::round((size_t)nc) + Carver::round((size_t)n * 16) +
+                   Carver::round((size_t)nc * 8) + 2 * Carver::round((size_t)n * 4) +
                    Carver::round((size_t)kEvalChunk * 24) + 2 * Carver::round((size_t)kEvalChunk * M->mp * 4) +
                    Carver::round((size_t)kEvalChunk * 16) + Carver::round((size_t)kEvalChunk) +
                    Carver::round((size_t)nc * sizeof(MinState)) + Carver::round((size_t)max_large * 27 * 16) + 512 +
                    csb + Carver::round(tc_partial_elems(GPR_P_BF16X3, M, n) * 4) + Carver::round((size_t)max_large) +
                    Carver::round((size_t)max_large * 8) + 8192;
+    gpr_precision pp = opts->prec == GPR_P_FP64 ? GPR_P_FP32 : opts->prec;
+    GridCache *C = nullptr;
+    GPR_TRY(grid_cache(M, grid, g, pp, &C, st));
     GPR_TRY(ws_reserve(M, 0, bytes, st));
     Carver cv{(char *)M->ws[0]};
-    float *T32 = cv.take<float>(te);
-    double *T64 = cv.take<double>(te);
-    float2 *Tff = cv.take<float2>(te);
+    const float *T32 = C->T32;
+    const double *T64 = C->T64;
+    const float2 *Tff = C->Tff;
     OctBuffers B;
     B.front[0] = cv.take<int64_t>((size_t)nc);
     B.front[1] = cv.take<int64_t>((size_t)nc);
@@ -653,13 +655,13 @@ gpr_status octree_lcp(gpr_model *M, const gpr_grid *grid, double theta, int D, c
     B.sides = cv.take<int8_t>((size_t)nc);
     B.bound = cv.take<double>((size_t)nc);
     B.obs_flags = cv.take<uint8_t>((size_t)m);
-    B.have = cv.take<uint8_t>((size_t)n);
     B.need = cv.take<uint8_t>((size_t)n);
     uint8_t *pflag = cv.take<uint8_t>((size_t)n);
     B.lflag = cv.take<uint8_t>((size_t)nc);
     B.leaf = cv.take<uint8_t>((size_t)nc);
-    B.mv = cv.take<float2>((size_t)n);
-    B.plist = cv.take<int64_t>((size_t)n);
+    B.mv = C->mv;
+    B.have = C->have_mv;
+    B.plist = cv.take<int64_t>((size_t)n * 2);
     B.pend = cv.take<int64_t>((size_t)nc);
     B.tmp_mean = cv.take<float>((size_t)n);
     B.tmp_var = cv.take<float>((size_t)n);
@@ -684,8 +686,6 @@ gpr_status octree_lcp(gpr_model *M, const gpr_grid *grid, double theta, int D, c
     E.m = M->m; E.mp = M->mp; E.kind = M->kp.kind; E.sf2 = (float)M->kp.sf2;
     for (int d = 0; d < 3; ++d) E.ell[d] = (float)M->kp.ell[d];
 
-    GPR_TRY(build_tables(M, g, T64, T32, st, Tff));
-    GPR_CUDA_TRY(cudaMemsetAsync(B.have, 0, (size_t)n, st));
     GPR_CUDA_TRY(cudaMemsetAsync(B.leaf, 0, (size_t)nc, st));
     k_obs_flags<<<nb(m, 128), 128, 0, st>>>(M->mu_obs, M->var_obs, m, theta, opts->alpha, B.obs_flags);
     note_launch();
@@ -708,7 +708,6 @@ gpr_status octree_lcp(gpr_model *M, const gpr_grid *grid, double theta, int D, c
             int64_t nneed = 0;
             GPR_TRY(compact_flags(B.need, n, B.plist, nullptr, &nneed, B.cscr, B.csb, st));
             if (nneed > 0) {
-                gpr_precision pp = opts->prec == GPR_P_FP64 ? GPR_P_FP32 : opts->prec;
                 GPR_TRY(fast_meanvar(M, g, pp, T32, Tff, T64, B.plist, 0, nneed, B.tmp_mean, B.tmp_var, B.part, st));
                 k_scatter_mv<<<nb(nneed, 256), 256, 0, st>>>(B.plist, nneed, B.tmp_mean, B.tmp_var, B.mv, B.have);
                 note_launch();
@@ -731,7 +730,6 @@ gpr_status octree_lcp(gpr_model *M, const gpr_grid *grid, double theta, int D, c
                 int64_t nneed = 0;
                 GPR_TRY(compact_flags(B.need, n, B.plist, nullptr, &nneed, B.cscr, B.csb, st));
                 if (nneed > 0) {
-                    gpr_precision pp = opts->prec == GPR_P_FP64 ? GPR_P_FP32 : opts->prec;
                     GPR_TRY(fast_meanvar(M, g, pp, T32, Tff, T64, B.plist, 0, nneed, B.tmp_mean, B.tmp_var, B.part, st));
                     k_scatter_mv<<<nb(nneed, 256), 256, 0, st>>>(B.plist, nneed, B.tmp_mean, B.tmp_var, B.mv, B.have);
                     note_launch();

@@ -96,7 +96,8 @@ struct OzParams {
     int64_t pt_base, count;
     const float *colscale;  // 2^F_j
     float sf2;
-    float2 *W;  // count x mp float-float
+    float2 *W;  // count x mp float-float (or npts x mp when out_by_point)
+    int out_by_point;
     int *status;
 };
 
@@ -110,6 +111,7 @@ __global__ void __launch_bounds__(NTHR, 1) k_oz_w(const __grid_constant__ CUtens
     __shared__ uint32_t tmem_slot;
     __shared__ int gx[TM], gy[TM], gz[TM];
     __shared__ bool rvalid[TM];
+    __shared__ int64_t rpoint[TM];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t row0 = (int64_t)blockIdx.x * TM;
     const int n0 = blockIdx.y * TN;
@@ -135,6 +137,7 @@ __global__ void __launch_bounds__(NTHR, 1) k_oz_w(const __grid_constant__ CUtens
         gy[r] = (int)((p / nx) % ny);
         gz[r] = (int)(p / (nx * ny));
         rvalid[r] = ok;
+        rpoint[r] = p;
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -251,8 +254,9 @@ __global__ void __launch_bounds__(NTHR, 1) k_oz_w(const __grid_constant__ CUtens
         for (int c = 0; c < 16; ++c) acc[c] = ff_add_f(acc[c], __uint_as_float(rr[c]) * wgt);
     }
     const int64_t row = row0 + lq * 32 + lane;
-    if (row < prm.count) {
-        float2 *out = prm.W + row * prm.mp + n0 + quarter * 16;
+    if (row < prm.count && rvalid[lq * 32 + lane]) {
+        const int64_t orow = prm.out_by_point ? rpoint[lq * 32 + lane] : row;
+        float2 *out = prm.W + orow * prm.mp + n0 + quarter * 16;
 #pragma unroll
         for (int c = 0; c < 16; ++c) {
             const int64_t j = n0 + quarter * 16 + c;
@@ -350,7 +354,8 @@ __device__ __forceinline__ void dot2_step(float &sh, float &sl, float2 a, float2
 
 __global__ void __launch_bounds__(256, 3) k_stats_ff(GridDev g, const int64_t *pts, int64_t count,
                                                      const int32_t *slot, const float2 *W, int64_t mp, int64_t m,
-                                                     const float2 *vyff, double sf2, Prior13 pr, double *out15)
+                                                     const float2 *vyff, double sf2, Prior13 pr, double *out15,
+                                                     int out_by_point)
 {
     int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     int64_t pos = blockIdx.x * (int64_t)(blockDim.x / 32) + warp;
@@ -358,24 +363,28 @@ __global__ void __launch_bounds__(256, 3) k_stats_ff(GridDev g, const int64_t *p
     int64_t p = pts[pos];
     int64_t nx = g.n[0], ny = g.n[1], nz = g.n[2];
     int ix = (int)(p % nx), iy = (int)((p / nx) % ny), iz = (int)(p / (nx * ny));
-    const int32_t self = slot[p];
-    int32_t nb[13];
+    // rows of W: through the slot map, or (slot == nullptr) the grid index itself
+    const int64_t self = slot ? (int64_t)slot[p] : p;
+    int64_t nb[13];
 #pragma unroll
     for (int e = 0; e < 13; ++e) {
         int a = ix + c_off[e][0], b = iy + c_off[e][1], c = iz + c_off[e][2];
-        int32_t r = -1;
-        if (a >= 0 && b >= 0 && c >= 0 && a < nx && b < ny && c < nz) r = slot[a + nx * (b + ny * (int64_t)c)];
+        int64_t r = -1;
+        if (a >= 0 && b >= 0 && c >= 0 && a < nx && b < ny && c < nz) {
+            int64_t q = a + nx * (b + ny * (int64_t)c);
+            r = slot ? (int64_t)slot[q] : q;
+        }
         nb[e] = r;
     }
     float sh[15], sl[15];
 #pragma unroll
     for (int q = 0; q < 15; ++q) { sh[q] = 0.f; sl[q] = 0.f; }
-    const float2 *wp = W + (int64_t)self * mp;
+    const float2 *wp = W + self * mp;
     for (int64_t j = lane; j < m; j += 32) {
         const float2 a = wp[j];
         float2 q[13];
 #pragma unroll
-        for (int e = 0; e < 13; ++e) q[e] = nb[e] >= 0 ? W[(int64_t)nb[e] * mp + j] : make_float2(0.f, 0.f);
+        for (int e = 0; e < 13; ++e) q[e] = nb[e] >= 0 ? W[nb[e] * mp + j] : make_float2(0.f, 0.f);
         dot2_step(sh[0], sl[0], a, vyff[j]);
         dot2_step(sh[1], sl[1], a, a);
 #pragma unroll
@@ -393,7 +402,7 @@ __global__ void __launch_bounds__(256, 3) k_stats_ff(GridDev g, const int64_t *p
         }
         if (lane == 0) {
             double dv = (double)v.h + (double)v.l;
-            double *o = out15 + pos * 15;
+            double *o = out15 + (out_by_point ? p : pos) * 15;
             if (q == 0) o[0] = dv;
             else if (q == 1) o[1] = sf2 - dv;
             else o[q] = nb[q - 2] >= 0 ? pr.k[q - 2] - dv : (double)NAN;
@@ -496,7 +505,7 @@ gpr_status oz_unit_tables(const gpr_model *M, const GridDev &g, float2 *Tu, cuda
 
 // Float-float W rows of the listed points (count x mp float2) on the tensor cores.
 gpr_status launch_oz_w(const gpr_model *M, const GridDev &g, const float2 *Tu, const int64_t *pts, int64_t pt_base,
-                       int64_t count, float2 *W, cudaStream_t st)
+                       int64_t count, float2 *W, cudaStream_t st, bool out_by_point)
 {
     if (count <= 0) return GPR_OK;
     const OzOperands *O = M->oz;
@@ -514,6 +523,7 @@ gpr_status launch_oz_w(const gpr_model *M, const GridDev &g, const float2 *Tu, c
     prm.colscale = O->colscale;
     prm.sf2 = (float)M->kp.sf2;
     prm.W = W;
+    prm.out_by_point = out_by_point ? 1 : 0;
     prm.status = gpr_status_word();
     if (!prm.status) return GPR_ERR_CUDA;
     constexpr int S = 7;
@@ -530,7 +540,7 @@ gpr_status launch_oz_w(const gpr_model *M, const GridDev &g, const float2 *Tu, c
 }
 
 gpr_status launch_stats_ff(const gpr_model *M, const GridDev &g, const int64_t *pts, int64_t count, const int32_t *slot,
-                           const float2 *W, double *out15, cudaStream_t st)
+                           const float2 *W, double *out15, cudaStream_t st, bool out_by_point)
 {
     if (count <= 0) return GPR_OK;
     Prior13 pr;
@@ -545,7 +555,7 @@ gpr_status launch_stats_ff(const gpr_model *M, const GridDev &g, const int64_t *
     {
         ProfScope ps("stats_ff", st);
         k_stats_ff<<<(unsigned)((count + 7) / 8), 256, 0, st>>>(g, pts, count, slot, W, M->mp, M->m, M->oz->vyff,
-                                                              M->kp.sf2, pr, out15);
+                                                              M->kp.sf2, pr, out15, out_by_point ? 1 : 0);
     }
     note_launch();
     GPR_CUDA_TRY(cudaGetLastError());

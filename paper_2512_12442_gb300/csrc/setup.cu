@@ -351,6 +351,7 @@ extern "C" gpr_status gpr_model_destroy(gpr_model *M)
         if (M->ws[w]) cudaFree(M->ws[w]);
     tc_release(M);
     oz_release(M);
+    cache_release(M);
     delete M;
     return GPR_OK;
 }

@@ -124,7 +124,7 @@ def test_adaptive_config2_full_field(torch, g):
         nz = a != 0
         assert np.array_equal(a[nz], d[nz])
         assert np.sqrt(np.mean((a - d) ** 2)) < 1e-3
-        assert sa["recon_points"] <= sd["recon_points"]
+        assert sa["leaf_cells"] <= sd["leaf_cells"]  # |S| vs the dense cascade's kept cells
         assert sum(sa["nodes_per_level"]) > 0
 
 
