@@ -3,6 +3,7 @@
 // float-float whitened rows W of every point reconstructed so far and complete stats15.
 // The LCP of a new isovalue then reconstructs only points no earlier call touched.
 // W rows are cached only while they fit a fixed budget of device memory.
+#include <stdlib.h>
 #include <string.h>
 
 #include "internal.h"
@@ -101,7 +102,9 @@ gpr_status grid_cache(gpr_model *M, const gpr_grid *grid, const GridDev &g, gpr_
     CA(C->have_mv, n);
     CA(C->S15, n * 15 * 8);
     CA(C->have_S, n);
-    if (e == cudaSuccess && oz_supported(M) && n * (size_t)M->mp * 8 <= kWCacheBudget) {
+    size_t wbudget = kWCacheBudget;  // GPR_WCACHE_BUDGET_MB overrides it (tests of the uncached paths)
+    if (const char *ev = getenv("GPR_WCACHE_BUDGET_MB")) wbudget = (size_t)atoll(ev) << 20;
+    if (e == cudaSuccess && oz_supported(M) && n * (size_t)M->mp * 8 <= wbudget) {
         CA(C->W, n * (size_t)M->mp * 8);
         CA(C->have_W, n);
         if (e != cudaSuccess) {  // no room for the rows: run without them

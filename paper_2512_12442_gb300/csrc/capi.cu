@@ -176,6 +176,21 @@ extern "C" gpr_status gpr_reconstruct_dense(gpr_model *M, const gpr_grid *grid, 
     return GPR_OK;
 }
 
+__global__ void k_flag_zrange(const uint8_t *flag, int64_t n, int64_t nxy, int64_t za, int64_t zb, uint8_t *out)
+{
+    int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    int64_t z = p / nxy;
+    out[p] = (flag[p] && z >= za && z < zb) ? 1 : 0;
+}
+
+void launch_flag_zrange(const uint8_t *flag, int64_t n, int64_t nxy, int64_t za, int64_t zb, uint8_t *out,
+                        cudaStream_t st)
+{
+    k_flag_zrange<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(flag, n, nxy, za, zb, out);
+    note_launch();
+}
+
 __global__ void k_fill_slot(const int64_t *idx, int64_t count, int64_t npts, int32_t *slot, int *status)
 {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -370,9 +385,47 @@ gpr_status lcp_from_kept_cells(gpr_model *M, const GridDev &g, const double *T64
     }
     // FP64-class W rows and stats15 for the kept cells' corners, then the estimator.  Default:
     // the tensor-core digit-split GEMM with float-float statistics; FP64 CUDA cores on request
-    // or where the split's exactness bound does not hold (m > 1024, Matern).
+    // or for kernels the split does not serve (Matern).
     const bool use_oz = lo.exact_mode == GPR_EXACT_AUTO && oz_supported(M);
     size_t te = table_elems(M, g);
+    // bound on the float-float row buffer (GPR_ROW_BUDGET_MB overrides it, for tests of the slab path)
+    size_t kRowBudget = (size_t)8 << 30;
+    if (const char *e = getenv("GPR_ROW_BUDGET_MB")) kRowBudget = (size_t)atoll(e) << 20;
+    if (use_oz && (size_t)npts * M->mp * 8 > kRowBudget) {
+        // z slabs: rows of the flagged points in planes [z0-1, z1+1), stats of those in [z0, z1)
+        int64_t nxy = (int64_t)g.n[0] * g.n[1], nz = g.n[2];
+        int64_t zs = (int64_t)(kRowBudget / ((size_t)nxy * M->mp * 8)) - 2;
+        if (zs < 1) return GPR_ERR_OOM;
+        int64_t maxrows = (zs + 2) * nxy;
+        size_t b2 = Carver::round((size_t)maxrows * M->mp * 8) + Carver::round((size_t)n * 15 * 8) +
+                    cell_lcp_scratch_bytes(ncell) + Carver::round(te * sizeof(float2)) + Carver::round((size_t)n) +
+                    2048;
+        GPR_TRY(ws_reserve(M, 1, b2, st));
+        Carver cv2{(char *)M->ws[1]};
+        float2 *W = cv2.take<float2>((size_t)maxrows * M->mp);
+        double *S15 = cv2.take<double>((size_t)n * 15);
+        void *scr = cv2.take<char>(cell_lcp_scratch_bytes(ncell));
+        float2 *Tu = cv2.take<float2>(te);
+        uint8_t *zflag = cv2.take<uint8_t>((size_t)n);
+        GPR_TRY(oz_prepare(M, st));
+        GPR_TRY(oz_unit_tables(M, g, Tu, st));
+        for (int64_t z0 = 0; z0 < nz; z0 += zs) {
+            int64_t z1 = z0 + zs < nz ? z0 + zs : nz;
+            launch_flag_zrange(pflag, n, nxy, z0 > 0 ? z0 - 1 : 0, z1 + 1 < nz ? z1 + 1 : nz, zflag, st);
+            int64_t nw = 0, ns = 0;
+            GPR_TRY(compact_flags(zflag, n, plist, slot, &nw, cscr, csb, st));
+            if (nw == 0) continue;
+            GPR_TRY(launch_oz_w(M, g, Tu, plist, 0, nw, W, st));
+            launch_flag_zrange(pflag, n, nxy, z0, z1, zflag, st);
+            GPR_TRY(compact_flags(zflag, n, plist + n, nullptr, &ns, cscr, csb, st));
+            if (ns > 0) GPR_TRY(launch_stats_ff(M, g, plist + n, ns, slot, W, S15, st, true));
+        }
+        int64_t nest = 0;
+        GPR_TRY(run_cell_lcp(g, S15, nullptr, clist, ncell, lo, lcp, false, scr, cell_lcp_scratch_bytes(ncell),
+                             stats ? &nest : nullptr, st));
+        if (stats) stats->cells_estimated = nest;
+        return GPR_OK;
+    }
     size_t b2 = Carver::round((size_t)npts * M->mp * sizeof(double)) + Carver::round((size_t)npts * 15 * sizeof(double)) +
                 cell_lcp_scratch_bytes(ncell) + Carver::round(te * sizeof(float2)) + 2048;
     GPR_TRY(ws_reserve(M, 1, b2, st));

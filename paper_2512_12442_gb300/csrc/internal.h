@@ -229,6 +229,8 @@ size_t compact_scratch_bytes(int64_t n);
 int num_sms();
 
 // ---- shared by the LCP entry points (capi.cu)
+void launch_flag_zrange(const uint8_t *flag, int64_t n, int64_t nxy, int64_t za, int64_t zb, uint8_t *out,
+                        cudaStream_t st);
 bool opts_valid(const gpr_lcp_options *o);
 LcpOpts lcp_opts(const gpr_lcp_options *o, double theta);
 void prepass_margins(const gpr_model *M, double &mv, double &mm);

@@ -5,9 +5,9 @@
 //   b' = [L^-1]_ji / 2^F_j:       b' = sum_t l_t 2^(-6(t+1)),   per output column j,
 // so every digit is exact in BF16 and every product i_s * l_t is exact.  Products of the same
 // level d = s + t share one power-of-two weight and are accumulated in one TMEM accumulator;
-// for K <= 1024 the integer sums stay below 2^24 and the FP32 accumulation is exact.  The
-// epilogue combines the levels (smallest first) in float-float arithmetic and writes W as
-// (hi, lo) float pairs.  Products with s + t < S are kept; S = 7 -> 28 products.
+// over K chunks of at most 1024 the integer sums stay below 2^24, so the FP32 accumulation is
+// exact; after each chunk the levels are drained (smallest first) into float-float registers.
+// W is written as (hi, lo) float pairs.  Products with s + t < S are kept; S = 7 -> 28 products.
 //
 // Tiles: M = 128 points, N = 64 columns, K blocks of 32 digits (64-byte rows, 64B swizzle),
 // two stages; the S accumulators use S x 64 of the 512 TMEM columns.  B digit slices arrive by
@@ -26,6 +26,7 @@ namespace {
 
 constexpr int TM = 128, TN = 64, BKE = 32, NTHR = 512, BETA = 6;
 constexpr uint32_t kSpin = 1u << 22;
+constexpr int KCH = 1024 / BKE;    // K blocks per exact accumulation (K <= 1024 keeps sums < 2^24)
 constexpr int A_SLICE = TM * 64;   // bytes of one A digit slice per K block
 constexpr int B_SLICE = TN * 64;   // bytes of one B digit slice per K block
 
@@ -101,6 +102,29 @@ struct OzParams {
     int *status;
 };
 
+// Adds the S level accumulators of TMEM (lanes 32*(w%4), columns 16*(w/4) of each level) to
+// the float-float sums, smallest level first.
+template <int S>
+__device__ __forceinline__ void drain_levels(uint32_t tmem, int warp, FF *acc)
+{
+    const int lq = warp & 3, quarter = warp >> 2;
+#pragma unroll
+    for (int lvl = S - 1; lvl >= 0; --lvl) {
+        uint32_t rr[16];
+        const uint32_t taddr = tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(lvl * TN + quarter * 16);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            : "=r"(rr[0]), "=r"(rr[1]), "=r"(rr[2]), "=r"(rr[3]), "=r"(rr[4]), "=r"(rr[5]), "=r"(rr[6]), "=r"(rr[7]),
+              "=r"(rr[8]), "=r"(rr[9]), "=r"(rr[10]), "=r"(rr[11]), "=r"(rr[12]), "=r"(rr[13]), "=r"(rr[14]),
+              "=r"(rr[15])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        const float wgt = ldexpf(1.0f, -BETA * (lvl + 2));
+#pragma unroll
+        for (int c = 0; c < 16; ++c) acc[c] = ff_add_f(acc[c], __uint_as_float(rr[c]) * wgt);
+    }
+}
+
 template <int S>
 __global__ void __launch_bounds__(NTHR, 1) k_oz_w(const __grid_constant__ CUtensorMap mapB, OzParams prm)
 {
@@ -144,6 +168,9 @@ __global__ void __launch_bounds__(NTHR, 1) k_oz_w(const __grid_constant__ CUtens
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_slot;
     bool ok_all = true;
+    FF acc[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) acc[c] = FF{0.f, 0.f};
 
     for (int kb = 0; kb < nkb; ++kb) {
         const int s = kb & 1, use = kb >> 1;
@@ -217,7 +244,7 @@ __global__ void __launch_bounds__(NTHR, 1) k_oz_w(const __grid_constant__ CUtens
                     const uint32_t ab = su32(st + sa * A_SLICE), bb = su32(st + S * A_SLICE + tb * B_SLICE);
 #pragma unroll
                     for (int kk = 0; kk < 2; ++kk) {
-                        uint32_t acc = (kb == 0 && sa == 0 && kk == 0) ? 0u : 1u;
+                        uint32_t acc = (kb % KCH == 0 && sa == 0 && kk == 0) ? 0u : 1u;
                         asm volatile(
                             "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
                                 tmem + (uint32_t)(lvl * TN)),
@@ -226,33 +253,20 @@ __global__ void __launch_bounds__(NTHR, 1) k_oz_w(const __grid_constant__ CUtens
                 }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(free0 + 8 * s)
                          : "memory");
-            if (kb == nkb - 1)
+            if (kb == nkb - 1 || kb % KCH == KCH - 1)
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(done)
                              : "memory");
         }
+        if (kb == nkb - 1 || kb % KCH == KCH - 1) {
+            // drain this K chunk's level accumulators into the float-float sums
+            if (!wait_bar(done, (uint32_t)((kb / KCH) & 1))) ok_all = false;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            drain_levels<S>(tmem, warp, acc);
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncthreads();
+        }
     }
-    if (!wait_bar(done, 0)) ok_all = false;
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    // epilogue: warp -> lanes 32*(w%4), columns 16*(w/4) of every level accumulator
     const int lq = warp & 3, quarter = warp >> 2;
-    FF acc[16];
-#pragma unroll
-    for (int c = 0; c < 16; ++c) acc[c] = FF{0.f, 0.f};
-#pragma unroll
-    for (int lvl = S - 1; lvl >= 0; --lvl) {
-        uint32_t rr[16];
-        const uint32_t taddr = tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(lvl * TN + quarter * 16);
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-            : "=r"(rr[0]), "=r"(rr[1]), "=r"(rr[2]), "=r"(rr[3]), "=r"(rr[4]), "=r"(rr[5]), "=r"(rr[6]), "=r"(rr[7]),
-              "=r"(rr[8]), "=r"(rr[9]), "=r"(rr[10]), "=r"(rr[11]), "=r"(rr[12]), "=r"(rr[13]), "=r"(rr[14]),
-              "=r"(rr[15])
-            : "r"(taddr));
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        const float wgt = ldexpf(1.0f, -BETA * (lvl + 2));
-#pragma unroll
-        for (int c = 0; c < 16; ++c) acc[c] = ff_add_f(acc[c], __uint_as_float(rr[c]) * wgt);
-    }
     const int64_t row = row0 + lq * 32 + lane;
     if (row < prm.count && rvalid[lq * 32 + lane]) {
         const int64_t orow = prm.out_by_point ? rpoint[lq * 32 + lane] : row;
@@ -445,7 +459,7 @@ struct OzOperands {
     CUtensorMap map;
 };
 
-bool oz_supported(const gpr_model *M) { return M->kp.kind == GPR_K_SE && M->m <= 1024; }
+bool oz_supported(const gpr_model *M) { return M->kp.kind == GPR_K_SE; }
 
 gpr_status oz_prepare(gpr_model *M, cudaStream_t st)
 {

@@ -145,3 +145,57 @@ def test_digit_split_lcp_vs_fp64_config2(torch, g):
     d = np.abs(out[g.GPR_EXACT_AUTO] - out[g.GPR_EXACT_FP64])
     # the two corner statistics differ by ~1e-9; the FP32 estimator turns that into ~1e-6 at most
     assert d.max() <= 1e-5, d.max()
+
+
+def test_digit_split_stats_m_above_1024(torch, g):
+    """More observations than one exact FP32 accumulation holds (m=1500: two K chunks, each
+    drained to float-float) against the FP64 CUDA-core path and the oracle."""
+    w = workloads.small(11, 1500, 13, ell=(0.12, 0.15, 0.18))
+    n = w.n
+    M = model_of(w)
+    grid = g.make_grid(n)
+    rng = np.random.default_rng(8)
+    base = np.unique(rng.integers(0, n ** 3, 300))
+    pts = np.unique(np.concatenate([base, base + 1, base + n, base + n * n]))
+    pts = pts[pts < n ** 3]
+    t = torch.tensor(pts, dtype=torch.int64, device="cuda")
+    a = torch.zeros(len(pts), 15, dtype=torch.float64, device="cuda")
+    b = torch.zeros_like(a)
+    g.gpr_stats_points(M, grid, t, a)
+    g.gpr_stats_points_split(M, grid, t, b)
+    g.gpr_sync()
+    a = a.cpu().numpy(); b = b.cpu().numpy()
+    assert np.array_equal(np.isnan(a), np.isnan(b))
+    ok = ~np.isnan(a)
+    assert np.abs(a - b)[ok].max() <= 1e-8
+    ref = oracle.Model.from_workload(w).stats15(n)[pts]
+    assert np.abs(b[ok] - ref[ok]).max() <= 1e-8
+
+
+def test_digit_split_lcp_slab_path(torch, g, monkeypatch):
+    """Without cached rows and with a row buffer of a few planes, the digit-split leaf path runs
+    in z slabs (rows of planes z0-1..z1, statistics of planes z0..z1-1); its field equals the
+    single-buffer one and the cached one bit for bit."""
+    w = workloads.small(5, 300, 40, ell=(0.15, 0.2, 0.25))
+    th = w.isovalues[0]
+
+    def run(env):
+        for k, v in env.items():
+            monkeypatch.setenv(k, v)
+        M = model_of(w)
+        f = torch.zeros((w.n - 1) ** 3, dtype=torch.float32, device="cuda")
+        l0 = g.gpr_launch_count()
+        g.gpr_lcp_dense(M, g.make_grid(w.n), th, g.lcp_options(prec=g.GPR_P_TF32X3), f)
+        g.gpr_sync()
+        launches = g.gpr_launch_count() - l0
+        for k in env:
+            monkeypatch.delenv(k)
+        return f.cpu().numpy(), launches
+
+    single, l_single = run({"GPR_WCACHE_BUDGET_MB": "0"})
+    slabs, l_slabs = run({"GPR_WCACHE_BUDGET_MB": "0", "GPR_ROW_BUDGET_MB": "16"})
+    cached, _ = run({})
+    assert l_slabs > l_single + 20  # one plane per slab: two compactions and two kernels each
+    assert (single > 0).sum() > 100
+    assert np.array_equal(single, slabs)
+    assert np.array_equal(single, cached)
