@@ -210,6 +210,34 @@ gpr_status gpr_lcp_adaptive(gpr_model *model, const gpr_grid *grid, double isova
                             const gpr_lcp_options *opts, float *lcp, gpr_adaptive_stats *stats, void *stream);
 
 /*
+ * gpr_lcp_adaptive_batched -- many fields at once (no counterpart in the paper,
+ * which treats one field per run): field i is gpr_lcp_adaptive(models[i],
+ * &grids[i], isovalues[i], max_depths[i], opts, lcps[i]) and its result is the
+ * same, value for value.  Fields are grouped by model (entries that share a
+ * model run one after another and share its grid cache), the groups are ordered
+ * by estimated cost (m^2 times the grid's face area, largest first) and taken by
+ * a pool of host worker threads, each with its own CUDA stream and a pooled
+ * device workspace, so small and large fields overlap on the GPU.  The cells
+ * that need the estimator, from every field, are collected in one record
+ * buffer and estimated by ONE persistent launch at the end.
+ *   models, grids, isovalues, max_depths, lcps   host arrays of `count` entries;
+ *                lcps[i] is a device float array of field i's cells
+ *   stats        host, nullable: `count` entries, as gpr_lcp_adaptive fills them
+ *   stream       the work is ordered after earlier work on `stream`, and later
+ *                work on `stream` sees the results; the call returns when the
+ *                host-side scheduling is done (results may still be in flight)
+ * Argument errors (any entry) return GPR_ERR_ARG before any work; otherwise
+ * the status of the first failing field (in index order) is returned.  The
+ * environment variable GPR_BATCH_WORKERS (1..64, default 8) sets the pool size.
+ */
+gpr_status gpr_lcp_adaptive_batched(gpr_model *const *models, const gpr_grid *grids, const double *isovalues,
+                                    const int32_t *max_depths, int32_t count, const gpr_lcp_options *opts,
+                                    float *const *lcps, gpr_adaptive_stats *stats, void *stream);
+
+/* Frees the batch workers' pooled device workspaces (they are kept between calls). */
+gpr_status gpr_batch_release(void);
+
+/*
  * gpr_cell_lcp_from_stats_noalloc -- no counterpart in the paper.  The same cell
  * LCP as gpr_cell_lcp_from_stats (same arguments, same results), for callers that
  * may not allocate device memory when they call: a plug-in inside an application

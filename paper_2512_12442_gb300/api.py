@@ -159,6 +159,27 @@ def gpr_lcp_adaptive(model: Model, grid: GridC, isovalue, max_depth, opts: LcpOp
     return _stats_dict(s)
 
 
+def gpr_lcp_adaptive_batched(models, grids, isovalues, max_depths, opts: LcpOptionsC, lcps, stream=None) -> list:
+    """Many adaptive fields in one call (field i as gpr_lcp_adaptive(models[i], grids[i], ...));
+    returns the per-field statistics."""
+    n = len(models)
+    if not (len(grids) == len(isovalues) == len(max_depths) == len(lcps) == n):
+        raise ValueError("gpr_lcp_adaptive_batched: per-field lists differ in length")
+    hm = (C.c_void_p * n)(*[m.handle for m in models])
+    hg = (GridC * n)(*grids)
+    hi = (C.c_double * n)(*[float(v) for v in isovalues])
+    hd = (C.c_int32 * n)(*[int(d) for d in max_depths])
+    hl = (C.c_void_p * n)(*[_ptr(t) for t in lcps])
+    st = (AdaptiveStatsC * n)()
+    rc = load().gpr_lcp_adaptive_batched(hm, hg, hi, hd, n, C.byref(opts), hl, st, _stream(stream))
+    _check(rc, "gpr_lcp_adaptive_batched")
+    return [_stats_dict(st[i]) for i in range(n)]
+
+
+def gpr_batch_release() -> None:
+    _check(load().gpr_batch_release(), "gpr_batch_release")
+
+
 def gpr_lcp_backward(model: Model, grid: GridC, isovalue, opts: LcpOptionsC, dL_dlcp, stream=None):
     """Adjoint of sum_c dL_dlcp[c] LCP_c: returns (dL/dy (m,), dL/dlog l (3,)) as numpy float64."""
     dy = np.zeros(model.m); dl = np.zeros(3)

@@ -6,10 +6,22 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <atomic>
+
 #include "internal.h"
 
 namespace {
-constexpr size_t kWCacheBudget = (size_t)24 << 30;
+constexpr size_t kWCacheBudget = (size_t)24 << 30;       // rows of one model and grid
+constexpr size_t kWCacheTotal = (size_t)64 << 30;        // rows of all models together
+std::atomic<size_t> g_wcache_total{0};
+
+bool reserve_rows(size_t b)
+{
+    size_t cur = g_wcache_total.load();
+    while (cur + b <= kWCacheTotal)
+        if (g_wcache_total.compare_exchange_weak(cur, cur + b)) return true;
+    return false;
+}
 
 bool same_grid(const gpr_grid &a, const gpr_grid &b) { return memcmp(&a, &b, sizeof a) == 0; }
 
@@ -65,6 +77,7 @@ void cache_release(gpr_model *M)
     if (!C) return;
     cudaFree(C->T32); cudaFree(C->T64); cudaFree(C->Tff); cudaFree(C->Tu);
     cudaFree(C->mv); cudaFree(C->have_mv); cudaFree(C->W); cudaFree(C->have_W); cudaFree(C->S15); cudaFree(C->have_S);
+    g_wcache_total -= C->wbytes;
     delete C;
     M->cache = nullptr;
 }
@@ -104,13 +117,17 @@ gpr_status grid_cache(gpr_model *M, const gpr_grid *grid, const GridDev &g, gpr_
     CA(C->have_S, n);
     size_t wbudget = kWCacheBudget;  // GPR_WCACHE_BUDGET_MB overrides it (tests of the uncached paths)
     if (const char *ev = getenv("GPR_WCACHE_BUDGET_MB")) wbudget = (size_t)atoll(ev) << 20;
-    if (e == cudaSuccess && oz_supported(M) && n * (size_t)M->mp * 8 <= wbudget) {
-        CA(C->W, n * (size_t)M->mp * 8);
+    const size_t wb = n * (size_t)M->mp * 8;
+    if (e == cudaSuccess && oz_supported(M) && wb <= wbudget && reserve_rows(wb)) {
+        C->wbytes = wb;
+        CA(C->W, wb);
         CA(C->have_W, n);
         if (e != cudaSuccess) {  // no room for the rows: run without them
             cudaGetLastError();
             cudaFree(C->W); cudaFree(C->have_W);
             C->W = nullptr; C->have_W = nullptr;
+            g_wcache_total -= wb;
+            C->wbytes = 0;
             e = cudaSuccess;
         }
     }

@@ -392,33 +392,38 @@ gpr_status lcp_from_kept_cells(gpr_model *M, const GridDev &g, const double *T64
     size_t kRowBudget = (size_t)8 << 30;
     if (const char *e = getenv("GPR_ROW_BUDGET_MB")) kRowBudget = (size_t)atoll(e) << 20;
     if (use_oz && (size_t)npts * M->mp * 8 > kRowBudget) {
-        // z slabs: rows of the flagged points in planes [z0-1, z1+1), stats of those in [z0, z1)
-        int64_t nxy = (int64_t)g.n[0] * g.n[1], nz = g.n[2];
-        int64_t zs = (int64_t)(kRowBudget / ((size_t)nxy * M->mp * 8)) - 2;
-        if (zs < 1) return GPR_ERR_OOM;
-        int64_t maxrows = (zs + 2) * nxy;
-        size_t b2 = Carver::round((size_t)maxrows * M->mp * 8) + Carver::round((size_t)n * 15 * 8) +
+        // Planes of rows in a ring of R grid planes (row of point p at p % (R nx ny)): slab
+        // [z0, z1) of R - 2 planes reconstructs the rows of its new planes up to z1 and then the
+        // statistics of planes z0..z1-1, whose neighbours lie in planes z0-1..z1, all resident.
+        const int64_t nxy = (int64_t)g.n[0] * g.n[1], nz = g.n[2];
+        const int64_t R = (int64_t)(kRowBudget / ((size_t)nxy * M->mp * 8));
+        if (R < 3) return GPR_ERR_OOM;
+        const int64_t zs = R - 2, ring = R * nxy;
+        size_t b2 = Carver::round((size_t)ring * M->mp * 8) + Carver::round((size_t)n * 15 * 8) +
                     cell_lcp_scratch_bytes(ncell) + Carver::round(te * sizeof(float2)) + Carver::round((size_t)n) +
                     2048;
         GPR_TRY(ws_reserve(M, 1, b2, st));
         Carver cv2{(char *)M->ws[1]};
-        float2 *W = cv2.take<float2>((size_t)maxrows * M->mp);
+        float2 *W = cv2.take<float2>((size_t)ring * M->mp);
         double *S15 = cv2.take<double>((size_t)n * 15);
         void *scr = cv2.take<char>(cell_lcp_scratch_bytes(ncell));
         float2 *Tu = cv2.take<float2>(te);
         uint8_t *zflag = cv2.take<uint8_t>((size_t)n);
         GPR_TRY(oz_prepare(M, st));
         GPR_TRY(oz_unit_tables(M, g, Tu, st));
+        int64_t rows_to = 0;  // rows of planes < rows_to are in the ring
         for (int64_t z0 = 0; z0 < nz; z0 += zs) {
-            int64_t z1 = z0 + zs < nz ? z0 + zs : nz;
-            launch_flag_zrange(pflag, n, nxy, z0 > 0 ? z0 - 1 : 0, z1 + 1 < nz ? z1 + 1 : nz, zflag, st);
-            int64_t nw = 0, ns = 0;
-            GPR_TRY(compact_flags(zflag, n, plist, slot, &nw, cscr, csb, st));
-            if (nw == 0) continue;
-            GPR_TRY(launch_oz_w(M, g, Tu, plist, 0, nw, W, st));
+            const int64_t z1 = z0 + zs < nz ? z0 + zs : nz, hi = z1 + 1 < nz ? z1 + 1 : nz;
+            int64_t cnt = 0;
+            if (hi > rows_to) {
+                launch_flag_zrange(pflag, n, nxy, rows_to, hi, zflag, st);
+                GPR_TRY(compact_flags(zflag, n, plist, nullptr, &cnt, cscr, csb, st));
+                if (cnt > 0) GPR_TRY(launch_oz_w(M, g, Tu, plist, 0, cnt, W, st, true, ring));
+                rows_to = hi;
+            }
             launch_flag_zrange(pflag, n, nxy, z0, z1, zflag, st);
-            GPR_TRY(compact_flags(zflag, n, plist + n, nullptr, &ns, cscr, csb, st));
-            if (ns > 0) GPR_TRY(launch_stats_ff(M, g, plist + n, ns, slot, W, S15, st, true));
+            GPR_TRY(compact_flags(zflag, n, plist, nullptr, &cnt, cscr, csb, st));
+            if (cnt > 0) GPR_TRY(launch_stats_ff(M, g, plist, cnt, nullptr, W, S15, st, true, ring));
         }
         int64_t nest = 0;
         GPR_TRY(run_cell_lcp(g, S15, nullptr, clist, ncell, lo, lcp, false, scr, cell_lcp_scratch_bytes(ncell),

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <vector>
 
 #include "../../include/gpr_lcp.h"
@@ -158,17 +159,22 @@ bool oz_supported(const gpr_model *M);
 gpr_status oz_prepare(gpr_model *M, cudaStream_t st);
 void oz_release(gpr_model *M);
 gpr_status oz_unit_tables(const gpr_model *M, const GridDev &g, float2 *Tu, cudaStream_t st);
-// out_by_point: row (or stats) of listed point p goes to position p of a full-grid array.
+// out_by_point: row (or stats) of listed point p goes to position p of a full-grid array (rows
+// at p % row_mod, a ring of grid planes, when row_mod > 0); without a slot map the statistics
+// read the row of point q at q % row_mod.
 gpr_status launch_oz_w(const gpr_model *M, const GridDev &g, const float2 *Tu, const int64_t *pts, int64_t pt_base,
-                       int64_t count, float2 *W, cudaStream_t st, bool out_by_point = false);
+                       int64_t count, float2 *W, cudaStream_t st, bool out_by_point = false,
+                       int64_t row_mod = 0);
 gpr_status launch_stats_ff(const gpr_model *M, const GridDev &g, const int64_t *pts, int64_t count, const int32_t *slot,
-                           const float2 *W, double *out15, cudaStream_t st, bool out_by_point = false);
+                           const float2 *W, double *out15, cudaStream_t st, bool out_by_point = false,
+                           int64_t row_mod = 0);
 
 // ---- per-model, per-grid cache of isovalue-independent results (cache.cu)
 struct GridCache {
     gpr_grid key;
     int64_t n = 0;
     size_t bytes = 0;
+    size_t wbytes = 0;           // bytes of W counted against the budget of all models
     float *T32 = nullptr;
     double *T64 = nullptr;
     float2 *Tff = nullptr, *Tu = nullptr;
@@ -184,6 +190,9 @@ struct GridCache {
 gpr_status grid_cache(gpr_model *M, const gpr_grid *grid, const GridDev &g, gpr_precision mv_prec, GridCache **out,
                       cudaStream_t st);
 void cache_release(gpr_model *M);
+struct OctTrace;
+gpr_status octree_lcp(gpr_model *M, const gpr_grid *grid, double theta, int D, const gpr_lcp_options *opts,
+                      float *lcp, gpr_adaptive_stats *stats, cudaStream_t st, OctTrace *trace);
 // Fills the per-point table for flagged points that lack it (flags: uint8 per point).
 gpr_status cache_fill_mv(gpr_model *M, GridCache *C, const GridDev &g, const uint8_t *flag, int64_t *list, float *tmp_mean,
                          float *tmp_var, float *part, void *cscr, size_t csb, cudaStream_t st);
@@ -201,6 +210,19 @@ struct LcpOpts {
 // For cells in `cells` (nullptr = all), build Sigma_8 from stats (indexed via slot map, nullptr = identity),
 // write 0/1 for skipped/deterministic cells into lcp[cell-or-position], and queue the rest.
 // out_by_position: lcp indexed by position in `cells` (true) or by linear cell index (false).
+// Records of several fields collected for one estimator launch (the batched entry point): a
+// worker thread sets its sink; run_cell_lcp then appends its records there while `reserved`
+// (host counter of records promised) stays within `capacity`, else estimates on its own.
+struct RecordSink {
+    void *recs;
+    unsigned long long *nrec;  // device counter of appended records
+    int64_t capacity;
+    std::atomic<int64_t> *reserved;
+};
+void set_record_sink(RecordSink *sink);  // for the calling thread; nullptr to clear
+size_t record_bytes();
+void launch_estimator(const void *recs, const unsigned long long *nrec, int64_t max_records, const LcpOpts &o,
+                      cudaStream_t st);
 gpr_status run_cell_lcp(const GridDev &g, const double *stats, const int32_t *slot, const int64_t *cells,
                         int64_t count, const LcpOpts &o, float *lcp, bool out_by_position, void *scratch,
                         size_t scratch_bytes, int64_t *n_estimated, cudaStream_t st);

@@ -40,14 +40,15 @@ struct CellRec {
     float b[8];       // theta - mu_c
     float L[36];      // lower Cholesky factor, row-major packed (row i: entries 0..i)
     int64_t cell;     // linear cell index (keys the lattice shift / Philox stream)
-    int64_t out;      // output position
+    float *out;       // output address (the records of several fields share one estimator launch)
 };
 
 __device__ __forceinline__ int tri(int i, int j) { return i * (i + 1) / 2 + j; }
 
 __global__ void k_cell_prep(GridDev g, const double *stats, const int32_t *slot, const int64_t *cells,
                             int64_t count, double theta, double tau, double skip_eps, PairTable pt, float *lcp,
-                            bool by_pos, CellRec *recs, unsigned long long *nrec, int *status)
+                            bool by_pos, CellRec *recs, unsigned long long *nrec, unsigned long long *nown,
+                            int *status)
 {
     int64_t pos = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     bool active = pos < count;
@@ -128,7 +129,7 @@ __global__ void k_cell_prep(GridDev g, const double *stats, const int32_t *slot,
                 }
                 int64_t mask = (mlo < 1e-7 ? 1 : 0) | (mhi < 1e-7 ? 2 : 0);
                 r.cell = cidx | (mask << 56);
-                r.out = outi;
+                r.out = lcp + outi;
                 need = true;
             }
         }
@@ -139,7 +140,10 @@ __global__ void k_cell_prep(GridDev g, const double *stats, const int32_t *slot,
     if (!mask) return;
     int lane = threadIdx.x & 31, leader = __ffs(mask) - 1;
     unsigned long long base = 0;
-    if (lane == leader) base = atomicAdd(nrec, (unsigned long long)__popc(mask));
+    if (lane == leader) {
+        base = atomicAdd(nrec, (unsigned long long)__popc(mask));
+        if (nown) atomicAdd(nown, (unsigned long long)__popc(mask));
+    }
     base = __shfl_sync(0xffffffffu, base, leader);
     if (need) recs[base + __popc(mask & ((1u << lane) - 1))] = r;
 }
@@ -160,7 +164,7 @@ struct Lattice {
 };
 
 __global__ void __launch_bounds__(256, 3) k_sov(const CellRec *recs, const unsigned long long *nrec, int N,
-                                               uint64_t seed, Lattice lat, float *lcp)
+                                               uint64_t seed, Lattice lat)
 {
     int lane = threadIdx.x & 31;
     int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -214,7 +218,7 @@ __global__ void __launch_bounds__(256, 3) k_sov(const CellRec *recs, const unsig
         }
         if (lane == 0) {
             double v = 1.0 - (double)acc_lo / N - (double)acc_hi / N;
-            lcp[r.out] = (float)(v < 0.0 ? 0.0 : (v > 1.0 ? 1.0 : v));
+            *r.out = (float)(v < 0.0 ? 0.0 : (v > 1.0 ? 1.0 : v));
         }
     }
 }
@@ -232,7 +236,7 @@ __device__ __forceinline__ void philox(uint32_t c[4], uint32_t k0, uint32_t k1)
     }
 }
 
-__global__ void k_mc(const CellRec *recs, const unsigned long long *nrec, int N, uint64_t seed, float *lcp)
+__global__ void k_mc(const CellRec *recs, const unsigned long long *nrec, int N, uint64_t seed)
 {
     int lane = threadIdx.x & 31;
     int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -278,7 +282,7 @@ __global__ void k_mc(const CellRec *recs, const unsigned long long *nrec, int N,
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) crossed += __shfl_xor_sync(0xffffffffu, crossed, o);
-        if (lane == 0) lcp[r.out] = (float)((double)crossed / (double)N);
+        if (lane == 0) *r.out = (float)((double)crossed / (double)N);
     }
 }
 
@@ -297,6 +301,30 @@ Lattice make_lattice()
 
 size_t cell_lcp_scratch_bytes(int64_t count) { return Carver::round(sizeof(CellRec) * (size_t)count) + 256; }
 
+namespace {
+thread_local RecordSink *tl_sink = nullptr;
+}
+
+void set_record_sink(RecordSink *sink) { tl_sink = sink; }
+size_t record_bytes() { return sizeof(CellRec); }
+
+void launch_estimator(const void *recs, const unsigned long long *nrec, int64_t max_records, const LcpOpts &o,
+                      cudaStream_t st)
+{
+    int64_t blocks = (max_records + 7) / 8;  // one warp per record, persistent over the device count
+    if (blocks > (int64_t)num_sms() * 16) blocks = (int64_t)num_sms() * 16;
+    if (blocks < 1) blocks = 1;
+    if (o.est == GPR_EST_SOV_QMC) {
+        static Lattice lat = make_lattice();
+        ProfScope _ps("sov", st);
+        k_sov<<<(unsigned)blocks, 256, 0, st>>>((const CellRec *)recs, nrec, o.n_samples, o.seed, lat);
+    } else {
+        ProfScope _ps("mc", st);
+        k_mc<<<(unsigned)blocks, 256, 0, st>>>((const CellRec *)recs, nrec, o.n_samples, o.seed);
+    }
+    note_launch();
+}
+
 gpr_status run_cell_lcp(const GridDev &g, const double *stats, const int32_t *slot, const int64_t *cells,
                         int64_t count, const LcpOpts &o, float *lcp, bool by_pos, void *scratch,
                         size_t scratch_bytes, int64_t *n_estimated, cudaStream_t st)
@@ -309,35 +337,28 @@ gpr_status run_cell_lcp(const GridDev &g, const double *stats, const int32_t *sl
     Carver cv{(char *)scratch};
     unsigned long long *nrec = cv.take<unsigned long long>(1);
     CellRec *recs = cv.take<CellRec>((size_t)count);
+    // a batch sink with room takes the records; its owner runs one estimator launch for all
+    RecordSink *sink = tl_sink;
+    bool to_sink = false;
+    if (sink) {
+        int64_t cur = sink->reserved->load();
+        while (cur + count <= sink->capacity && !sink->reserved->compare_exchange_weak(cur, cur + count)) {
+        }
+        to_sink = cur + count <= sink->capacity;
+    }
     GPR_CUDA_TRY(cudaMemsetAsync(nrec, 0, sizeof(unsigned long long), st));
     static PairTable pt = make_pair_table();
     int *status = gpr_status_word();
     if (!status) return GPR_ERR_CUDA;
     {
         ProfScope _ps("cell_prep", st);
-        k_cell_prep<<<(unsigned)((count + 127) / 128), 128, 0, st>>>(g, stats, slot, cells, count, o.theta, o.tau,
-                                                                 o.skip_eps, pt, lcp, by_pos, recs, nrec, status);
+        k_cell_prep<<<(unsigned)((count + 127) / 128), 128, 0, st>>>(
+            g, stats, slot, cells, count, o.theta, o.tau, o.skip_eps, pt, lcp, by_pos,
+            to_sink ? (CellRec *)sink->recs : recs, to_sink ? sink->nrec : nrec, to_sink ? nrec : nullptr, status);
     }
     note_launch();
     GPR_CUDA_TRY(cudaGetLastError());
-    int sms = num_sms();
-    int64_t warps_needed = count;
-    int64_t blocks = (warps_needed + 7) / 8;
-    if (blocks > (int64_t)sms * 16) blocks = (int64_t)sms * 16;
-    if (o.est == GPR_EST_SOV_QMC) {
-        static Lattice lat = make_lattice();
-        {
-            ProfScope _ps("sov", st);
-            k_sov<<<(unsigned)blocks, 256, 0, st>>>(recs, nrec, o.n_samples, o.seed, lat, lcp);
-        }
-        note_launch();
-    } else {
-        {
-            ProfScope _ps("mc", st);
-            k_mc<<<(unsigned)blocks, 256, 0, st>>>(recs, nrec, o.n_samples, o.seed, lcp);
-        }
-        note_launch();
-    }
+    if (!to_sink) launch_estimator(recs, nrec, count, o, st);
     GPR_CUDA_TRY(cudaGetLastError());
     if (n_estimated) {
         unsigned long long h = 0;
@@ -557,16 +578,17 @@ gpr_status run_cell_lcp_on_scratch(const GridDev &g, const double *stats, const 
     GPR_CUDA_TRY(cudaMemsetAsync(nrec, 0, sizeof(unsigned long long), st));
     static PairTable pt = make_pair_table();
     k_cell_prep<<<(unsigned)((count + 127) / 128), 128, 0, st>>>(g, stats, nullptr, cells, count, o.theta, o.tau,
-                                                                 o.skip_eps, pt, lcp, by_pos, recs, nrec, status);
+                                                                 o.skip_eps, pt, lcp, by_pos, recs, nrec, nullptr,
+                                                                 status);
     note_launch();
     GPR_CUDA_TRY(cudaGetLastError());
     int64_t blocks = (count + 7) / 8;
     if (blocks > (int64_t)num_sms() * 16) blocks = (int64_t)num_sms() * 16;
     if (o.est == GPR_EST_SOV_QMC) {
         static Lattice lat = make_lattice();
-        k_sov<<<(unsigned)blocks, 256, 0, st>>>(recs, nrec, o.n_samples, o.seed, lat, lcp);
+        k_sov<<<(unsigned)blocks, 256, 0, st>>>(recs, nrec, o.n_samples, o.seed, lat);
     } else {
-        k_mc<<<(unsigned)blocks, 256, 0, st>>>(recs, nrec, o.n_samples, o.seed, lcp);
+        k_mc<<<(unsigned)blocks, 256, 0, st>>>(recs, nrec, o.n_samples, o.seed);
     }
     note_launch();
     GPR_CUDA_TRY(cudaGetLastError());

@@ -97,8 +97,9 @@ struct OzParams {
     int64_t pt_base, count;
     const float *colscale;  // 2^F_j
     float sf2;
-    float2 *W;  // count x mp float-float (or npts x mp when out_by_point)
+    float2 *W;  // count x mp float-float (or rows at p % row_mod when out_by_point)
     int out_by_point;
+    int64_t row_mod;
     int *status;
 };
 
@@ -269,7 +270,7 @@ __global__ void __launch_bounds__(NTHR, 1) k_oz_w(const __grid_constant__ CUtens
     const int lq = warp & 3, quarter = warp >> 2;
     const int64_t row = row0 + lq * 32 + lane;
     if (row < prm.count && rvalid[lq * 32 + lane]) {
-        const int64_t orow = prm.out_by_point ? rpoint[lq * 32 + lane] : row;
+        const int64_t orow = prm.out_by_point ? rpoint[lq * 32 + lane] % prm.row_mod : row;
         float2 *out = prm.W + orow * prm.mp + n0 + quarter * 16;
 #pragma unroll
         for (int c = 0; c < 16; ++c) {
@@ -369,7 +370,7 @@ __device__ __forceinline__ void dot2_step(float &sh, float &sl, float2 a, float2
 __global__ void __launch_bounds__(256, 3) k_stats_ff(GridDev g, const int64_t *pts, int64_t count,
                                                      const int32_t *slot, const float2 *W, int64_t mp, int64_t m,
                                                      const float2 *vyff, double sf2, Prior13 pr, double *out15,
-                                                     int out_by_point)
+                                                     int out_by_point, int64_t row_mod)
 {
     int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     int64_t pos = blockIdx.x * (int64_t)(blockDim.x / 32) + warp;
@@ -377,8 +378,8 @@ __global__ void __launch_bounds__(256, 3) k_stats_ff(GridDev g, const int64_t *p
     int64_t p = pts[pos];
     int64_t nx = g.n[0], ny = g.n[1], nz = g.n[2];
     int ix = (int)(p % nx), iy = (int)((p / nx) % ny), iz = (int)(p / (nx * ny));
-    // rows of W: through the slot map, or (slot == nullptr) the grid index itself
-    const int64_t self = slot ? (int64_t)slot[p] : p;
+    // rows of W: through the slot map, or (slot == nullptr) at the grid index modulo row_mod
+    const int64_t self = slot ? (int64_t)slot[p] : p % row_mod;
     int64_t nb[13];
 #pragma unroll
     for (int e = 0; e < 13; ++e) {
@@ -386,7 +387,7 @@ __global__ void __launch_bounds__(256, 3) k_stats_ff(GridDev g, const int64_t *p
         int64_t r = -1;
         if (a >= 0 && b >= 0 && c >= 0 && a < nx && b < ny && c < nz) {
             int64_t q = a + nx * (b + ny * (int64_t)c);
-            r = slot ? (int64_t)slot[q] : q;
+            r = slot ? (int64_t)slot[q] : q % row_mod;
         }
         nb[e] = r;
     }
@@ -519,7 +520,7 @@ gpr_status oz_unit_tables(const gpr_model *M, const GridDev &g, float2 *Tu, cuda
 
 // Float-float W rows of the listed points (count x mp float2) on the tensor cores.
 gpr_status launch_oz_w(const gpr_model *M, const GridDev &g, const float2 *Tu, const int64_t *pts, int64_t pt_base,
-                       int64_t count, float2 *W, cudaStream_t st, bool out_by_point)
+                       int64_t count, float2 *W, cudaStream_t st, bool out_by_point, int64_t row_mod)
 {
     if (count <= 0) return GPR_OK;
     const OzOperands *O = M->oz;
@@ -538,6 +539,7 @@ gpr_status launch_oz_w(const gpr_model *M, const GridDev &g, const float2 *Tu, c
     prm.sf2 = (float)M->kp.sf2;
     prm.W = W;
     prm.out_by_point = out_by_point ? 1 : 0;
+    prm.row_mod = row_mod > 0 ? row_mod : g.npts();
     prm.status = gpr_status_word();
     if (!prm.status) return GPR_ERR_CUDA;
     constexpr int S = 7;
@@ -554,7 +556,8 @@ gpr_status launch_oz_w(const gpr_model *M, const GridDev &g, const float2 *Tu, c
 }
 
 gpr_status launch_stats_ff(const gpr_model *M, const GridDev &g, const int64_t *pts, int64_t count, const int32_t *slot,
-                           const float2 *W, double *out15, cudaStream_t st, bool out_by_point)
+                           const float2 *W, double *out15, cudaStream_t st, bool out_by_point,
+                           int64_t row_mod)
 {
     if (count <= 0) return GPR_OK;
     Prior13 pr;
@@ -569,7 +572,8 @@ gpr_status launch_stats_ff(const gpr_model *M, const GridDev &g, const int64_t *
     {
         ProfScope ps("stats_ff", st);
         k_stats_ff<<<(unsigned)((count + 7) / 8), 256, 0, st>>>(g, pts, count, slot, W, M->mp, M->m, M->oz->vyff,
-                                                              M->kp.sf2, pr, out15, out_by_point ? 1 : 0);
+                                                              M->kp.sf2, pr, out15, out_by_point ? 1 : 0,
+                                                              row_mod > 0 ? row_mod : g.npts());
     }
     note_launch();
     GPR_CUDA_TRY(cudaGetLastError());

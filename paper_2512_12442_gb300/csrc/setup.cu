@@ -5,6 +5,9 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <atomic>
+#include <mutex>
+
 #include "internal.h"
 
 static constexpr int NB = 32;  // Cholesky block size
@@ -13,6 +16,8 @@ static int *g_status_dev = nullptr;
 
 int *gpr_status_word()
 {
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lock(mu);
     if (!g_status_dev) {
         if (cudaMalloc(&g_status_dev, sizeof(int)) != cudaSuccess) return nullptr;
         cudaMemset(g_status_dev, 0, sizeof(int));
@@ -29,12 +34,14 @@ void gpr_internal_note_cuda_error(cudaError_t e, const char *what, int line)
 
 int num_sms()
 {
-    static int n = 0;
+    static std::atomic<int> cached{0};
+    int n = cached.load();
     if (!n) {
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
         if (n <= 0) n = 1;
+        cached = n;
     }
     return n;
 }
