@@ -113,8 +113,6 @@ gpr_status grid_cache(gpr_model *M, const gpr_grid *grid, const GridDev &g, gpr_
     CA(C->Tu, te * 8);
     CA(C->mv, n * 8);
     CA(C->have_mv, n);
-    CA(C->S15, n * 15 * 8);
-    CA(C->have_S, n);
     size_t wbudget = kWCacheBudget;  // GPR_WCACHE_BUDGET_MB overrides it (tests of the uncached paths)
     if (const char *ev = getenv("GPR_WCACHE_BUDGET_MB")) wbudget = (size_t)atoll(ev) << 20;
     const size_t wb = n * (size_t)M->mp * 8;
@@ -122,10 +120,12 @@ gpr_status grid_cache(gpr_model *M, const gpr_grid *grid, const GridDev &g, gpr_
         C->wbytes = wb;
         CA(C->W, wb);
         CA(C->have_W, n);
+        CA(C->S15, n * 15 * 8);  // complete statistics: kept only beside the rows
+        CA(C->have_S, n);
         if (e != cudaSuccess) {  // no room for the rows: run without them
             cudaGetLastError();
-            cudaFree(C->W); cudaFree(C->have_W);
-            C->W = nullptr; C->have_W = nullptr;
+            cudaFree(C->W); cudaFree(C->have_W); cudaFree(C->S15); cudaFree(C->have_S);
+            C->W = nullptr; C->have_W = nullptr; C->S15 = nullptr; C->have_S = nullptr;
             g_wcache_total -= wb;
             C->wbytes = 0;
             e = cudaSuccess;
@@ -138,7 +138,7 @@ gpr_status grid_cache(gpr_model *M, const gpr_grid *grid, const GridDev &g, gpr_
         return e == cudaErrorMemoryAllocation ? GPR_ERR_OOM : GPR_ERR_CUDA;
     }
     GPR_CUDA_TRY(cudaMemsetAsync(C->have_mv, 0, n, st));
-    GPR_CUDA_TRY(cudaMemsetAsync(C->have_S, 0, n, st));
+    if (C->have_S) GPR_CUDA_TRY(cudaMemsetAsync(C->have_S, 0, n, st));
     if (C->have_W) GPR_CUDA_TRY(cudaMemsetAsync(C->have_W, 0, n, st));
     GPR_TRY(build_tables(M, g, C->T64, C->T32, st, C->Tff));
     if (oz_supported(M)) GPR_TRY(oz_unit_tables(M, g, C->Tu, st));

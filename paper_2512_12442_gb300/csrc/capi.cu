@@ -389,7 +389,7 @@ gpr_status lcp_from_kept_cells(gpr_model *M, const GridDev &g, const double *T64
     const bool use_oz = lo.exact_mode == GPR_EXACT_AUTO && oz_supported(M);
     size_t te = table_elems(M, g);
     // bound on the float-float row buffer (GPR_ROW_BUDGET_MB overrides it, for tests of the slab path)
-    size_t kRowBudget = (size_t)8 << 30;
+    size_t kRowBudget = (size_t)4 << 30;
     if (const char *e = getenv("GPR_ROW_BUDGET_MB")) kRowBudget = (size_t)atoll(e) << 20;
     if (use_oz && (size_t)npts * M->mp * 8 > kRowBudget) {
         // Planes of rows in a ring of R grid planes (row of point p at p % (R nx ny)): slab
