@@ -61,6 +61,7 @@ SIGNATURES = {
     "gpr_model_export": (C.c_int, [C.c_void_p] + [C.c_void_p] * 5),
     "gpr_stats_points_split": (C.c_int, [C.c_void_p, C.POINTER(GridC), C.c_void_p, C.c_int64, C.c_void_p,
                                          C.c_void_p]),
+    "gpr_normal_approx_eval": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]),
     "gpr_octree_trace": (C.c_int, [C.c_void_p, C.POINTER(GridC), C.c_double, C.c_int32, C.POINTER(LcpOptionsC),
                                    C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
                                    C.POINTER(C.c_int64), C.c_void_p]),

@@ -15,6 +15,7 @@
 #include <string.h>
 
 #include "internal.h"
+#include "normal_fast.cuh"
 
 namespace {
 
@@ -174,10 +175,10 @@ __global__ void k_adj_cell(GridDev g, const double *stats, const int32_t *slot, 
 #pragma unroll
                 for (int j = 0; j < i; ++j) s = fmaf(W.L[tri(i, j)], z[j], s);
                 u[i] = (sg * W.b[i] - s) * W.inv[i];
-                e[i] = normcdff(u[i]);
+                e[i] = nrm_cdf(u[i]);
                 f *= e[i];
                 if (!(f > 0.f)) { ok = false; break; }
-                if (i < 7) z[i] = normcdfinvf(fmaxf(w[i] * e[i], 1e-37f));
+                if (i < 7) z[i] = nrm_ppf(fmaxf(w[i] * e[i], 1e-37f));
             }
             if (!ok) continue;
             P[side] += f;

@@ -1,0 +1,97 @@
+#!/usr/bin/env python
+"""Writes normal_approx.h: polynomial coefficients of the estimator's single-precision
+standard normal CDF and quantile, fitted here by weighted least squares (relative error)
+against SciPy's double-precision log_ndtr and ndtri.
+
+  CDF, x = -a <= 0:  Phi(-a) = exp(-a^2/2) * G(t),  t = 1 / (1 + 0.3 a),
+                     G a degree-10 polynomial in u = 2t - 1 (a in [0, 13.2]).
+  Quantile, p in (0, 1):  z = sqrt(2) (2p - 1) E,  w = -log(4 p (1 - p)),
+                     E a degree-9 polynomial in a scaled variable on three pieces:
+                     w in [0, 5];  s = sqrt(w) in [sqrt(5), 4];  s in [4, 9.3].
+The variable w is the one of M. Giles, "Approximating the erfinv function" (GPU Computing
+Gems, 2011), written in p so that the tails keep full relative precision; the
+coefficients are this script's own fit.  Run it to regenerate the header.
+"""
+import os
+
+import numpy as np
+from scipy.special import log_ndtr, ndtri
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CDF_C0 = 0.3
+CDF_DEG = 10
+PPF_DEG = 9
+PPF_PIECES = (("w", 0.0, 5.0), ("s", float(np.sqrt(5.0)), 4.0), ("s", 4.0, 9.3))
+
+
+def fit(u, f, deg):
+    V = np.vander(u, deg + 1, increasing=True)
+    wts = 1.0 / f
+    c, *_ = np.linalg.lstsq(V * wts[:, None], f * wts, rcond=None)
+    return c
+
+
+def cdf_coeffs():
+    a = np.linspace(0.0, 13.2, 600001)
+    G = np.exp(log_ndtr(-a) + 0.5 * a * a)
+    u = 2.0 / (1.0 + CDF_C0 * a) - 1.0
+    return fit(u, G, CDF_DEG)
+
+
+def ppf_coeffs():
+    p = np.logspace(-37, np.log10(0.5), 2000001)
+    x = 1.0 - 2.0 * p
+    E = np.where(x > 0, -ndtri(p) / (np.sqrt(2.0) * np.maximum(x, 1e-300)), np.sqrt(np.pi) / 2)
+    w = -np.log(4.0 * p * (1.0 - p))
+    s = np.sqrt(w)
+    out = []
+    for var, lo, hi in PPF_PIECES:
+        v = w if var == "w" else s
+        m = (v >= lo) & (v <= hi)
+        mid, half = 0.5 * (lo + hi), 0.5 * (hi - lo)
+        out.append((mid, 1.0 / half, fit((v[m] - mid) / half, E[m], PPF_DEG)))
+    return out
+
+
+def fmt(v):
+    return f"{np.float32(v)!r}f".replace("np.float32(", "").replace(")", "")
+
+
+def horner(coeffs, var, sel=None):
+    """C expression: Horner chain in `var`; with `sel`, coefficients (a if sel else b)."""
+    def c(k):
+        if sel is None:
+            return fmt(coeffs[k])
+        return f"({sel} ? {fmt(coeffs[1][k])} : {fmt(coeffs[0][k])})"
+    n = len(coeffs if sel is None else coeffs[0])
+    expr = c(n - 1)
+    for k in range(n - 2, -1, -1):
+        expr = f"fmaf({expr}, {var}, {c(k)})"
+    return expr
+
+
+def main():
+    c = cdf_coeffs()
+    (m0, h0, p0), (m1, h1, p1), (m2, h2, p2) = ppf_coeffs()
+    lines = [
+        "// Generated by fit_normal.py (weighted least-squares fits against SciPy); do not edit.",
+        "// Standard normal CDF:  Phi(-a) = exp(-a^2/2) G(u),  u = 2/(1 + 0.3 a) - 1.",
+        "// Quantile:  z = sqrt(2) (2p - 1) E,  w = -log(4p(1-p)); E a polynomial in",
+        "//   (w - mid)/half for w < 5, else in (sqrt(w) - mid)/half on [sqrt 5, 4] or [4, 9.3].",
+        "#pragma once",
+        f"#define NRM_CDF_C0 {fmt(CDF_C0)}",
+        "static __device__ __forceinline__ float nrm_cdf_g(float u) { return " + horner(c, "u") + "; }",
+        f"static __device__ __forceinline__ float nrm_ppf_mid(float w) {{ const float v = (w - {fmt(m0)}) * {fmt(h0)}; "
+        "return " + horner(p0, "v") + "; }",
+        "static __device__ __forceinline__ float nrm_ppf_tail(float s) {",
+        "    const bool hi = s >= 4.0f;",
+        f"    const float v = (s - (hi ? {fmt(m2)} : {fmt(m1)})) * (hi ? {fmt(h2)} : {fmt(h1)});",
+        "    return " + horner((p1, p2), "v", sel="hi") + ";",
+        "}",
+    ]
+    with open(os.path.join(HERE, "normal_approx.h"), "w") as f:
+        f.write("\n".join(lines) + "\n")
+
+
+if __name__ == "__main__":
+    main()

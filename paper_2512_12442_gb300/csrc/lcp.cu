@@ -7,6 +7,7 @@
 #include <math.h>
 
 #include "internal.h"
+#include "normal_fast.cuh"
 
 namespace {
 
@@ -159,6 +160,14 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t seed, uint64_t k)
 // odd multiples of 2^-24 in (0,1): exact in binary32
 __device__ __forceinline__ float u01f(uint32_t x) { return (float)(((x >> 9) << 1) | 1u) * (1.0f / 16777216.0f); }
 
+__global__ void k_normal_eval(const float *x, int64_t n, float *cdf, float *ppf)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    cdf[i] = nrm_cdf(x[i]);
+    ppf[i] = (x[i] > 0.0f && x[i] < 1.0f) ? nrm_ppf(x[i]) : 0.0f;
+}
+
 struct Lattice {
     uint32_t G[7];
 };
@@ -203,10 +212,10 @@ __global__ void __launch_bounds__(256, 3) k_sov(const CellRec *recs, const unsig
                     float s = 0.0f;
 #pragma unroll
                     for (int j = 0; j < i; ++j) s = fmaf(L[tri(i, j)], z[j], s);
-                    float e = normcdff((sg * b[i] - s) * inv[i]);
+                    float e = nrm_cdf((sg * b[i] - s) * inv[i]);
                     f *= e;
                     if (!(f > 0.0f)) { f = 0.0f; break; }
-                    if (i < 7) z[i] = normcdfinvf(fmaxf(w[i] * e, 1e-37f));
+                    if (i < 7) z[i] = nrm_ppf(fmaxf(w[i] * e, 1e-37f));
                 }
                 if (side == 0) acc_lo += f; else acc_hi += f;
             }
@@ -590,6 +599,18 @@ gpr_status run_cell_lcp_on_scratch(const GridDev &g, const double *stats, const 
     } else {
         k_mc<<<(unsigned)blocks, 256, 0, st>>>(recs, nrec, o.n_samples, o.seed);
     }
+    note_launch();
+    GPR_CUDA_TRY(cudaGetLastError());
+    return GPR_OK;
+}
+
+// Test hook (not in the public header): the estimator's FP32 normal CDF of every x and its
+// quantile of every x in (0, 1) (0 elsewhere).  x, cdf, ppf: device, n floats.
+extern "C" gpr_status gpr_normal_approx_eval(const float *x, int64_t n, float *cdf, float *ppf, void *stream)
+{
+    if (n < 0 || (n > 0 && (!x || !cdf || !ppf))) return GPR_ERR_ARG;
+    if (n == 0) return GPR_OK;
+    k_normal_eval<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(x, n, cdf, ppf);
     note_launch();
     GPR_CUDA_TRY(cudaGetLastError());
     return GPR_OK;
