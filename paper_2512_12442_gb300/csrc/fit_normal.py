@@ -73,19 +73,24 @@ def horner(coeffs, var, sel=None):
 def main():
     c = cdf_coeffs()
     (m0, h0, p0), (m1, h1, p1), (m2, h2, p2) = ppf_coeffs()
+    r2 = np.sqrt(2.0)
+    p0, p1, p2 = p0 * r2, p1 * r2, p2 * r2  # sqrt(2) folded into the quantile polynomials
+    ln2 = np.log(2.0)
+    # central piece from lg = log2(4p(1-p)):  v = (w - mid) / half = lg * (-ln2 / half) - mid / half
     lines = [
         "// Generated by fit_normal.py (weighted least-squares fits against SciPy); do not edit.",
         "// Standard normal CDF:  Phi(-a) = exp(-a^2/2) G(u),  u = 2/(1 + 0.3 a) - 1.",
-        "// Quantile:  z = sqrt(2) (2p - 1) E,  w = -log(4p(1-p)); E a polynomial in",
+        "// Quantile:  z = (2p - 1) sqrt(2) E,  w = -log(4p(1-p)) = -ln2 lg; sqrt(2) E a polynomial in",
         "//   (w - mid)/half for w < 5, else in (sqrt(w) - mid)/half on [sqrt 5, 4] or [4, 9.3].",
         "#pragma once",
         f"#define NRM_CDF_C0 {fmt(CDF_C0)}",
+        f"#define NRM_PPF_LG_SPLIT {fmt(-5.0 / ln2)}",
         "static __device__ __forceinline__ float nrm_cdf_g(float u) { return " + horner(c, "u") + "; }",
-        f"static __device__ __forceinline__ float nrm_ppf_mid(float w) {{ const float v = (w - {fmt(m0)}) * {fmt(h0)}; "
-        "return " + horner(p0, "v") + "; }",
+        f"static __device__ __forceinline__ float nrm_ppf_mid_lg(float lg) {{ const float v = fmaf(lg, {fmt(-ln2 * h0)}, "
+        f"{fmt(-m0 * h0)}); return " + horner(p0, "v") + "; }",
         "static __device__ __forceinline__ float nrm_ppf_tail(float s) {",
         "    const bool hi = s >= 4.0f;",
-        f"    const float v = (s - (hi ? {fmt(m2)} : {fmt(m1)})) * (hi ? {fmt(h2)} : {fmt(h1)});",
+        f"    const float v = fmaf(s, hi ? {fmt(h2)} : {fmt(h1)}, hi ? {fmt(-m2 * h2)} : {fmt(-m1 * h1)});",
         "    return " + horner((p1, p2), "v", sel="hi") + ";",
         "}",
     ]

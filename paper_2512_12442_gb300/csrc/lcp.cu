@@ -172,7 +172,42 @@ struct Lattice {
     uint32_t G[7];
 };
 
-__global__ void __launch_bounds__(256, 3) k_sov(const CellRec *recs, const unsigned long long *nrec, int N,
+// Lattice coordinate |2u - 1| of u = (2k + 1) 2^-24, k = U >> 9 (odd multiples of 2^-24): from the
+// float 1 + k 2^-23, 2u - 1 = (2 (1 + k 2^-23) - 3) + 2^-23, each step exact in binary32.
+__device__ __forceinline__ float lattice_w(uint32_t U)
+{
+    const float one_k = __uint_as_float(0x3F800000u | (U >> 9));
+    return fabsf(fmaf(2.0f, one_k, -3.0f) + 1.1920929e-07f);
+}
+
+// One orthant of the SOV recursion for two samples at once (independent chains, interleaved):
+// e_i = Phi(c_i - sum_j Ls_ij z_j) with the rows pre-scaled by 1/L_ii, f = prod e_i,
+// z_i = Phi^-1(w_i e_i).  An underflowed product stays 0 (z from the clamped argument).
+__device__ __forceinline__ void sov_pair(const float (&Ls)[28], const float (&cb)[8], float sg, const float (&w0)[7],
+                                         const float (&w1)[7], float &f0, float &f1)
+{
+    float z0[7], z1[7];
+    f0 = 1.0f;
+    f1 = 1.0f;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        float a0 = sg * cb[i], a1 = a0;
+#pragma unroll
+        for (int j = 0; j < i; ++j) {
+            a0 = fmaf(-Ls[i * (i - 1) / 2 + j], z0[j], a0);
+            a1 = fmaf(-Ls[i * (i - 1) / 2 + j], z1[j], a1);
+        }
+        const float e0 = nrm_cdf(a0), e1 = nrm_cdf(a1);
+        f0 *= e0;
+        f1 *= e1;
+        if (i < 7) {
+            z0[i] = nrm_ppf(fmaxf(w0[i] * e0, 1e-37f));
+            z1[i] = nrm_ppf(fmaxf(w1[i] * e1, 1e-37f));
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256, 2) k_sov(const CellRec *recs, const unsigned long long *nrec, int N,
                                                uint64_t seed, Lattice lat)
 {
     int lane = threadIdx.x & 31;
@@ -181,11 +216,14 @@ __global__ void __launch_bounds__(256, 3) k_sov(const CellRec *recs, const unsig
     int64_t n = (int64_t)*nrec;
     for (int64_t q = warp; q < n; q += nw) {
         const CellRec &r = recs[q];
-        float L[36], b[8], inv[8];
+        float Ls[28], cb[8];
 #pragma unroll
-        for (int t = 0; t < 36; ++t) L[t] = r.L[t];
+        for (int i = 0; i < 8; ++i) {
+            const float inv = 1.0f / r.L[tri(i, i)];
+            cb[i] = r.b[i] * inv;
 #pragma unroll
-        for (int t = 0; t < 8; ++t) { b[t] = r.b[t]; inv[t] = 1.0f / L[tri(t, t)]; }
+            for (int j = 0; j < i; ++j) Ls[i * (i - 1) / 2 + j] = r.L[tri(i, j)] * inv;
+        }
         const uint64_t cellid = (uint64_t)r.cell & ((1ull << 56) - 1);
         const int skip = (int)((uint64_t)r.cell >> 56);
         uint32_t D = 0;
@@ -194,30 +232,21 @@ __global__ void __launch_bounds__(256, 3) k_sov(const CellRec *recs, const unsig
 #pragma unroll
         for (int i = 0; i < 7; ++i) Ds[i] = __shfl_sync(0xffffffffu, D, i);
         float acc_lo = 0.f, acc_hi = 0.f;  // <= 50 samples per lane: FP32 sums are exact to ~1e-7
-        for (int k = lane; k < N; k += 32) {
-            float w[7];
+        for (int k = lane; k < N; k += 64) {
+            const bool two = k + 32 < N;
+            float w0[7], w1[7];
 #pragma unroll
             for (int i = 0; i < 7; ++i) {
-                uint32_t U = (uint32_t)k * lat.G[i] + Ds[i];
-                w[i] = fabsf(2.0f * u01f(U) - 1.0f);
+                w0[i] = lattice_w((uint32_t)k * lat.G[i] + Ds[i]);
+                w1[i] = lattice_w((uint32_t)(k + 32) * lat.G[i] + Ds[i]);
             }
-#pragma unroll
-            for (int side = 0; side < 2; ++side) {
+#pragma unroll 1
+            for (int side = 0; side < 2; ++side) {  // one copy of the recursion (instruction cache)
                 if (skip & (1 << side)) continue;
-                float sg = side == 0 ? 1.0f : -1.0f;
-                float z[7];
-                float f = 1.0f;
-#pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    float s = 0.0f;
-#pragma unroll
-                    for (int j = 0; j < i; ++j) s = fmaf(L[tri(i, j)], z[j], s);
-                    float e = nrm_cdf((sg * b[i] - s) * inv[i]);
-                    f *= e;
-                    if (!(f > 0.0f)) { f = 0.0f; break; }
-                    if (i < 7) z[i] = nrm_ppf(fmaxf(w[i] * e, 1e-37f));
-                }
-                if (side == 0) acc_lo += f; else acc_hi += f;
+                float f0, f1;
+                sov_pair(Ls, cb, side ? -1.0f : 1.0f, w0, w1, f0, f1);
+                const float f = two ? f0 + f1 : f0;
+                if (side) acc_hi += f; else acc_lo += f;
             }
         }
 #pragma unroll
