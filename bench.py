@@ -32,9 +32,12 @@ import numpy as np  # noqa: E402
 import workloads  # noqa: E402
 
 METRIC = "LCP grid points/s"
-# FP32 FLOPs executed by k_sov per estimated cell (1600 samples x 2 orthants), from the ncu
-# instruction counters of the small case; see the k_sov profile summary under profiles/.
-SOV_FP32_FLOPS_PER_CELL = 2.1255e6
+# Warp instructions k_sov issues per estimated cell (1600 lattice points, both orthants unless the
+# Frechet test drops one), from the ncu counters of the small case (sov_estimator profile summary).
+# The estimator is issue-bound: its roofline is the issue rate, 4 warp instructions per clock on
+# each of 152 SMs at 2.07 GHz.
+SOV_WARP_INST_PER_CELL = 35988.0
+ISSUE_PEAK_GINST = 152 * 4 * 2.07
 UNIT = "grid points/s"
 
 
@@ -267,10 +270,10 @@ def run_batched(args, g, torch, rank, world, local):
     if n_launch > 0:
         # the shared estimator runs alone on the caller's stream after every field's octree
         avg_s = c / n_launch / 1e3
-        flops = SOV_FP32_FLOPS_PER_CELL * est / (n_launch / args.steps)
-        roof = {"bound": "alu", "achieved": flops / avg_s / 1e12, "peak": 73.07, "unit": "TFLOP/s", "traffic": None,
-                "kernel": "k_sov (SOV-QMC estimator over every field's cells, one persistent launch)",
-                "peak_source": "FP32 FMA probe (73.07 TFLOP/s measured on this GB300 model)"}
+        inst = SOV_WARP_INST_PER_CELL * est / (n_launch / args.steps)
+        roof = {"bound": "alu", "achieved": inst / avg_s / 1e9, "peak": ISSUE_PEAK_GINST, "unit": "Gwarp-inst/s",
+                "traffic": None, "kernel": "k_sov (SOV-QMC estimator over every field's cells, one persistent launch)",
+                "peak_source": "issue rate 4 warp-inst/clk x 152 SMs x 2.07 GHz (recipe unit counts and clock)"}
         roof["frac"] = roof["achieved"] / roof["peak"]
     cpu = None
     if not args.no_cpu_baseline:
@@ -438,12 +441,10 @@ def main():
                     "traffic": None, "kernel": "k_oz_w (FP64-class whitening GEMM, BF16 digit split)",
                     "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained"}
         elif dom == "sov":
-            # FP32-pipe FLOPs executed per estimated cell (ncu instruction counters of k_sov on the small case:
-            # 2 x ffma + fadd + fmul thread-instructions per cell); MUFU and integer work are not counted
-            flops = SOV_FP32_FLOPS_PER_CELL * est_cells / nfield
-            roof = {"bound": "alu", "achieved": flops / avg_s / 1e12, "peak": 73.07, "unit": "TFLOP/s",
+            inst = SOV_WARP_INST_PER_CELL * est_cells / nfield
+            roof = {"bound": "alu", "achieved": inst / avg_s / 1e9, "peak": ISSUE_PEAK_GINST, "unit": "Gwarp-inst/s",
                     "traffic": None, "kernel": "k_sov (SOV-QMC estimator, FP32)",
-                    "peak_source": "FP32 FMA probe (73.07 TFLOP/s measured on this GB300 model)"}
+                    "peak_source": "issue rate 4 warp-inst/clk x 152 SMs x 2.07 GHz (recipe unit counts and clock)"}
         if roof:
             roof["frac"] = roof["achieved"] / roof["peak"]
     cpu = None if args.no_cpu_baseline else cpu_baseline(w, w.isovalues[1], args.cpu_sample)
