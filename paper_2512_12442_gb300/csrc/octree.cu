@@ -427,20 +427,20 @@ __global__ void k_scatter_lattice(const float4 *ev, const int64_t *ulist, int64_
 }
 
 // Start points (best lattice point per side) as evaluation points, for their gradients.
-__global__ void k_start_points(const MinState *ms, int64_t npend, int64_t first, int64_t cnt, double *xyz)
+__global__ void k_start_points(const MinState *ms, const int64_t *act, int64_t first, int64_t cnt, double *xyz)
 {
     int64_t le = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (le >= cnt) return;
-    int64_t e = first + le, q = e / 2;
+    int64_t e = first + le, q = act[e / 2];
     int side = (int)(e % 2);
     for (int d = 0; d < 3; ++d) xyz[3 * le + d] = ms[q].x[side][d];
 }
 
-__global__ void k_start_grad(const float4 *ev, int64_t first, int64_t cnt, MinState *ms)
+__global__ void k_start_grad(const float4 *ev, const int64_t *act, int64_t first, int64_t cnt, MinState *ms)
 {
     int64_t le = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (le >= cnt) return;
-    int64_t e = first + le, q = e / 2;
+    int64_t e = first + le, q = act[e / 2];
     int side = (int)(e % 2);
     float sg = side == 0 ? 1.f : -1.f;
     ms[q].g[side] = sg * ev[le].x;
@@ -485,13 +485,13 @@ __global__ void k_lattice_coords(GridDev g, int D, int l, const int64_t *nodes, 
 }
 
 // Candidate of projected step t for every (node, side): x' = clamp(x + eta_t w u/|u|_inf), u = -grad g * w.
-__global__ void k_candidates(GridDev g, int D, int l, const int64_t *nodes, const int64_t *pend, int64_t npend,
+__global__ void k_candidates(GridDev g, int D, int l, const int64_t *nodes, const int64_t *pend, const int64_t *act,
                              const MinState *ms, int step, int64_t first, int64_t cnt, double *xyz, uint8_t *valid)
 {
     int64_t le = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (le >= cnt) return;
     int64_t e = first + le;
-    int64_t q = e / 2;
+    int64_t q = act[e / 2];
     int side = (int)(e % 2);
     Geom G = node_geom(g, D, l, nodes[pend[q]]);
     double w[3], u[3], un = 0.0;
@@ -508,13 +508,13 @@ __global__ void k_candidates(GridDev g, int D, int l, const int64_t *nodes, cons
     valid[le] = un > 0.0 ? 1 : 0;
 }
 
-__global__ void k_accept(const double *xyz, const uint8_t *valid, const float4 *ev, int64_t first, int64_t cnt,
-                         MinState *ms)
+__global__ void k_accept(const double *xyz, const uint8_t *valid, const float4 *ev, const int64_t *act, int64_t first,
+                         int64_t cnt, MinState *ms)
 {
     int64_t le = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (le >= cnt) return;
     int64_t e = first + le;
-    int64_t q = e / 2;
+    int64_t q = act[e / 2];
     int side = (int)(e % 2);
     if (!valid[le]) return;
     float sg = side == 0 ? 1.f : -1.f;
@@ -528,17 +528,24 @@ __global__ void k_accept(const double *xyz, const uint8_t *valid, const float4 *
     }
 }
 
-__global__ void k_large_bound(GridDev g, int D, int l, const int64_t *nodes, const int64_t *pend, int64_t npend,
-                              const MinState *ms, double alpha, int8_t *decision, const int8_t *sides, double *bound)
+// Bound of each listed pending node from its current minima (act: positions in the pending list;
+// nullptr = every pending node).  With `active`, nodes whose bound already exceeds alpha are
+// decided (subdivide: the minimiser only lowers g, which only raises the bound) and the others
+// are flagged for the minimiser.
+__global__ void k_large_bound(GridDev g, int D, int l, const int64_t *nodes, const int64_t *pend, const int64_t *act,
+                              int64_t cnt, const MinState *ms, double alpha, int8_t *decision, const int8_t *sides,
+                              double *bound, uint8_t *active)
 {
-    int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (q >= npend) return;
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= cnt) return;
+    const int64_t q = act ? act[t] : t;
     int64_t node = pend[q];
     Geom G = node_geom(g, D, l, nodes[node]);
     double dcount = (double)((G.p1[0] - G.p0[0] + 1) * (G.p1[1] - G.p0[1] + 1) * (G.p1[2] - G.p0[2] + 1));
     double bnd = bound_of(sides[node], dcount, (double)ms[q].g[0], (double)ms[q].g[1]);
     bound[node] = bnd;
     decision[node] = bnd > alpha ? 2 : 0;
+    if (active) active[q] = bnd > alpha ? 0 : 1;
 }
 
 // Subdivided nodes -> children (next frontier) or, at the last level, cells of S.
@@ -751,29 +758,39 @@ gpr_status octree_lcp(gpr_model *M, const gpr_grid *grid, double theta, int D, c
                 note_launch();
                 k_lattice_coords<<<nb(npend, 128), 128, 0, st>>>(g, D, l, nodes, B.pend, npend, B.ms);
                 note_launch();
+                // nodes whose lattice minima already give a bound above alpha are decided; the
+                // minimiser runs on the others (the act list)
+                k_large_bound<<<nb(npend, 128), 128, 0, st>>>(g, D, l, nodes, B.pend, nullptr, npend, B.ms, opts->alpha,
+                                                             B.decision, B.sides, B.bound, B.unal);
+                note_launch();
+                int64_t nact = 0;
+                GPR_TRY(compact_flags(B.unal, npend, B.ulist, nullptr, &nact, B.cscr, B.csb, st));
+                const int64_t *act = B.ulist;
                 // g and its gradient at the start point of each side
-                for (int64_t first = 0; first < 2 * npend; first += kEvalChunk) {
-                    int64_t cnt = 2 * npend - first < kEvalChunk ? 2 * npend - first : kEvalChunk;
-                    k_start_points<<<nb(cnt, 256), 256, 0, st>>>(B.ms, npend, first, cnt, B.xyz);
+                for (int64_t first = 0; first < 2 * nact; first += kEvalChunk) {
+                    int64_t cnt = 2 * nact - first < kEvalChunk ? 2 * nact - first : kEvalChunk;
+                    k_start_points<<<nb(cnt, 256), 256, 0, st>>>(B.ms, act, first, cnt, B.xyz);
                     note_launch();
                     GPR_TRY(run_eval(M, E, B, cnt, theta, st));
-                    k_start_grad<<<nb(cnt, 256), 256, 0, st>>>(B.ev, first, cnt, B.ms);
+                    k_start_grad<<<nb(cnt, 256), 256, 0, st>>>(B.ev, act, first, cnt, B.ms);
                     note_launch();
                 }
-                for (int t = 0; t < T; ++t) {
-                    for (int64_t first = 0; first < 2 * npend; first += kEvalChunk) {
-                        int64_t cnt = 2 * npend - first < kEvalChunk ? 2 * npend - first : kEvalChunk;
-                        k_candidates<<<nb(cnt, 256), 256, 0, st>>>(g, D, l, nodes, B.pend, npend, B.ms, t, first, cnt,
+                for (int t = 0; t < T && nact > 0; ++t) {
+                    for (int64_t first = 0; first < 2 * nact; first += kEvalChunk) {
+                        int64_t cnt = 2 * nact - first < kEvalChunk ? 2 * nact - first : kEvalChunk;
+                        k_candidates<<<nb(cnt, 256), 256, 0, st>>>(g, D, l, nodes, B.pend, act, B.ms, t, first, cnt,
                                                                    B.xyz, B.cvalid);
                         note_launch();
                         GPR_TRY(run_eval(M, E, B, cnt, theta, st));
-                        k_accept<<<nb(cnt, 256), 256, 0, st>>>(B.xyz, B.cvalid, B.ev, first, cnt, B.ms);
+                        k_accept<<<nb(cnt, 256), 256, 0, st>>>(B.xyz, B.cvalid, B.ev, act, first, cnt, B.ms);
                         note_launch();
                     }
                 }
-                k_large_bound<<<nb(npend, 128), 128, 0, st>>>(g, D, l, nodes, B.pend, npend, B.ms, opts->alpha,
-                                                             B.decision, B.sides, B.bound);
-                note_launch();
+                if (nact > 0) {
+                    k_large_bound<<<nb(nact, 128), 128, 0, st>>>(g, D, l, nodes, B.pend, act, nact, B.ms, opts->alpha,
+                                                                 B.decision, B.sides, B.bound, nullptr);
+                    note_launch();
+                }
             }
         }
         GPR_CUDA_TRY(cudaMemsetAsync(B.counters, 0, 2 * sizeof(unsigned long long), st));
