@@ -147,7 +147,7 @@ __global__ void k_eval_reduce(EvalModel E, const double *xyz, const float *W, co
     if (q >= count) return;
     float x = (float)xyz[3 * q], y = (float)xyz[3 * q + 1], z = (float)xyz[3 * q + 2];
     float wsq = 0.f, mu_h = 0.f, mu_l = 0.f, gm[3] = {0, 0, 0}, gv[3] = {0, 0, 0};
-    const float *wr = W + q * E.mp, *pr = P + q * E.mp;
+    const float *wr = W + q * E.mp, *pr = P ? P + q * E.mp : nullptr;  // no P: value only (gradient of mu)
     float il2[3] = {1.f / (E.ell[0] * E.ell[0]), 1.f / (E.ell[1] * E.ell[1]), 1.f / (E.ell[2] * E.ell[2])};
     for (int64_t j = lane; j < E.m; j += 32) {
         float w = wr[j];
@@ -163,7 +163,7 @@ __global__ void k_eval_reduce(EvalModel E, const double *xyz, const float *W, co
             k = E.sf2 * (1.0f + s5r + (5.0f / 3.0f) * r2) * e;
             c = -(5.0f / 3.0f) * E.sf2 * (1.0f + s5r) * e;
         }
-        float a = E.alpha32[j], pj = pr[j];
+        float a = E.alpha32[j], pj = pr ? pr[j] : 0.f;
         // compensated accumulation of mu (terms k*alpha reach ~1e3 for an O(1) result)
         float term = k * a, s = mu_h + term, bv = s - mu_h;
         mu_l += (mu_h - (s - bv)) + (term - bv);
@@ -258,35 +258,78 @@ __global__ void k_obs_flags(const double *mu_obs, const double *var_obs, int64_t
 
 // p-test (warp per node).  decision: 1 = subdivide (p1 > alpha and p2 > alpha), 0 = bound needed;
 // sides: bit0 lower bound B_l, bit1 upper bound B_u.
-__global__ void k_ptest(GridDev g, int D, int l, const int64_t *nodes, int64_t count, const double *X, int64_t m,
-                        const uint8_t *flags, int8_t *decision, int8_t *sides)
+// p-test flags of the octree's nodes at every level, as a pyramid of bytes (bit 2: the node
+// holds an observation, bit 0 / bit 1: one with P(Y_i < t) > alpha / P(Y_i > t) > alpha).  The
+// finest level has one word per cell; an observation marks every cell whose closed box holds
+// it (two per axis on a shared face), with the box edges lo + c h of the node geometry, so the
+// OR over a node's cells is exactly "some observation lies in the node's closed box".
+struct Pyramid {
+    int64_t off[21];     // byte offset of level l in the level buffer
+    int32_t dim[21][3];  // nodes per axis at level l: ceil((n_d - 1) / 2^(D - l))
+};
+
+__global__ void k_obs_cells(GridDev g, const double *X, int64_t m, const uint8_t *flags, uint32_t *fine)
 {
-    int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    int64_t q = blockIdx.x * (int64_t)(blockDim.x / 32) + warp;
-    if (q >= count) return;
-    Geom G = node_geom(g, D, l, nodes[q]);
-    bool any = false, lo = false, hi = false;
-    for (int64_t i = lane; i < m; i += 32) {
-        const double *x = X + 3 * i;
-        bool in = x[0] >= G.blo[0] && x[0] <= G.bhi[0] && x[1] >= G.blo[1] && x[1] <= G.bhi[1] && x[2] >= G.blo[2] &&
-                  x[2] <= G.bhi[2];
-        if (in) {
-            any = true;
-            lo = lo || (flags[i] & 1);
-            hi = hi || (flags[i] & 2);
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    int64_t cand[3][2];
+    int cnt[3];
+    for (int d = 0; d < 3; ++d) {
+        const double x = X[3 * i + d];
+        const int64_t ncd = g.n[d] - 1;
+        const double t = (x - g.lo[d]) / g.h[d];
+        cnt[d] = 0;
+        if (!(t >= -2.0 && t <= (double)ncd + 2.0)) return;  // outside the grid (or NaN)
+        const int64_t c = (int64_t)floor(t);
+        for (int64_t cc = c - 1; cc <= c + 1; ++cc) {
+            if (cc < 0 || cc >= ncd || cnt[d] == 2) continue;
+            if (x >= g.lo[d] + (double)cc * g.h[d] && x <= g.lo[d] + (double)(cc + 1) * g.h[d]) cand[d][cnt[d]++] = cc;
         }
+        if (cnt[d] == 0) return;
     }
-    any = __any_sync(0xffffffffu, any);
-    lo = __any_sync(0xffffffffu, lo);
-    hi = __any_sync(0xffffffffu, hi);
-    if (lane == 0) {
-        if (any && lo && hi) {
-            decision[q] = 1;
-            sides[q] = 0;
-        } else {
-            decision[q] = 0;
-            sides[q] = (!any || (!lo && !hi)) ? 3 : (!hi ? 1 : 2);
-        }
+    const uint32_t v = 4u | (flags[i] & 3u);
+    const int64_t cx = g.n[0] - 1, cy = g.n[1] - 1;
+    for (int a = 0; a < cnt[0]; ++a)
+        for (int b = 0; b < cnt[1]; ++b)
+            for (int c = 0; c < cnt[2]; ++c) atomicOr(&fine[cand[0][a] + cx * (cand[1][b] + cy * cand[2][c])], v);
+}
+
+__global__ void k_cells_to_bytes(const uint32_t *fine, int64_t n, uint8_t *out)
+{
+    int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q < n) out[q] = (uint8_t)fine[q];
+}
+
+template <typename TC>
+__global__ void k_pyr_level(const TC *child, int32_t c0, int32_t c1, int32_t c2, uint8_t *parent, int32_t p0,
+                            int32_t p1, int32_t p2)
+{
+    int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= (int64_t)p0 * p1 * p2) return;
+    const int64_t i = q % p0, j = (q / p0) % p1, k = q / ((int64_t)p0 * p1);
+    uint32_t v = 0;
+    for (int b = 0; b < 8; ++b) {
+        const int64_t a0 = 2 * i + (b & 1), a1 = 2 * j + ((b >> 1) & 1), a2 = 2 * k + (b >> 2);
+        if (a0 < c0 && a1 < c1 && a2 < c2) v |= (uint32_t)child[a0 + (int64_t)c0 * (a1 + (int64_t)c1 * a2)];
+    }
+    parent[q] = (uint8_t)v;
+}
+
+__global__ void k_ptest(GridDev g, int D, int l, const int64_t *nodes, int64_t count, const uint8_t *lvl,
+                        int32_t d0, int32_t d1, int8_t *decision, int8_t *sides)
+{
+    int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= count) return;
+    const int64_t code = nodes[q];
+    const int64_t i = code & 0x1FFFFF, j = (code >> 21) & 0x1FFFFF, k = (code >> 42) & 0x1FFFFF;
+    const uint32_t v = lvl[i + (int64_t)d0 * (j + (int64_t)d1 * k)];
+    const bool any = v & 4, lo = v & 1, hi = v & 2;
+    if (any && lo && hi) {
+        decision[q] = 1;
+        sides[q] = 0;
+    } else {
+        decision[q] = 0;
+        sides[q] = (!any || (!lo && !hi)) ? 3 : (!hi ? 1 : 2);
     }
 }
 
@@ -610,7 +653,7 @@ struct OctTrace {
 };
 
 static gpr_status run_eval(const gpr_model *M, const EvalModel &E, OctBuffers &B, int64_t cnt, double theta,
-                           cudaStream_t st)
+                           cudaStream_t st, bool grad = true)
 {
     dim3 grid((unsigned)(M->mp / BN), nb(cnt, BM));
     {
@@ -618,9 +661,11 @@ static gpr_status run_eval(const gpr_model *M, const EvalModel &E, OctBuffers &B
         k_eval_w<<<grid, NT, 0, st>>>(E, B.xyz, cnt, B.W);
     }
     note_launch();
-    k_eval_p<<<grid, NT, 0, st>>>(E, B.W, cnt, B.P);
-    note_launch();
-    k_eval_reduce<<<nb(cnt, 8), 256, 0, st>>>(E, B.xyz, B.W, B.P, cnt, theta, B.ev);
+    if (grad) {
+        k_eval_p<<<grid, NT, 0, st>>>(E, B.W, cnt, B.P);
+        note_launch();
+    }
+    k_eval_reduce<<<nb(cnt, 8), 256, 0, st>>>(E, B.xyz, B.W, grad ? B.P : nullptr, cnt, theta, B.ev);
     note_launch();
     GPR_CUDA_TRY(cudaGetLastError());
     return GPR_OK;
@@ -646,7 +691,8 @@ gpr_status octree_lcp(gpr_model *M, const gpr_grid *grid, double theta, int D, c
                    Carver::round((size_t)kEvalChunk * 16) + Carver::round((size_t)kEvalChunk) +
                    Carver::round((size_t)nc * sizeof(MinState)) + Carver::round((size_t)max_large * 27 * 16) + 512 +
                    csb + Carver::round(tc_partial_elems(GPR_P_BF16X3, M, n) * 4) + Carver::round((size_t)max_large) +
-                   Carver::round((size_t)max_large * 8) + 8192;
+                   Carver::round((size_t)max_large * 8) + 8192 + Carver::round((size_t)nc * 4) + 2 * Carver::round((size_t)nc) +
+                   256 * 22;
     gpr_precision pp = opts->prec == GPR_P_FP64 ? GPR_P_FP32 : opts->prec;
     GridCache *C = nullptr;
     GPR_TRY(grid_cache(M, grid, g, pp, &C, st));
@@ -662,6 +708,16 @@ gpr_status octree_lcp(gpr_model *M, const gpr_grid *grid, double theta, int D, c
     B.sides = cv.take<int8_t>((size_t)nc);
     B.bound = cv.take<double>((size_t)nc);
     B.obs_flags = cv.take<uint8_t>((size_t)m);
+    Pyramid pyr;
+    int64_t pyr_bytes = 0;
+    for (int l = D; l >= 0; --l) {
+        const int64_t s = (int64_t)1 << (D - l);
+        for (int d = 0; d < 3; ++d) pyr.dim[l][d] = (int32_t)((g.n[d] - 1 + s - 1) / s);
+        pyr.off[l] = pyr_bytes;
+        pyr_bytes += Carver::round((size_t)pyr.dim[l][0] * pyr.dim[l][1] * pyr.dim[l][2]);
+    }
+    uint32_t *pyr_fine = cv.take<uint32_t>((size_t)nc);
+    uint8_t *pyr_lv = cv.take<uint8_t>((size_t)pyr_bytes);
     B.need = cv.take<uint8_t>((size_t)n);
     uint8_t *pflag = cv.take<uint8_t>((size_t)n);
     B.lflag = cv.take<uint8_t>((size_t)nc);
@@ -696,6 +752,21 @@ gpr_status octree_lcp(gpr_model *M, const gpr_grid *grid, double theta, int D, c
     GPR_CUDA_TRY(cudaMemsetAsync(B.leaf, 0, (size_t)nc, st));
     k_obs_flags<<<nb(m, 128), 128, 0, st>>>(M->mu_obs, M->var_obs, m, theta, opts->alpha, B.obs_flags);
     note_launch();
+    GPR_CUDA_TRY(cudaMemsetAsync(pyr_fine, 0, sizeof(uint32_t) * (size_t)nc, st));
+    k_obs_cells<<<nb(m, 128), 128, 0, st>>>(g, M->X, m, B.obs_flags, pyr_fine);
+    note_launch();
+    for (int l = D; l >= 0; --l) {  // level D from the words of the cells, then halving
+        const int32_t *pd = pyr.dim[l];
+        const int64_t np = (int64_t)pd[0] * pd[1] * pd[2];
+        if (l == D) {
+            k_cells_to_bytes<<<nb(np, 256), 256, 0, st>>>(pyr_fine, np, pyr_lv + pyr.off[l]);
+        } else {
+            const int32_t *cd = pyr.dim[l + 1];
+            k_pyr_level<uint8_t><<<nb(np, 256), 256, 0, st>>>(pyr_lv + pyr.off[l + 1], cd[0], cd[1], cd[2],
+                                                              pyr_lv + pyr.off[l], pd[0], pd[1], pd[2]);
+        }
+        note_launch();
+    }
     int64_t root = 0;
     GPR_CUDA_TRY(cudaMemcpyAsync(B.front[0], &root, sizeof root, cudaMemcpyHostToDevice, st));
     int64_t count = 1;
@@ -705,7 +776,8 @@ gpr_status octree_lcp(gpr_model *M, const gpr_grid *grid, double theta, int D, c
         const int64_t *nodes = B.front[cur];
         int64_t s = (int64_t)1 << (D - l);
         ProfScope lvl("oct_level", st);
-        k_ptest<<<nb(count, 8), 256, 0, st>>>(g, D, l, nodes, count, M->X, m, B.obs_flags, B.decision, B.sides);
+        k_ptest<<<nb(count, 256), 256, 0, st>>>(g, D, l, nodes, count, pyr_lv + pyr.off[l], pyr.dim[l][0],
+                                                 pyr.dim[l][1], B.decision, B.sides);
         note_launch();
         // small nodes: exact minimum over grid points from the per-point table
         {
@@ -750,7 +822,8 @@ gpr_status octree_lcp(gpr_model *M, const gpr_grid *grid, double theta, int D, c
                     int64_t cnt = nun * 27 - first < kEvalChunk ? nun * 27 - first : kEvalChunk;
                     k_lattice_points<<<nb(cnt, 256), 256, 0, st>>>(g, D, l, nodes, B.pend, B.ulist, first, cnt, B.xyz);
                     note_launch();
-                    GPR_TRY(run_eval(M, E, B, cnt, theta, st));
+                    // lattice values only: the start points' gradients are evaluated afresh below
+                    GPR_TRY(run_eval(M, E, B, cnt, theta, st, false));
                     k_scatter_lattice<<<nb(cnt, 256), 256, 0, st>>>(B.ev, B.ulist, first, cnt, B.lat);
                     note_launch();
                 }
