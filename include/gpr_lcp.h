@@ -276,6 +276,17 @@ gpr_status gpr_cell_lcp_from_stats_noalloc(const gpr_grid *grid, const double *s
 gpr_status gpr_lcp_backward(gpr_model *model, const gpr_grid *grid, double isovalue, const gpr_lcp_options *opts,
                             const float *dL_dlcp, double *dL_dy, double *dL_dloglen, void *stream);
 
+/* ---- Autotuner (no counterpart in the paper).  Launches with interchangeable shapes (the
+ * tensor-core pre-pass tile width per precision, the estimator's CTAs per SM) are timed on
+ * first use per (kernel, size bucket) and the fastest is kept for the process; the choice never
+ * changes results.  GPR_AUTOTUNE=0 disables timing (first alternative always);
+ * GPR_TUNE_FILE=<path> loads the table at first use and rewrites it on every new entry.
+ * gpr_autotune_table writes the table as "kernel bucket choice" lines into buf (host, len
+ * bytes, NUL-terminated, truncated if short) and returns the full length. */
+int64_t gpr_autotune_table(char *buf, int64_t len);
+/* Forgets every tuned choice. */
+void gpr_autotune_clear(void);
+
 /* Waits for `stream` and returns the first device-side error recorded by any
  * model since the last call (GPR_OK if none). */
 gpr_status gpr_sync(void *stream);

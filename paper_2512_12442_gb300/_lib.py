@@ -57,11 +57,14 @@ SIGNATURES = {
     "gpr_profile_reset": (None, []),
     "gpr_profile_read": (C.c_int, [C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     "gpr_launch_count": (C.c_int64, []),
+    "gpr_autotune_table": (C.c_int64, [C.c_char_p, C.c_int64]),
+    "gpr_autotune_clear": (None, []),
     # test hooks (not in the public header)
     "gpr_model_export": (C.c_int, [C.c_void_p] + [C.c_void_p] * 5),
     "gpr_stats_points_split": (C.c_int, [C.c_void_p, C.POINTER(GridC), C.c_void_p, C.c_int64, C.c_void_p,
                                          C.c_void_p]),
     "gpr_normal_approx_eval": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "gpr_autotune_force": (None, [C.c_char_p, C.c_int]),
     "gpr_octree_trace": (C.c_int, [C.c_void_p, C.POINTER(GridC), C.c_double, C.c_int32, C.POINTER(LcpOptionsC),
                                    C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
                                    C.POINTER(C.c_int64), C.c_void_p]),

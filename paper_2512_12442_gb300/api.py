@@ -236,5 +236,22 @@ def gpr_profile_read(name: str):
     return t.value, n.value
 
 
+def gpr_autotune_table() -> dict:
+    """The autotuner's choices: {(kernel, bucket): choice}."""
+    lib = load()
+    n = int(lib.gpr_autotune_table(None, 0))
+    buf = C.create_string_buffer(n + 1)
+    lib.gpr_autotune_table(buf, n + 1)
+    out = {}
+    for line in buf.value.decode().splitlines():
+        k, b, c = line.split()
+        out[(k, int(b))] = int(c)
+    return out
+
+
+def gpr_autotune_clear() -> None:
+    load().gpr_autotune_clear()
+
+
 def gpr_launch_count() -> int:
     return int(load().gpr_launch_count())

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <atomic>
+#include <functional>
 #include <vector>
 
 #include "../../include/gpr_lcp.h"
@@ -140,6 +141,14 @@ void launch_mean_compensated(const gpr_model *M, const GridDev &g, const float2 
 // Fused FP32 mean/variance (W never stored).
 void launch_meanvar32(const gpr_model *M, const GridDev &g, const float *T32, const int64_t *pts, int64_t pt_base,
                       int64_t count, float *mean, float *var, cudaStream_t st);
+
+// ---- launch-shape autotuner (tune.cu)
+// Smallest power of two >= v (at least 64): the size bucket of a tuned launch.
+int64_t tune_bucket(int64_t v);
+// Runs alternative `choice` of a launch with equal results; on the first use of (name, bucket)
+// all `ncand` alternatives are timed on `st` and the fastest is kept (and queued last).
+gpr_status tune_run(const char *name, int64_t bucket, int ncand, const std::function<gpr_status(int)> &run,
+                    cudaStream_t st);
 
 // ---- tensor cores (tc.cu)
 bool tc_precision(gpr_precision p);

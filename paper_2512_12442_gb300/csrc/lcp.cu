@@ -349,18 +349,25 @@ size_t record_bytes() { return sizeof(CellRec); }
 void launch_estimator(const void *recs, const unsigned long long *nrec, int64_t max_records, const LcpOpts &o,
                       cudaStream_t st)
 {
-    int64_t blocks = (max_records + 7) / 8;  // one warp per record, persistent over the device count
-    if (blocks > (int64_t)num_sms() * 16) blocks = (int64_t)num_sms() * 16;
-    if (blocks < 1) blocks = 1;
-    if (o.est == GPR_EST_SOV_QMC) {
-        static Lattice lat = make_lattice();
-        ProfScope _ps("sov", st);
-        k_sov<<<(unsigned)blocks, 256, 0, st>>>((const CellRec *)recs, nrec, o.n_samples, o.seed, lat);
-    } else {
-        ProfScope _ps("mc", st);
-        k_mc<<<(unsigned)blocks, 256, 0, st>>>((const CellRec *)recs, nrec, o.n_samples, o.seed);
-    }
-    note_launch();
+    // one warp per record, persistent over the device count; CTAs per SM chosen by the autotuner
+    static const int per_sm[3] = {2, 4, 16};
+    auto run = [&](int c) -> gpr_status {
+        int64_t blocks = (max_records + 7) / 8;
+        if (blocks > (int64_t)num_sms() * per_sm[c]) blocks = (int64_t)num_sms() * per_sm[c];
+        if (blocks < 1) blocks = 1;
+        if (o.est == GPR_EST_SOV_QMC) {
+            static Lattice lat = make_lattice();
+            ProfScope _ps("sov", st);
+            k_sov<<<(unsigned)blocks, 256, 0, st>>>((const CellRec *)recs, nrec, o.n_samples, o.seed, lat);
+        } else {
+            ProfScope _ps("mc", st);
+            k_mc<<<(unsigned)blocks, 256, 0, st>>>((const CellRec *)recs, nrec, o.n_samples, o.seed);
+        }
+        note_launch();
+        GPR_CUDA_TRY(cudaGetLastError());
+        return GPR_OK;
+    };
+    tune_run(o.est == GPR_EST_SOV_QMC ? "sov_ctas_per_sm" : "mc_ctas_per_sm", tune_bucket(max_records), 3, run, st);
 }
 
 gpr_status run_cell_lcp(const GridDev &g, const double *stats, const int32_t *slot, const int64_t *cells,

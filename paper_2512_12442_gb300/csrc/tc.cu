@@ -152,18 +152,23 @@ struct TcParams {
     GridDev g;
     const int64_t *pts;
     int64_t pt_base, count;
-    float *partial;  // count x nN partial sums of w^2
+    float *partial;  // count x nN partial sums of w^2, one per 64 columns
+    int64_t plen;    // floats in `partial` (bounds self-check)
+    int64_t tlen;    // floats in T32 (bounds self-check)
     int nN;
     int *status;
 };
 
-template <int P>
+// N: output columns per tile (64, 128 or 256; chosen per model size by the autotuner).  The
+// squares are summed per 32-column chunk and paired into 64-column partials, the same grouping
+// for every N, so all tile widths give the same bits.
+template <int P, int N>
 __global__ void __launch_bounds__(NTHR, 1) k_tc_sumsq(const __grid_constant__ CUtensorMap mapB0,
                                                      const __grid_constant__ CUtensorMap mapB1,
                                                      const __grid_constant__ CUtensorMap mapB2, TcParams prm)
 {
     using C = Cfg<P>;
-    constexpr int N = C::N, BKE = C::BKE;
+    constexpr int BKE = C::BKE;
     constexpr int A_TILE = TM * 128;   // bytes per A slice per stage
     constexpr int B_TILE = N * 128;    // bytes per B slice per stage
     constexpr int STAGE = C::NA * A_TILE + C::NB * B_TILE;
@@ -173,7 +178,7 @@ __global__ void __launch_bounds__(NTHR, 1) k_tc_sumsq(const __grid_constant__ CU
     __shared__ uint32_t tmem_slot;
     __shared__ int gx[TM], gy[TM], gz[TM];
     __shared__ bool rvalid[TM];
-    __shared__ float red[2][TM];
+    __shared__ float red[N / 32][TM];
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t row0 = (int64_t)blockIdx.x * TM;
@@ -240,7 +245,9 @@ __global__ void __launch_bounds__(NTHR, 1) k_tc_sumsq(const __grid_constant__ CU
 #pragma unroll
                 for (int e = 0; e < EPC; ++e) {
                     int64_t j = k0 + e;
-                    if (j < m) {
+                    if (j < m && prm.off2 + (int64_t)gz[r] * prm.mp + j >= prm.tlen) {
+                        atomicCAS(prm.status, 0, (int)GPR_ERR_ARG);  // self-check: never expected
+                    } else if (j < m) {
                         float a = tx[j], b = ty[j], cc = tz[j];
                         if (prm.kind == GPR_K_SE) {
                             v[e] = a * b * cc;
@@ -310,7 +317,6 @@ __global__ void __launch_bounds__(NTHR, 1) k_tc_sumsq(const __grid_constant__ CU
     if (!mbar_wait(bar_done, 0)) ok_all = false;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const int lq = warp & 3, half = warp >> 2;
-    float sum = 0.f;
 #pragma unroll
     for (int c0 = 0; c0 < N / 2; c0 += 32) {
         uint32_t rr[32];
@@ -325,18 +331,24 @@ __global__ void __launch_bounds__(NTHR, 1) k_tc_sumsq(const __grid_constant__ CU
               "=r"(rr[29]), "=r"(rr[30]), "=r"(rr[31])
             : "r"(taddr));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        float sum = 0.f;
 #pragma unroll
         for (int i = 0; i < 32; ++i) {
             float w = __uint_as_float(rr[i]);
             sum = fmaf(w, w, sum);
         }
+        red[(half * (N / 2) + c0) / 32][lq * 32 + lane] = sum;
     }
-    red[half][lq * 32 + lane] = sum;
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (tid < TM) {
-        int64_t row = row0 + tid;
-        if (row < prm.count) prm.partial[row * prm.nN + blockIdx.y] = red[0][tid] + red[1][tid];
+    if (tid < TM && row0 + tid < prm.count) {
+        const int64_t row = row0 + tid;
+#pragma unroll
+        for (int q = 0; q < N / 64; ++q) {
+            const int64_t idx = row * prm.nN + n0 / 64 + q;
+            if (idx < prm.plen) prm.partial[idx] = red[2 * q][tid] + red[2 * q + 1][tid];
+            else atomicCAS(prm.status, 0, (int)GPR_ERR_ARG);  // self-check: never expected
+        }
     }
     if (!ok_all) atomicCAS(prm.status, 0, (int)GPR_ERR_TIMEOUT);
     if (warp == 0) {
@@ -348,7 +360,7 @@ __global__ void __launch_bounds__(NTHR, 1) k_tc_sumsq(const __grid_constant__ CU
 __global__ void k_tc_finalize(const float *partial, int nN, int64_t count, double sf2, float *var)
 {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= count) return;
+    if (i >= count || nN > 64) return;
     float s = 0.f;
     for (int t = 0; t < nN; ++t) s += partial[i * nN + t];
     var[i] = (float)(sf2 - (double)s);
@@ -404,15 +416,15 @@ bool make_map(CUtensorMap *map, void *base, int64_t mpt, bool bf, int N)
     return r == CUDA_SUCCESS;
 }
 
-template <int P>
+template <int P, int N>
 size_t smem_bytes()
 {
     using C = Cfg<P>;
-    size_t stage = (size_t)C::NA * TM * 128 + (size_t)C::NB * C::N * 128;
+    size_t stage = (size_t)C::NA * TM * 128 + (size_t)C::NB * N * 128;
     return 2 * stage + 64 + 1024;
 }
 
-template <int P>
+template <int P, int N>
 gpr_status launch_tc(const gpr_model *M, const TcParams &prm, cudaStream_t st)
 {
     using C = Cfg<P>;
@@ -421,18 +433,18 @@ gpr_status launch_tc(const gpr_model *M, const TcParams &prm, cudaStream_t st)
     if (C::BF) {
         void *bases[3] = {B.b0, B.b1, B.b2};
         for (int i = 0; i < 3; ++i)
-            if (!make_map(&maps[i], bases[i], B.mpt, true, C::N)) return GPR_ERR_UNSUPPORTED;
+            if (!make_map(&maps[i], bases[i], B.mpt, true, N)) return GPR_ERR_UNSUPPORTED;
     } else {
         void *bases[3] = {B.thi, B.tlo, B.thi};
         for (int i = 0; i < 3; ++i)
-            if (!make_map(&maps[i], bases[i], B.mpt, false, C::N)) return GPR_ERR_UNSUPPORTED;
+            if (!make_map(&maps[i], bases[i], B.mpt, false, N)) return GPR_ERR_UNSUPPORTED;
     }
-    size_t smem = smem_bytes<P>();
-    GPR_CUDA_TRY(cudaFuncSetAttribute(k_tc_sumsq<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    dim3 grid((unsigned)((prm.count + TM - 1) / TM), (unsigned)prm.nN);
+    size_t smem = smem_bytes<P, N>();
+    GPR_CUDA_TRY(cudaFuncSetAttribute(k_tc_sumsq<P, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    dim3 grid((unsigned)((prm.count + TM - 1) / TM), (unsigned)(B.mpt / N));
     {
         ProfScope ps("tc_sumsq", st);
-        k_tc_sumsq<P><<<grid, NTHR, smem, st>>>(maps[0], maps[1], maps[2], prm);
+        k_tc_sumsq<P, N><<<grid, NTHR, smem, st>>>(maps[0], maps[1], maps[2], prm);
     }
     note_launch();
     GPR_CUDA_TRY(cudaGetLastError());
@@ -441,7 +453,13 @@ gpr_status launch_tc(const gpr_model *M, const TcParams &prm, cudaStream_t st)
 
 }  // namespace
 
-int tc_ntile(gpr_precision p) { return p == GPR_P_BF16X3 ? 128 : 256; }
+// Tile widths the autotuner chooses between, per precision (shared memory allows 256 columns
+// for all but the three-slice BF16 split).
+void tc_ntiles(gpr_precision p, int *a, int *b)
+{
+    if (p == GPR_P_BF16X3) { *a = 64; *b = 128; }
+    else { *a = 128; *b = 256; }
+}
 
 bool tc_precision(gpr_precision p)
 {
@@ -502,8 +520,9 @@ void tc_release(gpr_model *M)
 
 size_t tc_partial_elems(gpr_precision p, const gpr_model *M, int64_t count)
 {
+    (void)p;
     int64_t mpt = (M->mp + 255) / 256 * 256;
-    return (size_t)count * (size_t)((mpt + tc_ntile(p) - 1) / tc_ntile(p));
+    return (size_t)count * (size_t)(mpt / 64);
 }
 
 // var of the listed points by the tensor-core contraction; `partial` holds tc_partial_elems floats.
@@ -525,18 +544,29 @@ gpr_status launch_tc_var(const gpr_model *M, const GridDev &g, gpr_precision pre
     prm.pt_base = pt_base;
     prm.count = count;
     prm.partial = partial;
-    prm.nN = (int)((M->tc->mpt + tc_ntile(prec) - 1) / tc_ntile(prec));
+    prm.nN = (int)(M->tc->mpt / 64);
+    prm.plen = count * prm.nN;
+    prm.tlen = prm.off2 + (int64_t)g.n[2] * M->mp;
     prm.status = gpr_status_word();
     if (!prm.status) return GPR_ERR_CUDA;
-    gpr_status s;
-    switch (prec) {
-    case GPR_P_TF32: s = launch_tc<GPR_P_TF32>(M, prm, st); break;
-    case GPR_P_TF32X3: s = launch_tc<GPR_P_TF32X3>(M, prm, st); break;
-    case GPR_P_BF16: s = launch_tc<GPR_P_BF16>(M, prm, st); break;
-    case GPR_P_BF16X3: s = launch_tc<GPR_P_BF16X3>(M, prm, st); break;
-    default: return GPR_ERR_ARG;
-    }
-    if (s != GPR_OK) return s;
+    // tile width: the autotuner's choice for this precision and model size (results are the same)
+    auto run = [&](int c) -> gpr_status {
+        switch (prec) {
+        case GPR_P_TF32: return c ? launch_tc<GPR_P_TF32, 256>(M, prm, st) : launch_tc<GPR_P_TF32, 128>(M, prm, st);
+        case GPR_P_TF32X3:
+            return c ? launch_tc<GPR_P_TF32X3, 256>(M, prm, st) : launch_tc<GPR_P_TF32X3, 128>(M, prm, st);
+        case GPR_P_BF16: return c ? launch_tc<GPR_P_BF16, 256>(M, prm, st) : launch_tc<GPR_P_BF16, 128>(M, prm, st);
+        case GPR_P_BF16X3:
+            return c ? launch_tc<GPR_P_BF16X3, 128>(M, prm, st) : launch_tc<GPR_P_BF16X3, 64>(M, prm, st);
+        default: return GPR_ERR_ARG;
+        }
+    };
+    static const char *names[] = {"tc_sumsq_fp64", "tc_sumsq_fp32", "tc_sumsq_tf32", "tc_sumsq_tf32x3",
+                                  "tc_sumsq_bf16", "tc_sumsq_bf16x3"};
+    // key: model size and the order of magnitude of the point count
+    int lg = 0;
+    while (((int64_t)1 << lg) < count && lg < 62) ++lg;
+    GPR_TRY(tune_run(names[(int)prec], (tune_bucket(M->mp) << 6) | lg, 2, run, st));
     k_tc_finalize<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(partial, prm.nN, count, M->kp.sf2, var);
     note_launch();
     GPR_CUDA_TRY(cudaGetLastError());
