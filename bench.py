@@ -252,7 +252,7 @@ def run_batched(args, g, torch, rank, world, local):
     launches = g.gpr_launch_count()
     g.gpr_sync(stream)
     ms = e0.elapsed_time(e1) / args.steps
-    prof = {k: g.gpr_profile_read(k) for k in ("oz_w", "stats_ff", "tc_sumsq", "mean_ff", "w64", "cell_prep", "sov",
+    prof = {k: g.gpr_profile_read(k) for k in ("oz_adig", "oz_w", "stats_ff", "tc_sumsq", "mean_ff", "w64", "cell_prep", "sov",
                                                 "oct_eval_w", "oct_level")}
     e0.record(stream)
     for _ in range(args.steps):
@@ -373,7 +373,7 @@ def main():
     g.gpr_profile_enable(False)
     launches = g.gpr_launch_count()
     ms = ev0.elapsed_time(ev1) / args.steps
-    prof = {k: g.gpr_profile_read(k) for k in ("w64", "oz_w", "stats_ff", "meanvar32", "tc_sumsq", "mean_ff",
+    prof = {k: g.gpr_profile_read(k) for k in ("w64", "oz_adig", "oz_w", "stats_ff", "meanvar32", "tc_sumsq", "mean_ff",
                                                 "stats_from_w64", "cell_prep", "sov", "classify", "oct_eval_w",
                                                 "oct_level")}
     g.gpr_sync(stream)

@@ -9,22 +9,27 @@
 // exact; after each chunk the levels are drained (smallest first) into float-float registers.
 // W is written as (hi, lo) float pairs.  Products with s + t < S are kept; S = 7 -> 28 products.
 //
-// Tiles: M = 128 points, N = 64 columns, K blocks of 32 digits (64-byte rows, 64B swizzle),
-// two stages; the S accumulators use S x 64 of the 512 TMEM columns.  B digit slices arrive by
-// TMA (one 3-D tensor map: slice, row j, column i); A digits are generated from float-float
-// separable tables by all warps.  Mbarrier waits are bounded.
+// Two kernels.  k_oz_adig writes the A digit slices of a chunk of rows once (BF16, [slice][row]
+// [k]), from the float-float separable tables.  k_oz_gemm (M = 128 points, N = 64 columns, K
+// blocks of 32 digits with 64-byte rows and 64B swizzle, two stages) is warp-specialised: warp 0
+// loads all slices of A and of B for a K block with one 3-D TMA each; warp 1 issues the MMAs;
+// warps 2-9 drain the accumulators.  The S level accumulators use S x 64 of the 512 TMEM
+// columns, and because B's slices sit next to each other in shared memory, A slice s meets
+// B slices 0 .. S-1-s in one MMA of N = (S - s) 64 columns (split at 256) that lands exactly
+// on levels s .. S-1: 10 MMAs per K step instead of 28.  Mbarrier waits are bounded.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <math.h>
 
 #include <mutex>
+#include <vector>
 
 #include "internal.h"
 
 namespace {
 
-constexpr int TM = 128, TN = 64, BKE = 32, NTHR = 512, BETA = 6;
+constexpr int TM = 128, TN = 64, BKE = 32, BETA = 6;
 constexpr uint32_t kSpin = 1u << 22;
 constexpr int KCH = 1024 / BKE;    // K blocks per exact accumulation (K <= 1024 keeps sums < 2^24)
 constexpr int A_SLICE = TM * 64;   // bytes of one A digit slice per K block
@@ -44,7 +49,6 @@ __device__ __forceinline__ uint64_t desc_sw64(uint32_t addr)
     return d;
 }
 
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
 
 __device__ __forceinline__ bool wait_bar(uint32_t a, uint32_t par)
 {
@@ -97,194 +101,209 @@ struct OzParams {
     int64_t pt_base, count;
     const float *colscale;  // 2^F_j
     float sf2;
-    float2 *W;  // count x mp float-float (or rows at p % row_mod when out_by_point)
+    float2 *W;  // rows out_off + r, mp float-float each (or rows at p % row_mod when out_by_point)
     int out_by_point;
     int64_t row_mod;
+    int64_t mpt, out_off;
     int *status;
 };
 
-// Adds the S level accumulators of TMEM (lanes 32*(w%4), columns 16*(w/4) of each level) to
-// the float-float sums, smallest level first.
-template <int S>
-__device__ __forceinline__ void drain_levels(uint32_t tmem, int warp, FF *acc)
+// A digit slices of rows [0, count) of the list: out[s][row][k], k < mpt (zero beyond m and for
+// rows whose point is off the grid).  a' = k/sf2 from the unit tables in float-float; signed
+// 6-bit digits, the low word joining once the high word is consumed.  Thread: 8 consecutive k.
+__global__ void k_oz_adig(OzParams prm, __nv_bfloat16 *out)
 {
-    const int lq = warp & 3, quarter = warp >> 2;
+    constexpr int S = 7;
+    const int64_t chunks = prm.mpt / 8;
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= prm.count * chunks) return;
+    const int64_t row = t / chunks, j0 = (t % chunks) * 8;
+    int64_t p = prm.pts ? prm.pts[row] : prm.pt_base + row;
+    const int64_t nx = prm.g.n[0], ny = prm.g.n[1];
+    const bool rv = p >= 0 && p < nx * ny * (int64_t)prm.g.n[2];
+    if (!rv) p = 0;
+    const int gx = (int)(p % nx), gy = (int)((p / nx) % ny), gz = (int)(p / (nx * ny));
+    const float2 *px = prm.Tu + (int64_t)gx * prm.mp, *py = prm.Tu + prm.off1 + (int64_t)gy * prm.mp,
+                 *pz = prm.Tu + prm.off2 + (int64_t)gz * prm.mp;
+    float2 tx[8], ty[8], tz[8];
 #pragma unroll
-    for (int lvl = S - 1; lvl >= 0; --lvl) {
-        uint32_t rr[16];
-        const uint32_t taddr = tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(lvl * TN + quarter * 16);
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-            : "=r"(rr[0]), "=r"(rr[1]), "=r"(rr[2]), "=r"(rr[3]), "=r"(rr[4]), "=r"(rr[5]), "=r"(rr[6]), "=r"(rr[7]),
-              "=r"(rr[8]), "=r"(rr[9]), "=r"(rr[10]), "=r"(rr[11]), "=r"(rr[12]), "=r"(rr[13]), "=r"(rr[14]),
-              "=r"(rr[15])
-            : "r"(taddr));
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        const float wgt = ldexpf(1.0f, -BETA * (lvl + 2));
+    for (int e = 0; e < 8; ++e) {
+        const int64_t j = j0 + e < prm.m ? j0 + e : 0;
+        tx[e] = px[j];
+        ty[e] = py[j];
+        tz[e] = pz[j];
+    }
+    float dig[S][8];
 #pragma unroll
-        for (int c = 0; c < 16; ++c) acc[c] = ff_add_f(acc[c], __uint_as_float(rr[c]) * wgt);
+    for (int e = 0; e < 8; ++e) {
+        FF a = ff_mul(ff_mul(FF{tx[e].x, tx[e].y}, FF{ty[e].x, ty[e].y}), FF{tz[e].x, tz[e].y});
+        if (!rv || j0 + e >= prm.m) a = FF{0.f, 0.f};
+        float rr = a.h;
+#pragma unroll
+        for (int d = 0; d < S; ++d) {
+            if (d == 3) rr += a.l;
+            const float i = rintf(ldexpf(rr, BETA * (d + 1)));
+            dig[d][e] = i;
+            rr = fmaf(-i, ldexpf(1.0f, -BETA * (d + 1)), rr);
+        }
+    }
+#pragma unroll
+    for (int d = 0; d < S; ++d) {
+        uint32_t wd[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const uint32_t lo = __bfloat16_as_ushort(__float2bfloat16_rn(dig[d][2 * q]));
+            const uint32_t hi = __bfloat16_as_ushort(__float2bfloat16_rn(dig[d][2 * q + 1]));
+            wd[q] = lo | (hi << 16);
+        }
+        *(uint4 *)(out + ((int64_t)d * prm.count + row) * prm.mpt + j0) = make_uint4(wd[0], wd[1], wd[2], wd[3]);
     }
 }
 
-template <int S>
-__global__ void __launch_bounds__(NTHR, 1) k_oz_w(const __grid_constant__ CUtensorMap mapB, OzParams prm)
+constexpr int G_NTHR = 320;  // warp 0: TMA, warp 1: MMA, warps 2-9: TMEM drain and store
+
+__host__ __device__ constexpr uint32_t idesc_n(int n)
 {
-    constexpr int STAGE = S * A_SLICE + S * B_SLICE;
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+}
+
+template <int S>
+__global__ void __launch_bounds__(G_NTHR, 1) k_oz_gemm(const __grid_constant__ CUtensorMap mapA,
+                                                      const __grid_constant__ CUtensorMap mapB, OzParams prm)
+{
+    constexpr int A_ST = S * A_SLICE, B_ST = S * B_SLICE, STAGE = A_ST + B_ST;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint64_t *bars = (uint64_t *)(smem + 2 * STAGE);
+    uint64_t *bars = (uint64_t *)(smem + 2 * STAGE);  // full[2], empty[2], done, drained
     __shared__ uint32_t tmem_slot;
-    __shared__ int gx[TM], gy[TM], gz[TM];
-    __shared__ bool rvalid[TM];
-    __shared__ int64_t rpoint[TM];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t row0 = (int64_t)blockIdx.x * TM;
     const int n0 = blockIdx.y * TN;
     const int64_t m = prm.m;
     const int64_t kend = (int64_t)n0 + TN < m ? (int64_t)n0 + TN : m;
     const int nkb = (int)((kend + BKE - 1) / BKE);
-    const uint32_t full0 = su32(&bars[0]), free0 = su32(&bars[2]), done = su32(&bars[4]);
+    const int nch = (nkb + KCH - 1) / KCH;
+    const uint32_t full0 = su32(&bars[0]), empty0 = su32(&bars[2]), done = su32(&bars[4]), drained = su32(&bars[5]);
     if (tid == 0) {
         for (int b = 0; b < 5; ++b) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&bars[b])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 8;" ::"r"(drained));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(su32(&tmem_slot)));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
-    for (int r = tid; r < TM; r += NTHR) {
-        int64_t row = row0 + r;
-        bool ok = row < prm.count;
-        int64_t p = ok ? (prm.pts ? prm.pts[row] : prm.pt_base + row) : 0;
-        int64_t nx = prm.g.n[0], ny = prm.g.n[1];
-        if (p < 0 || p >= nx * ny * (int64_t)prm.g.n[2]) { ok = false; p = 0; }
-        gx[r] = (int)(p % nx);
-        gy[r] = (int)((p / nx) % ny);
-        gz[r] = (int)(p / (nx * ny));
-        rvalid[r] = ok;
-        rpoint[r] = p;
-    }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_slot;
-    bool ok_all = true;
-    FF acc[16];
-#pragma unroll
-    for (int c = 0; c < 16; ++c) acc[c] = FF{0.f, 0.f};
+    bool ok = true;
 
-    for (int kb = 0; kb < nkb; ++kb) {
-        const int s = kb & 1, use = kb >> 1;
-        unsigned char *st = smem + s * STAGE;
-        if (kb >= 2 && !wait_bar(free0 + 8 * s, (use - 1) & 1)) ok_all = false;
-        if (tid == 0) {
+    if (warp == 0 && lane == 0) {
+        // producer: all A slices (box 32 k x 128 rows x S) and all B slices (32 k x 64 x S) per K block
+        for (int kb = 0; kb < nkb; ++kb) {
+            const int s = kb & 1;
+            unsigned char *st = smem + s * STAGE;
+            if (kb >= 2 && !wait_bar(empty0 + 8 * s, ((kb >> 1) - 1) & 1)) ok = false;
             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(full0 + 8 * s),
-                         "r"((uint32_t)(S * B_SLICE))
+                         "r"((uint32_t)STAGE)
                          : "memory");
-            for (int t = 0; t < S; ++t)
-                asm volatile(
-                    "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
-                    "%4}], [%5];" ::"r"(su32(st + S * A_SLICE + t * B_SLICE)),
-                    "l"((uint64_t)&mapB), "r"(kb * BKE), "r"(n0), "r"(t), "r"(full0 + 8 * s)
-                    : "memory");
+            asm volatile(
+                "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
+                "%4}], [%5];" ::"r"(su32(st)),
+                "l"((uint64_t)&mapA), "r"(kb * BKE), "r"((int)row0), "r"(0), "r"(full0 + 8 * s)
+                : "memory");
+            asm volatile(
+                "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
+                "%4}], [%5];" ::"r"(su32(st + A_ST)),
+                "l"((uint64_t)&mapB), "r"(kb * BKE), "r"(n0), "r"(0), "r"(full0 + 8 * s)
+                : "memory");
         }
-        // A digits: thread -> (row r, 16-byte chunk c of 8 consecutive k); all 24 table loads
-        // are issued before the digit arithmetic
-        {
-            const int r = tid >> 2, c = tid & 3;
-            const int64_t j0 = (int64_t)kb * BKE + c * 8;
-            const bool rv = rvalid[r];
-            const float2 *px = prm.Tu + (int64_t)gx[r] * prm.mp, *py = prm.Tu + prm.off1 + (int64_t)gy[r] * prm.mp,
-                         *pz = prm.Tu + prm.off2 + (int64_t)gz[r] * prm.mp;
-            float2 tx[8], ty[8], tz[8];
-#pragma unroll
-            for (int e = 0; e < 8; ++e) {
-                const int64_t j = j0 + e < m ? j0 + e : 0;
-                tx[e] = px[j];
-                ty[e] = py[j];
-                tz[e] = pz[j];
-            }
-            float dig[S][8];
-#pragma unroll
-            for (int e = 0; e < 8; ++e) {
-                FF a = ff_mul(ff_mul(FF{tx[e].x, tx[e].y}, FF{ty[e].x, ty[e].y}), FF{tz[e].x, tz[e].y});
-                if (!rv || j0 + e >= m) a = FF{0.f, 0.f};
-                // signed 6-bit digits of a in [0,1]; the low part joins once the high part is consumed
-                float rr = a.h;
-#pragma unroll
-                for (int d = 0; d < S; ++d) {
-                    if (d == 3) rr += a.l;
-                    const float i = rintf(ldexpf(rr, BETA * (d + 1)));
-                    dig[d][e] = i;
-                    rr = fmaf(-i, ldexpf(1.0f, -BETA * (d + 1)), rr);
-                }
-            }
-            const int off = r * 64 + ((c ^ ((r >> 1) & 3)) << 4);
-#pragma unroll
-            for (int d = 0; d < S; ++d) {
-                uint32_t wd[4];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    uint32_t lo = __bfloat16_as_ushort(__float2bfloat16_rn(dig[d][2 * q]));
-                    uint32_t hi = __bfloat16_as_ushort(__float2bfloat16_rn(dig[d][2 * q + 1]));
-                    wd[q] = lo | (hi << 16);
-                }
-                *(uint4 *)(st + d * A_SLICE + off) = make_uint4(wd[0], wd[1], wd[2], wd[3]);
-            }
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        if (tid == 0) {
-            if (!wait_bar(full0 + 8 * s, use & 1)) ok_all = false;
+    } else if (warp == 1 && lane == 0) {
+        // MMA issue: A slice sa against B slices 0 .. S-1-sa, contiguous rows of the B stage
+        for (int kb = 0; kb < nkb; ++kb) {
+            const int s = kb & 1;
+            unsigned char *st = smem + s * STAGE;
+            if (!wait_bar(full0 + 8 * s, (kb >> 1) & 1)) ok = false;
+            if (kb % KCH == 0 && kb > 0 && !wait_bar(drained, ((kb / KCH) - 1) & 1)) ok = false;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t ab = su32(st), bb = su32(st + A_ST);
 #pragma unroll
-            for (int sa = 0; sa < S; ++sa)
+            for (int kk = 0; kk < 2; ++kk)
 #pragma unroll
-                for (int tb = 0; tb < S - sa; ++tb) {
-                    const int lvl = sa + tb;
-                    const uint32_t ab = su32(st + sa * A_SLICE), bb = su32(st + S * A_SLICE + tb * B_SLICE);
+                for (int sa = 0; sa < S; ++sa) {
+                    const int nrow = (S - sa) * TN;
 #pragma unroll
-                    for (int kk = 0; kk < 2; ++kk) {
-                        uint32_t acc = (kb % KCH == 0 && sa == 0 && kk == 0) ? 0u : 1u;
+                    for (int p0 = 0; p0 < nrow; p0 += 256) {
+                        const int nn = nrow - p0 < 256 ? nrow - p0 : 256;
+                        const uint32_t acc = (kb % KCH == 0 && kk == 0 && sa == 0) ? 0u : 1u;
                         asm volatile(
                             "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
-                                tmem + (uint32_t)(lvl * TN)),
-                            "l"(desc_sw64(ab + kk * 32)), "l"(desc_sw64(bb + kk * 32)), "r"(kIdesc), "r"(acc));
+                                tmem + (uint32_t)(sa * TN + p0)),
+                            "l"(desc_sw64(ab + sa * A_SLICE + kk * 32)), "l"(desc_sw64(bb + p0 * 64 + kk * 32)),
+                            "r"(idesc_n(nn)), "r"(acc));
                     }
                 }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(free0 + 8 * s)
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(empty0 + 8 * s)
                          : "memory");
             if (kb == nkb - 1 || kb % KCH == KCH - 1)
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(done)
                              : "memory");
         }
-        if (kb == nkb - 1 || kb % KCH == KCH - 1) {
-            // drain this K chunk's level accumulators into the float-float sums
-            if (!wait_bar(done, (uint32_t)((kb / KCH) & 1))) ok_all = false;
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            drain_levels<S>(tmem, warp, acc);
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            __syncthreads();
-        }
-    }
-    const int lq = warp & 3, quarter = warp >> 2;
-    const int64_t row = row0 + lq * 32 + lane;
-    if (row < prm.count && rvalid[lq * 32 + lane]) {
-        const int64_t orow = prm.out_by_point ? rpoint[lq * 32 + lane] % prm.row_mod : row;
-        float2 *out = prm.W + orow * prm.mp + n0 + quarter * 16;
+    } else if (warp >= 2) {
+        // drain: warp w reads TMEM lanes 32 (w % 4), columns 32 ((w - 2) / 4) of every level
+        const int lq = warp & 3, half = (warp - 2) >> 2;
+        FF acc[32];
 #pragma unroll
-        for (int c = 0; c < 16; ++c) {
-            const int64_t j = n0 + quarter * 16 + c;
-            float cs = (j < prm.mp) ? prm.colscale[j] : 0.f;
-            FF v = {acc[c].h * cs, acc[c].l * cs};  // power-of-two scale: exact
-            if (prm.sf2 != 1.0f) v = ff_mul(v, FF{prm.sf2, 0.f});
-            if (j < prm.mp) out[c] = make_float2(v.h, v.l);
+        for (int c = 0; c < 32; ++c) acc[c] = FF{0.f, 0.f};
+        for (int ch = 0; ch < nch; ++ch) {
+            if (!wait_bar(done, (uint32_t)(ch & 1))) ok = false;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+            for (int lvl = S - 1; lvl >= 0; --lvl) {
+                uint32_t rr[32];
+                const uint32_t taddr = tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(lvl * TN + half * 32);
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+                    "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                    : "=r"(rr[0]), "=r"(rr[1]), "=r"(rr[2]), "=r"(rr[3]), "=r"(rr[4]), "=r"(rr[5]), "=r"(rr[6]),
+                      "=r"(rr[7]), "=r"(rr[8]), "=r"(rr[9]), "=r"(rr[10]), "=r"(rr[11]), "=r"(rr[12]), "=r"(rr[13]),
+                      "=r"(rr[14]), "=r"(rr[15]), "=r"(rr[16]), "=r"(rr[17]), "=r"(rr[18]), "=r"(rr[19]), "=r"(rr[20]),
+                      "=r"(rr[21]), "=r"(rr[22]), "=r"(rr[23]), "=r"(rr[24]), "=r"(rr[25]), "=r"(rr[26]), "=r"(rr[27]),
+                      "=r"(rr[28]), "=r"(rr[29]), "=r"(rr[30]), "=r"(rr[31])
+                    : "r"(taddr));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                const float wgt = ldexpf(1.0f, -BETA * (lvl + 2));
+#pragma unroll
+                for (int c = 0; c < 32; ++c) acc[c] = ff_add_f(acc[c], __uint_as_float(rr[c]) * wgt);
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (ch < nch - 1 && lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(drained) : "memory");
+        }
+        const int64_t row = row0 + lq * 32 + lane;
+        if (row < prm.count) {
+            int64_t p = prm.pts ? prm.pts[row] : prm.pt_base + row;
+            const bool rv = p >= 0 && p < (int64_t)prm.g.n[0] * prm.g.n[1] * (int64_t)prm.g.n[2];
+            if (rv) {
+                const int64_t orow = prm.out_by_point ? p % prm.row_mod : prm.out_off + row;
+                float2 *out = prm.W + orow * prm.mp + n0 + half * 32;
+#pragma unroll
+                for (int c = 0; c < 32; ++c) {
+                    const int64_t j = n0 + half * 32 + c;
+                    float cs = (j < prm.mp) ? prm.colscale[j] : 0.f;
+                    FF v = {acc[c].h * cs, acc[c].l * cs};  // power-of-two scale: exact
+                    if (prm.sf2 != 1.0f) v = ff_mul(v, FF{prm.sf2, 0.f});
+                    if (j < prm.mp) out[c] = make_float2(v.h, v.l);
+                }
+            }
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (!ok_all) atomicCAS(prm.status, 0, (int)GPR_ERR_TIMEOUT);
+    if (!ok) atomicCAS(prm.status, 0, (int)GPR_ERR_TIMEOUT);
     if (warp == 0) {
+        __syncwarp();
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem));
     }
@@ -490,7 +509,7 @@ gpr_status oz_prepare(gpr_model *M, cudaStream_t st)
     if (!enc) { M->oz = O; return GPR_ERR_UNSUPPORTED; }
     cuuint64_t gdim[3] = {(cuuint64_t)mpt, (cuuint64_t)mpt, (cuuint64_t)O->S};
     cuuint64_t gstride[2] = {(cuuint64_t)mpt * 2, (cuuint64_t)mpt * mpt * 2};
-    cuuint32_t box[3] = {BKE, TN, 1};
+    cuuint32_t box[3] = {BKE, TN, (cuuint32_t)O->S};  // all slices of a K block in one copy
     cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = enc(&O->map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, O->B, gdim, gstride, box, estr,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
@@ -518,23 +537,79 @@ gpr_status oz_unit_tables(const gpr_model *M, const GridDev &g, float2 *Tu, cuda
     return GPR_OK;
 }
 
-// Float-float W rows of the listed points (count x mp float2) on the tensor cores.
+// Device scratch for the A digit slices, shared by host threads (batched workers): a buffer is
+// reused only after the stream that last used it has passed its release event.
+struct AdigBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    bool busy = false;
+    cudaEvent_t released = nullptr;
+};
+std::mutex g_adig_mu;
+std::vector<AdigBuf *> g_adig;
+
+gpr_status adig_acquire(size_t bytes, cudaStream_t st, AdigBuf **out)
+{
+    AdigBuf *b = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_adig_mu);
+        for (AdigBuf *c : g_adig)
+            if (!c->busy && c->bytes >= bytes) { b = c; break; }
+        if (!b)
+            for (AdigBuf *c : g_adig)
+                if (!c->busy) { b = c; break; }
+        if (!b) {
+            b = new AdigBuf();
+            g_adig.push_back(b);
+        }
+        b->busy = true;
+    }
+    if (!b->released) GPR_CUDA_TRY(cudaEventCreateWithFlags(&b->released, cudaEventDisableTiming));
+    if (b->bytes < bytes) {
+        GPR_CUDA_TRY(cudaEventSynchronize(b->released));
+        cudaFree(b->p);
+        b->p = nullptr;
+        b->bytes = 0;
+        cudaError_t e = cudaMalloc(&b->p, bytes);
+        if (e != cudaSuccess) {
+            std::lock_guard<std::mutex> lock(g_adig_mu);
+            b->busy = false;
+            return e == cudaErrorMemoryAllocation ? GPR_ERR_OOM : GPR_ERR_CUDA;
+        }
+        b->bytes = bytes;
+    }
+    GPR_CUDA_TRY(cudaStreamWaitEvent(st, b->released, 0));
+    *out = b;
+    return GPR_OK;
+}
+
+void adig_release(AdigBuf *b, cudaStream_t st)
+{
+    cudaEventRecord(b->released, st);
+    std::lock_guard<std::mutex> lock(g_adig_mu);
+    b->busy = false;
+}
+
+// Float-float W rows of the listed points on the tensor cores: row r of the list goes to row r
+// of W (count x mp float2), or to row p % row_mod for point p when out_by_point.  Rows are taken
+// in chunks whose A digits (S x rows x mpt BF16) fit 1.5 GB.
 gpr_status launch_oz_w(const gpr_model *M, const GridDev &g, const float2 *Tu, const int64_t *pts, int64_t pt_base,
                        int64_t count, float2 *W, cudaStream_t st, bool out_by_point, int64_t row_mod)
 {
     if (count <= 0) return GPR_OK;
     const OzOperands *O = M->oz;
     if (!O) return GPR_ERR_ARG;
+    auto enc = encoder();
+    if (!enc) return GPR_ERR_UNSUPPORTED;
+    constexpr int S = 7;
     OzParams prm;
     prm.Tu = Tu;
     prm.off1 = (int64_t)g.n[0] * M->mp;
     prm.off2 = prm.off1 + (int64_t)g.n[1] * M->mp;
     prm.mp = M->mp;
+    prm.mpt = O->mpt;
     prm.m = M->m;
     prm.g = g;
-    prm.pts = pts;
-    prm.pt_base = pt_base;
-    prm.count = count;
     prm.colscale = O->colscale;
     prm.sf2 = (float)M->kp.sf2;
     prm.W = W;
@@ -542,17 +617,48 @@ gpr_status launch_oz_w(const gpr_model *M, const GridDev &g, const float2 *Tu, c
     prm.row_mod = row_mod > 0 ? row_mod : g.npts();
     prm.status = gpr_status_word();
     if (!prm.status) return GPR_ERR_CUDA;
-    constexpr int S = 7;
+    const size_t per_row = (size_t)O->mpt * 2 * S;
+    int64_t chunk = (int64_t)(((size_t)3 << 29) / per_row) / TM * TM;
+    if (chunk < TM) chunk = TM;
+    if (chunk > count) chunk = count;
     size_t smem = 2 * (size_t)(S * A_SLICE + S * B_SLICE) + 64 + 1024;
-    GPR_CUDA_TRY(cudaFuncSetAttribute(k_oz_w<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    dim3 grid((unsigned)((count + TM - 1) / TM), (unsigned)(M->mp / TN));
-    {
-        ProfScope ps("oz_w", st);
-        k_oz_w<S><<<grid, NTHR, smem, st>>>(O->map, prm);
+    GPR_CUDA_TRY(cudaFuncSetAttribute(k_oz_gemm<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    AdigBuf *buf = nullptr;
+    GPR_TRY(adig_acquire((size_t)chunk * per_row, st, &buf));
+    gpr_status rs = GPR_OK;
+    for (int64_t c0 = 0; c0 < count && rs == GPR_OK; c0 += chunk) {
+        const int64_t cnt = count - c0 < chunk ? count - c0 : chunk;
+        prm.pts = pts ? pts + c0 : nullptr;
+        prm.pt_base = pt_base + c0;
+        prm.count = cnt;
+        prm.out_off = c0;
+        const int64_t nthr = cnt * (O->mpt / 8);
+        {
+            ProfScope ps("oz_adig", st);
+            k_oz_adig<<<(unsigned)((nthr + 255) / 256), 256, 0, st>>>(prm, (__nv_bfloat16 *)buf->p);
+        }
+        note_launch();
+        CUtensorMap mapA;
+        cuuint64_t gdim[3] = {(cuuint64_t)O->mpt, (cuuint64_t)cnt, (cuuint64_t)S};
+        cuuint64_t gstride[2] = {(cuuint64_t)O->mpt * 2, (cuuint64_t)cnt * O->mpt * 2};
+        cuuint32_t box[3] = {BKE, TM, (cuuint32_t)S};
+        cuuint32_t estr[3] = {1, 1, 1};
+        if (enc(&mapA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, buf->p, gdim, gstride, box, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS) {
+            rs = GPR_ERR_UNSUPPORTED;
+            break;
+        }
+        dim3 grid((unsigned)((cnt + TM - 1) / TM), (unsigned)(M->mp / TN));
+        {
+            ProfScope ps("oz_w", st);
+            k_oz_gemm<S><<<grid, G_NTHR, smem, st>>>(mapA, O->map, prm);
+        }
+        note_launch();
+        if (cudaGetLastError() != cudaSuccess) rs = GPR_ERR_CUDA;
     }
-    note_launch();
-    GPR_CUDA_TRY(cudaGetLastError());
-    return GPR_OK;
+    adig_release(buf, st);
+    return rs;
 }
 
 gpr_status launch_stats_ff(const gpr_model *M, const GridDev &g, const int64_t *pts, int64_t count, const int32_t *slot,
