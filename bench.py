@@ -435,10 +435,12 @@ def main():
             # 64 x ceil(min(n0+64, m)/32)*32 (the K range of each tile)
             mp = (m + 63) // 64 * 64
             kk = sum(64 * ((min(n0 + 64, m) + 31) // 32 * 32) for n0 in range(0, mp, 64))
-            flops = 28 * 2 * (recon / nfield) * kk
+            # all rows of the step over all launches of the step (launches are row chunks)
+            flops = 28 * 2 * recon * kk
             peak = float(peaks.get("bf16_tflops_sustained") or 1733.1)
-            roof = {"bound": "tensor", "achieved": flops / avg_s / 1e12, "peak": peak, "unit": "TFLOP/s",
-                    "traffic": None, "kernel": "k_oz_w (FP64-class whitening GEMM, BF16 digit split)",
+            roof = {"bound": "tensor", "achieved": flops / (kern[dom][0] / args.steps / 1e3) / 1e12, "peak": peak,
+                    "unit": "TFLOP/s", "traffic": None,
+                    "kernel": "k_oz_gemm (FP64-class whitening GEMM, BF16 digit split)",
                     "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained"}
         elif dom == "sov":
             inst = SOV_WARP_INST_PER_CELL * est_cells / nfield

@@ -183,14 +183,17 @@ __device__ __forceinline__ float lattice_w(uint32_t U)
 // One orthant of the SOV recursion for two samples at once (independent chains, interleaved):
 // e_i = Phi(c_i - sum_j Ls_ij z_j) with the rows pre-scaled by 1/L_ii, f = prod e_i,
 // z_i = Phi^-1(w_i e_i).  An underflowed product stays 0 (z from the clamped argument).
-__device__ __forceinline__ void sov_pair(const float (&Ls)[28], const float (&cb)[8], float sg, const float (&w0)[7],
-                                         const float (&w1)[7], float &f0, float &f1)
+// The first factor e_0 = Phi(c_0) does not depend on the sample: the caller passes it.
+__device__ __forceinline__ void sov_pair(const float (&Ls)[28], const float (&cb)[8], float sg, float e_first,
+                                         const float (&w0)[7], const float (&w1)[7], float &f0, float &f1)
 {
     float z0[7], z1[7];
-    f0 = 1.0f;
-    f1 = 1.0f;
+    f0 = e_first;
+    f1 = e_first;
+    z0[0] = nrm_ppf(fmaxf(w0[0] * e_first, 1e-37f));
+    z1[0] = nrm_ppf(fmaxf(w1[0] * e_first, 1e-37f));
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
+    for (int i = 1; i < 8; ++i) {
         float a0 = sg * cb[i], a1 = a0;
 #pragma unroll
         for (int j = 0; j < i; ++j) {
@@ -232,6 +235,7 @@ __global__ void __launch_bounds__(256, 2) k_sov(const CellRec *recs, const unsig
 #pragma unroll
         for (int i = 0; i < 7; ++i) Ds[i] = __shfl_sync(0xffffffffu, D, i);
         float acc_lo = 0.f, acc_hi = 0.f;  // <= 50 samples per lane: FP32 sums are exact to ~1e-7
+        const float e_first_lo = nrm_cdf(cb[0]), e_first_hi = nrm_cdf(-cb[0]);
         for (int k = lane; k < N; k += 64) {
             const bool two = k + 32 < N;
             float w0[7], w1[7];
@@ -244,7 +248,7 @@ __global__ void __launch_bounds__(256, 2) k_sov(const CellRec *recs, const unsig
             for (int side = 0; side < 2; ++side) {  // one copy of the recursion (instruction cache)
                 if (skip & (1 << side)) continue;
                 float f0, f1;
-                sov_pair(Ls, cb, side ? -1.0f : 1.0f, w0, w1, f0, f1);
+                sov_pair(Ls, cb, side ? -1.0f : 1.0f, side ? e_first_hi : e_first_lo, w0, w1, f0, f1);
                 const float f = two ? f0 + f1 : f0;
                 if (side) acc_hi += f; else acc_lo += f;
             }

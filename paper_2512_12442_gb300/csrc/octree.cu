@@ -474,8 +474,8 @@ __global__ void k_start_points(const MinState *ms, const int64_t *act, int64_t f
 {
     int64_t le = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (le >= cnt) return;
-    int64_t e = first + le, q = act[e / 2];
-    int side = (int)(e % 2);
+    const int64_t e = act[first + le], q = e / 2;
+    const int side = (int)(e % 2);
     for (int d = 0; d < 3; ++d) xyz[3 * le + d] = ms[q].x[side][d];
 }
 
@@ -483,8 +483,8 @@ __global__ void k_start_grad(const float4 *ev, const int64_t *act, int64_t first
 {
     int64_t le = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (le >= cnt) return;
-    int64_t e = first + le, q = act[e / 2];
-    int side = (int)(e % 2);
+    const int64_t e = act[first + le], q = e / 2;
+    const int side = (int)(e % 2);
     float sg = side == 0 ? 1.f : -1.f;
     ms[q].g[side] = sg * ev[le].x;
     ms[q].grad[side][0] = sg * ev[le].y;
@@ -533,9 +533,8 @@ __global__ void k_candidates(GridDev g, int D, int l, const int64_t *nodes, cons
 {
     int64_t le = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (le >= cnt) return;
-    int64_t e = first + le;
-    int64_t q = act[e / 2];
-    int side = (int)(e % 2);
+    const int64_t e = act[first + le], q = e / 2;
+    const int side = (int)(e % 2);
     Geom G = node_geom(g, D, l, nodes[pend[q]]);
     double w[3], u[3], un = 0.0;
     for (int d = 0; d < 3; ++d) {
@@ -556,9 +555,8 @@ __global__ void k_accept(const double *xyz, const uint8_t *valid, const float4 *
 {
     int64_t le = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (le >= cnt) return;
-    int64_t e = first + le;
-    int64_t q = act[e / 2];
-    int side = (int)(e % 2);
+    const int64_t e = act[first + le], q = e / 2;
+    const int side = (int)(e % 2);
     if (!valid[le]) return;
     float sg = side == 0 ? 1.f : -1.f;
     float v = sg * ev[le].x;
@@ -571,24 +569,32 @@ __global__ void k_accept(const double *xyz, const uint8_t *valid, const float4 *
     }
 }
 
-// Bound of each listed pending node from its current minima (act: positions in the pending list;
-// nullptr = every pending node).  With `active`, nodes whose bound already exceeds alpha are
-// decided (subdivide: the minimiser only lowers g, which only raises the bound) and the others
-// are flagged for the minimiser.
+// Bound of each listed pending node from its current minima (act: codes 2q + side of pending
+// nodes q; nullptr = every pending node).  With `active` (two flags per pending node), nodes whose
+// bound already exceeds alpha are decided (subdivide: the minimiser only lowers g, which only
+// raises the bound) and, for the others, each side the bound depends on is flagged for the
+// minimiser: a side outside the p-test's sides, or whose B^d is already below 1e-30 (further
+// descent moves the bound by less than that), is not minimised.
 __global__ void k_large_bound(GridDev g, int D, int l, const int64_t *nodes, const int64_t *pend, const int64_t *act,
                               int64_t cnt, const MinState *ms, double alpha, int8_t *decision, const int8_t *sides,
                               double *bound, uint8_t *active)
 {
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= cnt) return;
-    const int64_t q = act ? act[t] : t;
+    const int64_t q = act ? act[t] / 2 : t;
     int64_t node = pend[q];
     Geom G = node_geom(g, D, l, nodes[node]);
     double dcount = (double)((G.p1[0] - G.p0[0] + 1) * (G.p1[1] - G.p0[1] + 1) * (G.p1[2] - G.p0[2] + 1));
     double bnd = bound_of(sides[node], dcount, (double)ms[q].g[0], (double)ms[q].g[1]);
     bound[node] = bnd;
     decision[node] = bnd > alpha ? 2 : 0;
-    if (active) active[q] = bnd > alpha ? 0 : 1;
+    if (active) {
+        for (int sd = 0; sd < 2; ++sd) {
+            const bool need = bnd <= alpha && (sides[node] & (1 << sd)) &&
+                              dcount * log_norm_cdf((double)ms[q].g[sd]) > -69.0;  // B^d > 1e-30
+            active[2 * q + sd] = need ? 1 : 0;
+        }
+    }
 }
 
 // Subdivided nodes -> children (next frontier) or, at the last level, cells of S.
@@ -690,8 +696,8 @@ gpr_status octree_lcp(gpr_model *M, const gpr_grid *grid, double theta, int D, c
                    Carver::round((size_t)kEvalChunk * 24) + 2 * Carver::round((size_t)kEvalChunk * M->mp * 4) +
                    Carver::round((size_t)kEvalChunk * 16) + Carver::round((size_t)kEvalChunk) +
                    Carver::round((size_t)nc * sizeof(MinState)) + Carver::round((size_t)max_large * 27 * 16) + 512 +
-                   csb + Carver::round(tc_partial_elems(GPR_P_BF16X3, M, n) * 4) + Carver::round((size_t)max_large) +
-                   Carver::round((size_t)max_large * 8) + 8192 + Carver::round((size_t)nc * 4) + 2 * Carver::round((size_t)nc) +
+                   csb + Carver::round(tc_partial_elems(GPR_P_BF16X3, M, n) * 4) + Carver::round((size_t)max_large * 2) +
+                   Carver::round((size_t)max_large * 16) + 8192 + Carver::round((size_t)nc * 4) + 2 * Carver::round((size_t)nc) +
                    256 * 22;
     gpr_precision pp = opts->prec == GPR_P_FP64 ? GPR_P_FP32 : opts->prec;
     GridCache *C = nullptr;
@@ -739,8 +745,8 @@ gpr_status octree_lcp(gpr_model *M, const gpr_grid *grid, double theta, int D, c
     B.csb = csb;
     B.cscr = cv.take<char>(csb);
     B.part = cv.take<float>(tc_partial_elems(GPR_P_BF16X3, M, n));
-    B.unal = cv.take<uint8_t>((size_t)max_large);
-    B.ulist = cv.take<int64_t>((size_t)max_large);
+    B.unal = cv.take<uint8_t>((size_t)max_large * 2);
+    B.ulist = cv.take<int64_t>((size_t)max_large * 2);
     int32_t *slot = (int32_t *)B.tmp_mean;  // reused by the leaf phase (n int32 fits in n floats)
     int64_t *clist = B.pend;                 // reused by the leaf phase (nc int64)
 
@@ -836,12 +842,12 @@ gpr_status octree_lcp(gpr_model *M, const gpr_grid *grid, double theta, int D, c
                 k_large_bound<<<nb(npend, 128), 128, 0, st>>>(g, D, l, nodes, B.pend, nullptr, npend, B.ms, opts->alpha,
                                                              B.decision, B.sides, B.bound, B.unal);
                 note_launch();
-                int64_t nact = 0;
-                GPR_TRY(compact_flags(B.unal, npend, B.ulist, nullptr, &nact, B.cscr, B.csb, st));
+                int64_t nact = 0;  // (node, side) pairs to minimise
+                GPR_TRY(compact_flags(B.unal, 2 * npend, B.ulist, nullptr, &nact, B.cscr, B.csb, st));
                 const int64_t *act = B.ulist;
                 // g and its gradient at the start point of each side
-                for (int64_t first = 0; first < 2 * nact; first += kEvalChunk) {
-                    int64_t cnt = 2 * nact - first < kEvalChunk ? 2 * nact - first : kEvalChunk;
+                for (int64_t first = 0; first < nact; first += kEvalChunk) {
+                    int64_t cnt = nact - first < kEvalChunk ? nact - first : kEvalChunk;
                     k_start_points<<<nb(cnt, 256), 256, 0, st>>>(B.ms, act, first, cnt, B.xyz);
                     note_launch();
                     GPR_TRY(run_eval(M, E, B, cnt, theta, st));
@@ -849,8 +855,8 @@ gpr_status octree_lcp(gpr_model *M, const gpr_grid *grid, double theta, int D, c
                     note_launch();
                 }
                 for (int t = 0; t < T && nact > 0; ++t) {
-                    for (int64_t first = 0; first < 2 * nact; first += kEvalChunk) {
-                        int64_t cnt = 2 * nact - first < kEvalChunk ? 2 * nact - first : kEvalChunk;
+                    for (int64_t first = 0; first < nact; first += kEvalChunk) {
+                        int64_t cnt = nact - first < kEvalChunk ? nact - first : kEvalChunk;
                         k_candidates<<<nb(cnt, 256), 256, 0, st>>>(g, D, l, nodes, B.pend, act, B.ms, t, first, cnt,
                                                                    B.xyz, B.cvalid);
                         note_launch();
