@@ -175,7 +175,9 @@ gpr_status cache_fill_stats(gpr_model *M, GridCache *C, const GridDev &g, const 
     k_need<<<nb(n, 256), 256, 0, st>>>(flag, C->have_S, n, tmpflag);
     note_launch();
     int64_t ns = 0;
-    GPR_TRY(compact_flags(tmpflag, n, list, nullptr, &ns, cscr, csb, st));
+    // bricked order: the 13 forward neighbours' rows of a warp's point are mostly the rows of
+    // points that nearby warps read at the same time (L2 reuse); tmpflag holds 2n bytes
+    GPR_TRY(compact_flags_bricked(g, tmpflag, tmpflag + n, list, nullptr, &ns, cscr, csb, st));
     if (n_new_rows) *n_new_rows = 0;
     if (ns == 0) return GPR_OK;
     // W rows of those points and of their forward neighbours that the cache lacks

@@ -400,7 +400,7 @@ gpr_status lcp_from_kept_cells(gpr_model *M, const GridDev &g, const double *T64
         if (R < 3) return GPR_ERR_OOM;
         const int64_t zs = R - 2, ring = R * nxy;
         size_t b2 = Carver::round((size_t)ring * M->mp * 8) + Carver::round((size_t)n * 15 * 8) +
-                    cell_lcp_scratch_bytes(ncell) + Carver::round(te * sizeof(float2)) + Carver::round((size_t)n) +
+                    cell_lcp_scratch_bytes(ncell) + Carver::round(te * sizeof(float2)) + 2 * Carver::round((size_t)n) +
                     2048;
         GPR_TRY(ws_reserve(M, 1, b2, st));
         Carver cv2{(char *)M->ws[1]};
@@ -409,6 +409,7 @@ gpr_status lcp_from_kept_cells(gpr_model *M, const GridDev &g, const double *T64
         void *scr = cv2.take<char>(cell_lcp_scratch_bytes(ncell));
         float2 *Tu = cv2.take<float2>(te);
         uint8_t *zflag = cv2.take<uint8_t>((size_t)n);
+        uint8_t *bflag = cv2.take<uint8_t>((size_t)n);
         GPR_TRY(oz_prepare(M, st));
         GPR_TRY(oz_unit_tables(M, g, Tu, st));
         int64_t rows_to = 0;  // rows of planes < rows_to are in the ring
@@ -422,7 +423,7 @@ gpr_status lcp_from_kept_cells(gpr_model *M, const GridDev &g, const double *T64
                 rows_to = hi;
             }
             launch_flag_zrange(pflag, n, nxy, z0, z1, zflag, st);
-            GPR_TRY(compact_flags(zflag, n, plist, nullptr, &cnt, cscr, csb, st));
+            GPR_TRY(compact_flags_bricked(g, zflag, bflag, plist, nullptr, &cnt, cscr, csb, st));
             if (cnt > 0) GPR_TRY(launch_stats_ff(M, g, plist, cnt, nullptr, W, S15, st, true, ring));
         }
         int64_t nest = 0;

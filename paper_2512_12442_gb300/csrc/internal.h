@@ -206,6 +206,7 @@ gpr_status octree_lcp(gpr_model *M, const gpr_grid *grid, double theta, int D, c
 gpr_status cache_fill_mv(gpr_model *M, GridCache *C, const GridDev &g, const uint8_t *flag, int64_t *list, float *tmp_mean,
                          float *tmp_var, float *part, void *cscr, size_t csb, cudaStream_t st);
 // Complete FP64-class stats15 in C->S15 for every flagged point (digit-split W rows cached).
+// tmpflag: 2n bytes of scratch; list: 2n int64.
 gpr_status cache_fill_stats(gpr_model *M, GridCache *C, const GridDev &g, const uint8_t *flag, uint8_t *tmpflag,
                             int64_t *list, void *cscr, size_t csb, int64_t *n_new_rows, cudaStream_t st);
 
@@ -255,6 +256,12 @@ void launch_mark_corners(const GridDev &g, const uint8_t *keep_cell, uint8_t *po
 // *count_dev the number; slot (optional) gets the position of each flagged index (-1 otherwise).
 gpr_status compact_flags(const uint8_t *flag, int64_t n, int64_t *out_idx, int32_t *slot, int64_t *count_host,
                          void *scratch, size_t scratch_bytes, cudaStream_t st);
+// As compact_flags over the n grid points, the list in bricked order (8^3 bricks) so that
+// neighbouring points are processed together; bflag: n bytes of scratch; slot (nullable) maps
+// point -> position (-1 elsewhere).
+gpr_status compact_flags_bricked(const GridDev &g, const uint8_t *flag, uint8_t *bflag, int64_t *out_idx,
+                                 int32_t *slot, int64_t *count_host, void *scratch, size_t scratch_bytes,
+                                 cudaStream_t st);
 size_t compact_scratch_bytes(int64_t n);
 
 int num_sms();

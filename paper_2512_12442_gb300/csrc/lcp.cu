@@ -95,11 +95,13 @@ __global__ void k_cell_prep(GridDev g, const double *stats, const int32_t *slot,
         } else {
             double jit = tau * maxd;
             for (int c = 0; c < 8; ++c) S[c][c] += jit;
-            double sa = 0.0, sb = 0.0;
+            double sa = 0.0, sb = 0.0, pa[8], pb[8];  // P(Y_c > theta), P(Y_c < theta)
             for (int c = 0; c < 8; ++c) {
                 double sd = sqrt(S[c][c]);
-                sa += normcdf((mu[c] - theta) / sd);
-                sb += normcdf((theta - mu[c]) / sd);
+                pa[c] = normcdf((mu[c] - theta) / sd);
+                pb[c] = normcdf((theta - mu[c]) / sd);
+                sa += pa[c];
+                sb += pb[c];
             }
             if (!(sa < skip_eps || sb < skip_eps)) {
                 double Lm[8][8];
@@ -124,9 +126,8 @@ __global__ void k_cell_prep(GridDev g, const double *stats, const int32_t *slot,
                 // orthant bounded below 1e-7 is taken as 0: the LCP moves by less than 1e-7.
                 double mlo = 1.0, mhi = 1.0;
                 for (int c = 0; c < 8; ++c) {
-                    double sd = sqrt(S[c][c]);
-                    mlo = fmin(mlo, normcdf((theta - mu[c]) / sd));
-                    mhi = fmin(mhi, normcdf((mu[c] - theta) / sd));
+                    mlo = fmin(mlo, pb[c]);
+                    mhi = fmin(mhi, pa[c]);
                 }
                 int64_t mask = (mlo < 1e-7 ? 1 : 0) | (mhi < 1e-7 ? 2 : 0);
                 r.cell = cidx | (mask << 56);
@@ -608,6 +609,65 @@ gpr_status compact_flags(const uint8_t *flag, int64_t n, int64_t *out_idx, int32
     GPR_CUDA_TRY(cudaMemcpyAsync(&h, total, sizeof h, cudaMemcpyDeviceToHost, st));
     GPR_CUDA_TRY(cudaStreamSynchronize(st));
     *count_host = (int64_t)h;
+    return GPR_OK;
+}
+
+// Bricked order of the grid points: 8 x 8 x 8 bricks (clipped at the far faces), bricks x-fastest
+// within 8-row bands, bands within 8-plane slabs; x-fastest inside a brick.  t -> point index.
+__device__ __forceinline__ int64_t brick_point(const GridDev &g, int64_t t)
+{
+    const int64_t nx = g.n[0], ny = g.n[1], nz = g.n[2];
+    const int64_t slab = nx * ny * 8;
+    int64_t bz = t / slab;
+    const int64_t nbz = (nz + 7) / 8;
+    if (bz > nbz - 1) bz = nbz - 1;
+    t -= bz * slab;
+    const int64_t hz = nz - 8 * bz < 8 ? nz - 8 * bz : 8;
+    const int64_t band = nx * 8 * hz;
+    int64_t by = t / band;
+    const int64_t nby = (ny + 7) / 8;
+    if (by > nby - 1) by = nby - 1;
+    t -= by * band;
+    const int64_t hy = ny - 8 * by < 8 ? ny - 8 * by : 8;
+    const int64_t brick = 8 * hy * hz;
+    int64_t bx = t / brick;
+    const int64_t nbx = (nx + 7) / 8;
+    if (bx > nbx - 1) bx = nbx - 1;
+    t -= bx * brick;
+    const int64_t hx = nx - 8 * bx < 8 ? nx - 8 * bx : 8;
+    const int64_t lx = t % hx, ly = (t / hx) % hy, lz = t / (hx * hy);
+    return (8 * bx + lx) + nx * ((8 * by + ly) + ny * (8 * bz + lz));
+}
+
+__global__ void k_brick_gather(GridDev g, const uint8_t *flag, uint8_t *bflag)
+{
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t < (int64_t)g.n[0] * g.n[1] * g.n[2]) bflag[t] = flag[brick_point(g, t)];
+}
+
+__global__ void k_brick_map(GridDev g, int64_t *list, int64_t count, int32_t *slot)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const int64_t p = brick_point(g, list[i]);
+    list[i] = p;
+    if (slot) slot[p] = (int32_t)i;
+}
+
+gpr_status compact_flags_bricked(const GridDev &g, const uint8_t *flag, uint8_t *bflag, int64_t *out_idx,
+                                 int32_t *slot, int64_t *count_host, void *scratch, size_t scratch_bytes,
+                                 cudaStream_t st)
+{
+    const int64_t n = g.npts();
+    k_brick_gather<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(g, flag, bflag);
+    note_launch();
+    if (slot) GPR_CUDA_TRY(cudaMemsetAsync(slot, 0xff, sizeof(int32_t) * (size_t)n, st));
+    GPR_TRY(compact_flags(bflag, n, out_idx, nullptr, count_host, scratch, scratch_bytes, st));
+    if (*count_host > 0) {
+        k_brick_map<<<(unsigned)((*count_host + 255) / 256), 256, 0, st>>>(g, out_idx, *count_host, slot);
+        note_launch();
+    }
+    GPR_CUDA_TRY(cudaGetLastError());
     return GPR_OK;
 }
 
