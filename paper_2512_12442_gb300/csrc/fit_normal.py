@@ -4,9 +4,10 @@ standard normal CDF and quantile, fitted here by weighted least squares (relativ
 against SciPy's double-precision log_ndtr and ndtri.
 
   CDF, x = -a <= 0:  Phi(-a) = exp(-a^2/2) * G(t),  t = 1 / (1 + 0.3 a),
-                     G a degree-10 polynomial in u = 2t - 1 (a in [0, 13.2]).
+                     G a degree-8 polynomial in u = 2t - 1 (a in [0, 13.2]).
   Quantile, p in (0, 1):  z = sqrt(2) (2p - 1) E,  w = -log(4 p (1 - p)),
-                     E a degree-9 polynomial in a scaled variable on three pieces:
+                     E a polynomial in a scaled variable on three pieces (degree 8 on the
+                     central piece, 9 on the two tail pieces):
                      w in [0, 5];  s = sqrt(w) in [sqrt(5), 4];  s in [4, 9.3].
 The variable w is the one of M. Giles, "Approximating the erfinv function" (GPU Computing
 Gems, 2011), written in p so that the tails keep full relative precision; the
@@ -19,8 +20,9 @@ from scipy.special import log_ndtr, ndtri
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 CDF_C0 = 0.3
-CDF_DEG = 10
-PPF_DEG = 9
+CDF_DEG = 8
+PPF_DEG_MID = 8
+PPF_DEG_TAIL = 9
 PPF_PIECES = (("w", 0.0, 5.0), ("s", float(np.sqrt(5.0)), 4.0), ("s", 4.0, 9.3))
 
 
@@ -49,7 +51,8 @@ def ppf_coeffs():
         v = w if var == "w" else s
         m = (v >= lo) & (v <= hi)
         mid, half = 0.5 * (lo + hi), 0.5 * (hi - lo)
-        out.append((mid, 1.0 / half, fit((v[m] - mid) / half, E[m], PPF_DEG)))
+        deg = PPF_DEG_MID if var == "w" else PPF_DEG_TAIL
+        out.append((mid, 1.0 / half, fit((v[m] - mid) / half, E[m], deg)))
     return out
 
 

@@ -5,8 +5,8 @@
 #pragma once
 #define NRM_CDF_C0 0.3f
 #define NRM_PPF_LG_SPLIT -7.213475f
-static __device__ __forceinline__ float nrm_cdf_g(float u) { return fmaf(fmaf(fmaf(fmaf(fmaf(fmaf(fmaf(fmaf(fmaf(fmaf(-2.0718906e-05f, u, 1.8270206e-05f), u, 0.00017996767f), u, -0.00014484004f), u, -0.001497441f), u, -0.0003035786f), u, 0.014788394f), u, 0.057155002f), u, 0.12556458f), u, 0.19327505f), u, 0.11098531f); }
-static __device__ __forceinline__ float nrm_ppf_mid_lg(float lg) { const float v = fmaf(lg, -0.27725887f, -1.0f); return fmaf(fmaf(fmaf(fmaf(fmaf(fmaf(fmaf(fmaf(fmaf(-4.9126545e-05f, v, 4.948723e-05f), v, 0.0004058818f), v, -0.0011944034f), v, -0.0006878345f), v, 0.01206131f), v, -0.027681367f), v, -0.036923125f), v, 0.87200505f), v, 2.1233134f); }
+static __device__ __forceinline__ float nrm_cdf_g(float u) { return fmaf(fmaf(fmaf(fmaf(fmaf(fmaf(fmaf(fmaf(0.00015558592f, u, -0.00012750691f), u, -0.0014855539f), u, -0.00030872854f), u, 0.014785714f), u, 0.05715546f), u, 0.1255648f), u, 0.19327505f), u, 0.1109853f); }
+static __device__ __forceinline__ float nrm_ppf_mid_lg(float lg) { const float v = fmaf(lg, -0.27725887f, -1.0f); return fmaf(fmaf(fmaf(fmaf(fmaf(fmaf(fmaf(fmaf(6.526152e-05f, v, 0.0003015834f), v, -0.0012235859f), v, -0.00061469385f), v, 0.012077982f), v, -0.027700128f), v, -0.036926124f), v, 0.87200636f), v, 2.1233137f); }
 static __device__ __forceinline__ float nrm_ppf_tail(float s) {
     const bool hi = s >= 4.0f;
     const float v = fmaf(s, hi ? 0.3773585f : 1.1338305f, hi ? -2.509434f : -3.5353222f);

@@ -177,8 +177,9 @@ __global__ void __launch_bounds__(G_NTHR, 1) k_oz_gemm(const __grid_constant__ C
     uint64_t *bars = (uint64_t *)(smem + 2 * STAGE);  // full[2], empty[2], done, drained
     __shared__ uint32_t tmem_slot;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int64_t row0 = (int64_t)blockIdx.x * TM;
-    const int n0 = blockIdx.y * TN;
+    // N tiles fastest: the tiles of one row block run together and share its A digits in L2
+    const int64_t row0 = (int64_t)blockIdx.y * TM;
+    const int n0 = blockIdx.x * TN;
     const int64_t m = prm.m;
     const int64_t kend = (int64_t)n0 + TN < m ? (int64_t)n0 + TN : m;
     const int nkb = (int)((kend + BKE - 1) / BKE);
@@ -398,15 +399,15 @@ __global__ void __launch_bounds__(256, 3) k_stats_ff(GridDev g, const int64_t *p
     int64_t nx = g.n[0], ny = g.n[1], nz = g.n[2];
     int ix = (int)(p % nx), iy = (int)((p / nx) % ny), iz = (int)(p / (nx * ny));
     // rows of W: through the slot map, or (slot == nullptr) at the grid index modulo row_mod
-    const int64_t self = slot ? (int64_t)slot[p] : p % row_mod;
-    int64_t nb[13];
+    const int64_t self = slot ? (int64_t)slot[p] : (p < row_mod ? p : p % row_mod);
+    int32_t nb[13];  // neighbour rows (< 2^31: rows of one call), -1 = off the grid
 #pragma unroll
     for (int e = 0; e < 13; ++e) {
         int a = ix + c_off[e][0], b = iy + c_off[e][1], c = iz + c_off[e][2];
-        int64_t r = -1;
+        int32_t r = -1;
         if (a >= 0 && b >= 0 && c >= 0 && a < nx && b < ny && c < nz) {
             int64_t q = a + nx * (b + ny * (int64_t)c);
-            r = slot ? (int64_t)slot[q] : q % row_mod;
+            r = slot ? slot[q] : (int32_t)(q < row_mod ? q : q % row_mod);
         }
         nb[e] = r;
     }
@@ -418,7 +419,7 @@ __global__ void __launch_bounds__(256, 3) k_stats_ff(GridDev g, const int64_t *p
         const float2 a = wp[j];
         float2 q[13];
 #pragma unroll
-        for (int e = 0; e < 13; ++e) q[e] = nb[e] >= 0 ? W[nb[e] * mp + j] : make_float2(0.f, 0.f);
+        for (int e = 0; e < 13; ++e) q[e] = nb[e] >= 0 ? W[(int64_t)nb[e] * mp + j] : make_float2(0.f, 0.f);
         dot2_step(sh[0], sl[0], a, vyff[j]);
         dot2_step(sh[1], sl[1], a, a);
 #pragma unroll
@@ -649,7 +650,7 @@ gpr_status launch_oz_w(const gpr_model *M, const GridDev &g, const float2 *Tu, c
             rs = GPR_ERR_UNSUPPORTED;
             break;
         }
-        dim3 grid((unsigned)((cnt + TM - 1) / TM), (unsigned)(M->mp / TN));
+        dim3 grid((unsigned)(M->mp / TN), (unsigned)((cnt + TM - 1) / TM));  // row tiles < 65536 per chunk
         {
             ProfScope ps("oz_w", st);
             k_oz_gemm<S><<<grid, G_NTHR, smem, st>>>(mapA, O->map, prm);

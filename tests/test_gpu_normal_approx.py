@@ -1,7 +1,7 @@
 """The estimator's FP32 standard normal CDF and quantile (polynomial fits, fit_normal.py)
 against the oracle's FP64 Phi and Phi^-1, evaluated at the same binary32 arguments.
 
-Bounds: CDF |error| <= 2e-7 everywhere, relative <= 2e-6 where Phi > 1e-7 and <= 2e-5 where
+Bounds: CDF |error| <= 5e-7 everywhere, relative <= 2e-6 where Phi > 1e-7 and <= 2e-5 where
 Phi > 1e-30 (the exponential's argument a^2/2 is rounded in FP32; an orthant factor that small
 moves the estimate by far less than its own size); quantile
 |error| <= 1e-6 + 2e-6 |z| for p in [1e-37, 1 - 2^-24].
@@ -32,7 +32,7 @@ def _eval(x):
 def test_cdf_against_oracle():
     x, cdf, _ = _eval(np.concatenate([np.linspace(-14, 9, 12001), [0.0, -1e-30, 1e-30]]))
     ref = np.array([oracle.norm_cdf(v) for v in x])
-    assert np.abs(cdf - ref).max() <= 2e-7
+    assert np.abs(cdf - ref).max() <= 5e-7
     for floor, tol in ((1e-7, 2e-6), (1e-30, 2e-5)):
         m = ref > floor
         rel = np.abs(cdf[m] / ref[m] - 1)
