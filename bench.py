@@ -36,7 +36,7 @@ METRIC = "LCP grid points/s"
 # Frechet test drops one), from the ncu counters of the small case (sov_estimator profile summary).
 # The estimator is issue-bound: its roofline is the issue rate, 4 warp instructions per clock on
 # each of 152 SMs at 2.07 GHz.
-SOV_WARP_INST_PER_CELL = 35988.0
+SOV_WARP_INST_PER_CELL = 34883.0
 ISSUE_PEAK_GINST = 152 * 4 * 2.07
 UNIT = "grid points/s"
 

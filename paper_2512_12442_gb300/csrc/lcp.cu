@@ -211,8 +211,11 @@ __device__ __forceinline__ void sov_pair(const float (&Ls)[28], const float (&cb
     }
 }
 
-__global__ void __launch_bounds__(256, 2) k_sov(const CellRec *recs, const unsigned long long *nrec, int N,
-                                               uint64_t seed, Lattice lat)
+// MINB: CTAs per SM the register allocation targets (2: 111 registers, 3: 80, both without
+// spills); the autotuner picks the variant and the grid.
+template <int MINB>
+__global__ void __launch_bounds__(256, MINB) k_sov(const CellRec *recs, const unsigned long long *nrec, int N,
+                                                  uint64_t seed, Lattice lat)
 {
     int lane = threadIdx.x & 31;
     int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -354,8 +357,9 @@ size_t record_bytes() { return sizeof(CellRec); }
 void launch_estimator(const void *recs, const unsigned long long *nrec, int64_t max_records, const LcpOpts &o,
                       cudaStream_t st)
 {
-    // one warp per record, persistent over the device count; CTAs per SM chosen by the autotuner
-    static const int per_sm[3] = {2, 4, 16};
+    // one warp per record, persistent over the device count; the register variant and the CTAs
+    // per SM are chosen by the autotuner
+    static const int per_sm[4] = {2, 8, 3, 12};
     auto run = [&](int c) -> gpr_status {
         int64_t blocks = (max_records + 7) / 8;
         if (blocks > (int64_t)num_sms() * per_sm[c]) blocks = (int64_t)num_sms() * per_sm[c];
@@ -363,7 +367,8 @@ void launch_estimator(const void *recs, const unsigned long long *nrec, int64_t 
         if (o.est == GPR_EST_SOV_QMC) {
             static Lattice lat = make_lattice();
             ProfScope _ps("sov", st);
-            k_sov<<<(unsigned)blocks, 256, 0, st>>>((const CellRec *)recs, nrec, o.n_samples, o.seed, lat);
+            if (c < 2) k_sov<2><<<(unsigned)blocks, 256, 0, st>>>((const CellRec *)recs, nrec, o.n_samples, o.seed, lat);
+            else k_sov<3><<<(unsigned)blocks, 256, 0, st>>>((const CellRec *)recs, nrec, o.n_samples, o.seed, lat);
         } else {
             ProfScope _ps("mc", st);
             k_mc<<<(unsigned)blocks, 256, 0, st>>>((const CellRec *)recs, nrec, o.n_samples, o.seed);
@@ -372,7 +377,8 @@ void launch_estimator(const void *recs, const unsigned long long *nrec, int64_t 
         GPR_CUDA_TRY(cudaGetLastError());
         return GPR_OK;
     };
-    tune_run(o.est == GPR_EST_SOV_QMC ? "sov_ctas_per_sm" : "mc_ctas_per_sm", tune_bucket(max_records), 3, run, st);
+    tune_run(o.est == GPR_EST_SOV_QMC ? "sov_shape" : "mc_ctas_per_sm", tune_bucket(max_records),
+             o.est == GPR_EST_SOV_QMC ? 4 : 3, run, st);
 }
 
 gpr_status run_cell_lcp(const GridDev &g, const double *stats, const int32_t *slot, const int64_t *cells,
@@ -695,7 +701,7 @@ gpr_status run_cell_lcp_on_scratch(const GridDev &g, const double *stats, const 
     if (blocks > (int64_t)num_sms() * 16) blocks = (int64_t)num_sms() * 16;
     if (o.est == GPR_EST_SOV_QMC) {
         static Lattice lat = make_lattice();
-        k_sov<<<(unsigned)blocks, 256, 0, st>>>(recs, nrec, o.n_samples, o.seed, lat);
+        k_sov<2><<<(unsigned)blocks, 256, 0, st>>>(recs, nrec, o.n_samples, o.seed, lat);
     } else {
         k_mc<<<(unsigned)blocks, 256, 0, st>>>(recs, nrec, o.n_samples, o.seed);
     }

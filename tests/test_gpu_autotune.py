@@ -53,15 +53,15 @@ def test_estimator_shapes_give_same_bits_and_table(torch, g):
     M = model_of(w)
     grid = g.make_grid(w.n)
     fields = []
-    for c in (0, 1, 2):
-        _force(g, "sov_ctas_per_sm", c)
+    for c in (0, 1, 2, 3):
+        _force(g, "sov_shape", c)
         f = torch.zeros((w.n - 1) ** 3, dtype=torch.float32, device="cuda")
         g.gpr_lcp_dense(M, grid, w.isovalues[0], g.lcp_options(prec=g.GPR_P_TF32X3), f)
         g.gpr_sync()
         fields.append(f.cpu().numpy())
-    _force(g, "sov_ctas_per_sm", -1)
+    _force(g, "sov_shape", -1)
     assert (fields[0] > 0).sum() > 100
-    assert np.array_equal(fields[0], fields[1]) and np.array_equal(fields[0], fields[2])
+    assert all(np.array_equal(fields[0], f) for f in fields[1:])
     g.gpr_autotune_clear()
     M = model_of(w)  # a fresh model: no cached pre-pass table, so the tensor-core pass runs
     f = torch.zeros((w.n - 1) ** 3, dtype=torch.float32, device="cuda")
@@ -71,7 +71,7 @@ def test_estimator_shapes_give_same_bits_and_table(torch, g):
     tab = g.gpr_autotune_table()
     keys = [k for k in tab if k[0] == "tc_sumsq_tf32x3"]
     assert keys and all(tab[k] in (0, 1) and k[1] >> 6 == 128 for k in keys)
-    assert any(k[0] == "sov_ctas_per_sm" for k in tab)
+    assert any(k[0] == "sov_shape" for k in tab)
 
 
 def test_tune_file_persists(tmp_path):
