@@ -53,6 +53,9 @@ def parse():
                         "many-model workload (64 SE models, m in [100, 2000], grids 64^3/128^3/256^3) in one "
                         "gpr_lcp_adaptive_batched call per step")
     p.add_argument("--batch-count", type=int, default=64, help="models of the batched workload")
+    p.add_argument("--api", default="single", choices=["batched", "single"],
+                   help="adaptive mode: the three isovalue fields in one gpr_lcp_adaptive_batched call "
+                        "(concurrent fields of one model) or one gpr_lcp_adaptive call each")
     p.add_argument("--prec", default="tf32x3", choices=["fp32", "fp64", "tf32", "tf32x3", "bf16", "bf16x3"],
                    help="precision of the pre-classification / octree pass")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -338,6 +341,15 @@ def main():
 
     def step(e2e=False):
         M = g.gpr_model_create(w.X, w.y, w.kernel, w.ell, w.sf2, w.sn2, stream=stream)
+        if args.mode == "adaptive" and args.api == "batched":
+            nf = len(w.isovalues)
+            sts = g.gpr_lcp_adaptive_batched([M] * nf, [grid] * nf, list(w.isovalues), [w.max_depth] * nf, opts,
+                                             fields, stream=stream)
+            for t in range(nf):
+                stats_last[t] = sts[t]
+                if e2e:
+                    host[t].copy_(fields[t], non_blocking=True)
+            return M
         for t, th in enumerate(w.isovalues):
             if args.mode == "dense":
                 st = g.gpr_lcp_dense(M, grid, th, opts, fields[t], stream=stream)
@@ -456,6 +468,7 @@ def main():
         "dtype": "f64" if True else "f32", "data": "synthetic",
         "config": {"workload": f"{w.name}, 3 isovalues (P25/P50/P75 of y), SOV-QMC 1600, {args.mode}",
                    "m": m, "grid": n, "mode": args.mode, "prepass": args.prec,
+                   "api": args.api if args.mode == "adaptive" else "single",
                    "l2": "working set > L2 (FP64 whitened rows of the kept points, GBs)",
                    "parallelism": f"replicas x{world}"},
         "roofline": roof,

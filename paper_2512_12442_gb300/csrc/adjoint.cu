@@ -520,7 +520,7 @@ extern "C" gpr_status gpr_lcp_backward(gpr_model *M, const gpr_grid *grid, doubl
                 Carver::round((size_t)n * 4) + Carver::round((size_t)nc * 8) + csb +
                 Carver::round(tc_partial_elems(GPR_P_BF16X3, M, n) * 4) + 8192;
     GPR_TRY(ws_reserve(M, 0, b1, st));
-    Carver cv{(char *)M->ws[0]};
+    Carver cv{(char *)ws_ptr(M, 0)};
     float *T32 = cv.take<float>(te);
     double *T64 = cv.take<double>(te);
     float2 *Tff = cv.take<float2>(te);
@@ -565,7 +565,7 @@ extern "C" gpr_status gpr_lcp_backward(gpr_model *M, const gpr_grid *grid, doubl
                 Carver::round((size_t)splits * mp * mp * 8) + 3 * Carver::round((size_t)mp * mp * 8) +
                 4 * Carver::round((size_t)mp * 8) + 4096;
     GPR_TRY(ws_reserve(M, 1, b2, st));
-    Carver cv2{(char *)M->ws[1]};
+    Carver cv2{(char *)ws_ptr(M, 1)};
     double *W = cv2.take<double>((size_t)npts * mp);
     double *Zh = cv2.take<double>((size_t)npts * mp);
     double *S15 = cv2.take<double>((size_t)npts * 15);

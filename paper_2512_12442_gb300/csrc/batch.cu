@@ -19,14 +19,9 @@
 
 namespace {
 
-struct Arena {
-    void *ws[2] = {nullptr, nullptr};
-    size_t bytes[2] = {0, 0};
-};
-
 struct Pool {
     std::mutex mu;  // held for the whole batched call: one batch at a time per process
-    std::vector<Arena> arenas;
+    std::vector<Workspace> arenas;  // one per worker thread
     void *recs = nullptr;
     size_t rec_bytes = 0;
     unsigned long long *nrec = nullptr;
@@ -40,32 +35,6 @@ Pool &pool()
 }
 
 constexpr size_t kRecordBudget = (size_t)8 << 30;  // shared estimator records (192 B each)
-
-// The model's workspaces are swapped for the worker's pooled ones while it runs a field.
-struct ArenaSwap {
-    gpr_model *M;
-    Arena &A;
-    void *own[2];
-    size_t own_bytes[2];
-    ArenaSwap(gpr_model *M_, Arena &A_) : M(M_), A(A_)
-    {
-        for (int i = 0; i < 2; ++i) {
-            own[i] = M->ws[i];
-            own_bytes[i] = M->ws_bytes[i];
-            M->ws[i] = A.ws[i];
-            M->ws_bytes[i] = A.bytes[i];
-        }
-    }
-    ~ArenaSwap()
-    {
-        for (int i = 0; i < 2; ++i) {
-            A.ws[i] = M->ws[i];
-            A.bytes[i] = M->ws_bytes[i];
-            M->ws[i] = own[i];
-            M->ws_bytes[i] = own_bytes[i];
-        }
-    }
-};
 
 struct Job {
     gpr_model *M;
@@ -104,18 +73,38 @@ extern "C" gpr_status gpr_lcp_adaptive_batched(gpr_model *const *models, const g
     int dev = 0;
     GPR_CUDA_TRY(cudaGetDevice(&dev));
 
-    // fields grouped by model (one worker runs a model's fields in order), largest cost first
+    // Jobs: a model whose fields all use one grid gives one job per field (they may run
+    // concurrently: its grid cache and operands are created under the model's lock and its cache
+    // fills are idempotent); a model with fields on several grids gives one job that runs them in
+    // order (the cache holds one grid).  Largest estimated cost first.
     std::vector<Job> jobs;
-    std::unordered_map<gpr_model *, int> job_of;
+    std::unordered_map<gpr_model *, int> first_of, one_grid;
     int64_t total_cells = 0;
     for (int i = 0; i < count; ++i) {
-        auto it = job_of.find(models[i]);
-        if (it == job_of.end()) {
-            job_of[models[i]] = (int)jobs.size();
-            jobs.push_back(Job{models[i], {}, 0.0});
-            it = job_of.find(models[i]);
+        auto it = first_of.find(models[i]);
+        if (it == first_of.end()) {
+            first_of[models[i]] = i;
+            one_grid[models[i]] = 1;
+        } else if (memcmp(&grids[it->second], &grids[i], sizeof(gpr_grid)) != 0) {
+            one_grid[models[i]] = 0;
         }
-        Job &J = jobs[it->second];
+    }
+    std::unordered_map<gpr_model *, int> job_of;
+    for (int i = 0; i < count; ++i) {
+        int jix;
+        if (one_grid[models[i]]) {
+            jix = (int)jobs.size();
+            jobs.push_back(Job{models[i], {}, 0.0});
+        } else {
+            auto it = job_of.find(models[i]);
+            if (it == job_of.end()) {
+                job_of[models[i]] = (int)jobs.size();
+                jobs.push_back(Job{models[i], {}, 0.0});
+                it = job_of.find(models[i]);
+            }
+            jix = it->second;
+        }
+        Job &J = jobs[jix];
         J.items.push_back(i);
         const double n0 = grids[i].n[0], n1 = grids[i].n[1], n2 = grids[i].n[2];
         const double mp = (double)J.M->mp;
@@ -171,11 +160,11 @@ extern "C" gpr_status gpr_lcp_adaptive_batched(gpr_model *const *models, const g
         auto work = [&](int w) {
             cudaSetDevice(dev);
             set_record_sink(&sink);
+            set_thread_workspace(&P.arenas[w]);
             for (;;) {
                 const int j = ticket.fetch_add(1);
                 if (j >= (int)jobs.size()) break;
                 Job &J = jobs[j];
-                ArenaSwap swap(J.M, P.arenas[w]);
                 for (int i : J.items) {
                     gpr_adaptive_stats *si = stats ? &stats[i] : nullptr;
                     status[i] = octree_lcp(J.M, &grids[i], isovalues[i], max_depths[i], opts, lcps[i], si,
@@ -183,6 +172,7 @@ extern "C" gpr_status gpr_lcp_adaptive_batched(gpr_model *const *models, const g
                 }
             }
             set_record_sink(nullptr);
+            set_thread_workspace(nullptr);
             cudaEventRecord(joins[w], streams[w]);
         };
         std::vector<std::thread> threads;
@@ -215,10 +205,10 @@ extern "C" gpr_status gpr_batch_release(void)
     Pool &P = pool();
     std::lock_guard<std::mutex> lock(P.mu);
     cudaDeviceSynchronize();
-    for (Arena &A : P.arenas)
+    for (Workspace &A : P.arenas)
         for (int i = 0; i < 2; ++i) {
-            cudaFree(A.ws[i]);
-            A.ws[i] = nullptr;
+            cudaFree(A.ptr[i]);
+            A.ptr[i] = nullptr;
             A.bytes[i] = 0;
         }
     cudaFree(P.recs);

@@ -38,6 +38,7 @@ __global__ void k_scatter_mv2(const int64_t *pts, int64_t count, const float *me
     if (i >= count) return;
     int64_t p = pts[i];
     mv[p] = make_float2(mean[i], var[i]);
+    __threadfence();  // the value before its flag, for readers on other streams
     have[p] = 1;
 }
 
@@ -82,8 +83,24 @@ void cache_release(gpr_model *M)
     M->cache = nullptr;
 }
 
+static gpr_status grid_cache_locked(gpr_model *M, const gpr_grid *grid, const GridDev &g, gpr_precision mv_prec,
+                                    GridCache **out, cudaStream_t st);
+
+// Under the model's lock; a new or reset cache is finished on the stream before it is shared
+// (fields of one model on one grid can run concurrently in the batched path).
 gpr_status grid_cache(gpr_model *M, const gpr_grid *grid, const GridDev &g, gpr_precision mv_prec, GridCache **out,
                       cudaStream_t st)
+{
+    std::lock_guard<std::mutex> lock(M->init_mu);
+    GridCache *before = M->cache;
+    gpr_precision pbefore = before ? before->mv_prec : mv_prec;
+    GPR_TRY(grid_cache_locked(M, grid, g, mv_prec, out, st));
+    if (M->cache != before || pbefore != mv_prec) GPR_CUDA_TRY(cudaStreamSynchronize(st));
+    return GPR_OK;
+}
+
+static gpr_status grid_cache_locked(gpr_model *M, const gpr_grid *grid, const GridDev &g, gpr_precision mv_prec,
+                                    GridCache **out, cudaStream_t st)
 {
     if (M->cache && same_grid(M->cache->key, *grid)) {
         GridCache *C = M->cache;

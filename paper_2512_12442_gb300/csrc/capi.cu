@@ -126,7 +126,7 @@ extern "C" gpr_status gpr_reconstruct_dense(gpr_model *M, const gpr_grid *grid, 
         size_t bytes = Carver::round(te * sizeof(float)) + Carver::round(te * sizeof(float2)) +
                        Carver::round(te * sizeof(double)) + Carver::round(np * sizeof(float)) + 1024;
         GPR_TRY(ws_reserve(M, 0, bytes, st));
-        Carver cv{(char *)M->ws[0]};
+        Carver cv{(char *)ws_ptr(M, 0)};
         float *T32 = cv.take<float>(te);
         float2 *Tff = cv.take<float2>(te);
         double *T64 = cv.take<double>(te);
@@ -138,7 +138,7 @@ extern "C" gpr_status gpr_reconstruct_dense(gpr_model *M, const gpr_grid *grid, 
         size_t rows = slab_rows(g, M->mp, sizeof(double), kWBudget);
         size_t bytes = Carver::round(te * sizeof(double)) + Carver::round(rows * M->mp * sizeof(double)) + 1024;
         GPR_TRY(ws_reserve(M, 0, bytes, st));
-        Carver cv{(char *)M->ws[0]};
+        Carver cv{(char *)ws_ptr(M, 0)};
         double *T64 = cv.take<double>(te);
         double *W = cv.take<double>(rows * M->mp);
         GPR_TRY(build_tables(M, g, T64, nullptr, st));
@@ -150,7 +150,7 @@ extern "C" gpr_status gpr_reconstruct_dense(gpr_model *M, const gpr_grid *grid, 
         size_t bytes = Carver::round(te * sizeof(float)) + Carver::round(te * sizeof(float2)) +
                        Carver::round(te * sizeof(double)) + 1024;
         GPR_TRY(ws_reserve(M, 0, bytes, st));
-        Carver cv{(char *)M->ws[0]};
+        Carver cv{(char *)ws_ptr(M, 0)};
         T32 = cv.take<float>(te);
         Tff = cv.take<float2>(te);
         double *T64 = cv.take<double>(te);
@@ -164,7 +164,7 @@ extern "C" gpr_status gpr_reconstruct_dense(gpr_model *M, const gpr_grid *grid, 
     size_t bytes = Carver::round(te * sizeof(float)) + Carver::round(te * sizeof(float2)) +
                    Carver::round(te * sizeof(double)) + Carver::round(rows * M->mp * sizeof(float)) + 1024;
     GPR_TRY(ws_reserve(M, 0, bytes, st));
-    Carver cv{(char *)M->ws[0]};
+    Carver cv{(char *)ws_ptr(M, 0)};
     T32 = cv.take<float>(te);
     Tff = cv.take<float2>(te);
     double *T64 = cv.take<double>(te);
@@ -215,7 +215,7 @@ extern "C" gpr_status gpr_stats_points(gpr_model *M, const gpr_grid *grid, const
     size_t bytes = Carver::round(te * sizeof(double)) + Carver::round((size_t)g.npts() * sizeof(int32_t)) +
                    Carver::round((size_t)count * M->mp * sizeof(double)) + 1024;
     GPR_TRY(ws_reserve(M, 0, bytes, st));
-    Carver cv{(char *)M->ws[0]};
+    Carver cv{(char *)ws_ptr(M, 0)};
     double *T64 = cv.take<double>(te);
     int32_t *slot = cv.take<int32_t>((size_t)g.npts());
     double *W = cv.take<double>((size_t)count * M->mp);
@@ -304,7 +304,7 @@ extern "C" gpr_status gpr_lcp_dense(gpr_model *M, const gpr_grid *grid, double i
         size_t bytes = Carver::round(te * sizeof(double)) + Carver::round(rows * M->mp * sizeof(double)) +
                        Carver::round((size_t)n * 15 * sizeof(double)) + cell_lcp_scratch_bytes(nc) + 2048;
         GPR_TRY(ws_reserve(M, 0, bytes, st));
-        Carver cv{(char *)M->ws[0]};
+        Carver cv{(char *)ws_ptr(M, 0)};
         double *T64 = cv.take<double>(te);
         double *W = cv.take<double>(rows * M->mp);
         double *S15 = cv.take<double>((size_t)n * 15);
@@ -330,7 +330,7 @@ extern "C" gpr_status gpr_lcp_dense(gpr_model *M, const gpr_grid *grid, double i
                 Carver::round((size_t)nc * sizeof(int64_t)) + compact_scratch_bytes(nc > n ? nc : n) +
                 Carver::round(tc_partial_elems(GPR_P_BF16X3, M, n) * 4) + 4096;
     GPR_TRY(ws_reserve(M, 0, b1, st));
-    Carver cv{(char *)M->ws[0]};
+    Carver cv{(char *)ws_ptr(M, 0)};
     float *mean = cv.take<float>((size_t)n);
     float *var = cv.take<float>((size_t)n);
     uint8_t *keep = cv.take<uint8_t>((size_t)nc);
@@ -378,7 +378,7 @@ gpr_status lcp_from_kept_cells(gpr_model *M, const GridDev &g, const double *T64
         GPR_TRY(ws_reserve(M, 1, cell_lcp_scratch_bytes(ncell) + 1024, st));
         if (stats) stats->recon_points = nrows;
         int64_t nest = 0;
-        GPR_TRY(run_cell_lcp(g, C->S15, nullptr, clist, ncell, lo, lcp, false, M->ws[1], M->ws_bytes[1],
+        GPR_TRY(run_cell_lcp(g, C->S15, nullptr, clist, ncell, lo, lcp, false, ws_ptr(M, 1), ws_size(M, 1),
                              stats ? &nest : nullptr, st));
         if (stats) stats->cells_estimated = nest;
         return GPR_OK;
@@ -403,7 +403,7 @@ gpr_status lcp_from_kept_cells(gpr_model *M, const GridDev &g, const double *T64
                     cell_lcp_scratch_bytes(ncell) + Carver::round(te * sizeof(float2)) + 2 * Carver::round((size_t)n) +
                     2048;
         GPR_TRY(ws_reserve(M, 1, b2, st));
-        Carver cv2{(char *)M->ws[1]};
+        Carver cv2{(char *)ws_ptr(M, 1)};
         float2 *W = cv2.take<float2>((size_t)ring * M->mp);
         double *S15 = cv2.take<double>((size_t)n * 15);
         void *scr = cv2.take<char>(cell_lcp_scratch_bytes(ncell));
@@ -435,7 +435,7 @@ gpr_status lcp_from_kept_cells(gpr_model *M, const GridDev &g, const double *T64
     size_t b2 = Carver::round((size_t)npts * M->mp * sizeof(double)) + Carver::round((size_t)npts * 15 * sizeof(double)) +
                 cell_lcp_scratch_bytes(ncell) + Carver::round(te * sizeof(float2)) + 2048;
     GPR_TRY(ws_reserve(M, 1, b2, st));
-    Carver cv2{(char *)M->ws[1]};
+    Carver cv2{(char *)ws_ptr(M, 1)};
     double *W = cv2.take<double>((size_t)npts * M->mp);
     double *S15 = cv2.take<double>((size_t)npts * 15);
     void *scr = cv2.take<char>(cell_lcp_scratch_bytes(ncell));

@@ -6,6 +6,7 @@
 
 #include <atomic>
 #include <functional>
+#include <mutex>
 #include <vector>
 
 #include "../../include/gpr_lcp.h"
@@ -62,6 +63,13 @@ struct TcOperands {
 };
 
 struct OzOperands;  // tensor-core FP64-class operands (ozaki.cu)
+
+// Two independent device workspaces (grow, never shrink): slot 0 for a call's first phase,
+// slot 1 for buffers sized after a device->host count read-back.
+struct Workspace {
+    void *ptr[2] = {nullptr, nullptr};
+    size_t bytes[2] = {0, 0};
+};
 struct GridCache;   // isovalue-independent per-grid results (cache.cu)
 
 struct gpr_model {
@@ -91,14 +99,18 @@ struct gpr_model {
     GridCache *cache = nullptr;
     // host copies used by the octree p-test
     std::vector<double> hX, hy;
-    // two independent workspaces (grow, never shrink): slot 0 for a call's first phase,
-    // slot 1 for buffers sized after a device->host count read-back
-    void *ws[2] = {nullptr, nullptr};
-    size_t ws_bytes[2] = {0, 0};
+    // the model's own workspaces (see Workspace); batch workers use theirs instead
+    Workspace own_ws;
+    // serialises the lazy creation of tc / oz operands when fields of one model run concurrently
+    std::mutex init_mu;
 };
 
-// Makes workspace slot `which` at least `bytes` long (cudaMalloc only when it grows).
+// Makes workspace slot `which` at least `bytes` long (cudaMalloc only when it grows).  The
+// workspace is the model's own, or the calling thread's if one is set (batch workers).
 gpr_status ws_reserve(gpr_model *M, int which, size_t bytes, cudaStream_t st);
+void *ws_ptr(gpr_model *M, int which);
+size_t ws_size(gpr_model *M, int which);
+void set_thread_workspace(Workspace *w);  // nullptr: back to the models' own
 
 // Bump allocator over a workspace block (256-byte aligned pieces).
 struct Carver {

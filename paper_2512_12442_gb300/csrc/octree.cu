@@ -356,6 +356,7 @@ __global__ void k_scatter_mv(const int64_t *pts, int64_t count, const float *mea
     if (i >= count) return;
     int64_t p = pts[i];
     mv[p] = make_float2(mean[i], var[i]);
+    __threadfence();  // the value before its flag, for readers on other streams
     have[p] = 1;
 }
 
@@ -703,7 +704,7 @@ gpr_status octree_lcp(gpr_model *M, const gpr_grid *grid, double theta, int D, c
     GridCache *C = nullptr;
     GPR_TRY(grid_cache(M, grid, g, pp, &C, st));
     GPR_TRY(ws_reserve(M, 0, bytes, st));
-    Carver cv{(char *)M->ws[0]};
+    Carver cv{(char *)ws_ptr(M, 0)};
     const float *T32 = C->T32;
     const double *T64 = C->T64;
     const float2 *Tff = C->Tff;

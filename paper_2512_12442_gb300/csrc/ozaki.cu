@@ -482,7 +482,19 @@ struct OzOperands {
 
 bool oz_supported(const gpr_model *M) { return M->kp.kind == GPR_K_SE; }
 
+static gpr_status oz_prepare_locked(gpr_model *M, cudaStream_t st);
+
+// Lazily built per model; under the model's lock, finished on the stream before it is shared.
 gpr_status oz_prepare(gpr_model *M, cudaStream_t st)
+{
+    std::lock_guard<std::mutex> lock(M->init_mu);
+    if (M->oz) return GPR_OK;
+    GPR_TRY(oz_prepare_locked(M, st));
+    GPR_CUDA_TRY(cudaStreamSynchronize(st));
+    return GPR_OK;
+}
+
+static gpr_status oz_prepare_locked(gpr_model *M, cudaStream_t st)
 {
     if (M->oz) return GPR_OK;
     OzOperands *O = new OzOperands();
@@ -706,7 +718,7 @@ extern "C" gpr_status gpr_stats_points_split(gpr_model *M, const gpr_grid *grid,
     size_t bytes = Carver::round(te * sizeof(float2)) + Carver::round((size_t)g.npts() * 4) +
                    Carver::round((size_t)count * M->mp * 8) + 1024;
     GPR_TRY(ws_reserve(M, 0, bytes, st));
-    Carver cv{(char *)M->ws[0]};
+    Carver cv{(char *)ws_ptr(M, 0)};
     float2 *Tu = cv.take<float2>(te);
     int32_t *slot = cv.take<int32_t>((size_t)g.npts());
     float2 *W = cv.take<float2>((size_t)count * M->mp);

@@ -355,7 +355,7 @@ extern "C" gpr_status gpr_model_destroy(gpr_model *M)
     cudaFree(M->X); cudaFree(M->y); cudaFree(M->L); cudaFree(M->Linv); cudaFree(M->vy); cudaFree(M->alpha);
     cudaFree(M->mu_obs); cudaFree(M->var_obs); cudaFree(M->BT64); cudaFree(M->BT32); cudaFree(M->vy32); cudaFree(M->alpha_ff); cudaFree(M->Linv32); cudaFree(M->X32); cudaFree(M->alpha32);
     for (int w = 0; w < 2; ++w)
-        if (M->ws[w]) cudaFree(M->ws[w]);
+        if (M->own_ws.ptr[w]) cudaFree(M->own_ws.ptr[w]);
     tc_release(M);
     oz_release(M);
     cache_release(M);
@@ -365,23 +365,34 @@ extern "C" gpr_status gpr_model_destroy(gpr_model *M)
 
 extern "C" int64_t gpr_model_m(const gpr_model *M) { return M ? M->m : -1; }
 
+namespace {
+thread_local Workspace *tl_ws = nullptr;  // a batch worker's pooled workspace, used for every model
+}
+
+void set_thread_workspace(Workspace *w) { tl_ws = w; }
+
+static Workspace &ws_of(gpr_model *M) { return tl_ws ? *tl_ws : M->own_ws; }
+void *ws_ptr(gpr_model *M, int which) { return ws_of(M).ptr[which]; }
+size_t ws_size(gpr_model *M, int which) { return ws_of(M).bytes[which]; }
+
 gpr_status ws_reserve(gpr_model *M, int which, size_t bytes, cudaStream_t st)
 {
-    if (bytes <= M->ws_bytes[which]) return GPR_OK;
-    if (M->ws[which]) {
+    Workspace &W = ws_of(M);
+    if (bytes <= W.bytes[which]) return GPR_OK;
+    if (W.ptr[which]) {
         cudaStreamSynchronize(st);
-        cudaFree(M->ws[which]);
-        M->ws[which] = nullptr;
-        M->ws_bytes[which] = 0;
+        cudaFree(W.ptr[which]);
+        W.ptr[which] = nullptr;
+        W.bytes[which] = 0;
     }
     size_t want = bytes + bytes / 8;
-    cudaError_t e = cudaMalloc(&M->ws[which], want);
+    cudaError_t e = cudaMalloc(&W.ptr[which], want);
     if (e != cudaSuccess) {
         gpr_internal_note_cuda_error(e, "workspace", __LINE__);
-        M->ws[which] = nullptr;
+        W.ptr[which] = nullptr;
         return e == cudaErrorMemoryAllocation ? GPR_ERR_OOM : GPR_ERR_CUDA;
     }
-    M->ws_bytes[which] = want;
+    W.bytes[which] = want;
     return GPR_OK;
 }
 

@@ -482,7 +482,20 @@ gpr_status fast_meanvar(gpr_model *M, const GridDev &g, gpr_precision prec, cons
     return GPR_OK;
 }
 
+static gpr_status tc_prepare_locked(gpr_model *M, cudaStream_t st);
+
+// Lazily built per model; under the model's lock, and finished on the stream before another
+// thread may use it (fields of one model can run concurrently in the batched path).
 gpr_status tc_prepare(gpr_model *M, cudaStream_t st)
+{
+    std::lock_guard<std::mutex> lock(M->init_mu);
+    if (M->tc) return GPR_OK;
+    GPR_TRY(tc_prepare_locked(M, st));
+    GPR_CUDA_TRY(cudaStreamSynchronize(st));
+    return GPR_OK;
+}
+
+static gpr_status tc_prepare_locked(gpr_model *M, cudaStream_t st)
 {
     if (M->tc) return GPR_OK;
     int64_t mb = (M->m + 31) / 32 * 32;

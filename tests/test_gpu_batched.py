@@ -94,3 +94,19 @@ def test_batched_empty_and_errors(torch, g):
     with pytest.raises(g.GPRError) as e:
         g.gpr_lcp_adaptive_batched([M], [g.make_grid(w.n)], [float("nan")], [w.max_depth], opts, [f])
     assert e.value.status == g.GPR_ERR_ARG
+
+
+def test_batched_same_model_concurrent_fields(torch, g):
+    """Four isovalue fields of one model on one grid run concurrently (one job each, shared grid
+    cache filled idempotently); each equals its single-field call."""
+    w = workloads.small(41, 300, 40, ell=(0.15, 0.2, 0.25))
+    opts = g.lcp_options(prec=g.GPR_P_TF32X3)
+    ths = [float(np.percentile(w.y, q)) for q in (20, 40, 60, 80)]
+    ref = [_run_single(g, torch, w, th, opts) for th in ths]
+    M = model_of(w)
+    out = [torch.full(((w.n - 1) ** 3,), -1.0, dtype=torch.float32, device="cuda") for _ in ths]
+    st = g.gpr_lcp_adaptive_batched([M] * 4, [g.make_grid(w.n)] * 4, ths, [w.max_depth] * 4, opts, out)
+    g.gpr_sync()
+    for (f_ref, s_ref), f, s in zip(ref, out, st):
+        assert np.array_equal(f_ref, f.cpu().numpy())
+        assert s["leaf_cells"] == s_ref["leaf_cells"]
