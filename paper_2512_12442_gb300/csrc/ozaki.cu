@@ -387,7 +387,7 @@ __device__ __forceinline__ void dot2_step(float &sh, float &sl, float2 a, float2
     sh = s;
 }
 
-__global__ void __launch_bounds__(256, 3) k_stats_ff(GridDev g, const int64_t *pts, int64_t count,
+__global__ void __launch_bounds__(256, 2) k_stats_ff(GridDev g, const int64_t *pts, int64_t count,
                                                      const int32_t *slot, const float2 *W, int64_t mp, int64_t m,
                                                      const float2 *vyff, double sf2, Prior13 pr, double *out15,
                                                      int out_by_point, int64_t row_mod)
@@ -414,16 +414,27 @@ __global__ void __launch_bounds__(256, 3) k_stats_ff(GridDev g, const int64_t *p
     float sh[15], sl[15];
 #pragma unroll
     for (int q = 0; q < 15; ++q) { sh[q] = 0.f; sl[q] = 0.f; }
-    const float2 *wp = W + self * mp;
-    for (int64_t j = lane; j < m; j += 32) {
-        const float2 a = wp[j];
-        float2 q[13];
+    // two consecutive float-float elements per lane and load (rows are 512-byte aligned, mp even,
+    // and W, vyff are zero from m to mp)
+    const float4 *wp = (const float4 *)(W + self * mp);
+    const float4 *W4 = (const float4 *)W;
+    const float4 *v4 = (const float4 *)vyff;
+    const int64_t half_mp = mp / 2, m2 = (m + 1) / 2;
+    for (int64_t j = lane; j < m2; j += 32) {
+        const float4 a = wp[j], v = v4[j];
+        float4 q[13];
 #pragma unroll
-        for (int e = 0; e < 13; ++e) q[e] = nb[e] >= 0 ? W[(int64_t)nb[e] * mp + j] : make_float2(0.f, 0.f);
-        dot2_step(sh[0], sl[0], a, vyff[j]);
-        dot2_step(sh[1], sl[1], a, a);
+        for (int e = 0; e < 13; ++e) q[e] = nb[e] >= 0 ? W4[(int64_t)nb[e] * half_mp + j] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float2 a0 = make_float2(a.x, a.y), a1 = make_float2(a.z, a.w);
+        dot2_step(sh[0], sl[0], a0, make_float2(v.x, v.y));
+        dot2_step(sh[0], sl[0], a1, make_float2(v.z, v.w));
+        dot2_step(sh[1], sl[1], a0, a0);
+        dot2_step(sh[1], sl[1], a1, a1);
 #pragma unroll
-        for (int e = 0; e < 13; ++e) dot2_step(sh[2 + e], sl[2 + e], a, q[e]);
+        for (int e = 0; e < 13; ++e) {
+            dot2_step(sh[2 + e], sl[2 + e], a0, make_float2(q[e].x, q[e].y));
+            dot2_step(sh[2 + e], sl[2 + e], a1, make_float2(q[e].z, q[e].w));
+        }
     }
 #pragma unroll
     for (int q = 0; q < 15; ++q) {
