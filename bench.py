@@ -480,6 +480,7 @@ def main():
                 "h2d_bytes_per_step": int(w.X.nbytes + w.y.nbytes),
                 "d2h_bytes_per_step": int(len(w.isovalues) * ncell * 4)},
         "gpu_launches": launches,
+        "autotune": {f"{k[0]}@{k[1]}": v for k, v in g.gpr_autotune_table().items()},
         "clocks": clk.summary(),
         "measured_peaks": {k: peaks.get(k) for k in ("hbm_gbs", "bf16_tflops", "bf16_tflops_sustained")},
     }
