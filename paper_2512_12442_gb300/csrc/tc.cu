@@ -159,6 +159,78 @@ struct TcParams {
     int *status;
 };
 
+// One 16-byte chunk c (of 8) of row r of the A tile for K block kb, in every A slice of the
+// stage: kernel values from the separable FP32 tables, split as the precision wants (TF32 hi/lo
+// or three BF16 slices), stored in the 128-byte-swizzled K-major layout.
+template <int P>
+__device__ __forceinline__ void gen_a_chunk(const TcParams &prm, unsigned char *st, int r, int c, int kb,
+                                            const int *gx, const int *gy, const int *gz, const bool *rvalid)
+{
+    using C = Cfg<P>;
+    constexpr int BKE = C::BKE;
+    constexpr int A_TILE = TM * 128;
+    const int64_t m = prm.m;
+    const int64_t k0 = (int64_t)kb * BKE + c * (16 / C::ESZ);
+    float v[8];
+    constexpr int EPC = 16 / C::ESZ;  // elements per chunk
+#pragma unroll
+    for (int e = 0; e < EPC; ++e) v[e] = 0.f;
+    if (rvalid[r]) {
+        const float *tx = prm.T32 + (int64_t)gx[r] * prm.mp, *ty = prm.T32 + prm.off1 + (int64_t)gy[r] * prm.mp,
+                    *tz = prm.T32 + prm.off2 + (int64_t)gz[r] * prm.mp;
+#pragma unroll
+        for (int e = 0; e < EPC; ++e) {
+            int64_t j = k0 + e;
+            if (j < m && prm.off2 + (int64_t)gz[r] * prm.mp + j >= prm.tlen) {
+                atomicCAS(prm.status, 0, (int)GPR_ERR_ARG);  // self-check: never expected
+            } else if (j < m) {
+                float a = tx[j], b = ty[j], cc = tz[j];
+                if (prm.kind == GPR_K_SE) {
+                    v[e] = a * b * cc;
+                } else {
+                    float r2 = a + b + cc, rr = sqrtf(r2), s5r = 2.23606797749979f * rr;
+                    v[e] = prm.sf2 * (1.0f + s5r + (5.0f / 3.0f) * r2) * __expf(-s5r);
+                }
+            }
+        }
+    }
+    const int off = r * 128 + ((c ^ (r & 7)) << 4);
+    if (!C::BF) {
+        float4 hi, lo;
+        float *h = &hi.x, *l = &lo.x;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            h[e] = tf32_round(v[e]);
+            l[e] = tf32_round(v[e] - h[e]);
+        }
+        *(float4 *)(st + off) = hi;
+        if (C::NA > 1) *(float4 *)(st + A_TILE + off) = lo;
+    } else {
+        uint32_t wd[3][4];
+#pragma unroll
+        for (int e = 0; e < 8; e += 2) {
+            uint32_t bits[3][2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                float x = v[e + h];
+                __nv_bfloat16 b0 = __float2bfloat16_rn(x);
+                float r1 = x - __bfloat162float(b0);
+                __nv_bfloat16 b1 = __float2bfloat16_rn(r1);
+                float r2 = r1 - __bfloat162float(b1);
+                __nv_bfloat16 b2 = __float2bfloat16_rn(r2);
+                bits[0][h] = __bfloat16_as_ushort(b0);
+                bits[1][h] = __bfloat16_as_ushort(b1);
+                bits[2][h] = __bfloat16_as_ushort(b2);
+            }
+#pragma unroll
+            for (int a = 0; a < 3; ++a) wd[a][e / 2] = bits[a][0] | (bits[a][1] << 16);
+        }
+#pragma unroll
+        for (int a = 0; a < C::NA; ++a)
+            *(uint4 *)(st + a * A_TILE + off) = make_uint4(wd[a][0], wd[a][1], wd[a][2], wd[a][3]);
+    }
+}
+
 // N: output columns per tile (64, 128 or 256; chosen per model size by the autotuner).  The
 // squares are summed per 32-column chunk and paired into 64-column partials, the same grouping
 // for every N, so all tile widths give the same bits.
@@ -232,68 +304,7 @@ __global__ void __launch_bounds__(NTHR, 1) k_tc_sumsq(const __grid_constant__ CU
                 tma_load_2d(smem_u32(st + C::NA * A_TILE + b * B_TILE), maps[b], kb * BKE, n0, bar_full0 + 8 * s);
         }
         // A tile: 128 rows x 128 bytes per slice; one 16-byte chunk per (row, c)
-        for (int q = tid; q < TM * 8; q += NTHR) {
-            const int r = q >> 3, c = q & 7;
-            const int64_t k0 = (int64_t)kb * BKE + c * (16 / C::ESZ);
-            float v[8];
-            constexpr int EPC = 16 / C::ESZ;  // elements per chunk
-#pragma unroll
-            for (int e = 0; e < EPC; ++e) v[e] = 0.f;
-            if (rvalid[r]) {
-                const float *tx = prm.T32 + (int64_t)gx[r] * prm.mp, *ty = prm.T32 + prm.off1 + (int64_t)gy[r] * prm.mp,
-                            *tz = prm.T32 + prm.off2 + (int64_t)gz[r] * prm.mp;
-#pragma unroll
-                for (int e = 0; e < EPC; ++e) {
-                    int64_t j = k0 + e;
-                    if (j < m && prm.off2 + (int64_t)gz[r] * prm.mp + j >= prm.tlen) {
-                        atomicCAS(prm.status, 0, (int)GPR_ERR_ARG);  // self-check: never expected
-                    } else if (j < m) {
-                        float a = tx[j], b = ty[j], cc = tz[j];
-                        if (prm.kind == GPR_K_SE) {
-                            v[e] = a * b * cc;
-                        } else {
-                            float r2 = a + b + cc, rr = sqrtf(r2), s5r = 2.23606797749979f * rr;
-                            v[e] = prm.sf2 * (1.0f + s5r + (5.0f / 3.0f) * r2) * __expf(-s5r);
-                        }
-                    }
-                }
-            }
-            const int off = r * 128 + ((c ^ (r & 7)) << 4);
-            if (!C::BF) {
-                float4 hi, lo;
-                float *h = &hi.x, *l = &lo.x;
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    h[e] = tf32_round(v[e]);
-                    l[e] = tf32_round(v[e] - h[e]);
-                }
-                *(float4 *)(st + off) = hi;
-                if (C::NA > 1) *(float4 *)(st + A_TILE + off) = lo;
-            } else {
-                uint32_t wd[3][4];
-#pragma unroll
-                for (int e = 0; e < 8; e += 2) {
-                    uint32_t bits[3][2];
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        float x = v[e + h];
-                        __nv_bfloat16 b0 = __float2bfloat16_rn(x);
-                        float r1 = x - __bfloat162float(b0);
-                        __nv_bfloat16 b1 = __float2bfloat16_rn(r1);
-                        float r2 = r1 - __bfloat162float(b1);
-                        __nv_bfloat16 b2 = __float2bfloat16_rn(r2);
-                        bits[0][h] = __bfloat16_as_ushort(b0);
-                        bits[1][h] = __bfloat16_as_ushort(b1);
-                        bits[2][h] = __bfloat16_as_ushort(b2);
-                    }
-#pragma unroll
-                    for (int a = 0; a < 3; ++a) wd[a][e / 2] = bits[a][0] | (bits[a][1] << 16);
-                }
-#pragma unroll
-                for (int a = 0; a < C::NA; ++a)
-                    *(uint4 *)(st + a * A_TILE + off) = make_uint4(wd[a][0], wd[a][1], wd[a][2], wd[a][3]);
-            }
-        }
+        for (int q = tid; q < TM * 8; q += NTHR) gen_a_chunk<P>(prm, st, q >> 3, q & 7, kb, gx, gy, gz, rvalid);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
         if (tid == 0) {
@@ -352,6 +363,157 @@ __global__ void __launch_bounds__(NTHR, 1) k_tc_sumsq(const __grid_constant__ CU
     }
     if (!ok_all) atomicCAS(prm.status, 0, (int)GPR_ERR_TIMEOUT);
     if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)N));
+    }
+}
+
+// Warp-specialised variant with the same products, order and epilogue grouping (the same bits):
+// warp 0 loads the B slices by TMA, warp 1 issues the MMAs, warps 2-9 generate the A tile of each
+// stage (waiting only for that stage to be free) and finally drain the accumulator.
+constexpr int WS_NTHR = 320;
+
+template <int P, int N>
+__global__ void __launch_bounds__(WS_NTHR, 1) k_tc_sumsq_ws(const __grid_constant__ CUtensorMap mapB0,
+                                                           const __grid_constant__ CUtensorMap mapB1,
+                                                           const __grid_constant__ CUtensorMap mapB2, TcParams prm)
+{
+    using C = Cfg<P>;
+    constexpr int BKE = C::BKE;
+    constexpr int A_TILE = TM * 128;
+    constexpr int B_TILE = N * 128;
+    constexpr int STAGE = C::NA * A_TILE + C::NB * B_TILE;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t *bars = (uint64_t *)(smem + 2 * STAGE);  // fullB[2], fullA[2], empty[2], done
+    __shared__ uint32_t tmem_slot;
+    __shared__ int gx[TM], gy[TM], gz[TM];
+    __shared__ bool rvalid[TM];
+    __shared__ float red[N / 32][TM];
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int64_t row0 = (int64_t)blockIdx.x * TM;
+    const int n0 = blockIdx.y * N;
+    const int64_t m = prm.m;
+    const int64_t kend = (int64_t)n0 + N < m ? (int64_t)n0 + N : m;
+    const int nkb = (int)((kend + BKE - 1) / BKE);
+    const uint32_t fullB0 = smem_u32(&bars[0]), fullA0 = smem_u32(&bars[2]), empty0 = smem_u32(&bars[4]),
+                   bar_done = smem_u32(&bars[6]);
+    if (tid == 0) {
+        mbar_init(fullB0, 1);
+        mbar_init(fullB0 + 8, 1);
+        mbar_init(fullA0, 256);
+        mbar_init(fullA0 + 8, 256);
+        mbar_init(empty0, 1);
+        mbar_init(empty0 + 8, 1);
+        mbar_init(bar_done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                     "r"((uint32_t)N));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    for (int r = tid; r < TM; r += WS_NTHR) {
+        int64_t row = row0 + r;
+        bool ok = row < prm.count;
+        int64_t p = ok ? (prm.pts ? prm.pts[row] : prm.pt_base + row) : 0;
+        int64_t nx = prm.g.n[0], ny = prm.g.n[1];
+        if (p < 0 || p >= nx * ny * (int64_t)prm.g.n[2]) { ok = false; p = 0; }
+        gx[r] = (int)(p % nx);
+        gy[r] = (int)((p / nx) % ny);
+        gz[r] = (int)(p / (nx * ny));
+        rvalid[r] = ok;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_slot;
+    bool ok_all = true;
+    constexpr uint32_t ID = idesc<C::BF>(TM, N);
+
+    if (warp == 0 && lane == 0) {
+        const CUtensorMap *maps[3] = {&mapB0, &mapB1, &mapB2};
+        for (int kb = 0; kb < nkb; ++kb) {
+            const int s = kb & 1, use = kb >> 1;
+            unsigned char *st = smem + s * STAGE;
+            if (kb >= 2 && !mbar_wait(empty0 + 8 * s, (use - 1) & 1)) ok_all = false;
+            mbar_expect_tx(fullB0 + 8 * s, (uint32_t)(C::NB * B_TILE));
+            for (int b = 0; b < C::NB; ++b)
+                tma_load_2d(smem_u32(st + C::NA * A_TILE + b * B_TILE), maps[b], kb * BKE, n0, fullB0 + 8 * s);
+        }
+    } else if (warp == 1 && lane == 0) {
+        for (int kb = 0; kb < nkb; ++kb) {
+            const int s = kb & 1, use = kb >> 1;
+            unsigned char *st = smem + s * STAGE;
+            if (!mbar_wait(fullB0 + 8 * s, use & 1)) ok_all = false;
+            if (!mbar_wait(fullA0 + 8 * s, use & 1)) ok_all = false;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            for (int t = 0; t < C::NPROD; ++t) {
+                int ia, ib;
+                prod_pair(P, t, ia, ib);
+                const uint32_t abase = smem_u32(st + ia * A_TILE), bbase = smem_u32(st + C::NA * A_TILE + ib * B_TILE);
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk) {
+                    uint32_t acc = (kb > 0 || t > 0 || kk > 0) ? 1u : 0u;
+                    mma<C::BF>(tmem, desc_sw128(abase + kk * 32), desc_sw128(bbase + kk * 32), ID, acc);
+                }
+            }
+            mma_commit(empty0 + 8 * s);
+            if (kb == nkb - 1) mma_commit(bar_done);
+        }
+    } else if (warp >= 2) {
+        const int at = tid - 64;  // 0 .. 255
+        for (int kb = 0; kb < nkb; ++kb) {
+            const int s = kb & 1, use = kb >> 1;
+            unsigned char *st = smem + s * STAGE;
+            if (kb >= 2 && !mbar_wait(empty0 + 8 * s, (use - 1) & 1)) ok_all = false;
+            for (int q = at; q < TM * 8; q += 256) gen_a_chunk<P>(prm, st, q >> 3, q & 7, kb, gx, gy, gz, rvalid);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> tensor-core reads
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(fullA0 + 8 * s) : "memory");
+        }
+        // epilogue: warp w reads TMEM lanes 32 (w % 4), column half (w - 2) / 4
+        if (!mbar_wait(bar_done, 0)) ok_all = false;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const int lq = warp & 3, half = (warp - 2) >> 2;
+#pragma unroll
+        for (int c0 = 0; c0 < N / 2; c0 += 32) {
+            uint32_t rr[32];
+            const uint32_t taddr = tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(half * (N / 2) + c0);
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,"
+                "%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                : "=r"(rr[0]), "=r"(rr[1]), "=r"(rr[2]), "=r"(rr[3]), "=r"(rr[4]), "=r"(rr[5]), "=r"(rr[6]), "=r"(rr[7]),
+                  "=r"(rr[8]), "=r"(rr[9]), "=r"(rr[10]), "=r"(rr[11]), "=r"(rr[12]), "=r"(rr[13]), "=r"(rr[14]),
+                  "=r"(rr[15]), "=r"(rr[16]), "=r"(rr[17]), "=r"(rr[18]), "=r"(rr[19]), "=r"(rr[20]), "=r"(rr[21]),
+                  "=r"(rr[22]), "=r"(rr[23]), "=r"(rr[24]), "=r"(rr[25]), "=r"(rr[26]), "=r"(rr[27]), "=r"(rr[28]),
+                  "=r"(rr[29]), "=r"(rr[30]), "=r"(rr[31])
+                : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            float sum = 0.f;
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+                float w = __uint_as_float(rr[i]);
+                sum = fmaf(w, w, sum);
+            }
+            red[(half * (N / 2) + c0) / 32][lq * 32 + lane] = sum;
+        }
+        asm volatile("bar.sync 1, 256;" ::: "memory");  // the epilogue warps only
+        if (at < TM && row0 + at < prm.count) {
+            const int64_t row = row0 + at;
+#pragma unroll
+            for (int q = 0; q < N / 64; ++q) {
+                const int64_t idx = row * prm.nN + n0 / 64 + q;
+                if (idx < prm.plen) prm.partial[idx] = red[2 * q][at] + red[2 * q + 1][at];
+                else atomicCAS(prm.status, 0, (int)GPR_ERR_ARG);  // self-check: never expected
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (!ok_all) atomicCAS(prm.status, 0, (int)GPR_ERR_TIMEOUT);
+    if (warp == 0) {
+        __syncwarp();
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)N));
     }
@@ -424,7 +586,7 @@ size_t smem_bytes()
     return 2 * stage + 64 + 1024;
 }
 
-template <int P, int N>
+template <int P, int N, bool WS>
 gpr_status launch_tc(const gpr_model *M, const TcParams &prm, cudaStream_t st)
 {
     using C = Cfg<P>;
@@ -440,9 +602,13 @@ gpr_status launch_tc(const gpr_model *M, const TcParams &prm, cudaStream_t st)
             if (!make_map(&maps[i], bases[i], B.mpt, false, N)) return GPR_ERR_UNSUPPORTED;
     }
     size_t smem = smem_bytes<P, N>();
-    GPR_CUDA_TRY(cudaFuncSetAttribute(k_tc_sumsq<P, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     dim3 grid((unsigned)((prm.count + TM - 1) / TM), (unsigned)(B.mpt / N));
-    {
+    if (WS) {
+        GPR_CUDA_TRY(cudaFuncSetAttribute(k_tc_sumsq_ws<P, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        ProfScope ps("tc_sumsq", st);
+        k_tc_sumsq_ws<P, N><<<grid, WS_NTHR, smem, st>>>(maps[0], maps[1], maps[2], prm);
+    } else {
+        GPR_CUDA_TRY(cudaFuncSetAttribute(k_tc_sumsq<P, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         ProfScope ps("tc_sumsq", st);
         k_tc_sumsq<P, N><<<grid, NTHR, smem, st>>>(maps[0], maps[1], maps[2], prm);
     }
@@ -563,14 +729,28 @@ gpr_status launch_tc_var(const gpr_model *M, const GridDev &g, gpr_precision pre
     prm.status = gpr_status_word();
     if (!prm.status) return GPR_ERR_CUDA;
     // tile width: the autotuner's choice for this precision and model size (results are the same)
+    // alternatives (same bits): tile width N and the plain or warp-specialised kernel
     auto run = [&](int c) -> gpr_status {
+        const bool wide = c & 1, ws = c >> 1;
         switch (prec) {
-        case GPR_P_TF32: return c ? launch_tc<GPR_P_TF32, 256>(M, prm, st) : launch_tc<GPR_P_TF32, 128>(M, prm, st);
+        case GPR_P_TF32:
+            return ws ? (wide ? launch_tc<GPR_P_TF32, 256, true>(M, prm, st) : launch_tc<GPR_P_TF32, 128, true>(M, prm, st))
+                      : (wide ? launch_tc<GPR_P_TF32, 256, false>(M, prm, st)
+                              : launch_tc<GPR_P_TF32, 128, false>(M, prm, st));
         case GPR_P_TF32X3:
-            return c ? launch_tc<GPR_P_TF32X3, 256>(M, prm, st) : launch_tc<GPR_P_TF32X3, 128>(M, prm, st);
-        case GPR_P_BF16: return c ? launch_tc<GPR_P_BF16, 256>(M, prm, st) : launch_tc<GPR_P_BF16, 128>(M, prm, st);
+            return ws ? (wide ? launch_tc<GPR_P_TF32X3, 256, true>(M, prm, st)
+                              : launch_tc<GPR_P_TF32X3, 128, true>(M, prm, st))
+                      : (wide ? launch_tc<GPR_P_TF32X3, 256, false>(M, prm, st)
+                              : launch_tc<GPR_P_TF32X3, 128, false>(M, prm, st));
+        case GPR_P_BF16:
+            return ws ? (wide ? launch_tc<GPR_P_BF16, 256, true>(M, prm, st) : launch_tc<GPR_P_BF16, 128, true>(M, prm, st))
+                      : (wide ? launch_tc<GPR_P_BF16, 256, false>(M, prm, st)
+                              : launch_tc<GPR_P_BF16, 128, false>(M, prm, st));
         case GPR_P_BF16X3:
-            return c ? launch_tc<GPR_P_BF16X3, 128>(M, prm, st) : launch_tc<GPR_P_BF16X3, 64>(M, prm, st);
+            return ws ? (wide ? launch_tc<GPR_P_BF16X3, 128, true>(M, prm, st)
+                              : launch_tc<GPR_P_BF16X3, 64, true>(M, prm, st))
+                      : (wide ? launch_tc<GPR_P_BF16X3, 128, false>(M, prm, st)
+                              : launch_tc<GPR_P_BF16X3, 64, false>(M, prm, st));
         default: return GPR_ERR_ARG;
         }
     };
@@ -579,7 +759,7 @@ gpr_status launch_tc_var(const gpr_model *M, const GridDev &g, gpr_precision pre
     // key: model size and the order of magnitude of the point count
     int lg = 0;
     while (((int64_t)1 << lg) < count && lg < 62) ++lg;
-    GPR_TRY(tune_run(names[(int)prec], (tune_bucket(M->mp) << 6) | lg, 2, run, st));
+    GPR_TRY(tune_run(names[(int)prec], (tune_bucket(M->mp) << 6) | lg, 4, run, st));
     k_tc_finalize<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(partial, prm.nN, count, M->kp.sf2, var);
     note_launch();
     GPR_CUDA_TRY(cudaGetLastError());
