@@ -427,6 +427,22 @@ gpr_status run_cell_lcp(const GridDev &g, const double *stats, const int32_t *sl
 
 // ------------------------------------------------------------ pre-classification
 
+// Widened Boole test of the pre-classification in FP32: the estimator's Phi is accurate to ~1e-5
+// relative down to 1e-30, so a cell is dropped only when a sum is below 0.99 skip_eps (never a cell
+// the FP64 test with the same margins keeps; the few extra cells are dropped by the exact test).
+__device__ __forceinline__ uint8_t classify_keep(const double (&mu)[8], const double (&v)[8], double maxv,
+                                                 double theta, double skip_eps, double tau, double mm)
+{
+    float sa = 0.f, sb = 0.f;
+    for (int c = 0; c < 8; ++c) {
+        const float isd = rsqrtf((float)(v[c] + tau * maxv));
+        sa += nrm_cdf((float)(mu[c] + mm - theta) * isd);
+        sb += nrm_cdf((float)(theta - mu[c] + mm) * isd);
+    }
+    const float lim = (float)(0.99 * skip_eps);
+    return (sa < lim || sb < lim) ? 0 : 1;
+}
+
 __global__ void k_classify(GridDev g, const float *mean, const float *var, double theta, double skip_eps,
                            double tau, double mv, double mm, uint8_t *keep)
 {
@@ -441,13 +457,7 @@ __global__ void k_classify(GridDev g, const float *mean, const float *var, doubl
         v[c] = fmax((double)var[p], 0.0) + mv;
         maxv = fmax(maxv, v[c]);
     }
-    double sa = 0.0, sb = 0.0;
-    for (int c = 0; c < 8; ++c) {
-        double sd = sqrt(v[c] + tau * maxv);
-        sa += normcdf((mu[c] + mm - theta) / sd);
-        sb += normcdf((theta - mu[c] + mm) / sd);
-    }
-    keep[cidx] = (sa < skip_eps || sb < skip_eps) ? 0 : 1;
+    keep[cidx] = classify_keep(mu, v, maxv, theta, skip_eps, tau, mm);
 }
 
 void launch_classify_cells(const GridDev &g, const float *mean, const float *var, double theta, double skip_eps,
@@ -488,13 +498,7 @@ __global__ void k_classify_mv(GridDev g, const float2 *mvt, double theta, double
         v[c] = fmax((double)t.y, 0.0) + mv;
         maxv = fmax(maxv, v[c]);
     }
-    double sa = 0.0, sb = 0.0;
-    for (int c = 0; c < 8; ++c) {
-        double sd = sqrt(v[c] + tau * maxv);
-        sa += normcdf((mu[c] + mm - theta) / sd);
-        sb += normcdf((theta - mu[c] + mm) / sd);
-    }
-    keep[cidx] = (sa < skip_eps || sb < skip_eps) ? 0 : 1;
+    keep[cidx] = classify_keep(mu, v, maxv, theta, skip_eps, tau, mm);
 }
 
 void launch_classify_cells_mv(const GridDev &g, const float2 *mvt, double theta, double skip_eps, double tau,
