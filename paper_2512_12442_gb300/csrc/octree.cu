@@ -861,7 +861,8 @@ gpr_status octree_lcp(gpr_model *M, const gpr_grid *grid, double theta, int D, c
                         k_candidates<<<nb(cnt, 256), 256, 0, st>>>(g, D, l, nodes, B.pend, act, B.ms, t, first, cnt,
                                                                    B.xyz, B.cvalid);
                         note_launch();
-                        GPR_TRY(run_eval(M, E, B, cnt, theta, st));
+                        // the last step's gradients are never used: value only
+                        GPR_TRY(run_eval(M, E, B, cnt, theta, st, t < T - 1));
                         k_accept<<<nb(cnt, 256), 256, 0, st>>>(B.xyz, B.cvalid, B.ev, act, first, cnt, B.ms);
                         note_launch();
                     }
