@@ -27,12 +27,14 @@ struct EvalModel {
     int64_t m, mp;
     int kind;
     float ell[3];
+    float iell[3];  // 1 / ell
     float sf2;
 };
 
 __device__ __forceinline__ float kdirect(const EvalModel &E, float x, float y, float z, int64_t j)
 {
-    float a = (x - E.X32[3 * j]) / E.ell[0], b = (y - E.X32[3 * j + 1]) / E.ell[1], c = (z - E.X32[3 * j + 2]) / E.ell[2];
+    float a = (x - E.X32[3 * j]) * E.iell[0], b = (y - E.X32[3 * j + 1]) * E.iell[1],
+          c = (z - E.X32[3 * j + 2]) * E.iell[2];
     float r2 = a * a + b * b + c * c;
     if (E.kind == GPR_K_SE) return E.sf2 * __expf(-0.5f * r2);
     float r = sqrtf(r2), s5r = 2.23606797749979f * r;
@@ -754,7 +756,10 @@ gpr_status octree_lcp(gpr_model *M, const gpr_grid *grid, double theta, int D, c
     EvalModel E;
     E.X32 = M->X32; E.BT32 = M->BT32; E.Linv32 = M->Linv32; E.alpha32 = M->alpha32;
     E.m = M->m; E.mp = M->mp; E.kind = M->kp.kind; E.sf2 = (float)M->kp.sf2;
-    for (int d = 0; d < 3; ++d) E.ell[d] = (float)M->kp.ell[d];
+    for (int d = 0; d < 3; ++d) {
+        E.ell[d] = (float)M->kp.ell[d];
+        E.iell[d] = (float)(1.0 / M->kp.ell[d]);
+    }
 
     GPR_CUDA_TRY(cudaMemsetAsync(B.leaf, 0, (size_t)nc, st));
     k_obs_flags<<<nb(m, 128), 128, 0, st>>>(M->mu_obs, M->var_obs, m, theta, opts->alpha, B.obs_flags);
