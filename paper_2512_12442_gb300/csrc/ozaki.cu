@@ -125,13 +125,15 @@ __global__ void k_oz_adig(OzParams prm, __nv_bfloat16 *out)
     const int gx = (int)(p % nx), gy = (int)((p / nx) % ny), gz = (int)(p / (nx * ny));
     const float2 *px = prm.Tu + (int64_t)gx * prm.mp, *py = prm.Tu + prm.off1 + (int64_t)gy * prm.mp,
                  *pz = prm.Tu + prm.off2 + (int64_t)gz * prm.mp;
+    // table rows are 512-byte aligned and zero from m to mp: two elements per 16-byte load
     float2 tx[8], ty[8], tz[8];
 #pragma unroll
-    for (int e = 0; e < 8; ++e) {
-        const int64_t j = j0 + e < prm.m ? j0 + e : 0;
-        tx[e] = px[j];
-        ty[e] = py[j];
-        tz[e] = pz[j];
+    for (int e = 0; e < 8; e += 2) {
+        const float4 a = *(const float4 *)(px + j0 + e), b = *(const float4 *)(py + j0 + e),
+                     c = *(const float4 *)(pz + j0 + e);
+        tx[e] = make_float2(a.x, a.y); tx[e + 1] = make_float2(a.z, a.w);
+        ty[e] = make_float2(b.x, b.y); ty[e + 1] = make_float2(b.z, b.w);
+        tz[e] = make_float2(c.x, c.y); tz[e + 1] = make_float2(c.z, c.w);
     }
     float dig[S][8];
 #pragma unroll
