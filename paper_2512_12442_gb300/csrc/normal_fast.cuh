@@ -29,7 +29,7 @@ static __device__ __forceinline__ float rsqrt_approx(float x)
     return r;
 }
 
-// Phi(x): Phi(-a) = 2^(-a^2 log2(e) / 2) G(1/(1 + 0.3a)), G a polynomial fitted by
+// Phi(x): Phi(-a) = 2^(-a^2 log2(e) / 2) G(1/(1 + 0.35a)), G a polynomial fitted by
 // fit_normal.py.  Relative error about 1e-6 where Phi > 1e-7 (below 1e-5 down to 1e-30: the
 // FP32 rounding of a^2/2 grows with a).  No branch.
 static __device__ __forceinline__ float nrm_cdf(float x)
