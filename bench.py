@@ -65,6 +65,19 @@ def parse():
     return p.parse_args()
 
 
+def max_over_ranks(x: float, world: int) -> float:
+    """Largest value of x over the ranks (identity for one rank); a CUDA tensor under NCCL, a host
+    tensor under gloo."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -202,7 +215,7 @@ def run_backward(args, g, torch, rank, world, local):
         e1.record(stream)
         torch.cuda.synchronize()
     g.gpr_profile_enable(False)
-    ms = e0.elapsed_time(e1) / args.steps
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world)
     prof = {k: g.gpr_profile_read(k) for k in ("w64", "tc_sumsq", "stats_from_w64", "sov", "adj_cell", "adj_R", "adj_Z")}
     if rank != 0:
         return
@@ -254,7 +267,7 @@ def run_batched(args, g, torch, rank, world, local):
     g.gpr_profile_enable(False)
     launches = g.gpr_launch_count()
     g.gpr_sync(stream)
-    ms = e0.elapsed_time(e1) / args.steps
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world)
     prof = {k: g.gpr_profile_read(k) for k in ("oz_adig", "oz_w", "stats_ff", "tc_sumsq", "mean_ff", "w64", "cell_prep", "sov",
                                                 "oct_eval_w", "oct_level")}
     e0.record(stream)
@@ -263,7 +276,7 @@ def run_batched(args, g, torch, rank, world, local):
             M.close()
     e1.record(stream)
     torch.cuda.synchronize()
-    ms_e2e = e0.elapsed_time(e1) / args.steps
+    ms_e2e = max_over_ranks(e0.elapsed_time(e1) / args.steps, world)
     if rank != 0:
         return
     pts = sum(w.n ** 3 for w in ws)
@@ -390,12 +403,7 @@ def main():
                                                 "oct_level")}
     g.gpr_sync(stream)
     M.close()
-    t_max = ms
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
+    t_max = max_over_ranks(ms, world)
     pts_per_step = len(w.isovalues) * n ** 3
     value = world * pts_per_step / (t_max / 1e3)
 
@@ -408,12 +416,7 @@ def main():
         M.close()
     e1.record(stream)
     barrier()
-    ms_e2e = e0.elapsed_time(e1) / args.steps
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms_e2e], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_e2e = float(t.item())
+    ms_e2e = max_over_ranks(e0.elapsed_time(e1) / args.steps, world)
 
     if rank != 0:
         if world > 1:
