@@ -552,8 +552,6 @@ void oz_release(gpr_model *M)
     M->oz = nullptr;
 }
 
-size_t oz_unit_table_elems(const gpr_model *M, const GridDev &g) { return table_elems(M, g); }
-
 gpr_status oz_unit_tables(const gpr_model *M, const GridDev &g, float2 *Tu, cudaStream_t st)
 {
     int64_t total = (int64_t)table_elems(M, g);

@@ -619,14 +619,6 @@ gpr_status launch_tc(const gpr_model *M, const TcParams &prm, cudaStream_t st)
 
 }  // namespace
 
-// Tile widths the autotuner chooses between, per precision (shared memory allows 256 columns
-// for all but the three-slice BF16 split).
-void tc_ntiles(gpr_precision p, int *a, int *b)
-{
-    if (p == GPR_P_BF16X3) { *a = 64; *b = 128; }
-    else { *a = 128; *b = 256; }
-}
-
 bool tc_precision(gpr_precision p)
 {
     return p == GPR_P_TF32 || p == GPR_P_TF32X3 || p == GPR_P_BF16 || p == GPR_P_BF16X3;
