@@ -53,7 +53,7 @@ def parse():
                         "many-model workload (64 SE models, m in [100, 2000], grids 64^3/128^3/256^3) in one "
                         "gpr_lcp_adaptive_batched call per step")
     p.add_argument("--batch-count", type=int, default=64, help="models of the batched workload")
-    p.add_argument("--api", default="single", choices=["batched", "single"],
+    p.add_argument("--api", default="batched", choices=["batched", "single"],
                    help="adaptive mode: the three isovalue fields in one gpr_lcp_adaptive_batched call "
                         "(concurrent fields of one model) or one gpr_lcp_adaptive call each")
     p.add_argument("--prec", default="tf32x3", choices=["fp32", "fp64", "tf32", "tf32x3", "bf16", "bf16x3"],
@@ -439,11 +439,12 @@ def main():
     roof = None
     if kern[dom][1] > 0:
         avg_s = kern[dom][0] / kern[dom][1] / 1e3
+        per_launch = args.steps / kern[dom][1]  # share of a step's units one launch processes
         if dom == "w64":
-            flops = recon / nfield * m * (m + 1)  # triangular whitening GEMM, per launch
+            flops = recon * per_launch * m * (m + 1)  # triangular whitening GEMM, per launch
             peak = 2.0 * 2 * 152 * 2.07e9 / 1e12
             roof = {"bound": "alu", "achieved": flops / avg_s / 1e12, "peak": peak, "unit": "TFLOP/s",
-                    "traffic": 609.7e6 / 161920 * recon / nfield, "kernel": "k_w_store<double> (FP64 whitening GEMM)",
+                    "traffic": 609.7e6 / 161920 * recon * per_launch, "kernel": "k_w_store<double> (FP64 whitening GEMM)",
                     "peak_source": "derived FP64 issue rate 2 DFMA/clk/SM x 152 x 2.07 GHz (probe measured 1.202)"}
         elif dom == "oz_w":
             # BF16 tensor work actually issued: 28 digit products x 2 x rows x sum over 64-column tiles of
@@ -458,7 +459,7 @@ def main():
                     "kernel": "k_oz_gemm (FP64-class whitening GEMM, BF16 digit split)",
                     "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained"}
         elif dom == "sov":
-            inst = SOV_WARP_INST_PER_CELL * est_cells / nfield
+            inst = SOV_WARP_INST_PER_CELL * est_cells * per_launch  # one launch per field, or one per step
             roof = {"bound": "alu", "achieved": inst / avg_s / 1e9, "peak": ISSUE_PEAK_GINST, "unit": "Gwarp-inst/s",
                     "traffic": None, "kernel": "k_sov (SOV-QMC estimator, FP32)",
                     "peak_source": "issue rate 4 warp-inst/clk x 152 SMs x 2.07 GHz (recipe unit counts and clock)"}
@@ -476,6 +477,9 @@ def main():
                    "parallelism": f"replicas x{world}"},
         "roofline": roof,
         "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
+        "kernel_ms_note": ("CUDA-event time per stage; with api=batched the three fields' octree and leaf stages "
+                           "run on worker streams and their event times overlap (the estimator is one launch)"
+                           if args.mode == "adaptive" and args.api == "batched" else "CUDA-event time per stage"),
         "kept_cells": [stats_last[t]["leaf_cells"] for t in stats_last],
         "recon_points": [stats_last[t]["recon_points"] for t in stats_last],
         "cpu_baseline": cpu,

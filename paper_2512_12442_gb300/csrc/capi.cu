@@ -355,6 +355,7 @@ gpr_status lcp_from_kept_cells(gpr_model *M, const GridDev &g, const double *T64
                                int64_t *plist, int32_t *slot, int64_t *clist, void *cscr, size_t csb, const LcpOpts &lo,
                                float *lcp, gpr_adaptive_stats *stats, cudaStream_t st)
 {
+    std::lock_guard<std::mutex> leaf_lock(M->leaf_mu);
     int64_t n = g.npts(), nc = g.ncells();
     GPR_CUDA_TRY(cudaMemsetAsync(pflag, 0, (size_t)n, st));
     launch_mark_corners(g, keep, pflag, st);

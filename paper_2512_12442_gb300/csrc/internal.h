@@ -103,6 +103,9 @@ struct gpr_model {
     Workspace own_ws;
     // serialises the lazy creation of tc / oz operands when fields of one model run concurrently
     std::mutex init_mu;
+    // serialises the leaf phases of concurrent fields of one model, so that each finds the rows
+    // and statistics the previous one cached instead of recomputing them alongside it
+    std::mutex leaf_mu;
 };
 
 // Makes workspace slot `which` at least `bytes` long (cudaMalloc only when it grows).  The
