@@ -216,7 +216,7 @@ def run_backward(args, g, torch, rank, world, local):
         torch.cuda.synchronize()
     g.gpr_profile_enable(False)
     ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world)
-    prof = {k: g.gpr_profile_read(k) for k in ("w64", "tc_sumsq", "stats_from_w64", "sov", "adj_cell", "adj_R", "adj_Z")}
+    prof = {k: g.gpr_profile_read(k) for k in ("w64", "oz_adig", "oz_w", "stats_ff", "tc_sumsq", "stats_from_w64", "sov", "adj_cell", "adj_prep", "adj_sample", "adj_chol", "adj_R", "adj_Z")}
     if rank != 0:
         return
     out = {"metric": METRIC + " (forward + backward)", "value": world * n ** 3 / (ms / 1e3), "unit": UNIT, "n_gpus": world,

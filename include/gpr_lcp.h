@@ -264,8 +264,10 @@ gpr_status gpr_cell_lcp_from_stats_noalloc(const gpr_grid *grid, const double *s
  * gpr_lcp_backward -- hand-written adjoint (no counterpart in the paper) of
  * loss = sum_c dL_dlcp[c] * LCP_c, the SOV-QMC cell LCP of gpr_lcp_dense, with
  * respect to the observation values y and the log length scales.  The forward
- * quantities are recomputed (kernel rows regenerated, never stored): FP64
- * whitened rows of the kept cells' corners, the reverse sweep of the estimator
+ * quantities are recomputed (kernel rows regenerated, never stored): FP64-class
+ * whitened rows of the kept cells' corners (the tensor-core digit split widened
+ * to FP64 under GPR_EXACT_AUTO where it applies, FP64 cores under
+ * GPR_EXACT_FP64 or for Matern kernels), the reverse sweep of the estimator
  * per cell (FP32 samples, FP64 8x8 Cholesky adjoint), then through Eq. 1 in
  * FP64.  Cells with dL_dlcp[c] == 0 or dropped by the Boole test contribute 0.
  *   dL_dlcp     device float, one weight per cell

@@ -60,99 +60,126 @@ struct Lat {
     uint32_t G[7];
 };
 
-struct WarpCell {
-    double L64[36];
+// FP32 view of one kept cell's factor for the sampling sweep.
+struct AdjRec {
     float L[36];
     float inv[8];
     float b[8];
-    int slot[8];
     int active;
-    int amax;
+    int pad[3];
 };
+constexpr int kRed = 1 + 8 + 36;  // P_lo + P_hi, mu adjoint (8), Lbar (36): FP32 sums per cell
 
-// K9: one warp per kept cell.
-__global__ void k_adj_cell(GridDev g, const double *stats, const int32_t *slot, const int64_t *cells, int64_t count,
-                           const float *dldlcp, double theta, double tau, double skip_eps, int N, uint64_t seed,
-                           Lat lat, Pairs pt, double *G16)
+// The cell's 8 corner statistics, jitter and FP64 Cholesky factor, exactly as the forward
+// estimator forms them; false when the cell is skipped (zero weight, no variance, Boole test).
+__device__ bool adj_factor(const GridDev &g, const double *stats, const int32_t *slot, int64_t cidx, float wbar,
+                           double theta, double tau, double skip_eps, const Pairs &pt, double Lm[8][8], double mu[8],
+                           int slots[8], int &am)
 {
-    __shared__ WarpCell wc[8];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int64_t q = blockIdx.x * (int64_t)(blockDim.x >> 5) + warp;
+    const int64_t cx = g.n[0] - 1, cy = g.n[1] - 1;
+    const int64_t i = cidx % cx, j = (cidx / cx) % cy, k = cidx / (cx * cy);
+    const double *row[8];
+    double S[8][8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const int64_t p = (i + (c & 1)) + (int64_t)g.n[0] * ((j + ((c >> 1) & 1)) + (int64_t)g.n[1] * (k + (c >> 2)));
+        slots[c] = slot[p];
+        row[c] = stats + (int64_t)slots[c] * 15;
+        mu[c] = row[c][0];
+        S[c][c] = row[c][1];
+    }
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int b = a + 1; b < 8; ++b) {
+            const double v = pt.owner[a][b] == 0 ? row[a][2 + pt.slot[a][b]] : row[b][2 + pt.slot[a][b]];
+            S[a][b] = v;
+            S[b][a] = v;
+        }
+    double maxd = 0.0;
+    am = 0;
+#pragma unroll
+    for (int c = 0; c < 8; ++c)
+        if (S[c][c] > maxd) { maxd = S[c][c]; am = c; }
+    if (wbar == 0.0f || !(maxd > 1e-30)) return false;
+    const double jit = tau * maxd;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) S[c][c] += jit;
+    double sa = 0.0, sb = 0.0;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const double sd = sqrt(S[c][c]);
+        sa += normcdf((mu[c] - theta) / sd);
+        sb += normcdf((theta - mu[c]) / sd);
+    }
+    if (sa < skip_eps || sb < skip_eps) return false;
+    const double fl = 1e-3 * jit;
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int b = 0; b <= a; ++b) {
+            double v = S[a][b];
+#pragma unroll
+            for (int r = 0; r < b; ++r) v -= Lm[a][r] * Lm[b][r];
+            if (a == b) {
+                if (!(v > fl)) v = fl;
+                Lm[a][a] = sqrt(v);
+            } else {
+                Lm[a][b] = v / Lm[b][b];
+            }
+        }
+    return true;
+}
+
+// K9a: thread per kept cell: the FP64 factor and its FP32 record for the sweep.
+__global__ void k_adj_prep(GridDev g, const double *stats, const int32_t *slot, const int64_t *cells, int64_t count,
+                           const float *dldlcp, double theta, double tau, double skip_eps, Pairs pt, AdjRec *rec)
+{
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (q >= count) return;
-    WarpCell &W = wc[warp];
+    const int64_t cidx = cells[q];
+    double Lm[8][8], mu[8];
+    int slots[8], am;
+    AdjRec &R = rec[q];
+    if (!adj_factor(g, stats, slot, cidx, dldlcp[cidx], theta, tau, skip_eps, pt, Lm, mu, slots, am)) {
+        R.active = 0;
+        return;
+    }
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+        R.b[a] = (float)(theta - mu[a]);
+        R.inv[a] = (float)(1.0 / Lm[a][a]);
+#pragma unroll
+        for (int b = 0; b <= a; ++b) R.L[tri(a, b)] = (float)Lm[a][b];
+    }
+    R.active = 1;
+}
+
+// K9b: warp per kept cell: the estimator's samples forward and their reverse sweep (FP32,
+// lanes over lattice points), reduced over the warp to the kRed sums of the cell.
+__global__ void __launch_bounds__(256, 2) k_adj_sample(const AdjRec *rec, const int64_t *cells, int64_t count, const float *dldlcp, int N,
+                             uint64_t seed, Lat lat, float *red)
+{
+    __shared__ AdjRec wc[8];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t q = blockIdx.x * (int64_t)(blockDim.x >> 5) + warp;
+    if (q >= count) return;
+    if (!rec[q].active) return;
+    AdjRec &W = wc[warp];
+    for (int t = lane; t < (int)(sizeof(AdjRec) / 4); t += 32) ((float *)&W)[t] = ((const float *)&rec[q])[t];
+    __syncwarp();
     const int64_t cidx = cells[q];
     const float wbar = dldlcp[cidx];
-    if (lane == 0) {
-        W.active = 0;
-        int64_t cx = g.n[0] - 1, cy = g.n[1] - 1;
-        int64_t i = cidx % cx, j = (cidx / cx) % cy, k = cidx / (cx * cy);
-        const double *row[8];
-        double mu[8], S[8][8];
-        for (int c = 0; c < 8; ++c) {
-            int64_t p = (i + (c & 1)) + (int64_t)g.n[0] * ((j + ((c >> 1) & 1)) + (int64_t)g.n[1] * (k + (c >> 2)));
-            int s = slot[p];
-            W.slot[c] = s;
-            row[c] = stats + (int64_t)s * 15;
-            mu[c] = row[c][0];
-            S[c][c] = row[c][1];
-        }
-        for (int a = 0; a < 8; ++a)
-            for (int b = a + 1; b < 8; ++b) {
-                double v = pt.owner[a][b] == 0 ? row[a][2 + pt.slot[a][b]] : row[b][2 + pt.slot[a][b]];
-                S[a][b] = v;
-                S[b][a] = v;
-            }
-        double maxd = 0.0;
-        int am = 0;
-        for (int c = 0; c < 8; ++c)
-            if (S[c][c] > maxd) { maxd = S[c][c]; am = c; }
-        if (wbar != 0.0f && maxd > 1e-30) {
-            double jit = tau * maxd;
-            for (int c = 0; c < 8; ++c) S[c][c] += jit;
-            double sa = 0.0, sb = 0.0;
-            for (int c = 0; c < 8; ++c) {
-                double sd = sqrt(S[c][c]);
-                sa += normcdf((mu[c] - theta) / sd);
-                sb += normcdf((theta - mu[c]) / sd);
-            }
-            if (!(sa < skip_eps || sb < skip_eps)) {
-                double Lm[8][8];
-                double fl = 1e-3 * jit;
-                for (int a = 0; a < 8; ++a)
-                    for (int b = 0; b <= a; ++b) {
-                        double s = S[a][b];
-                        for (int r = 0; r < b; ++r) s -= Lm[a][r] * Lm[b][r];
-                        if (a == b) {
-                            if (!(s > fl)) s = fl;
-                            Lm[a][a] = sqrt(s);
-                        } else {
-                            Lm[a][b] = s / Lm[b][b];
-                        }
-                    }
-                for (int a = 0; a < 8; ++a) {
-                    W.b[a] = (float)(theta - mu[a]);
-                    W.inv[a] = (float)(1.0 / Lm[a][a]);
-                    for (int b = 0; b <= a; ++b) {
-                        W.L64[tri(a, b)] = Lm[a][b];
-                        W.L[tri(a, b)] = (float)Lm[a][b];
-                    }
-                }
-                W.amax = am;
-                W.active = 1;
-            }
-        }
-    }
-    __syncwarp();
-    if (!W.active) return;
     uint32_t D = 0;
     if (lane < 7) D = (uint32_t)(splitmix64(seed, (uint64_t)cidx * 8 + lane + 1) >> 32);
     uint32_t Ds[7];
 #pragma unroll
     for (int i = 0; i < 7; ++i) Ds[i] = __shfl_sync(0xffffffffu, D, i);
-    float bbar[2][8], Lbar[36];
-    float P[2] = {0.f, 0.f};
+    // mbar: adjoint of mu (b_lo = theta - mu, b_hi = mu - theta), P: both orthant sums
+    float mbar[8], Lbar[36];
+    float P = 0.f;
 #pragma unroll
-    for (int i = 0; i < 8; ++i) { bbar[0][i] = 0.f; bbar[1][i] = 0.f; }
+    for (int i = 0; i < 8; ++i) mbar[i] = 0.f;
 #pragma unroll
     for (int t = 0; t < 36; ++t) Lbar[t] = 0.f;
     const float fbar = -wbar / (float)N;
@@ -181,20 +208,20 @@ __global__ void k_adj_cell(GridDev g, const double *stats, const int32_t *slot, 
                 if (i < 7) z[i] = nrm_ppf(fmaxf(w[i] * e[i], 1e-37f));
             }
             if (!ok) continue;
-            P[side] += f;
+            P += f;
             if (!(f > 1e-30f)) continue;  // negligible share of value and gradient (both scale with f)
             float zbar[7];
 #pragma unroll
             for (int i = 0; i < 7; ++i) zbar[i] = 0.f;
 #pragma unroll
             for (int i = 7; i >= 0; --i) {
-                float ebar = fbar * (f / e[i]);
+                float ebar = fbar * __fdividef(f, e[i]);  // e[i] >= f > 1e-30
                 if (i < 7) {
-                    float ph = npdf(z[i]);
-                    if (ph > 0.f) ebar += zbar[i] * w[i] / ph;
+                    const float iph = 2.50662827f * __expf(0.5f * z[i] * z[i]);  // 1 / phi(z)
+                    if (iph < INFINITY) ebar = fmaf(zbar[i] * w[i], iph, ebar);
                 }
                 float ubar = ebar * npdf(u[i]);
-                bbar[side][i] += ubar * W.inv[i];
+                mbar[i] = fmaf(side == 0 ? -ubar : ubar, W.inv[i], mbar[i]);
                 float sbar = -ubar * W.inv[i];
                 Lbar[tri(i, i)] += -ubar * u[i] * W.inv[i];
 #pragma unroll
@@ -205,81 +232,102 @@ __global__ void k_adj_cell(GridDev g, const double *stats, const int32_t *slot, 
             }
         }
     }
-    // warp reductions (sample partial sums: FP64 for the probabilities, FP32 for the adjoints)
+    // warp reductions; lane t stores sums t and t + 32
+    float out0 = 0.f, out1 = 0.f;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        P[0] += __shfl_xor_sync(0xffffffffu, P[0], o);
-        P[1] += __shfl_xor_sync(0xffffffffu, P[1], o);
+    for (int t = 0; t < kRed; ++t) {
+        float v = t == 0 ? P : (t < 9 ? mbar[t - 1] : Lbar[t - 9]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (t == lane) out0 = v;
+        if (t == lane + 32) out1 = v;
     }
-#pragma unroll
-    for (int i = 0; i < 8; ++i)
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            bbar[0][i] += __shfl_xor_sync(0xffffffffu, bbar[0][i], o);
-            bbar[1][i] += __shfl_xor_sync(0xffffffffu, bbar[1][i], o);
-        }
-#pragma unroll
-    for (int t = 0; t < 36; ++t)
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) Lbar[t] += __shfl_xor_sync(0xffffffffu, Lbar[t], o);
-    if (lane != 0) return;
-    double red[2 + 16 + 36];
-    red[0] = P[0];
-    red[1] = P[1];
-    for (int i = 0; i < 8; ++i) { red[2 + i] = bbar[0][i]; red[10 + i] = bbar[1][i]; }
-    for (int t = 0; t < 36; ++t) red[18 + t] = Lbar[t];
-    double lcp = 1.0 - red[0] / N - red[1] / N;
+    red[q * kRed + lane] = out0;
+    if (lane + 32 < kRed) red[q * kRed + lane + 32] = out1;
+}
+
+// K9c: thread per kept cell: the FP64 factor again (same bits as in K9a), the Cholesky /
+// jitter adjoint Sbar = L^-T sym(Phi(L^T Lbar)) L^-1, scattered onto the per-point weights.
+__global__ void k_adj_chol(GridDev g, const double *stats, const int32_t *slot, const int64_t *cells, int64_t count,
+                           const float *dldlcp, double theta, double tau, double skip_eps, int N, Pairs pt,
+                           const AdjRec *rec, const float *red, double *G16)
+{
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= count || !rec[q].active) return;
+    const int64_t cidx = cells[q];
+    double L[8][8], mu[8];
+    int slots[8], am;
+    if (!adj_factor(g, stats, slot, cidx, dldlcp[cidx], theta, tau, skip_eps, pt, L, mu, slots, am)) return;
+    const float *rd = red + q * kRed;
+    const double lcp = 1.0 - (double)rd[0] / N;
     if (lcp < 0.0 || lcp > 1.0) return;  // clamped: constant in a neighbourhood
-    // mu adjoint: b_lo = theta - mu, b_hi = mu - theta
-    double mubar[8];
-    for (int i = 0; i < 8; ++i) mubar[i] = -red[2 + i] + red[10 + i];
-    // Cholesky adjoint: Sbar = L^-T sym(Phi(L^T Lbar)) L^-1
-    double L[8][8], Lb[8][8], Pm[8][8], T[8][8], Li[8][8], Sb[8][8];
+    double Lb[8][8], Pm[8][8], T[8][8], Li[8][8];
+#pragma unroll
     for (int i = 0; i < 8; ++i)
+#pragma unroll
         for (int j = 0; j < 8; ++j) {
-            L[i][j] = j <= i ? W.L64[tri(i, j)] : 0.0;
-            Lb[i][j] = j <= i ? red[18 + tri(i, j)] : 0.0;
+            if (j > i) L[i][j] = 0.0;
+            Lb[i][j] = j <= i ? (double)rd[9 + tri(i, j)] : 0.0;
         }
+#pragma unroll
     for (int i = 0; i < 8; ++i)
+#pragma unroll
         for (int j = 0; j < 8; ++j) {
             double s = 0.0;
+#pragma unroll
             for (int k = 0; k < 8; ++k) s += L[k][i] * Lb[k][j];
             Pm[i][j] = s;
         }
+#pragma unroll
     for (int i = 0; i < 8; ++i)
+#pragma unroll
         for (int j = 0; j < 8; ++j) T[i][j] = j < i ? Pm[i][j] : (j == i ? 0.5 * Pm[i][i] : 0.0);
+#pragma unroll
     for (int i = 0; i < 8; ++i)
+#pragma unroll
         for (int j = 0; j < 8; ++j) Pm[i][j] = 0.5 * (T[i][j] + T[j][i]);
+#pragma unroll
     for (int c = 0; c < 8; ++c)
+#pragma unroll
         for (int i = 0; i < 8; ++i) {
             double s = (i == c) ? 1.0 : 0.0;
+#pragma unroll
             for (int k = 0; k < i; ++k) s -= L[i][k] * Li[k][c];
             Li[i][c] = i < c ? 0.0 : s / L[i][i];
         }
+#pragma unroll
     for (int i = 0; i < 8; ++i)
+#pragma unroll
         for (int j = 0; j < 8; ++j) {
             double s = 0.0;
+#pragma unroll
             for (int k = 0; k < 8; ++k) s += Pm[i][k] * Li[k][j];
             T[i][j] = s;
         }
+    double tr = 0.0;
+#pragma unroll
     for (int i = 0; i < 8; ++i)
+#pragma unroll
         for (int j = 0; j < 8; ++j) {
             double s = 0.0;
+#pragma unroll
             for (int k = 0; k < 8; ++k) s += Li[k][i] * T[k][j];
-            Sb[i][j] = s;
+            Pm[i][j] = s;  // Sbar
+            if (i == j) tr += s;
         }
-    double tr = 0.0;
-    for (int i = 0; i < 8; ++i) tr += Sb[i][i];
-    Sb[W.amax][W.amax] += tau * tr;
+    // mu adjoint: b_lo = theta - mu, b_hi = mu - theta; jitter tau * max diag on the argmax
+#pragma unroll
     for (int i = 0; i < 8; ++i) {
-        double *gp = G16 + (int64_t)W.slot[i] * 16;
-        atomicAdd(gp + 0, mubar[i]);
-        atomicAdd(gp + 1, Sb[i][i]);
+        double *gp = G16 + (int64_t)slots[i] * 16;
+        atomicAdd(gp + 0, (double)rd[1 + i]);
+        atomicAdd(gp + 1, Pm[i][i] + (i == am ? tau * tr : 0.0));
     }
+#pragma unroll
     for (int a = 0; a < 8; ++a)
+#pragma unroll
         for (int b = a + 1; b < 8; ++b) {
-            int own = pt.owner[a][b] == 0 ? a : b;
-            atomicAdd(G16 + (int64_t)W.slot[own] * 16 + 2 + pt.slot[a][b], 2.0 * Sb[a][b]);
+            const int own = pt.owner[a][b] == 0 ? a : b;
+            atomicAdd(G16 + (int64_t)slots[own] * 16 + 2 + pt.slot[a][b], 2.0 * Pm[a][b]);
         }
 }
 
@@ -501,6 +549,12 @@ __global__ void k_mask_keep(uint8_t *keep, const float *dl, int64_t nc)
     if (c < nc && dl[c] == 0.0f) keep[c] = 0;
 }
 
+__global__ void k_ff_to_double(const float2 *ff, int64_t n, double *out)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (double)ff[i].x + (double)ff[i].y;
+}
+
 }  // namespace
 
 extern "C" gpr_status gpr_lcp_backward(gpr_model *M, const gpr_grid *grid, double isovalue,
@@ -518,7 +572,7 @@ extern "C" gpr_status gpr_lcp_backward(gpr_model *M, const gpr_grid *grid, doubl
     size_t b1 = Carver::round(te * 4) + Carver::round(te * 8) + Carver::round(te * 8) + 2 * Carver::round((size_t)n * 4) +
                 Carver::round((size_t)nc) + Carver::round((size_t)n) + Carver::round((size_t)n * 8) +
                 Carver::round((size_t)n * 4) + Carver::round((size_t)nc * 8) + csb +
-                Carver::round(tc_partial_elems(GPR_P_BF16X3, M, n) * 4) + 8192;
+                Carver::round(tc_partial_elems(GPR_P_BF16X3, M, n) * 4) + Carver::round(te * 8) + 8192;
     GPR_TRY(ws_reserve(M, 0, b1, st));
     Carver cv{(char *)ws_ptr(M, 0)};
     float *T32 = cv.take<float>(te);
@@ -533,6 +587,7 @@ extern "C" gpr_status gpr_lcp_backward(gpr_model *M, const gpr_grid *grid, doubl
     int64_t *clist = cv.take<int64_t>((size_t)nc);
     void *cscr = cv.take<char>(csb);
     float *part = cv.take<float>(tc_partial_elems(GPR_P_BF16X3, M, n));
+    float2 *Tu = cv.take<float2>(te);
     GPR_TRY(build_tables(M, g, T64, T32, st, Tff));
     // cells whose LCP is not identically 0 near the current parameters (same cascade as the forward)
     if (opts->prec == GPR_P_FP64) {
@@ -563,7 +618,8 @@ extern "C" gpr_status gpr_lcp_backward(gpr_model *M, const gpr_grid *grid, doubl
     size_t b2 = 2 * Carver::round((size_t)npts * mp * 8) + Carver::round((size_t)npts * 15 * 8) +
                 Carver::round((size_t)npts * 16 * 8) + Carver::round((size_t)nchunks * mp * 8) +
                 Carver::round((size_t)splits * mp * mp * 8) + 3 * Carver::round((size_t)mp * mp * 8) +
-                4 * Carver::round((size_t)mp * 8) + 4096;
+                4 * Carver::round((size_t)mp * 8) + Carver::round((size_t)ncell * sizeof(AdjRec)) +
+                Carver::round((size_t)ncell * kRed * 4) + 4096;
     GPR_TRY(ws_reserve(M, 1, b2, st));
     Carver cv2{(char *)ws_ptr(M, 1)};
     double *W = cv2.take<double>((size_t)npts * mp);
@@ -578,8 +634,22 @@ extern "C" gpr_status gpr_lcp_backward(gpr_model *M, const gpr_grid *grid, doubl
     double *t = cv2.take<double>((size_t)mp);
     double *dy = cv2.take<double>((size_t)mp);
     double *acc = cv2.take<double>(4);
-    launch_w64(M, g, T64, plist, 0, npts, W, st);
-    launch_stats_from_w64(M, g, plist, 0, npts, slot, 0, W, S15, nullptr, nullptr, nullptr, st);
+    AdjRec *arec = cv2.take<AdjRec>((size_t)ncell);
+    float *ared = cv2.take<float>((size_t)ncell * kRed);
+    if (opts->exact == GPR_EXACT_AUTO && oz_supported(M)) {
+        // FP64-class rows on the tensor cores (digit split), their float-float statistics, and the
+        // rows widened to FP64 for the FP64 chain rule below; the Zh buffer holds the pairs meanwhile
+        float2 *Wff = (float2 *)Zh;
+        GPR_TRY(oz_prepare(M, st));
+        GPR_TRY(oz_unit_tables(M, g, Tu, st));
+        GPR_TRY(launch_oz_w(M, g, Tu, plist, 0, npts, Wff, st));
+        GPR_TRY(launch_stats_ff(M, g, plist, npts, slot, Wff, S15, st));
+        k_ff_to_double<<<(unsigned)((npts * mp + 255) / 256), 256, 0, st>>>(Wff, npts * mp, W);
+        note_launch();
+    } else {
+        launch_w64(M, g, T64, plist, 0, npts, W, st);
+        launch_stats_from_w64(M, g, plist, 0, npts, slot, 0, W, S15, nullptr, nullptr, nullptr, st);
+    }
     GPR_CUDA_TRY(cudaMemsetAsync(G16, 0, sizeof(double) * (size_t)npts * 16, st));
     GPR_CUDA_TRY(cudaMemsetAsync(acc, 0, sizeof(double) * 4, st));
     static Pairs pt = make_pairs();
@@ -593,10 +663,23 @@ extern "C" gpr_status gpr_lcp_backward(gpr_model *M, const gpr_grid *grid, doubl
     }
     {
         ProfScope ps("adj_cell", st);
-        k_adj_cell<<<(unsigned)((ncell + 7) / 8), 256, 0, st>>>(g, S15, slot, clist, ncell, dL_dlcp, isovalue,
-                                                               opts->jitter, opts->skip_eps, opts->n_samples, opts->seed,
-                                                               lat, pt, G16);
+        {
+            ProfScope p1("adj_prep", st);
+            k_adj_prep<<<(unsigned)((ncell + 127) / 128), 128, 0, st>>>(g, S15, slot, clist, ncell, dL_dlcp, isovalue,
+                                                                        opts->jitter, opts->skip_eps, pt, arec);
+        }
+        {
+            ProfScope p2("adj_sample", st);
+            k_adj_sample<<<(unsigned)((ncell + 7) / 8), 256, 0, st>>>(arec, clist, ncell, dL_dlcp, opts->n_samples,
+                                                                      opts->seed, lat, ared);
+        }
+        ProfScope p3("adj_chol", st);
+        k_adj_chol<<<(unsigned)((ncell + 127) / 128), 128, 0, st>>>(g, S15, slot, clist, ncell, dL_dlcp, isovalue,
+                                                                    opts->jitter, opts->skip_eps, opts->n_samples, pt,
+                                                                    arec, ared, G16);
     }
+    note_launch();
+    note_launch();
     note_launch();
     // t = W^T g_mu
     k_wt_vec<<<dim3((unsigned)((mp + 255) / 256), (unsigned)nchunks), 256, 0, st>>>(W, G16, npts, mp, chunk, tp);

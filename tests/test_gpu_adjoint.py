@@ -45,13 +45,16 @@ def test_backward_small_vs_oracle(torch, g, prec):
     assert _rel(dl, odl) <= 2e-3, (dl, odl)
 
 
-def test_backward_config5_field_32cubed_vs_oracle(torch, g):
+@pytest.mark.parametrize("exact", ["auto", "fp64"])
+def test_backward_config5_field_32cubed_vs_oracle(torch, g, exact):
     """The differentiation workload's field (m=500, ARD SE, noise 1e-4) on a 32^3 grid with U(0,1)
-    cell weights: GPU gradient vs the oracle's FP64 analytic gradient."""
+    cell weights: GPU gradient vs the oracle's FP64 analytic gradient, with the corner rows from
+    the tensor-core digit split (auto) and from the FP64 cores."""
     w = workloads.config5()
     n, th = 32, w.isovalues[0]
     wts = np.random.default_rng(5).random((n - 1) ** 3)
-    dy, dl = _gpu_grad(g, torch, w, n, th, wts)
+    ex = g.GPR_EXACT_AUTO if exact == "auto" else g.GPR_EXACT_FP64
+    dy, dl = _gpu_grad(g, torch, w, n, th, wts, exact=ex)
     loss, ody, odl = oracle.Model.from_workload(w).lcp_grad(n, th, wts)
     assert _rel(dy, ody) <= 2e-3 and _rel(dl, odl) <= 2e-3, (_rel(dy, ody), dl, odl)
 
