@@ -65,6 +65,9 @@ SIGNATURES = {
                                          C.c_void_p]),
     "gpr_normal_approx_eval": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]),
     "gpr_autotune_force": (None, [C.c_char_p, C.c_int]),
+    "gpr_oz_mul_tn_test": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_int64, C.c_int32, C.c_void_p,
+                                     C.c_void_p]),
+    "gpr_oz_mul_linv_test": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
     "gpr_octree_trace": (C.c_int, [C.c_void_p, C.POINTER(GridC), C.c_double, C.c_int32, C.POINTER(LcpOptionsC),
                                    C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
                                    C.POINTER(C.c_int64), C.c_void_p]),

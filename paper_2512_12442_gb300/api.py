@@ -212,6 +212,23 @@ def gpr_stats_points_split(model: Model, grid: GridC, point_idx, stats, stream=N
     _check(rc, "gpr_stats_points_split")
 
 
+def gpr_oz_mul_tn_test(A, B, kchunk=0, nsplit=19, stream=None):
+    """Test hook: C = A^T B (device FP64 K x nc tensors) by the tensor-core digit split."""
+    K, nc = A.shape
+    out = A.new_zeros((nc, nc))
+    _check(load().gpr_oz_mul_tn_test(_ptr(A), _ptr(B), K, nc, int(kchunk), int(nsplit), _ptr(out), _stream(stream)),
+           "gpr_oz_mul_tn_test")
+    return out
+
+
+def gpr_oz_mul_linv_test(model: Model, X, stream=None):
+    """Test hook: X L^-1 (device FP64 rows x m) by the tensor-core digit split."""
+    out = X.new_zeros(X.shape)
+    _check(load().gpr_oz_mul_linv_test(model.handle, _ptr(X), int(X.shape[0]), _ptr(out), _stream(stream)),
+           "gpr_oz_mul_linv_test")
+    return out
+
+
 def gpr_model_export(model: Model):
     """Test hook: FP64 factors of the device model as numpy arrays."""
     m = model.m

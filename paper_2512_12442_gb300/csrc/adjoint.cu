@@ -636,7 +636,8 @@ extern "C" gpr_status gpr_lcp_backward(gpr_model *M, const gpr_grid *grid, doubl
     double *acc = cv2.take<double>(4);
     AdjRec *arec = cv2.take<AdjRec>((size_t)ncell);
     float *ared = cv2.take<float>((size_t)ncell * kRed);
-    if (opts->exact == GPR_EXACT_AUTO && oz_supported(M)) {
+    const bool use_oz = opts->exact == GPR_EXACT_AUTO && oz_supported(M);
+    if (use_oz) {
         // FP64-class rows on the tensor cores (digit split), their float-float statistics, and the
         // rows widened to FP64 for the FP64 chain rule below; the Zh buffer holds the pairs meanwhile
         float2 *Wff = (float2 *)Zh;
@@ -689,11 +690,14 @@ extern "C" gpr_status gpr_lcp_backward(gpr_model *M, const gpr_grid *grid, doubl
     // Zh rows, R = Zh^T W (split over points), M = R - v t^T, N = L^-T M L^-1
     k_zhat<<<(unsigned)((npts + 7) / 8), 256, 0, st>>>(g, plist, npts, slot, W, G16, mp, Zh);
     note_launch();
+    // R splits: 19 x (mp/64) x (mp/128) tiles = 608 CTAs = 4 waves of 152 for mp = 512
+    const int rsplits = use_oz ? 19 : splits;
     {
         ProfScope ps("adj_R", st);
-        gemm64<true, false>(mp, mp, npts, Zh, mp, W, mp, Rp, mp, splits, st);
+        if (use_oz) GPR_TRY(oz_mul_tn(Zh, W, npts, m, mp, Rp, rsplits, st));
+        else gemm64<true, false>(mp, mp, npts, Zh, mp, W, mp, Rp, mp, splits, st);
     }
-    k_sum_rows<<<(unsigned)((mp * mp + 255) / 256), 256, 0, st>>>(Rp, splits, mp * mp, R);
+    k_sum_rows<<<(unsigned)((mp * mp + 255) / 256), 256, 0, st>>>(Rp, rsplits, mp * mp, R);
     note_launch();
     k_form_m<<<(unsigned)((mp * mp + 255) / 256), 256, 0, st>>>(R, M->vy, t, m, mp);
     note_launch();
@@ -705,7 +709,8 @@ extern "C" gpr_status gpr_lcp_backward(gpr_model *M, const gpr_grid *grid, doubl
     // Z = Zh L^-1 into the W buffer (W no longer needed), then the per-point terms
     {
         ProfScope ps("adj_Z", st);
-        gemm64<false, true>(npts, m, m, Zh, mp, M->Linv, mb, W, mp, 1, st);
+        if (use_oz) GPR_TRY(oz_mul_linv(M, Zh, npts, mp, W, mp, st));
+        else gemm64<false, true>(npts, m, m, Zh, mp, M->Linv, mb, W, mp, 1, st);
     }
     KdPrior kdp;
     for (int e = 0; e < 13; ++e) {

@@ -192,6 +192,13 @@ gpr_status launch_oz_w(const gpr_model *M, const GridDev &g, const float2 *Tu, c
 gpr_status launch_stats_ff(const gpr_model *M, const GridDev &g, const int64_t *pts, int64_t count, const int32_t *slot,
                            const float2 *W, double *out15, cudaStream_t st, bool out_by_point = false,
                            int64_t row_mod = 0);
+// FP64-class products of FP64 matrices by the same digit split (42-bit fixed-point digits per
+// row / column exponent): C = X L^-1 (X rows x m, ld ldx; C ld ldc), and C = A^T B for
+// A, B: K x nc (ld) as nsplit partials of (nc rounded up to 64)^2 whose sum is C.
+gpr_status oz_mul_linv(gpr_model *M, const double *X, int64_t rows, int64_t ldx, double *C, int64_t ldc,
+                       cudaStream_t st);
+gpr_status oz_mul_tn(const double *A, const double *B, int64_t K, int64_t nc, int64_t ld, double *part, int nsplit,
+                     cudaStream_t st, int64_t kchunk = 0);
 
 // ---- per-model, per-grid cache of isovalue-independent results (cache.cu)
 struct GridCache {

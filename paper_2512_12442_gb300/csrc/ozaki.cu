@@ -169,15 +169,160 @@ __host__ __device__ constexpr uint32_t idesc_n(int n)
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
 }
 
+// The pipeline shared by the digit-split GEMMs.  Stage layout: S A slices (TM rows x 64 B) then
+// S B slices (TN rows x 64 B) per K block of BKE digits.
+template <int S>
+struct OzPipe {
+    static constexpr int A_ST = S * A_SLICE, B_ST = S * B_SLICE, STAGE = A_ST + B_ST;
+    unsigned char *smem;
+    uint32_t full0, empty0, done, drained, tmem;
+};
+
+// Producer (one thread): K blocks kb0 .. kb0 + nkb - 1 of all A slices (rows arow ..) and all
+// B slices (rows brow ..), one 3-D TMA copy each, into a two-stage ring.
+template <int S>
+__device__ __forceinline__ void oz_produce(const OzPipe<S> &P, const CUtensorMap *mapA, const CUtensorMap *mapB, int kb0,
+                                           int nkb, int arow, int brow, bool &ok)
+{
+    for (int kb = 0; kb < nkb; ++kb) {
+        const int s = kb & 1;
+        unsigned char *st = P.smem + s * OzPipe<S>::STAGE;
+        if (kb >= 2 && !wait_bar(P.empty0 + 8 * s, ((kb >> 1) - 1) & 1)) ok = false;
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(P.full0 + 8 * s),
+                     "r"((uint32_t)OzPipe<S>::STAGE)
+                     : "memory");
+        asm volatile(
+            "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
+            "%4}], [%5];" ::"r"(su32(st)),
+            "l"((uint64_t)mapA), "r"((kb0 + kb) * BKE), "r"(arow), "r"(0), "r"(P.full0 + 8 * s)
+            : "memory");
+        asm volatile(
+            "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
+            "%4}], [%5];" ::"r"(su32(st + OzPipe<S>::A_ST)),
+            "l"((uint64_t)mapB), "r"((kb0 + kb) * BKE), "r"(brow), "r"(0), "r"(P.full0 + 8 * s)
+            : "memory");
+    }
+}
+
+// MMA issue (one thread): A slice sa against B slices 0 .. S-1-sa, contiguous rows of the B
+// stage, onto TMEM levels sa .. S-1; `done` after every KCH blocks, then wait for the drain.
+template <int S>
+__device__ __forceinline__ void oz_issue(const OzPipe<S> &P, int nkb, bool &ok)
+{
+    for (int kb = 0; kb < nkb; ++kb) {
+        const int s = kb & 1;
+        unsigned char *st = P.smem + s * OzPipe<S>::STAGE;
+        if (!wait_bar(P.full0 + 8 * s, (kb >> 1) & 1)) ok = false;
+        if (kb % KCH == 0 && kb > 0 && !wait_bar(P.drained, ((kb / KCH) - 1) & 1)) ok = false;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t ab = su32(st), bb = su32(st + OzPipe<S>::A_ST);
+#pragma unroll
+        for (int kk = 0; kk < 2; ++kk)
+#pragma unroll
+            for (int sa = 0; sa < S; ++sa) {
+                const int nrow = (S - sa) * TN;
+#pragma unroll
+                for (int p0 = 0; p0 < nrow; p0 += 256) {
+                    const int nn = nrow - p0 < 256 ? nrow - p0 : 256;
+                    const uint32_t acc = (kb % KCH == 0 && kk == 0 && sa == 0) ? 0u : 1u;
+                    asm volatile(
+                        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+                            P.tmem + (uint32_t)(sa * TN + p0)),
+                        "l"(desc_sw64(ab + sa * A_SLICE + kk * 32)), "l"(desc_sw64(bb + p0 * 64 + kk * 32)),
+                        "r"(idesc_n(nn)), "r"(acc));
+                }
+            }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(P.empty0 + 8 * s)
+                     : "memory");
+        if (kb == nkb - 1 || kb % KCH == KCH - 1)
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(P.done)
+                         : "memory");
+    }
+}
+
+// Drain (warps 2-9): warp w reads TMEM lanes 32 (w % 4), columns 32 ((w - 2) / 4) of every
+// level after each K chunk and adds the exact level sums, smallest first, in float-float.
+template <int S>
+__device__ __forceinline__ void oz_drain(const OzPipe<S> &P, int nch, int lq, int half, int lane, FF acc[32], bool &ok)
+{
+#pragma unroll
+    for (int c = 0; c < 32; ++c) acc[c] = FF{0.f, 0.f};
+    for (int ch = 0; ch < nch; ++ch) {
+        if (!wait_bar(P.done, (uint32_t)(ch & 1))) ok = false;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+        for (int lvl = S - 1; lvl >= 0; --lvl) {
+            uint32_t rr[32];
+            const uint32_t taddr = P.tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(lvl * TN + half * 32);
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+                "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                : "=r"(rr[0]), "=r"(rr[1]), "=r"(rr[2]), "=r"(rr[3]), "=r"(rr[4]), "=r"(rr[5]), "=r"(rr[6]),
+                  "=r"(rr[7]), "=r"(rr[8]), "=r"(rr[9]), "=r"(rr[10]), "=r"(rr[11]), "=r"(rr[12]), "=r"(rr[13]),
+                  "=r"(rr[14]), "=r"(rr[15]), "=r"(rr[16]), "=r"(rr[17]), "=r"(rr[18]), "=r"(rr[19]), "=r"(rr[20]),
+                  "=r"(rr[21]), "=r"(rr[22]), "=r"(rr[23]), "=r"(rr[24]), "=r"(rr[25]), "=r"(rr[26]), "=r"(rr[27]),
+                  "=r"(rr[28]), "=r"(rr[29]), "=r"(rr[30]), "=r"(rr[31])
+                : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            const float wgt = ldexpf(1.0f, -BETA * (lvl + 2));
+#pragma unroll
+            for (int c = 0; c < 32; ++c) acc[c] = ff_add_f(acc[c], __uint_as_float(rr[c]) * wgt);
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (ch < nch - 1 && lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(P.drained) : "memory");
+    }
+}
+
+// Barriers and the 512 TMEM columns of a digit-split GEMM CTA (G_NTHR threads).
+template <int S>
+__device__ __forceinline__ OzPipe<S> oz_setup(unsigned char *smem_raw, uint32_t *tmem_slot)
+{
+    OzPipe<S> P;
+    P.smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t *bars = (uint64_t *)(P.smem + 2 * OzPipe<S>::STAGE);  // full[2], empty[2], done, drained
+    P.full0 = su32(&bars[0]);
+    P.empty0 = su32(&bars[2]);
+    P.done = su32(&bars[4]);
+    P.drained = su32(&bars[5]);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    if (tid == 0) {
+        for (int b = 0; b < 5; ++b) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&bars[b])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 8;" ::"r"(P.drained));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(su32(tmem_slot)));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    P.tmem = *tmem_slot;
+    return P;
+}
+
+__device__ __forceinline__ void oz_teardown(uint32_t tmem, bool ok, int *status)
+{
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (!ok) atomicCAS(status, 0, (int)GPR_ERR_TIMEOUT);
+    if ((threadIdx.x >> 5) == 0) {
+        __syncwarp();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem));
+    }
+}
+
+// W rows: kernel-row digits (A, 128 points) x L^-1 digits (B, 64 output columns); B is lower
+// triangular, so K stops at the tile's last column.
 template <int S>
 __global__ void __launch_bounds__(G_NTHR, 1) k_oz_gemm(const __grid_constant__ CUtensorMap mapA,
                                                       const __grid_constant__ CUtensorMap mapB, OzParams prm)
 {
-    constexpr int A_ST = S * A_SLICE, B_ST = S * B_SLICE, STAGE = A_ST + B_ST;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint64_t *bars = (uint64_t *)(smem + 2 * STAGE);  // full[2], empty[2], done, drained
     __shared__ uint32_t tmem_slot;
+    const OzPipe<S> P = oz_setup<S>(smem_raw, &tmem_slot);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     // N tiles fastest: the tiles of one row block run together and share its A digits in L2
     const int64_t row0 = (int64_t)blockIdx.y * TM;
@@ -186,104 +331,16 @@ __global__ void __launch_bounds__(G_NTHR, 1) k_oz_gemm(const __grid_constant__ C
     const int64_t kend = (int64_t)n0 + TN < m ? (int64_t)n0 + TN : m;
     const int nkb = (int)((kend + BKE - 1) / BKE);
     const int nch = (nkb + KCH - 1) / KCH;
-    const uint32_t full0 = su32(&bars[0]), empty0 = su32(&bars[2]), done = su32(&bars[4]), drained = su32(&bars[5]);
-    if (tid == 0) {
-        for (int b = 0; b < 5; ++b) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&bars[b])));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 8;" ::"r"(drained));
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(su32(&tmem_slot)));
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const uint32_t tmem = tmem_slot;
     bool ok = true;
 
     if (warp == 0 && lane == 0) {
-        // producer: all A slices (box 32 k x 128 rows x S) and all B slices (32 k x 64 x S) per K block
-        for (int kb = 0; kb < nkb; ++kb) {
-            const int s = kb & 1;
-            unsigned char *st = smem + s * STAGE;
-            if (kb >= 2 && !wait_bar(empty0 + 8 * s, ((kb >> 1) - 1) & 1)) ok = false;
-            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(full0 + 8 * s),
-                         "r"((uint32_t)STAGE)
-                         : "memory");
-            asm volatile(
-                "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
-                "%4}], [%5];" ::"r"(su32(st)),
-                "l"((uint64_t)&mapA), "r"(kb * BKE), "r"((int)row0), "r"(0), "r"(full0 + 8 * s)
-                : "memory");
-            asm volatile(
-                "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
-                "%4}], [%5];" ::"r"(su32(st + A_ST)),
-                "l"((uint64_t)&mapB), "r"(kb * BKE), "r"(n0), "r"(0), "r"(full0 + 8 * s)
-                : "memory");
-        }
+        oz_produce<S>(P, &mapA, &mapB, 0, nkb, (int)row0, n0, ok);
     } else if (warp == 1 && lane == 0) {
-        // MMA issue: A slice sa against B slices 0 .. S-1-sa, contiguous rows of the B stage
-        for (int kb = 0; kb < nkb; ++kb) {
-            const int s = kb & 1;
-            unsigned char *st = smem + s * STAGE;
-            if (!wait_bar(full0 + 8 * s, (kb >> 1) & 1)) ok = false;
-            if (kb % KCH == 0 && kb > 0 && !wait_bar(drained, ((kb / KCH) - 1) & 1)) ok = false;
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t ab = su32(st), bb = su32(st + A_ST);
-#pragma unroll
-            for (int kk = 0; kk < 2; ++kk)
-#pragma unroll
-                for (int sa = 0; sa < S; ++sa) {
-                    const int nrow = (S - sa) * TN;
-#pragma unroll
-                    for (int p0 = 0; p0 < nrow; p0 += 256) {
-                        const int nn = nrow - p0 < 256 ? nrow - p0 : 256;
-                        const uint32_t acc = (kb % KCH == 0 && kk == 0 && sa == 0) ? 0u : 1u;
-                        asm volatile(
-                            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
-                                tmem + (uint32_t)(sa * TN + p0)),
-                            "l"(desc_sw64(ab + sa * A_SLICE + kk * 32)), "l"(desc_sw64(bb + p0 * 64 + kk * 32)),
-                            "r"(idesc_n(nn)), "r"(acc));
-                    }
-                }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(empty0 + 8 * s)
-                         : "memory");
-            if (kb == nkb - 1 || kb % KCH == KCH - 1)
-                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(done)
-                             : "memory");
-        }
+        oz_issue<S>(P, nkb, ok);
     } else if (warp >= 2) {
-        // drain: warp w reads TMEM lanes 32 (w % 4), columns 32 ((w - 2) / 4) of every level
         const int lq = warp & 3, half = (warp - 2) >> 2;
         FF acc[32];
-#pragma unroll
-        for (int c = 0; c < 32; ++c) acc[c] = FF{0.f, 0.f};
-        for (int ch = 0; ch < nch; ++ch) {
-            if (!wait_bar(done, (uint32_t)(ch & 1))) ok = false;
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-#pragma unroll
-            for (int lvl = S - 1; lvl >= 0; --lvl) {
-                uint32_t rr[32];
-                const uint32_t taddr = tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(lvl * TN + half * 32);
-                asm volatile(
-                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
-                    "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-                    : "=r"(rr[0]), "=r"(rr[1]), "=r"(rr[2]), "=r"(rr[3]), "=r"(rr[4]), "=r"(rr[5]), "=r"(rr[6]),
-                      "=r"(rr[7]), "=r"(rr[8]), "=r"(rr[9]), "=r"(rr[10]), "=r"(rr[11]), "=r"(rr[12]), "=r"(rr[13]),
-                      "=r"(rr[14]), "=r"(rr[15]), "=r"(rr[16]), "=r"(rr[17]), "=r"(rr[18]), "=r"(rr[19]), "=r"(rr[20]),
-                      "=r"(rr[21]), "=r"(rr[22]), "=r"(rr[23]), "=r"(rr[24]), "=r"(rr[25]), "=r"(rr[26]), "=r"(rr[27]),
-                      "=r"(rr[28]), "=r"(rr[29]), "=r"(rr[30]), "=r"(rr[31])
-                    : "r"(taddr));
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                const float wgt = ldexpf(1.0f, -BETA * (lvl + 2));
-#pragma unroll
-                for (int c = 0; c < 32; ++c) acc[c] = ff_add_f(acc[c], __uint_as_float(rr[c]) * wgt);
-            }
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            __syncwarp();
-            if (ch < nch - 1 && lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(drained) : "memory");
-        }
+        oz_drain<S>(P, nch, lq, half, lane, acc, ok);
         const int64_t row = row0 + lq * 32 + lane;
         if (row < prm.count) {
             int64_t p = prm.pts ? prm.pts[row] : prm.pt_base + row;
@@ -302,14 +359,63 @@ __global__ void __launch_bounds__(G_NTHR, 1) k_oz_gemm(const __grid_constant__ C
             }
         }
     }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    if (!ok) atomicCAS(prm.status, 0, (int)GPR_ERR_TIMEOUT);
-    if (warp == 0) {
-        __syncwarp();
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem));
+    oz_teardown(P.tmem, ok, prm.status);
+}
+
+// General FP64-class product C = A B of FP64 matrices given as digit slices: A rows (M, K-major,
+// row r scaled by 2^-ea[r]) and B columns (N rows of K, column j scaled by 2^-eb[j]); C is
+// written in FP64, scaled back by 2^(ea + eb) (or added to C).  Split z of the K range
+// (kb_per_split blocks) writes its own partial at C + z cstride; with lower_b (B[k][j] = 0 for
+// k < j) K starts at the tile's first column instead.
+struct OzG {
+    int64_t M, N, kblocks, kb_per_split;
+    int lower_b, accumulate;  // accumulate: C += A B
+    const int *ea, *eb;
+    double *C;
+    int64_t ldc, cstride;
+    int *status;
+};
+
+template <int S>
+__global__ void __launch_bounds__(G_NTHR, 1) k_oz_dgemm(const __grid_constant__ CUtensorMap mapA,
+                                                       const __grid_constant__ CUtensorMap mapB, OzG prm)
+{
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __shared__ uint32_t tmem_slot;
+    const OzPipe<S> P = oz_setup<S>(smem_raw, &tmem_slot);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int64_t row0 = (int64_t)blockIdx.y * TM;
+    const int n0 = blockIdx.x * TN;
+    int64_t kb0 = prm.lower_b ? n0 / BKE : (int64_t)blockIdx.z * prm.kb_per_split;
+    int64_t kb1 = prm.lower_b ? prm.kblocks : kb0 + prm.kb_per_split;
+    if (kb1 > prm.kblocks) kb1 = prm.kblocks;
+    const int nkb = kb1 > kb0 ? (int)(kb1 - kb0) : 0;
+    const int nch = (nkb + KCH - 1) / KCH;
+    bool ok = true;
+
+    if (warp == 0 && lane == 0) {
+        oz_produce<S>(P, &mapA, &mapB, (int)kb0, nkb, (int)row0, n0, ok);
+    } else if (warp == 1 && lane == 0) {
+        oz_issue<S>(P, nkb, ok);
+    } else if (warp >= 2) {
+        const int lq = warp & 3, half = (warp - 2) >> 2;
+        FF acc[32];
+        oz_drain<S>(P, nch, lq, half, lane, acc, ok);
+        const int64_t row = row0 + lq * 32 + lane;
+        if (row < prm.M) {
+            const int er = prm.ea[row];
+            double *out = prm.C + (int64_t)blockIdx.z * prm.cstride + row * prm.ldc;
+#pragma unroll
+            for (int c = 0; c < 32; ++c) {
+                const int64_t j = n0 + half * 32 + c;
+                if (j < prm.N) {
+                    const double v = ldexp((double)acc[c].h + (double)acc[c].l, er + prm.eb[j]);
+                    out[j] = prm.accumulate ? out[j] + v : v;
+                }
+            }
+        }
     }
+    oz_teardown(P.tmem, ok, prm.status);
 }
 
 // Digit slices of b' = [L^-1]_ji / 2^F_j, layout [S][mpt rows j][mpt cols i] (K-major), BF16.
@@ -467,6 +573,126 @@ __global__ void k_vyff(const double *vy, int64_t mp, float2 *out)
     out[i] = make_float2(h, (float)(v - (double)h));
 }
 
+// Digits of an FP64 value x with |x| < 2^e: the fixed-point integer q = round(x 2^(42-e))
+// (|q| <= 2^42, from the bit pattern: integer work only) in balanced base 64, most significant
+// first: q = sum_s d_s 2^(6(6-s)), |d_0| <= 64, |d_s| <= 32.  Zero and subnormal x give 0.
+__device__ __forceinline__ void fixed_digits7(double x, int e, float d[7])
+{
+    const long long bits = __double_as_longlong(x);
+    const int E = (int)((bits >> 52) & 0x7FF);
+    long long q = 0;
+    if (E != 0) {
+        const long long mant = (bits & 0xFFFFFFFFFFFFFLL) | (1LL << 52);  // x = mant 2^(E - 1075)
+        const int rs = 1033 + e - E;                                        // q = mant 2^-rs, rs >= 11
+        if (rs < 63) q = (mant + (1LL << (rs - 1))) >> rs;
+        if (bits < 0) q = -q;
+    }
+#pragma unroll
+    for (int t = 0; t < 6; ++t) {
+        const int sh = 6 * (6 - t);
+        const long long dt = (q + (1LL << (sh - 1))) >> sh;  // floor: balanced digit
+        d[t] = (float)dt;
+        q -= dt * (1LL << sh);
+    }
+    d[6] = (float)q;
+}
+
+// Power-of-two exponent e with |x| < 2^e for every x of a slice whose largest magnitude is mx.
+__device__ __forceinline__ int exp_above(double mx)
+{
+    int e = 0;
+    if (mx > 0.0) frexp(mx, &e);
+    return e;
+}
+
+// Row digits (K-major as stored): out[s][r][k] for rows r < rows of X (ld ldx), k < kv, zero
+// to kpad; ea[r] the row's exponent.  Warp per row.
+__global__ void k_oz_rowdig(const double *X, int64_t ldx, int64_t rows, int64_t kv, int64_t kpad, __nv_bfloat16 *out,
+                            int *ea)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t r = blockIdx.x * (int64_t)(blockDim.x >> 5) + warp;
+    if (r >= rows) return;
+    const double *x = X + r * ldx;
+    double mx = 0.0;
+    for (int64_t k = lane; k < kv; k += 32) mx = fmax(mx, fabs(x[k]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    const int e = exp_above(mx);
+    if (lane == 0) ea[r] = e;
+    for (int64_t k0 = (int64_t)lane * 8; k0 < kpad; k0 += 256) {
+        float d[7][8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            float t[7];
+            fixed_digits7(k0 + c < kv ? x[k0 + c] : 0.0, e, t);
+#pragma unroll
+            for (int q = 0; q < 7; ++q) d[q][c] = t[q];
+        }
+#pragma unroll
+        for (int q = 0; q < 7; ++q) {
+            uint32_t wd[4];
+#pragma unroll
+            for (int h = 0; h < 4; ++h)
+                wd[h] = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(d[q][2 * h])) |
+                        ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(d[q][2 * h + 1])) << 16);
+            *(uint4 *)(out + ((int64_t)q * rows + r) * kpad + k0) = make_uint4(wd[0], wd[1], wd[2], wd[3]);
+        }
+    }
+}
+
+// Largest magnitude per column over rows [0, rows) of X (ld ldx), columns < nc: non-negative
+// doubles order like their bit patterns, so an integer atomicMax suffices (cmax zeroed first).
+__global__ void k_oz_colmax(const double *X, int64_t ldx, int64_t rows, int64_t nc, int64_t rows_per_block,
+                            unsigned long long *cmax)
+{
+    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c >= nc) return;
+    const int64_t r0 = blockIdx.y * rows_per_block, r1 = r0 + rows_per_block < rows ? r0 + rows_per_block : rows;
+    double mx = 0.0;
+    for (int64_t r = r0; r < r1; ++r) mx = fmax(mx, fabs(X[r * ldx + c]));
+    atomicMax(cmax + c, (unsigned long long)__double_as_longlong(mx));
+}
+
+__global__ void k_oz_colexp(const unsigned long long *cmax, int64_t n, int *e)
+{
+    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c < n) e[c] = exp_above(__longlong_as_double((long long)cmax[c]));
+}
+
+// Column digits (the transpose, K-major over rows): out[s][c][r] for columns c < ncpad (zero
+// from nc) and rows r < kpad (zero from rows), column c scaled by 2^-e[c]; with `lower`,
+// X[r][c] = 0 for r < c.  Thread per column and 16 consecutive rows.
+__global__ void k_oz_coldig(const double *X, int64_t ldx, int64_t rows, int64_t nc, int64_t ncpad, int64_t kpad,
+                            int lower, const int *e, __nv_bfloat16 *out)
+{
+    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t r0 = (int64_t)blockIdx.y * 16;
+    if (c >= ncpad || r0 >= kpad) return;
+    const int ec = c < nc ? e[c] : 0;
+    float d[7][16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        const int64_t r = r0 + i;
+        const double v = (c < nc && r < rows && !(lower && r < c)) ? X[r * ldx + c] : 0.0;
+        float t[7];
+        fixed_digits7(v, ec, t);
+#pragma unroll
+        for (int q = 0; q < 7; ++q) d[q][i] = t[q];
+    }
+#pragma unroll
+    for (int q = 0; q < 7; ++q) {
+        uint32_t wd[8];
+#pragma unroll
+        for (int h = 0; h < 8; ++h)
+            wd[h] = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(d[q][2 * h])) |
+                    ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(d[q][2 * h + 1])) << 16);
+        uint4 *o = (uint4 *)(out + ((int64_t)q * ncpad + c) * kpad + r0);
+        o[0] = make_uint4(wd[0], wd[1], wd[2], wd[3]);
+        o[1] = make_uint4(wd[4], wd[5], wd[6], wd[7]);
+    }
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 encoder()
 {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -491,6 +717,9 @@ struct OzOperands {
     float *colscale = nullptr;
     float2 *vyff = nullptr;
     CUtensorMap map;
+    void *Bc = nullptr;  // S x mpt x mpt BF16 digits of the columns of L^-1 (for X L^-1)
+    int *ec = nullptr;   // their exponents
+    CUtensorMap mapc;
 };
 
 bool oz_supported(const gpr_model *M) { return M->kp.kind == GPR_K_SE; }
@@ -548,6 +777,7 @@ void oz_release(gpr_model *M)
 {
     if (!M->oz) return;
     cudaFree(M->oz->B); cudaFree(M->oz->colscale); cudaFree(M->oz->vyff);
+    cudaFree(M->oz->Bc); cudaFree(M->oz->ec);
     delete M->oz;
     M->oz = nullptr;
 }
@@ -710,6 +940,180 @@ gpr_status launch_stats_ff(const gpr_model *M, const GridDev &g, const int64_t *
     return GPR_OK;
 }
 
+// 3-D tensor map over BF16 digit slices [S][rows][kpad], boxes of BKE digits x box_rows x S.
+static bool encode_digits(CUtensorMap *map, void *base, int64_t kpad, int64_t rows, int box_rows)
+{
+    auto enc = encoder();
+    if (!enc) return false;
+    constexpr int S = 7;
+    cuuint64_t gdim[3] = {(cuuint64_t)kpad, (cuuint64_t)rows, (cuuint64_t)S};
+    cuuint64_t gstride[2] = {(cuuint64_t)kpad * 2, (cuuint64_t)rows * kpad * 2};
+    cuuint32_t box[3] = {BKE, (cuuint32_t)box_rows, (cuuint32_t)S};
+    cuuint32_t estr[3] = {1, 1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, gdim, gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+static size_t dgemm_smem()
+{
+    constexpr int S = 7;
+    return 2 * (size_t)(S * A_SLICE + S * B_SLICE) + 64 + 1024;
+}
+
+// Digits of the columns of L^-1 (lower triangular), built once per model.
+gpr_status oz_prepare_cols(gpr_model *M, cudaStream_t st)
+{
+    GPR_TRY(oz_prepare(M, st));
+    std::lock_guard<std::mutex> lock(M->init_mu);
+    OzOperands *O = M->oz;
+    if (O->Bc) return GPR_OK;
+    constexpr int S = 7;
+    const int64_t mpt = O->mpt, m = M->m, mb = (m + 31) / 32 * 32;
+    void *Bc = nullptr;
+    int *ec = nullptr;
+    unsigned long long *cmax = nullptr;
+    cudaError_t e = cudaMalloc(&Bc, (size_t)S * mpt * mpt * 2);
+    if (e == cudaSuccess) e = cudaMalloc(&ec, sizeof(int) * mpt);
+    if (e == cudaSuccess) e = cudaMalloc(&cmax, sizeof(unsigned long long) * mpt);
+    if (e != cudaSuccess) {
+        cudaFree(Bc); cudaFree(ec); cudaFree(cmax);
+        return e == cudaErrorMemoryAllocation ? GPR_ERR_OOM : GPR_ERR_CUDA;
+    }
+    GPR_CUDA_TRY(cudaMemsetAsync(cmax, 0, sizeof(unsigned long long) * mpt, st));
+    GPR_CUDA_TRY(cudaMemsetAsync(ec, 0, sizeof(int) * mpt, st));
+    k_oz_colmax<<<dim3((unsigned)((m + 255) / 256), (unsigned)((m + 63) / 64)), 256, 0, st>>>(M->Linv, mb, m, m, 64, cmax);
+    k_oz_colexp<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(cmax, m, ec);
+    k_oz_coldig<<<dim3((unsigned)((mpt + 127) / 128), (unsigned)(mpt / 16)), 128, 0, st>>>(M->Linv, mb, m, m, mpt, mpt,
+                                                                                       1, ec, (__nv_bfloat16 *)Bc);
+    note_launch();
+    note_launch();
+    note_launch();
+    GPR_CUDA_TRY(cudaGetLastError());
+    GPR_CUDA_TRY(cudaStreamSynchronize(st));
+    cudaFree(cmax);
+    if (!encode_digits(&O->mapc, Bc, mpt, mpt, TN)) {
+        cudaFree(Bc); cudaFree(ec);
+        return GPR_ERR_UNSUPPORTED;
+    }
+    O->ec = ec;
+    O->Bc = Bc;
+    return GPR_OK;
+}
+
+// FP64-class C = X L^-1 (X: rows x m FP64, ld ldx; C: rows x m, ld ldc) on the tensor cores.
+gpr_status oz_mul_linv(gpr_model *M, const double *X, int64_t rows, int64_t ldx, double *C, int64_t ldc,
+                       cudaStream_t st)
+{
+    if (rows <= 0) return GPR_OK;
+    GPR_TRY(oz_prepare_cols(M, st));
+    const OzOperands *O = M->oz;
+    constexpr int S = 7;
+    const int64_t mpt = O->mpt, m = M->m;
+    const size_t per_row = (size_t)mpt * 2 * S + sizeof(int);
+    int64_t chunk = (int64_t)(((size_t)3 << 29) / per_row) / TM * TM;
+    if (chunk < TM) chunk = TM;
+    if (chunk > rows) chunk = rows;
+    const size_t smem = dgemm_smem();
+    GPR_CUDA_TRY(cudaFuncSetAttribute(k_oz_dgemm<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    AdigBuf *buf = nullptr;
+    GPR_TRY(adig_acquire((size_t)chunk * per_row + 256, st, &buf));
+    __nv_bfloat16 *dig = (__nv_bfloat16 *)buf->p;
+    int *ea = (int *)((char *)buf->p + (size_t)chunk * mpt * 2 * S);
+    OzG prm;
+    prm.N = m;
+    prm.kblocks = (m + BKE - 1) / BKE;
+    prm.kb_per_split = prm.kblocks;
+    prm.lower_b = 1;
+    prm.accumulate = 0;
+    prm.ea = ea;
+    prm.eb = O->ec;
+    prm.ldc = ldc;
+    prm.cstride = 0;
+    prm.status = gpr_status_word();
+    gpr_status rs = prm.status ? GPR_OK : GPR_ERR_CUDA;
+    for (int64_t c0 = 0; c0 < rows && rs == GPR_OK; c0 += chunk) {
+        const int64_t cnt = rows - c0 < chunk ? rows - c0 : chunk;
+        k_oz_rowdig<<<(unsigned)((cnt + 7) / 8), 256, 0, st>>>(X + c0 * ldx, ldx, cnt, m, mpt, dig, ea);
+        note_launch();
+        CUtensorMap mapA;
+        if (!encode_digits(&mapA, dig, mpt, cnt, TM)) { rs = GPR_ERR_UNSUPPORTED; break; }
+        prm.M = cnt;
+        prm.C = C + c0 * ldc;
+        k_oz_dgemm<S><<<dim3((unsigned)(mpt / TN), (unsigned)((cnt + TM - 1) / TM), 1), G_NTHR, smem, st>>>(mapA, O->mapc,
+                                                                                                      prm);
+        note_launch();
+        if (cudaGetLastError() != cudaSuccess) rs = GPR_ERR_CUDA;
+    }
+    adig_release(buf, st);
+    return rs;
+}
+
+// FP64-class C = A^T B for A, B: K x nc FP64 (row-major, ld) on the tensor cores, as nsplit
+// partial products part[z] (ncp x ncp each, ncp = nc rounded up to 64, zero beyond nc) whose
+// sum is C.  K runs in chunks whose digits fit 2 GB, each chunk scaled by its own column
+// exponents and added onto the partials in order (deterministic).
+gpr_status oz_mul_tn(const double *A, const double *B, int64_t K, int64_t nc, int64_t ld, double *part, int nsplit,
+                     cudaStream_t st, int64_t kchunk)
+{
+    constexpr int S = 7;
+    const int64_t ncp = (nc + 63) / 64 * 64;
+    if (K <= 0) {
+        GPR_CUDA_TRY(cudaMemsetAsync(part, 0, sizeof(double) * (size_t)nsplit * ncp * ncp, st));
+        return GPR_OK;
+    }
+    int64_t kc = kchunk > 0 ? (kchunk + 31) / 32 * 32 : (int64_t)131072 * 512 / ncp / 32 * 32;
+    const int64_t kall = (K + 31) / 32 * 32;
+    if (kc > kall) kc = kall;
+    const size_t dig_bytes = (size_t)S * ncp * kc * 2;
+    const size_t bytes = 2 * dig_bytes + 2 * ncp * (sizeof(unsigned long long) + sizeof(int)) + 256;
+    const size_t smem = dgemm_smem();
+    GPR_CUDA_TRY(cudaFuncSetAttribute(k_oz_dgemm<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    AdigBuf *buf = nullptr;
+    GPR_TRY(adig_acquire(bytes, st, &buf));
+    __nv_bfloat16 *dA = (__nv_bfloat16 *)buf->p, *dB = (__nv_bfloat16 *)((char *)buf->p + dig_bytes);
+    unsigned long long *cmax = (unsigned long long *)((char *)buf->p + 2 * dig_bytes);
+    int *eA = (int *)(cmax + 2 * ncp), *eB = eA + ncp;
+    OzG prm;
+    prm.M = ncp;
+    prm.N = ncp;
+    prm.lower_b = 0;
+    prm.ea = eA;
+    prm.eb = eB;
+    prm.C = part;
+    prm.ldc = ncp;
+    prm.cstride = ncp * ncp;
+    prm.status = gpr_status_word();
+    gpr_status rs = prm.status ? GPR_OK : GPR_ERR_CUDA;
+    for (int64_t c0 = 0; c0 < K && rs == GPR_OK; c0 += kc) {
+        const int64_t cnt = K - c0 < kc ? K - c0 : kc, kpad = (cnt + 31) / 32 * 32;
+        GPR_CUDA_TRY(cudaMemsetAsync(cmax, 0, sizeof(unsigned long long) * 2 * ncp, st));
+        const int64_t rpb = 512;
+        const dim3 gmax((unsigned)((nc + 255) / 256), (unsigned)((cnt + rpb - 1) / rpb));
+        k_oz_colmax<<<gmax, 256, 0, st>>>(A + c0 * ld, ld, cnt, nc, rpb, cmax);
+        k_oz_colmax<<<gmax, 256, 0, st>>>(B + c0 * ld, ld, cnt, nc, rpb, cmax + ncp);
+        k_oz_colexp<<<(unsigned)((2 * ncp + 255) / 256), 256, 0, st>>>(cmax, 2 * ncp, eA);
+        const dim3 gdig((unsigned)((ncp + 127) / 128), (unsigned)(kpad / 16));
+        k_oz_coldig<<<gdig, 128, 0, st>>>(A + c0 * ld, ld, cnt, nc, ncp, kpad, 0, eA, dA);
+        k_oz_coldig<<<gdig, 128, 0, st>>>(B + c0 * ld, ld, cnt, nc, ncp, kpad, 0, eB, dB);
+        for (int q = 0; q < 5; ++q) note_launch();
+        CUtensorMap mapA, mapB;
+        if (!encode_digits(&mapA, dA, kpad, ncp, TM) || !encode_digits(&mapB, dB, kpad, ncp, TN)) {
+            rs = GPR_ERR_UNSUPPORTED;
+            break;
+        }
+        prm.kblocks = kpad / BKE;
+        prm.kb_per_split = (prm.kblocks + nsplit - 1) / nsplit;
+        prm.accumulate = c0 > 0;
+        k_oz_dgemm<S><<<dim3((unsigned)(ncp / TN), (unsigned)((ncp + TM - 1) / TM), (unsigned)nsplit), G_NTHR, smem,
+                        st>>>(mapA, mapB, prm);
+        note_launch();
+        if (cudaGetLastError() != cudaSuccess) rs = GPR_ERR_CUDA;
+    }
+    adig_release(buf, st);
+    return rs;
+}
+
 __global__ void k_fill_slot_oz(const int64_t *idx, int64_t count, int64_t npts, int32_t *slot)
 {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -740,5 +1144,48 @@ extern "C" gpr_status gpr_stats_points_split(gpr_model *M, const gpr_grid *grid,
     note_launch();
     GPR_TRY(launch_oz_w(M, g, Tu, point_idx, 0, count, W, st));
     GPR_TRY(launch_stats_ff(M, g, point_idx, count, slot, W, stats, st));
+    return GPR_OK;
+}
+
+__global__ void k_sum_parts(const double *part, int n, int64_t len, double *out)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= len) return;
+    double s = 0.0;
+    for (int z = 0; z < n; ++z) s += part[z * len + i];
+    out[i] = s;
+}
+
+// Test hooks (not in the public header) for the FP64-class products: C (nc x nc, device) =
+// A^T B with A, B device K x nc (ld nc) in K chunks of kchunk rows (0: default), and
+// C (rows x m, ld m) = X L^-1 for device X (rows x m, ld m).
+extern "C" gpr_status gpr_oz_mul_tn_test(const double *A, const double *B, int64_t K, int64_t nc, int64_t kchunk,
+                                         int32_t nsplit, double *C, void *stream)
+{
+    if (!A || !B || !C || K < 0 || nc <= 0 || nsplit <= 0 || nsplit > 64) return GPR_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t ncp = (nc + 63) / 64 * 64;
+    double *part = nullptr, *full = nullptr;
+    GPR_CUDA_TRY(cudaMalloc(&part, sizeof(double) * (size_t)nsplit * ncp * ncp));
+    GPR_CUDA_TRY(cudaMalloc(&full, sizeof(double) * (size_t)ncp * ncp));
+    gpr_status rs = oz_mul_tn(A, B, K, nc, nc, part, nsplit, st, kchunk);
+    if (rs == GPR_OK) {
+        k_sum_parts<<<(unsigned)((ncp * ncp + 255) / 256), 256, 0, st>>>(part, nsplit, ncp * ncp, full);
+        cudaMemcpy2DAsync(C, nc * sizeof(double), full, ncp * sizeof(double), nc * sizeof(double), nc,
+                          cudaMemcpyDeviceToDevice, st);
+        if (cudaStreamSynchronize(st) != cudaSuccess) rs = GPR_ERR_CUDA;
+    }
+    cudaFree(part);
+    cudaFree(full);
+    return rs;
+}
+
+extern "C" gpr_status gpr_oz_mul_linv_test(gpr_model *M, const double *X, int64_t rows, double *C, void *stream)
+{
+    if (!M || !X || !C || rows < 0) return GPR_ERR_ARG;
+    if (!oz_supported(M)) return GPR_ERR_UNSUPPORTED;
+    cudaStream_t st = (cudaStream_t)stream;
+    GPR_TRY(oz_mul_linv(M, X, rows, M->m, C, M->m, st));
+    GPR_CUDA_TRY(cudaStreamSynchronize(st));
     return GPR_OK;
 }
