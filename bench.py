@@ -196,10 +196,17 @@ def run_backward(args, g, torch, rank, world, local):
     field = torch.zeros((n - 1) ** 3, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
+    split_ev = []
+
     def step():
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        ev[0].record(stream)
         M = g.gpr_model_create(w.X, w.y, w.kernel, w.ell, w.sf2, w.sn2, stream=stream)
         g.gpr_lcp_dense(M, grid, th, opts, field, stream=stream)
+        ev[1].record(stream)
         dy, dl = g.gpr_lcp_backward(M, grid, th, opts, wts, stream=stream)
+        ev[2].record(stream)
+        split_ev.append(ev)
         M.close()
         return dy, dl
 
@@ -207,6 +214,7 @@ def run_backward(args, g, torch, rank, world, local):
         step()
     torch.cuda.synchronize()
     g.gpr_profile_reset(); g.gpr_profile_enable(True)
+    split_ev.clear()
     with ClockSampler(local) as clk:
         e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -216,7 +224,7 @@ def run_backward(args, g, torch, rank, world, local):
         torch.cuda.synchronize()
     g.gpr_profile_enable(False)
     ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world)
-    prof = {k: g.gpr_profile_read(k) for k in ("w64", "oz_adig", "oz_w", "stats_ff", "tc_sumsq", "stats_from_w64", "sov", "adj_cell", "adj_prep", "adj_sample", "adj_chol", "adj_R", "adj_Z")}
+    prof = {k: g.gpr_profile_read(k) for k in ("w64", "oz_adig", "oz_w", "stats_ff", "tc_sumsq", "stats_from_w64", "sov", "adj_cell", "adj_prep", "adj_sample", "adj_chol", "adj_zhat", "adj_R", "adj_Z", "adj_points")}
     if rank != 0:
         return
     out = {"metric": METRIC + " (forward + backward)", "value": world * n ** 3 / (ms / 1e3), "unit": UNIT, "n_gpus": world,
@@ -224,6 +232,8 @@ def run_backward(args, g, torch, rank, world, local):
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": f"{w.name}: loss = sum_c U(0,1)_c LCP_c, d/dy (500) and d/dlog l (3)"},
            "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
+           "forward_ms": float(np.mean([e[0].elapsed_time(e[1]) for e in split_ev])),
+           "backward_ms": float(np.mean([e[1].elapsed_time(e[2]) for e in split_ev])),
            "grad_norm_y": float(np.linalg.norm(dy)), "grad_loglen": [float(v) for v in dl],
            "clocks": clk.summary(), "gpu_launches": g.gpr_launch_count()}
     print(json.dumps(out), flush=True)

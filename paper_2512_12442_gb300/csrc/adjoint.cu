@@ -533,6 +533,59 @@ __global__ void k_point_terms(GridDev g, const int64_t *pts, int64_t np, const d
         for (int d = 0; d < 3; ++d) atomicAdd(out + d, acc[d]);
 }
 
+// Squared scaled distances per axis, Q_d[g][j] = ((x_g - X_jd) / l_d)^2 (zero for j >= m), laid out
+// like the kernel tables.
+__global__ void k_sqdist_tables(const double *X, int64_t m, int64_t mp, KernParams kp, GridDev g, double *Q)
+{
+    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t total = (int64_t)(g.n[0] + g.n[1] + g.n[2]) * mp;
+    if (idx >= total) return;
+    const int64_t row = idx / mp, j = idx % mp;
+    int d = 0;
+    int64_t gi = row;
+    if (gi >= g.n[0]) { gi -= g.n[0]; d = 1; if (gi >= g.n[1]) { gi -= g.n[1]; d = 2; } }
+    double v = 0.0;
+    if (j < m) {
+        const double t = (g.lo[d] + (double)gi * g.h[d] - X[3 * j + d]) / kp.ell[d];
+        v = t * t;
+    }
+    Q[idx] = v;
+}
+
+// As k_point_terms for the SE kernel from its separable tables: k_pj = Tx Ty Tz (signal variance
+// in Tx) and dk_pj/dlog l_d = k_pj Q_d, so each (p, j) costs a handful of FP64 multiply-adds.
+__global__ void k_point_terms_se(GridDev g, const int64_t *pts, int64_t np, const double *T64, const double *Q,
+                                 int64_t m, const double *alpha, const double *Z, int64_t mp, const double *G16,
+                                 KdPrior kdp, double *out)
+{
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int64_t pos = blockIdx.x * (int64_t)(blockDim.x / 32) + warp;
+    double acc[3] = {0, 0, 0};
+    if (pos < np) {
+        const int64_t p = pts[pos], nx = g.n[0], ny = g.n[1];
+        const int64_t o0 = (p % nx) * mp, o1 = ((int64_t)g.n[0] + (p / nx) % ny) * mp,
+                      o2 = ((int64_t)g.n[0] + g.n[1] + p / (nx * ny)) * mp;
+        const double gm = G16[pos * 16];
+        const double *zr = Z + pos * mp;
+        for (int64_t j = lane; j < m; j += 32) {
+            const double kc = T64[o0 + j] * T64[o1 + j] * T64[o2 + j] * fma(gm, alpha[j], -2.0 * zr[j]);
+            acc[0] = fma(kc, Q[o0 + j], acc[0]);
+            acc[1] = fma(kc, Q[o1 + j], acc[1]);
+            acc[2] = fma(kc, Q[o2 + j], acc[2]);
+        }
+        if (lane == 0)
+            for (int e = 0; e < 13; ++e) {
+                const double gc = G16[pos * 16 + 2 + e];
+                if (gc != 0.0)
+                    for (int d = 0; d < 3; ++d) acc[d] += gc * kdp.k[e][d];
+            }
+    }
+    for (int d = 0; d < 3; ++d)
+        for (int o = 16; o > 0; o >>= 1) acc[d] += __shfl_xor_sync(0xffffffffu, acc[d], o);
+    if (lane == 0 && pos < np)
+        for (int d = 0; d < 3; ++d) atomicAdd(out + d, acc[d]);
+}
+
 // dy_i = sum_{j >= i} Linv[j][i] t_j.
 __global__ void k_dy(const double *Linv, int64_t mb, const double *t, int64_t m, double *dy)
 {
@@ -572,7 +625,7 @@ extern "C" gpr_status gpr_lcp_backward(gpr_model *M, const gpr_grid *grid, doubl
     size_t b1 = Carver::round(te * 4) + Carver::round(te * 8) + Carver::round(te * 8) + 2 * Carver::round((size_t)n * 4) +
                 Carver::round((size_t)nc) + Carver::round((size_t)n) + Carver::round((size_t)n * 8) +
                 Carver::round((size_t)n * 4) + Carver::round((size_t)nc * 8) + csb +
-                Carver::round(tc_partial_elems(GPR_P_BF16X3, M, n) * 4) + Carver::round(te * 8) + 8192;
+                Carver::round(tc_partial_elems(GPR_P_BF16X3, M, n) * 4) + 2 * Carver::round(te * 8) + 8192;
     GPR_TRY(ws_reserve(M, 0, b1, st));
     Carver cv{(char *)ws_ptr(M, 0)};
     float *T32 = cv.take<float>(te);
@@ -588,6 +641,7 @@ extern "C" gpr_status gpr_lcp_backward(gpr_model *M, const gpr_grid *grid, doubl
     void *cscr = cv.take<char>(csb);
     float *part = cv.take<float>(tc_partial_elems(GPR_P_BF16X3, M, n));
     float2 *Tu = cv.take<float2>(te);
+    double *Q64 = cv.take<double>(te);
     GPR_TRY(build_tables(M, g, T64, T32, st, Tff));
     // cells whose LCP is not identically 0 near the current parameters (same cascade as the forward)
     if (opts->prec == GPR_P_FP64) {
@@ -688,7 +742,10 @@ extern "C" gpr_status gpr_lcp_backward(gpr_model *M, const gpr_grid *grid, doubl
     k_sum_rows<<<(unsigned)((mp + 255) / 256), 256, 0, st>>>(tp, nchunks, mp, t);
     note_launch();
     // Zh rows, R = Zh^T W (split over points), M = R - v t^T, N = L^-T M L^-1
-    k_zhat<<<(unsigned)((npts + 7) / 8), 256, 0, st>>>(g, plist, npts, slot, W, G16, mp, Zh);
+    {
+        ProfScope ps("adj_zhat", st);
+        k_zhat<<<(unsigned)((npts + 7) / 8), 256, 0, st>>>(g, plist, npts, slot, W, G16, mp, Zh);
+    }
     note_launch();
     // R splits: 19 x (mp/64) x (mp/128) tiles = 608 CTAs = 4 waves of 152 for mp = 512
     const int rsplits = use_oz ? 19 : splits;
@@ -728,8 +785,18 @@ extern "C" gpr_status gpr_lcp_backward(gpr_model *M, const gpr_grid *grid, doubl
         }
         (void)a;
     }
-    k_point_terms<<<(unsigned)((npts + 7) / 8), 256, 0, st>>>(g, plist, npts, M->X, m, M->kp, M->alpha, W, mp, G16,
-                                                              kdp, acc);
+    {
+        ProfScope ps("adj_points", st);
+        if (M->kp.kind == GPR_K_SE) {
+            k_sqdist_tables<<<(unsigned)((te + 255) / 256), 256, 0, st>>>(M->X, m, mp, M->kp, g, Q64);
+            k_point_terms_se<<<(unsigned)((npts + 7) / 8), 256, 0, st>>>(g, plist, npts, T64, Q64, m, M->alpha, W, mp,
+                                                                         G16, kdp, acc);
+            note_launch();
+        } else {
+            k_point_terms<<<(unsigned)((npts + 7) / 8), 256, 0, st>>>(g, plist, npts, M->X, m, M->kp, M->alpha, W, mp,
+                                                                      G16, kdp, acc);
+        }
+    }
     note_launch();
     k_dy<<<(unsigned)((m + 127) / 128), 128, 0, st>>>(M->Linv, mb, t, m, dy);
     note_launch();

@@ -362,6 +362,21 @@ __global__ void __launch_bounds__(G_NTHR, 1) k_oz_gemm(const __grid_constant__ C
     oz_teardown(P.tmem, ok, prm.status);
 }
 
+// (double)f * 2^sc built from the bit pattern (no FP64 instructions): exact for normal f while
+// the result stays normal; zero and subnormal f give 0, a result outside the normal range its
+// FP64 evaluation.
+__device__ __forceinline__ double f2d_scaled(float f, int sc)
+{
+    const uint32_t b = __float_as_uint(f);
+    const int ef = (int)((b >> 23) & 0xFF);
+    if (ef == 0) return 0.0;
+    const int ed = ef + 896 + sc;  // FP64 biased exponent
+    if (ed <= 0 || ed >= 2047) return ldexp((double)f, sc);
+    const unsigned long long db = ((unsigned long long)(b >> 31) << 63) | ((unsigned long long)ed << 52) |
+                                  ((unsigned long long)(b & 0x7FFFFF) << 29);
+    return __longlong_as_double((long long)db);
+}
+
 // General FP64-class product C = A B of FP64 matrices given as digit slices: A rows (M, K-major,
 // row r scaled by 2^-ea[r]) and B columns (N rows of K, column j scaled by 2^-eb[j]); C is
 // written in FP64, scaled back by 2^(ea + eb) (or added to C).  Split z of the K range
@@ -409,7 +424,8 @@ __global__ void __launch_bounds__(G_NTHR, 1) k_oz_dgemm(const __grid_constant__ 
             for (int c = 0; c < 32; ++c) {
                 const int64_t j = n0 + half * 32 + c;
                 if (j < prm.N) {
-                    const double v = ldexp((double)acc[c].h + (double)acc[c].l, er + prm.eb[j]);
+                    const int sc = er + prm.eb[j];
+                    const double v = f2d_scaled(acc[c].h, sc) + f2d_scaled(acc[c].l, sc);
                     out[j] = prm.accumulate ? out[j] + v : v;
                 }
             }
@@ -574,27 +590,40 @@ __global__ void k_vyff(const double *vy, int64_t mp, float2 *out)
 }
 
 // Digits of an FP64 value x with |x| < 2^e: the fixed-point integer q = round(x 2^(42-e))
-// (|q| <= 2^42, from the bit pattern: integer work only) in balanced base 64, most significant
-// first: q = sum_s d_s 2^(6(6-s)), |d_0| <= 64, |d_s| <= 32.  Zero and subnormal x give 0.
-__device__ __forceinline__ void fixed_digits7(double x, int e, float d[7])
+// (|q| <= 2^42, from the bit pattern) in balanced base 64, q = sum_s d_s 2^(6(6-s)), returned as
+// BF16 bit patterns.  Integer work only: |q| is split at bit 18 and each 32-bit half yields three
+// digits in [-32, 31] (the carry moving up), the top digit |d_0| <= 64 is what remains; the
+// signs follow x.  Zero and subnormal x give 0.
+__device__ __forceinline__ void fixed_digits7(double x, int e, uint32_t d[7])
 {
     const long long bits = __double_as_longlong(x);
     const int E = (int)((bits >> 52) & 0x7FF);
-    long long q = 0;
+    unsigned long long q = 0;
     if (E != 0) {
-        const long long mant = (bits & 0xFFFFFFFFFFFFFLL) | (1LL << 52);  // x = mant 2^(E - 1075)
-        const int rs = 1033 + e - E;                                        // q = mant 2^-rs, rs >= 11
-        if (rs < 63) q = (mant + (1LL << (rs - 1))) >> rs;
-        if (bits < 0) q = -q;
+        const unsigned long long mant = (unsigned long long)(bits & 0xFFFFFFFFFFFFFLL) | (1ULL << 52);  // x = mant 2^(E-1075)
+        const int rs = 1033 + e - E;  // q = mant 2^-rs, rs >= 11
+        if (rs < 63) q = (mant + (1ULL << (rs - 1))) >> rs;
     }
+    int lo = (int)(q & 0x3FFFF), hi = (int)(q >> 18), v[7];
 #pragma unroll
-    for (int t = 0; t < 6; ++t) {
-        const int sh = 6 * (6 - t);
-        const long long dt = (q + (1LL << (sh - 1))) >> sh;  // floor: balanced digit
-        d[t] = (float)dt;
-        q -= dt * (1LL << sh);
+    for (int t = 6; t >= 4; --t) {
+        v[t] = ((lo + 32) & 63) - 32;
+        lo = (lo - v[t]) >> 6;
     }
-    d[6] = (float)q;
+    hi += lo;  // carry out of the low 18 bits (0 or 1)
+#pragma unroll
+    for (int t = 3; t >= 1; --t) {
+        v[t] = ((hi + 32) & 63) - 32;
+        hi = (hi - v[t]) >> 6;
+    }
+    v[0] = hi;
+    const int sg = bits < 0 ? -1 : 1;
+#pragma unroll
+    for (int t = 0; t < 7; ++t) {
+        // small integer -> FP32 through the 1.5 * 2^23 magic constant (exact), then its BF16 half
+        const float f = __int_as_float(0x4B400000 + sg * v[t]) - 12582912.0f;
+        d[t] = __float_as_uint(f) >> 16;
+    }
 }
 
 // Power-of-two exponent e with |x| < 2^e for every x of a slice whose largest magnitude is mx.
@@ -605,8 +634,8 @@ __device__ __forceinline__ int exp_above(double mx)
     return e;
 }
 
-// Row digits (K-major as stored): out[s][r][k] for rows r < rows of X (ld ldx), k < kv, zero
-// to kpad; ea[r] the row's exponent.  Warp per row.
+// Row digits (K-major as stored): out[s][r][k] for rows r < rows of X (ld ldx, even), k < kv,
+// zero to kpad (a multiple of 8); ea[r] the row's exponent.  Warp per row, 8 k per lane.
 __global__ void k_oz_rowdig(const double *X, int64_t ldx, int64_t rows, int64_t kv, int64_t kpad, __nv_bfloat16 *out,
                             int *ea)
 {
@@ -621,21 +650,26 @@ __global__ void k_oz_rowdig(const double *X, int64_t ldx, int64_t rows, int64_t 
     const int e = exp_above(mx);
     if (lane == 0) ea[r] = e;
     for (int64_t k0 = (int64_t)lane * 8; k0 < kpad; k0 += 256) {
-        float d[7][8];
+        double v[8];
+        if (k0 + 8 <= kv) {
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            float t[7];
-            fixed_digits7(k0 + c < kv ? x[k0 + c] : 0.0, e, t);
+            for (int c = 0; c < 8; c += 2) {
+                const double2 p = *(const double2 *)(x + k0 + c);
+                v[c] = p.x;
+                v[c + 1] = p.y;
+            }
+        } else {
 #pragma unroll
-            for (int q = 0; q < 7; ++q) d[q][c] = t[q];
+            for (int c = 0; c < 8; ++c) v[c] = k0 + c < kv ? x[k0 + c] : 0.0;
         }
+        uint32_t d[8][7];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) fixed_digits7(v[c], e, d[c]);
 #pragma unroll
         for (int q = 0; q < 7; ++q) {
             uint32_t wd[4];
 #pragma unroll
-            for (int h = 0; h < 4; ++h)
-                wd[h] = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(d[q][2 * h])) |
-                        ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(d[q][2 * h + 1])) << 16);
+            for (int h = 0; h < 4; ++h) wd[h] = d[2 * h][q] | (d[2 * h + 1][q] << 16);
             *(uint4 *)(out + ((int64_t)q * rows + r) * kpad + k0) = make_uint4(wd[0], wd[1], wd[2], wd[3]);
         }
     }
@@ -661,35 +695,38 @@ __global__ void k_oz_colexp(const unsigned long long *cmax, int64_t n, int *e)
 }
 
 // Column digits (the transpose, K-major over rows): out[s][c][r] for columns c < ncpad (zero
-// from nc) and rows r < kpad (zero from rows), column c scaled by 2^-e[c]; with `lower`,
-// X[r][c] = 0 for r < c.  Thread per column and 16 consecutive rows.
-__global__ void k_oz_coldig(const double *X, int64_t ldx, int64_t rows, int64_t nc, int64_t ncpad, int64_t kpad,
-                            int lower, const int *e, __nv_bfloat16 *out)
+// from nc) and rows r < kpad (zero from rows; kpad a multiple of 32), column c scaled by
+// 2^-e[c]; with `lower`, X[r][c] = 0 for r < c.  Block: a tile of 64 columns x 32 rows, read
+// row by row (coalesced), its digits transposed in shared memory (row pairs as 32-bit words,
+// rows padded to 17 words) and written 64 bytes per (slice, column).
+__global__ void __launch_bounds__(256) k_oz_coldig(const double *X, int64_t ldx, int64_t rows, int64_t nc,
+                                                   int64_t ncpad, int64_t kpad, int lower, const int *e,
+                                                   __nv_bfloat16 *out)
 {
-    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int64_t r0 = (int64_t)blockIdx.y * 16;
-    if (c >= ncpad || r0 >= kpad) return;
+    __shared__ uint32_t sd[7][64][17];
+    const int t = threadIdx.x, cl = t & 63, grp = t >> 6;
+    const int64_t c0 = (int64_t)blockIdx.x * 64, r0 = (int64_t)blockIdx.y * 32, c = c0 + cl;
     const int ec = c < nc ? e[c] : 0;
-    float d[7][16];
 #pragma unroll
-    for (int i = 0; i < 16; ++i) {
-        const int64_t r = r0 + i;
-        const double v = (c < nc && r < rows && !(lower && r < c)) ? X[r * ldx + c] : 0.0;
-        float t[7];
-        fixed_digits7(v, ec, t);
+    for (int i = 0; i < 4; ++i) {
+        const int rp = grp + 4 * i;  // row pair 0..15
+        uint32_t d0[7], d1[7];
 #pragma unroll
-        for (int q = 0; q < 7; ++q) d[q][i] = t[q];
+        for (int h = 0; h < 2; ++h) {
+            const int64_t r = r0 + 2 * rp + h;
+            const double v = (c < nc && r < rows && !(lower && r < c)) ? X[r * ldx + c] : 0.0;
+            fixed_digits7(v, ec, h ? d1 : d0);
+        }
+#pragma unroll
+        for (int q = 0; q < 7; ++q) sd[q][cl][rp] = d0[q] | (d1[q] << 16);
     }
-#pragma unroll
-    for (int q = 0; q < 7; ++q) {
-        uint32_t wd[8];
-#pragma unroll
-        for (int h = 0; h < 8; ++h)
-            wd[h] = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(d[q][2 * h])) |
-                    ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(d[q][2 * h + 1])) << 16);
-        uint4 *o = (uint4 *)(out + ((int64_t)q * ncpad + c) * kpad + r0);
-        o[0] = make_uint4(wd[0], wd[1], wd[2], wd[3]);
-        o[1] = make_uint4(wd[4], wd[5], wd[6], wd[7]);
+    __syncthreads();
+    // 7 x 64 (slice, column) rows of 4 16-byte pieces
+    for (int u = t; u < 7 * 64 * 4; u += 256) {
+        const int row = u >> 2, k = u & 3, q = row >> 6, cc = row & 63;
+        if (c0 + cc >= ncpad) continue;
+        const uint32_t *w = &sd[q][cc][4 * k];
+        *(uint4 *)(out + ((int64_t)q * ncpad + c0 + cc) * kpad + r0 + 8 * k) = make_uint4(w[0], w[1], w[2], w[3]);
     }
 }
 
@@ -984,8 +1021,8 @@ gpr_status oz_prepare_cols(gpr_model *M, cudaStream_t st)
     GPR_CUDA_TRY(cudaMemsetAsync(ec, 0, sizeof(int) * mpt, st));
     k_oz_colmax<<<dim3((unsigned)((m + 255) / 256), (unsigned)((m + 63) / 64)), 256, 0, st>>>(M->Linv, mb, m, m, 64, cmax);
     k_oz_colexp<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(cmax, m, ec);
-    k_oz_coldig<<<dim3((unsigned)((mpt + 127) / 128), (unsigned)(mpt / 16)), 128, 0, st>>>(M->Linv, mb, m, m, mpt, mpt,
-                                                                                       1, ec, (__nv_bfloat16 *)Bc);
+    k_oz_coldig<<<dim3((unsigned)(mpt / 64), (unsigned)(mpt / 32)), 256, 0, st>>>(M->Linv, mb, m, m, mpt, mpt, 1, ec,
+                                                                                (__nv_bfloat16 *)Bc);
     note_launch();
     note_launch();
     note_launch();
@@ -1093,9 +1130,9 @@ gpr_status oz_mul_tn(const double *A, const double *B, int64_t K, int64_t nc, in
         k_oz_colmax<<<gmax, 256, 0, st>>>(A + c0 * ld, ld, cnt, nc, rpb, cmax);
         k_oz_colmax<<<gmax, 256, 0, st>>>(B + c0 * ld, ld, cnt, nc, rpb, cmax + ncp);
         k_oz_colexp<<<(unsigned)((2 * ncp + 255) / 256), 256, 0, st>>>(cmax, 2 * ncp, eA);
-        const dim3 gdig((unsigned)((ncp + 127) / 128), (unsigned)(kpad / 16));
-        k_oz_coldig<<<gdig, 128, 0, st>>>(A + c0 * ld, ld, cnt, nc, ncp, kpad, 0, eA, dA);
-        k_oz_coldig<<<gdig, 128, 0, st>>>(B + c0 * ld, ld, cnt, nc, ncp, kpad, 0, eB, dB);
+        const dim3 gdig((unsigned)(ncp / 64), (unsigned)(kpad / 32));
+        k_oz_coldig<<<gdig, 256, 0, st>>>(A + c0 * ld, ld, cnt, nc, ncp, kpad, 0, eA, dA);
+        k_oz_coldig<<<gdig, 256, 0, st>>>(B + c0 * ld, ld, cnt, nc, ncp, kpad, 0, eB, dB);
         for (int q = 0; q < 5; ++q) note_launch();
         CUtensorMap mapA, mapB;
         if (!encode_digits(&mapA, dA, kpad, ncp, TM) || !encode_digits(&mapB, dB, kpad, ncp, TN)) {
