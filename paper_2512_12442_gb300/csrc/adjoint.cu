@@ -390,6 +390,82 @@ __global__ void k_zhat(GridDev g, const int64_t *pts, int64_t np, const int32_t 
     }
 }
 
+// (sh, sl) += (gh + gl)(wh + wl) in float-float (compensated dot product: the product's high
+// part joins the running sum by an error-free TwoSum, every rounding error goes to sl).
+__device__ __forceinline__ void ff_dot_step(float &sh, float &sl, float gh, float gl, float wh, float wl)
+{
+    const float p = gh * wh;
+    float e = fmaf(gh, wh, -p);
+    e = fmaf(gh, wl, fmaf(gl, wh, e));
+    const float t = sh + p;
+    const float bv = t - sh;
+    sl += ((sh - (t - bv)) + (p - bv)) + e;
+    sh = t;
+}
+
+// Exact FP64 value of a normal FP32 number (or 0) from its bit pattern, without FP64 instructions.
+__device__ __forceinline__ double f2d_bits(float f)
+{
+    const uint32_t b = __float_as_uint(f);
+    const uint32_t ef = (b >> 23) & 0xFF;
+    if (ef == 0) return 0.0;
+    const unsigned long long db = ((unsigned long long)(b >> 31) << 63) | ((unsigned long long)(ef + 896) << 52) |
+                                  ((unsigned long long)(b & 0x7FFFFF) << 29);
+    return __longlong_as_double((long long)db);
+}
+
+// k_zhat from the float-float rows (hi, lo pairs, 512-byte aligned rows of even length mp):
+// the same sums as float-float compensated dot products, two columns per lane, FP64 out.
+__global__ void k_zhat_ff(GridDev g, const int64_t *pts, int64_t np, const int32_t *slot, const float2 *Wff,
+                          const double *G16, int64_t mp, double *Zh)
+{
+    __shared__ int4 lst[8][27];  // per warp: (row, weight hi bits, weight lo bits)
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int64_t pos = blockIdx.x * (int64_t)(blockDim.x / 32) + warp;
+    if (pos >= np) return;
+    const int64_t p = pts[pos];
+    const int64_t nx = g.n[0], ny = g.n[1], nz = g.n[2];
+    const int ix = (int)(p % nx), iy = (int)((p / nx) % ny), iz = (int)(p / (nx * ny));
+    int4 *L = lst[warp];
+    int cnt = 0;
+    auto add = [&](int64_t r, double w) {
+        if (lane == 0) {
+            const float h = (float)w;
+            L[cnt] = make_int4((int)r, __float_as_int(h), __float_as_int((float)(w - (double)h)), 0);
+        }
+        ++cnt;
+    };
+    add(pos, G16[pos * 16 + 1]);
+    for (int e = 0; e < 13; ++e) {
+        int a = ix + c_off[e][0], b = iy + c_off[e][1], c = iz + c_off[e][2];
+        if (a >= 0 && b >= 0 && c >= 0 && a < nx && b < ny && c < nz) {
+            const int s = slot[a + nx * (b + ny * (int64_t)c)];
+            const double gv = G16[pos * 16 + 2 + e];
+            if (s >= 0 && gv != 0.0) add(s, 0.5 * gv);
+        }
+        a = ix - c_off[e][0]; b = iy - c_off[e][1]; c = iz - c_off[e][2];
+        if (a >= 0 && b >= 0 && c >= 0 && a < nx && b < ny && c < nz) {
+            const int s = slot[a + nx * (b + ny * (int64_t)c)];
+            if (s >= 0) {
+                const double gv = G16[(int64_t)s * 16 + 2 + e];
+                if (gv != 0.0) add(s, 0.5 * gv);
+            }
+        }
+    }
+    __syncwarp();
+    for (int64_t j2 = lane; j2 < mp / 2; j2 += 32) {
+        float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
+        for (int t = 0; t < cnt; ++t) {
+            const int4 e = L[t];
+            const float gh = __int_as_float(e.y), gl = __int_as_float(e.z);
+            const float4 v = *(const float4 *)(Wff + (int64_t)e.x * mp + 2 * j2);
+            ff_dot_step(h0, l0, gh, gl, v.x, v.y);
+            ff_dot_step(h1, l1, gh, gl, v.z, v.w);
+        }
+        *(double2 *)(Zh + pos * mp + 2 * j2) = make_double2(f2d_bits(h0) + f2d_bits(l0), f2d_bits(h1) + f2d_bits(l1));
+    }
+}
+
 // Generic FP64 tiled GEMM: C_z = opA(A) B over the K range of split z (partials stacked by z).
 // opA(i,k) = TA ? A[k*lda + i] : A[i*lda + k];  LOWERB: B[k][j] = 0 for k < j (skip those k).
 constexpr int GB = 64, GK = 16;
@@ -666,6 +742,7 @@ extern "C" gpr_status gpr_lcp_backward(gpr_model *M, const gpr_grid *grid, doubl
         memcpy(dL_dloglen, h_out, sizeof h_out);
         return GPR_OK;
     }
+    const bool use_oz = opts->exact == GPR_EXACT_AUTO && oz_supported(M);
     const int splits = 32;
     const int64_t chunk = 4096;
     int64_t nchunks = (npts + chunk - 1) / chunk;
@@ -673,7 +750,7 @@ extern "C" gpr_status gpr_lcp_backward(gpr_model *M, const gpr_grid *grid, doubl
                 Carver::round((size_t)npts * 16 * 8) + Carver::round((size_t)nchunks * mp * 8) +
                 Carver::round((size_t)splits * mp * mp * 8) + 3 * Carver::round((size_t)mp * mp * 8) +
                 4 * Carver::round((size_t)mp * 8) + Carver::round((size_t)ncell * sizeof(AdjRec)) +
-                Carver::round((size_t)ncell * kRed * 4) + 4096;
+                Carver::round((size_t)ncell * kRed * 4) + (use_oz ? Carver::round((size_t)npts * mp * 8) : 0) + 4096;
     GPR_TRY(ws_reserve(M, 1, b2, st));
     Carver cv2{(char *)ws_ptr(M, 1)};
     double *W = cv2.take<double>((size_t)npts * mp);
@@ -690,11 +767,10 @@ extern "C" gpr_status gpr_lcp_backward(gpr_model *M, const gpr_grid *grid, doubl
     double *acc = cv2.take<double>(4);
     AdjRec *arec = cv2.take<AdjRec>((size_t)ncell);
     float *ared = cv2.take<float>((size_t)ncell * kRed);
-    const bool use_oz = opts->exact == GPR_EXACT_AUTO && oz_supported(M);
+    float2 *Wff = use_oz ? cv2.take<float2>((size_t)npts * mp) : nullptr;
     if (use_oz) {
         // FP64-class rows on the tensor cores (digit split), their float-float statistics, and the
-        // rows widened to FP64 for the FP64 chain rule below; the Zh buffer holds the pairs meanwhile
-        float2 *Wff = (float2 *)Zh;
+        // rows widened to FP64 for the FP64 chain rule below
         GPR_TRY(oz_prepare(M, st));
         GPR_TRY(oz_unit_tables(M, g, Tu, st));
         GPR_TRY(launch_oz_w(M, g, Tu, plist, 0, npts, Wff, st));
@@ -744,7 +820,8 @@ extern "C" gpr_status gpr_lcp_backward(gpr_model *M, const gpr_grid *grid, doubl
     // Zh rows, R = Zh^T W (split over points), M = R - v t^T, N = L^-T M L^-1
     {
         ProfScope ps("adj_zhat", st);
-        k_zhat<<<(unsigned)((npts + 7) / 8), 256, 0, st>>>(g, plist, npts, slot, W, G16, mp, Zh);
+        if (use_oz) k_zhat_ff<<<(unsigned)((npts + 7) / 8), 256, 0, st>>>(g, plist, npts, slot, Wff, G16, mp, Zh);
+        else k_zhat<<<(unsigned)((npts + 7) / 8), 256, 0, st>>>(g, plist, npts, slot, W, G16, mp, Zh);
     }
     note_launch();
     // R splits: 19 x (mp/64) x (mp/128) tiles = 608 CTAs = 4 waves of 152 for mp = 512
