@@ -61,7 +61,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-sample", type=int, default=64, help="cells per axis of the oracle sample")
     p.add_argument("--case", default="full", choices=["full", "small"],
-                   help="small: one dense LCP field of the same field on a 64^3 grid (for ncu captures)")
+                   help="small: one dense LCP field of the same field on a 64^3 grid (for ncu captures); "
+                        "with --mode backward, the backward step on a 64^3 grid")
     return p.parse_args()
 
 
@@ -188,21 +189,22 @@ def run_backward(args, g, torch, rank, world, local):
     """Forward LCP field + gpr_lcp_backward on the differentiation workload; metric: grid points/s
     of (forward + backward) steps."""
     w = workloads.config5()
-    n = w.n
+    n = 64 if args.case == "small" else w.n
     grid = g.make_grid(n)
     th = w.isovalues[0]
     opts = g.lcp_options(prec=g.GPR_P_TF32X3)
-    wts = torch.tensor(w.extra["cell_weights"], dtype=torch.float32, device="cuda")
+    cw = w.extra["cell_weights"] if n == w.n else np.random.default_rng(5).random((n - 1) ** 3)
+    wts = torch.tensor(cw, dtype=torch.float32, device="cuda")
     field = torch.zeros((n - 1) ** 3, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
-    split_ev = []
+    split_ev, dstats = [], []
 
     def step():
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
         ev[0].record(stream)
         M = g.gpr_model_create(w.X, w.y, w.kernel, w.ell, w.sf2, w.sn2, stream=stream)
-        g.gpr_lcp_dense(M, grid, th, opts, field, stream=stream)
+        dstats[:] = [g.gpr_lcp_dense(M, grid, th, opts, field, stream=stream)]
         ev[1].record(stream)
         dy, dl = g.gpr_lcp_backward(M, grid, th, opts, wts, stream=stream)
         ev[2].record(stream)
@@ -230,9 +232,11 @@ def run_backward(args, g, torch, rank, world, local):
     out = {"metric": METRIC + " (forward + backward)", "value": world * n ** 3 / (ms / 1e3), "unit": UNIT, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": f"{w.name}: loss = sum_c U(0,1)_c LCP_c, d/dy (500) and d/dlog l (3)"},
+           "config": {"workload": f"{w.name}: loss = sum_c U(0,1)_c LCP_c, d/dy (500) and d/dlog l (3)",
+                      "grid": n},
            "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
            "forward_ms": float(np.mean([e[0].elapsed_time(e[1]) for e in split_ev])),
+           "corner_points": dstats[0]["recon_points"], "cells_estimated": dstats[0]["cells_estimated"],
            "backward_ms": float(np.mean([e[1].elapsed_time(e[2]) for e in split_ev])),
            "grad_norm_y": float(np.linalg.norm(dy)), "grad_loglen": [float(v) for v in dl],
            "clocks": clk.summary(), "gpu_launches": g.gpr_launch_count()}
@@ -336,7 +340,7 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl")
     w = workloads.config2()
-    if args.case == "small":
+    if args.case == "small" and args.mode != "backward":
         n = 64
         grid = g.make_grid(n)
         out = torch.zeros((n - 1) ** 3, dtype=torch.float32, device="cuda")
