@@ -466,6 +466,22 @@ __global__ void k_zhat_ff(GridDev g, const int64_t *pts, int64_t np, const int32
     }
 }
 
+// Rows and statistics of the listed points from the model's grid cache (rows and stats15 by
+// grid point): float-float rows, their FP64 values and stats15 in list order.  Thread per pair of
+// row elements (rows 512-byte aligned, mp even).
+__global__ void k_gather_rows(const float2 *Wc, const double *Sc, const int64_t *pts, int64_t np, int64_t mp,
+                              float2 *Wff, double *W, double *S15)
+{
+    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t half = mp / 2;
+    if (idx >= np * half) return;
+    const int64_t r = idx / half, j2 = idx % half, p = pts[r];
+    const float4 v = ((const float4 *)(Wc + p * mp))[j2];
+    ((float4 *)(Wff + r * mp))[j2] = v;
+    ((double2 *)(W + r * mp))[j2] = make_double2(f2d_bits(v.x) + f2d_bits(v.y), f2d_bits(v.z) + f2d_bits(v.w));
+    if (j2 < 15) S15[r * 15 + j2] = Sc[p * 15 + j2];
+}
+
 // Generic FP64 tiled GEMM: C_z = opA(A) B over the K range of split z (partials stacked by z).
 // opA(i,k) = TA ? A[k*lda + i] : A[i*lda + k];  LOWERB: B[k][j] = 0 for k < j (skip those k).
 constexpr int GB = 64, GK = 16;
@@ -719,9 +735,21 @@ extern "C" gpr_status gpr_lcp_backward(gpr_model *M, const gpr_grid *grid, doubl
     float2 *Tu = cv.take<float2>(te);
     double *Q64 = cv.take<double>(te);
     GPR_TRY(build_tables(M, g, T64, T32, st, Tff));
+    // The model's grid cache: the per-point FP32-class mean/variance, float-float rows and complete
+    // statistics that forward calls on this grid left are reused (what is missing is added).
+    GridCache *C = nullptr;
+    if (opts->exact == GPR_EXACT_AUTO && oz_supported(M) && opts->prec != GPR_P_FP64)
+        GPR_TRY(grid_cache(M, grid, g, opts->prec, &C, st));
     // cells whose LCP is not identically 0 near the current parameters (same cascade as the forward)
     if (opts->prec == GPR_P_FP64) {
         GPR_CUDA_TRY(cudaMemsetAsync(keep, 1, (size_t)nc, st));
+    } else if (C) {
+        GPR_CUDA_TRY(cudaMemsetAsync(pflag, 1, (size_t)n, st));
+        GPR_TRY(cache_fill_mv(M, C, g, pflag, plist, mean, var, part, cscr, csb, st));
+        double mv, mm;
+        prepass_margins(M, mv, mm);
+        if (opts->prec == GPR_P_TF32 || opts->prec == GPR_P_BF16) mv = M->kp.sf2;
+        launch_classify_cells_mv(g, C->mv, isovalue, opts->skip_eps, opts->jitter, mv, mm, keep, st);
     } else {
         GPR_TRY(fast_meanvar(M, g, opts->prec, T32, Tff, T64, nullptr, 0, n, mean, var, part, st));
         double mv, mm;
@@ -750,7 +778,8 @@ extern "C" gpr_status gpr_lcp_backward(gpr_model *M, const gpr_grid *grid, doubl
                 Carver::round((size_t)npts * 16 * 8) + Carver::round((size_t)nchunks * mp * 8) +
                 Carver::round((size_t)splits * mp * mp * 8) + 3 * Carver::round((size_t)mp * mp * 8) +
                 4 * Carver::round((size_t)mp * 8) + Carver::round((size_t)ncell * sizeof(AdjRec)) +
-                Carver::round((size_t)ncell * kRed * 4) + (use_oz ? Carver::round((size_t)npts * mp * 8) : 0) + 4096;
+                Carver::round((size_t)ncell * kRed * 4) + (use_oz ? Carver::round((size_t)npts * mp * 8) : 0) +
+                (C && C->W ? Carver::round((size_t)n * 2) + Carver::round((size_t)n * 16) : 0) + 4096;
     GPR_TRY(ws_reserve(M, 1, b2, st));
     Carver cv2{(char *)ws_ptr(M, 1)};
     double *W = cv2.take<double>((size_t)npts * mp);
@@ -768,7 +797,16 @@ extern "C" gpr_status gpr_lcp_backward(gpr_model *M, const gpr_grid *grid, doubl
     AdjRec *arec = cv2.take<AdjRec>((size_t)ncell);
     float *ared = cv2.take<float>((size_t)ncell * kRed);
     float2 *Wff = use_oz ? cv2.take<float2>((size_t)npts * mp) : nullptr;
-    if (use_oz) {
+    if (C && C->W) {
+        uint8_t *tmpflag = cv2.take<uint8_t>((size_t)n * 2);
+        int64_t *list2 = cv2.take<int64_t>((size_t)n * 2);
+        std::lock_guard<std::mutex> leaf_lock(M->leaf_mu);
+        int64_t nrows = 0;
+        GPR_TRY(cache_fill_stats(M, C, g, pflag, tmpflag, list2, cscr, csb, &nrows, st));
+        k_gather_rows<<<(unsigned)((npts * (mp / 2) + 255) / 256), 256, 0, st>>>(C->W, C->S15, plist, npts, mp, Wff,
+                                                                                 W, S15);
+        note_launch();
+    } else if (use_oz) {
         // FP64-class rows on the tensor cores (digit split), their float-float statistics, and the
         // rows widened to FP64 for the FP64 chain rule below
         GPR_TRY(oz_prepare(M, st));

@@ -108,3 +108,20 @@ def test_backward_rejects_mc(torch, g):
     with pytest.raises(g.GPRError) as e:
         g.gpr_lcp_backward(M, g.make_grid(9), 0.0, g.lcp_options(est=g.GPR_EST_MC), dl)
     assert e.value.status == g.GPR_ERR_UNSUPPORTED
+
+
+def test_backward_after_forward_reuses_cache(torch, g):
+    """A backward after a forward call on the same model and grid takes the pre-pass table, rows and
+    statistics from the model's grid cache; the gradient equals that of a backward on a fresh model
+    (up to the order of the FP64 atomic sums)."""
+    w = workloads.small(7, 60, 17, ell=(0.2, 0.25, 0.3))
+    n, th = 17, w.isovalues[0]
+    wts = np.random.default_rng(3).random((n - 1) ** 3)
+    dy0, dl0 = _gpu_grad(g, torch, w, n, th, wts)
+    M = model_of(w)
+    f = torch.zeros((n - 1) ** 3, dtype=torch.float32, device="cuda")
+    g.gpr_lcp_dense(M, g.make_grid(n), th, g.lcp_options(), f)
+    dl_t = torch.tensor(wts, dtype=torch.float32, device="cuda")
+    dy1, dl1 = g.gpr_lcp_backward(M, g.make_grid(n), th, g.lcp_options(), dl_t)
+    np.testing.assert_allclose(dy1, dy0, rtol=1e-10, atol=1e-12 * np.abs(dy0).max())
+    np.testing.assert_allclose(dl1, dl0, rtol=1e-10, atol=1e-12 * np.abs(dl0).max())
