@@ -513,7 +513,8 @@ __device__ __forceinline__ void dot2_step(float &sh, float &sl, float2 a, float2
 
 __global__ void __launch_bounds__(256, 2) k_stats_ff(GridDev g, const int64_t *pts, int64_t count,
                                                      const int32_t *slot, const float2 *W, int64_t mp, int64_t m,
-                                                     const float2 *vyff, double sf2, Prior13 pr, double *out15,
+                                                     const float2 *vyff, double sf2, const __grid_constant__ Prior13 pr,
+                                                     double *out15,
                                                      int out_by_point, int64_t row_mod)
 {
     int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
@@ -560,23 +561,38 @@ __global__ void __launch_bounds__(256, 2) k_stats_ff(GridDev g, const int64_t *p
             dot2_step(sh[2 + e], sl[2 + e], a1, make_float2(q[e].z, q[e].w));
         }
     }
+    // Combine the lanes in float-float (FP64 arithmetic runs at 1/64 rate on this part) by a
+    // halving exchange: at offset o each lane keeps one half of its values and adds its partner's
+    // copy of that half, so 16 values take 8 + 4 + 2 + 1 + 1 exchanges instead of 16 x 5; value
+    // q ends in lanes 2q and 2q + 1.
+    FF v[16];
 #pragma unroll
-    for (int q = 0; q < 15; ++q) {
-        // combine lanes in float-float (FP64 arithmetic runs at 1/64 rate on this part)
-        FF v = {sh[q], sl[q]};
-        v = ff_add(FF{v.h, 0.f}, FF{v.l, 0.f});
+    for (int q = 0; q < 15; ++q) v[q] = ff_add(FF{sh[q], 0.f}, FF{sl[q], 0.f});
+    v[15] = FF{0.f, 0.f};
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            FF t = {__shfl_xor_sync(0xffffffffu, v.h, o), __shfl_xor_sync(0xffffffffu, v.l, o)};
-            v = ff_add(v, t);
+    for (int half = 8, o = 16; half >= 1; half >>= 1, o >>= 1) {
+        const bool hi = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < half; ++i) {
+            const FF keep = hi ? v[i + half] : v[i], send = hi ? v[i] : v[i + half];
+            const FF t = {__shfl_xor_sync(0xffffffffu, send.h, o), __shfl_xor_sync(0xffffffffu, send.l, o)};
+            v[i] = ff_add(keep, t);
         }
-        if (lane == 0) {
-            double dv = (double)v.h + (double)v.l;
-            double *o = out15 + (out_by_point ? p : pos) * 15;
-            if (q == 0) o[0] = dv;
-            else if (q == 1) o[1] = sf2 - dv;
-            else o[q] = nb[q - 2] >= 0 ? pr.k[q - 2] - dv : (double)NAN;
-        }
+    }
+    {
+        const FF t = {__shfl_xor_sync(0xffffffffu, v[0].h, 1), __shfl_xor_sync(0xffffffffu, v[0].l, 1)};
+        v[0] = ff_add(v[0], t);
+    }
+    uint32_t valid = 0;  // neighbours on the grid, as bits (no runtime index into nb)
+#pragma unroll
+    for (int e = 0; e < 13; ++e) valid |= (nb[e] >= 0 ? 1u : 0u) << e;
+    const int q = lane >> 1;
+    if ((lane & 1) == 0 && q < 15) {
+        const double dv = (double)v[0].h + (double)v[0].l;
+        double *o = out15 + (out_by_point ? p : pos) * 15;
+        if (q == 0) o[0] = dv;
+        else if (q == 1) o[1] = sf2 - dv;
+        else o[q] = (valid >> (q - 2)) & 1u ? pr.k[q - 2] - dv : (double)NAN;
     }
 }
 
