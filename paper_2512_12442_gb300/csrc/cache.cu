@@ -168,6 +168,7 @@ gpr_status cache_fill_mv(gpr_model *M, GridCache *C, const GridDev &g, const uin
                          float *tmp_var, float *part, void *cscr, size_t csb, cudaStream_t st)
 {
     // `list` doubles as the need-flag buffer (n bytes) before holding the compacted indices
+    MvFillScope fill(M, st);
     int64_t n = C->n;
     uint8_t *need = (uint8_t *)tmp_var;  // n floats >= n bytes
     k_need<<<nb(n, 256), 256, 0, st>>>(flag, C->have_mv, n, need);

@@ -106,6 +106,27 @@ struct gpr_model {
     // serialises the leaf phases of concurrent fields of one model, so that each finds the rows
     // and statistics the previous one cached instead of recomputing them alongside it
     std::mutex leaf_mu;
+    // orders the fills of the per-point (mean, var) table by concurrent fields of one model: a
+    // fill waits (on the device) for the previous one, so no point is computed twice
+    std::mutex mv_mu;
+    cudaEvent_t mv_ev = nullptr;
+};
+
+// Scope of one fill of the per-point (mean, var) table: holds the model's mv lock, orders the
+// caller's stream after the previous fill, and marks the end of this fill on exit.
+struct MvFillScope {
+    gpr_model *M;
+    cudaStream_t st;
+    std::lock_guard<std::mutex> lock;
+    MvFillScope(gpr_model *m, cudaStream_t s) : M(m), st(s), lock(m->mv_mu)
+    {
+        if (M->mv_ev) cudaStreamWaitEvent(st, M->mv_ev, 0);
+        else cudaEventCreateWithFlags(&M->mv_ev, cudaEventDisableTiming);
+    }
+    ~MvFillScope()
+    {
+        if (M->mv_ev) cudaEventRecord(M->mv_ev, st);
+    }
 };
 
 // Makes workspace slot `which` at least `bytes` long (cudaMalloc only when it grows).  The

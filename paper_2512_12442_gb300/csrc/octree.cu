@@ -793,6 +793,7 @@ gpr_status octree_lcp(gpr_model *M, const gpr_grid *grid, double theta, int D, c
         note_launch();
         // small nodes: exact minimum over grid points from the per-point table
         {
+            MvFillScope fill(M, st);
             GPR_CUDA_TRY(cudaMemsetAsync(B.need, 0, (size_t)n, st));
             k_mark_small_points<<<nb(count, 128), 128, 0, st>>>(g, D, l, nodes, count, B.decision, B.have, B.need);
             note_launch();
@@ -815,15 +816,21 @@ gpr_status octree_lcp(gpr_model *M, const gpr_grid *grid, double theta, int D, c
             GPR_TRY(compact_flags(B.lflag, count, B.pend, nullptr, &npend, B.cscr, B.csb, st));
             if (npend > 0) {
                 // lattice values: aligned nodes from the per-point table, unaligned ones evaluated
-                GPR_CUDA_TRY(cudaMemsetAsync(B.need, 0, (size_t)n, st));
-                k_mark_lattice<<<nb(npend, 128), 128, 0, st>>>(g, D, l, nodes, B.pend, npend, B.have, B.need, B.unal);
-                note_launch();
-                int64_t nneed = 0;
-                GPR_TRY(compact_flags(B.need, n, B.plist, nullptr, &nneed, B.cscr, B.csb, st));
-                if (nneed > 0) {
-                    GPR_TRY(fast_meanvar(M, g, pp, T32, Tff, T64, B.plist, 0, nneed, B.tmp_mean, B.tmp_var, B.part, st));
-                    k_scatter_mv<<<nb(nneed, 256), 256, 0, st>>>(B.plist, nneed, B.tmp_mean, B.tmp_var, B.mv, B.have);
+                {
+                    MvFillScope fill(M, st);
+                    GPR_CUDA_TRY(cudaMemsetAsync(B.need, 0, (size_t)n, st));
+                    k_mark_lattice<<<nb(npend, 128), 128, 0, st>>>(g, D, l, nodes, B.pend, npend, B.have, B.need,
+                                                                   B.unal);
                     note_launch();
+                    int64_t nneed = 0;
+                    GPR_TRY(compact_flags(B.need, n, B.plist, nullptr, &nneed, B.cscr, B.csb, st));
+                    if (nneed > 0) {
+                        GPR_TRY(fast_meanvar(M, g, pp, T32, Tff, T64, B.plist, 0, nneed, B.tmp_mean, B.tmp_var,
+                                             B.part, st));
+                        k_scatter_mv<<<nb(nneed, 256), 256, 0, st>>>(B.plist, nneed, B.tmp_mean, B.tmp_var, B.mv,
+                                                                     B.have);
+                        note_launch();
+                    }
                 }
                 k_lattice_from_table<<<nb(npend * 27, 256), 256, 0, st>>>(g, D, l, nodes, B.pend, npend, B.unal, B.mv,
                                                                           theta, M->kp.sf2, B.lat);

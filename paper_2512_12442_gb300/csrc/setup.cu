@@ -359,6 +359,7 @@ extern "C" gpr_status gpr_model_destroy(gpr_model *M)
     tc_release(M);
     oz_release(M);
     cache_release(M);
+    if (M->mv_ev) cudaEventDestroy(M->mv_ev);
     delete M;
     return GPR_OK;
 }
