@@ -341,22 +341,34 @@ __global__ void __launch_bounds__(G_NTHR, 1) k_oz_gemm(const __grid_constant__ C
         const int lq = warp & 3, half = (warp - 2) >> 2;
         FF acc[32];
         oz_drain<S>(P, nch, lq, half, lane, acc, ok);
-        const int64_t row = row0 + lq * 32 + lane;
-        if (row < prm.count) {
-            int64_t p = prm.pts ? prm.pts[row] : prm.pt_base + row;
-            const bool rv = p >= 0 && p < (int64_t)prm.g.n[0] * prm.g.n[1] * (int64_t)prm.g.n[2];
-            if (rv) {
-                const int64_t orow = prm.out_by_point ? p % prm.row_mod : prm.out_off + row;
-                float2 *out = prm.W + orow * prm.mp + n0 + half * 32;
+        // Stage the 128 x 64 tile in shared memory (the pipeline stages are free: every MMA has
+        // completed), 16-byte chunks XOR-swizzled by row, then store whole 512-byte row pieces.
+        float4 *tile = (float4 *)P.smem;  // row r, chunk k (columns 2k, 2k+1) at r * 32 + (k ^ (r & 31))
+        const int r = lq * 32 + lane;
 #pragma unroll
-                for (int c = 0; c < 32; ++c) {
-                    const int64_t j = n0 + half * 32 + c;
-                    float cs = (j < prm.mp) ? prm.colscale[j] : 0.f;
-                    FF v = {acc[c].h * cs, acc[c].l * cs};  // power-of-two scale: exact
-                    if (prm.sf2 != 1.0f) v = ff_mul(v, FF{prm.sf2, 0.f});
-                    if (j < prm.mp) out[c] = make_float2(v.h, v.l);
-                }
+        for (int c = 0; c < 32; c += 2) {
+            const int64_t j = n0 + half * 32 + c;
+            FF v[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const float cs = (j + h < prm.mp) ? prm.colscale[j + h] : 0.f;
+                v[h] = FF{acc[c + h].h * cs, acc[c + h].l * cs};  // power-of-two scale: exact
+                if (prm.sf2 != 1.0f) v[h] = ff_mul(v[h], FF{prm.sf2, 0.f});
             }
+            const int k = (half * 32 + c) >> 1;
+            tile[r * 32 + (k ^ (r & 31))] = make_float4(v[0].h, v[0].l, v[1].h, v[1].l);
+        }
+        asm volatile("bar.sync 1, 256;" ::: "memory");  // the 8 drain warps
+        const int64_t npts = (int64_t)prm.g.n[0] * prm.g.n[1] * (int64_t)prm.g.n[2];
+        for (int rr = 0; rr < 16; ++rr) {
+            const int rt = (warp - 2) * 16 + rr;
+            const int64_t row = row0 + rt;
+            if (row >= prm.count) break;
+            const int64_t p = prm.pts ? prm.pts[row] : prm.pt_base + row;
+            if (p < 0 || p >= npts) continue;
+            const int64_t orow = prm.out_by_point ? p % prm.row_mod : prm.out_off + row;
+            if (n0 + 2 * lane < prm.mp)
+                *(float4 *)(prm.W + orow * prm.mp + n0 + 2 * lane) = tile[rt * 32 + (lane ^ (rt & 31))];
         }
     }
     oz_teardown(P.tmem, ok, prm.status);
@@ -416,18 +428,37 @@ __global__ void __launch_bounds__(G_NTHR, 1) k_oz_dgemm(const __grid_constant__ 
         const int lq = warp & 3, half = (warp - 2) >> 2;
         FF acc[32];
         oz_drain<S>(P, nch, lq, half, lane, acc, ok);
-        const int64_t row = row0 + lq * 32 + lane;
-        if (row < prm.M) {
-            const int er = prm.ea[row];
-            double *out = prm.C + (int64_t)blockIdx.z * prm.cstride + row * prm.ldc;
+        // FP64 values staged in shared memory (16-byte chunks XOR-swizzled by row, as in
+        // k_oz_gemm), then stored (or added) as whole row pieces
+        double2 *tile = (double2 *)P.smem;
+        const int r = lq * 32 + lane;
+        const int64_t row = row0 + r;
+        const int er = row < prm.M ? prm.ea[row] : 0;
 #pragma unroll
-            for (int c = 0; c < 32; ++c) {
-                const int64_t j = n0 + half * 32 + c;
-                if (j < prm.N) {
-                    const int sc = er + prm.eb[j];
-                    const double v = f2d_scaled(acc[c].h, sc) + f2d_scaled(acc[c].l, sc);
-                    out[j] = prm.accumulate ? out[j] + v : v;
+        for (int c = 0; c < 32; c += 2) {
+            const int64_t j = n0 + half * 32 + c;
+            const int s0 = er + (j < prm.N ? prm.eb[j] : 0), s1 = er + (j + 1 < prm.N ? prm.eb[j + 1] : 0);
+            const int k = (half * 32 + c) >> 1;
+            tile[r * 32 + (k ^ (r & 31))] = make_double2(f2d_scaled(acc[c].h, s0) + f2d_scaled(acc[c].l, s0),
+                                                         f2d_scaled(acc[c + 1].h, s1) + f2d_scaled(acc[c + 1].l, s1));
+        }
+        asm volatile("bar.sync 1, 256;" ::: "memory");  // the 8 drain warps
+        const int64_t j = n0 + 2 * lane;
+        for (int rr = 0; rr < 16; ++rr) {
+            const int rt = (warp - 2) * 16 + rr;
+            const int64_t orow = row0 + rt;
+            if (orow >= prm.M) break;
+            const double2 v = tile[rt * 32 + (lane ^ (rt & 31))];
+            double *out = prm.C + (int64_t)blockIdx.z * prm.cstride + orow * prm.ldc + j;
+            if (j + 1 < prm.N) {
+                double2 o = v;
+                if (prm.accumulate) {
+                    const double2 a = *(const double2 *)out;
+                    o = make_double2(a.x + v.x, a.y + v.y);
                 }
+                *(double2 *)out = o;
+            } else if (j < prm.N) {
+                out[0] = prm.accumulate ? out[0] + v.x : v.x;
             }
         }
     }
