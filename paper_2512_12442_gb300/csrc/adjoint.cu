@@ -60,15 +60,16 @@ struct Lat {
     uint32_t G[7];
 };
 
-// FP32 view of one kept cell's factor for the sampling sweep.
+// FP32 view of one kept cell's factor for the sampling sweep, rows pre-scaled by 1/L_ii:
+// u_i = sg bs_i - sum_{j<i} Ls_ij z_j with Ls_ij = L_ij / L_ii, bs_i = (theta - mu_i) / L_ii.
 struct AdjRec {
-    float L[36];
-    float inv[8];
-    float b[8];
+    float Ls[28];  // strictly lower part, entry (i, j) at trs(i, j)
+    float bs[8];
     int active;
     int pad[3];
 };
-constexpr int kRed = 1 + 8 + 36;  // P_lo + P_hi, mu adjoint (8), Lbar (36): FP32 sums per cell
+__device__ __forceinline__ int trs(int i, int j) { return i * (i - 1) / 2 + j; }
+constexpr int kRed = 1 + 8 + 28;  // P_lo + P_hi, bs adjoint (8), Ls adjoint (28): FP32 sums per cell
 
 // The cell's 8 corner statistics, jitter and FP64 Cholesky factor, exactly as the forward
 // estimator forms them; false when the cell is skipped (zero weight, no variance, Boole test).
@@ -147,10 +148,10 @@ __global__ void k_adj_prep(GridDev g, const double *stats, const int32_t *slot, 
     }
 #pragma unroll
     for (int a = 0; a < 8; ++a) {
-        R.b[a] = (float)(theta - mu[a]);
-        R.inv[a] = (float)(1.0 / Lm[a][a]);
+        const double inv = 1.0 / Lm[a][a];
+        R.bs[a] = (float)((theta - mu[a]) * inv);
 #pragma unroll
-        for (int b = 0; b <= a; ++b) R.L[tri(a, b)] = (float)Lm[a][b];
+        for (int b = 0; b < a; ++b) R.Ls[trs(a, b)] = (float)(Lm[a][b] * inv);
     }
     R.active = 1;
 }
@@ -175,13 +176,13 @@ __global__ void __launch_bounds__(256, 2) k_adj_sample(const AdjRec *rec, const 
     uint32_t Ds[7];
 #pragma unroll
     for (int i = 0; i < 7; ++i) Ds[i] = __shfl_sync(0xffffffffu, D, i);
-    // mbar: adjoint of mu (b_lo = theta - mu, b_hi = mu - theta), P: both orthant sums
-    float mbar[8], Lbar[36];
+    // bbar: adjoint of bs (orthant sign folded in), Lbar: of Ls, P: both orthant sums
+    float bbar[8], Lbar[28];
     float P = 0.f;
 #pragma unroll
-    for (int i = 0; i < 8; ++i) mbar[i] = 0.f;
+    for (int i = 0; i < 8; ++i) bbar[i] = 0.f;
 #pragma unroll
-    for (int t = 0; t < 36; ++t) Lbar[t] = 0.f;
+    for (int t = 0; t < 28; ++t) Lbar[t] = 0.f;
     const float fbar = -wbar / (float)N;
     for (int k = lane; k < N; k += 32) {
         float w[7];
@@ -195,19 +196,17 @@ __global__ void __launch_bounds__(256, 2) k_adj_sample(const AdjRec *rec, const 
             float sg = side == 0 ? 1.f : -1.f;
             float u[8], e[8], z[7];
             float f = 1.f;
-            bool ok = true;
+            // no early exit: once f underflows to 0 the rest stays finite and the sample adds 0
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
-                float s = 0.f;
+                float s = sg * W.bs[i];
 #pragma unroll
-                for (int j = 0; j < i; ++j) s = fmaf(W.L[tri(i, j)], z[j], s);
-                u[i] = (sg * W.b[i] - s) * W.inv[i];
+                for (int j = 0; j < i; ++j) s = fmaf(-W.Ls[trs(i, j)], z[j], s);
+                u[i] = s;
                 e[i] = nrm_cdf(u[i]);
                 f *= e[i];
-                if (!(f > 0.f)) { ok = false; break; }
                 if (i < 7) z[i] = nrm_ppf(fmaxf(w[i] * e[i], 1e-37f));
             }
-            if (!ok) continue;
             P += f;
             if (!(f > 1e-30f)) continue;  // negligible share of value and gradient (both scale with f)
             float zbar[7];
@@ -220,14 +219,12 @@ __global__ void __launch_bounds__(256, 2) k_adj_sample(const AdjRec *rec, const 
                     const float iph = 2.50662827f * __expf(0.5f * z[i] * z[i]);  // 1 / phi(z)
                     if (iph < INFINITY) ebar = fmaf(zbar[i] * w[i], iph, ebar);
                 }
-                float ubar = ebar * npdf(u[i]);
-                mbar[i] = fmaf(side == 0 ? -ubar : ubar, W.inv[i], mbar[i]);
-                float sbar = -ubar * W.inv[i];
-                Lbar[tri(i, i)] += -ubar * u[i] * W.inv[i];
+                const float ubar = ebar * npdf(u[i]);
+                bbar[i] = fmaf(sg, ubar, bbar[i]);
 #pragma unroll
                 for (int j = 0; j < i; ++j) {
-                    Lbar[tri(i, j)] = fmaf(sbar, z[j], Lbar[tri(i, j)]);
-                    zbar[j] = fmaf(sbar, W.L[tri(i, j)], zbar[j]);
+                    Lbar[trs(i, j)] = fmaf(-ubar, z[j], Lbar[trs(i, j)]);
+                    zbar[j] = fmaf(-ubar, W.Ls[trs(i, j)], zbar[j]);
                 }
             }
         }
@@ -236,7 +233,7 @@ __global__ void __launch_bounds__(256, 2) k_adj_sample(const AdjRec *rec, const 
     float out0 = 0.f, out1 = 0.f;
 #pragma unroll
     for (int t = 0; t < kRed; ++t) {
-        float v = t == 0 ? P : (t < 9 ? mbar[t - 1] : Lbar[t - 9]);
+        float v = t == 0 ? P : (t < 9 ? bbar[t - 1] : Lbar[t - 9]);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         if (t == lane) out0 = v;
@@ -261,14 +258,26 @@ __global__ void k_adj_chol(GridDev g, const double *stats, const int32_t *slot, 
     const float *rd = red + q * kRed;
     const double lcp = 1.0 - (double)rd[0] / N;
     if (lcp < 0.0 || lcp > 1.0) return;  // clamped: constant in a neighbourhood
-    double Lb[8][8], Pm[8][8], T[8][8], Li[8][8];
+    // adjoints of the pre-scaled rows back to L: Ls_ij = L_ij / L_ii, bs_i = (theta - mu_i) / L_ii
+    double Lb[8][8], Pm[8][8], T[8][8], Li[8][8], mubar[8];
 #pragma unroll
-    for (int i = 0; i < 8; ++i)
+    for (int i = 0; i < 8; ++i) {
+        const double inv = 1.0 / L[i][i], bsb = (double)rd[1 + i];
+        double dg = bsb * (theta - mu[i]) * inv;
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             if (j > i) L[i][j] = 0.0;
-            Lb[i][j] = j <= i ? (double)rd[9 + tri(i, j)] : 0.0;
+            Lb[i][j] = 0.0;
         }
+#pragma unroll
+        for (int j = 0; j < i; ++j) {
+            const double lsb = (double)rd[9 + trs(i, j)];
+            Lb[i][j] = lsb * inv;
+            dg += lsb * L[i][j] * inv;
+        }
+        Lb[i][i] = -dg * inv;
+        mubar[i] = -bsb * inv;
+    }
 #pragma unroll
     for (int i = 0; i < 8; ++i)
 #pragma unroll
@@ -319,7 +328,7 @@ __global__ void k_adj_chol(GridDev g, const double *stats, const int32_t *slot, 
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
         double *gp = G16 + (int64_t)slots[i] * 16;
-        atomicAdd(gp + 0, (double)rd[1 + i]);
+        atomicAdd(gp + 0, mubar[i]);
         atomicAdd(gp + 1, Pm[i][i] + (i == am ? tau * tr : 0.0));
     }
 #pragma unroll
