@@ -44,8 +44,6 @@ Pairs make_pairs()
     return t;
 }
 
-__device__ __forceinline__ int tri(int i, int j) { return i * (i + 1) / 2 + j; }
-
 __device__ __forceinline__ uint64_t splitmix64(uint64_t seed, uint64_t k)
 {
     uint64_t z = seed + k * 0x9E3779B97F4A7C15ULL;
@@ -184,6 +182,8 @@ __global__ void __launch_bounds__(256, 2) k_adj_sample(const AdjRec *rec, const 
 #pragma unroll
     for (int t = 0; t < 28; ++t) Lbar[t] = 0.f;
     const float fbar = -wbar / (float)N;
+    // the first coordinate does not depend on the sample: its factor and density, per orthant
+    const float e0lo = nrm_cdf(W.bs[0]), e0hi = nrm_cdf(-W.bs[0]), pdf0 = npdf(W.bs[0]);
     for (int k = lane; k < N; k += 32) {
         float w[7];
 #pragma unroll
@@ -203,7 +203,7 @@ __global__ void __launch_bounds__(256, 2) k_adj_sample(const AdjRec *rec, const 
 #pragma unroll
                 for (int j = 0; j < i; ++j) s = fmaf(-W.Ls[trs(i, j)], z[j], s);
                 u[i] = s;
-                e[i] = nrm_cdf(u[i]);
+                e[i] = i == 0 ? (side ? e0hi : e0lo) : nrm_cdf(u[i]);
                 f *= e[i];
                 if (i < 7) z[i] = nrm_ppf(fmaxf(w[i] * e[i], 1e-37f));
             }
@@ -219,7 +219,7 @@ __global__ void __launch_bounds__(256, 2) k_adj_sample(const AdjRec *rec, const 
                     const float iph = 2.50662827f * __expf(0.5f * z[i] * z[i]);  // 1 / phi(z)
                     if (iph < INFINITY) ebar = fmaf(zbar[i] * w[i], iph, ebar);
                 }
-                const float ubar = ebar * npdf(u[i]);
+                const float ubar = ebar * (i == 0 ? pdf0 : npdf(u[i]));
                 bbar[i] = fmaf(sg, ubar, bbar[i]);
 #pragma unroll
                 for (int j = 0; j < i; ++j) {
@@ -636,7 +636,8 @@ __global__ void k_point_terms(GridDev g, const int64_t *pts, int64_t np, const d
 
 // Squared scaled distances per axis, Q_d[g][j] = ((x_g - X_jd) / l_d)^2 (zero for j >= m), laid out
 // like the kernel tables.
-__global__ void k_sqdist_tables(const double *X, int64_t m, int64_t mp, KernParams kp, GridDev g, double *Q)
+__global__ void k_sqdist_tables(const double *X, int64_t m, int64_t mp, KernParams kp, GridDev g, double *Q,
+                                float2 *Qff)
 {
     const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t total = (int64_t)(g.n[0] + g.n[1] + g.n[2]) * mp;
@@ -651,13 +652,54 @@ __global__ void k_sqdist_tables(const double *X, int64_t m, int64_t mp, KernPara
         v = t * t;
     }
     Q[idx] = v;
+    const float h = (float)v;
+    Qff[idx] = make_float2(h, (float)(v - (double)h));
 }
 
-// As k_point_terms for the SE kernel from its separable tables: k_pj = Tx Ty Tz (signal variance
-// in Tx) and dk_pj/dlog l_d = k_pj Q_d, so each (p, j) costs a handful of FP64 multiply-adds.
-__global__ void k_point_terms_se(GridDev g, const int64_t *pts, int64_t np, const double *T64, const double *Q,
-                                 int64_t m, const double *alpha, const double *Z, int64_t mp, const double *G16,
-                                 KdPrior kdp, double *out)
+// Float-float value of an FP64 number from its bit pattern (integer steps): hi = x rounded to 24
+// bits, lo = the remainder (rounded to 24 bits), |x - hi - lo| <= 2^-48 |x|.  Magnitudes outside
+// [2^-60, 2^61) take FP64 conversions instead.
+__device__ __forceinline__ float2 d2ff(double x)
+{
+    const long long b = __double_as_longlong(x);
+    const int E = (int)((b >> 52) & 0x7FF);
+    if (E < 1023 - 60 || E > 1023 + 60) {
+        const float h = (float)x;
+        return make_float2(h, (float)(x - (double)h));
+    }
+    const long long m53 = (b & 0xFFFFFFFFFFFFFLL) | (1LL << 52);  // x = m53 2^(E-1075)
+    const long long r = (m53 + (1LL << 28)) >> 29;                 // 24-bit rounding (2^24 carries)
+    const int rem = (int)(m53 - (r << 29));                          // |rem| <= 2^28
+    const float h = __int_as_float(((E - 896) << 23) + (int)(r - (1LL << 23)));
+    const float l = (float)rem * __int_as_float((E - 948) << 23);   // times 2^(E-1075)
+    return b < 0 ? make_float2(-h, -l) : make_float2(h, l);
+}
+
+__device__ __forceinline__ float2 ffmul(float2 a, float2 b)
+{
+    const float p = a.x * b.x;
+    float e = fmaf(a.x, b.x, -p);
+    e = fmaf(a.x, b.y, fmaf(a.y, b.x, e));
+    const float s = p + e;
+    return make_float2(s, e - (s - p));
+}
+
+__device__ __forceinline__ float2 ffadd(float2 a, float2 b)
+{
+    const float s = a.x + b.x;
+    const float bv = s - a.x;
+    const float err = ((a.x - (s - bv)) + (b.x - bv)) + (a.y + b.y);
+    const float r = s + err;
+    return make_float2(r, err - (r - s));
+}
+
+// k_point_terms for the SE kernel from its separable tables, k_pj = Tx Ty Tz (signal variance in
+// Tx) and dk_pj/dlog l_d = k_pj Q_d, in float-float arithmetic on the FP32 pipe (the FP64 pipe
+// runs at 1/64 of its rate): tables, alpha and g_mu as float-float, Z converted from FP64 by d2ff,
+// the three sums as compensated dot products; FP64 from the warp reduction on.
+__global__ void k_point_terms_se_ff(GridDev g, const int64_t *pts, int64_t np, const float2 *Tff, const float2 *Qff,
+                                    int64_t m, const float2 *alpha_ff, const double *Z, int64_t mp,
+                                    const double *G16, KdPrior kdp, double *out)
 {
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int64_t pos = blockIdx.x * (int64_t)(blockDim.x / 32) + warp;
@@ -666,14 +708,19 @@ __global__ void k_point_terms_se(GridDev g, const int64_t *pts, int64_t np, cons
         const int64_t p = pts[pos], nx = g.n[0], ny = g.n[1];
         const int64_t o0 = (p % nx) * mp, o1 = ((int64_t)g.n[0] + (p / nx) % ny) * mp,
                       o2 = ((int64_t)g.n[0] + g.n[1] + p / (nx * ny)) * mp;
-        const double gm = G16[pos * 16];
+        const float2 gm = d2ff(G16[pos * 16]);
         const double *zr = Z + pos * mp;
+        float sh[3] = {0.f, 0.f, 0.f}, sl[3] = {0.f, 0.f, 0.f};
         for (int64_t j = lane; j < m; j += 32) {
-            const double kc = T64[o0 + j] * T64[o1 + j] * T64[o2 + j] * fma(gm, alpha[j], -2.0 * zr[j]);
-            acc[0] = fma(kc, Q[o0 + j], acc[0]);
-            acc[1] = fma(kc, Q[o1 + j], acc[1]);
-            acc[2] = fma(kc, Q[o2 + j], acc[2]);
+            const float2 k = ffmul(ffmul(Tff[o0 + j], Tff[o1 + j]), Tff[o2 + j]);
+            const float2 z = d2ff(zr[j]);
+            const float2 kc = ffmul(k, ffadd(ffmul(gm, alpha_ff[j]), make_float2(-2.f * z.x, -2.f * z.y)));
+            const float2 q[3] = {Qff[o0 + j], Qff[o1 + j], Qff[o2 + j]};
+#pragma unroll
+            for (int d = 0; d < 3; ++d) ff_dot_step(sh[d], sl[d], kc.x, kc.y, q[d].x, q[d].y);
         }
+#pragma unroll
+        for (int d = 0; d < 3; ++d) acc[d] = f2d_bits(sh[d]) + f2d_bits(sl[d]);
         if (lane == 0)
             for (int e = 0; e < 13; ++e) {
                 const double gc = G16[pos * 16 + 2 + e];
@@ -726,7 +773,7 @@ extern "C" gpr_status gpr_lcp_backward(gpr_model *M, const gpr_grid *grid, doubl
     size_t b1 = Carver::round(te * 4) + Carver::round(te * 8) + Carver::round(te * 8) + 2 * Carver::round((size_t)n * 4) +
                 Carver::round((size_t)nc) + Carver::round((size_t)n) + Carver::round((size_t)n * 8) +
                 Carver::round((size_t)n * 4) + Carver::round((size_t)nc * 8) + csb +
-                Carver::round(tc_partial_elems(GPR_P_BF16X3, M, n) * 4) + 2 * Carver::round(te * 8) + 8192;
+                Carver::round(tc_partial_elems(GPR_P_BF16X3, M, n) * 4) + 3 * Carver::round(te * 8) + 8192;
     GPR_TRY(ws_reserve(M, 0, b1, st));
     Carver cv{(char *)ws_ptr(M, 0)};
     float *T32 = cv.take<float>(te);
@@ -743,6 +790,7 @@ extern "C" gpr_status gpr_lcp_backward(gpr_model *M, const gpr_grid *grid, doubl
     float *part = cv.take<float>(tc_partial_elems(GPR_P_BF16X3, M, n));
     float2 *Tu = cv.take<float2>(te);
     double *Q64 = cv.take<double>(te);
+    float2 *Qff = cv.take<float2>(te);
     GPR_TRY(build_tables(M, g, T64, T32, st, Tff));
     // The model's grid cache: the per-point FP32-class mean/variance, float-float rows and complete
     // statistics that forward calls on this grid left are reused (what is missing is added).
@@ -895,7 +943,7 @@ extern "C" gpr_status gpr_lcp_backward(gpr_model *M, const gpr_grid *grid, doubl
     }
     KdPrior kdp;
     for (int e = 0; e < 13; ++e) {
-        double a[3] = {0, 0, 0}, b[3];
+        double b[3];
         for (int d = 0; d < 3; ++d) b[d] = kOff13[e][d] * g.h[d];
         double r2 = 0.0;
         for (int d = 0; d < 3; ++d) r2 += (b[d] / M->kp.ell[d]) * (b[d] / M->kp.ell[d]);
@@ -907,14 +955,13 @@ extern "C" gpr_status gpr_lcp_backward(gpr_model *M, const gpr_grid *grid, doubl
                 kdp.k[e][d] = (5.0 / 3.0) * M->kp.sf2 * (1.0 + s5r) * exp(-s5r) * t2;
             }
         }
-        (void)a;
     }
     {
         ProfScope ps("adj_points", st);
         if (M->kp.kind == GPR_K_SE) {
-            k_sqdist_tables<<<(unsigned)((te + 255) / 256), 256, 0, st>>>(M->X, m, mp, M->kp, g, Q64);
-            k_point_terms_se<<<(unsigned)((npts + 7) / 8), 256, 0, st>>>(g, plist, npts, T64, Q64, m, M->alpha, W, mp,
-                                                                         G16, kdp, acc);
+            k_sqdist_tables<<<(unsigned)((te + 255) / 256), 256, 0, st>>>(M->X, m, mp, M->kp, g, Q64, Qff);
+            k_point_terms_se_ff<<<(unsigned)((npts + 7) / 8), 256, 0, st>>>(g, plist, npts, Tff, Qff, m, M->alpha_ff,
+                                                                            W, mp, G16, kdp, acc);
             note_launch();
         } else {
             k_point_terms<<<(unsigned)((npts + 7) / 8), 256, 0, st>>>(g, plist, npts, M->X, m, M->kp, M->alpha, W, mp,
