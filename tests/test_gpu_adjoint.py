@@ -45,6 +45,18 @@ def test_backward_small_vs_oracle(torch, g, prec):
     assert _rel(dl, odl) <= 2e-3, (dl, odl)
 
 
+def test_backward_matern_vs_oracle(torch, g):
+    """Matern-5/2: no digit split for its rows, so the FP64 rows, the FP64 GEMMs, the FP64 Zh and
+    the FP64 point terms (kernel derivative through r) carry the backward."""
+    w = workloads.small(6, 40, 11, ell=(0.25, 0.3, 0.35), kernel=workloads.MATERN52)
+    n, th = 11, w.isovalues[0]
+    wts = np.random.default_rng(6).random((n - 1) ** 3)
+    dy, dl = _gpu_grad(g, torch, w, n, th, wts)
+    loss, ody, odl = oracle.Model.from_workload(w).lcp_grad(n, th, wts)
+    assert _rel(dy, ody) <= 2e-3, (_rel(dy, ody), dy[:4], ody[:4])
+    assert _rel(dl, odl) <= 2e-3, (dl, odl)
+
+
 @pytest.mark.parametrize("exact", ["auto", "fp64"])
 def test_backward_config5_field_32cubed_vs_oracle(torch, g, exact):
     """The differentiation workload's field (m=500, ARD SE, noise 1e-4) on a 32^3 grid with U(0,1)
