@@ -711,6 +711,7 @@ __global__ void k_point_terms_se_ff(GridDev g, const int64_t *pts, int64_t np, c
         const float2 gm = d2ff(G16[pos * 16]);
         const double *zr = Z + pos * mp;
         float sh[3] = {0.f, 0.f, 0.f}, sl[3] = {0.f, 0.f, 0.f};
+#pragma unroll 4
         for (int64_t j = lane; j < m; j += 32) {
             const float2 k = ffmul(ffmul(Tff[o0 + j], Tff[o1 + j]), Tff[o2 + j]);
             const float2 z = d2ff(zr[j]);
