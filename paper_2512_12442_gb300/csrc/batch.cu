@@ -136,7 +136,7 @@ extern "C" gpr_status gpr_lcp_adaptive_batched(gpr_model *const *models, const g
         GPR_CUDA_TRY(cudaMalloc(&P.recs, want));
         P.rec_bytes = want;
     }
-    if (!P.nrec) GPR_CUDA_TRY(cudaMalloc(&P.nrec, sizeof(unsigned long long)));
+    if (!P.nrec) GPR_CUDA_TRY(cudaMalloc(&P.nrec, 2 * sizeof(unsigned long long)));  // count, estimator ticket
     std::atomic<int64_t> reserved{0};
     RecordSink sink{P.recs, P.nrec, cap, &reserved};
 

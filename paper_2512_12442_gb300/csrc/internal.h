@@ -268,13 +268,14 @@ struct LcpOpts {
 // (host counter of records promised) stays within `capacity`, else estimates on its own.
 struct RecordSink {
     void *recs;
-    unsigned long long *nrec;  // device counter of appended records
+    unsigned long long *nrec;  // device counter of appended records (and the estimator's ticket after it)
     int64_t capacity;
     std::atomic<int64_t> *reserved;
 };
 void set_record_sink(RecordSink *sink);  // for the calling thread; nullptr to clear
 size_t record_bytes();
-void launch_estimator(const void *recs, const unsigned long long *nrec, int64_t max_records, const LcpOpts &o,
+// nrec[0]: the device record count; nrec[1]: scratch for the estimator's work ticket.
+void launch_estimator(const void *recs, unsigned long long *nrec, int64_t max_records, const LcpOpts &o,
                       cudaStream_t st);
 gpr_status run_cell_lcp(const GridDev &g, const double *stats, const int32_t *slot, const int64_t *cells,
                         int64_t count, const LcpOpts &o, float *lcp, bool out_by_position, void *scratch,

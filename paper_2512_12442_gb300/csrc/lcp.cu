@@ -217,14 +217,18 @@ __device__ __forceinline__ void sov_pair(const float (&Ls)[28], const float (&cb
 // MINB: CTAs per SM the register allocation targets (2: 111 registers, 3: 80, both without
 // spills); the autotuner picks the variant and the grid.
 template <int MINB>
-__global__ void __launch_bounds__(256, MINB) k_sov(const CellRec *recs, const unsigned long long *nrec, int N,
-                                                  uint64_t seed, Lattice lat)
+__global__ void __launch_bounds__(256, MINB) k_sov(const CellRec *recs, const unsigned long long *nrec,
+                                                  unsigned long long *ticket, int N, uint64_t seed, Lattice lat)
 {
     int lane = threadIdx.x & 31;
-    int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     int64_t n = (int64_t)*nrec;
-    for (int64_t q = warp; q < n; q += nw) {
+    // records taken from a ticket counter, one per warp at a time: records whose Frechet test
+    // dropped an orthant cost half, so a fixed stride would leave some warps with more work
+    for (;;) {
+        unsigned long long t = 0;
+        if (lane == 0) t = atomicAdd(ticket, 1ull);
+        const int64_t q = (int64_t)__shfl_sync(0xffffffffu, t, 0);
+        if (q >= n) break;
         const CellRec &r = recs[q];
         float Ls[28], cb[8];
 #pragma unroll
@@ -357,11 +361,11 @@ thread_local RecordSink *tl_sink = nullptr;
 void set_record_sink(RecordSink *sink) { tl_sink = sink; }
 size_t record_bytes() { return sizeof(CellRec); }
 
-void launch_estimator(const void *recs, const unsigned long long *nrec, int64_t max_records, const LcpOpts &o,
+void launch_estimator(const void *recs, unsigned long long *nrec, int64_t max_records, const LcpOpts &o,
                       cudaStream_t st)
 {
-    // one warp per record, persistent over the device count; the register variant and the CTAs
-    // per SM are chosen by the autotuner
+    // one warp per record, persistent over the device count (nrec[0]; nrec[1] is the work ticket);
+    // the register variant and the CTAs per SM are chosen by the autotuner
     static const int per_sm[4] = {2, 8, 3, 12};
     auto run = [&](int c) -> gpr_status {
         int64_t blocks = (max_records + 7) / 8;
@@ -369,9 +373,14 @@ void launch_estimator(const void *recs, const unsigned long long *nrec, int64_t 
         if (blocks < 1) blocks = 1;
         if (o.est == GPR_EST_SOV_QMC) {
             static Lattice lat = make_lattice();
+            GPR_CUDA_TRY(cudaMemsetAsync(nrec + 1, 0, sizeof(unsigned long long), st));
             ProfScope _ps("sov", st);
-            if (c < 2) k_sov<2><<<(unsigned)blocks, 256, 0, st>>>((const CellRec *)recs, nrec, o.n_samples, o.seed, lat);
-            else k_sov<3><<<(unsigned)blocks, 256, 0, st>>>((const CellRec *)recs, nrec, o.n_samples, o.seed, lat);
+            if (c < 2)
+                k_sov<2><<<(unsigned)blocks, 256, 0, st>>>((const CellRec *)recs, nrec, nrec + 1, o.n_samples, o.seed,
+                                                           lat);
+            else
+                k_sov<3><<<(unsigned)blocks, 256, 0, st>>>((const CellRec *)recs, nrec, nrec + 1, o.n_samples, o.seed,
+                                                           lat);
         } else {
             ProfScope _ps("mc", st);
             k_mc<<<(unsigned)blocks, 256, 0, st>>>((const CellRec *)recs, nrec, o.n_samples, o.seed);
@@ -394,7 +403,7 @@ gpr_status run_cell_lcp(const GridDev &g, const double *stats, const int32_t *sl
     }
     if (scratch_bytes < cell_lcp_scratch_bytes(count)) return GPR_ERR_ARG;
     Carver cv{(char *)scratch};
-    unsigned long long *nrec = cv.take<unsigned long long>(1);
+    unsigned long long *nrec = cv.take<unsigned long long>(2);  // record count, estimator ticket
     CellRec *recs = cv.take<CellRec>((size_t)count);
     // a batch sink with room takes the records; its owner runs one estimator launch for all
     RecordSink *sink = tl_sink;
@@ -695,9 +704,9 @@ gpr_status run_cell_lcp_on_scratch(const GridDev &g, const double *stats, const 
 {
     if (count <= 0) return GPR_OK;
     if (count > max_records) return GPR_ERR_ARG;
-    unsigned long long *nrec = (unsigned long long *)scratch;
+    unsigned long long *nrec = (unsigned long long *)scratch;  // record count, estimator ticket
     CellRec *recs = (CellRec *)((char *)scratch + 256);
-    GPR_CUDA_TRY(cudaMemsetAsync(nrec, 0, sizeof(unsigned long long), st));
+    GPR_CUDA_TRY(cudaMemsetAsync(nrec, 0, 2 * sizeof(unsigned long long), st));
     static PairTable pt = make_pair_table();
     k_cell_prep<<<(unsigned)((count + 127) / 128), 128, 0, st>>>(g, stats, nullptr, cells, count, o.theta, o.tau,
                                                                  o.skip_eps, pt, lcp, by_pos, recs, nrec, nullptr,
@@ -708,7 +717,7 @@ gpr_status run_cell_lcp_on_scratch(const GridDev &g, const double *stats, const 
     if (blocks > (int64_t)num_sms() * 16) blocks = (int64_t)num_sms() * 16;
     if (o.est == GPR_EST_SOV_QMC) {
         static Lattice lat = make_lattice();
-        k_sov<2><<<(unsigned)blocks, 256, 0, st>>>(recs, nrec, o.n_samples, o.seed, lat);
+        k_sov<2><<<(unsigned)blocks, 256, 0, st>>>(recs, nrec, nrec + 1, o.n_samples, o.seed, lat);
     } else {
         k_mc<<<(unsigned)blocks, 256, 0, st>>>(recs, nrec, o.n_samples, o.seed);
     }
