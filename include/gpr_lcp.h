@@ -234,7 +234,9 @@ gpr_status gpr_lcp_adaptive_batched(gpr_model *const *models, const gpr_grid *gr
                                     const int32_t *max_depths, int32_t count, const gpr_lcp_options *opts,
                                     float *const *lcps, gpr_adaptive_stats *stats, void *stream);
 
-/* Frees the batch workers' pooled device workspaces (they are kept between calls). */
+/* Frees the library's pooled device scratch that is kept between calls: the batch workers'
+ * workspaces and record buffer, and the digit buffers of the tensor-core FP64-class products
+ * (those no call is using; up to a few GB).  Synchronises the device. */
 gpr_status gpr_batch_release(void);
 
 /*

@@ -216,5 +216,6 @@ extern "C" gpr_status gpr_batch_release(void)
     P.recs = nullptr;
     P.nrec = nullptr;
     P.rec_bytes = 0;
+    adig_free_idle();
     return GPR_OK;
 }

@@ -213,6 +213,8 @@ gpr_status launch_oz_w(const gpr_model *M, const GridDev &g, const float2 *Tu, c
 gpr_status launch_stats_ff(const gpr_model *M, const GridDev &g, const int64_t *pts, int64_t count, const int32_t *slot,
                            const float2 *W, double *out15, cudaStream_t st, bool out_by_point = false,
                            int64_t row_mod = 0);
+// Frees the digit-split GEMMs' pooled digit buffers that no call is using.
+void adig_free_idle();
 // FP64-class products of FP64 matrices by the same digit split (42-bit fixed-point digits per
 // row / column exponent): C = X L^-1 (X rows x m, ld ldx; C ld ldc), and C = A^T B for
 // A, B: K x nc (ld) as nsplit partials of (nc rounded up to 64)^2 whose sum is C.

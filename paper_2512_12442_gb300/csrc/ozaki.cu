@@ -921,6 +921,26 @@ gpr_status adig_acquire(size_t bytes, cudaStream_t st, AdigBuf **out)
     return GPR_OK;
 }
 
+// Frees the pooled digit buffers no call is using (after their last use has finished).
+void adig_free_idle()
+{
+    std::lock_guard<std::mutex> lock(g_adig_mu);
+    std::vector<AdigBuf *> keep;
+    for (AdigBuf *b : g_adig) {
+        if (b->busy) {
+            keep.push_back(b);
+            continue;
+        }
+        if (b->released) {
+            cudaEventSynchronize(b->released);
+            cudaEventDestroy(b->released);
+        }
+        cudaFree(b->p);
+        delete b;
+    }
+    g_adig.swap(keep);
+}
+
 void adig_release(AdigBuf *b, cudaStream_t st)
 {
     cudaEventRecord(b->released, st);

@@ -137,3 +137,16 @@ def test_backward_after_forward_reuses_cache(torch, g):
     dy1, dl1 = g.gpr_lcp_backward(M, g.make_grid(n), th, g.lcp_options(), dl_t)
     np.testing.assert_allclose(dy1, dy0, rtol=1e-10, atol=1e-12 * np.abs(dy0).max())
     np.testing.assert_allclose(dl1, dl0, rtol=1e-10, atol=1e-12 * np.abs(dl0).max())
+
+
+def test_scratch_release_between_calls(torch, g):
+    """gpr_batch_release frees the pooled scratch (batch workspaces, digit buffers of the FP64-class
+    products); the next call allocates it again and gives the same gradient."""
+    w = workloads.small(5, 30, 9, ell=(0.2, 0.25, 0.3))
+    n, th = 9, w.isovalues[0]
+    wts = np.random.default_rng(5).random((n - 1) ** 3)
+    dy0, dl0 = _gpu_grad(g, torch, w, n, th, wts)
+    g.gpr_batch_release()
+    dy1, dl1 = _gpu_grad(g, torch, w, n, th, wts)
+    np.testing.assert_allclose(dy1, dy0, rtol=1e-10, atol=1e-12 * np.abs(dy0).max())
+    np.testing.assert_allclose(dl1, dl0, rtol=1e-10, atol=1e-12 * np.abs(dl0).max())
