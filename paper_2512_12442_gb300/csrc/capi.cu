@@ -58,8 +58,6 @@ bool opts_valid(const gpr_lcp_options *o)
     return true;
 }
 
-static bool simt_precision(gpr_precision p) { return p == GPR_P_FP64 || p == GPR_P_FP32; }
-
 // FP64 stats of every grid point, in z-slabs whose W rows fit `w_budget` bytes.
 static gpr_status dense_stats64(gpr_model *M, const GridDev &g, const double *T64, double *W, size_t w_rows,
                                 double *out15, double *mean, double *var, double *cov13, cudaStream_t st)

@@ -265,7 +265,6 @@ extern "C" gpr_status gpr_model_create(const double *obs_xyz, const double *y, i
     M->hy.assign(y, y + m);
     int64_t mb = (m + NB - 1) / NB * NB, mp = M->mp;
     double *A = nullptr;
-    gpr_status rc = GPR_OK;
     auto fail = [&](gpr_status s) {
         if (A) cudaFree(A);
         gpr_model_destroy(M);
@@ -343,7 +342,6 @@ extern "C" gpr_status gpr_model_create(const double *obs_xyz, const double *y, i
         gpr_model_destroy(M);
         return (gpr_status)hs;
     }
-    (void)rc;
     *out = M;
     return GPR_OK;
 }

@@ -32,22 +32,22 @@ struct Cfg;
 // P = precision code (GPR_P_TF32 .. GPR_P_BF16X3)
 template <>
 struct Cfg<GPR_P_TF32> {
-    static constexpr int NA = 1, NB = 1, NPROD = 1, BKE = 32, ESZ = 4, N = 256;
+    static constexpr int NA = 1, NB = 1, NPROD = 1, BKE = 32, ESZ = 4;
     static constexpr bool BF = false;
 };
 template <>
 struct Cfg<GPR_P_TF32X3> {
-    static constexpr int NA = 2, NB = 2, NPROD = 3, BKE = 32, ESZ = 4, N = 256;
+    static constexpr int NA = 2, NB = 2, NPROD = 3, BKE = 32, ESZ = 4;
     static constexpr bool BF = false;
 };
 template <>
 struct Cfg<GPR_P_BF16> {
-    static constexpr int NA = 1, NB = 1, NPROD = 1, BKE = 64, ESZ = 2, N = 256;
+    static constexpr int NA = 1, NB = 1, NPROD = 1, BKE = 64, ESZ = 2;
     static constexpr bool BF = true;
 };
 template <>
 struct Cfg<GPR_P_BF16X3> {
-    static constexpr int NA = 3, NB = 3, NPROD = 6, BKE = 64, ESZ = 2, N = 128;
+    static constexpr int NA = 3, NB = 3, NPROD = 6, BKE = 64, ESZ = 2;
     static constexpr bool BF = true;
 };
 
