@@ -73,3 +73,23 @@ def test_product_package_does_not_import_the_oracle():
             if f.endswith((".py", ".cu", ".h", ".cuh")):
                 txt = open(os.path.join(dp, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt and "gpr_oracle" not in txt, f
+
+
+def test_tune_file_is_read_without_a_gpu(tmp_path):
+    """The autotuner's table file (GPR_TUNE_FILE, "kernel bucket choice" lines) is parsed on the
+    host: a fresh process sees the entries through gpr_autotune_table, and gpr_autotune_clear
+    empties the table (no GPU involved)."""
+    import subprocess
+    import sys
+    path = tmp_path / "tune.txt"
+    path.write_text("sov_shape 2097152 3\ntc_sumsq_tf32x3 32772 1\n")
+    code = ("import sys; sys.path.insert(0, %r)\n"
+            "import paper_2512_12442_gb300 as g\n"
+            "t = g.gpr_autotune_table(); print(sorted(t.items()))\n"
+            "g.gpr_autotune_clear(); print(len(g.gpr_autotune_table()))\n") % ROOT
+    env = dict(os.environ, GPR_TUNE_FILE=str(path))
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    out = r.stdout.strip().splitlines()
+    assert out[-2] == "[(('sov_shape', 2097152), 3), (('tc_sumsq_tf32x3', 32772), 1)]"
+    assert out[-1] == "0"
