@@ -46,7 +46,7 @@ typedef enum {
     GPR_ERR_CUDA = 3,        /* a CUDA runtime call failed */
     GPR_ERR_OOM = 4,         /* device allocation failed */
     GPR_ERR_TIMEOUT = 5,     /* a bounded device wait ran out */
-    GPR_ERR_UNSUPPORTED = 6  /* valid request this build does not serve */
+    GPR_ERR_UNSUPPORTED = 6  /* valid request this library does not serve */
 } gpr_status;
 
 typedef enum { GPR_K_SE = 0, GPR_K_MATERN52 = 1 } gpr_kernel;
@@ -81,7 +81,7 @@ typedef struct {
 /* Options of the LCP calls.  Defaults come from gpr_lcp_options_default(). */
 typedef struct {
     double alpha;          /* octree threshold (Algorithm 1), default 1e-3 (Sec. 6.3) */
-    double beta;           /* local-GP radius in length scales (Sec. 4.2), default 6; unused by this build */
+    double beta;           /* local-GP radius in length scales (Sec. 4.2), default 6; unused by this library */
     gpr_estimator est;     /* cell estimator, default SOV-QMC */
     int32_t n_samples;     /* samples per cell, default 1600 (Sec. 5.4) */
     uint64_t seed;         /* lattice shifts / Philox key */
