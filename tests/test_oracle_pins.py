@@ -384,10 +384,12 @@ def test_cell_adjoint_matches_finite_differences():
         assert an == pytest.approx(fd, rel=1e-5, abs=1e-9)
 
 
-def test_field_gradient_matches_finite_differences():
+@pytest.mark.parametrize("kernel", [workloads.SE, workloads.MATERN52])
+def test_field_gradient_matches_finite_differences(kernel):
     """loss = sum_c w_c LCP_c on a small field: dloss/dy_i and dloss/dlog l_d (analytic, chain rule
-    through Eq. 1) against central differences with h = 1e-3."""
-    w = workloads.small(5, 30, 9, ell=(0.2, 0.25, 0.3))
+    through Eq. 1, the kernel derivative through r for Matern-5/2) against central differences
+    with h = 1e-3."""
+    w = workloads.small(5, 30, 9, ell=(0.2, 0.25, 0.3), kernel=kernel)
     M = oracle.Model.from_workload(w)
     th = w.isovalues[0]
     wts = np.random.default_rng(5).random(512)
