@@ -93,3 +93,10 @@ def test_tune_file_is_read_without_a_gpu(tmp_path):
     out = r.stdout.strip().splitlines()
     assert out[-2] == "[(('sov_shape', 2097152), 3), (('tc_sumsq_tf32x3', 32772), 1)]"
     assert out[-1] == "0"
+
+
+def test_batched_binding_checks_list_lengths(lib):
+    """The batched call's per-field lists must have one entry per field (checked before any call)."""
+    import paper_2512_12442_gb300 as g
+    with pytest.raises(ValueError):
+        g.gpr_lcp_adaptive_batched([], [g.make_grid(9)], [0.0], [3], g.lcp_options(), [])
