@@ -67,6 +67,9 @@ def lib():
         L.or_octree_level.argtypes = [C.c_void_p, C.POINTER(_Grid), C.c_int, C.c_int, C.c_double,
                                       C.c_double, C.c_int, _i64p, C.c_int64, _i8p, _dp, _i8p]
         L.or_eval_g.argtypes = [C.c_void_p, _dp, C.c_int64, C.c_double, C.c_int, _dp, _dp]
+        L.or_node_min.restype = C.c_double
+        L.or_node_min.argtypes = [C.c_void_p, C.POINTER(_Grid), C.c_int, C.c_int, C.c_int64, C.c_double, C.c_int,
+                                  C.c_int, _dp, _dp, _dp]
         L.or_num_threads.restype = C.c_int
         L.or_cell_lcp_adj.restype = C.c_double
         L.or_cell_lcp_adj.argtypes = [C.c_int, _dp, _dp, C.c_double, C.c_int64, C.c_uint64, C.c_uint64, C.c_double,
@@ -254,6 +257,15 @@ class Model:
         loss = lib().or_lcp_grad_block(self._h, C.byref(g), float(theta), int(n_samples), C.c_uint64(seed), float(tau),
                                        float(skip_eps), np.ascontiguousarray(weights, np.float64), c0, c1, dy, dl)
         return loss, dy, dl
+
+    def node_min(self, n, D, l, node, theta, side, T=4):
+        """The node minimiser of Algorithm 1's bound (Sec. 5.1) for one node and one side:
+        (min g, the point where it was found, box lo, box hi), g = side*(theta-mu)/sigma."""
+        g = grid(n)
+        x = np.zeros(3); lo = np.zeros(3); hi = np.zeros(3)
+        v = lib().or_node_min(self._h, C.byref(g), int(D), int(l), int(node), float(theta), int(side), int(T),
+                              x, lo, hi)
+        return v, x, lo, hi
 
     def eval_g(self, x, theta, side):
         x = np.ascontiguousarray(x, np.float64).reshape(-1, 3)

@@ -656,7 +656,7 @@ static void node_geom(const or_grid *g, int D, int l, const int64_t ijk[3], int6
  * lowers g. */
 static double node_min_g(const or_model *M, const or_grid *g, const int64_t p0[3], const int64_t p1[3],
                          const double blo[3], const double bhi[3], double theta, int side, int T,
-                         double *kb, double *dk, double *v, double *P)
+                         double *kb, double *dk, double *v, double *P, double *xbest)
 {
     double grad[3];
     int small = 1;
@@ -668,7 +668,10 @@ static double node_min_g(const or_model *M, const or_grid *g, const int64_t p0[3
                 for (int64_t a = p0[0]; a <= p1[0]; ++a) {
                     double x[3] = {grid_x(g, 0, a), grid_x(g, 1, b), grid_x(g, 2, c)};
                     double val = eval_g(M, x, theta, side, grad, kb, dk, v, P);
-                    if (val < best) best = val;
+                    if (val < best) {
+                        best = val;
+                        if (xbest) for (int d = 0; d < 3; ++d) xbest[d] = x[d];
+                    }
                 }
         return best;
     }
@@ -697,6 +700,7 @@ static double node_min_g(const or_model *M, const or_grid *g, const int64_t p0[3
         double val = eval_g(M, xc, theta, side, grad, kb, dk, v, P);
         if (val < bestg) { bestg = val; for (int d = 0; d < 3; ++d) { bx[d] = xc[d]; bestgrad[d] = grad[d]; } }
     }
+    if (xbest) for (int d = 0; d < 3; ++d) xbest[d] = bx[d];
     return bestg;
 }
 
@@ -740,8 +744,8 @@ void or_octree_level(const or_model *M, const or_grid *g, int D, int l, double t
             else { do_lo = 0; do_hi = 1; }
             double dcount = (double)((p1[0] - p0[0] + 1) * (p1[1] - p0[1] + 1) * (p1[2] - p0[2] + 1));
             double lB_lo = -INFINITY, lB_hi = -INFINITY; /* ln B; B = 0 when the side is not used */
-            if (do_lo) lB_lo = log_norm_cdf(node_min_g(M, g, p0, p1, blo, bhi, theta, +1, T, kb, dk, v, P));
-            if (do_hi) lB_hi = log_norm_cdf(node_min_g(M, g, p0, p1, blo, bhi, theta, -1, T, kb, dk, v, P));
+            if (do_lo) lB_lo = log_norm_cdf(node_min_g(M, g, p0, p1, blo, bhi, theta, +1, T, kb, dk, v, P, NULL));
+            if (do_hi) lB_hi = log_norm_cdf(node_min_g(M, g, p0, p1, blo, bhi, theta, -1, T, kb, dk, v, P, NULL));
             double bnd;
             if (do_lo && do_hi) bnd = -expm1(dcount * lB_lo) - exp(dcount * lB_hi);
             else if (do_lo) bnd = -expm1(dcount * lB_lo);
@@ -753,6 +757,29 @@ void or_octree_level(const or_model *M, const or_grid *g, int D, int l, double t
         free(kb); free(dk); free(v); free(P);
     }
     free(flo); free(fhi);
+}
+
+/* The box minimiser of one node on its own (test hook for the minimiser pins): node
+ * (i | j<<21 | k<<42) at level l of a depth-D octree, one side; returns min g and writes the
+ * point where it was found to x_out, and the node box to box_lo / box_hi (all nullable). */
+double or_node_min(const or_model *M, const or_grid *g, int D, int l, int64_t node, double theta, int side, int T,
+                   double *x_out, double *box_lo, double *box_hi)
+{
+    int64_t m = M->m;
+    int64_t ijk[3] = {node & 0x1FFFFF, (node >> 21) & 0x1FFFFF, (node >> 42) & 0x1FFFFF};
+    int64_t p0[3], p1[3];
+    double blo[3], bhi[3], xb[3];
+    node_geom(g, D, l, ijk, p0, p1, blo, bhi);
+    double *kb = (double *)malloc(sizeof(double) * m), *dk = (double *)malloc(sizeof(double) * 3 * m);
+    double *v = (double *)malloc(sizeof(double) * m), *P = (double *)malloc(sizeof(double) * m);
+    double r = node_min_g(M, g, p0, p1, blo, bhi, theta, side, T, kb, dk, v, P, xb);
+    free(kb); free(dk); free(v); free(P);
+    for (int d = 0; d < 3; ++d) {
+        if (x_out) x_out[d] = xb[d];
+        if (box_lo) box_lo[d] = blo[d];
+        if (box_hi) box_hi[d] = bhi[d];
+    }
+    return r;
 }
 
 /* g at arbitrary points (test hook for the minimiser pins). */

@@ -321,24 +321,185 @@ def test_bound_dominates_true_regional_lcp():
     assert checked >= 6
 
 
+def _brute_box(M, th, side, lo, hi, n=41):
+    t = np.linspace(0, 1, n)
+    pts = np.stack(np.meshgrid(t, t, t, indexing="ij"), -1).reshape(-1, 3) * (hi - lo) + lo
+    g, _ = M.eval_g(pts, th, side)
+    return g.min(), pts[np.argmin(g)]
+
+
+def _polish(M, th, side, lo, hi, x0):
+    """L-BFGS-B (the paper's minimiser, Sec. 5.1) from x0 inside the box, via SciPy."""
+    from scipy.optimize import minimize
+    r = minimize(lambda z: M.eval_g(z, th, side)[0][0], x0, jac=lambda z: M.eval_g(z, th, side)[1][0],
+                 method="L-BFGS-B", bounds=list(zip(lo, hi)))
+    return float(r.fun)
+
+
 def test_minimiser_vs_brute_force_lattice():
-    """The box minimiser never reports a value below the true box minimum and is close to a dense
-    33^3 brute-force lattice minimum on a 5^3-point node (the paper's continuous min, Sec. 4.1)."""
+    """The continuous-box minimiser of the regional bound (Sec. 5.1; the paper minimises with
+    L-BFGS-B, the oracle with a 3x3x3 lattice start and T projected steps) on nodes of 5^3 and 9^3
+    grid points, both sides:
+      - the point it reports lies in the node box and g there equals the value it reports;
+      - the value is never above the lattice start and never below the box minimum (a 41^3
+        brute-force lattice, and L-BFGS-B polished from the reported point, both bound it);
+      - on nodes whose minimum is interior, the projected steps close at least half of the gap
+        between the lattice start and the box minimum.
+    A flipped step sign (u = +grad g * w) never accepts a step and fails the last check; an
+    unclamped step leaves the box; a step evaluated at one point but kept at another breaks the
+    value-at-point check."""
     w = workloads.small(8, 40, 17, ell=(0.3, 0.3, 0.3))
     M = oracle.Model.from_workload(w)
     th = w.isovalues[0]
-    lo = np.array([4, 8, 4]) / 16; hi = np.array([8, 12, 8]) / 16
-    t = np.linspace(0, 1, 33)
-    pts = np.stack(np.meshgrid(t, t, t, indexing="ij"), -1).reshape(-1, 3) * (hi - lo) + lo
-    gb, _ = M.eval_g(pts, th, 1)
-    D, l = 4, 2  # node width 4 cells, 5 points per axis -> continuous minimiser
-    node = np.array([1 | (2 << 21) | (1 << 42)], np.int64)
-    dec, bnd, side = M.octree_level(17, D, l, th, node, alpha=1e-300)
-    # recover ln B from the bound for the used side(s) only when one-sided
-    assert np.isfinite(bnd[0]) or dec[0] == 1
-    # direct: minimiser value is within the brute-force range
-    g_lat, _ = M.eval_g(np.array([lo + (hi - lo) * np.array(c) / 2 for c in np.ndindex(3, 3, 3)]), th, 1)
-    assert gb.min() <= g_lat.min() + 1e-12
+    n, D = 17, 4
+    improved, checked = 0, 0
+    for l, nodes in ((2, [(0, 0, 0), (2, 0, 0), (0, 1, 0), (1, 1, 0), (3, 2, 1), (2, 2, 1), (1, 0, 1)]),
+                     (1, [(0, 0, 0), (1, 1, 1), (0, 1, 0)])):
+        for (i, j, k) in nodes:
+            node = i | (j << 21) | (k << 42)
+            for side in (1, -1):
+                v, x, lo, hi = M.node_min(n, D, l, node, th, side)
+                assert np.all(hi - lo > 0) and (hi[0] - lo[0]) * 16 == pytest.approx(1 << (D - l))
+                assert np.all(x >= lo) and np.all(x <= hi)
+                gx, _ = M.eval_g(x, th, side)
+                assert gx[0] == pytest.approx(v, rel=1e-12, abs=1e-12)
+                lat = np.array([lo + (hi - lo) * np.array(c) / 2 for c in np.ndindex(3, 3, 3)])
+                g_lat = M.eval_g(lat, th, side)[0].min()
+                g_brute, x_brute = _brute_box(M, th, side, lo, hi)
+                g_true = min(g_brute, _polish(M, th, side, lo, hi, x), _polish(M, th, side, lo, hi, x_brute))
+                assert v <= g_lat + 1e-12
+                assert v >= g_true - 1e-9
+                checked += 1
+                if g_lat - g_true > 1e-3 and v < g_lat - 1e-9:
+                    improved += 1
+    assert checked == 20
+    assert improved >= 10
+    # interior minima: the steps must do real work here (values measured with the 41^3 lattice)
+    for l, (i, j, k), side in ((2, (2, 0, 0), -1), (2, (0, 1, 0), -1), (2, (3, 2, 1), 1), (2, (2, 2, 2), 1),
+                             (1, (0, 0, 0), -1), (1, (1, 1, 1), 1)):
+        node = i | (j << 21) | (k << 42)
+        v, x, lo, hi = M.node_min(n, D, l, node, th, side)
+        g_lat = M.eval_g(np.array([lo + (hi - lo) * np.array(c) / 2 for c in np.ndindex(3, 3, 3)]), th, side)[0].min()
+        g_brute, x_brute = _brute_box(M, th, side, lo, hi)
+        assert np.all((x_brute > lo) & (x_brute < hi))  # the brute-force minimum is interior
+        assert (g_lat - v) >= 0.5 * (g_lat - g_brute)
+
+
+def test_minimiser_small_nodes_take_the_exact_grid_minimum():
+    """Nodes with at most 3 grid points per axis: the minimum over their grid points (brute force
+    over the 27 points, Sec. 5.1's min over D), and the reported point is one of them."""
+    w = workloads.small(8, 40, 17, ell=(0.3, 0.3, 0.3))
+    M = oracle.Model.from_workload(w)
+    th = w.isovalues[0]
+    for (i, j, k) in ((0, 0, 0), (3, 5, 2), (7, 7, 7), (4, 1, 6)):
+        node = i | (j << 21) | (k << 42)
+        for side in (1, -1):
+            v, x, lo, hi = M.node_min(17, 4, 3, node, th, side)
+            pts = np.array([lo + (hi - lo) * np.array(c) / 2 for c in np.ndindex(3, 3, 3)])
+            g = M.eval_g(pts, th, side)[0]
+            assert v == g.min()
+            assert np.min(np.abs(pts - x).sum(1)) == 0.0
+
+
+def _np_gp(X, y, ell, sn2):
+    """Plain GPR from its definition with a dense inverse (NumPy), independent of the oracle."""
+    ell = np.asarray(ell, float)
+
+    def k(A, B):
+        d = (A[:, None, :] - B[None, :, :]) / ell
+        return np.exp(-0.5 * (d ** 2).sum(-1))
+    Q = np.linalg.inv(k(X, X) + sn2 * np.eye(len(y)))
+
+    def post(P):
+        ks = k(P, X)
+        return ks @ Q @ y, 1.0 - np.einsum("ij,jk,ik->i", ks, Q, ks)
+    K = k(X, X)
+    mu_M = K @ Q @ y                      # Eq. 1 with the observations as inducing points
+    var_M = np.diag(K - K @ Q @ K)
+    return post, mu_M, var_M
+
+
+def _expected_level(X, y, ell, sn2, th, alpha, n, D, l, nodes):
+    """Algorithm 1 (Sec. 5.3) for one level, written from the algorithm: p1/p2 from the latent
+    posterior at the observations in the closed node box; both > alpha -> subdivide directly;
+    p2 <= alpha -> only B_l = min P(Y < theta); p1 <= alpha -> only B_u = min P(Y > theta); no
+    observation -> both; bound 1 - B_l^d - B_u^d (Eq. upper_bound, Sec. 5.1) over the node's d grid
+    points (nodes of <= 3 points per axis: the exact minimum over them)."""
+    from scipy.special import log_ndtr, ndtr
+    post, mu_M, var_M = _np_gp(X, y, ell, sn2)
+    p_lo = ndtr((th - mu_M) / np.sqrt(var_M))
+    p_hi = ndtr((mu_M - th) / np.sqrt(var_M))
+    s = 1 << (D - l)
+    gx = np.arange(n) / (n - 1)
+    out = []
+    for nd in nodes:
+        ijk = [(nd >> (21 * a)) & 0x1FFFFF for a in range(3)]
+        p0 = [c * s for c in ijk]
+        p1 = [min((c + 1) * s, n - 1) for c in ijk]
+        lo = np.array([gx[a] for a in p0]); hi = np.array([gx[a] for a in p1])
+        inside = np.all((X >= lo) & (X <= hi), 1)
+        P = np.array([[gx[a], gx[b], gx[c]] for c in range(p0[2], p1[2] + 1)
+                      for b in range(p0[1], p1[1] + 1) for a in range(p0[0], p1[0] + 1)])
+        mu, var = post(P)
+        sd = np.sqrt(var)
+        d = len(P)
+        has_lo = bool(np.any(p_lo[inside] > alpha)); has_hi = bool(np.any(p_hi[inside] > alpha))
+        if inside.any() and has_lo and has_hi:
+            out.append((1, None, 0)); continue
+        use_lo = (not inside.any()) or not has_hi
+        use_hi = (not inside.any()) or not has_lo
+        Bl = np.exp(d * log_ndtr(((th - mu) / sd).min())) if use_lo else 0.0
+        Bu = np.exp(d * log_ndtr(((mu - th) / sd).min())) if use_hi else 0.0
+        bound = 1.0 - Bl - Bu
+        side = 0 if (use_lo and use_hi) else (1 if use_lo else 2)
+        out.append((2 if bound > alpha else 0, bound, side))
+    return out
+
+
+def test_ptest_side_selection_and_one_sided_bounds():
+    """Algorithm 1's p-test with hand-placed observations (theta = 0, alpha = 1e-3, nodes of 3^3
+    grid points): node 0 holds an observation far above and one far below theta (direct
+    subdivide); node 1 only observations below (p2 <= alpha: lower side only); node 2 only above
+    (upper side only); node 3 a dense block of observations below theta (lower side, bound far
+    below alpha: dropped); node 6 and 7 share an observation on their common face (closed boxes);
+    nodes 4, 5 are empty (both sides).  A swapped lower/upper flag gives node 3 the upper side and
+    a bound of 1, and fails."""
+    obs = [((0.2, 0.25, 0.25), 2.0), ((0.3, 0.25, 0.3), -2.0), ((0.75, 0.25, 0.25), -3.0),
+           ((0.8, 0.3, 0.2), -2.5), ((0.25, 0.75, 0.25), 3.0), ((0.2, 0.8, 0.3), 2.5), ((0.5, 0.75, 0.75), 3.0)]
+    obs += [((a, b, c), -3.0) for a in (0.55, 0.75, 0.95) for b in (0.55, 0.75, 0.95) for c in (0.05, 0.25, 0.45)]
+    X = np.array([o[0] for o in obs]); y = np.array([o[1] for o in obs])
+    ell, sn2, th, alpha = (0.2, 0.2, 0.2), 1e-4, 0.0, 1e-3
+    M = oracle.Model(X, y, oracle.SE, ell, 1.0, sn2)
+    nodes = np.array([i | (j << 21) | (k << 42) for k in range(2) for j in range(2) for i in range(2)], np.int64)
+    dec, bnd, side = M.octree_level(5, 2, 1, th, nodes, alpha=alpha)
+    exp = _expected_level(X, y, ell, sn2, th, alpha, 5, 2, 1, nodes)
+    for q, (e_dec, e_bnd, e_side) in enumerate(exp):
+        assert dec[q] == e_dec, q
+        assert side[q] == e_side, q
+        if e_bnd is None:
+            assert np.isnan(bnd[q])
+        else:
+            assert bnd[q] == pytest.approx(e_bnd, rel=1e-9, abs=1e-12), q
+    assert [int(v) for v in dec[:4]] == [1, 2, 2, 0]
+    assert [int(v) for v in side] == [0, 1, 2, 1, 0, 0, 2, 2]
+    assert bnd[3] < 1e-10
+
+
+def test_two_sided_bound_when_the_node_is_empty():
+    """An empty node takes both sides, 1 - B_l^d - B_u^d (Eq. upper_bound): with the mean near theta
+    over single-cell nodes (d = 8) both terms are ~0.5^8, so dropping either term or using the
+    one-sided form moves the bound by ~4e-3."""
+    X = np.array([[0.1, 0.1, 0.1], [0.15, 0.12, 0.08]]); y = np.array([0.01, -0.02])
+    ell, sn2, th, alpha = (0.5, 0.5, 0.5), 1e-4, 0.0, 1e-3
+    M = oracle.Model(X, y, oracle.SE, ell, 1.0, sn2)
+    nodes = np.array([i | (j << 21) | (k << 42) for k in range(2) for j in range(2) for i in range(2)], np.int64)
+    dec, bnd, side = M.octree_level(3, 1, 1, th, nodes, alpha=alpha)
+    exp = _expected_level(X, y, ell, sn2, th, alpha, 3, 1, 1, nodes)
+    for q in range(1, 8):
+        e_dec, e_bnd, e_side = exp[q]
+        assert side[q] == 0 and e_side == 0
+        assert bnd[q] == pytest.approx(e_bnd, rel=1e-12, abs=1e-13)
+        assert 1e-3 < 1.0 - bnd[q] < 0.1  # both terms matter
 
 
 def test_octree_alpha_zero_keeps_nonzero_cells_and_adaptive_equals_dense():
