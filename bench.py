@@ -5,7 +5,7 @@ Workload (one step): build the GP model from m=500 observations (anisotropic SE,
 lengths (0.15, 0.2, 0.25), noise 1e-4) and compute the level-crossing probability
 field of a 128^3 grid (127^3 cells, 1600-sample SOV-QMC estimator) at the 25th,
 50th and 75th percentile of y.  Metric: target grid points per second
-(3 x 128^3 points per step), as the paper reports seconds per field (Sec. 6.1).
+(3 x 128^3 points per step), as the paper reports seconds per field (Sec. 6.2, Sec. 7.1).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--mode adaptive|dense]
   python bench.py --impl reference ...   # the FP64 CPU oracle on host cores

@@ -26,7 +26,7 @@
  *     (1,-1,-1) (1,-1,0) (1,-1,1) (1,0,-1) (1,0,0) (1,0,1) (1,1,-1) (1,1,0)
  *     (1,1,1) (0,1,-1) (0,1,0) (0,1,1) (0,0,1); NaN where the neighbour is off
  *     the grid.  These 15 numbers per point determine every cell's 8x8 corner
- *     covariance (Sec. 3).
+ *     covariance (Sec. 4).
  */
 #ifndef GPR_LCP_H
 #define GPR_LCP_H
@@ -80,10 +80,10 @@ typedef struct {
 
 /* Options of the LCP calls.  Defaults come from gpr_lcp_options_default(). */
 typedef struct {
-    double alpha;          /* octree threshold (Algorithm 1), default 1e-3 (Sec. 6.3) */
-    double beta;           /* local-GP radius in length scales (Sec. 4.2), default 6; unused by this library */
+    double alpha;          /* octree threshold (Algorithm 1), default 1e-3 (Sec. 7.3) */
+    double beta;           /* local-GP radius in length scales (Sec. 5.2), default 6; unused by this library */
     gpr_estimator est;     /* cell estimator, default SOV-QMC */
-    int32_t n_samples;     /* samples per cell, default 1600 (Sec. 5.4) */
+    int32_t n_samples;     /* samples per cell, default 1600 (Sec. 6.4) */
     uint64_t seed;         /* lattice shifts / Philox key */
     double jitter;         /* tau: Sigma_8 += tau * max diag * I, default 1e-4 */
     double skip_eps;       /* Boole pre-skip threshold, default 1e-9 */
@@ -162,7 +162,7 @@ gpr_status gpr_stats_points(gpr_model *model, const gpr_grid *grid, const int64_
                             double *stats, void *stream);
 
 /*
- * gpr_cell_lcp_from_stats -- cell LCP (Sec. 3): LCP = 1 - P(all 8 corners <
+ * gpr_cell_lcp_from_stats -- cell LCP (Sec. 4): LCP = 1 - P(all 8 corners <
  * theta) - P(all 8 corners > theta) for the listed cells, from FP64 stats15 of
  * a full grid (device, n x 15 double).  Sigma_8 gets jitter*max(diag) on its
  * diagonal; if sum_c P(Y_c > theta) or sum_c P(Y_c < theta) is below skip_eps
@@ -182,7 +182,7 @@ gpr_status gpr_cell_lcp_from_stats(const gpr_grid *grid, const double *stats15, 
                                    float *lcp, void *stream);
 
 /*
- * gpr_lcp_dense -- the dense baseline LCP field (Sec. 3, Sec. 5.4): every cell's
+ * gpr_lcp_dense -- the dense baseline LCP field (Sec. 4, Sec. 6.4): every cell's
  * LCP.  A pre-pass in opts->prec computes mean/variance at all points and drops
  * cells whose Boole bound, widened by a margin that covers that precision's
  * error, is below skip_eps; the remaining cells' corners are reconstructed in
@@ -193,7 +193,7 @@ gpr_status gpr_lcp_dense(gpr_model *model, const gpr_grid *grid, double isovalue
                          float *lcp, gpr_adaptive_stats *stats, void *stream);
 
 /*
- * gpr_lcp_adaptive -- Algorithm 1 (Sec. 4.3) then leaf reconstruction: the
+ * gpr_lcp_adaptive -- Algorithm 1 (Sec. 5.3) then leaf reconstruction: the
  * octree over the cell grid (root = cells [0, 2^D)^3) is refined level by level
  * on the device.  A node is subdivided when the observations inside it have
  * p1 > alpha and p2 > alpha, or when the regional upper bound 1 - B_l^d - B_u^d
@@ -255,7 +255,8 @@ gpr_status gpr_batch_release(void);
  *     before any stream capture on the device.
  *   - All calls share the array and it keeps the last call's contents; calls that
  *     overlap on the GPU race on it, so order them (one stream, or events).
- *   - Cell indices off the grid are skipped (their output is left unchanged).
+ *   - Cell indices off the grid are skipped (their output is left unchanged) and
+ *     reported as GPR_ERR_ARG by the next gpr_sync(), as for gpr_cell_lcp_from_stats.
  */
 #define GPR_NOALLOC_MAX_CELLS 16384
 gpr_status gpr_cell_lcp_from_stats_noalloc(const gpr_grid *grid, const double *stats15, double isovalue,
@@ -280,6 +281,22 @@ gpr_status gpr_cell_lcp_from_stats_noalloc(const gpr_grid *grid, const double *s
 gpr_status gpr_lcp_backward(gpr_model *model, const gpr_grid *grid, double isovalue, const gpr_lcp_options *opts,
                             const float *dL_dlcp, double *dL_dy, double *dL_dloglen, void *stream);
 
+/*
+ * gpr_lcp_backward_adaptive -- as gpr_lcp_backward, for the adaptive field of
+ * gpr_lcp_adaptive (same model, grid, isovalue, max_depth and opts): Algorithm 1
+ * (Sec. 5.3) is run again on the device to find the leaf cells S, and cells outside
+ * S (whose adaptive LCP is the constant 0) contribute 0 whatever their weight.
+ * The set S itself is piecewise constant in y and the length scales, so this is
+ * the gradient of the adaptive field wherever it is differentiable.
+ *   max_depth  D as for gpr_lcp_adaptive
+ *   other arguments, errors and synchronisation as gpr_lcp_backward; the call
+ *   allocates one byte per cell for S (stream-ordered) and frees it before it
+ *   returns.
+ */
+gpr_status gpr_lcp_backward_adaptive(gpr_model *model, const gpr_grid *grid, double isovalue, int32_t max_depth,
+                                     const gpr_lcp_options *opts, const float *dL_dlcp, double *dL_dy,
+                                     double *dL_dloglen, void *stream);
+
 /* ---- Autotuner (no counterpart in the paper).  Launches with interchangeable shapes (the
  * tensor-core pre-pass tile width per precision, the estimator's CTAs per SM) are timed on
  * first use per (kernel, size bucket) and the fastest is kept for the process; the choice never
@@ -291,12 +308,13 @@ int64_t gpr_autotune_table(char *buf, int64_t len);
 /* Forgets every tuned choice. */
 void gpr_autotune_clear(void);
 
-/* Waits for `stream` and returns the first device-side error recorded by any
- * model since the last call (GPR_OK if none). */
+/* Waits for `stream` and returns the first device-side error recorded on the
+ * current device since the last call (GPR_OK if none); the status word is one
+ * per device, held by the library (no allocation). */
 gpr_status gpr_sync(void *stream);
 
 /* ---- Tracing (no counterpart in the paper; the paper reports per-phase wall time,
- * Sec. 5.2).  When enabled, the library records CUDA events on the launching stream
+ * Sec. 6.2).  When enabled, the library records CUDA events on the launching stream
  * around its main kernels, grouped by name ("w64", "meanvar32", "stats_from_w64",
  * "cell_prep", "sov", "mc", "classify", ...). */
 void gpr_profile_enable(int on);

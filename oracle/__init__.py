@@ -3,7 +3,7 @@
 TEST INFRASTRUCTURE ONLY: imported by tests/, __graft_entry__.smoke() and the
 CPU-baseline leg of bench.py, never by the product package.  It shares no code
 with the CUDA path.  Each function cites the passage of the paper it follows:
-Eq. (1) (posterior), Sec. 3 (cell LCP, MC estimator), Sec. 4.1 (Slepian bound,
+Eq. (1) (posterior), Sec. 4 (cell LCP, MC estimator), Sec. 5.1 (Slepian bound,
 Eq. upper_bound), Algorithm 1 (octree adaptive query).
 
 Parity pins live in tests/test_oracle_pins.py.  Functions without a pin:
@@ -181,7 +181,7 @@ class Model:
 
     def lcp_block(self, n, theta, c0=(0, 0, 0), c1=None, est=EST_SOV, n_samples=1600, seed=0,
                   tau=1e-4, skip_eps=1e-9, lo=(0, 0, 0), hi=(1, 1, 1)):
-        """Cell LCP (Sec. 3) for cells with min corner in [c0, c1), x-fastest."""
+        """Cell LCP (Sec. 4) for cells with min corner in [c0, c1), x-fastest."""
         g = grid(n, lo, hi)
         if c1 is None:
             c1 = tuple(int(v) - 1 for v in g.n)
@@ -193,7 +193,7 @@ class Model:
         return out
 
     def lcp_dense(self, n, theta, slab=8, **kw):
-        """Dense baseline LCP field (Sec. 3 / Sec. 5.4), computed in z-slabs."""
+        """Dense baseline LCP field (Sec. 4 / Sec. 6.4), computed in z-slabs."""
         nc = n - 1
         out = np.zeros(nc ** 3)
         for z0 in range(0, nc, slab):
@@ -235,7 +235,7 @@ class Model:
         return leaves, levels
 
     def lcp_adaptive(self, n, D, theta, alpha=1e-3, T=4, **kw):
-        """Adaptive LCP field: the dense cell LCP on the leaves S of Algorithm 1, 0 elsewhere (Sec. 4.3)."""
+        """Adaptive LCP field: the dense cell LCP on the leaves S of Algorithm 1, 0 elsewhere (Sec. 5.3)."""
         leaves, levels = self.octree(n, D, theta, alpha, T)
         nc = n - 1
         field = np.zeros(nc ** 3)
@@ -286,7 +286,7 @@ def cell_lcp_adj(mu, S, theta, wbar=1.0, n_samples=1600, seed=0, cell=0, tau=1e-
 
 
 def cell_lcp(mu, S, theta, est=EST_SOV, n_samples=1600, seed=0, cell=0, tau=1e-4, skip_eps=1e-9):
-    """LCP of one cell (or any d <= 16 corner variables) from (mu, Sigma) (Sec. 3)."""
+    """LCP of one cell (or any d <= 16 corner variables) from (mu, Sigma) (Sec. 4)."""
     mu = np.ascontiguousarray(mu, np.float64)
     S = np.ascontiguousarray(S, np.float64)
     d = mu.shape[0]

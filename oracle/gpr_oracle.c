@@ -6,7 +6,7 @@
  * It shares no code, header, table or constant with the CUDA library.
  *
  * Plain, slow, obviously-correct definitions, in the paper's order:
- *   - kernel k(x1,x2): RBF sigma^2 exp(-|x1-x2|^2/(2 l^2)) (Sec. 3, Sec. 4.2);
+ *   - kernel k(x1,x2): RBF sigma^2 exp(-|x1-x2|^2/(2 l^2)) (Sec. 3, Sec. 5.2);
  *     anisotropic lengths divide each axis; Matern-5/2 is the textbook
  *     (1+sqrt5 r+5r^2/3)exp(-sqrt5 r) (Rasmussen & Williams eq. 4.17).
  *   - posterior, Eq. (1): for plain GPR the stored inducing distribution is the
@@ -14,13 +14,13 @@
  *     mu(x) = k_x^T Kt^-1 y, Sigma(a,b) = k(a,b) - k_a^T Kt^-1 k_b,
  *     Kt = K(X,X) + sn2 I.  Both forms are implemented (or_posterior,
  *     or_posterior_sgpr) so a test can check the reduction.
- *   - cell LCP (Sec. 3): 1 - P(all 8 corners < theta) - P(all 8 > theta),
+ *   - cell LCP (Sec. 4): 1 - P(all 8 corners < theta) - P(all 8 > theta),
  *     estimated either by the Genz sequential-conditioning (SOV) rule over a
  *     shifted rank-1 lattice or by Monte Carlo (the paper's estimator, 1600
- *     samples, Sec. 5.4) with Philox-4x32-10 + Box-Muller normals.
- *   - regional bound, Eq. (upper_bound) with Slepian's inequality (Sec. 4.1):
+ *     samples, Sec. 6.4) with Philox-4x32-10 + Box-Muller normals.
+ *   - regional bound, Eq. (upper_bound) with Slepian's inequality (Sec. 5.1):
  *     1 - B_l^d - B_u^d, B = min over the node of Phi(+-(theta-mu)/sigma).
- *   - octree adaptive query, Algorithm 1 (Sec. 4.3), one level per call.
+ *   - octree adaptive query, Algorithm 1 (Sec. 5.3), one level per call.
  *
  * Readings where the paper is silent are fixed by the caller-visible options
  * (jitter tau, skip epsilon, minimiser steps T) and documented at each site.
@@ -148,7 +148,7 @@ void or_model_destroy(or_model *M)
 }
 
 /* Builds Kt = K(X,X) + sn2 I, its Cholesky factor, L^-1, L^-1 y, Kt^-1 y and the
- * latent posterior at the observations (Sec. 4.3's p1/p2 test needs it).  With
+ * latent posterior at the observations (Sec. 5.3's p1/p2 test needs it).  With
  * the observations as inducing set, mu_M = K Kt^-1 y = y - sn2 Kt^-1 y and
  * A_M = K - K Kt^-1 K = sn2 I - sn2^2 Kt^-1 (because K = Kt - sn2 I).
  * Variance floor: 1e-12 sf2 (reading; the paper is silent).
@@ -416,7 +416,7 @@ static void chol_floor(const double *S, int d, double floor_, double *L)
 #define EST_MC 1
 
 /* Cell level-crossing probability for d corner variables (d = 8 for a cell):
- * LCP = 1 - P(all < theta) - P(all > theta)  (Sec. 3).
+ * LCP = 1 - P(all < theta) - P(all > theta)  (Sec. 4).
  * Readings (paper silent): Sigma += tau * max diag * I; pivot floor
  * 1e-3 * tau * max diag; if sum_c P(Y_c > theta) or sum_c P(Y_c < theta) is below
  * skip_eps, Boole's inequality bounds the LCP by it and the result is 0; a
@@ -553,7 +553,7 @@ void or_stats15_block(const or_model *M, const or_grid *g, const int64_t *i0, co
 
 /* LCP of the cells whose min-corner index lies in the box [c0, c1), written
  * x-fastest inside the box.  The 8x8 corner covariance of each cell is formed
- * directly as K_88 - V_8 V_8^T from the corners' whitened rows (Sec. 3, the
+ * directly as K_88 - V_8 V_8^T from the corners' whitened rows (Sec. 4, the
  * baseline dense method).  Corner c = bx + 2 by + 4 bz.  The cell index used
  * to key the estimator is the linear index of the cell in the whole grid. */
 void or_lcp_block(const or_model *M, const or_grid *g, double theta, int est, int64_t N, uint64_t seed,
@@ -603,7 +603,7 @@ void or_lcp_block(const or_model *M, const or_grid *g, double theta, int est, in
 /* ---------------------------------------------------- regional bound, octree */
 
 /* g(x) = side * (theta - mu(x)) / sigma(x) and its gradient; side = +1 gives
- * F = Phi(g) = P(Y < theta), side = -1 gives 1 - F = P(Y > theta) (Sec. 4.1). */
+ * F = Phi(g) = P(Y < theta), side = -1 gives 1 - F = P(Y > theta) (Sec. 5.1). */
 static double eval_g(const or_model *M, const double *x, double theta, int side, double grad[3],
                      double *kb, double *dk, double *v, double *P)
 {

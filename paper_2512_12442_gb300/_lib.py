@@ -52,6 +52,9 @@ SIGNATURES = {
     "gpr_batch_release": (C.c_int, []),
     "gpr_lcp_backward": (C.c_int, [C.c_void_p, C.POINTER(GridC), C.c_double, C.POINTER(LcpOptionsC), C.c_void_p,
                                    C.c_void_p, C.c_void_p, C.c_void_p]),
+    "gpr_lcp_backward_adaptive": (C.c_int, [C.c_void_p, C.POINTER(GridC), C.c_double, C.c_int32,
+                                            C.POINTER(LcpOptionsC), C.c_void_p, C.c_void_p, C.c_void_p,
+                                            C.c_void_p]),
     "gpr_sync": (C.c_int, [C.c_void_p]),
     "gpr_profile_enable": (None, [C.c_int]),
     "gpr_profile_reset": (None, []),

@@ -189,6 +189,17 @@ def gpr_lcp_backward(model: Model, grid: GridC, isovalue, opts: LcpOptionsC, dL_
     return dy, dl
 
 
+def gpr_lcp_backward_adaptive(model: Model, grid: GridC, isovalue, max_depth, opts: LcpOptionsC, dL_dlcp,
+                              stream=None):
+    """Adjoint of sum_c dL_dlcp[c] LCP_c for the adaptive field: (dL/dy, dL/dlog l) as numpy float64."""
+    dy = np.zeros(model.m); dl = np.zeros(3)
+    rc = load().gpr_lcp_backward_adaptive(model.handle, C.byref(grid), float(isovalue), int(max_depth),
+                                          C.byref(opts), _ptr(dL_dlcp), dy.ctypes.data, dl.ctypes.data,
+                                          _stream(stream))
+    _check(rc, "gpr_lcp_backward_adaptive")
+    return dy, dl
+
+
 def gpr_sync(stream=None):
     _check(load().gpr_sync(_stream(stream)), "gpr_sync")
 

@@ -1,10 +1,8 @@
 """torch.autograd.Function over the C ABI: the LCP field as a differentiable function of the
 observation values y and the log length scales (forward: gpr_model_create + gpr_lcp_dense or
-gpr_lcp_adaptive; backward: gpr_lcp_backward).  Marshalling only: both passes run in
+gpr_lcp_adaptive; backward: gpr_lcp_backward or gpr_lcp_backward_adaptive).  Marshalling only: both passes run in
 libgprlcp.so."""
 from __future__ import annotations
-
-import math
 
 import numpy as np
 import torch
@@ -28,20 +26,18 @@ class LCPFunction(torch.autograd.Function):
         else:
             api.gpr_lcp_adaptive(model, grid, isovalue, adaptive_depth, opts, out)
         ctx.model, ctx.grid, ctx.theta, ctx.opts = model, grid, float(isovalue), opts
-        ctx.adaptive = adaptive_depth is not None
+        ctx.depth = adaptive_depth
         ctx.y_meta = (y.device, y.dtype)
         ctx.l_meta = (log_len.device, log_len.dtype)
-        ctx.save_for_backward(out)
         return out
 
     @staticmethod
     def backward(ctx, grad_out):
-        (out,) = ctx.saved_tensors
         g = grad_out.detach().to(device="cuda", dtype=torch.float32).contiguous()
-        if ctx.adaptive:
-            # cells outside S are constant (0) in the adaptive field
-            g = torch.where(out != 0, g, torch.zeros_like(g))
-        dy, dl = api.gpr_lcp_backward(ctx.model, ctx.grid, ctx.theta, ctx.opts, g)
+        if ctx.depth is None:
+            dy, dl = api.gpr_lcp_backward(ctx.model, ctx.grid, ctx.theta, ctx.opts, g)
+        else:
+            dy, dl = api.gpr_lcp_backward_adaptive(ctx.model, ctx.grid, ctx.theta, ctx.depth, ctx.opts, g)
         gy = torch.from_numpy(dy).to(device=ctx.y_meta[0], dtype=ctx.y_meta[1])
         gl = torch.from_numpy(dl).to(device=ctx.l_meta[0], dtype=ctx.l_meta[1])
         return gy, gl, None, None, None, None, None, None, None, None

@@ -745,10 +745,11 @@ __global__ void k_dy(const double *Linv, int64_t mb, const double *t, int64_t m,
     dy[i] = s;
 }
 
-__global__ void k_mask_keep(uint8_t *keep, const float *dl, int64_t nc)
+// Cells without weight, or (adaptive field) outside the leaf set S, have a constant LCP.
+__global__ void k_mask_keep(uint8_t *keep, const float *dl, const uint8_t *leaf, int64_t nc)
 {
     int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (c < nc && dl[c] == 0.0f) keep[c] = 0;
+    if (c < nc && (dl[c] == 0.0f || (leaf && !leaf[c]))) keep[c] = 0;
 }
 
 __global__ void k_ff_to_double(const float2 *ff, int64_t n, double *out)
@@ -759,14 +760,10 @@ __global__ void k_ff_to_double(const float2 *ff, int64_t n, double *out)
 
 }  // namespace
 
-extern "C" gpr_status gpr_lcp_backward(gpr_model *M, const gpr_grid *grid, double isovalue,
-                                       const gpr_lcp_options *opts, const float *dL_dlcp, double *dL_dy,
-                                       double *dL_dloglen, void *stream)
+static gpr_status lcp_backward(gpr_model *M, const gpr_grid *grid, double isovalue, const gpr_lcp_options *opts,
+                               const float *dL_dlcp, const uint8_t *leaf, double *dL_dy, double *dL_dloglen,
+                               cudaStream_t st)
 {
-    if (!M || !grid_valid(grid) || !opts_valid(opts) || !dL_dlcp || !dL_dy || !dL_dloglen || !isfinite(isovalue))
-        return GPR_ERR_ARG;
-    if (opts->est != GPR_EST_SOV_QMC) return GPR_ERR_UNSUPPORTED;  // the indicator MC has no useful gradient
-    cudaStream_t st = (cudaStream_t)stream;
     GridDev g = make_grid(grid);
     int64_t n = g.npts(), nc = g.ncells(), m = M->m, mp = M->mp, mb = (m + 31) / 32 * 32;
     size_t te = table_elems(M, g);
@@ -815,7 +812,7 @@ extern "C" gpr_status gpr_lcp_backward(gpr_model *M, const gpr_grid *grid, doubl
         if (opts->prec == GPR_P_TF32 || opts->prec == GPR_P_BF16) mv = M->kp.sf2;
         launch_classify_cells(g, mean, var, isovalue, opts->skip_eps, opts->jitter, mv, mm, keep, st);
     }
-    k_mask_keep<<<(unsigned)((nc + 255) / 256), 256, 0, st>>>(keep, dL_dlcp, nc);
+    k_mask_keep<<<(unsigned)((nc + 255) / 256), 256, 0, st>>>(keep, dL_dlcp, leaf, nc);
     note_launch();
     GPR_CUDA_TRY(cudaMemsetAsync(pflag, 0, (size_t)n, st));
     launch_mark_corners(g, keep, pflag, st);
@@ -978,4 +975,38 @@ extern "C" gpr_status gpr_lcp_backward(gpr_model *M, const gpr_grid *grid, doubl
     GPR_CUDA_TRY(cudaStreamSynchronize(st));
     memcpy(dL_dloglen, h_out, sizeof h_out);
     return GPR_OK;
+}
+
+extern "C" gpr_status gpr_lcp_backward(gpr_model *M, const gpr_grid *grid, double isovalue,
+                                       const gpr_lcp_options *opts, const float *dL_dlcp, double *dL_dy,
+                                       double *dL_dloglen, void *stream)
+{
+    if (!M || !grid_valid(grid) || !opts_valid(opts) || !dL_dlcp || !dL_dy || !dL_dloglen || !isfinite(isovalue))
+        return GPR_ERR_ARG;
+    if (opts->est != GPR_EST_SOV_QMC) return GPR_ERR_UNSUPPORTED;  // the indicator MC has no useful gradient
+    return lcp_backward(M, grid, isovalue, opts, dL_dlcp, nullptr, dL_dy, dL_dloglen, (cudaStream_t)stream);
+}
+
+extern "C" gpr_status gpr_lcp_backward_adaptive(gpr_model *M, const gpr_grid *grid, double isovalue,
+                                                int32_t max_depth, const gpr_lcp_options *opts, const float *dL_dlcp,
+                                                double *dL_dy, double *dL_dloglen, void *stream)
+{
+    if (!M || !grid_valid(grid) || !opts_valid(opts) || !dL_dlcp || !dL_dy || !dL_dloglen || !isfinite(isovalue))
+        return GPR_ERR_ARG;
+    if (max_depth < 0 || max_depth > 20) return GPR_ERR_ARG;
+    for (int d = 0; d < 3; ++d)
+        if (((int64_t)1 << max_depth) < (int64_t)grid->n[d] - 1) return GPR_ERR_ARG;
+    if (opts->est != GPR_EST_SOV_QMC) return GPR_ERR_UNSUPPORTED;
+    cudaStream_t st = (cudaStream_t)stream;
+    GridDev g = make_grid(grid);
+    uint8_t *leaf = nullptr;
+    GPR_CUDA_TRY(cudaMallocAsync((void **)&leaf, (size_t)g.ncells(), st));
+    gpr_status s = octree_leaf_mask(M, grid, isovalue, max_depth, opts, leaf, st);
+    if (s == GPR_OK) s = lcp_backward(M, grid, isovalue, opts, dL_dlcp, leaf, dL_dy, dL_dloglen, st);
+    cudaError_t e = cudaFreeAsync(leaf, st);
+    if (s == GPR_OK && e != cudaSuccess) {
+        gpr_internal_note_cuda_error(e, "cudaFreeAsync(leaf)", __LINE__);
+        s = GPR_ERR_CUDA;
+    }
+    return s;
 }

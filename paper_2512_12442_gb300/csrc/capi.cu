@@ -45,12 +45,18 @@ extern "C" gpr_status gpr_sync(void *stream)
     return (gpr_status)h;
 }
 
-bool opts_valid(const gpr_lcp_options *o)
+bool est_opts_valid(const gpr_lcp_options *o)
 {
     if (!o) return false;
     if (o->est != GPR_EST_SOV_QMC && o->est != GPR_EST_MC) return false;
     if (o->n_samples < 1 || o->n_samples > (1 << 24)) return false;
     if (!(o->jitter >= 0.0) || !(o->skip_eps >= 0.0) || !isfinite(o->jitter) || !isfinite(o->skip_eps)) return false;
+    return true;
+}
+
+bool opts_valid(const gpr_lcp_options *o)
+{
+    if (!est_opts_valid(o)) return false;
     if (!(o->alpha >= 0.0) || !isfinite(o->alpha)) return false;
     if (o->prec < GPR_P_FP64 || o->prec > GPR_P_BF16X3) return false;
     if (o->max_iters_min < 0 || o->max_iters_min > 64) return false;

@@ -247,6 +247,10 @@ void cache_release(gpr_model *M);
 struct OctTrace;
 gpr_status octree_lcp(gpr_model *M, const gpr_grid *grid, double theta, int D, const gpr_lcp_options *opts,
                       float *lcp, gpr_adaptive_stats *stats, cudaStream_t st, OctTrace *trace);
+// Algorithm 1's leaf cells S for one isovalue (leaf: device, one byte per cell), without the
+// leaf reconstruction.
+gpr_status octree_leaf_mask(gpr_model *M, const gpr_grid *grid, double theta, int D, const gpr_lcp_options *opts,
+                            uint8_t *leaf, cudaStream_t st);
 // Fills the per-point table for flagged points that lack it (flags: uint8 per point).
 gpr_status cache_fill_mv(gpr_model *M, GridCache *C, const GridDev &g, const uint8_t *flag, int64_t *list, float *tmp_mean,
                          float *tmp_var, float *part, void *cscr, size_t csb, cudaStream_t st);
@@ -316,6 +320,7 @@ int num_sms();
 void launch_flag_zrange(const uint8_t *flag, int64_t n, int64_t nxy, int64_t za, int64_t zb, uint8_t *out,
                         cudaStream_t st);
 bool opts_valid(const gpr_lcp_options *o);
+bool est_opts_valid(const gpr_lcp_options *o);  // the fields the cell estimator reads
 LcpOpts lcp_opts(const gpr_lcp_options *o, double theta);
 void prepass_margins(const gpr_model *M, double &mv, double &mm);
 // keep[cell] != 0 cells: FP64 stats of their corners, estimator, field (zeroed elsewhere).

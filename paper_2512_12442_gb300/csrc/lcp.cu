@@ -1,4 +1,4 @@
-// Cell level-crossing probability (Sec. 3): LCP = 1 - P(all 8 corners < theta)
+// Cell level-crossing probability (Sec. 4): LCP = 1 - P(all 8 corners < theta)
 // - P(all 8 corners > theta) for the 8-variate Gaussian of a cell's corners.
 // Stage 1 (FP64, thread per cell): assemble (mu_8, Sigma_8) from per-point stats15,
 // add the jitter, apply Boole's pre-skip and factor Sigma_8 = L L^T.

@@ -6,8 +6,8 @@
 // fragment that pool), and latency-critical loops, where cudaFree synchronises the
 // whole device.  The other entry points grow a workspace with cudaMalloc on first use.
 //
-// The estimator's scratch (record counter, status word, per-cell records) lives in one
-// file-scope __device__ array below.  Every GPU that loads the library holds it until
+// The estimator's scratch (record counter, per-cell records) lives in one file-scope
+// __device__ array below.  Every GPU that loads the library holds it until
 // the process exits.  All calls share it and it keeps the last call's contents, so
 // calls that overlap on the GPU (different streams, or different host threads) race
 // on it; callers must order them (one stream, or events).
@@ -19,7 +19,7 @@ namespace {
 
 constexpr int64_t kMaxCells = GPR_NOALLOC_MAX_CELLS;
 constexpr size_t kRecBytes = 192;  // sizeof(CellRec) in lcp.cu, checked at set-up
-constexpr size_t kScratchBytes = 256 /* counter */ + kRecBytes * (size_t)kMaxCells + 256 /* status */;
+constexpr size_t kScratchBytes = 256 /* counter */ + kRecBytes * (size_t)kMaxCells;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
@@ -54,10 +54,7 @@ extern "C" gpr_status gpr_cell_lcp_from_stats_noalloc(const gpr_grid *grid, cons
                                                       const gpr_lcp_options *opts, const int64_t *cell_idx,
                                                       int64_t count, float *lcp, void *stream)
 {
-    if (!grid_valid(grid) || !stats15 || !lcp || !opts || !isfinite(isovalue)) return GPR_ERR_ARG;
-    if (opts->est != GPR_EST_SOV_QMC && opts->est != GPR_EST_MC) return GPR_ERR_ARG;
-    if (opts->n_samples < 1 || opts->n_samples > (1 << 24)) return GPR_ERR_ARG;
-    if (!(opts->jitter >= 0.0) || !(opts->skip_eps >= 0.0)) return GPR_ERR_ARG;
+    if (!grid_valid(grid) || !stats15 || !lcp || !est_opts_valid(opts) || !isfinite(isovalue)) return GPR_ERR_ARG;
     GridDev g = make_grid(grid);
     if (!cell_idx) count = g.ncells();
     if (count < 0 || count > g.ncells()) return GPR_ERR_ARG;
@@ -65,9 +62,11 @@ extern "C" gpr_status gpr_cell_lcp_from_stats_noalloc(const gpr_grid *grid, cons
     if (count == 0) return GPR_OK;
     void *base = nullptr;
     GPR_TRY(scratch_address(&base));
+    // Listed cells off the grid are reported through the library's status word (gpr_sync), as
+    // the allocating entry point reports them; the word is a module global, not an allocation.
+    int *status = gpr_status_word();
+    if (!status) return GPR_ERR_CUDA;
     cudaStream_t st = (cudaStream_t)stream;
-    int *status = (int *)((char *)base + kScratchBytes - 256);
-    GPR_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int), st));
     LcpOpts o;
     o.theta = isovalue;
     o.tau = opts->jitter;

@@ -1,10 +1,10 @@
-// Algorithm 1 (octree adaptive query, Sec. 4.3) on the device, level by level, followed by
-// the leaf reconstruction of Sec. 4.3's last paragraph: the cells of S get the dense
+// Algorithm 1 (octree adaptive query, Sec. 5.3) on the device, level by level, followed by
+// the leaf reconstruction of Sec. 5.3's last paragraph: the cells of S get the dense
 // method's LCP, every other cell 0.
 //
-// Per level: (1) p-test on the observations inside each node (Sec. 4.3: p1 = max P(Y_i<t),
+// Per level: (1) p-test on the observations inside each node (Sec. 5.3: p1 = max P(Y_i<t),
 // p2 = max P(Y_i>t) over the node's observations, with the latent posterior at the
-// observations); (2) the regional upper bound 1 - B_l^d - B_u^d (Eq. upper_bound, Sec. 4.1)
+// observations); (2) the regional upper bound 1 - B_l^d - B_u^d (Eq. upper_bound, Sec. 5.1)
 // for the remaining nodes, B = min over the node of Phi(+-(t - mu)/sigma): exact over the
 // grid points when a node has <= 3 points per axis, otherwise a 3x3x3 lattice start plus T
 // projected gradient steps (our reading of the paper's L-BFGS-B minimiser); (3) compaction
@@ -652,6 +652,8 @@ struct OctBuffers {
 }  // namespace
 
 // Trace hook for tests: records one level's frontier, decisions and bounds on the host.
+// With leaf_out set (and level -1) the call stops after the last level and copies the leaf-cell
+// flags S (one byte per cell, device) there instead of reconstructing the leaves.
 struct OctTrace {
     int level;
     int64_t *nodes;
@@ -659,6 +661,7 @@ struct OctTrace {
     double *bound;
     int64_t capacity;
     int64_t count;
+    uint8_t *leaf_out;
 };
 
 static gpr_status run_eval(const gpr_model *M, const EvalModel &E, OctBuffers &B, int64_t cnt, double theta,
@@ -908,7 +911,11 @@ gpr_status octree_lcp(gpr_model *M, const gpr_grid *grid, double theta, int D, c
         count = (int64_t)hc[0];
         cur = 1 - cur;
     }
-    if (trace) return GPR_OK;
+    if (trace) {
+        if (trace->leaf_out)
+            GPR_CUDA_TRY(cudaMemcpyAsync(trace->leaf_out, B.leaf, (size_t)nc, cudaMemcpyDeviceToDevice, st));
+        return GPR_OK;
+    }
     int64_t leaf_cells = 0, rp = 0, est = 0;
     gpr_adaptive_stats tmp;
     memset(&tmp, 0, sizeof tmp);
@@ -936,6 +943,14 @@ extern "C" gpr_status gpr_lcp_adaptive(gpr_model *M, const gpr_grid *grid, doubl
     return octree_lcp(M, grid, isovalue, max_depth, opts, lcp, stats, (cudaStream_t)stream, nullptr);
 }
 
+// The leaf cells S of Algorithm 1 only (one byte per cell, device), for the adaptive backward.
+gpr_status octree_leaf_mask(gpr_model *M, const gpr_grid *grid, double theta, int D, const gpr_lcp_options *opts,
+                            uint8_t *leaf, cudaStream_t st)
+{
+    OctTrace tr{-1, nullptr, nullptr, nullptr, 0, 0, leaf};
+    return octree_lcp(M, grid, theta, D, opts, nullptr, nullptr, st, &tr);
+}
+
 // Test hook (not in the public header): the frontier, decisions and bounds of one level.
 extern "C" gpr_status gpr_octree_trace(gpr_model *M, const gpr_grid *grid, double isovalue, int32_t max_depth,
                                        const gpr_lcp_options *opts, int32_t level, int64_t *nodes, int8_t *decision,
@@ -943,7 +958,7 @@ extern "C" gpr_status gpr_octree_trace(gpr_model *M, const gpr_grid *grid, doubl
 {
     if (!M || !grid_valid(grid) || !opts_valid(opts) || !nodes || !decision || !bound || !count) return GPR_ERR_ARG;
     if (max_depth < 0 || max_depth > 20 || level < 0 || level > max_depth) return GPR_ERR_ARG;
-    OctTrace tr{level, nodes, decision, bound, capacity, 0};
+    OctTrace tr{level, nodes, decision, bound, capacity, 0, nullptr};
     gpr_status s = octree_lcp(M, grid, isovalue, max_depth, opts, nullptr, nullptr, (cudaStream_t)stream, &tr);
     *count = tr.count;
     return s;

@@ -12,17 +12,28 @@
 
 static constexpr int NB = 32;  // Cholesky block size
 
-static int *g_status_dev = nullptr;
+// The status word is a module global, so every device that loads the library has its own copy
+// (zero at load); its device address is resolved once per device, with that device current.
+static __device__ int g_status_word;
+static constexpr int kMaxDevices = 128;
 
 int *gpr_status_word()
 {
     static std::mutex mu;
+    static int *addr[kMaxDevices] = {nullptr};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
     std::lock_guard<std::mutex> lock(mu);
-    if (!g_status_dev) {
-        if (cudaMalloc(&g_status_dev, sizeof(int)) != cudaSuccess) return nullptr;
-        cudaMemset(g_status_dev, 0, sizeof(int));
+    if (!addr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_status_word);
+        if (e != cudaSuccess || !p) {
+            gpr_internal_note_cuda_error(e, "cudaGetSymbolAddress(g_status_word)", __LINE__);
+            return nullptr;
+        }
+        addr[dev] = (int *)p;
     }
-    return g_status_dev;
+    return addr[dev];
 }
 
 static char g_last_err[256];
@@ -34,14 +45,14 @@ void gpr_internal_note_cuda_error(cudaError_t e, const char *what, int line)
 
 int num_sms()
 {
-    static std::atomic<int> cached{0};
-    int n = cached.load();
+    static std::atomic<int> cached[kMaxDevices];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) dev = 0;
+    int n = cached[dev].load();
     if (!n) {
-        int dev = 0;
-        cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
         if (n <= 0) n = 1;
-        cached = n;
+        cached[dev] = n;
     }
     return n;
 }

@@ -65,6 +65,34 @@ def test_host_argument_checks_need_no_gpu(lib):
                                        None) == g.GPR_ERR_ARG
 
 
+def test_noalloc_entry_checks_estimator_options_on_the_host(lib):
+    """The allocation-free estimator entry rejects the option values the allocating entry rejects
+    (non-finite jitter or skip threshold, bad sample counts) before any CUDA call."""
+    import paper_2512_12442_gb300 as g
+    grid = g.make_grid(9)
+    for kw in ({"jitter": float("inf")}, {"skip_eps": float("inf")}, {"jitter": float("nan")},
+               {"n_samples": 0}, {"est": 7}):
+        o = g.lcp_options(**kw)
+        assert lib.gpr_cell_lcp_from_stats_noalloc(ctypes.byref(grid), 1, 0.0, ctypes.byref(o), None, 0, 1,
+                                                   None) == g.GPR_ERR_ARG, kw
+        assert lib.gpr_cell_lcp_from_stats(ctypes.byref(grid), 1, 0.0, ctypes.byref(o), None, 0, 1,
+                                           None) == g.GPR_ERR_ARG, kw
+
+
+def test_fault_injection_alloc_reports_oom_without_a_gpu(lib, monkeypatch):
+    """GPR_FAULT=alloc makes model creation fail as an allocation failure would (GPR_ERR_OOM),
+    on the host, before any device work: the caller's error path can be exercised without a GPU."""
+    import numpy as np
+    import paper_2512_12442_gb300 as g
+    X = np.random.default_rng(0).random((8, 3)); y = np.zeros(8)
+    h = ctypes.c_void_p()
+    monkeypatch.setenv("GPR_FAULT", "alloc")
+    rc = lib.gpr_model_create(X.ctypes.data, y.ctypes.data, 8, 0, np.full(3, 0.2).ctypes.data, 1.0, 1e-4, None,
+                              ctypes.byref(h))
+    assert rc == g.GPR_ERR_OOM and not h.value
+    assert lib.gpr_status_string(rc) == b"out of device memory"
+
+
 def test_product_package_does_not_import_the_oracle():
     """The product path never routes through the CPU oracle."""
     pkg = os.path.join(ROOT, "paper_2512_12442_gb300")

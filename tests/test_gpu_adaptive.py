@@ -94,7 +94,7 @@ def test_adaptive_field_vs_dense_and_oracle(torch, g, case):
     # cells the oracle kept and the GPU dropped (or vice versa) carry an LCP below a few alpha
     assert diff.max() <= 5e-3, diff.max()
     assert np.sum(diff > 1e-4) <= 0.01 * a.size + 2
-    # RMSE adaptive vs dense (the paper's accuracy metric, Sec. 5.2): small
+    # RMSE adaptive vs dense (the paper's accuracy metric, Sec. 6.2): small
     assert np.sqrt(np.mean((a - d) ** 2)) < 2e-3
 
 

@@ -140,7 +140,7 @@ def test_sgpr_equation1_reduces_to_plain_gpr():
     mu2, var2, cov2 = M.posterior(P, full_cov=True)
     np.testing.assert_allclose(mu1, mu2, rtol=1e-8, atol=1e-10)
     np.testing.assert_allclose(cov1, cov2, rtol=1e-6, atol=1e-9)
-    # and the latent posterior at the observations matches mu_M, diag(A_M) (Sec. 4.3 p-test input)
+    # and the latent posterior at the observations matches mu_M, diag(A_M) (Sec. 5.3 p-test input)
     f = M.factors()
     np.testing.assert_allclose(f["mu_obs"], muM, rtol=1e-9, atol=1e-11)
     np.testing.assert_allclose(f["var_obs"], np.maximum(np.diag(AM), 1e-12), rtol=1e-6, atol=1e-12)
@@ -170,7 +170,7 @@ def test_stats15_match_full_covariance():
                 p += 1
 
 
-# --------------------------------------------------------- cell LCP (Sec. 3)
+# --------------------------------------------------------- cell LCP (Sec. 4)
 
 def _shift(seed=0, d=8):
     return np.array([oracle.splitmix64(seed, i + 1) >> 32 for i in range(d - 1)], np.uint32)
@@ -227,7 +227,7 @@ def test_lcp_perfect_correlation_vanishes():
 
 
 def test_lcp_mc_agrees_with_sov():
-    """Paper's MC estimator (Sec. 3, 1600 samples, Sec. 5.4) agrees with SOV within its standard error."""
+    """Paper's MC estimator (Sec. 4, 1600 samples, Sec. 6.4) agrees with SOV within its standard error."""
     rng = np.random.default_rng(9)
     A = rng.normal(size=(8, 8)); S = A @ A.T / 8 + 0.2 * np.eye(8)
     mu = rng.normal(0, 0.3, 8)
@@ -252,7 +252,7 @@ def test_lcp_skip_and_range():
 
 
 def test_lcp_field_brute_force_mc_small():
-    """Dense LCP of a few real cells (Sec. 3): SOV agrees with a brute-force numpy MC of the same
+    """Dense LCP of a few real cells (Sec. 4): SOV agrees with a brute-force numpy MC of the same
     8-variate posterior, built from full joint covariance by an independent route."""
     w = workloads.config1()
     M = oracle.Model.from_workload(w)
@@ -274,7 +274,7 @@ def test_lcp_field_brute_force_mc_small():
                 idx += 1
 
 
-# ------------------------------------------------- bound + octree (Sec. 4)
+# ------------------------------------------------- bound + octree (Sec. 5)
 
 def test_eval_g_gradient_matches_finite_differences():
     w = workloads.small(5, 40, 9)
@@ -504,7 +504,7 @@ def test_two_sided_bound_when_the_node_is_empty():
 
 def test_octree_alpha_zero_keeps_nonzero_cells_and_adaptive_equals_dense():
     """Algorithm 1 with alpha -> 0 keeps every cell whose dense LCP is non-zero, and the adaptive
-    field equals the dense field on S and is 0 elsewhere (Sec. 4.3, last paragraph)."""
+    field equals the dense field on S and is 0 elsewhere (Sec. 5.3, last paragraph)."""
     w = workloads.small(2, 30, 9, ell=(0.3, 0.3, 0.3))
     M = oracle.Model.from_workload(w)
     th = w.isovalues[0]
@@ -517,7 +517,7 @@ def test_octree_alpha_zero_keeps_nonzero_cells_and_adaptive_equals_dense():
     np.testing.assert_array_equal(field3[lin], dense[lin])
     mask = np.ones(dense.size, bool); mask[lin] = False
     assert np.all(field3[mask] == 0)
-    # RMSE against dense is small, as the paper reports (Sec. 6.2): a sanity range, not a pin
+    # RMSE against dense is small, as the paper reports (Sec. 7.2): a sanity range, not a pin
     assert math.sqrt(np.mean((field3 - dense) ** 2)) < 5e-3
 
 

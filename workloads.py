@@ -2,10 +2,10 @@
 
 This module holds no arithmetic of the method: it only draws observation sites,
 observation values and run parameters.  The paper's datasets (Tangle, Ethanediol;
-Sec. 5.3) are not available, so these fields stand in for them with the workload
+Sec. 6.3) are not available, so these fields stand in for them with the workload
 shapes the paper reports (m = 50..500 observations, 64^3..1024^3 grids, an RBF
 kernel whose length scale is ~0.1 of the domain, alpha = 1e-3, beta = 6, 1600 MC
-samples; Sec. 5, Table 1, Sec. 6.3).
+samples; Sec. 6, Table 1, Sec. 7.3).
 
 Field recipe: y = sum of Gaussian bumps a*exp(-|x-c|^2/(2w^2)) [+ 0.3 sin(pi(x+y+z))]
 + 0.01 N(0,1), observation sites uniform in [0,1]^3.  The draw order below is part
