@@ -32,12 +32,16 @@ import numpy as np  # noqa: E402
 import workloads  # noqa: E402
 
 METRIC = "LCP grid points/s"
-# Warp instructions k_sov issues per estimated cell (1600 lattice points, both orthants unless the
-# Frechet test drops one), from the ncu counters of the small case (sov_estimator profile summary).
-# The estimator is issue-bound: its roofline is the issue rate, 4 warp instructions per clock on
-# each of 152 SMs at 2.07 GHz.
-SOV_WARP_INST_PER_CELL = 34883.0
+# Warp instructions k_sov issues per orthant-sample (one lattice point of one orthant,
+# P(all < theta) or P(all > theta)): ncu's smsp__inst_executed.sum of the tuned launch shape on the
+# 64^3 case (3,152,591,626) over the orthant-samples the device counted for it (138,575 orthants x
+# 1600), profiles/sov_estimator_m500_grid64.txt.  The estimator is issue-bound: its roofline is the
+# issue rate, 4 warp instructions per clock on each of 152 SMs at 2.07 GHz; achieved =
+# orthant-samples counted on the device x this figure / launch time.
+SOV_WARP_INST_PER_ORTHANT_SAMPLE = 14.22
 ISSUE_PEAK_GINST = 152 * 4 * 2.07
+# Dense tensor peaks relative to BF16 (nominal dense rates: TF32 1.1, BF16 2.25 PFLOP/s)
+TF32_OVER_BF16 = 1.1 / 2.25
 UNIT = "grid points/s"
 
 
@@ -59,6 +63,7 @@ def parse():
     p.add_argument("--prec", default="tf32x3", choices=["fp32", "fp64", "tf32", "tf32x3", "bf16", "bf16x3"],
                    help="precision of the pre-classification / octree pass")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-side-by-side", action="store_true", help="skip the dense / FP32-SIMT comparison runs")
     p.add_argument("--cpu-sample", type=int, default=64, help="cells per axis of the oracle sample")
     p.add_argument("--case", default="full", choices=["full", "small"],
                    help="small: one dense LCP field of the same field on a 64^3 grid (for ncu captures); "
@@ -141,20 +146,25 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def oracle_block(w, cells_per_axis):
+    """Cell box [c0, c1) of the bounded oracle sample: a cube of cells at the centre of the grid."""
+    c0 = (w.n - 1) // 2 - cells_per_axis // 2
+    return (c0, c0, c0), (c0 + cells_per_axis,) * 3
+
+
 def cpu_baseline(w, theta, cells_per_axis):
-    """The FP64 oracle as it stands, on a bounded block of cells straddling the field."""
+    """The FP64 oracle as it stands, on a bounded block of cells straddling the field.  Returns the
+    baseline record and the oracle's LCP of the block (x-fastest)."""
     import oracle
     t0 = time.perf_counter()
     om = oracle.Model.from_workload(w)
-    c0 = (w.n - 1) // 2 - cells_per_axis // 2
-    c = (c0, c0, c0)
-    c1 = tuple(v + cells_per_axis for v in c)
-    om.lcp_block(w.n, theta, c, c1)
+    c, c1 = oracle_block(w, cells_per_axis)
+    vals = om.lcp_block(w.n, theta, c, c1)
     dt = time.perf_counter() - t0
     cells = cells_per_axis ** 3
     return {"value": cells / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
             "sample": f"model set-up + SOV-1600 LCP of a {cells_per_axis}^3-cell block at the median isovalue "
-                      f"({cells} cells ~ grid points), {dt:.1f} s"}
+                      f"({cells} cells ~ grid points), {dt:.1f} s"}, vals
 
 
 def run_reference(args):
@@ -231,7 +241,7 @@ def run_backward(args, g, torch, rank, world, local):
         return
     out = {"metric": METRIC + " (forward + backward)", "value": world * n ** 3 / (ms / 1e3), "unit": UNIT, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "vs_baseline": None, "dtype": "fp32", "data": "synthetic",
            "config": {"workload": f"{w.name}: loss = sum_c U(0,1)_c LCP_c, d/dy (500) and d/dlog l (3)",
                       "grid": n},
            "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
@@ -284,6 +294,7 @@ def run_batched(args, g, torch, rank, world, local):
     ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world)
     prof = {k: g.gpr_profile_read(k) for k in ("oz_adig", "oz_w", "stats_ff", "tc_sumsq", "mean_ff", "w64", "cell_prep", "sov",
                                                 "oct_eval_w", "oct_level")}
+    orth = g.gpr_profile_units("sov_orthants")
     e0.record(stream)
     for _ in range(args.steps):
         for M in step(e2e=True):
@@ -300,17 +311,17 @@ def run_batched(args, g, torch, rank, world, local):
     if n_launch > 0:
         # the shared estimator runs alone on the caller's stream after every field's octree
         avg_s = c / n_launch / 1e3
-        inst = SOV_WARP_INST_PER_CELL * est / (n_launch / args.steps)
+        inst = SOV_WARP_INST_PER_ORTHANT_SAMPLE * orth * opts.n_samples / n_launch
         roof = {"bound": "alu", "achieved": inst / avg_s / 1e9, "peak": ISSUE_PEAK_GINST, "unit": "Gwarp-inst/s",
                 "traffic": None, "kernel": "k_sov (SOV-QMC estimator over every field's cells, one persistent launch)",
                 "peak_source": "issue rate 4 warp-inst/clk x 152 SMs x 2.07 GHz (recipe unit counts and clock)"}
         roof["frac"] = roof["achieved"] / roof["peak"]
     cpu = None
     if not args.no_cpu_baseline:
-        cpu = cpu_baseline(ws[0], ws[0].isovalues[0], min(32, ws[0].n - 1))
+        cpu = cpu_baseline(ws[0], ws[0].isovalues[0], min(32, ws[0].n - 1))[0]
     out = {"metric": METRIC, "value": world * pts / (ms / 1e3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "vs_baseline": None, "dtype": "fp32", "data": "synthetic",
            "config": {"workload": f"{len(ws)} SE models, m log-uniform [100, 2000], l in [0.05, 0.3], "
                                   f"grids 64^3/128^3/256^3, median isovalue, adaptive, batched",
                       "models": len(ws), "grid_points": pts, "m": [w.m for w in ws], "grid": [w.n for w in ws],
@@ -345,9 +356,14 @@ def main():
         grid = g.make_grid(n)
         out = torch.zeros((n - 1) ** 3, dtype=torch.float32, device="cuda")
         M = g.gpr_model_create(w.X, w.y, w.kernel, w.ell, w.sf2, w.sn2)
+        g.gpr_profile_reset(); g.gpr_profile_enable(True)
         st = g.gpr_lcp_dense(M, grid, w.isovalues[1], g.lcp_options(prec=g.GPR_P_TF32X3), out)
         g.gpr_sync()
-        print(json.dumps({"case": "small", "grid": n, "m": w.m, **{k: st[k] for k in ("recon_points", "leaf_cells", "cells_estimated")}}))
+        g.gpr_profile_enable(False)
+        print(json.dumps({"case": "small", "grid": n, "m": w.m,
+                          **{k: st[k] for k in ("recon_points", "leaf_cells", "cells_estimated")},
+                          "sov_orthants": g.gpr_profile_units("sov_orthants"),
+                          "sov_launches": g.gpr_profile_read("sov")[1]}))
         return
     if args.mode == "backward":
         run_backward(args, g, torch, rank, world, local)
@@ -358,19 +374,19 @@ def main():
     n = w.n
     ncell = (n - 1) ** 3
     grid = g.make_grid(n)
-    prec = {"fp64": g.GPR_P_FP64, "fp32": g.GPR_P_FP32, "tf32": g.GPR_P_TF32, "tf32x3": g.GPR_P_TF32X3,
-            "bf16": g.GPR_P_BF16, "bf16x3": g.GPR_P_BF16X3}[args.prec]
-    opts = g.lcp_options(prec=prec)
+    precs = {"fp64": g.GPR_P_FP64, "fp32": g.GPR_P_FP32, "tf32": g.GPR_P_TF32, "tf32x3": g.GPR_P_TF32X3,
+             "bf16": g.GPR_P_BF16, "bf16x3": g.GPR_P_BF16X3}
+    opts = g.lcp_options(prec=precs[args.prec])
     stream = torch.cuda.current_stream()
     fields = [torch.zeros(ncell, dtype=torch.float32, device="cuda") for _ in w.isovalues]
     host = [torch.zeros(ncell, dtype=torch.float32).pin_memory() for _ in w.isovalues]
     stats_last = {}
 
-    def step(e2e=False):
+    def step(mode=args.mode, o=opts, e2e=False):
         M = g.gpr_model_create(w.X, w.y, w.kernel, w.ell, w.sf2, w.sn2, stream=stream)
-        if args.mode == "adaptive" and args.api == "batched":
+        if mode == "adaptive" and args.api == "batched":
             nf = len(w.isovalues)
-            sts = g.gpr_lcp_adaptive_batched([M] * nf, [grid] * nf, list(w.isovalues), [w.max_depth] * nf, opts,
+            sts = g.gpr_lcp_adaptive_batched([M] * nf, [grid] * nf, list(w.isovalues), [w.max_depth] * nf, o,
                                              fields, stream=stream)
             for t in range(nf):
                 stats_last[t] = sts[t]
@@ -378,10 +394,10 @@ def main():
                     host[t].copy_(fields[t], non_blocking=True)
             return M
         for t, th in enumerate(w.isovalues):
-            if args.mode == "dense":
-                st = g.gpr_lcp_dense(M, grid, th, opts, fields[t], stream=stream)
+            if mode == "dense":
+                st = g.gpr_lcp_dense(M, grid, th, o, fields[t], stream=stream)
             else:
-                st = g.gpr_lcp_adaptive(M, grid, th, w.max_depth, opts, fields[t], stream=stream)
+                st = g.gpr_lcp_adaptive(M, grid, th, w.max_depth, o, fields[t], stream=stream)
             stats_last[t] = st
             if e2e:
                 host[t].copy_(fields[t], non_blocking=True)
@@ -393,44 +409,57 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    for _ in range(args.warmup):
-        M = step()
-        M.close()
-    g.gpr_sync(stream)
-
-    # timed region: device-resident inputs
-    barrier()
-    g.gpr_profile_reset()
-    g.gpr_profile_enable(True)
-    with ClockSampler(local) as clk:
+    def timed(k, **kw):
+        """CUDA-event milliseconds per step over k steps (barrier + synchronize on both sides)."""
+        barrier()
         ev0 = torch.cuda.Event(enable_timing=True); ev1 = torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
-        for _ in range(args.steps):
-            M = step()
+        for _ in range(k):
+            step(**kw).close()
         ev1.record(stream)
         barrier()
-    g.gpr_profile_enable(False)
-    launches = g.gpr_launch_count()
-    ms = ev0.elapsed_time(ev1) / args.steps
-    prof = {k: g.gpr_profile_read(k) for k in ("w64", "oz_adig", "oz_w", "stats_ff", "meanvar32", "tc_sumsq", "mean_ff",
-                                                "stats_from_w64", "cell_prep", "sov", "classify", "oct_eval_w",
-                                                "oct_level")}
+        g.gpr_sync(stream)
+        return ev0.elapsed_time(ev1) / k
+
+    for _ in range(args.warmup):
+        step().close()
     g.gpr_sync(stream)
-    M.close()
+
+    # headline: device-resident inputs, tracing off
+    g.gpr_profile_reset()
+    with ClockSampler(local) as clk:
+        ms = timed(args.steps)
+    launches = g.gpr_launch_count()
     t_max = max_over_ranks(ms, world)
     pts_per_step = len(w.isovalues) * n ** 3
     value = world * pts_per_step / (t_max / 1e3)
 
-    # end-to-end: host inputs in, fields copied back to pinned host memory every step
-    barrier()
-    e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        M = step(e2e=True)
-        M.close()
-    e1.record(stream)
-    barrier()
-    ms_e2e = max_over_ranks(e0.elapsed_time(e1) / args.steps, world)
+    # end to end: host inputs in, the fields copied back to pinned host memory every step
+    ms_e2e = max_over_ranks(timed(args.steps, e2e=True), world)
+
+    # the same steps again with the tracer on: per-stage CUDA-event times and work units
+    g.gpr_profile_reset()
+    g.gpr_profile_enable(True)
+    ms_traced = timed(args.steps)
+    g.gpr_profile_enable(False)
+    names = ("w64", "oz_adig", "oz_w", "stats_ff", "meanvar32", "tc_sumsq", "mean_ff", "stats_from_w64",
+             "cell_prep", "sov", "classify", "oct_eval_w", "oct_level")
+    prof = {k: g.gpr_profile_read(k) for k in names}
+    units = {k: g.gpr_profile_units(k) for k in ("oz_w", "oz_adig", "stats_ff", "tc_sumsq", "sov_orthants")}
+    g.gpr_sync(stream)
+
+    # the same field by the other paths, side by side at the same accuracy (same FP64-class leaf
+    # statistics and estimator): dense with the TF32x3 pre-pass, dense with the plain FP32 SIMT pre-pass
+    side = {}
+    if args.mode == "adaptive" and not args.no_side_by_side:
+        for label, mode, pr in (("dense_tf32x3", "dense", "tf32x3"), ("dense_fp32_simt", "dense", "fp32")):
+            o2 = g.lcp_options(prec=precs[pr])
+            step(mode=mode, o=o2).close()
+            k2 = max(1, min(args.steps, 3))
+            t2 = max_over_ranks(timed(k2, mode=mode, o=o2), world)
+            side[label] = {"ms_per_step": t2, "value": world * pts_per_step / (t2 / 1e3), "steps": k2}
+        step().close()  # the default path's fields again, for the accuracy check below
+        g.gpr_sync(stream)
 
     if rank != 0:
         if world > 1:
@@ -438,64 +467,110 @@ def main():
             dist.destroy_process_group()
         return
 
-    # roofline of the dominant kernel (oct_level spans whole octree levels, not one kernel)
-    kern = {k: v for k, v in prof.items() if k != "oct_level"}
-    dom = max(kern, key=lambda k: kern[k][0])
     m = w.m
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         pass
-    nfield = len(stats_last)
-    recon = sum(stats_last[t]["recon_points"] for t in stats_last)
+    bf16_sus = float(peaks.get("bf16_tflops_sustained") or 1733.1)
     est_cells = sum(stats_last[t]["cells_estimated"] for t in stats_last)
+
+    def per_step(k):
+        return prof[k][0] / args.steps
+
+    # roofline of the dominant kernel (oct_level spans whole octree levels, not one kernel)
+    kern = {k: v for k, v in prof.items() if k != "oct_level" and v[1] > 0}
+    dom = max(kern, key=lambda k: kern[k][0]) if kern else None
     roof = None
-    if kern[dom][1] > 0:
-        avg_s = kern[dom][0] / kern[dom][1] / 1e3
-        per_launch = args.steps / kern[dom][1]  # share of a step's units one launch processes
-        if dom == "w64":
-            flops = recon * per_launch * m * (m + 1)  # triangular whitening GEMM, per launch
-            peak = 2.0 * 2 * 152 * 2.07e9 / 1e12
-            roof = {"bound": "alu", "achieved": flops / avg_s / 1e12, "peak": peak, "unit": "TFLOP/s",
-                    "traffic": 609.7e6 / 161920 * recon * per_launch, "kernel": "k_w_store<double> (FP64 whitening GEMM)",
-                    "peak_source": "derived FP64 issue rate 2 DFMA/clk/SM x 152 x 2.07 GHz (probe measured 1.202)"}
-        elif dom == "oz_w":
-            # BF16 tensor work actually issued: 28 digit products x 2 x rows x sum over 64-column tiles of
-            # 64 x ceil(min(n0+64, m)/32)*32 (the K range of each tile)
-            mp = (m + 63) // 64 * 64
-            kk = sum(64 * ((min(n0 + 64, m) + 31) // 32 * 32) for n0 in range(0, mp, 64))
-            # all rows of the step over all launches of the step (launches are row chunks)
-            flops = 28 * 2 * recon * kk
-            peak = float(peaks.get("bf16_tflops_sustained") or 1733.1)
-            roof = {"bound": "tensor", "achieved": flops / (kern[dom][0] / args.steps / 1e3) / 1e12, "peak": peak,
-                    "unit": "TFLOP/s", "traffic": None,
-                    "kernel": "k_oz_gemm (FP64-class whitening GEMM, BF16 digit split)",
-                    "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained"}
-        elif dom == "sov":
-            inst = SOV_WARP_INST_PER_CELL * est_cells * per_launch  # one launch per field, or one per step
-            roof = {"bound": "alu", "achieved": inst / avg_s / 1e9, "peak": ISSUE_PEAK_GINST, "unit": "Gwarp-inst/s",
-                    "traffic": None, "kernel": "k_sov (SOV-QMC estimator, FP32)",
-                    "peak_source": "issue rate 4 warp-inst/clk x 152 SMs x 2.07 GHz (recipe unit counts and clock)"}
-        if roof:
-            roof["frac"] = roof["achieved"] / roof["peak"]
-    cpu = None if args.no_cpu_baseline else cpu_baseline(w, w.isovalues[1], args.cpu_sample)
+    if dom == "sov" and units["sov_orthants"] > 0:
+        # orthant-samples counted on the device (orthants queued x samples), per launch
+        avg_s = prof["sov"][0] / prof["sov"][1] / 1e3
+        osamp = units["sov_orthants"] * opts.n_samples / prof["sov"][1]
+        inst = SOV_WARP_INST_PER_ORTHANT_SAMPLE * osamp
+        roof = {"bound": "alu", "achieved": inst / avg_s / 1e9, "peak": ISSUE_PEAK_GINST, "unit": "Gwarp-inst/s",
+                "traffic": None, "kernel": "k_sov (SOV-QMC estimator, FP32)",
+                "orthant_samples_per_launch": osamp, "orthant_samples_per_s": osamp / avg_s,
+                "peak_source": "issue rate 4 warp-inst/clk x 152 SMs x 2.07 GHz (recipe unit counts and clock); "
+                               f"{SOV_WARP_INST_PER_ORTHANT_SAMPLE} warp-inst per orthant-sample from ncu"}
+    elif dom == "oz_w" and units["oz_w"] > 0:
+        mp = (m + 63) // 64 * 64
+        kk = sum(64 * ((min(n0 + 64, m) + 31) // 32 * 32) for n0 in range(0, mp, 64))
+        flops = 28 * 2 * units["oz_w"] * kk
+        roof = {"bound": "tensor", "achieved": flops / (prof["oz_w"][0] / 1e3) / 1e12, "peak": bf16_sus,
+                "unit": "TFLOP/s", "traffic": None, "kernel": "k_oz_gemm (FP64-class whitening GEMM, BF16 digit split)",
+                "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained"}
+    if roof:
+        roof["frac"] = roof["achieved"] / roof["peak"]
+
+    # tensor-pipe throughput of the two contractions (CUDA-event time, FLOPs from the rows processed)
+    tensor = {}
+    if prof["tc_sumsq"][1] > 0 and units["tc_sumsq"] > 0:
+        nprod = {"tf32x3": 3, "bf16x3": 6, "tf32": 1, "bf16": 1}.get(args.prec, 1)
+        fl = nprod * m * (m + 1) * units["tc_sumsq"]  # triangular whitening w = L^-1 k: m(m+1) per product
+        pk = bf16_sus * (TF32_OVER_BF16 if args.prec.startswith("tf32") else 1.0)
+        tensor["k_tc_sumsq"] = {"ms_per_step": per_step("tc_sumsq"), "points_per_step": units["tc_sumsq"] / args.steps,
+                                "tflops": fl / (prof["tc_sumsq"][0] / 1e3) / 1e12, "peak_tflops": pk,
+                                "flops": f"{nprod} products x m(m+1) per point (algorithmic)"}
+        tensor["k_tc_sumsq"]["frac"] = tensor["k_tc_sumsq"]["tflops"] / pk
+    if prof["oz_w"][1] > 0 and units["oz_w"] > 0:
+        mp = (m + 63) // 64 * 64
+        kk = sum(64 * ((min(n0 + 64, m) + 31) // 32 * 32) for n0 in range(0, mp, 64))
+        fl = 28 * 2 * units["oz_w"] * kk
+        tensor["k_oz_gemm"] = {"ms_per_step": per_step("oz_w"), "rows_per_step": units["oz_w"] / args.steps,
+                               "tflops": fl / (prof["oz_w"][0] / 1e3) / 1e12, "peak_tflops": bf16_sus,
+                               "fp64_equiv_tflops": m * (m + 1) * units["oz_w"] / (prof["oz_w"][0] / 1e3) / 1e12,
+                               "flops": "28 digit products x 2 x sum of the 64-column tiles' K ranges per row "
+                                        "(issued BF16 work); fp64_equiv: m(m+1) per row"}
+        tensor["k_oz_gemm"]["frac"] = tensor["k_oz_gemm"]["tflops"] / bf16_sus
+
+    # accuracy against the FP64 oracle on the bounded sample block (median isovalue)
+    cpu, acc = None, None
+    if not args.no_cpu_baseline:
+        cpu, ovals = cpu_baseline(w, w.isovalues[1], args.cpu_sample)
+        (a0, b0, z0), (a1, b1, z1) = oracle_block(w, args.cpu_sample)
+        blk = fields[1].cpu().numpy().reshape(n - 1, n - 1, n - 1)[z0:z1, b0:b1, a0:a1].reshape(-1).astype(np.float64)
+        d = np.abs(blk - ovals)
+        acc = {"block": f"cells [{a0},{a1})^3 of the 127^3 grid, median isovalue, {ovals.size} cells",
+               "max_abs_dLCP_vs_fp64": float(d.max()), "mean_abs_dLCP_vs_fp64": float(d.mean()),
+               "tolerance": 1e-4}
+        if args.mode == "adaptive":
+            nodes, dec, _ = g.gpr_octree_trace(M_acc := g.gpr_model_create(w.X, w.y, w.kernel, w.ell, w.sf2, w.sn2),
+                                               grid, w.isovalues[1], w.max_depth, opts, w.max_depth)
+            M_acc.close()
+            leaf = nodes[dec > 0]
+            lin = (leaf & 0x1FFFFF) + (n - 1) * (((leaf >> 21) & 0x1FFFFF) + (n - 1) * ((leaf >> 42) & 0x1FFFFF))
+            inS = np.zeros(ncell, bool); inS[lin] = True
+            sblk = inS.reshape(n - 1, n - 1, n - 1)[z0:z1, b0:b1, a0:a1].reshape(-1)
+            acc["on_S"] = {"cells": int(sblk.sum()), "max_abs_dLCP_vs_fp64": float(d[sblk].max()) if sblk.any() else 0.0}
+            acc["off_S"] = {"cells": int((~sblk).sum()),
+                            "max_oracle_LCP": float(ovals[~sblk].max()) if (~sblk).any() else 0.0,
+                            "note": "cells Algorithm 1 dropped (adaptive field 0): the method's approximation, "
+                                    "bounded by alpha per region"}
+
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": t_max, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if True else "f32", "data": "synthetic",
+        "dtype": "fp32", "data": "synthetic",
         "config": {"workload": f"{w.name}, 3 isovalues (P25/P50/P75 of y), SOV-QMC 1600, {args.mode}",
                    "m": m, "grid": n, "mode": args.mode, "prepass": args.prec,
+                   "arithmetic": "FP64 model set-up; FP64-class corner statistics (BF16 tensor-core digit split, "
+                                 "float-float); FP32 estimator; pre-pass/octree in " + args.prec,
                    "api": args.api if args.mode == "adaptive" else "single",
-                   "l2": "working set > L2 (FP64 whitened rows of the kept points, GBs)",
+                   "l2": "working set > L2 (FP64-class whitened rows of the kept points, GBs)",
                    "parallelism": f"replicas x{world}"},
         "roofline": roof,
+        "tensor_pipe": tensor,
+        "accuracy": acc,
+        "side_by_side": side,
         "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
-        "kernel_ms_note": ("CUDA-event time per stage; with api=batched the three fields' octree and leaf stages "
-                           "run on worker streams and their event times overlap (the estimator is one launch)"
-                           if args.mode == "adaptive" and args.api == "batched" else "CUDA-event time per stage"),
+        "traced_ms_per_step": ms_traced,
+        "kernel_ms_note": ("CUDA-event times from a separate traced pass (the headline pass runs untraced); with "
+                           "api=batched the three fields' octree and leaf stages run on worker streams and their "
+                           "times overlap (the estimator is one launch)"),
         "kept_cells": [stats_last[t]["leaf_cells"] for t in stats_last],
         "recon_points": [stats_last[t]["recon_points"] for t in stats_last],
+        "cells_estimated": est_cells,
         "cpu_baseline": cpu,
         "e2e": {"value": world * pts_per_step / (ms_e2e / 1e3), "unit": UNIT,
                 "h2d_bytes_per_step": int(w.X.nbytes + w.y.nbytes),

@@ -323,6 +323,12 @@ void gpr_profile_reset(void);
 /* Synchronises the recorded events; total milliseconds and launches of `name`.
  * Returns 1 if the name was seen, else 0 (outputs zeroed).  Pointers are host. */
 int gpr_profile_read(const char *name, double *total_ms, int64_t *count);
+/* Work units behind the time of `name` while profiling was on (host): rows for "oz_w",
+ * "oz_adig" and "stats_ff", points for "tc_sumsq"; "sov_orthants" is counted on the device:
+ * the orthants (P(all < theta), P(all > theta)) that the cell estimator integrated, one or two per
+ * estimated cell.  Returns 1 if the name has units, else 0 (*units = 0).  Synchronises the device
+ * for "sov_orthants". */
+int gpr_profile_units(const char *name, double *units);
 /* Number of the library's own kernel launches since the last reset. */
 int64_t gpr_launch_count(void);
 

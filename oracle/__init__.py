@@ -41,6 +41,8 @@ def lib():
         L.or_model_create.restype = C.c_void_p
         L.or_model_create.argtypes = [_dp, _dp, C.c_int64, C.c_int, _dp, C.c_double, C.c_double]
         L.or_model_destroy.argtypes = [C.c_void_p]
+        L.or_model_create_sgpr.restype = C.c_void_p
+        L.or_model_create_sgpr.argtypes = [_dp, _dp, _dp, C.c_int64, C.c_int, _dp, C.c_double, C.c_double]
         L.or_model_get.argtypes = [C.c_void_p] + [C.c_void_p] * 5
         L.or_kernel_eval.restype = C.c_double
         L.or_kernel_eval.argtypes = [C.c_int, _dp, C.c_double, _dp, _dp]
@@ -134,7 +136,26 @@ class Model:
 
     @classmethod
     def from_workload(cls, w):
+        if "A_M" in w.extra:
+            return cls.sgpr(w.X, w.y, w.extra["A_M"], w.kernel, w.ell, w.sf2, w.extra["kmm_jitter"])
         return cls(w.X, w.y, w.kernel, w.ell, w.sf2, w.sn2)
+
+    @classmethod
+    def sgpr(cls, X, mu_M, A_M, kernel_kind=SE, ell=(0.2, 0.2, 0.2), sf2=1.0, jitter=0.0):
+        """SGPR model (Sec. 3): inducing sites X with the stored distribution N(mu_M, A_M); the
+        posterior is Eq. 1 as printed, with K_MM = K(X, X) + jitter I."""
+        self = cls.__new__(cls)
+        X = np.ascontiguousarray(X, np.float64)
+        mu_M = np.ascontiguousarray(mu_M, np.float64)
+        A_M = np.ascontiguousarray(A_M, np.float64)
+        self.m = int(mu_M.shape[0])
+        self.kernel, self.ell, self.sf2, self.sn2 = int(kernel_kind), tuple(float(e) for e in ell), float(sf2), 0.0
+        self.X, self.y = X, mu_M
+        self._h = lib().or_model_create_sgpr(X, mu_M, A_M.reshape(-1), self.m, self.kernel,
+                                             np.asarray(self.ell, np.float64), self.sf2, float(jitter))
+        if not self._h:
+            raise ValueError("K_MM + jitter I is not positive definite")
+        return self
 
     def __del__(self):
         h = getattr(self, "_h", None)
@@ -143,6 +164,8 @@ class Model:
             self._h = None
 
     def factors(self):
+        """Cholesky factor (of Kt, or of K_MM + jitter I for an SGPR model), alpha, L^-1 y (or
+        L^-1 mu_M), and the p-test's per-observation mean and variance."""
         m = self.m
         L = np.zeros((m, m)); a = np.zeros(m); vy = np.zeros(m); mo = np.zeros(m); vo = np.zeros(m)
         lib().or_model_get(self._h, L.ctypes.data, a.ctypes.data, vy.ctypes.data, mo.ctypes.data, vo.ctypes.data)
@@ -247,8 +270,12 @@ class Model:
         return field, leaves, levels
 
     def lcp_grad(self, n, theta, weights, c0=(0, 0, 0), c1=None, n_samples=1600, seed=0, tau=1e-4, skip_eps=1e-9):
-        """Gradient of sum_c weights[c] LCP_c over cells [c0, c1) wrt y and log length scales.
+        """Gradient of sum_c weights[c] LCP_c over cells [c0, c1) wrt y and log length scales;
+        `weights` is indexed by the linear cell index of the whole grid (one per grid cell).
         Returns (loss, dL/dy, dL/dlog l)."""
+        weights = np.ascontiguousarray(weights, np.float64)
+        if weights.size != int(np.prod([v - 1 for v in (n, n, n)])):
+            raise ValueError("lcp_grad: one weight per cell of the whole grid")
         g = grid(n)
         if c1 is None:
             c1 = tuple(int(v) - 1 for v in g.n)

@@ -49,6 +49,11 @@ typedef struct {
     double *alpha;  /* Kt^-1 y */
     double *mu_obs; /* latent posterior mean at the observations */
     double *var_obs;/* latent posterior variance at the observations */
+    /* SGPR model (Eq. 1 with a stored inducing distribution N(mu_M, A_M)); 0 for plain GPR.
+     * Then L is the Cholesky factor of K_MM (+ jitter I), alpha = K_MM^-1 mu_M, y = mu_M,
+     * and mu_obs / var_obs are mu_M and diag(A_M). */
+    int sgpr;
+    double *A;      /* m x m A_M */
 } or_model;
 
 /* ------------------------------------------------------------------ kernel */
@@ -143,7 +148,7 @@ void or_model_destroy(or_model *M)
 {
     if (!M) return;
     free(M->X); free(M->y); free(M->L); free(M->Linv); free(M->vy); free(M->alpha);
-    free(M->mu_obs); free(M->var_obs);
+    free(M->mu_obs); free(M->var_obs); free(M->A);
     free(M);
 }
 
@@ -196,6 +201,62 @@ or_model *or_model_create(const double *X, const double *y, int64_t m, int kerne
     return M;
 }
 
+/* SGPR model (Sec. 3): inducing sites X (m x 3) with the stored distribution N(mu_M, A_M) of
+ * their values.  K_MM = K(X, X) + jitter I is factorised once; Eq. 1 is evaluated as printed by
+ * the sgpr_* helpers below.  Algorithm 1's p-test reads the inducing distribution itself
+ * (Sec. 5.3: mean vector mu_M and covariance A_M of the inducing points in the node), so
+ * mu_obs = mu_M and var_obs = diag(A_M) (floor 1e-12 sf2).  NULL if K_MM is not PD. */
+or_model *or_model_create_sgpr(const double *X, const double *muM, const double *AM, int64_t m, int kernel,
+                               const double *ell, double sf2, double jitter)
+{
+    or_model *M = (or_model *)calloc(1, sizeof(or_model));
+    M->m = m; M->kernel = kernel; M->sf2 = sf2; M->sn2 = 0.0; M->sgpr = 1;
+    for (int d = 0; d < 3; ++d) M->ell[d] = ell[d];
+    M->X = (double *)malloc(sizeof(double) * 3 * m);
+    M->y = (double *)malloc(sizeof(double) * m);
+    M->A = (double *)malloc(sizeof(double) * m * m);
+    memcpy(M->X, X, sizeof(double) * 3 * m);
+    memcpy(M->y, muM, sizeof(double) * m);
+    memcpy(M->A, AM, sizeof(double) * m * m);
+    M->L = (double *)malloc(sizeof(double) * m * m);
+    for (int64_t i = 0; i < m; ++i)
+        for (int64_t j = 0; j < m; ++j)
+            M->L[i * m + j] = or_kernel_eval(kernel, ell, sf2, X + 3 * i, X + 3 * j) + (i == j ? jitter : 0.0);
+    if (or_cholesky(M->L, m) != 0) { or_model_destroy(M); return NULL; }
+    M->vy = (double *)malloc(sizeof(double) * m);
+    M->alpha = (double *)malloc(sizeof(double) * m);
+    fwd_sub(M->L, m, muM, M->vy);
+    back_sub_T(M->L, m, M->vy, M->alpha);
+    M->mu_obs = (double *)malloc(sizeof(double) * m);
+    M->var_obs = (double *)malloc(sizeof(double) * m);
+    for (int64_t i = 0; i < m; ++i) {
+        double fl = 1e-12 * sf2, v = AM[i * m + i];
+        M->mu_obs[i] = muM[i];
+        M->var_obs[i] = v > fl ? v : fl;
+    }
+    return M;
+}
+
+/* Eq. 1 pieces of one point x for an SGPR model: k = K_MI column of x, a = K_MM^-1 k,
+ * c = A_M a.  Then mu(x) = a . mu_M, Sigma(x, z) = k(x, z) - k_x . a_z + a_x . c_z. */
+static void sgpr_row(const or_model *M, const double *x, double *k, double *a, double *c, double *tmp)
+{
+    int64_t m = M->m;
+    for (int64_t j = 0; j < m; ++j) k[j] = or_kernel_eval(M->kernel, M->ell, M->sf2, x, M->X + 3 * j);
+    fwd_sub(M->L, m, k, tmp);
+    back_sub_T(M->L, m, tmp, a);
+    for (int64_t i = 0; i < m; ++i) c[i] = dot(M->A + i * m, a, m);
+}
+
+/* Sigma(x_a, x_b) of Eq. 1 from the pieces of sgpr_row: k(x_a, x_b) - K_aM K_MM^-1 K_Mb
+ * + K_aM K_MM^-1 A_M K_MM^-1 K_Mb = k(a, b) - k_a . a_b + a_a . c_b. */
+static double sgpr_cov(const or_model *M, const double *xa, const double *xb, const double *ka, const double *aa,
+                       const double *ab, const double *cb)
+{
+    int64_t m = M->m;
+    return or_kernel_eval(M->kernel, M->ell, M->sf2, xa, xb) - dot(ka, ab, m) + dot(aa, cb, m);
+}
+
 void or_model_get(const or_model *M, double *L, double *alpha, double *vy, double *mu_obs, double *var_obs)
 {
     int64_t m = M->m;
@@ -218,6 +279,21 @@ static void whiten_row(const or_model *M, const double *x, double *kbuf, double 
 void or_posterior(const or_model *M, const double *P, int64_t n, double *mu, double *var, double *cov)
 {
     int64_t m = M->m;
+    if (M->sgpr) { /* Eq. 1 as printed */
+        double *K = (double *)malloc(sizeof(double) * n * m), *A = (double *)malloc(sizeof(double) * n * m);
+        double *Cr = (double *)malloc(sizeof(double) * n * m), *tmp = (double *)malloc(sizeof(double) * m);
+        for (int64_t a = 0; a < n; ++a) {
+            sgpr_row(M, P + 3 * a, K + a * m, A + a * m, Cr + a * m, tmp);
+            mu[a] = dot(A + a * m, M->y, m);
+            var[a] = sgpr_cov(M, P + 3 * a, P + 3 * a, K + a * m, A + a * m, A + a * m, Cr + a * m);
+        }
+        if (cov)
+            for (int64_t a = 0; a < n; ++a)
+                for (int64_t b = 0; b < n; ++b)
+                    cov[a * n + b] = sgpr_cov(M, P + 3 * a, P + 3 * b, K + a * m, A + a * m, A + b * m, Cr + b * m);
+        free(K); free(A); free(Cr); free(tmp);
+        return;
+    }
     double *V = (double *)malloc(sizeof(double) * n * m);
 #pragma omp parallel
     {
@@ -508,8 +584,12 @@ static const int OFF13[13][3] = {
  * out[p*15 + 0] = mu, [1] = var, [2+e] = cov(p, p+OFF13[e]) (NaN off-grid).
  * Points are ordered x-fastest inside the box.  Whitened rows are computed for
  * the box grown by one point on each side. */
+static void sgpr_stats15_block(const or_model *M, const or_grid *g, const int64_t *i0, const int64_t *i1,
+                               double *out);
+
 void or_stats15_block(const or_model *M, const or_grid *g, const int64_t *i0, const int64_t *i1, double *out)
 {
+    if (M->sgpr) { sgpr_stats15_block(M, g, i0, i1, out); return; }
     int64_t m = M->m;
     int64_t e0[3], e1[3], en[3];
     for (int d = 0; d < 3; ++d) {
@@ -551,6 +631,57 @@ void or_stats15_block(const or_model *M, const or_grid *g, const int64_t *i0, co
     free(V);
 }
 
+/* or_stats15_block for an SGPR model: Eq. 1 as printed, from the rows (k, K_MM^-1 k, A_M K_MM^-1 k)
+ * of the box grown by one point on each side. */
+static void sgpr_stats15_block(const or_model *M, const or_grid *g, const int64_t *i0, const int64_t *i1,
+                               double *out)
+{
+    int64_t m = M->m;
+    int64_t e0[3], e1[3], en[3];
+    for (int d = 0; d < 3; ++d) {
+        e0[d] = i0[d] > 0 ? i0[d] - 1 : 0;
+        e1[d] = i1[d] < g->n[d] ? i1[d] + 1 : g->n[d];
+        en[d] = e1[d] - e0[d];
+    }
+    int64_t ne = en[0] * en[1] * en[2];
+    double *K = (double *)malloc(sizeof(double) * ne * m), *A = (double *)malloc(sizeof(double) * ne * m);
+    double *Cr = (double *)malloc(sizeof(double) * ne * m);
+#pragma omp parallel
+    {
+        double *tmp = (double *)malloc(sizeof(double) * m);
+#pragma omp for schedule(static)
+        for (int64_t q = 0; q < ne; ++q) {
+            int64_t a = e0[0] + q % en[0], b = e0[1] + (q / en[0]) % en[1], c = e0[2] + q / (en[0] * en[1]);
+            double x[3] = {grid_x(g, 0, a), grid_x(g, 1, b), grid_x(g, 2, c)};
+            sgpr_row(M, x, K + q * m, A + q * m, Cr + q * m, tmp);
+        }
+        free(tmp);
+    }
+    int64_t bn[3] = {i1[0] - i0[0], i1[1] - i0[1], i1[2] - i0[2]};
+    int64_t nb = bn[0] * bn[1] * bn[2];
+#pragma omp parallel for schedule(static)
+    for (int64_t p = 0; p < nb; ++p) {
+        int64_t a = i0[0] + p % bn[0], b = i0[1] + (p / bn[0]) % bn[1], c = i0[2] + p / (bn[0] * bn[1]);
+        int64_t q = (a - e0[0]) + en[0] * ((b - e0[1]) + en[1] * (c - e0[2]));
+        double x[3] = {grid_x(g, 0, a), grid_x(g, 1, b), grid_x(g, 2, c)};
+        double *o = out + p * 15;
+        o[0] = dot(A + q * m, M->y, m);
+        o[1] = sgpr_cov(M, x, x, K + q * m, A + q * m, A + q * m, Cr + q * m);
+        for (int e = 0; e < 13; ++e) {
+            int64_t a2 = a + OFF13[e][0], b2 = b + OFF13[e][1], c2 = c + OFF13[e][2];
+            if (a2 < 0 || b2 < 0 || c2 < 0 || a2 >= g->n[0] || b2 >= g->n[1] || c2 >= g->n[2]) { o[2 + e] = NAN; continue; }
+            int64_t q2 = (a2 - e0[0]) + en[0] * ((b2 - e0[1]) + en[1] * (c2 - e0[2]));
+            double x2[3] = {grid_x(g, 0, a2), grid_x(g, 1, b2), grid_x(g, 2, c2)};
+            o[2 + e] = sgpr_cov(M, x, x2, K + q * m, A + q * m, A + q2 * m, Cr + q2 * m);
+        }
+    }
+    free(K); free(A); free(Cr);
+}
+
+/* or_lcp_block for an SGPR model: the corners' (mu_8, Sigma_8) from Eq. 1 as printed. */
+static void sgpr_lcp_block(const or_model *M, const or_grid *g, double theta, int est, int64_t N, uint64_t seed,
+                           double tau, double skip_eps, const int64_t *c0, const int64_t *c1, double *out);
+
 /* LCP of the cells whose min-corner index lies in the box [c0, c1), written
  * x-fastest inside the box.  The 8x8 corner covariance of each cell is formed
  * directly as K_88 - V_8 V_8^T from the corners' whitened rows (Sec. 4, the
@@ -559,6 +690,7 @@ void or_stats15_block(const or_model *M, const or_grid *g, const int64_t *i0, co
 void or_lcp_block(const or_model *M, const or_grid *g, double theta, int est, int64_t N, uint64_t seed,
                   double tau, double skip_eps, const int64_t *c0, const int64_t *c1, double *out)
 {
+    if (M->sgpr) { sgpr_lcp_block(M, g, theta, est, N, seed, tau, skip_eps, c0, c1, out); return; }
     int64_t m = M->m;
     int64_t pn[3];
     for (int d = 0; d < 3; ++d) pn[d] = c1[d] - c0[d] + 1;
@@ -600,6 +732,51 @@ void or_lcp_block(const or_model *M, const or_grid *g, double theta, int est, in
     free(V);
 }
 
+static void sgpr_lcp_block(const or_model *M, const or_grid *g, double theta, int est, int64_t N, uint64_t seed,
+                           double tau, double skip_eps, const int64_t *c0, const int64_t *c1, double *out)
+{
+    int64_t m = M->m;
+    int64_t pn[3];
+    for (int d = 0; d < 3; ++d) pn[d] = c1[d] - c0[d] + 1;
+    int64_t np = pn[0] * pn[1] * pn[2];
+    double *K = (double *)malloc(sizeof(double) * np * m), *A = (double *)malloc(sizeof(double) * np * m);
+    double *Cr = (double *)malloc(sizeof(double) * np * m);
+#pragma omp parallel
+    {
+        double *tmp = (double *)malloc(sizeof(double) * m);
+#pragma omp for schedule(static)
+        for (int64_t q = 0; q < np; ++q) {
+            int64_t a = c0[0] + q % pn[0], b = c0[1] + (q / pn[0]) % pn[1], c = c0[2] + q / (pn[0] * pn[1]);
+            double x[3] = {grid_x(g, 0, a), grid_x(g, 1, b), grid_x(g, 2, c)};
+            sgpr_row(M, x, K + q * m, A + q * m, Cr + q * m, tmp);
+        }
+        free(tmp);
+    }
+    int64_t cn[3] = {c1[0] - c0[0], c1[1] - c0[1], c1[2] - c0[2]};
+    int64_t nc = cn[0] * cn[1] * cn[2];
+    int64_t gc[3] = {g->n[0] - 1, g->n[1] - 1, g->n[2] - 1};
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t p = 0; p < nc; ++p) {
+        int64_t a = c0[0] + p % cn[0], b = c0[1] + (p / cn[0]) % cn[1], c = c0[2] + p / (cn[0] * cn[1]);
+        int64_t q[8];
+        double x[8][3], mu[8], S[64];
+        for (int cc = 0; cc < 8; ++cc) {
+            int bx = cc & 1, by = (cc >> 1) & 1, bz = (cc >> 2) & 1;
+            q[cc] = (a + bx - c0[0]) + pn[0] * ((b + by - c0[1]) + pn[1] * (c + bz - c0[2]));
+            x[cc][0] = grid_x(g, 0, a + bx); x[cc][1] = grid_x(g, 1, b + by); x[cc][2] = grid_x(g, 2, c + bz);
+            mu[cc] = dot(A + q[cc] * m, M->y, m);
+        }
+        for (int i = 0; i < 8; ++i)
+            for (int j = 0; j <= i; ++j) {
+                double s = sgpr_cov(M, x[i], x[j], K + q[i] * m, A + q[i] * m, A + q[j] * m, Cr + q[j] * m);
+                S[i * 8 + j] = s; S[j * 8 + i] = s;
+            }
+        uint64_t cell = (uint64_t)(a + gc[0] * (b + gc[1] * c));
+        out[p] = or_cell_lcp(8, mu, S, theta, est, N, seed, cell, tau, skip_eps);
+    }
+    free(K); free(A); free(Cr);
+}
+
 /* ---------------------------------------------------- regional bound, octree */
 
 /* g(x) = side * (theta - mu(x)) / sigma(x) and its gradient; side = +1 gives
@@ -609,13 +786,30 @@ static double eval_g(const or_model *M, const double *x, double theta, int side,
 {
     int64_t m = M->m;
     for (int64_t j = 0; j < m; ++j) kernel_grad(M->kernel, M->ell, M->sf2, x, M->X + 3 * j, kb + j, dk + 3 * j);
-    fwd_sub(M->L, m, kb, v);
-    double mu = dot(v, M->vy, m);
-    double var = or_kernel_eval(M->kernel, M->ell, M->sf2, x, x) - dot(v, v, m);
+    double mu, var;
+    if (M->sgpr) {
+        /* Eq. 1: mu = k^T K_MM^-1 mu_M; var = k(x,x) - k^T a + a^T A_M a with a = K_MM^-1 k;
+         * d var / dx = -2 (dk)^T (a - K_MM^-1 A_M a), so P = a - K_MM^-1 A_M a plays the role of
+         * Kt^-1 k below. */
+        double *a = (double *)malloc(sizeof(double) * m), *c = (double *)malloc(sizeof(double) * m);
+        fwd_sub(M->L, m, kb, v);
+        back_sub_T(M->L, m, v, a);
+        for (int64_t i = 0; i < m; ++i) c[i] = dot(M->A + i * m, a, m);
+        mu = dot(a, M->y, m);
+        var = or_kernel_eval(M->kernel, M->ell, M->sf2, x, x) - dot(kb, a, m) + dot(a, c, m);
+        fwd_sub(M->L, m, c, v);
+        back_sub_T(M->L, m, v, P);
+        for (int64_t j = 0; j < m; ++j) P[j] = a[j] - P[j];
+        free(a); free(c);
+    } else {
+        fwd_sub(M->L, m, kb, v);
+        mu = dot(v, M->vy, m);
+        var = or_kernel_eval(M->kernel, M->ell, M->sf2, x, x) - dot(v, v, m);
+    }
     double fl = 1e-12 * M->sf2;
     if (!(var > fl)) var = fl;
     double sd = sqrt(var);
-    back_sub_T(M->L, m, v, P); /* P = Kt^-1 k */
+    if (!M->sgpr) back_sub_T(M->L, m, v, P); /* P = Kt^-1 k */
     double gmu[3] = {0, 0, 0}, gvar[3] = {0, 0, 0};
     for (int64_t j = 0; j < m; ++j)
         for (int d = 0; d < 3; ++d) {
@@ -970,6 +1164,7 @@ double or_lcp_grad_block(const or_model *M, const or_grid *g, double theta, int6
                          double skip_eps, const double *weights, const int64_t *c0, const int64_t *c1, double *dy,
                          double *dlogl)
 {
+    if (M->sgpr) return NAN; /* the gradient is written for plain GPR only */
     int64_t m = M->m;
     int64_t pn[3];
     for (int d = 0; d < 3; ++d) pn[d] = c1[d] - c0[d] + 1;

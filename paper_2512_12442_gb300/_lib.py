@@ -59,6 +59,7 @@ SIGNATURES = {
     "gpr_profile_enable": (None, [C.c_int]),
     "gpr_profile_reset": (None, []),
     "gpr_profile_read": (C.c_int, [C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
+    "gpr_profile_units": (C.c_int, [C.c_char_p, C.POINTER(C.c_double)]),
     "gpr_launch_count": (C.c_int64, []),
     "gpr_autotune_table": (C.c_int64, [C.c_char_p, C.c_int64]),
     "gpr_autotune_clear": (None, []),

@@ -264,6 +264,13 @@ def gpr_profile_read(name: str):
     return t.value, n.value
 
 
+def gpr_profile_units(name: str) -> float:
+    """Work units (rows, points, estimator orthants) behind the recorded time of `name`."""
+    u = C.c_double()
+    load().gpr_profile_units(name.encode(), C.byref(u))
+    return u.value
+
+
 def gpr_autotune_table() -> dict:
     """The autotuner's choices: {(kernel, bucket): choice}."""
     lib = load()

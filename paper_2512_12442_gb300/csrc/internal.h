@@ -330,12 +330,18 @@ gpr_status lcp_from_kept_cells(gpr_model *M, const GridDev &g, const double *T64
 
 // ---- tracing (profile.cu)
 void note_launch(int n = 1);
-// RAII scope: records CUDA events around the enclosed launches when profiling is on.
+// RAII scope: records CUDA events around the enclosed launches when profiling is on, and adds
+// `units` (rows, points: the work the launches process) to the scope's total.
 struct ProfScope {
     const char *name;
     cudaStream_t st;
     bool active;
+    double units;
     void *a = nullptr, *b = nullptr;
-    ProfScope(const char *name, cudaStream_t st);
+    ProfScope(const char *name, cudaStream_t st, double units = 0.0);
     ~ProfScope();
 };
+// Device-side work counters of the tracer (a module global per device, no allocation): nullptr
+// unless profiling is on.  Counter 0: orthants queued for the estimator (1 or 2 per cell record).
+enum { PROF_CTR_ORTHANTS = 0, PROF_NCTR = 4 };
+unsigned long long *prof_counter(int which);

@@ -49,7 +49,7 @@ __device__ __forceinline__ int tri(int i, int j) { return i * (i + 1) / 2 + j; }
 __global__ void k_cell_prep(GridDev g, const double *stats, const int32_t *slot, const int64_t *cells,
                             int64_t count, double theta, double tau, double skip_eps, PairTable pt, float *lcp,
                             bool by_pos, CellRec *recs, unsigned long long *nrec, unsigned long long *nown,
-                            int *status)
+                            int *status, unsigned long long *orth_ctr)
 {
     int64_t pos = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     bool active = pos < count;
@@ -143,6 +143,11 @@ __global__ void k_cell_prep(GridDev g, const double *stats, const int32_t *slot,
     // warp-aggregated append of the cells that need the estimator
     unsigned mask = __ballot_sync(0xffffffffu, need);
     if (!mask) return;
+    if (orth_ctr) {  // tracing: orthants the estimator will integrate (the Frechet test drops some)
+        const unsigned no = need ? 2u - (unsigned)__popcll((unsigned long long)(r.cell >> 56) & 3ull) : 0u;
+        const unsigned tot = __reduce_add_sync(0xffffffffu, no);
+        if ((threadIdx.x & 31) == 0 && tot) atomicAdd(orth_ctr, (unsigned long long)tot);
+    }
     int lane = threadIdx.x & 31, leader = __ffs(mask) - 1;
     unsigned long long base = 0;
     if (lane == leader) {
@@ -422,7 +427,8 @@ gpr_status run_cell_lcp(const GridDev &g, const double *stats, const int32_t *sl
         ProfScope _ps("cell_prep", st);
         k_cell_prep<<<(unsigned)((count + 127) / 128), 128, 0, st>>>(
             g, stats, slot, cells, count, o.theta, o.tau, o.skip_eps, pt, lcp, by_pos,
-            to_sink ? (CellRec *)sink->recs : recs, to_sink ? sink->nrec : nrec, to_sink ? nrec : nullptr, status);
+            to_sink ? (CellRec *)sink->recs : recs, to_sink ? sink->nrec : nrec, to_sink ? nrec : nullptr, status,
+            prof_counter(PROF_CTR_ORTHANTS));
     }
     note_launch();
     GPR_CUDA_TRY(cudaGetLastError());
@@ -710,7 +716,7 @@ gpr_status run_cell_lcp_on_scratch(const GridDev &g, const double *stats, const 
     static PairTable pt = make_pair_table();
     k_cell_prep<<<(unsigned)((count + 127) / 128), 128, 0, st>>>(g, stats, nullptr, cells, count, o.theta, o.tau,
                                                                  o.skip_eps, pt, lcp, by_pos, recs, nrec, nullptr,
-                                                                 status);
+                                                                 status, nullptr);
     note_launch();
     GPR_CUDA_TRY(cudaGetLastError());
     int64_t blocks = (count + 7) / 8;

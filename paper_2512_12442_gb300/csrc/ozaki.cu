@@ -992,7 +992,7 @@ gpr_status launch_oz_w(const gpr_model *M, const GridDev &g, const float2 *Tu, c
         prm.out_off = c0;
         const int64_t nthr = cnt * (O->mpt / 8);
         {
-            ProfScope ps("oz_adig", st);
+            ProfScope ps("oz_adig", st, (double)cnt);
             k_oz_adig<<<(unsigned)((nthr + 255) / 256), 256, 0, st>>>(prm, (__nv_bfloat16 *)buf->p);
         }
         note_launch();
@@ -1009,7 +1009,7 @@ gpr_status launch_oz_w(const gpr_model *M, const GridDev &g, const float2 *Tu, c
         }
         dim3 grid((unsigned)(M->mp / TN), (unsigned)((cnt + TM - 1) / TM));  // row tiles < 65536 per chunk
         {
-            ProfScope ps("oz_w", st);
+            ProfScope ps("oz_w", st, (double)cnt);
             k_oz_gemm<S><<<grid, G_NTHR, smem, st>>>(mapA, O->map, prm);
         }
         note_launch();
@@ -1034,7 +1034,7 @@ gpr_status launch_stats_ff(const gpr_model *M, const GridDev &g, const int64_t *
         pr.k[e] = M->kp.sf2 * exp(-0.5 * r2);
     }
     {
-        ProfScope ps("stats_ff", st);
+        ProfScope ps("stats_ff", st, (double)count);
         k_stats_ff<<<(unsigned)((count + 7) / 8), 256, 0, st>>>(g, pts, count, slot, W, M->mp, M->m, M->oz->vyff,
                                                               M->kp.sf2, pr, out15, out_by_point ? 1 : 0,
                                                               row_mod > 0 ? row_mod : g.npts());

@@ -1,6 +1,8 @@
 // Phase timing and launch counting (tracing support): when enabled, CUDA events are
 // recorded on the launching stream around each instrumented kernel, and launches of the
 // library's own kernels are counted.
+#include <string.h>
+
 #include <map>
 #include <mutex>
 #include <string>
@@ -12,11 +14,17 @@ namespace {
 struct Rec {
     std::string name;
     cudaEvent_t a, b;
+    double units;
+};
+struct Total {
+    double ms = 0.0;
+    int64_t count = 0;
+    double units = 0.0;
 };
 std::mutex mu;
 bool enabled = false;
 std::vector<Rec> pending;
-std::map<std::string, std::pair<double, int64_t>> totals;
+std::map<std::string, Total> totals;
 long long launches = 0;
 std::vector<cudaEvent_t> pool;
 
@@ -39,14 +47,38 @@ void drain()
         float ms = 0.f;
         cudaEventElapsedTime(&ms, r.a, r.b);
         auto &t = totals[r.name];
-        t.first += ms;
-        t.second += 1;
+        t.ms += ms;
+        t.count += 1;
+        t.units += r.units;
         pool.push_back(r.a);
         pool.push_back(r.b);
     }
     pending.clear();
 }
+constexpr int kMaxDev = 128;
+__device__ unsigned long long g_prof_ctr[PROF_NCTR];
+unsigned long long *g_ctr_addr[kMaxDev] = {nullptr};
+
+unsigned long long *ctr_base(bool create)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) return nullptr;
+    if (!g_ctr_addr[dev] && create) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_prof_ctr) != cudaSuccess) return nullptr;
+        g_ctr_addr[dev] = (unsigned long long *)p;
+    }
+    return g_ctr_addr[dev];
+}
 }  // namespace
+
+unsigned long long *prof_counter(int which)
+{
+    std::lock_guard<std::mutex> g(mu);
+    if (!enabled || which < 0 || which >= PROF_NCTR) return nullptr;
+    unsigned long long *b = ctr_base(true);
+    return b ? b + which : nullptr;
+}
 
 void note_launch(int n)
 {
@@ -54,7 +86,8 @@ void note_launch(int n)
     launches += n;
 }
 
-ProfScope::ProfScope(const char *name_, cudaStream_t st_) : name(name_), st(st_), active(false)
+ProfScope::ProfScope(const char *name_, cudaStream_t st_, double units_)
+    : name(name_), st(st_), active(false), units(units_)
 {
     std::lock_guard<std::mutex> g(mu);
     if (!enabled) return;
@@ -69,7 +102,7 @@ ProfScope::~ProfScope()
     if (!active) return;
     std::lock_guard<std::mutex> g(mu);
     cudaEventRecord((cudaEvent_t)b, st);
-    pending.push_back(Rec{name, (cudaEvent_t)a, (cudaEvent_t)b});
+    pending.push_back(Rec{name, (cudaEvent_t)a, (cudaEvent_t)b, units});
     if (pending.size() > 4096) drain();
 }
 
@@ -85,6 +118,12 @@ extern "C" void gpr_profile_reset(void)
     drain();
     totals.clear();
     launches = 0;
+    unsigned long long *b = ctr_base(false);
+    if (b) {
+        cudaDeviceSynchronize();
+        cudaMemset(b, 0, sizeof(unsigned long long) * PROF_NCTR);
+        cudaDeviceSynchronize();
+    }
 }
 
 extern "C" int gpr_profile_read(const char *name, double *total_ms, int64_t *count)
@@ -97,8 +136,31 @@ extern "C" int gpr_profile_read(const char *name, double *total_ms, int64_t *cou
         if (count) *count = 0;
         return 0;
     }
-    if (total_ms) *total_ms = it->second.first;
-    if (count) *count = it->second.second;
+    if (total_ms) *total_ms = it->second.ms;
+    if (count) *count = it->second.count;
+    return 1;
+}
+
+extern "C" int gpr_profile_units(const char *name, double *units)
+{
+    if (units) *units = 0.0;
+    if (!name) return 0;
+    if (strcmp(name, "sov_orthants") == 0) {
+        std::lock_guard<std::mutex> g(mu);
+        unsigned long long *b = ctr_base(false);
+        if (!b) return 0;
+        unsigned long long h = 0;
+        if (cudaDeviceSynchronize() != cudaSuccess ||
+            cudaMemcpy(&h, b + PROF_CTR_ORTHANTS, sizeof h, cudaMemcpyDeviceToHost) != cudaSuccess)
+            return 0;
+        if (units) *units = (double)h;
+        return 1;
+    }
+    std::lock_guard<std::mutex> g(mu);
+    drain();
+    auto it = totals.find(name);
+    if (it == totals.end()) return 0;
+    if (units) *units = it->second.units;
     return 1;
 }
 

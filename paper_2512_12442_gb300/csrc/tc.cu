@@ -605,11 +605,11 @@ gpr_status launch_tc(const gpr_model *M, const TcParams &prm, cudaStream_t st)
     dim3 grid((unsigned)((prm.count + TM - 1) / TM), (unsigned)(B.mpt / N));
     if (WS) {
         GPR_CUDA_TRY(cudaFuncSetAttribute(k_tc_sumsq_ws<P, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        ProfScope ps("tc_sumsq", st);
+        ProfScope ps("tc_sumsq", st, (double)prm.count);
         k_tc_sumsq_ws<P, N><<<grid, WS_NTHR, smem, st>>>(maps[0], maps[1], maps[2], prm);
     } else {
         GPR_CUDA_TRY(cudaFuncSetAttribute(k_tc_sumsq<P, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        ProfScope ps("tc_sumsq", st);
+        ProfScope ps("tc_sumsq", st, (double)prm.count);
         k_tc_sumsq<P, N><<<grid, NTHR, smem, st>>>(maps[0], maps[1], maps[2], prm);
     }
     note_launch();

@@ -93,8 +93,7 @@ def test_backward_config5_grid128_subgrid_vs_oracle(torch, g):
     mask[c0[2]:c1[2], c0[1]:c1[1], c0[0]:c1[0]] = 1.0
     wts = (wfull * mask).reshape(-1)
     dy, dl = _gpu_grad(g, torch, w, n, th, wts)
-    sub = wfull[c0[2]:c1[2], c0[1]:c1[1], c0[0]:c1[0]].reshape(-1)
-    loss, ody, odl = oracle.Model.from_workload(w).lcp_grad(n, th, sub, c0=c0, c1=c1)
+    loss, ody, odl = oracle.Model.from_workload(w).lcp_grad(n, th, wts, c0=c0, c1=c1)
     assert loss > 0.0
     _check_entries(dy, dl, ody, odl)
 

@@ -146,6 +146,72 @@ def test_sgpr_equation1_reduces_to_plain_gpr():
     np.testing.assert_allclose(f["var_obs"], np.maximum(np.diag(AM), 1e-12), rtol=1e-6, atol=1e-12)
 
 
+def _se_np(A, B, ell):
+    d = (A[:, None, :] - B[None, :, :]) / np.asarray(ell, float)
+    return np.exp(-0.5 * (d ** 2).sum(-1))
+
+
+def test_sgpr_model_with_exact_inducing_distribution_equals_plain_gpr():
+    """An SGPR model (Eq. 1 with a stored N(mu_M, A_M)) whose inducing points are the observations
+    and whose distribution is their exact latent posterior (mu_M = K Kt^-1 y, A_M = K - K Kt^-1 K,
+    computed here with a dense NumPy solve) reproduces the plain GPR model: the 15 per-point
+    statistics, the cell LCP, and the p-test inputs (Sec. 5.3: mu_M and diag A_M)."""
+    rng = np.random.default_rng(12)
+    X = rng.random((24, 3)); y = rng.standard_normal(24)
+    ell, sn2 = (0.3, 0.35, 0.4), 1e-2
+    K = _se_np(X, X, ell); Kt = K + sn2 * np.eye(24)
+    muM = K @ np.linalg.solve(Kt, y); AM = K - K @ np.linalg.solve(Kt, K); AM = 0.5 * (AM + AM.T)
+    plain = oracle.Model(X, y, oracle.SE, ell, 1.0, sn2)
+    sg = oracle.Model.sgpr(X, muM, AM, oracle.SE, ell, 1.0, 0.0)
+    a = sg.stats15(7); b = plain.stats15(7)
+    ok = ~np.isnan(b)
+    assert np.array_equal(ok, ~np.isnan(a))
+    np.testing.assert_allclose(a[ok], b[ok], rtol=1e-7, atol=1e-9)
+    th = float(np.median(y))
+    np.testing.assert_allclose(sg.lcp_dense(7, th), plain.lcp_dense(7, th), atol=1e-7)
+    f = sg.factors()
+    np.testing.assert_array_equal(f["mu_obs"], muM)
+    np.testing.assert_array_equal(f["var_obs"], np.maximum(np.diag(AM), 1e-12))
+
+
+def test_sgpr_terms_special_cases():
+    """Each term of Eq. 1 in isolation (jitter 0): with A_M = 0 the inducing values are known, so the
+    posterior interpolates them (mu(x_i) = mu_M,i, var(x_i) = 0: the second term cancels the prior);
+    with A_M = K_MM and mu_M = 0 they carry no information, so the posterior is the prior
+    (mu = 0, Sigma = K_II: the third term cancels the second)."""
+    rng = np.random.default_rng(13)
+    X = rng.random((12, 3)); ell = (0.35, 0.35, 0.35)
+    K = _se_np(X, X, ell)
+    muM = rng.standard_normal(12)
+    known = oracle.Model.sgpr(X, muM, np.zeros((12, 12)), oracle.SE, ell, 1.0, 0.0)
+    mu, var = known.posterior(X)
+    np.testing.assert_allclose(mu, muM, rtol=1e-8, atol=1e-9)
+    np.testing.assert_allclose(var, 0.0, atol=1e-8)
+    blind = oracle.Model.sgpr(X, np.zeros(12), K, oracle.SE, ell, 1.0, 0.0)
+    P = rng.random((6, 3))
+    mu, var, cov = blind.posterior(P, full_cov=True)
+    np.testing.assert_allclose(mu, 0.0, atol=1e-12)
+    np.testing.assert_allclose(cov, _se_np(P, P, ell), atol=1e-8)
+
+
+def test_sgpr_bound_gradient_matches_finite_differences():
+    """The regional bound's g = side (theta - mu) / sigma on an SGPR model: its gradient (through
+    Eq. 1: d mu = dk^T K_MM^-1 mu_M, d var = -2 dk^T (K_MM^-1 k - K_MM^-1 A_M K_MM^-1 k)) against central
+    differences, and g against the posterior at the point."""
+    w = workloads.sgpr(seed=3, m=60, n_train=400, n=9)
+    M = oracle.Model.from_workload(w)
+    th = w.isovalues[1]
+    x = np.array([[0.43, 0.31, 0.57]])
+    for side in (1, -1):
+        g, gr = M.eval_g(x, th, side)
+        for d in range(3):
+            e = np.zeros(3); e[d] = 1e-6
+            gp, _ = M.eval_g(x + e, th, side); gm, _ = M.eval_g(x - e, th, side)
+            assert gr[0, d] == pytest.approx((gp[0] - gm[0]) / 2e-6, rel=1e-5, abs=1e-5)
+        mu, var = M.posterior(x)
+        assert g[0] == pytest.approx(side * (th - mu[0]) / math.sqrt(var[0]), rel=1e-12)
+
+
 def test_stats15_match_full_covariance():
     """The 15 per-point stats equal the entries of the joint posterior of the point and its
     13 forward neighbours, and cover every corner pair of a cell."""

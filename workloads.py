@@ -116,6 +116,36 @@ def small(seed: int, m: int, n: int, ell=(0.2, 0.2, 0.2), kernel=SE, sn2=1e-4,
                     [float(np.median(y))], depth_for(n))
 
 
+def _se(A, B, ell, sf2=1.0):
+    d = (A[:, None, :] - B[None, :, :]) / np.asarray(ell, float)
+    return sf2 * np.exp(-0.5 * (d ** 2).sum(-1))
+
+
+def sgpr(seed: int = 6, m: int = 500, n_train: int = 4000, n: int = 128, ell=(0.15, 0.2, 0.25),
+         noise: float = 1e-4, jitter: float = 1e-6) -> Workload:
+    """A fitted sparse GP model (the stored {M, mu_M, A_M} of Sec. 3) on the paper-scale field.
+
+    The paper fits its SGPR models with GPy (out of scope here).  Stand-in: n_train training
+    points of the config-2 field recipe, m inducing sites drawn uniformly, and the inducing
+    distribution that maximises the sparse-GP variational bound (Titsias 2009) for the given
+    kernel and noise: S = (K_MM + K_MN K_NM / noise)^-1, mu_M = K_MM S K_MN y / noise,
+    A_M = K_MM S K_MM, with K_MM = K(M, M) + jitter I.  Draw order: training sites and values (the
+    field recipe), then the inducing sites."""
+    rng = np.random.default_rng(seed)
+    Xn, yn = _field(rng, n_train, 16, -1.0, 1.0, sinusoid=True)
+    Xm = rng.random((m, 3))
+    Kmm = _se(Xm, Xm, ell) + jitter * np.eye(m)
+    Kmn = _se(Xm, Xn, ell)
+    S = np.linalg.inv(Kmm + Kmn @ Kmn.T / noise)
+    S = 0.5 * (S + S.T)
+    mu = Kmm @ (S @ (Kmn @ yn)) / noise
+    A = Kmm @ S @ Kmm
+    A = 0.5 * (A + A.T)
+    th = [float(np.percentile(yn, q)) for q in (25, 50, 75)]
+    return Workload(f"sgpr_m{m}_train{n_train}_grid{n}", Xm, mu, SE, tuple(ell), 1.0, 0.0, n, th, depth_for(n),
+                    extra={"A_M": A, "kmm_jitter": jitter, "train_X": Xn, "train_y": yn, "noise": noise})
+
+
 def grid_points(n: int, lo=0.0, hi=1.0) -> np.ndarray:
     """Grid coordinates x_i = lo + i*(hi-lo)/(n-1), x-fastest order, (n^3, 3)."""
     g = lo + np.arange(n) * ((hi - lo) / (n - 1))
