@@ -64,7 +64,15 @@ typedef enum {
     GPR_P_BF16X3 = 5  /* three bf16 slices, six products */
 } gpr_precision;
 
-typedef enum { GPR_EST_SOV_QMC = 0, GPR_EST_MC = 1 } gpr_estimator;
+/* Cell estimators (Sec. 4 and the alternatives the paper reviews, Sec. 2.2 and Sec. 9):
+ *   GPR_EST_SOV_QMC   the orthant probabilities by sequential conditioning on a lattice
+ *   GPR_EST_MC        the paper's Monte Carlo estimator
+ *   GPR_EST_INDEP     closed form with the corners taken as independent (correlation ignored):
+ *                     1 - prod_c P(Y_c < theta) - prod_c P(Y_c > theta)
+ *   GPR_EST_EDGE_MAX  Pothkow et al.'s approximation: the largest edge-crossing probability
+ *                     1 - P(Y_i < theta, Y_j < theta) - P(Y_i > theta, Y_j > theta) over the 12
+ *                     cell edges, bivariate normal probabilities by Owen's T function */
+typedef enum { GPR_EST_SOV_QMC = 0, GPR_EST_MC = 1, GPR_EST_INDEP = 2, GPR_EST_EDGE_MAX = 3 } gpr_estimator;
 
 /* Arithmetic of the FP64-class reconstruction of the LCP cells' corners.
  * GPR_EXACT_AUTO: BF16 tensor cores with an error-free split of both operands into
@@ -129,6 +137,31 @@ const char *gpr_status_string(gpr_status s);
 gpr_status gpr_model_create(const double *obs_xyz, const double *y, int64_t m, gpr_kernel kernel,
                             const double length_scales[3], double signal_var, double noise_var,
                             void *stream, gpr_model **out);
+
+/*
+ * gpr_model_create_sgpr -- the general stored model of Sec. 3: a sparse GP given by
+ * m inducing sites and the distribution N(mu_M, A_M) of the field values there
+ * (as a fitted SGPR model stores it), whose posterior is Eq. 1:
+ *   mu(x)      = k_xM K_MM^-1 mu_M
+ *   Sigma(a,b) = k(a,b) - k_aM K_MM^-1 k_Mb + k_aM K_MM^-1 A_M K_MM^-1 k_Mb,
+ * with K_MM = K(M, M) + kmm_jitter I.  Built on the device in FP64: the
+ * Cholesky factor of K_MM, alpha = K_MM^-1 mu_M, and the lower-triangular G
+ * with G^T G = K_MM^-1 - K_MM^-1 A_M K_MM^-1 (a Cholesky factorisation in
+ * reversed index order), so that Sigma(a,b) = k(a,b) - (G k_a).(G k_b) and every
+ * other entry point computes Eq. 1 with the same kernels as for plain GPR.
+ * Algorithm 1's p-test (Sec. 5.3) reads mu_M and diag(A_M) directly.
+ *   inducing_xyz  host, m x 3 row-major FP64 sites
+ *   mu_M          host, m FP64;   A_M  host, m x m row-major FP64, symmetric
+ *   kmm_jitter    >= 0 added to the diagonal of K_MM (fitting libraries add one)
+ *   other arguments as gpr_model_create (no noise term: Eq. 1 has none)
+ * Returns GPR_ERR_NOT_PD if K_MM + kmm_jitter I is not positive definite, or if
+ * A_M is not strictly below K_MM (K_MM - A_M must be positive definite, as it is
+ * for any inducing distribution conditioned on data).  gpr_lcp_backward does
+ * not serve these models (GPR_ERR_UNSUPPORTED).  Synchronises `stream`.
+ */
+gpr_status gpr_model_create_sgpr(const double *inducing_xyz, const double *mu_M, const double *A_M, int64_t m,
+                                 gpr_kernel kernel, const double length_scales[3], double signal_var,
+                                 double kmm_jitter, void *stream, gpr_model **out);
 
 /* Frees the model and its workspace (synchronises the device first). */
 gpr_status gpr_model_destroy(gpr_model *model);

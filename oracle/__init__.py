@@ -22,6 +22,8 @@ SE = 0
 MATERN52 = 1
 EST_SOV = 0
 EST_MC = 1
+EST_INDEP = 2
+EST_EDGE = 3
 
 _lib = None
 _dp = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
@@ -72,6 +74,8 @@ def lib():
         L.or_node_min.restype = C.c_double
         L.or_node_min.argtypes = [C.c_void_p, C.POINTER(_Grid), C.c_int, C.c_int, C.c_int64, C.c_double, C.c_int,
                                   C.c_int, _dp, _dp, _dp]
+        L.or_bvn_lower.restype = C.c_double
+        L.or_bvn_lower.argtypes = [C.c_double, C.c_double, C.c_double]
         L.or_num_threads.restype = C.c_int
         L.or_cell_lcp_adj.restype = C.c_double
         L.or_cell_lcp_adj.argtypes = [C.c_int, _dp, _dp, C.c_double, C.c_int64, C.c_uint64, C.c_uint64, C.c_double,
@@ -95,6 +99,12 @@ def kernel(kind, ell, sf2, a, b) -> float:
 
 def norm_cdf(x: float) -> float:
     return lib().or_norm_cdf(float(x))
+
+
+def bvn_lower(a: float, b: float, r: float) -> float:
+    """P(X1 < a, X2 < b) of a standard bivariate normal with correlation r (the edge-crossing
+    probability's building block, Sec. 4's line-segment formula)."""
+    return lib().or_bvn_lower(float(a), float(b), float(r))
 
 
 def norm_ppf(p: float) -> float:

@@ -490,6 +490,50 @@ static void chol_floor(const double *S, int d, double floor_, double *L)
 
 #define EST_SOV 0
 #define EST_MC 1
+#define EST_INDEP 2
+#define EST_EDGE 3
+
+/* P(X1 < a, X2 < b) for a standard bivariate normal with correlation r (|r| < 1): the
+ * integral over x1 < a of phi(x1) P(X2 < b | X1 = x1) = phi(x1) Phi((b - r x1) / sqrt(1 - r^2)),
+ * by adaptive Simpson on [-40, a] (the mass below -40 is under 1e-300). */
+static double bvn_integrand(double t, double b, double r, double s)
+{
+    return exp(-0.5 * t * t) / sqrt(2.0 * M_PI) * or_norm_cdf((b - r * t) / s);
+}
+
+static double simpson_rec(double lo, double hi, double flo, double fmid, double fhi, double whole, double tol,
+                          int depth, double b, double r, double s)
+{
+    double mid = 0.5 * (lo + hi), lm = 0.5 * (lo + mid), rm = 0.5 * (mid + hi);
+    double flm = bvn_integrand(lm, b, r, s), frm = bvn_integrand(rm, b, r, s);
+    double left = (mid - lo) / 6.0 * (flo + 4.0 * flm + fmid), right = (hi - mid) / 6.0 * (fmid + 4.0 * frm + fhi);
+    double diff = left + right - whole;
+    if (depth <= 0 || fabs(diff) <= 15.0 * tol) return left + right + diff / 15.0;
+    return simpson_rec(lo, mid, flo, flm, fmid, left, 0.5 * tol, depth - 1, b, r, s) +
+           simpson_rec(mid, hi, fmid, frm, fhi, right, 0.5 * tol, depth - 1, b, r, s);
+}
+
+double or_bvn_lower(double a, double b, double r)
+{
+    double s = sqrt(1.0 - r * r);
+    double lo = -40.0, hi = a < 40.0 ? a : 40.0;
+    if (!(hi > lo)) return 0.0;
+    /* split at the kink of the conditional CDF (x1 = b / r) so each piece is smooth */
+    double cuts[3] = {lo, hi, hi};
+    int nc = 2;
+    if (r != 0.0) {
+        double k = b / r;
+        if (k > lo && k < hi) { cuts[1] = k; cuts[2] = hi; nc = 3; }
+    }
+    double total = 0.0;
+    for (int i = 0; i + 1 < nc; ++i) {
+        double x0 = cuts[i], x1 = cuts[i + 1];
+        double f0 = bvn_integrand(x0, b, r, s), f1 = bvn_integrand(x1, b, r, s), fm = bvn_integrand(0.5 * (x0 + x1), b, r, s);
+        double whole = (x1 - x0) / 6.0 * (f0 + 4.0 * fm + f1);
+        total += simpson_rec(x0, x1, f0, fm, f1, whole, 1e-15, 50, b, r, s);
+    }
+    return total;
+}
 
 /* Cell level-crossing probability for d corner variables (d = 8 for a cell):
  * LCP = 1 - P(all < theta) - P(all > theta)  (Sec. 4).
@@ -499,7 +543,13 @@ static void chol_floor(const double *S, int d, double floor_, double *L)
  * cell whose largest variance is below 1e-30 is deterministic.
  * est = EST_SOV: shifts of cell `cell` are SplitMix64 outputs 8*cell+i+1, top
  * 32 bits.  est = EST_MC: Philox-4x32-10 with key (seed lo, seed hi) and counter
- * (sample, cell lo, cell hi, r), r = 0,1 giving 8 normals by Box-Muller. */
+ * (sample, cell lo, cell hi, r), r = 0,1 giving 8 normals by Box-Muller.
+ * est = EST_INDEP: the corners taken as independent (the closed forms of the
+ * uncorrelated uncertainty models the paper reviews in Sec. 2.2):
+ * 1 - prod_c P(Y_c < theta) - prod_c P(Y_c > theta).
+ * est = EST_EDGE: Pothkow et al.'s approximation (Sec. 2.2, Sec. 9): the largest
+ * crossing probability 1 - P(Y_i < theta, Y_j < theta) - P(Y_i > theta, Y_j > theta)
+ * over the cell's edges (corner pairs i, j = i ^ 2^a; 12 for d = 8). */
 double or_cell_lcp(int d, const double *mu, const double *S, double theta, int est, int64_t N,
                    uint64_t seed, uint64_t cell, double tau, double skip_eps)
 {
@@ -521,6 +571,29 @@ double or_cell_lcp(int d, const double *mu, const double *S, double theta, int e
         s_below += or_norm_cdf((theta - mu[i]) / sd);
     }
     if (s_above < skip_eps || s_below < skip_eps) return 0.0;
+    if (est == EST_INDEP) {
+        double plo = 1.0, phi = 1.0;
+        for (int i = 0; i < d; ++i) {
+            double sd = sqrt(Sj[i * d + i]);
+            plo *= or_norm_cdf((theta - mu[i]) / sd);
+            phi *= or_norm_cdf((mu[i] - theta) / sd);
+        }
+        return 1.0 - plo - phi;
+    }
+    if (est == EST_EDGE) {
+        double best = 0.0;
+        for (int i = 0; i < d; ++i)
+            for (int a = 0; (1 << a) < d; ++a) {
+                int j = i ^ (1 << a);
+                if (j < i || j >= d) continue;
+                double si = sqrt(Sj[i * d + i]), sj = sqrt(Sj[j * d + j]);
+                double r = Sj[i * d + j] / (si * sj);
+                double zi = (theta - mu[i]) / si, zj = (theta - mu[j]) / sj;
+                double pe = 1.0 - or_bvn_lower(zi, zj, r) - or_bvn_lower(-zi, -zj, r);
+                if (pe > best) best = pe;
+            }
+        return best;
+    }
     chol_floor(Sj, d, 1e-3 * jit, L);
     double p_lo, p_hi;
     if (est == EST_SOV) {

@@ -32,6 +32,8 @@ SIGNATURES = {
     "gpr_status_string": (C.c_char_p, [C.c_int]),
     "gpr_model_create": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int, C.c_void_p, C.c_double,
                                    C.c_double, C.c_void_p, C.POINTER(C.c_void_p)]),
+    "gpr_model_create_sgpr": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int, C.c_void_p,
+                                        C.c_double, C.c_double, C.c_void_p, C.POINTER(C.c_void_p)]),
     "gpr_model_destroy": (C.c_int, [C.c_void_p]),
     "gpr_model_m": (C.c_int64, [C.c_void_p]),
     "gpr_reconstruct_dense": (C.c_int, [C.c_void_p, C.POINTER(GridC), C.c_int, C.c_void_p, C.c_void_p,

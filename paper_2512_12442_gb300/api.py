@@ -12,7 +12,7 @@ from ._lib import AdaptiveStatsC, GridC, LcpOptionsC, load
 
 GPR_K_SE, GPR_K_MATERN52 = 0, 1
 GPR_P_FP64, GPR_P_FP32, GPR_P_TF32, GPR_P_TF32X3, GPR_P_BF16, GPR_P_BF16X3 = range(6)
-GPR_EST_SOV_QMC, GPR_EST_MC = 0, 1
+GPR_EST_SOV_QMC, GPR_EST_MC, GPR_EST_INDEP, GPR_EST_EDGE_MAX = 0, 1, 2, 3
 GPR_EXACT_AUTO, GPR_EXACT_FP64 = 0, 1
 GPR_OK, GPR_ERR_ARG, GPR_ERR_NOT_PD, GPR_ERR_CUDA, GPR_ERR_OOM, GPR_ERR_TIMEOUT, GPR_ERR_UNSUPPORTED = range(7)
 
@@ -103,6 +103,21 @@ def gpr_model_create(obs_xyz, y, kernel=GPR_K_SE, length_scales=(0.2, 0.2, 0.2),
     rc = load().gpr_model_create(X.ctypes.data, yy.ctypes.data, yy.shape[0], int(kernel), ell.ctypes.data,
                                  float(signal_var), float(noise_var), _stream(stream), C.byref(h))
     _check(rc, "gpr_model_create")
+    return Model(h.value)
+
+
+def gpr_model_create_sgpr(inducing_xyz, mu_M, A_M, kernel=GPR_K_SE, length_scales=(0.2, 0.2, 0.2),
+                          signal_var=1.0, kmm_jitter=0.0, stream=None) -> Model:
+    """Sparse-GP model from m inducing sites and their stored distribution N(mu_M, A_M) (Eq. 1)."""
+    X = np.ascontiguousarray(inducing_xyz, np.float64).reshape(-1, 3)
+    mu = np.ascontiguousarray(mu_M, np.float64).reshape(-1)
+    m = mu.shape[0]
+    A = np.ascontiguousarray(A_M, np.float64).reshape(m, m)
+    ell = np.ascontiguousarray(length_scales, np.float64).reshape(3)
+    h = C.c_void_p()
+    rc = load().gpr_model_create_sgpr(X.ctypes.data, mu.ctypes.data, A.ctypes.data, m, int(kernel), ell.ctypes.data,
+                                      float(signal_var), float(kmm_jitter), _stream(stream), C.byref(h))
+    _check(rc, "gpr_model_create_sgpr")
     return Model(h.value)
 
 

@@ -760,6 +760,19 @@ __global__ void k_ff_to_double(const float2 *ff, int64_t n, double *out)
 
 }  // namespace
 
+// Plain FP64 products for the model set-up of other translation units: C = A B or A^T B
+// (row-major, leading dimensions lda/ldb/ldc), no split.
+void gemm64_nn(int64_t M, int64_t N, int64_t K, const double *A, int64_t lda, const double *B, int64_t ldb, double *C,
+               int64_t ldc, cudaStream_t st)
+{
+    gemm64<false, false>(M, N, K, A, lda, B, ldb, C, ldc, 1, st);
+}
+void gemm64_tn(int64_t M, int64_t N, int64_t K, const double *A, int64_t lda, const double *B, int64_t ldb, double *C,
+               int64_t ldc, cudaStream_t st)
+{
+    gemm64<true, false>(M, N, K, A, lda, B, ldb, C, ldc, 1, st);
+}
+
 static gpr_status lcp_backward(gpr_model *M, const gpr_grid *grid, double isovalue, const gpr_lcp_options *opts,
                                const float *dL_dlcp, const uint8_t *leaf, double *dL_dy, double *dL_dloglen,
                                cudaStream_t st)
@@ -984,6 +997,7 @@ extern "C" gpr_status gpr_lcp_backward(gpr_model *M, const gpr_grid *grid, doubl
     if (!M || !grid_valid(grid) || !opts_valid(opts) || !dL_dlcp || !dL_dy || !dL_dloglen || !isfinite(isovalue))
         return GPR_ERR_ARG;
     if (opts->est != GPR_EST_SOV_QMC) return GPR_ERR_UNSUPPORTED;  // the indicator MC has no useful gradient
+    if (M->sgpr) return GPR_ERR_UNSUPPORTED;                        // written for plain GPR models
     return lcp_backward(M, grid, isovalue, opts, dL_dlcp, nullptr, dL_dy, dL_dloglen, (cudaStream_t)stream);
 }
 
@@ -996,7 +1010,7 @@ extern "C" gpr_status gpr_lcp_backward_adaptive(gpr_model *M, const gpr_grid *gr
     if (max_depth < 0 || max_depth > 20) return GPR_ERR_ARG;
     for (int d = 0; d < 3; ++d)
         if (((int64_t)1 << max_depth) < (int64_t)grid->n[d] - 1) return GPR_ERR_ARG;
-    if (opts->est != GPR_EST_SOV_QMC) return GPR_ERR_UNSUPPORTED;
+    if (opts->est != GPR_EST_SOV_QMC || M->sgpr) return GPR_ERR_UNSUPPORTED;
     cudaStream_t st = (cudaStream_t)stream;
     GridDev g = make_grid(grid);
     uint8_t *leaf = nullptr;

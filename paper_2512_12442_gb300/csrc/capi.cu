@@ -48,7 +48,8 @@ extern "C" gpr_status gpr_sync(void *stream)
 bool est_opts_valid(const gpr_lcp_options *o)
 {
     if (!o) return false;
-    if (o->est != GPR_EST_SOV_QMC && o->est != GPR_EST_MC) return false;
+    if (o->est != GPR_EST_SOV_QMC && o->est != GPR_EST_MC && o->est != GPR_EST_INDEP && o->est != GPR_EST_EDGE_MAX)
+        return false;
     if (o->n_samples < 1 || o->n_samples > (1 << 24)) return false;
     if (!(o->jitter >= 0.0) || !(o->skip_eps >= 0.0) || !isfinite(o->jitter) || !isfinite(o->skip_eps)) return false;
     return true;

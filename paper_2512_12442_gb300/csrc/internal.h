@@ -110,6 +110,10 @@ struct gpr_model {
     // fill waits (on the device) for the previous one, so no point is computed twice
     std::mutex mv_mu;
     cudaEvent_t mv_ev = nullptr;
+    // SGPR model (gpr_model_create_sgpr): Linv holds G, the lower-triangular factor of
+    // Q = K_MM^-1 - K_MM^-1 A_M K_MM^-1 = G^T G, so every whitened kernel computes Eq. 1 unchanged;
+    // vy = G^-T alpha, alpha = K_MM^-1 mu_M, y = mu_M, L = chol(K_MM + jitter I), sn2 = 0
+    bool sgpr = false;
 };
 
 // Scope of one fill of the per-point (mean, var) table: holds the model's mv lock, orders the
@@ -149,6 +153,12 @@ struct Carver {
     }
     static size_t round(size_t b) { return (b + 255) & ~size_t(255); }
 };
+
+// ---- plain FP64 products (adjoint.cu): C = A B, C = A^T B (row-major, one launch each)
+void gemm64_nn(int64_t M, int64_t N, int64_t K, const double *A, int64_t lda, const double *B, int64_t ldb, double *C,
+               int64_t ldc, cudaStream_t st);
+void gemm64_tn(int64_t M, int64_t N, int64_t K, const double *A, int64_t lda, const double *B, int64_t ldb, double *C,
+               int64_t ldc, cudaStream_t st);
 
 // ---- stats (stats.cu)
 // Per-axis SE factor tables E_d[g][j] (or squared scaled distance for Matern), FP64 and FP32.

@@ -46,11 +46,70 @@ struct CellRec {
 
 __device__ __forceinline__ int tri(int i, int j) { return i * (i + 1) / 2 + j; }
 
+// ---- closed-form cell estimators (FP32 with this library's Phi)
+
+// 12-point Gauss-Legendre rule on [-1, 1] (symmetric half: nodes, weights).
+__constant__ float kGLx[6] = {0.1252334085114689f, 0.3678314989981802f, 0.5873179542866175f,
+                              0.7699026741943047f, 0.9041172563704748f, 0.9815606342467192f};
+__constant__ float kGLw[6] = {0.2491470458134027f, 0.2334925365383546f, 0.20316742672306573f,
+                              0.16007832854334642f, 0.10693932599531907f, 0.04717533638651141f};
+
+// Owen's T(h, a) = (1/2pi) int_0^a exp(-h^2 (1 + x^2) / 2) / (1 + x^2) dx for 0 <= a <= 1, by the
+// Gauss-Legendre rule on [0, a] (a smooth integrand there).
+__device__ float owen_t_small(float h, float a)
+{
+    const float hh = -0.5f * h * h, half = 0.5f * a;
+    float s = 0.f;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+#pragma unroll
+        for (int sg = -1; sg <= 1; sg += 2) {
+            const float x = half * (1.0f + (float)sg * kGLx[i]);
+            const float q = 1.0f + x * x;
+            s = fmaf(kGLw[i], __expf(hh * q) / q, s);
+        }
+    }
+    return s * half * 0.15915494309189535f;
+}
+
+// Owen's T for any a: odd in a, even in h; for a > 1 through Owen's identity
+// T(h, a) + T(ah, 1/a) = (Phi(h) + Phi(ah)) / 2 - Phi(h) Phi(ah)   (h >= 0, a > 0).
+__device__ float owen_t(float h, float a)
+{
+    const float sg = a < 0.f ? -1.f : 1.f;
+    a = fabsf(a);
+    h = fabsf(h);
+    if (a <= 1.0f) return sg * owen_t_small(h, a);
+    const float ah = a * h, ph = nrm_cdf(h), pah = nrm_cdf(ah);
+    return sg * (0.5f * (ph + pah) - ph * pah - owen_t_small(ah, 1.0f / a));
+}
+
+// P(X1 < h, X2 < k), standard bivariate normal with correlation r = rr (FP64 in, for the
+// arguments of T, which cancel when r is near 1): Owen's (1956) formula
+// Phi2 = Phi(h)/2 + Phi(k)/2 - T(h, (k - r h)/(h s)) - T(k, (h - r k)/(k s)) - beta, s = sqrt(1-r^2),
+// beta = 1/2 when h k < 0 or (h k = 0 and h + k < 0).
+__device__ float bvn_lower(double h, double k, double r)
+{
+    const double s = sqrt((1.0 - r) * (1.0 + r));
+    if (h == 0.0 && k == 0.0) return 0.25f + asinf((float)r) * 0.15915494309189535f;
+    float t1, t2;
+    if (h == 0.0) t1 = (k > 0.0) ? 0.25f : (k < 0.0 ? -0.25f : 0.f);
+    else t1 = owen_t((float)h, (float)((k - r * h) / (h * s)));
+    if (k == 0.0) t2 = (h > 0.0) ? 0.25f : (h < 0.0 ? -0.25f : 0.f);
+    else t2 = owen_t((float)k, (float)((h - r * k) / (k * s)));
+    const float beta = (h * k < 0.0 || (h * k == 0.0 && h + k < 0.0)) ? 0.5f : 0.f;
+    return 0.5f * nrm_cdf((float)h) + 0.5f * nrm_cdf((float)k) - t1 - t2 - beta;
+}
+
+// CF: 0 = queue records for the sampling estimators, 1 = independent-corner closed form,
+// 2 = edge-max closed form (results written in place, no records).
+template <int CF>
 __global__ void k_cell_prep(GridDev g, const double *stats, const int32_t *slot, const int64_t *cells,
                             int64_t count, double theta, double tau, double skip_eps, PairTable pt, float *lcp,
                             bool by_pos, CellRec *recs, unsigned long long *nrec, unsigned long long *nown,
                             int *status, unsigned long long *orth_ctr)
 {
+    bool closed = false;  // a closed-form estimator evaluated this cell (counted as estimated)
     int64_t pos = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     bool active = pos < count;
     bool need = false;
@@ -106,7 +165,38 @@ __global__ void k_cell_prep(GridDev g, const double *stats, const int32_t *slot,
                 sb += pb[c];
             }
             const float lim = (float)(0.99 * skip_eps);
-            if (!(sa < lim || sb < lim)) {
+            if (CF == 1 && !(sa < lim || sb < lim)) {
+                // corners taken as independent: 1 - prod P(Y_c < theta) - prod P(Y_c > theta)
+                float plo = 1.f, phi = 1.f;
+                for (int c = 0; c < 8; ++c) {
+                    plo *= pb[c];
+                    phi *= pa[c];
+                }
+                result = fminf(fmaxf(1.f - plo - phi, 0.f), 1.f);
+                closed = true;
+            } else if (CF == 2 && !(sa < lim || sb < lim)) {
+                // largest edge-crossing probability over the 12 edges: P(Y_i < t) + P(Y_j < t) - 2 P(both < t)
+                double z[8], isd[8];
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    isd[c] = 1.0 / sqrt(S[c][c]);
+                    z[c] = (theta - mu[c]) * isd[c];
+                }
+                float best = 0.f;
+#pragma unroll
+                for (int c = 0; c < 8; ++c)
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        const int d = c ^ (1 << a);
+                        if (d < c) continue;
+                        const double r = S[c][d] * isd[c] * isd[d];
+                        const double rc = r > 0.9999999999 ? 0.9999999999 : (r < -0.9999999999 ? -0.9999999999 : r);
+                        const float pe = pb[c] + pb[d] - 2.f * bvn_lower(z[c], z[d], rc);
+                        best = fmaxf(best, pe);
+                    }
+                result = fminf(fmaxf(best, 0.f), 1.f);
+                closed = true;
+            } else if (CF == 0 && !(sa < lim || sb < lim)) {
                 double Lm[8][8];
                 double fl = 1e-3 * jit;
                 for (int a = 0; a < 8; ++a) {
@@ -139,6 +229,11 @@ __global__ void k_cell_prep(GridDev g, const double *stats, const int32_t *slot,
             }
         }
         if (!need) lcp[outi] = result;
+    }
+    if (CF != 0) {  // closed-form estimators: count the cells they evaluated (no records)
+        const unsigned cmask = __ballot_sync(0xffffffffu, closed);
+        if (cmask && (threadIdx.x & 31) == __ffs(cmask) - 1) atomicAdd(nrec, (unsigned long long)__popc(cmask));
+        return;
     }
     // warp-aggregated append of the cells that need the estimator
     unsigned mask = __ballot_sync(0xffffffffu, need);
@@ -413,7 +508,8 @@ gpr_status run_cell_lcp(const GridDev &g, const double *stats, const int32_t *sl
     // a batch sink with room takes the records; its owner runs one estimator launch for all
     RecordSink *sink = tl_sink;
     bool to_sink = false;
-    if (sink) {
+    const bool closed = o.est == GPR_EST_INDEP || o.est == GPR_EST_EDGE_MAX;  // no records, no estimator
+    if (sink && !closed) {
         int64_t cur = sink->reserved->load();
         while (cur + count <= sink->capacity && !sink->reserved->compare_exchange_weak(cur, cur + count)) {
         }
@@ -425,14 +521,22 @@ gpr_status run_cell_lcp(const GridDev &g, const double *stats, const int32_t *sl
     if (!status) return GPR_ERR_CUDA;
     {
         ProfScope _ps("cell_prep", st);
-        k_cell_prep<<<(unsigned)((count + 127) / 128), 128, 0, st>>>(
-            g, stats, slot, cells, count, o.theta, o.tau, o.skip_eps, pt, lcp, by_pos,
-            to_sink ? (CellRec *)sink->recs : recs, to_sink ? sink->nrec : nrec, to_sink ? nrec : nullptr, status,
-            prof_counter(PROF_CTR_ORTHANTS));
+        const unsigned nb = (unsigned)((count + 127) / 128);
+        if (o.est == GPR_EST_INDEP)
+            k_cell_prep<1><<<nb, 128, 0, st>>>(g, stats, slot, cells, count, o.theta, o.tau, o.skip_eps, pt, lcp,
+                                               by_pos, recs, nrec, nullptr, status, nullptr);
+        else if (o.est == GPR_EST_EDGE_MAX)
+            k_cell_prep<2><<<nb, 128, 0, st>>>(g, stats, slot, cells, count, o.theta, o.tau, o.skip_eps, pt, lcp,
+                                               by_pos, recs, nrec, nullptr, status, nullptr);
+        else
+            k_cell_prep<0><<<nb, 128, 0, st>>>(
+                g, stats, slot, cells, count, o.theta, o.tau, o.skip_eps, pt, lcp, by_pos,
+                to_sink ? (CellRec *)sink->recs : recs, to_sink ? sink->nrec : nrec, to_sink ? nrec : nullptr,
+                status, prof_counter(PROF_CTR_ORTHANTS));
     }
     note_launch();
     GPR_CUDA_TRY(cudaGetLastError());
-    if (!to_sink) launch_estimator(recs, nrec, count, o, st);
+    if (!to_sink && !closed) launch_estimator(recs, nrec, count, o, st);
     GPR_CUDA_TRY(cudaGetLastError());
     if (n_estimated) {
         unsigned long long h = 0;
@@ -714,11 +818,19 @@ gpr_status run_cell_lcp_on_scratch(const GridDev &g, const double *stats, const 
     CellRec *recs = (CellRec *)((char *)scratch + 256);
     GPR_CUDA_TRY(cudaMemsetAsync(nrec, 0, 2 * sizeof(unsigned long long), st));
     static PairTable pt = make_pair_table();
-    k_cell_prep<<<(unsigned)((count + 127) / 128), 128, 0, st>>>(g, stats, nullptr, cells, count, o.theta, o.tau,
-                                                                 o.skip_eps, pt, lcp, by_pos, recs, nrec, nullptr,
-                                                                 status, nullptr);
+    const unsigned nb = (unsigned)((count + 127) / 128);
+    if (o.est == GPR_EST_INDEP)
+        k_cell_prep<1><<<nb, 128, 0, st>>>(g, stats, nullptr, cells, count, o.theta, o.tau, o.skip_eps, pt, lcp,
+                                           by_pos, recs, nrec, nullptr, status, nullptr);
+    else if (o.est == GPR_EST_EDGE_MAX)
+        k_cell_prep<2><<<nb, 128, 0, st>>>(g, stats, nullptr, cells, count, o.theta, o.tau, o.skip_eps, pt, lcp,
+                                           by_pos, recs, nrec, nullptr, status, nullptr);
+    else
+        k_cell_prep<0><<<nb, 128, 0, st>>>(g, stats, nullptr, cells, count, o.theta, o.tau, o.skip_eps, pt, lcp,
+                                           by_pos, recs, nrec, nullptr, status, nullptr);
     note_launch();
     GPR_CUDA_TRY(cudaGetLastError());
+    if (o.est == GPR_EST_INDEP || o.est == GPR_EST_EDGE_MAX) return GPR_OK;  // evaluated in place
     int64_t blocks = (count + 7) / 8;
     if (blocks > (int64_t)num_sms() * 16) blocks = (int64_t)num_sms() * 16;
     if (o.est == GPR_EST_SOV_QMC) {

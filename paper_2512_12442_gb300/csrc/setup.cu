@@ -244,6 +244,35 @@ __global__ void k_unpad(const double *A, int64_t mb, int64_t m, double *out)
 
 static unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
+// Blocked Cholesky in place (lower factor of the padded mb x mb matrix A); a pivot that is not
+// positive sets GPR_ERR_NOT_PD in the status word.
+static void chol_blocked(double *A, int64_t mb, int *status, cudaStream_t st)
+{
+    int nbk = (int)(mb / NB);
+    for (int kb = 0; kb < nbk; ++kb) {
+        k_potrf_diag<<<1, 32, 0, st>>>(A, mb, kb, status);
+        note_launch();
+        int64_t rows = mb - (int64_t)(kb + 1) * NB;
+        if (rows > 0) {
+            k_trsm_panel<<<nblk(rows, 128), 128, 0, st>>>(A, mb, kb);
+            note_launch();
+            unsigned T = (unsigned)(nbk - kb - 1);
+            k_syrk_update<<<dim3(T, T), 256, 0, st>>>(A, mb, kb);
+            note_launch();
+        }
+    }
+}
+
+// Linv = L^-1 of a padded lower factor (column by column).
+static void trtri(const double *L, int64_t mb, double *Linv, cudaStream_t st)
+{
+    const int wpb = (sizeof(double) * mb * 4 <= 200 * 1024) ? 4 : ((sizeof(double) * mb * 2 <= 200 * 1024) ? 2 : 1);
+    size_t smem = sizeof(double) * mb * wpb;
+    if (smem > 48 * 1024) cudaFuncSetAttribute(k_trtri_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_trtri_cols<<<nblk(mb, wpb), 32 * wpb, smem, st>>>(L, mb, Linv);
+    note_launch();
+}
+
 extern "C" gpr_status gpr_model_create(const double *obs_xyz, const double *y, int64_t m, gpr_kernel kernel,
                                        const double length_scales[3], double signal_var, double noise_var,
                                        void *stream, gpr_model **out)
@@ -313,24 +342,8 @@ extern "C" gpr_status gpr_model_create(const double *obs_xyz, const double *y, i
 
     k_build_K<<<nblk(mb * mb, 256), 256, 0, st>>>(M->X, m, mb, M->kp, noise_var, A);
     note_launch();
-    int nbk = (int)(mb / NB);
-    for (int kb = 0; kb < nbk; ++kb) {
-        k_potrf_diag<<<1, 32, 0, st>>>(A, mb, kb, status);
-        note_launch();
-        int64_t rows = mb - (int64_t)(kb + 1) * NB;
-        if (rows > 0) {
-            k_trsm_panel<<<nblk(rows, 128), 128, 0, st>>>(A, mb, kb);
-            note_launch();
-            unsigned T = (unsigned)(nbk - kb - 1);
-            k_syrk_update<<<dim3(T, T), 256, 0, st>>>(A, mb, kb);
-            note_launch();
-        }
-    }
-    const int wpb = (sizeof(double) * mb * 4 <= 200 * 1024) ? 4 : ((sizeof(double) * mb * 2 <= 200 * 1024) ? 2 : 1);
-    size_t smem = sizeof(double) * mb * wpb;
-    if (smem > 48 * 1024) cudaFuncSetAttribute(k_trtri_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_trtri_cols<<<nblk(mb, wpb), 32 * wpb, smem, st>>>(A, mb, M->Linv);
-    note_launch();
+    chol_blocked(A, mb, status, st);
+    trtri(A, mb, M->Linv, st);
     k_vy<<<nblk(mp, 8), 256, 0, st>>>(M->Linv, mb, M->y, m, M->vy, mp);
     note_launch();
     k_alpha_obs<<<nblk(m, 128), 128, 0, st>>>(M->Linv, mb, M->vy, M->y, m, noise_var, signal_var, M->alpha,
@@ -348,6 +361,233 @@ extern "C" gpr_status gpr_model_create(const double *obs_xyz, const double *y, i
     cudaMemcpy(&hs, status, sizeof(int), cudaMemcpyDeviceToHost);
     cudaFree(A);
     A = nullptr;
+    if (hs != 0) {
+        cudaMemset(status, 0, sizeof(int));
+        gpr_model_destroy(M);
+        return (gpr_status)hs;
+    }
+    *out = M;
+    return GPR_OK;
+}
+
+// ---- SGPR model (Eq. 1 with a stored inducing distribution)
+
+// dst (mb x mb) = src (m x m, contiguous), zero padding.
+__global__ void k_pad(const double *src, int64_t m, int64_t mb, double *dst)
+{
+    int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= mb * mb) return;
+    int64_t i = idx / mb, j = idx % mb;
+    dst[idx] = (i < m && j < m) ? src[i * m + j] : 0.0;
+}
+
+// out[j] = sum_i P[i][j] v[i] for lower-triangular P (i >= j): alpha = L^-T (L^-1 mu_M).
+__global__ void k_ltv(const double *P, int64_t mb, const double *v, int64_t m, double *out)
+{
+    int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= m) return;
+    double a = 0.0;
+    for (int64_t i = j; i < m; ++i) a += P[i * mb + j] * v[i];
+    out[j] = a;
+}
+
+__global__ void k_transpose(const double *A, int64_t mb, double *At)
+{
+    int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= mb * mb) return;
+    int64_t i = idx / mb, j = idx % mb;
+    At[j * mb + i] = A[idx];
+}
+
+// E = I - (B + B^T) / 2 on the m x m block, 0 on the padding.
+__global__ void k_eye_minus_sym(const double *B, int64_t mb, int64_t m, double *E)
+{
+    int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= mb * mb) return;
+    int64_t i = idx / mb, j = idx % mb;
+    E[idx] = (i < m && j < m) ? (i == j ? 1.0 : 0.0) - 0.5 * (B[idx] + B[j * mb + i]) : 0.0;
+}
+
+// R = J Q J (index reversal on the m x m block, symmetrised), identity on the padding.
+__global__ void k_reverse(const double *Q, int64_t mb, int64_t m, double *R)
+{
+    int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= mb * mb) return;
+    int64_t i = idx / mb, j = idx % mb;
+    double v;
+    if (i < m && j < m) {
+        int64_t a = m - 1 - i, b = m - 1 - j;
+        v = 0.5 * (Q[a * mb + b] + Q[b * mb + a]);
+    } else {
+        v = (i == j) ? 1.0 : 0.0;
+    }
+    R[idx] = v;
+}
+
+// G = J Lr^T J (lower triangular), identity on the padding: Q = G^T G when J Q J = Lr Lr^T.
+__global__ void k_unreverse_t(const double *Lr, int64_t mb, int64_t m, double *G)
+{
+    int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= mb * mb) return;
+    int64_t i = idx / mb, j = idx % mb;
+    G[idx] = (i < m && j < m) ? Lr[(m - 1 - j) * mb + (m - 1 - i)] : (i == j ? 1.0 : 0.0);
+}
+
+// v = G^-T alpha with G^-1 = J Lr^-T J: v_i = sum_{j >= i} Lrinv[m-1-i][m-1-j] alpha_j (warp per row),
+// zero on the padding (mp entries).
+__global__ void k_sgpr_v(const double *Lrinv, int64_t mb, const double *alpha, int64_t m, double *v, int64_t mp)
+{
+    int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    int64_t i = blockIdx.x * (int64_t)(blockDim.x / 32) + warp;
+    if (i >= mp) return;
+    double s = 0.0;
+    if (i < m) {
+        const double *row = Lrinv + (m - 1 - i) * mb;
+        for (int64_t j = i + lane; j < m; j += 32) s += row[m - 1 - j] * alpha[j];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) v[i] = s;
+}
+
+// The p-test reads the inducing distribution itself: mean mu_M, variance diag(A_M) (floored).
+__global__ void k_sgpr_obs(const double *muM, const double *AM, int64_t m, int64_t mb, double sf2, double *mu_obs,
+                           double *var_obs)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    mu_obs[i] = muM[i];
+    double v = AM[i * mb + i], fl = 1e-12 * sf2;
+    var_obs[i] = v > fl ? v : fl;
+}
+
+extern "C" gpr_status gpr_model_create_sgpr(const double *inducing_xyz, const double *mu_M, const double *A_M,
+                                            int64_t m, gpr_kernel kernel, const double length_scales[3],
+                                            double signal_var, double kmm_jitter, void *stream, gpr_model **out)
+{
+    if (!out) return GPR_ERR_ARG;
+    *out = nullptr;
+    if (!inducing_xyz || !mu_M || !A_M || !length_scales || m < 1 || m > 8192) return GPR_ERR_ARG;
+    if (kernel != GPR_K_SE && kernel != GPR_K_MATERN52) return GPR_ERR_ARG;
+    if (!(signal_var > 0.0) || !(kmm_jitter >= 0.0) || !isfinite(signal_var) || !isfinite(kmm_jitter))
+        return GPR_ERR_ARG;
+    for (int d = 0; d < 3; ++d)
+        if (!(length_scales[d] > 0.0) || !isfinite(length_scales[d])) return GPR_ERR_ARG;
+    for (int64_t i = 0; i < 3 * m; ++i)
+        if (!isfinite(inducing_xyz[i])) return GPR_ERR_ARG;
+    for (int64_t i = 0; i < m; ++i)
+        if (!isfinite(mu_M[i])) return GPR_ERR_ARG;
+    for (int64_t i = 0; i < m * m; ++i)
+        if (!isfinite(A_M[i])) return GPR_ERR_ARG;
+    if (getenv("GPR_FAULT") && strcmp(getenv("GPR_FAULT"), "alloc") == 0) return GPR_ERR_OOM;
+
+    cudaStream_t st = (cudaStream_t)stream;
+    int *status = gpr_status_word();
+    if (!status) return GPR_ERR_CUDA;
+    gpr_model *M = new gpr_model();
+    M->sgpr = true;
+    M->m = m;
+    M->mp = (m + 63) / 64 * 64;
+    M->kp.kind = kernel;
+    for (int d = 0; d < 3; ++d) M->kp.ell[d] = length_scales[d];
+    M->kp.sf2 = signal_var;
+    M->sn2 = 0.0;
+    cudaGetDevice(&M->device);
+    M->hX.assign(inducing_xyz, inducing_xyz + 3 * m);
+    M->hy.assign(mu_M, mu_M + m);
+    int64_t mb = (m + NB - 1) / NB * NB, mp = M->mp;
+    const size_t sq = sizeof(double) * mb * mb;
+    double *A = nullptr, *P = nullptr, *T1 = nullptr, *T2 = nullptr, *T3 = nullptr, *AMd = nullptr, *v0 = nullptr;
+    auto release = [&]() {
+        cudaFree(A); cudaFree(P); cudaFree(T1); cudaFree(T2); cudaFree(T3); cudaFree(AMd); cudaFree(v0);
+        A = P = T1 = T2 = T3 = AMd = v0 = nullptr;
+    };
+    auto fail = [&](gpr_status s) {
+        cudaStreamSynchronize(st);
+        release();
+        gpr_model_destroy(M);
+        return s;
+    };
+#define ALLOC(ptr, bytes)                                                   \
+    do {                                                                    \
+        cudaError_t _e = cudaMalloc((void **)&(ptr), (bytes));              \
+        if (_e != cudaSuccess) {                                            \
+            gpr_internal_note_cuda_error(_e, "cudaMalloc", __LINE__);       \
+            return fail(_e == cudaErrorMemoryAllocation ? GPR_ERR_OOM : GPR_ERR_CUDA); \
+        }                                                                   \
+    } while (0)
+    ALLOC(M->X, sizeof(double) * 3 * m);
+    ALLOC(M->y, sizeof(double) * m);
+    ALLOC(M->L, sizeof(double) * m * m);
+    ALLOC(M->Linv, sq);
+    ALLOC(M->vy, sizeof(double) * mp);
+    ALLOC(M->alpha, sizeof(double) * m);
+    ALLOC(M->mu_obs, sizeof(double) * m);
+    ALLOC(M->var_obs, sizeof(double) * m);
+    ALLOC(M->BT64, sizeof(double) * mp * mp);
+    ALLOC(M->BT32, sizeof(float) * mp * mp);
+    ALLOC(M->vy32, sizeof(float) * mp);
+    ALLOC(M->alpha_ff, sizeof(float2) * mp);
+    ALLOC(M->Linv32, sizeof(float) * mp * mp);
+    ALLOC(M->X32, sizeof(float) * 3 * m);
+    ALLOC(M->alpha32, sizeof(float) * mp);
+    ALLOC(A, sq);
+    ALLOC(P, sq);
+    ALLOC(T1, sq);
+    ALLOC(T2, sq);
+    ALLOC(T3, sq);
+    ALLOC(AMd, sq);
+    ALLOC(v0, sizeof(double) * mb);
+#undef ALLOC
+    if (cudaMemcpyAsync(M->X, inducing_xyz, sizeof(double) * 3 * m, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(M->y, mu_M, sizeof(double) * m, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(T3, A_M, sizeof(double) * m * m, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess)
+        return fail(GPR_ERR_CUDA);
+    const unsigned gsq = nblk(mb * mb, 256);
+    k_pad<<<gsq, 256, 0, st>>>(T3, m, mb, AMd);
+    note_launch();
+    // K_MM + jitter I = Lk Lk^T, P = Lk^-1, alpha = K_MM^-1 mu_M
+    k_build_K<<<gsq, 256, 0, st>>>(M->X, m, mb, M->kp, kmm_jitter, A);
+    note_launch();
+    chol_blocked(A, mb, status, st);
+    trtri(A, mb, P, st);
+    k_unpad<<<nblk(m * m, 256), 256, 0, st>>>(A, mb, m, M->L);
+    note_launch();
+    k_vy<<<nblk(m, 8), 256, 0, st>>>(P, mb, M->y, m, v0, m);
+    note_launch();
+    k_ltv<<<nblk(m, 128), 128, 0, st>>>(P, mb, v0, m, M->alpha);
+    note_launch();
+    // Q = K_MM^-1 - K_MM^-1 A_M K_MM^-1 = P^T (I - P A_M P^T) P
+    k_transpose<<<gsq, 256, 0, st>>>(P, mb, T1);  // T1 = P^T
+    note_launch();
+    gemm64_nn(mb, mb, mb, P, mb, AMd, mb, T2, mb, st);   // T2 = P A_M
+    gemm64_nn(mb, mb, mb, T2, mb, T1, mb, T3, mb, st);   // T3 = P A_M P^T
+    k_eye_minus_sym<<<gsq, 256, 0, st>>>(T3, mb, m, T2);  // T2 = E = I - P A_M P^T
+    note_launch();
+    gemm64_nn(mb, mb, mb, T2, mb, P, mb, T3, mb, st);    // T3 = E P
+    gemm64_tn(mb, mb, mb, P, mb, T3, mb, T2, mb, st);    // T2 = Q = P^T E P
+    // Q = G^T G with G lower triangular: J Q J = Lr Lr^T, G = J Lr^T J
+    k_reverse<<<gsq, 256, 0, st>>>(T2, mb, m, A);
+    note_launch();
+    chol_blocked(A, mb, status, st);  // not positive definite: A_M is not below K_MM
+    k_unreverse_t<<<gsq, 256, 0, st>>>(A, mb, m, M->Linv);
+    note_launch();
+    trtri(A, mb, T1, st);  // T1 = Lr^-1
+    k_sgpr_v<<<nblk(mp, 8), 256, 0, st>>>(T1, mb, M->alpha, m, M->vy, mp);
+    note_launch();
+    k_sgpr_obs<<<nblk(m, 128), 128, 0, st>>>(M->y, AMd, m, mb, signal_var, M->mu_obs, M->var_obs);
+    note_launch();
+    k_operands<<<nblk(mp * mp, 256), 256, 0, st>>>(M->Linv, mb, m, mp, M->BT64, M->BT32, M->vy, M->vy32, M->alpha,
+                                                   M->alpha_ff, M->Linv32, M->X, M->X32, M->alpha32);
+    note_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) { gpr_internal_note_cuda_error(e, "sgpr setup launch", __LINE__); return fail(GPR_ERR_CUDA); }
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) { gpr_internal_note_cuda_error(e, "sgpr setup sync", __LINE__); return fail(GPR_ERR_CUDA); }
+    int hs = 0;
+    cudaMemcpy(&hs, status, sizeof(int), cudaMemcpyDeviceToHost);
+    release();
     if (hs != 0) {
         cudaMemset(status, 0, sizeof(int));
         gpr_model_destroy(M);

@@ -10,6 +10,9 @@ def torch_cuda():
 
 def model_of(w, stream=None):
     import paper_2512_12442_gb300 as g
+    if "A_M" in w.extra:
+        return g.gpr_model_create_sgpr(w.X, w.y, w.extra["A_M"], w.kernel, w.ell, w.sf2, w.extra["kmm_jitter"],
+                                       stream=stream)
     return g.gpr_model_create(w.X, w.y, w.kernel, w.ell, w.sf2, w.sn2, stream=stream)
 
 

@@ -93,6 +93,21 @@ def test_fault_injection_alloc_reports_oom_without_a_gpu(lib, monkeypatch):
     assert lib.gpr_status_string(rc) == b"out of device memory"
 
 
+def test_sgpr_model_arguments_checked_on_the_host(lib):
+    """gpr_model_create_sgpr rejects bad inducing inputs before any CUDA call."""
+    import numpy as np
+    import paper_2512_12442_gb300 as g
+    X = np.random.default_rng(0).random((6, 3)); mu = np.zeros(6); A = np.eye(6) * 1e-3
+    ell = np.full(3, 0.2)
+    h = ctypes.c_void_p()
+    for (Xa, ma, Aa, jit) in ((X, mu, A, -1.0), (X, mu, A, float("nan")), (X, mu, np.full((6, 6), np.inf), 0.0)):
+        rc = lib.gpr_model_create_sgpr(Xa.ctypes.data, ma.ctypes.data, Aa.ctypes.data, 6, 0, ell.ctypes.data, 1.0,
+                                       jit, None, ctypes.byref(h))
+        assert rc == g.GPR_ERR_ARG
+    assert lib.gpr_model_create_sgpr(X.ctypes.data, mu.ctypes.data, None, 6, 0, ell.ctypes.data, 1.0, 0.0, None,
+                                     ctypes.byref(h)) == g.GPR_ERR_ARG
+
+
 def test_product_package_does_not_import_the_oracle():
     """The product path never routes through the CPU oracle."""
     pkg = os.path.join(ROOT, "paper_2512_12442_gb300")

@@ -143,9 +143,10 @@ def test_autograd_function(torch, g):
 def test_backward_adaptive_masks_cells_outside_the_leaf_set(torch, g):
     """gpr_lcp_backward_adaptive equals gpr_lcp_backward with the weights of cells outside Algorithm
     1's leaf set S set to 0; S is read from the device octree's last level (gpr_octree_trace), and
-    the adaptive forward field is 0 exactly outside S."""
-    w = workloads.small(7, 60, 17, ell=(0.2, 0.25, 0.3))
-    n, th, D = 17, w.isovalues[0], workloads.depth_for(17)
+    the adaptive forward field is 0 exactly outside S.  The paper-scale field on a 33^3 grid keeps
+    about a third of the cells."""
+    w = workloads.config2()
+    n, th, D = 33, w.isovalues[1], workloads.depth_for(33)
     wts = np.random.default_rng(3).random((n - 1) ** 3)
     M = model_of(w)
     grid, opts = g.make_grid(n), g.lcp_options()

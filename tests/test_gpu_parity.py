@@ -209,6 +209,47 @@ def test_lcp_dense_config2_full_size_subblock(torch, g):
         assert 0.0 <= gpu.min() and gpu.max() <= 1.0
 
 
+@pytest.mark.parametrize("est", ["indep", "edge"])
+def test_lcp_closed_form_estimators_config1(torch, g, est):
+    """The closed-form cell estimators (independent corners; Pothkow et al.'s edge maximum) on the
+    config-1 field, every cell against the oracle.  Tolerance 2e-5: the GPU evaluates them in FP32
+    with this library's Phi (absolute error <= 5e-7 per evaluation, at most 8 factors of a product)
+    and Owen's T by a 12-point Gauss-Legendre rule."""
+    w = workloads.config1()
+    M = model_of(w)
+    th = w.isovalues[0]
+    e_gpu = g.GPR_EST_INDEP if est == "indep" else g.GPR_EST_EDGE_MAX
+    e_or = oracle.EST_INDEP if est == "indep" else oracle.EST_EDGE
+    gpu, st = _lcp_dense_gpu(g, torch, M, w.n, th, prec=g.GPR_P_FP64, est=e_gpu)
+    ref = oracle.Model.from_workload(w).lcp_dense(w.n, th, est=e_or)
+    assert np.abs(gpu - ref).max() <= 2e-5, np.abs(gpu - ref).max()
+    assert st["cells_estimated"] > 100 and (ref > 0.01).sum() > 100
+    sov, _ = _lcp_dense_gpu(g, torch, M, w.n, th, prec=g.GPR_P_FP64)
+    if est == "edge":
+        assert np.all(gpu <= sov + 1e-3)  # a crossed edge crosses the cell
+
+
+def test_lcp_closed_form_estimators_paper_scale_adaptive(torch, g):
+    """The edge-maximum estimator on the paper-scale field (m=500, 128^3), adaptive as the bench runs
+    fields: equal to the dense field on S, and a 12^3 block against the oracle."""
+    w = workloads.config2()
+    M = model_of(w)
+    n, th = w.n, w.isovalues[1]
+    grid = g.make_grid(n)
+    opts = g.lcp_options(est=g.GPR_EST_EDGE_MAX)
+    ad = torch.zeros((n - 1) ** 3, dtype=torch.float32, device="cuda")
+    de = torch.zeros_like(ad)
+    sa = g.gpr_lcp_adaptive(M, grid, th, w.max_depth, opts, ad)
+    g.gpr_lcp_dense(M, grid, th, opts, de)
+    g.gpr_sync()
+    a, d = _np(ad), _np(de)
+    nz = a != 0
+    assert np.array_equal(a[nz], d[nz]) and sa["cells_estimated"] > 1000
+    ref = oracle.Model.from_workload(w).lcp_block(n, th, (50, 60, 40), (62, 72, 52), est=oracle.EST_EDGE)
+    f = d.reshape(n - 1, n - 1, n - 1)[40:52, 60:72, 50:62].reshape(-1)
+    assert np.abs(f - ref).max() <= 2e-5
+
+
 @pytest.mark.parametrize("n", [2, 3])
 def test_lcp_tiny_grids(torch, g, n):
     """Degenerate grids: one cell (n=2) and 8 cells (n=3)."""

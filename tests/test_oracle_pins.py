@@ -304,6 +304,66 @@ def test_lcp_mc_agrees_with_sov():
         assert abs(mc - sov) < tol * se + 1e-12
 
 
+def test_bivariate_normal_against_library_and_closed_form():
+    """P(X1 < a, X2 < b) (the edge estimator's building block): SciPy's multivariate normal CDF over
+    random thresholds and correlations up to |r| = 1 - 1e-8, and the orthant 1/4 + asin(r) / (2 pi)."""
+    from scipy.stats import multivariate_normal
+    rng = np.random.default_rng(21)
+    for _ in range(120):
+        a, b = rng.uniform(-6, 6, 2)
+        r = rng.choice([rng.uniform(-0.99, 0.99), 1 - 10 ** rng.uniform(-8, -1), -(1 - 10 ** rng.uniform(-8, -1))])
+        ref = multivariate_normal.cdf([a, b], mean=[0, 0], cov=[[1, r], [r, 1]], abseps=1e-13, releps=1e-13)
+        assert oracle.bvn_lower(a, b, r) == pytest.approx(ref, abs=1e-12)
+    for r in (-0.9, -0.3, 0.0, 0.5, 0.999):
+        assert oracle.bvn_lower(0.0, 0.0, r) == pytest.approx(0.25 + math.asin(r) / (2 * math.pi), abs=1e-13)
+
+
+def test_independent_corner_estimator():
+    """The independent-corner closed form equals the exact LCP when the corners are independent
+    (diagonal Sigma: the sequential-conditioning estimator is exact there) and ignores the
+    off-diagonal entries otherwise."""
+    rng = np.random.default_rng(22)
+    mu = rng.normal(0, 0.3, 8); d = rng.uniform(0.05, 0.3, 8)
+    S = np.diag(d)
+    assert oracle.cell_lcp(mu, S, 0.1, est=oracle.EST_INDEP) == pytest.approx(oracle.cell_lcp(mu, S, 0.1), abs=1e-12)
+    A = rng.normal(size=(8, 8)); C = A @ A.T / 8
+    Sc = C + np.diag(np.diag(S) + 0.02 - np.diag(C))  # same diagonal, correlated
+    assert oracle.cell_lcp(mu, Sc, 0.1, est=oracle.EST_INDEP) == \
+        pytest.approx(oracle.cell_lcp(mu, np.diag(np.diag(Sc)), 0.1, est=oracle.EST_INDEP), abs=1e-15)
+
+
+def test_edge_max_estimator():
+    """Pothkow et al.'s edge approximation: for two variables it is the exact segment crossing
+    probability of Sec. 4's first formula (SciPy's bivariate CDF); for a cell it is the largest of the
+    12 edge probabilities and never exceeds the cell's LCP (a crossed edge crosses the cell)."""
+    from scipy.stats import multivariate_normal
+    rng = np.random.default_rng(23)
+    mu2 = np.array([0.05, -0.1]); S2 = np.array([[0.04, 0.03], [0.03, 0.05]])
+    sd = np.sqrt(np.diag(S2)) * np.sqrt(1 + 1e-4 * 0.05 / np.diag(S2))  # the jittered diagonal
+    Sj = S2 + np.eye(2) * 1e-4 * 0.05
+    lo = multivariate_normal.cdf([0.0, 0.0], mean=mu2, cov=Sj)
+    hi = multivariate_normal.cdf([0.0, 0.0], mean=-mu2, cov=Sj)
+    assert oracle.cell_lcp(mu2, S2, 0.0, est=oracle.EST_EDGE) == pytest.approx(1 - lo - hi, abs=1e-9)
+    for _ in range(6):
+        A = rng.normal(size=(8, 8)); S = A @ A.T / 8 + 0.3 * np.ones((8, 8)) + 0.02 * np.eye(8)
+        mu = rng.normal(0, 0.3, 8)
+        e = oracle.cell_lcp(mu, S, 0.05, est=oracle.EST_EDGE)
+        full = oracle.cell_lcp(mu, S, 0.05, n_samples=20000)
+        assert e <= full + 1e-3
+        Sj = S + np.eye(8) * 1e-4 * np.max(np.diag(S))
+        best = 0.0
+        for i in range(8):
+            for a in range(3):
+                j = i ^ (1 << a)
+                if j < i:
+                    continue
+                C = Sj[np.ix_([i, j], [i, j])]
+                p_lo = multivariate_normal.cdf([0.05, 0.05], mean=mu[[i, j]], cov=C, abseps=1e-12)
+                p_hi = multivariate_normal.cdf([-0.05, -0.05], mean=-mu[[i, j]], cov=C, abseps=1e-12)
+                best = max(best, 1 - p_lo - p_hi)
+        assert e == pytest.approx(best, abs=1e-9)
+
+
 def test_lcp_skip_and_range():
     """LCP in [0,1]; the Boole pre-skip returns exactly 0 far from theta; deterministic cells."""
     S = 0.01 * (np.full((8, 8), 0.9) + 0.1 * np.eye(8))
