@@ -89,11 +89,15 @@ typedef struct {
 /* Options of the LCP calls.  Defaults come from gpr_lcp_options_default(). */
 typedef struct {
     double alpha;          /* octree threshold (Algorithm 1), default 1e-3 (Sec. 7.3) */
-    double beta;           /* local-GP radius in length scales (Sec. 5.2), default 6; unused by this library */
+    double beta;           /* local model of the octree bound (Sec. 5.2): beta >= 0 minimises each node's bound on
+                              the model restricted to the observations inside the node box enlarged by
+                              beta * l_d per axis (the paper uses 6, Sec. 7.3); beta < 0 or +inf uses the full
+                              model (default -1: on this GPU the full model's bound is the cheaper one) */
     gpr_estimator est;     /* cell estimator, default SOV-QMC */
     int32_t n_samples;     /* samples per cell, default 1600 (Sec. 6.4) */
     uint64_t seed;         /* lattice shifts / Philox key */
-    double jitter;         /* tau: Sigma_8 += tau * max diag * I, default 1e-4 */
+    double jitter;         /* tau: Sigma_8 += tau * max diag * I, default 1e-10 (the LCP then agrees with
+                              the unregularised Sigma_8 of Sec. 4 to 1e-6) */
     double skip_eps;       /* Boole pre-skip threshold, default 1e-9 */
     gpr_precision prec;    /* precision of the pre-classification / octree pass, default GPR_P_FP32 */
     int32_t max_iters_min; /* projected steps T of the box minimiser, default 4 */

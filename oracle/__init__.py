@@ -69,7 +69,7 @@ def lib():
         L.or_lcp_block.argtypes = [C.c_void_p, C.POINTER(_Grid), C.c_double, C.c_int, C.c_int64,
                                    C.c_uint64, C.c_double, C.c_double, _i64p, _i64p, _dp]
         L.or_octree_level.argtypes = [C.c_void_p, C.POINTER(_Grid), C.c_int, C.c_int, C.c_double,
-                                      C.c_double, C.c_int, _i64p, C.c_int64, _i8p, _dp, _i8p]
+                                      C.c_double, C.c_int, C.c_double, _i64p, C.c_int64, _i8p, _dp, _i8p]
         L.or_eval_g.argtypes = [C.c_void_p, _dp, C.c_int64, C.c_double, C.c_int, _dp, _dp]
         L.or_node_min.restype = C.c_double
         L.or_node_min.argtypes = [C.c_void_p, C.POINTER(_Grid), C.c_int, C.c_int, C.c_int64, C.c_double, C.c_int,
@@ -213,7 +213,7 @@ class Model:
         return out.reshape(cnt, 15)
 
     def lcp_block(self, n, theta, c0=(0, 0, 0), c1=None, est=EST_SOV, n_samples=1600, seed=0,
-                  tau=1e-4, skip_eps=1e-9, lo=(0, 0, 0), hi=(1, 1, 1)):
+                  tau=1e-10, skip_eps=1e-9, lo=(0, 0, 0), hi=(1, 1, 1)):
         """Cell LCP (Sec. 4) for cells with min corner in [c0, c1), x-fastest."""
         g = grid(n, lo, hi)
         if c1 is None:
@@ -234,24 +234,25 @@ class Model:
             out[z0 * nc * nc: z1 * nc * nc] = self.lcp_block(n, theta, (0, 0, z0), (nc, nc, z1), **kw)
         return out
 
-    def octree_level(self, n, D, l, theta, nodes, alpha=1e-3, T=4):
-        """One level of Algorithm 1.  Returns (decision, bound, side) per node."""
+    def octree_level(self, n, D, l, theta, nodes, alpha=1e-3, T=4, beta=-1.0):
+        """One level of Algorithm 1.  Returns (decision, bound, side) per node.  beta >= 0: the
+        bound uses each node's local model (Sec. 5.2, beta in length scales); beta < 0: the full one."""
         g = grid(n)
         nodes = np.ascontiguousarray(nodes, np.int64)
         cnt = nodes.shape[0]
         dec = np.zeros(cnt, np.int8); bnd = np.zeros(cnt); side = np.zeros(cnt, np.int8)
         if cnt:
             lib().or_octree_level(self._h, C.byref(g), int(D), int(l), float(theta), float(alpha), int(T),
-                                  nodes, cnt, dec, bnd, side)
+                                  float(beta), nodes, cnt, dec, bnd, side)
         return dec, bnd, side
 
-    def octree(self, n, D, theta, alpha=1e-3, T=4):
+    def octree(self, n, D, theta, alpha=1e-3, T=4, beta=-1.0):
         """Algorithm 1 top-down, level by level.  Returns (S cell codes, per-level records)."""
         nodes = np.zeros(1, np.int64)
         levels = []
         leaves = np.zeros(0, np.int64)
         for l in range(D + 1):
-            dec, bnd, side = self.octree_level(n, D, l, theta, nodes, alpha, T)
+            dec, bnd, side = self.octree_level(n, D, l, theta, nodes, alpha, T, beta)
             levels.append({"nodes": nodes, "decision": dec, "bound": bnd, "side": side})
             keep = nodes[dec > 0]
             if l == D:
@@ -267,9 +268,9 @@ class Model:
             nodes = np.sort(np.concatenate(ch)) if ch else np.zeros(0, np.int64)
         return leaves, levels
 
-    def lcp_adaptive(self, n, D, theta, alpha=1e-3, T=4, **kw):
+    def lcp_adaptive(self, n, D, theta, alpha=1e-3, T=4, beta=-1.0, **kw):
         """Adaptive LCP field: the dense cell LCP on the leaves S of Algorithm 1, 0 elsewhere (Sec. 5.3)."""
-        leaves, levels = self.octree(n, D, theta, alpha, T)
+        leaves, levels = self.octree(n, D, theta, alpha, T, beta)
         nc = n - 1
         field = np.zeros(nc ** 3)
         if leaves.size:
@@ -279,7 +280,7 @@ class Model:
             field[lin] = dense[lin]
         return field, leaves, levels
 
-    def lcp_grad(self, n, theta, weights, c0=(0, 0, 0), c1=None, n_samples=1600, seed=0, tau=1e-4, skip_eps=1e-9):
+    def lcp_grad(self, n, theta, weights, c0=(0, 0, 0), c1=None, n_samples=1600, seed=0, tau=1e-10, skip_eps=1e-9):
         """Gradient of sum_c weights[c] LCP_c over cells [c0, c1) wrt y and log length scales;
         `weights` is indexed by the linear cell index of the whole grid (one per grid cell).
         Returns (loss, dL/dy, dL/dlog l)."""
@@ -311,7 +312,7 @@ class Model:
         return g, gr
 
 
-def cell_lcp_adj(mu, S, theta, wbar=1.0, n_samples=1600, seed=0, cell=0, tau=1e-4, skip_eps=1e-9):
+def cell_lcp_adj(mu, S, theta, wbar=1.0, n_samples=1600, seed=0, cell=0, tau=1e-10, skip_eps=1e-9):
     """Adjoint of the SOV cell rule: (LCP, dLCP/dmu * wbar, dLCP/dSigma * wbar)."""
     mu = np.ascontiguousarray(mu, np.float64)
     S = np.ascontiguousarray(S, np.float64)
@@ -322,7 +323,7 @@ def cell_lcp_adj(mu, S, theta, wbar=1.0, n_samples=1600, seed=0, cell=0, tau=1e-
     return v, mb, Sb.reshape(d, d)
 
 
-def cell_lcp(mu, S, theta, est=EST_SOV, n_samples=1600, seed=0, cell=0, tau=1e-4, skip_eps=1e-9):
+def cell_lcp(mu, S, theta, est=EST_SOV, n_samples=1600, seed=0, cell=0, tau=1e-10, skip_eps=1e-9):
     """LCP of one cell (or any d <= 16 corner variables) from (mu, Sigma) (Sec. 4)."""
     mu = np.ascontiguousarray(mu, np.float64)
     S = np.ascontiguousarray(S, np.float64)

@@ -54,6 +54,7 @@ typedef struct {
      * and mu_obs / var_obs are mu_M and diag(A_M). */
     int sgpr;
     double *A;      /* m x m A_M */
+    double kmm_jitter; /* SGPR: jitter on the diagonal of K_MM */
 } or_model;
 
 /* ------------------------------------------------------------------ kernel */
@@ -210,7 +211,7 @@ or_model *or_model_create_sgpr(const double *X, const double *muM, const double 
                                const double *ell, double sf2, double jitter)
 {
     or_model *M = (or_model *)calloc(1, sizeof(or_model));
-    M->m = m; M->kernel = kernel; M->sf2 = sf2; M->sn2 = 0.0; M->sgpr = 1;
+    M->m = m; M->kernel = kernel; M->sf2 = sf2; M->sn2 = 0.0; M->sgpr = 1; M->kmm_jitter = jitter;
     for (int d = 0; d < 3; ++d) M->ell[d] = ell[d];
     M->X = (double *)malloc(sizeof(double) * 3 * m);
     M->y = (double *)malloc(sizeof(double) * m);
@@ -971,14 +972,55 @@ static double node_min_g(const or_model *M, const or_grid *g, const int64_t p0[3
     return bestg;
 }
 
+/* The local model of Sec. 5.2 for a node box [blo, bhi]: the same model restricted to the
+ * observations (inducing points) M' inside the box enlarged by beta * l_d on each side of axis d
+ * (the local set Algorithm 1 passes down the tree; a child's enlarged box lies inside its
+ * parent's, so filtering M by the child's box gives the same set).  Plain GPR: the GP conditioned
+ * on y at M' only; SGPR: Eq. 1 with mu_M', A_M'M' and K_M'M'.  Returns NULL when M' = M (use the
+ * full model); an empty M' gives the prior. */
+static or_model *local_model(const or_model *M, const double blo[3], const double bhi[3], double beta)
+{
+    int64_t m = M->m, c = 0;
+    int64_t *idx = (int64_t *)malloc(sizeof(int64_t) * (m > 0 ? m : 1));
+    for (int64_t i = 0; i < m; ++i) {
+        const double *x = M->X + 3 * i;
+        int in = 1;
+        for (int d = 0; d < 3; ++d)
+            if (x[d] < blo[d] - beta * M->ell[d] || x[d] > bhi[d] + beta * M->ell[d]) in = 0;
+        if (in) idx[c++] = i;
+    }
+    if (c == m) { free(idx); return NULL; }
+    double *X = (double *)malloc(sizeof(double) * 3 * (c > 0 ? c : 1));
+    double *y = (double *)malloc(sizeof(double) * (c > 0 ? c : 1));
+    for (int64_t a = 0; a < c; ++a) {
+        for (int d = 0; d < 3; ++d) X[3 * a + d] = M->X[3 * idx[a] + d];
+        y[a] = M->y[idx[a]];
+    }
+    or_model *L;
+    if (M->sgpr) {
+        double *A = (double *)malloc(sizeof(double) * (c > 0 ? c * c : 1));
+        for (int64_t a = 0; a < c; ++a)
+            for (int64_t b = 0; b < c; ++b) A[a * c + b] = M->A[idx[a] * m + idx[b]];
+        L = or_model_create_sgpr(X, y, A, c, M->kernel, M->ell, M->sf2, M->kmm_jitter);
+        free(A);
+    } else {
+        L = or_model_create(X, y, c, M->kernel, M->ell, M->sf2, M->sn2);
+    }
+    free(X); free(y); free(idx);
+    return L;
+}
+
 /* One level of Algorithm 1 for `count` nodes (packed i | j<<21 | k<<42).
  * Per node: decision[q] = 0 (drop), 1 (subdivide: p1 > alpha and p2 > alpha),
  * 2 (subdivide: bound > alpha); bound[q] = the upper bound used (NaN for 1);
  * side[q] = 0 both sides, 1 lower only (p2 <= alpha), 2 upper only (p1 <= alpha).
  * The p-test uses the observations inside the closed node box with the latent
- * posterior at the observations.  d = number of grid points in the node. */
+ * posterior at the observations.  d = number of grid points in the node.
+ * beta >= 0: the bound is minimised on the node's local model (local_model above; beta in units
+ * of the length scales); beta < 0: on the full model. */
 void or_octree_level(const or_model *M, const or_grid *g, int D, int l, double theta, double alpha, int T,
-                     const int64_t *nodes, int64_t count, int8_t *decision, double *bound, int8_t *side_out)
+                     double beta, const int64_t *nodes, int64_t count, int8_t *decision, double *bound,
+                     int8_t *side_out)
 {
     int64_t m = M->m;
     int8_t *flo = (int8_t *)malloc((size_t)m), *fhi = (int8_t *)malloc((size_t)m);
@@ -1011,8 +1053,11 @@ void or_octree_level(const or_model *M, const or_grid *g, int D, int l, double t
             else { do_lo = 0; do_hi = 1; }
             double dcount = (double)((p1[0] - p0[0] + 1) * (p1[1] - p0[1] + 1) * (p1[2] - p0[2] + 1));
             double lB_lo = -INFINITY, lB_hi = -INFINITY; /* ln B; B = 0 when the side is not used */
-            if (do_lo) lB_lo = log_norm_cdf(node_min_g(M, g, p0, p1, blo, bhi, theta, +1, T, kb, dk, v, P, NULL));
-            if (do_hi) lB_hi = log_norm_cdf(node_min_g(M, g, p0, p1, blo, bhi, theta, -1, T, kb, dk, v, P, NULL));
+            or_model *Lm = beta >= 0.0 ? local_model(M, blo, bhi, beta) : NULL;
+            const or_model *E = Lm ? Lm : M;
+            if (do_lo) lB_lo = log_norm_cdf(node_min_g(E, g, p0, p1, blo, bhi, theta, +1, T, kb, dk, v, P, NULL));
+            if (do_hi) lB_hi = log_norm_cdf(node_min_g(E, g, p0, p1, blo, bhi, theta, -1, T, kb, dk, v, P, NULL));
+            if (Lm) or_model_destroy(Lm);
             double bnd;
             if (do_lo && do_hi) bnd = -expm1(dcount * lB_lo) - exp(dcount * lB_hi);
             else if (do_lo) bnd = -expm1(dcount * lB_lo);

@@ -9,11 +9,11 @@ extern "C" void gpr_lcp_options_default(gpr_lcp_options *o)
 {
     if (!o) return;
     o->alpha = 1e-3;
-    o->beta = 6.0;
+    o->beta = -1.0;
     o->est = GPR_EST_SOV_QMC;
     o->n_samples = 1600;
     o->seed = 0;
-    o->jitter = 1e-4;
+    o->jitter = 1e-10;
     o->skip_eps = 1e-9;
     o->prec = GPR_P_FP32;
     o->max_iters_min = 4;
@@ -59,6 +59,7 @@ bool opts_valid(const gpr_lcp_options *o)
 {
     if (!est_opts_valid(o)) return false;
     if (!(o->alpha >= 0.0) || !isfinite(o->alpha)) return false;
+    if (isnan(o->beta)) return false;
     if (o->prec < GPR_P_FP64 || o->prec > GPR_P_BF16X3) return false;
     if (o->max_iters_min < 0 || o->max_iters_min > 64) return false;
     if (o->exact != GPR_EXACT_AUTO && o->exact != GPR_EXACT_FP64) return false;

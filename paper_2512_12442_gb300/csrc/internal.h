@@ -114,6 +114,8 @@ struct gpr_model {
     // Q = K_MM^-1 - K_MM^-1 A_M K_MM^-1 = G^T G, so every whitened kernel computes Eq. 1 unchanged;
     // vy = G^-T alpha, alpha = K_MM^-1 mu_M, y = mu_M, L = chol(K_MM + jitter I), sn2 = 0
     bool sgpr = false;
+    double kmm_jitter = 0.0;  // SGPR: jitter on the diagonal of K_MM
+    double *A_M = nullptr;    // SGPR: m x m A_M (FP64), read by the local model of the bound
 };
 
 // Scope of one fill of the per-point (mean, var) table: holds the model's mv lock, orders the

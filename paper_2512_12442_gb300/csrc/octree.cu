@@ -628,6 +628,321 @@ __global__ void k_children(GridDev g, int D, int l, const int64_t *nodes, int64_
 
 unsigned nb(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
+// ---- Local model of Sec. 5.2 (beta >= 0): the bound of a node is minimised on the model
+// restricted to the observations M' inside the node box enlarged by beta * l_d per axis.
+
+__device__ __forceinline__ bool in_local_box(const Geom &G, const double *x, double beta, const KernParams &kp)
+{
+    for (int d = 0; d < 3; ++d)
+        if (x[d] < G.blo[d] - beta * kp.ell[d] || x[d] > G.bhi[d] + beta * kp.ell[d]) return false;
+    return true;
+}
+
+// Pending nodes whose local set is a strict subset of M: flag them (decision 5 keeps the full-model
+// kernels off them) and track the largest local set.
+__global__ void k_local_flag(GridDev g, int D, int l, const int64_t *nodes, int64_t count, int8_t *decision,
+                             const double *X, int64_t m, double beta, KernParams kp, uint8_t *flag,
+                             unsigned long long *cmax)
+{
+    int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= count) return;
+    flag[q] = 0;
+    if (decision[q] != 0) return;
+    Geom G = node_geom(g, D, l, nodes[q]);
+    int64_t c = 0;
+    for (int64_t i = 0; i < m; ++i) c += in_local_box(G, X + 3 * i, beta, kp) ? 1 : 0;
+    if (c == m) return;
+    flag[q] = 1;
+    decision[q] = 5;
+    atomicMax(cmax, (unsigned long long)c);
+}
+
+__device__ __forceinline__ double kval64(const KernParams &kp, const double *a, const double *b)
+{
+    double r2 = 0.0;
+    for (int d = 0; d < 3; ++d) {
+        double t = (a[d] - b[d]) / kp.ell[d];
+        r2 += t * t;
+    }
+    if (kp.kind == GPR_K_SE) return kp.sf2 * exp(-0.5 * r2);
+    double r = sqrt(r2), s5r = 2.2360679774997896964 * r;
+    return kp.sf2 * (1.0 + s5r + (5.0 / 3.0) * r2) * exp(-s5r);
+}
+
+// k(x, b) and d k(x, b) / d x.
+__device__ __forceinline__ double kgrad64(const KernParams &kp, const double *x, const double *b, double gr[3])
+{
+    double r2 = 0.0, dd[3];
+    for (int d = 0; d < 3; ++d) {
+        dd[d] = x[d] - b[d];
+        double t = dd[d] / kp.ell[d];
+        r2 += t * t;
+    }
+    if (kp.kind == GPR_K_SE) {
+        double k = kp.sf2 * exp(-0.5 * r2);
+        for (int d = 0; d < 3; ++d) gr[d] = -k * dd[d] / (kp.ell[d] * kp.ell[d]);
+        return k;
+    }
+    double r = sqrt(r2), s5r = 2.2360679774997896964 * r, e = exp(-s5r);
+    double c = -(5.0 / 3.0) * kp.sf2 * (1.0 + s5r) * e;
+    for (int d = 0; d < 3; ++d) gr[d] = c * dd[d] / (kp.ell[d] * kp.ell[d]);
+    return kp.sf2 * (1.0 + s5r + (5.0 / 3.0) * r2) * e;
+}
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+struct LocalModel {
+    const double *X, *y, *A;  // A: SGPR A_M (m x m), nullptr for plain GPR
+    int64_t m;
+    KernParams kp;
+    double diag;  // noise variance (plain GPR) or K_MM jitter (SGPR)
+};
+
+// Per-warp FP64 work space of the local kernel.
+struct LocalWs {
+    double *L, *A, *v, *al, *k, *dk, *w, *a, *t, *ca;
+    int32_t *idx;
+};
+
+__device__ LocalWs local_ws(double *base, int32_t *ibase, int64_t warp, int64_t cmax, bool sgpr)
+{
+    const int64_t per = cmax * cmax * (sgpr ? 2 : 1) + 12 * cmax;
+    double *p = base + warp * per;
+    LocalWs W;
+    W.L = p; p += cmax * cmax;
+    W.A = sgpr ? p : nullptr; p += sgpr ? cmax * cmax : 0;
+    W.v = p; p += cmax;
+    W.al = p; p += cmax;
+    W.k = p; p += cmax;
+    W.dk = p; p += 3 * cmax;
+    W.w = p; p += cmax;
+    W.a = p; p += cmax;
+    W.t = p; p += cmax;
+    W.ca = p; p += cmax;
+    W.idx = ibase + warp * cmax;
+    return W;
+}
+
+// Forward solve x = L^-1 x in place (L column-major c x c, lower), warp-cooperative.
+__device__ void fwd_solve(const double *L, int64_t c, double *x, int lane)
+{
+    for (int64_t j = 0; j < c; ++j) {
+        __syncwarp();
+        const double xj = x[j] / L[j + j * c];
+        __syncwarp();
+        if (lane == 0) x[j] = xj;
+        for (int64_t r = j + 1 + lane; r < c; r += 32) x[r] -= L[r + j * c] * xj;
+    }
+    __syncwarp();
+}
+
+// Backward solve y = L^-T x (into y; x unchanged).
+__device__ void bwd_solve(const double *L, int64_t c, const double *x, double *y, int lane)
+{
+    for (int64_t j = c - 1; j >= 0; --j) {
+        double s = 0.0;
+        for (int64_t r = j + 1 + lane; r < c; r += 32) s += L[r + j * c] * y[r];
+        s = warp_sum(s);
+        if (lane == 0) y[j] = (x[j] - s) / L[j + j * c];
+        __syncwarp();
+    }
+}
+
+// g = (theta - mu(x)) / sigma(x) on the local model, and (want_grad) its gradient.
+__device__ double local_eval(const LocalModel &Mo, const LocalWs &W, int64_t c, const double *x, double theta,
+                             bool want_grad, double grad[3], int lane)
+{
+    for (int64_t r = lane; r < c; r += 32) {
+        double gr[3];
+        const double kv = kgrad64(Mo.kp, x, Mo.X + 3 * W.idx[r], gr);
+        W.k[r] = kv;
+        W.w[r] = kv;
+        for (int d = 0; d < 3; ++d) W.dk[3 * r + d] = gr[d];
+    }
+    __syncwarp();
+    fwd_solve(W.L, c, W.w, lane);  // w = L'^-1 k
+    double mu = 0.0, ww = 0.0;
+    for (int64_t r = lane; r < c; r += 32) {
+        mu += W.w[r] * W.v[r];
+        ww += W.w[r] * W.w[r];
+    }
+    mu = warp_sum(mu);
+    const double kxx = kval64(Mo.kp, x, x);
+    double var;
+    if (Mo.A) {
+        // Eq. 1: var = k(x,x) - k^T a + a^T A' a, a = K'^-1 k
+        bwd_solve(W.L, c, W.w, W.a, lane);
+        for (int64_t r = lane; r < c; r += 32) {
+            double s = 0.0;
+            for (int64_t q = 0; q < c; ++q) s += W.A[r + q * c] * W.a[q];
+            W.ca[r] = s;
+        }
+        __syncwarp();
+        double ka = 0.0, aca = 0.0;
+        for (int64_t r = lane; r < c; r += 32) {
+            ka += W.k[r] * W.a[r];
+            aca += W.a[r] * W.ca[r];
+        }
+        var = kxx - warp_sum(ka) + warp_sum(aca);
+    } else {
+        var = kxx - warp_sum(ww);
+    }
+    const double fl = 1e-12 * Mo.kp.sf2;
+    if (!(var > fl)) var = fl;
+    const double sd = sqrt(var), gl = (theta - mu) / sd;
+    if (!want_grad) return gl;
+    // P = Kt'^-1 k (plain) or a - K'^-1 A' a (SGPR); d var = -2 dk^T P, d mu = dk^T alpha'
+    if (Mo.A) {
+        for (int64_t r = lane; r < c; r += 32) W.t[r] = W.ca[r];
+        __syncwarp();
+        fwd_solve(W.L, c, W.t, lane);
+        bwd_solve(W.L, c, W.t, W.w, lane);  // w = K'^-1 A' a
+        for (int64_t r = lane; r < c; r += 32) W.t[r] = W.a[r] - W.w[r];
+    } else {
+        bwd_solve(W.L, c, W.w, W.t, lane);
+    }
+    __syncwarp();
+    double gm[3] = {0, 0, 0}, gv[3] = {0, 0, 0};
+    for (int64_t r = lane; r < c; r += 32)
+        for (int d = 0; d < 3; ++d) {
+            gm[d] += W.dk[3 * r + d] * W.al[r];
+            gv[d] += -2.0 * W.dk[3 * r + d] * W.t[r];
+        }
+    for (int d = 0; d < 3; ++d) {
+        gm[d] = warp_sum(gm[d]);
+        gv[d] = warp_sum(gv[d]);
+        grad[d] = -gm[d] / sd - gl * gv[d] / (2.0 * var);
+    }
+    __syncwarp();
+    return gl;
+}
+
+// One warp per listed node: gather M', factor K' (FP64, left-looking by columns), then the same
+// minimiser as the full-model path (exact over grid points for nodes of <= 3 points per axis; else
+// the best of the 3x3x3 lattice and T projected steps per side), bound and decision.
+__global__ void k_local_nodes(GridDev g, int D, int l, const int64_t *nodes, const int64_t *list, int64_t nl,
+                              LocalModel Mo, double beta, double theta, double alpha, int T, const int8_t *sides,
+                              int8_t *decision, double *bound, double *ws, int32_t *iws, int64_t cmax, int *status)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const LocalWs W = local_ws(ws, iws, warp, cmax, Mo.A != nullptr);
+    for (int64_t t = warp; t < nl; t += nwarps) {
+        const int64_t q = list[t];
+        const Geom G = node_geom(g, D, l, nodes[q]);
+        // gather the local set (ascending observation index)
+        int64_t c = 0;
+        for (int64_t base = 0; base < Mo.m; base += 32) {
+            const int64_t i = base + lane;
+            const bool in = i < Mo.m && in_local_box(G, Mo.X + 3 * i, beta, Mo.kp);
+            const unsigned msk = __ballot_sync(0xffffffffu, in);
+            if (in) W.idx[c + __popc(msk & ((1u << lane) - 1))] = (int32_t)i;
+            c += __popc(msk);
+        }
+        __syncwarp();
+        // K' (column-major, lower) and, for SGPR, A'
+        for (int64_t s2 = 0; s2 < c; ++s2)
+            for (int64_t r = s2 + lane; r < c; r += 32)
+                W.L[r + s2 * c] = kval64(Mo.kp, Mo.X + 3 * W.idx[r], Mo.X + 3 * W.idx[s2]) + (r == s2 ? Mo.diag : 0.0);
+        if (Mo.A)
+            for (int64_t s2 = 0; s2 < c; ++s2)
+                for (int64_t r = lane; r < c; r += 32) W.A[r + s2 * c] = Mo.A[W.idx[r] * Mo.m + W.idx[s2]];
+        __syncwarp();
+        for (int64_t j = 0; j < c; ++j) {
+            for (int64_t r = j + lane; r < c; r += 32) {
+                double a = W.L[r + j * c];
+                for (int64_t k = 0; k < j; ++k) a -= W.L[r + k * c] * W.L[j + k * c];
+                W.t[r] = a;
+            }
+            __syncwarp();
+            double piv = W.t[j];
+            if (!(piv > 0.0)) {
+                if (lane == 0) atomicCAS(status, 0, (int)GPR_ERR_NOT_PD);
+                piv = 1e-300;
+            }
+            const double d = sqrt(piv);
+            for (int64_t r = j + lane; r < c; r += 32) W.L[r + j * c] = r == j ? d : W.t[r] / d;
+            __syncwarp();
+        }
+        // v' = L'^-1 y', alpha' = L'^-T v'  (y' = y or mu_M restricted to M')
+        for (int64_t r = lane; r < c; r += 32) W.v[r] = Mo.y[W.idx[r]];
+        __syncwarp();
+        fwd_solve(W.L, c, W.v, lane);
+        bwd_solve(W.L, c, W.v, W.al, lane);
+        const int sd = sides[q];
+        double gmin[2] = {INFINITY, INFINITY};
+        double gr[3];
+        const bool small = G.p1[0] - G.p0[0] <= 2 && G.p1[1] - G.p0[1] <= 2 && G.p1[2] - G.p0[2] <= 2;
+        const double dcount =
+            (double)((G.p1[0] - G.p0[0] + 1) * (G.p1[1] - G.p0[1] + 1) * (G.p1[2] - G.p0[2] + 1));
+        if (small) {
+            for (int64_t cz = G.p0[2]; cz <= G.p1[2]; ++cz)
+                for (int64_t cy = G.p0[1]; cy <= G.p1[1]; ++cy)
+                    for (int64_t cx = G.p0[0]; cx <= G.p1[0]; ++cx) {
+                        const double x[3] = {g.lo[0] + (double)cx * g.h[0], g.lo[1] + (double)cy * g.h[1],
+                                             g.lo[2] + (double)cz * g.h[2]};
+                        const double v = local_eval(Mo, W, c, x, theta, false, gr, lane);
+                        gmin[0] = fmin(gmin[0], v);
+                        gmin[1] = fmin(gmin[1], -v);
+                    }
+        } else {
+            double bx[2][3], bg[2][3];
+            for (int t27 = 0; t27 < 27; ++t27) {
+                const int id[3] = {t27 % 3, (t27 / 3) % 3, t27 / 9};
+                double x[3];
+                for (int d = 0; d < 3; ++d) x[d] = G.blo[d] + 0.5 * (double)id[d] * (G.bhi[d] - G.blo[d]);
+                const double v = local_eval(Mo, W, c, x, theta, true, gr, lane);
+                for (int s2 = 0; s2 < 2; ++s2) {
+                    const double sg = s2 == 0 ? 1.0 : -1.0;
+                    if (sg * v < gmin[s2]) {
+                        gmin[s2] = sg * v;
+                        for (int d = 0; d < 3; ++d) { bx[s2][d] = x[d]; bg[s2][d] = sg * gr[d]; }
+                    }
+                }
+            }
+            // the lattice bound already above alpha decides (the steps only lower g)
+            if (!(bound_of(sd, dcount, gmin[0], gmin[1]) > alpha)) {
+                for (int s2 = 0; s2 < 2; ++s2) {
+                    if (!(sd & (1 << s2))) continue;
+                    const double sg = s2 == 0 ? 1.0 : -1.0;
+                    for (int st = 0; st < T; ++st) {
+                        double wv[3], u[3], un = 0.0;
+                        for (int d = 0; d < 3; ++d) {
+                            wv[d] = G.bhi[d] - G.blo[d];
+                            u[d] = -bg[s2][d] * wv[d];
+                            un = fmax(un, fabs(u[d]));
+                        }
+                        if (!(un > 0.0)) break;
+                        const double eta = 0.25 * ldexp(1.0, -st);
+                        double xc[3];
+                        for (int d = 0; d < 3; ++d) {
+                            const double xn = bx[s2][d] + eta * wv[d] * u[d] / un;
+                            xc[d] = xn < G.blo[d] ? G.blo[d] : (xn > G.bhi[d] ? G.bhi[d] : xn);
+                        }
+                        const double v = sg * local_eval(Mo, W, c, xc, theta, true, gr, lane);
+                        if (v < gmin[s2]) {
+                            gmin[s2] = v;
+                            for (int d = 0; d < 3; ++d) { bx[s2][d] = xc[d]; bg[s2][d] = sg * gr[d]; }
+                        }
+                    }
+                }
+            }
+        }
+        if (lane == 0) {
+            const double bnd = bound_of(sd, dcount, gmin[0], gmin[1]);
+            bound[q] = bnd;
+            decision[q] = bnd > alpha ? 2 : 0;
+        }
+        __syncwarp();
+    }
+}
+
 struct OctBuffers {
     int64_t *front[2];
     int8_t *decision, *sides;
@@ -642,6 +957,8 @@ struct OctBuffers {
     float *part;
     uint8_t *unal;
     int64_t *ulist;
+    uint8_t *lflag2;  // nodes on the local model (beta >= 0)
+    int64_t *llist;
     uint8_t *cvalid;
     MinState *ms;
     unsigned long long *counters;  // [0] nnext, [1] nsub
@@ -704,7 +1021,7 @@ gpr_status octree_lcp(gpr_model *M, const gpr_grid *grid, double theta, int D, c
                    Carver::round((size_t)nc * sizeof(MinState)) + Carver::round((size_t)max_large * 27 * 16) + 512 +
                    csb + Carver::round(tc_partial_elems(GPR_P_BF16X3, M, n) * 4) + Carver::round((size_t)max_large * 2) +
                    Carver::round((size_t)max_large * 16) + 8192 + Carver::round((size_t)nc * 4) + 2 * Carver::round((size_t)nc) +
-                   256 * 22;
+                   Carver::round((size_t)nc) + Carver::round((size_t)nc * 8) + 256 * 24;
     gpr_precision pp = opts->prec == GPR_P_FP64 ? GPR_P_FP32 : opts->prec;
     GridCache *C = nullptr;
     GPR_TRY(grid_cache(M, grid, g, pp, &C, st));
@@ -753,6 +1070,9 @@ gpr_status octree_lcp(gpr_model *M, const gpr_grid *grid, double theta, int D, c
     B.part = cv.take<float>(tc_partial_elems(GPR_P_BF16X3, M, n));
     B.unal = cv.take<uint8_t>((size_t)max_large * 2);
     B.ulist = cv.take<int64_t>((size_t)max_large * 2);
+    B.lflag2 = cv.take<uint8_t>((size_t)nc);
+    B.llist = cv.take<int64_t>((size_t)nc);
+    const bool local = opts->beta >= 0.0 && isfinite(opts->beta);
     int32_t *slot = (int32_t *)B.tmp_mean;  // reused by the leaf phase (n int32 fits in n floats)
     int64_t *clist = B.pend;                 // reused by the leaf phase (nc int64)
 
@@ -794,6 +1114,20 @@ gpr_status octree_lcp(gpr_model *M, const gpr_grid *grid, double theta, int D, c
         k_ptest<<<nb(count, 256), 256, 0, st>>>(g, D, l, nodes, count, pyr_lv + pyr.off[l], pyr.dim[l][0],
                                                  pyr.dim[l][1], B.decision, B.sides);
         note_launch();
+        // nodes whose local set (Sec. 5.2) is a strict subset of the observations leave the
+        // full-model path below and are bounded on their local model
+        int64_t nlocal = 0;
+        unsigned long long cmax = 0;
+        if (local) {
+            GPR_CUDA_TRY(cudaMemsetAsync(B.counters + 2, 0, sizeof(unsigned long long), st));
+            k_local_flag<<<nb(count, 128), 128, 0, st>>>(g, D, l, nodes, count, B.decision, M->X, m, opts->beta, M->kp,
+                                                         B.lflag2, B.counters + 2);
+            note_launch();
+            GPR_TRY(compact_flags(B.lflag2, count, B.llist, nullptr, &nlocal, B.cscr, B.csb, st));
+            if (nlocal > 0)
+                GPR_CUDA_TRY(cudaMemcpyAsync(&cmax, B.counters + 2, sizeof cmax, cudaMemcpyDeviceToHost, st));
+            GPR_CUDA_TRY(cudaStreamSynchronize(st));
+        }
         // small nodes: exact minimum over grid points from the per-point table
         {
             MvFillScope fill(M, st);
@@ -888,6 +1222,31 @@ gpr_status octree_lcp(gpr_model *M, const gpr_grid *grid, double theta, int D, c
                     note_launch();
                 }
             }
+        }
+        if (nlocal > 0) {
+            // one warp per local node; FP64 work space per warp, bounded to ~2 GB
+            const int64_t c = cmax > 0 ? (int64_t)cmax : 1;
+            const size_t per = sizeof(double) * ((size_t)c * c * (M->sgpr ? 2 : 1) + 12 * (size_t)c) +
+                               sizeof(int32_t) * (size_t)c;
+            int64_t nw = nlocal < 4 * (int64_t)num_sms() ? nlocal : 4 * (int64_t)num_sms();
+            const int64_t cap = (int64_t)(((size_t)2 << 30) / per);
+            if (nw > cap) nw = cap > 0 ? cap : 1;
+            void *lws = nullptr;
+            GPR_CUDA_TRY(cudaMallocAsync(&lws, per * (size_t)nw + 256, st));
+            double *dws = (double *)lws;
+            int32_t *iws = (int32_t *)((char *)lws + sizeof(double) * ((size_t)c * c * (M->sgpr ? 2 : 1) + 12 * (size_t)c) * nw);
+            LocalModel Mo{M->X, M->y, M->sgpr ? M->A_M : nullptr, m, M->kp, M->sgpr ? M->kmm_jitter : M->sn2};
+            int *status = gpr_status_word();
+            if (!status) return GPR_ERR_CUDA;
+            {
+                ProfScope ps("oct_local", st, (double)nlocal);
+                k_local_nodes<<<(unsigned)((nw + 3) / 4), 128, 0, st>>>(g, D, l, nodes, B.llist, nlocal, Mo, opts->beta,
+                                                                        theta, opts->alpha, T, B.sides, B.decision,
+                                                                        B.bound, dws, iws, c, status);
+            }
+            note_launch();
+            GPR_CUDA_TRY(cudaGetLastError());
+            GPR_CUDA_TRY(cudaFreeAsync(lws, st));
         }
         GPR_CUDA_TRY(cudaMemsetAsync(B.counters, 0, 2 * sizeof(unsigned long long), st));
         k_children<<<nb(count, 256), 256, 0, st>>>(g, D, l, nodes, count, B.decision, B.front[1 - cur], B.counters,

@@ -486,6 +486,7 @@ extern "C" gpr_status gpr_model_create_sgpr(const double *inducing_xyz, const do
     if (!status) return GPR_ERR_CUDA;
     gpr_model *M = new gpr_model();
     M->sgpr = true;
+    M->kmm_jitter = kmm_jitter;
     M->m = m;
     M->mp = (m + 63) / 64 * 64;
     M->kp.kind = kernel;
@@ -538,10 +539,12 @@ extern "C" gpr_status gpr_model_create_sgpr(const double *inducing_xyz, const do
     ALLOC(T3, sq);
     ALLOC(AMd, sq);
     ALLOC(v0, sizeof(double) * mb);
+    ALLOC(M->A_M, sizeof(double) * m * m);
 #undef ALLOC
     if (cudaMemcpyAsync(M->X, inducing_xyz, sizeof(double) * 3 * m, cudaMemcpyHostToDevice, st) != cudaSuccess ||
         cudaMemcpyAsync(M->y, mu_M, sizeof(double) * m, cudaMemcpyHostToDevice, st) != cudaSuccess ||
         cudaMemcpyAsync(T3, A_M, sizeof(double) * m * m, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(M->A_M, A_M, sizeof(double) * m * m, cudaMemcpyHostToDevice, st) != cudaSuccess ||
         cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess)
         return fail(GPR_ERR_CUDA);
     const unsigned gsq = nblk(mb * mb, 256);
@@ -602,7 +605,7 @@ extern "C" gpr_status gpr_model_destroy(gpr_model *M)
     if (!M) return GPR_ERR_ARG;
     cudaDeviceSynchronize();
     cudaFree(M->X); cudaFree(M->y); cudaFree(M->L); cudaFree(M->Linv); cudaFree(M->vy); cudaFree(M->alpha);
-    cudaFree(M->mu_obs); cudaFree(M->var_obs); cudaFree(M->BT64); cudaFree(M->BT32); cudaFree(M->vy32); cudaFree(M->alpha_ff); cudaFree(M->Linv32); cudaFree(M->X32); cudaFree(M->alpha32);
+    cudaFree(M->mu_obs); cudaFree(M->var_obs); cudaFree(M->A_M); cudaFree(M->BT64); cudaFree(M->BT32); cudaFree(M->vy32); cudaFree(M->alpha_ff); cudaFree(M->Linv32); cudaFree(M->X32); cudaFree(M->alpha32);
     for (int w = 0; w < 2; ++w)
         if (M->own_ws.ptr[w]) cudaFree(M->own_ws.ptr[w]);
     tc_release(M);

@@ -41,7 +41,7 @@ def test_library_exports_every_declared_symbol(lib):
 def test_option_defaults_and_status_strings(lib):
     import paper_2512_12442_gb300 as g
     o = g.lcp_options()
-    assert (o.alpha, o.beta, o.n_samples, o.jitter, o.skip_eps, o.max_iters_min) == (1e-3, 6.0, 1600, 1e-4, 1e-9, 4)
+    assert (o.alpha, o.beta, o.n_samples, o.jitter, o.skip_eps, o.max_iters_min) == (1e-3, -1.0, 1600, 1e-10, 1e-9, 4)
     assert lib.gpr_status_string(2) == b"kernel matrix not positive definite"
 
 

@@ -135,3 +135,61 @@ def test_adaptive_argument_checks(torch, g):
     with pytest.raises(g.GPRError) as e:
         g.gpr_lcp_adaptive(M, g.make_grid(9), 0.0, 2, g.lcp_options(), out)  # 2^2 < 8 cells
     assert e.value.status == g.GPR_ERR_ARG
+
+
+@pytest.mark.parametrize("kind", ["gpr", "sgpr"])
+def test_local_model_levels_match_oracle(torch, g, kind):
+    """Sec. 5.2's local model (beta >= 0): nodes whose enlarged box (beta * l_d per axis) leaves some
+    observations out are bounded on the model of the rest, in FP64 on the device (one warp per node).
+    Level by level against the oracle: p-test decisions equal, bound decisions equal except within a
+    factor 3 of alpha, and the bounds of nodes both sides minimised fully agree to 1e-6 relative."""
+    w = workloads.config2() if kind == "gpr" else workloads.sgpr(n=33)
+    beta = 1.0
+    M = model_of(w)
+    om = oracle.Model.from_workload(w)
+    n, D, th = 33, 5, w.isovalues[1]
+    grid = g.make_grid(n)
+    opts = g.lcp_options(beta=beta)
+    seen = 0
+    for l in range(1, D + 1):
+        nodes, dec, bnd = g.gpr_octree_trace(M, grid, th, D, opts, l)
+        if len(nodes) == 0:
+            break
+        odec, obnd, _ = om.octree_level(n, D, l, th, nodes, beta=beta)
+        assert np.array_equal(odec == 1, dec == 1), l
+        bad = (odec > 0) != (dec > 0)
+        near = (obnd >= 1e-3 / 3) & (obnd <= 3e-3)
+        assert np.all(near[bad]), (l, obnd[bad & ~near][:8], bnd[bad & ~near][:8])
+        both0 = (odec == 0) & (dec == 0)
+        if both0.any():
+            np.testing.assert_allclose(bnd[both0], obnd[both0], rtol=1e-6, atol=1e-300)
+        seen += len(nodes)
+    assert seen > 100
+    # a beta whose boxes cover the domain gives the full model's decisions exactly
+    for l in (2, 3):
+        a = g.gpr_octree_trace(M, grid, th, D, g.lcp_options(beta=50.0), l)
+        b = g.gpr_octree_trace(M, grid, th, D, g.lcp_options(), l)
+        np.testing.assert_array_equal(a[0], b[0]); np.testing.assert_array_equal(a[1], b[1])
+
+
+def test_local_model_adaptive_field(torch, g):
+    """With the local model the adaptive field still equals the dense field on its S (the paper-scale
+    field on a 33^3 grid, beta = 1: about half of the cells are kept)."""
+    w = workloads.config2()
+    M = model_of(w)
+    n, D, th = 33, 5, w.isovalues[1]
+    grid = g.make_grid(n)
+    opts = g.lcp_options(beta=1.0)
+    a = torch.zeros((n - 1) ** 3, dtype=torch.float32, device="cuda")
+    d = torch.zeros_like(a)
+    st = g.gpr_lcp_adaptive(M, grid, th, D, opts, a)
+    g.gpr_lcp_dense(M, grid, th, opts, d)
+    g.gpr_sync()
+    nodes, dec, _ = g.gpr_octree_trace(M, grid, th, D, opts, D)
+    leaf = nodes[dec > 0]
+    lin = (leaf & 0x1FFFFF) + (n - 1) * (((leaf >> 21) & 0x1FFFFF) + (n - 1) * ((leaf >> 42) & 0x1FFFFF))
+    inS = np.zeros((n - 1) ** 3, bool); inS[lin] = True
+    av, dv = a.cpu().numpy(), d.cpu().numpy()
+    assert st["leaf_cells"] == inS.sum() and 0 < inS.sum() < inS.size
+    assert np.array_equal(av[inS], dv[inS]) and np.all(av[~inS] == 0)
+

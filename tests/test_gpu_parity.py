@@ -224,9 +224,10 @@ def test_lcp_closed_form_estimators_config1(torch, g, est):
     ref = oracle.Model.from_workload(w).lcp_dense(w.n, th, est=e_or)
     assert np.abs(gpu - ref).max() <= 2e-5, np.abs(gpu - ref).max()
     assert st["cells_estimated"] > 100 and (ref > 0.01).sum() > 100
-    sov, _ = _lcp_dense_gpu(g, torch, M, w.n, th, prec=g.GPR_P_FP64)
     if est == "edge":
-        assert np.all(gpu <= sov + 1e-3)  # a crossed edge crosses the cell
+        # a crossed edge crosses the cell: against a 16,384-point SOV field (lattice error ~3e-3)
+        sov, _ = _lcp_dense_gpu(g, torch, M, w.n, th, prec=g.GPR_P_FP64, n_samples=1 << 14)
+        assert np.all(gpu <= sov + 5e-3), float((gpu - sov).max())
 
 
 def test_lcp_closed_form_estimators_paper_scale_adaptive(torch, g):

@@ -4,8 +4,10 @@ K_MM^-1 - K_MM^-1 A_M K_MM^-1 and runs the plain-GPR kernels; the oracle evaluat
 
 Inputs: workloads.sgpr, the optimal inducing distribution (Titsias 2009) fitted to training samples
 of the paper-scale field (GPy stands in for the paper's fitting, which is out of scope).
-Tolerances as in test_gpu_parity: FP64 statistics within 1e-9 of the field scale; cell LCP within
-1e-4 absolute; octree decisions as in test_gpu_adaptive (p-test exact, bound decisions may differ
+Tolerances as in test_gpu_parity: FP64 statistics within 1e-9 of the field scale (variances within
+1e-10 of the signal variance, 1e-8 for the paper-scale model: its K_MM carries only the fitting jitter
+1e-6, so kappa(K_MM) ~ 5e7 against kappa(Kt) ~ 4e5 for the plain models and both sides round ~100x
+more); cell LCP within 1e-4 absolute; octree decisions as in test_gpu_adaptive (p-test exact, bound decisions may differ
 only where the oracle's bound lies within a factor 3 of alpha).
 """
 import numpy as np
@@ -146,7 +148,7 @@ def test_sgpr_paper_scale_full_grid(torch, g, paper_scale):
     mu, var = om.posterior(P)
     o = _np(out)
     assert np.abs(o[:, 0] - mu).max() <= 1e-9 * np.abs(w.y).max()
-    assert np.abs(o[:, 1] - var).max() <= 1e-10
+    assert np.abs(o[:, 1] - var).max() <= 1e-8 * w.sf2
     field = torch.zeros((n - 1) ** 3, dtype=torch.float32, device="cuda")
     st = g.gpr_lcp_dense(M, grid, th, g.lcp_options(), field)
     g.gpr_sync()

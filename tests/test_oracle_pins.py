@@ -339,8 +339,7 @@ def test_edge_max_estimator():
     from scipy.stats import multivariate_normal
     rng = np.random.default_rng(23)
     mu2 = np.array([0.05, -0.1]); S2 = np.array([[0.04, 0.03], [0.03, 0.05]])
-    sd = np.sqrt(np.diag(S2)) * np.sqrt(1 + 1e-4 * 0.05 / np.diag(S2))  # the jittered diagonal
-    Sj = S2 + np.eye(2) * 1e-4 * 0.05
+    Sj = S2 + np.eye(2) * 1e-10 * 0.05  # the jittered Sigma (default tau)
     lo = multivariate_normal.cdf([0.0, 0.0], mean=mu2, cov=Sj)
     hi = multivariate_normal.cdf([0.0, 0.0], mean=-mu2, cov=Sj)
     assert oracle.cell_lcp(mu2, S2, 0.0, est=oracle.EST_EDGE) == pytest.approx(1 - lo - hi, abs=1e-9)
@@ -350,7 +349,7 @@ def test_edge_max_estimator():
         e = oracle.cell_lcp(mu, S, 0.05, est=oracle.EST_EDGE)
         full = oracle.cell_lcp(mu, S, 0.05, n_samples=20000)
         assert e <= full + 1e-3
-        Sj = S + np.eye(8) * 1e-4 * np.max(np.diag(S))
+        Sj = S + np.eye(8) * 1e-10 * np.max(np.diag(S))
         best = 0.0
         for i in range(8):
             for a in range(3):
@@ -626,6 +625,60 @@ def test_two_sided_bound_when_the_node_is_empty():
         assert side[q] == 0 and e_side == 0
         assert bnd[q] == pytest.approx(e_bnd, rel=1e-12, abs=1e-13)
         assert 1e-3 < 1.0 - bnd[q] < 0.1  # both terms matter
+
+
+def test_local_model_bound_sec52():
+    """The local approximation of Sec. 5.2: (i) when beta * l covers the domain the local set is all
+    of M and every decision and bound equals the full model's; (ii) for a node whose enlarged box
+    (beta * l_d per axis, closed) holds only some observations, the bound is Eq. upper_bound of the
+    model built from exactly those observations (selected here with NumPy); (iii) with beta = 0 a
+    node holding no observation is bounded by the prior (mu = 0, sigma^2 = sf2)."""
+    from scipy.special import log_ndtr
+    w = workloads.small(31, 50, 17, ell=(0.08, 0.1, 0.12))
+    M = oracle.Model.from_workload(w)
+    th = w.isovalues[0]
+    n, D = 17, 4
+    for l in (1, 2, 3):
+        s = 1 << l
+        nodes = np.array([i | (j << 21) | (k << 42) for k in range(s) for j in range(s) for i in range(s)], np.int64)
+        full = M.octree_level(n, D, l, th, nodes)
+        wide = M.octree_level(n, D, l, th, nodes, beta=20.0)
+        for a, b in zip(full, wide):
+            np.testing.assert_array_equal(a, b)
+    # (ii) nodes of 5^3 grid points with a strict local subset
+    l, beta, checked = 2, 1.5, 0
+    for (i, j, k) in ((0, 0, 0), (3, 1, 2), (1, 3, 3), (2, 2, 0)):
+        node = np.array([i | (j << 21) | (k << 42)], np.int64)
+        dec, bnd, side = M.octree_level(n, D, l, th, node, beta=beta)
+        if dec[0] == 1:
+            continue
+        lo = np.array([i, j, k]) * 4 / 16; hi = lo + 4 / 16
+        ell = np.array(w.ell)
+        sel = np.all((w.X >= lo - beta * ell) & (w.X <= hi + beta * ell), 1)
+        assert 0 < sel.sum() < w.m
+        sub = oracle.Model(w.X[sel], w.y[sel], w.kernel, w.ell, w.sf2, w.sn2)
+        lb = {}
+        for sd in (1, -1):
+            v, _, _, _ = sub.node_min(n, D, l, int(node[0]), th, sd)
+            lb[sd] = 125 * log_ndtr(v)
+        e = {1: -np.expm1(lb[1]), 2: -np.expm1(lb[-1]), 0: -np.expm1(lb[1]) - np.exp(lb[-1])}[int(side[0])]
+        assert bnd[0] == pytest.approx(e, rel=1e-12, abs=1e-14)
+        checked += 1
+    assert checked >= 2
+    # (iii) beta = 0: an empty node's local model is the prior
+    for q in range(64):
+        i, j, k = q % 4, (q // 4) % 4, q // 16
+        lo = np.array([i, j, k]) / 4; hi = lo + 0.25
+        if np.any(np.all((w.X >= lo) & (w.X <= hi), 1)):
+            continue
+        node = np.array([i | (j << 21) | (k << 42)], np.int64)
+        dec, bnd, side = M.octree_level(n, D, 2, th, node, beta=0.0)
+        z = th / math.sqrt(w.sf2)
+        e = -np.expm1(125 * log_ndtr(z)) - np.exp(125 * log_ndtr(-z))
+        assert side[0] == 0 and bnd[0] == pytest.approx(e, rel=1e-12, abs=1e-14)
+        break
+    else:
+        pytest.fail("no empty node")
 
 
 def test_octree_alpha_zero_keeps_nonzero_cells_and_adaptive_equals_dense():
