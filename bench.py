@@ -51,12 +51,15 @@ def parse():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--mode", default="adaptive", choices=["dense", "adaptive", "backward", "batched"],
+    p.add_argument("--mode", default="adaptive", choices=["dense", "adaptive", "backward", "batched", "sweep"],
                    help="backward: the differentiation workload (m=500 SE, 128^3, median isovalue, U(0,1) "
                         "cell weights): forward field + hand-written adjoint per step; batched: the "
                         "many-model workload (64 SE models, m in [100, 2000], grids 64^3/128^3/256^3) in one "
-                        "gpr_lcp_adaptive_batched call per step")
+                        "gpr_lcp_adaptive_batched call per step; sweep: the alpha / beta study of Sec. 7.3 "
+                        "(Fig. 5) on the paper-scale field at the median isovalue: per (alpha, beta) the adaptive "
+                        "field's time, |S| and MSE against the dense field")
     p.add_argument("--batch-count", type=int, default=64, help="models of the batched workload")
+    p.add_argument("--sweep-betas", default="0.5,1,2,8,-1", help="sweep mode: beta values (-1: full model)")
     p.add_argument("--api", default="batched", choices=["batched", "single"],
                    help="adaptive mode: the three isovalue fields in one gpr_lcp_adaptive_batched call "
                         "(concurrent fields of one model) or one gpr_lcp_adaptive call each")
@@ -337,6 +340,60 @@ def run_batched(args, g, torch, rank, world, local):
     print(json.dumps(out), flush=True)
 
 
+def run_sweep(args, g, torch, rank, world, local):
+    """Sec. 7.3's hyperparameter study on the paper-scale field (m=500, 128^3, median isovalue):
+    for every alpha in 1e-1 .. 1e-7 and beta in {1, 2, 4, 6, 8, 10, full model}, the adaptive field
+    of a freshly built model (CUDA-event time of the gpr_lcp_adaptive call; model set-up excluded),
+    its |S| and its MSE and max |dLCP| against the dense field of the same estimator."""
+    w = workloads.config2()
+    n, th = w.n, w.isovalues[1]
+    grid = g.make_grid(n)
+    stream = torch.cuda.current_stream()
+    dense = torch.zeros((n - 1) ** 3, dtype=torch.float32, device="cuda")
+    field = torch.zeros_like(dense)
+    M = g.gpr_model_create(w.X, w.y, w.kernel, w.ell, w.sf2, w.sn2, stream=stream)
+    g.gpr_lcp_dense(M, grid, th, g.lcp_options(prec=g.GPR_P_TF32X3), dense, stream=stream)
+    M.close()
+    alphas = [1e-1, 1e-2, 1e-3, 1e-4, 1e-5, 1e-6, 1e-7]
+    # beta in length scales; 8 and above cover the domain on every axis here (the full model's
+    # bound), 4 and 6 leave out a few far observations for boundary nodes and cost 10-30 s per
+    # field on the FP64 local path (--sweep-betas to include them)
+    betas = [float(b) for b in args.sweep_betas.split(",")]
+    rows = []
+
+    def one(alpha, beta):
+        Mf = g.gpr_model_create(w.X, w.y, w.kernel, w.ell, w.sf2, w.sn2, stream=stream)
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        st = g.gpr_lcp_adaptive(Mf, grid, th, w.max_depth, g.lcp_options(prec=g.GPR_P_TF32X3, alpha=alpha, beta=beta),
+                                field, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        Mf.close()
+        d = (field - dense).double()
+        return {"alpha": alpha, "beta": beta if beta >= 0 else None, "ms": e0.elapsed_time(e1),
+                "leaf_cells": st["leaf_cells"], "mse": float((d * d).mean()), "max_abs_dlcp": float(d.abs().max())}
+
+    for _ in range(max(1, args.warmup)):
+        one(1e-3, -1.0)
+    with ClockSampler(local) as clk:
+        for a in alphas:
+            for b in betas:
+                rows.append(one(a, b))
+    if rank != 0:
+        return
+    ref = next(r for r in rows if r["alpha"] == 1e-3 and r["beta"] is None)
+    out = {"metric": METRIC + " (alpha/beta study)", "value": n ** 3 / (ref["ms"] / 1e3), "unit": UNIT,
+           "n_gpus": world, "steps": len(rows), "warmup": args.warmup, "ms_per_step": ref["ms"],
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "fp32", "data": "synthetic",
+           "config": {"workload": f"{w.name}, median isovalue, adaptive D=7, SOV-QMC 1600; value/ms_per_step: "
+                                  "alpha 1e-3 with the full model", "grid": n, "m": w.m},
+           "sweep": rows, "dense_cells_nonzero": int((dense > 0).sum().item()),
+           "clocks": clk.summary(), "gpu_launches": g.gpr_launch_count()}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -370,6 +427,9 @@ def main():
         return
     if args.mode == "batched":
         run_batched(args, g, torch, rank, world, local)
+        return
+    if args.mode == "sweep":
+        run_sweep(args, g, torch, rank, world, local)
         return
     n = w.n
     ncell = (n - 1) ** 3

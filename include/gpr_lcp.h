@@ -86,6 +86,12 @@ typedef struct {
     int32_t n[3]; /* points per axis */
 } gpr_grid;
 
+/* Subdivision of the adaptive query: the paper's octree (Algorithm 1), or the K-D tree it
+ * proposes as future work (Sec. 9), which halves one axis per level (x, y, z in turn), so a
+ * region can be dropped after one halving instead of three; max_depth D keeps its meaning
+ * (cell cube 2^D per axis) and the K-D tree has 3D + 1 levels. */
+typedef enum { GPR_TREE_OCTREE = 0, GPR_TREE_KD = 1 } gpr_tree;
+
 /* Options of the LCP calls.  Defaults come from gpr_lcp_options_default(). */
 typedef struct {
     double alpha;          /* octree threshold (Algorithm 1), default 1e-3 (Sec. 7.3) */
@@ -102,10 +108,11 @@ typedef struct {
     gpr_precision prec;    /* precision of the pre-classification / octree pass, default GPR_P_FP32 */
     int32_t max_iters_min; /* projected steps T of the box minimiser, default 4 */
     gpr_exact_mode exact;  /* FP64-class corner statistics: tensor-core digit split or FP64, default AUTO */
+    gpr_tree tree;         /* subdivision of the adaptive query, default GPR_TREE_OCTREE */
 } gpr_lcp_options;
 
 typedef struct {
-    int64_t nodes_per_level[24];   /* nodes evaluated at each level of Algorithm 1 */
+    int64_t nodes_per_level[24];   /* nodes evaluated at each level of Algorithm 1 (the first 24) */
     int64_t subdiv_per_level[24];  /* nodes subdivided at each level */
     int64_t leaf_cells;            /* |S|: cells kept at the deepest level */
     int64_t recon_points;          /* grid points whose FP64-class rows this call reconstructed (points

@@ -68,12 +68,12 @@ def lib():
         L.or_stats15_block.argtypes = [C.c_void_p, C.POINTER(_Grid), _i64p, _i64p, _dp]
         L.or_lcp_block.argtypes = [C.c_void_p, C.POINTER(_Grid), C.c_double, C.c_int, C.c_int64,
                                    C.c_uint64, C.c_double, C.c_double, _i64p, _i64p, _dp]
-        L.or_octree_level.argtypes = [C.c_void_p, C.POINTER(_Grid), C.c_int, C.c_int, C.c_double,
+        L.or_octree_level.argtypes = [C.c_void_p, C.POINTER(_Grid), C.c_int, C.c_int, C.c_int, C.c_double,
                                       C.c_double, C.c_int, C.c_double, _i64p, C.c_int64, _i8p, _dp, _i8p]
         L.or_eval_g.argtypes = [C.c_void_p, _dp, C.c_int64, C.c_double, C.c_int, _dp, _dp]
         L.or_node_min.restype = C.c_double
-        L.or_node_min.argtypes = [C.c_void_p, C.POINTER(_Grid), C.c_int, C.c_int, C.c_int64, C.c_double, C.c_int,
-                                  C.c_int, _dp, _dp, _dp]
+        L.or_node_min.argtypes = [C.c_void_p, C.POINTER(_Grid), C.c_int, C.c_int, C.c_int, C.c_int64, C.c_double,
+                                  C.c_int, C.c_int, _dp, _dp, _dp]
         L.or_bvn_lower.restype = C.c_double
         L.or_bvn_lower.argtypes = [C.c_double, C.c_double, C.c_double]
         L.or_num_threads.restype = C.c_int
@@ -234,43 +234,55 @@ class Model:
             out[z0 * nc * nc: z1 * nc * nc] = self.lcp_block(n, theta, (0, 0, z0), (nc, nc, z1), **kw)
         return out
 
-    def octree_level(self, n, D, l, theta, nodes, alpha=1e-3, T=4, beta=-1.0):
+    def octree_level(self, n, D, l, theta, nodes, alpha=1e-3, T=4, beta=-1.0, kd=False):
         """One level of Algorithm 1.  Returns (decision, bound, side) per node.  beta >= 0: the
-        bound uses each node's local model (Sec. 5.2, beta in length scales); beta < 0: the full one."""
+        bound uses each node's local model (Sec. 5.2, beta in length scales); beta < 0: the full one.
+        kd: level l (0 .. 3D) of the K-D tree of Sec. 9 instead of the octree."""
         g = grid(n)
         nodes = np.ascontiguousarray(nodes, np.int64)
         cnt = nodes.shape[0]
         dec = np.zeros(cnt, np.int8); bnd = np.zeros(cnt); side = np.zeros(cnt, np.int8)
         if cnt:
-            lib().or_octree_level(self._h, C.byref(g), int(D), int(l), float(theta), float(alpha), int(T),
-                                  float(beta), nodes, cnt, dec, bnd, side)
+            lib().or_octree_level(self._h, C.byref(g), int(D), int(l), int(bool(kd)), float(theta), float(alpha),
+                                  int(T), float(beta), nodes, cnt, dec, bnd, side)
         return dec, bnd, side
 
-    def octree(self, n, D, theta, alpha=1e-3, T=4, beta=-1.0):
-        """Algorithm 1 top-down, level by level.  Returns (S cell codes, per-level records)."""
+    def octree(self, n, D, theta, alpha=1e-3, T=4, beta=-1.0, kd=False):
+        """Algorithm 1 top-down, level by level (D + 1 octree levels, or 3D + 1 levels of the K-D tree
+        of Sec. 9, which halves x, y, z in turn).  Returns (S cell codes, per-level records)."""
         nodes = np.zeros(1, np.int64)
         levels = []
         leaves = np.zeros(0, np.int64)
-        for l in range(D + 1):
-            dec, bnd, side = self.octree_level(n, D, l, theta, nodes, alpha, T, beta)
+        last = 3 * D if kd else D
+        for l in range(last + 1):
+            dec, bnd, side = self.octree_level(n, D, l, theta, nodes, alpha, T, beta, kd)
             levels.append({"nodes": nodes, "decision": dec, "bound": bnd, "side": side})
             keep = nodes[dec > 0]
-            if l == D:
+            if l == last:
                 leaves = keep
                 break
             i = keep & 0x1FFFFF; j = (keep >> 21) & 0x1FFFFF; k = (keep >> 42) & 0x1FFFFF
-            s_child = 1 << (D - l - 1)
             ch = []
-            for c in range(8):
-                ci = 2 * i + (c & 1); cj = 2 * j + ((c >> 1) & 1); ck = 2 * k + ((c >> 2) & 1)
-                ok = (ci * s_child < n - 1) & (cj * s_child < n - 1) & (ck * s_child < n - 1)
-                ch.append((ci | (cj << 21) | (ck << 42))[ok])
+            if kd:
+                a = l % 3  # the axis this level halves
+                s_child = [1 << (D - (l + 1 + 2 - d) // 3) for d in range(3)]
+                for b in range(2):
+                    c3 = [i, j, k]
+                    c3[a] = 2 * c3[a] + b
+                    ok = (c3[0] * s_child[0] < n - 1) & (c3[1] * s_child[1] < n - 1) & (c3[2] * s_child[2] < n - 1)
+                    ch.append((c3[0] | (c3[1] << 21) | (c3[2] << 42))[ok])
+            else:
+                s_child = 1 << (D - l - 1)
+                for c in range(8):
+                    ci = 2 * i + (c & 1); cj = 2 * j + ((c >> 1) & 1); ck = 2 * k + ((c >> 2) & 1)
+                    ok = (ci * s_child < n - 1) & (cj * s_child < n - 1) & (ck * s_child < n - 1)
+                    ch.append((ci | (cj << 21) | (ck << 42))[ok])
             nodes = np.sort(np.concatenate(ch)) if ch else np.zeros(0, np.int64)
         return leaves, levels
 
-    def lcp_adaptive(self, n, D, theta, alpha=1e-3, T=4, beta=-1.0, **kw):
+    def lcp_adaptive(self, n, D, theta, alpha=1e-3, T=4, beta=-1.0, kd=False, **kw):
         """Adaptive LCP field: the dense cell LCP on the leaves S of Algorithm 1, 0 elsewhere (Sec. 5.3)."""
-        leaves, levels = self.octree(n, D, theta, alpha, T, beta)
+        leaves, levels = self.octree(n, D, theta, alpha, T, beta, kd)
         nc = n - 1
         field = np.zeros(nc ** 3)
         if leaves.size:
@@ -296,13 +308,13 @@ class Model:
                                        float(skip_eps), np.ascontiguousarray(weights, np.float64), c0, c1, dy, dl)
         return loss, dy, dl
 
-    def node_min(self, n, D, l, node, theta, side, T=4):
+    def node_min(self, n, D, l, node, theta, side, T=4, kd=False):
         """The node minimiser of Algorithm 1's bound (Sec. 5.1) for one node and one side:
         (min g, the point where it was found, box lo, box hi), g = side*(theta-mu)/sigma."""
         g = grid(n)
         x = np.zeros(3); lo = np.zeros(3); hi = np.zeros(3)
-        v = lib().or_node_min(self._h, C.byref(g), int(D), int(l), int(node), float(theta), int(side), int(T),
-                              x, lo, hi)
+        v = lib().or_node_min(self._h, C.byref(g), int(D), int(l), int(bool(kd)), int(node), float(theta), int(side),
+                              int(T), x, lo, hi)
         return v, x, lo, hi
 
     def eval_g(self, x, theta, side):

@@ -900,12 +900,20 @@ static double eval_g(const or_model *M, const double *x, double theta, int side,
 
 /* Node geometry at level l of a depth-D octree over the cell grid: node (i,j,k)
  * spans cells [i s, (i+1) s) per axis, s = 2^(D-l), i.e. grid points
- * [i s, min((i+1) s, n-1)]; its box is the span of those points. */
-static void node_geom(const or_grid *g, int D, int l, const int64_t ijk[3], int64_t p0[3], int64_t p1[3],
+ * [i s, min((i+1) s, n-1)]; its box is the span of those points.
+ * kd != 0: the K-D tree of Sec. 9, which splits one axis per level in turn (x, y, z):
+ * at level l (0 .. 3D) axis d has been halved floor((l + 2 - d) / 3) times, so its extent is
+ * s_d = 2^(D - floor((l + 2 - d) / 3)). */
+static int64_t axis_extent(int D, int l, int kd, int d)
+{
+    return (int64_t)1 << (D - (kd ? (l + 2 - d) / 3 : l));
+}
+
+static void node_geom(const or_grid *g, int D, int l, int kd, const int64_t ijk[3], int64_t p0[3], int64_t p1[3],
                       double blo[3], double bhi[3])
 {
-    int64_t s = (int64_t)1 << (D - l);
     for (int d = 0; d < 3; ++d) {
+        int64_t s = axis_extent(D, l, kd, d);
         p0[d] = ijk[d] * s;
         p1[d] = (ijk[d] + 1) * s;
         if (p1[d] > g->n[d] - 1) p1[d] = g->n[d] - 1;
@@ -1017,8 +1025,8 @@ static or_model *local_model(const or_model *M, const double blo[3], const doubl
  * The p-test uses the observations inside the closed node box with the latent
  * posterior at the observations.  d = number of grid points in the node.
  * beta >= 0: the bound is minimised on the node's local model (local_model above; beta in units
- * of the length scales); beta < 0: on the full model. */
-void or_octree_level(const or_model *M, const or_grid *g, int D, int l, double theta, double alpha, int T,
+ * of the length scales); beta < 0: on the full model.  kd: the level of a K-D tree (node_geom). */
+void or_octree_level(const or_model *M, const or_grid *g, int D, int l, int kd, double theta, double alpha, int T,
                      double beta, const int64_t *nodes, int64_t count, int8_t *decision, double *bound,
                      int8_t *side_out)
 {
@@ -1038,7 +1046,7 @@ void or_octree_level(const or_model *M, const or_grid *g, int D, int l, double t
             int64_t ijk[3] = {nodes[q] & 0x1FFFFF, (nodes[q] >> 21) & 0x1FFFFF, (nodes[q] >> 42) & 0x1FFFFF};
             int64_t p0[3], p1[3];
             double blo[3], bhi[3];
-            node_geom(g, D, l, ijk, p0, p1, blo, bhi);
+            node_geom(g, D, l, kd, ijk, p0, p1, blo, bhi);
             int any = 0, anylo = 0, anyhi = 0;
             for (int64_t i = 0; i < m; ++i) {
                 const double *x = M->X + 3 * i;
@@ -1072,16 +1080,16 @@ void or_octree_level(const or_model *M, const or_grid *g, int D, int l, double t
 }
 
 /* The box minimiser of one node on its own (test hook for the minimiser pins): node
- * (i | j<<21 | k<<42) at level l of a depth-D octree, one side; returns min g and writes the
+ * (i | j<<21 | k<<42) at level l of a depth-D octree (kd: of the K-D tree), one side; returns min g and writes the
  * point where it was found to x_out, and the node box to box_lo / box_hi (all nullable). */
-double or_node_min(const or_model *M, const or_grid *g, int D, int l, int64_t node, double theta, int side, int T,
-                   double *x_out, double *box_lo, double *box_hi)
+double or_node_min(const or_model *M, const or_grid *g, int D, int l, int kd, int64_t node, double theta, int side,
+                   int T, double *x_out, double *box_lo, double *box_hi)
 {
     int64_t m = M->m;
     int64_t ijk[3] = {node & 0x1FFFFF, (node >> 21) & 0x1FFFFF, (node >> 42) & 0x1FFFFF};
     int64_t p0[3], p1[3];
     double blo[3], bhi[3], xb[3];
-    node_geom(g, D, l, ijk, p0, p1, blo, bhi);
+    node_geom(g, D, l, kd, ijk, p0, p1, blo, bhi);
     double *kb = (double *)malloc(sizeof(double) * m), *dk = (double *)malloc(sizeof(double) * 3 * m);
     double *v = (double *)malloc(sizeof(double) * m), *P = (double *)malloc(sizeof(double) * m);
     double r = node_min_g(M, g, p0, p1, blo, bhi, theta, side, T, kb, dk, v, P, xb);

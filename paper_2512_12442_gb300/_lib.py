@@ -18,7 +18,7 @@ class GridC(C.Structure):
 class LcpOptionsC(C.Structure):
     _fields_ = [("alpha", C.c_double), ("beta", C.c_double), ("est", C.c_int), ("n_samples", C.c_int32),
                 ("seed", C.c_uint64), ("jitter", C.c_double), ("skip_eps", C.c_double), ("prec", C.c_int),
-                ("max_iters_min", C.c_int32), ("exact", C.c_int)]
+                ("max_iters_min", C.c_int32), ("exact", C.c_int), ("tree", C.c_int)]
 
 
 class AdaptiveStatsC(C.Structure):

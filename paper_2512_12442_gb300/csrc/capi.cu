@@ -18,6 +18,7 @@ extern "C" void gpr_lcp_options_default(gpr_lcp_options *o)
     o->prec = GPR_P_FP32;
     o->max_iters_min = 4;
     o->exact = GPR_EXACT_AUTO;
+    o->tree = GPR_TREE_OCTREE;
 }
 
 extern "C" const char *gpr_status_string(gpr_status s)
@@ -60,6 +61,7 @@ bool opts_valid(const gpr_lcp_options *o)
     if (!est_opts_valid(o)) return false;
     if (!(o->alpha >= 0.0) || !isfinite(o->alpha)) return false;
     if (isnan(o->beta)) return false;
+    if (o->tree != GPR_TREE_OCTREE && o->tree != GPR_TREE_KD) return false;
     if (o->prec < GPR_P_FP64 || o->prec > GPR_P_BF16X3) return false;
     if (o->max_iters_min < 0 || o->max_iters_min > 64) return false;
     if (o->exact != GPR_EXACT_AUTO && o->exact != GPR_EXACT_FP64) return false;

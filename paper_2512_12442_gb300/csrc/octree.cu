@@ -209,12 +209,19 @@ struct Geom {
     double blo[3], bhi[3];
 };
 
-__device__ __forceinline__ Geom node_geom(const GridDev &g, int D, int l, int64_t code)
+// Cells per axis of a node at level l: 2^(D - l) in the octree; in the K-D tree (Sec. 9), which
+// halves x, y, z in turn, axis d has been halved floor((l + 2 - d) / 3) times by level l (0 .. 3D).
+__host__ __device__ __forceinline__ int64_t axis_extent(int D, int l, int kd, int d)
+{
+    return (int64_t)1 << (D - (kd ? (l + 2 - d) / 3 : l));
+}
+
+__device__ __forceinline__ Geom node_geom(const GridDev &g, int D, int l, int kd, int64_t code)
 {
     Geom G;
-    int64_t s = (int64_t)1 << (D - l);
     int64_t ijk[3] = {code & 0x1FFFFF, (code >> 21) & 0x1FFFFF, (code >> 42) & 0x1FFFFF};
     for (int d = 0; d < 3; ++d) {
+        const int64_t s = axis_extent(D, l, kd, d);
         G.p0[d] = ijk[d] * s;
         G.p1[d] = (ijk[d] + 1) * s;
         if (G.p1[d] > g.n[d] - 1) G.p1[d] = g.n[d] - 1;
@@ -317,14 +324,27 @@ __global__ void k_pyr_level(const TC *child, int32_t c0, int32_t c1, int32_t c2,
     parent[q] = (uint8_t)v;
 }
 
-__global__ void k_ptest(GridDev g, int D, int l, const int64_t *nodes, int64_t count, const uint8_t *lvl,
-                        int32_t d0, int32_t d1, int8_t *decision, int8_t *sides)
+__global__ void k_ptest(GridDev g, int D, int l, int kd, const int64_t *nodes, int64_t count, const uint8_t *lvl,
+                        int32_t d0, int32_t d1, int32_t d2, int8_t *decision, int8_t *sides)
 {
     int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (q >= count) return;
     const int64_t code = nodes[q];
-    const int64_t i = code & 0x1FFFFF, j = (code >> 21) & 0x1FFFFF, k = (code >> 42) & 0x1FFFFF;
-    const uint32_t v = lvl[i + (int64_t)d0 * (j + (int64_t)d1 * k)];
+    const int64_t ijk[3] = {code & 0x1FFFFF, (code >> 21) & 0x1FFFFF, (code >> 42) & 0x1FFFFF};
+    // `lvl` is the pyramid level of the node's smallest extent; a K-D node spans 1, 2 or 4 of its
+    // entries (2^(q_0 - q_d) along axis d, q_d the halvings of axis d)
+    int64_t span[3] = {1, 1, 1}, base[3];
+    for (int d = 0; d < 3; ++d) {
+        if (kd) span[d] = axis_extent(D, l, kd, d) / axis_extent(D, l, kd, 0);
+        base[d] = ijk[d] * span[d];
+    }
+    uint32_t v = 0;
+    for (int64_t c = 0; c < span[2]; ++c)
+        for (int64_t b = 0; b < span[1]; ++b)
+            for (int64_t a = 0; a < span[0]; ++a) {
+                const int64_t ii = base[0] + a, jj = base[1] + b, kk = base[2] + c;
+                if (ii < d0 && jj < d1 && kk < d2) v |= lvl[ii + (int64_t)d0 * (jj + (int64_t)d1 * kk)];
+            }
     const bool any = v & 4, lo = v & 1, hi = v & 2;
     if (any && lo && hi) {
         decision[q] = 1;
@@ -336,12 +356,12 @@ __global__ void k_ptest(GridDev g, int D, int l, const int64_t *nodes, int64_t c
 }
 
 // Flags the grid points of pending small nodes whose mean/variance is not yet in the table.
-__global__ void k_mark_small_points(GridDev g, int D, int l, const int64_t *nodes, int64_t count,
+__global__ void k_mark_small_points(GridDev g, int D, int l, int kd, const int64_t *nodes, int64_t count,
                                     const int8_t *decision, const uint8_t *have, uint8_t *need)
 {
     int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (q >= count || decision[q] != 0) return;
-    Geom G = node_geom(g, D, l, nodes[q]);
+    Geom G = node_geom(g, D, l, kd, nodes[q]);
     if (!is_small(G)) return;
     for (int64_t c = G.p0[2]; c <= G.p1[2]; ++c)
         for (int64_t b = G.p0[1]; b <= G.p1[1]; ++b)
@@ -363,13 +383,13 @@ __global__ void k_scatter_mv(const int64_t *pts, int64_t count, const float *mea
 }
 
 // Exact minimum over the grid points of small pending nodes -> bound -> decision.
-__global__ void k_small_bound(GridDev g, int D, int l, const int64_t *nodes, int64_t count, const float2 *mv,
+__global__ void k_small_bound(GridDev g, int D, int l, int kd, const int64_t *nodes, int64_t count, const float2 *mv,
                               double theta, double alpha, double sf2, int8_t *decision, const int8_t *sides,
                               double *bound)
 {
     int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (q >= count || decision[q] != 0) return;
-    Geom G = node_geom(g, D, l, nodes[q]);
+    Geom G = node_geom(g, D, l, kd, nodes[q]);
     if (!is_small(G)) return;
     double glo = INFINITY, ghi = INFINITY;
     for (int64_t c = G.p0[2]; c <= G.p1[2]; ++c)
@@ -388,25 +408,25 @@ __global__ void k_small_bound(GridDev g, int D, int l, const int64_t *nodes, int
 }
 
 // Pending large nodes -> compact list (positions in the frontier).
-__global__ void k_flag_large(GridDev g, int D, int l, const int64_t *nodes, int64_t count, const int8_t *decision,
+__global__ void k_flag_large(GridDev g, int D, int l, int kd, const int64_t *nodes, int64_t count, const int8_t *decision,
                              uint8_t *flag)
 {
     int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (q >= count) return;
     bool f = false;
-    if (decision[q] == 0) f = !is_small(node_geom(g, D, l, nodes[q]));
+    if (decision[q] == 0) f = !is_small(node_geom(g, D, l, kd, nodes[q]));
     flag[q] = f ? 1 : 0;
 }
 
 // Lattice points (3x3x3 per node; corners, edge/face midpoints, centre, x fastest).
-__global__ void k_lattice_points(GridDev g, int D, int l, const int64_t *nodes, const int64_t *pend,
+__global__ void k_lattice_points(GridDev g, int D, int l, int kd, const int64_t *nodes, const int64_t *pend,
                                  const int64_t *ulist, int64_t first, int64_t cnt, double *xyz)
 {
     int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= cnt) return;
     int64_t gi = first + e, q = ulist[gi / 27];
     int t = (int)(gi % 27);
-    Geom G = node_geom(g, D, l, nodes[pend[q]]);
+    Geom G = node_geom(g, D, l, kd, nodes[pend[q]]);
     int id[3] = {t % 3, (t / 3) % 3, t / 9};
     for (int d = 0; d < 3; ++d) xyz[3 * e + d] = G.blo[d] + 0.5 * (double)id[d] * (G.bhi[d] - G.blo[d]);
 }
@@ -427,12 +447,12 @@ __device__ __forceinline__ int64_t lattice_point(const GridDev &g, const Geom &G
 
 // Marks the lattice grid points of aligned pending large nodes that the table lacks; flags the
 // unaligned nodes (their lattice is evaluated point by point).
-__global__ void k_mark_lattice(GridDev g, int D, int l, const int64_t *nodes, const int64_t *pend, int64_t npend,
+__global__ void k_mark_lattice(GridDev g, int D, int l, int kd, const int64_t *nodes, const int64_t *pend, int64_t npend,
                                const uint8_t *have, uint8_t *need, uint8_t *unaligned)
 {
     int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (q >= npend) return;
-    Geom G = node_geom(g, D, l, nodes[pend[q]]);
+    Geom G = node_geom(g, D, l, kd, nodes[pend[q]]);
     bool al = lattice_aligned(G);
     unaligned[q] = al ? 0 : 1;
     if (!al) return;
@@ -443,7 +463,7 @@ __global__ void k_mark_lattice(GridDev g, int D, int l, const int64_t *nodes, co
 }
 
 // g = (theta - mu)/sigma at the 27 lattice points of aligned nodes, from the table.
-__global__ void k_lattice_from_table(GridDev g, int D, int l, const int64_t *nodes, const int64_t *pend,
+__global__ void k_lattice_from_table(GridDev g, int D, int l, int kd, const int64_t *nodes, const int64_t *pend,
                                      int64_t npend, const uint8_t *unaligned, const float2 *mv, double theta,
                                      double sf2, float4 *lat)
 {
@@ -451,7 +471,7 @@ __global__ void k_lattice_from_table(GridDev g, int D, int l, const int64_t *nod
     if (e >= npend * 27) return;
     int64_t q = e / 27;
     if (unaligned[q]) return;
-    Geom G = node_geom(g, D, l, nodes[pend[q]]);
+    Geom G = node_geom(g, D, l, kd, nodes[pend[q]]);
     float2 v = mv[lattice_point(g, G, (int)(e % 27))];
     double var = fmax((double)v.y, 1e-12 * sf2);
     lat[e] = make_float4((float)((theta - (double)v.x) / sqrt(var)), 0.f, 0.f, 0.f);
@@ -520,25 +540,25 @@ __global__ void k_lattice_best(const float4 *ev, int64_t npend, MinState *ms)
     ms[q] = s;
 }
 
-__global__ void k_lattice_coords(GridDev g, int D, int l, const int64_t *nodes, const int64_t *pend, int64_t npend,
+__global__ void k_lattice_coords(GridDev g, int D, int l, int kd, const int64_t *nodes, const int64_t *pend, int64_t npend,
                                  MinState *ms)
 {
     int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (q >= npend) return;
-    Geom G = node_geom(g, D, l, nodes[pend[q]]);
+    Geom G = node_geom(g, D, l, kd, nodes[pend[q]]);
     for (int side = 0; side < 2; ++side)
         for (int d = 0; d < 3; ++d) ms[q].x[side][d] = G.blo[d] + 0.5 * ms[q].x[side][d] * (G.bhi[d] - G.blo[d]);
 }
 
 // Candidate of projected step t for every (node, side): x' = clamp(x + eta_t w u/|u|_inf), u = -grad g * w.
-__global__ void k_candidates(GridDev g, int D, int l, const int64_t *nodes, const int64_t *pend, const int64_t *act,
+__global__ void k_candidates(GridDev g, int D, int l, int kd, const int64_t *nodes, const int64_t *pend, const int64_t *act,
                              const MinState *ms, int step, int64_t first, int64_t cnt, double *xyz, uint8_t *valid)
 {
     int64_t le = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (le >= cnt) return;
     const int64_t e = act[first + le], q = e / 2;
     const int side = (int)(e % 2);
-    Geom G = node_geom(g, D, l, nodes[pend[q]]);
+    Geom G = node_geom(g, D, l, kd, nodes[pend[q]]);
     double w[3], u[3], un = 0.0;
     for (int d = 0; d < 3; ++d) {
         w[d] = G.bhi[d] - G.blo[d];
@@ -578,7 +598,7 @@ __global__ void k_accept(const double *xyz, const uint8_t *valid, const float4 *
 // raises the bound) and, for the others, each side the bound depends on is flagged for the
 // minimiser: a side outside the p-test's sides, or whose B^d is already below 1e-30 (further
 // descent moves the bound by less than that), is not minimised.
-__global__ void k_large_bound(GridDev g, int D, int l, const int64_t *nodes, const int64_t *pend, const int64_t *act,
+__global__ void k_large_bound(GridDev g, int D, int l, int kd, const int64_t *nodes, const int64_t *pend, const int64_t *act,
                               int64_t cnt, const MinState *ms, double alpha, int8_t *decision, const int8_t *sides,
                               double *bound, uint8_t *active)
 {
@@ -586,7 +606,7 @@ __global__ void k_large_bound(GridDev g, int D, int l, const int64_t *nodes, con
     if (t >= cnt) return;
     const int64_t q = act ? act[t] / 2 : t;
     int64_t node = pend[q];
-    Geom G = node_geom(g, D, l, nodes[node]);
+    Geom G = node_geom(g, D, l, kd, nodes[node]);
     double dcount = (double)((G.p1[0] - G.p0[0] + 1) * (G.p1[1] - G.p0[1] + 1) * (G.p1[2] - G.p0[2] + 1));
     double bnd = bound_of(sides[node], dcount, (double)ms[q].g[0], (double)ms[q].g[1]);
     bound[node] = bnd;
@@ -601,7 +621,7 @@ __global__ void k_large_bound(GridDev g, int D, int l, const int64_t *nodes, con
 }
 
 // Subdivided nodes -> children (next frontier) or, at the last level, cells of S.
-__global__ void k_children(GridDev g, int D, int l, const int64_t *nodes, int64_t count, const int8_t *decision,
+__global__ void k_children(GridDev g, int D, int l, int kd, const int64_t *nodes, int64_t count, const int8_t *decision,
                            int64_t *next, unsigned long long *nnext, uint8_t *leaf, unsigned long long *nsub)
 {
     int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -611,16 +631,27 @@ __global__ void k_children(GridDev g, int D, int l, const int64_t *nodes, int64_
     if (!sub) return;
     int64_t code = nodes[q];
     int64_t i = code & 0x1FFFFF, j = (code >> 21) & 0x1FFFFF, k = (code >> 42) & 0x1FFFFF;
-    if (l == D) {
+    if (l == (kd ? 3 * D : D)) {
         leaf[i + (int64_t)(g.n[0] - 1) * (j + (int64_t)(g.n[1] - 1) * k)] = 1;
         return;
     }
-    int64_t sc = (int64_t)1 << (D - l - 1);
+    int64_t sc[3];
+    for (int d = 0; d < 3; ++d) sc[d] = axis_extent(D, l + 1, kd, d);
     int64_t out[8];
     int c = 0;
-    for (int b = 0; b < 8; ++b) {
-        int64_t ci = 2 * i + (b & 1), cj = 2 * j + ((b >> 1) & 1), ck = 2 * k + ((b >> 2) & 1);
-        if (ci * sc < g.n[0] - 1 && cj * sc < g.n[1] - 1 && ck * sc < g.n[2] - 1) out[c++] = ci | (cj << 21) | (ck << 42);
+    // octree: 8 children; K-D tree: 2 children along the axis this level halves (l mod 3)
+    const int nch = kd ? 2 : 8, ax = l % 3;
+    for (int b = 0; b < nch; ++b) {
+        int64_t ci, cj, ck;
+        if (kd) {
+            ci = ax == 0 ? 2 * i + b : i;
+            cj = ax == 1 ? 2 * j + b : j;
+            ck = ax == 2 ? 2 * k + b : k;
+        } else {
+            ci = 2 * i + (b & 1); cj = 2 * j + ((b >> 1) & 1); ck = 2 * k + ((b >> 2) & 1);
+        }
+        if (ci * sc[0] < g.n[0] - 1 && cj * sc[1] < g.n[1] - 1 && ck * sc[2] < g.n[2] - 1)
+            out[c++] = ci | (cj << 21) | (ck << 42);
     }
     unsigned long long base = atomicAdd(nnext, (unsigned long long)c);
     for (int t = 0; t < c; ++t) next[base + t] = out[t];
@@ -640,7 +671,7 @@ __device__ __forceinline__ bool in_local_box(const Geom &G, const double *x, dou
 
 // Pending nodes whose local set is a strict subset of M: flag them (decision 5 keeps the full-model
 // kernels off them) and track the largest local set.
-__global__ void k_local_flag(GridDev g, int D, int l, const int64_t *nodes, int64_t count, int8_t *decision,
+__global__ void k_local_flag(GridDev g, int D, int l, int kd, const int64_t *nodes, int64_t count, int8_t *decision,
                              const double *X, int64_t m, double beta, KernParams kp, uint8_t *flag,
                              unsigned long long *cmax)
 {
@@ -648,7 +679,7 @@ __global__ void k_local_flag(GridDev g, int D, int l, const int64_t *nodes, int6
     if (q >= count) return;
     flag[q] = 0;
     if (decision[q] != 0) return;
-    Geom G = node_geom(g, D, l, nodes[q]);
+    Geom G = node_geom(g, D, l, kd, nodes[q]);
     int64_t c = 0;
     for (int64_t i = 0; i < m; ++i) c += in_local_box(G, X + 3 * i, beta, kp) ? 1 : 0;
     if (c == m) return;
@@ -825,7 +856,7 @@ __device__ double local_eval(const LocalModel &Mo, const LocalWs &W, int64_t c, 
 // One warp per listed node: gather M', factor K' (FP64, left-looking by columns), then the same
 // minimiser as the full-model path (exact over grid points for nodes of <= 3 points per axis; else
 // the best of the 3x3x3 lattice and T projected steps per side), bound and decision.
-__global__ void k_local_nodes(GridDev g, int D, int l, const int64_t *nodes, const int64_t *list, int64_t nl,
+__global__ void k_local_nodes(GridDev g, int D, int l, int kd, const int64_t *nodes, const int64_t *list, int64_t nl,
                               LocalModel Mo, double beta, double theta, double alpha, int T, const int8_t *sides,
                               int8_t *decision, double *bound, double *ws, int32_t *iws, int64_t cmax, int *status)
 {
@@ -835,7 +866,7 @@ __global__ void k_local_nodes(GridDev g, int D, int l, const int64_t *nodes, con
     const LocalWs W = local_ws(ws, iws, warp, cmax, Mo.A != nullptr);
     for (int64_t t = warp; t < nl; t += nwarps) {
         const int64_t q = list[t];
-        const Geom G = node_geom(g, D, l, nodes[q]);
+        const Geom G = node_geom(g, D, l, kd, nodes[q]);
         // gather the local set (ascending observation index)
         int64_t c = 0;
         for (int64_t base = 0; base < Mo.m; base += 32) {
@@ -1007,9 +1038,12 @@ gpr_status octree_lcp(gpr_model *M, const gpr_grid *grid, double theta, int D, c
     int64_t n = g.npts(), nc = g.ncells(), m = M->m;
     size_t te = table_elems(M, g);
     int T = opts->max_iters_min;
-    // nodes with >= 4 cells per side: at most prod ceil((n_d - 1) / 4) of them in any level
+    const int kd = opts->tree == GPR_TREE_KD ? 1 : 0;
+    const int last = kd ? 3 * D : D;  // the level whose subdivided nodes are cells of S
+    // nodes with >= 4 cells along an axis: at most prod ceil((n_d - 1) / 4) of them in any octree
+    // level; a K-D node's extents differ by at most a factor 2, so (4, 2, 2) bounds its count
     int64_t max_large = 1;
-    for (int d = 0; d < 3; ++d) max_large *= (int64_t)(g.n[d] - 1 + 3) / 4;
+    for (int d = 0; d < 3; ++d) max_large *= (int64_t)(g.n[d] - 1 + (kd && d < 2 ? 1 : 3)) / (kd && d < 2 ? 2 : 4);
     // workspace (slot 0): tables, frontier, per-point mean/var table, evaluation chunk
     size_t csb = compact_scratch_bytes(nc > n ? nc : n);
     size_t bytes = 2 * Carver::round((size_t)nc * 8) + 2 * Carver::round((size_t)nc) +
@@ -1107,12 +1141,13 @@ gpr_status octree_lcp(gpr_model *M, const gpr_grid *grid, double theta, int D, c
     int64_t count = 1;
     int cur = 0;
     if (stats) memset(stats, 0, sizeof *stats);
-    for (int l = 0; l <= D && count > 0; ++l) {
+    for (int l = 0; l <= last && count > 0; ++l) {
         const int64_t *nodes = B.front[cur];
-        int64_t s = (int64_t)1 << (D - l);
+        const int64_t s = axis_extent(D, l, kd, 2);  // the node's largest extent
+        const int lp = kd ? (l + 2) / 3 : l;          // pyramid level of its smallest extent
         ProfScope lvl("oct_level", st);
-        k_ptest<<<nb(count, 256), 256, 0, st>>>(g, D, l, nodes, count, pyr_lv + pyr.off[l], pyr.dim[l][0],
-                                                 pyr.dim[l][1], B.decision, B.sides);
+        k_ptest<<<nb(count, 256), 256, 0, st>>>(g, D, l, kd, nodes, count, pyr_lv + pyr.off[lp], pyr.dim[lp][0],
+                                                 pyr.dim[lp][1], pyr.dim[lp][2], B.decision, B.sides);
         note_launch();
         // nodes whose local set (Sec. 5.2) is a strict subset of the observations leave the
         // full-model path below and are bounded on their local model
@@ -1120,7 +1155,7 @@ gpr_status octree_lcp(gpr_model *M, const gpr_grid *grid, double theta, int D, c
         unsigned long long cmax = 0;
         if (local) {
             GPR_CUDA_TRY(cudaMemsetAsync(B.counters + 2, 0, sizeof(unsigned long long), st));
-            k_local_flag<<<nb(count, 128), 128, 0, st>>>(g, D, l, nodes, count, B.decision, M->X, m, opts->beta, M->kp,
+            k_local_flag<<<nb(count, 128), 128, 0, st>>>(g, D, l, kd, nodes, count, B.decision, M->X, m, opts->beta, M->kp,
                                                          B.lflag2, B.counters + 2);
             note_launch();
             GPR_TRY(compact_flags(B.lflag2, count, B.llist, nullptr, &nlocal, B.cscr, B.csb, st));
@@ -1132,7 +1167,7 @@ gpr_status octree_lcp(gpr_model *M, const gpr_grid *grid, double theta, int D, c
         {
             MvFillScope fill(M, st);
             GPR_CUDA_TRY(cudaMemsetAsync(B.need, 0, (size_t)n, st));
-            k_mark_small_points<<<nb(count, 128), 128, 0, st>>>(g, D, l, nodes, count, B.decision, B.have, B.need);
+            k_mark_small_points<<<nb(count, 128), 128, 0, st>>>(g, D, l, kd, nodes, count, B.decision, B.have, B.need);
             note_launch();
             int64_t nneed = 0;
             GPR_TRY(compact_flags(B.need, n, B.plist, nullptr, &nneed, B.cscr, B.csb, st));
@@ -1142,12 +1177,12 @@ gpr_status octree_lcp(gpr_model *M, const gpr_grid *grid, double theta, int D, c
                 note_launch();
             }
         }
-        k_small_bound<<<nb(count, 128), 128, 0, st>>>(g, D, l, nodes, count, B.mv, theta, opts->alpha, M->kp.sf2,
+        k_small_bound<<<nb(count, 128), 128, 0, st>>>(g, D, l, kd, nodes, count, B.mv, theta, opts->alpha, M->kp.sf2,
                                                       B.decision, B.sides, B.bound);
         note_launch();
         // large nodes: lattice start + projected gradient steps
         if (s > 2) {
-            k_flag_large<<<nb(count, 256), 256, 0, st>>>(g, D, l, nodes, count, B.decision, B.lflag);
+            k_flag_large<<<nb(count, 256), 256, 0, st>>>(g, D, l, kd, nodes, count, B.decision, B.lflag);
             note_launch();
             int64_t npend = 0;
             GPR_TRY(compact_flags(B.lflag, count, B.pend, nullptr, &npend, B.cscr, B.csb, st));
@@ -1156,7 +1191,7 @@ gpr_status octree_lcp(gpr_model *M, const gpr_grid *grid, double theta, int D, c
                 {
                     MvFillScope fill(M, st);
                     GPR_CUDA_TRY(cudaMemsetAsync(B.need, 0, (size_t)n, st));
-                    k_mark_lattice<<<nb(npend, 128), 128, 0, st>>>(g, D, l, nodes, B.pend, npend, B.have, B.need,
+                    k_mark_lattice<<<nb(npend, 128), 128, 0, st>>>(g, D, l, kd, nodes, B.pend, npend, B.have, B.need,
                                                                    B.unal);
                     note_launch();
                     int64_t nneed = 0;
@@ -1169,14 +1204,14 @@ gpr_status octree_lcp(gpr_model *M, const gpr_grid *grid, double theta, int D, c
                         note_launch();
                     }
                 }
-                k_lattice_from_table<<<nb(npend * 27, 256), 256, 0, st>>>(g, D, l, nodes, B.pend, npend, B.unal, B.mv,
+                k_lattice_from_table<<<nb(npend * 27, 256), 256, 0, st>>>(g, D, l, kd, nodes, B.pend, npend, B.unal, B.mv,
                                                                           theta, M->kp.sf2, B.lat);
                 note_launch();
                 int64_t nun = 0;
                 GPR_TRY(compact_flags(B.unal, npend, B.ulist, nullptr, &nun, B.cscr, B.csb, st));
                 for (int64_t first = 0; first < nun * 27; first += kEvalChunk) {
                     int64_t cnt = nun * 27 - first < kEvalChunk ? nun * 27 - first : kEvalChunk;
-                    k_lattice_points<<<nb(cnt, 256), 256, 0, st>>>(g, D, l, nodes, B.pend, B.ulist, first, cnt, B.xyz);
+                    k_lattice_points<<<nb(cnt, 256), 256, 0, st>>>(g, D, l, kd, nodes, B.pend, B.ulist, first, cnt, B.xyz);
                     note_launch();
                     // lattice values only: the start points' gradients are evaluated afresh below
                     GPR_TRY(run_eval(M, E, B, cnt, theta, st, false));
@@ -1185,11 +1220,11 @@ gpr_status octree_lcp(gpr_model *M, const gpr_grid *grid, double theta, int D, c
                 }
                 k_lattice_best<<<nb(npend, 128), 128, 0, st>>>(B.lat, npend, B.ms);
                 note_launch();
-                k_lattice_coords<<<nb(npend, 128), 128, 0, st>>>(g, D, l, nodes, B.pend, npend, B.ms);
+                k_lattice_coords<<<nb(npend, 128), 128, 0, st>>>(g, D, l, kd, nodes, B.pend, npend, B.ms);
                 note_launch();
                 // nodes whose lattice minima already give a bound above alpha are decided; the
                 // minimiser runs on the others (the act list)
-                k_large_bound<<<nb(npend, 128), 128, 0, st>>>(g, D, l, nodes, B.pend, nullptr, npend, B.ms, opts->alpha,
+                k_large_bound<<<nb(npend, 128), 128, 0, st>>>(g, D, l, kd, nodes, B.pend, nullptr, npend, B.ms, opts->alpha,
                                                              B.decision, B.sides, B.bound, B.unal);
                 note_launch();
                 int64_t nact = 0;  // (node, side) pairs to minimise
@@ -1207,7 +1242,7 @@ gpr_status octree_lcp(gpr_model *M, const gpr_grid *grid, double theta, int D, c
                 for (int t = 0; t < T && nact > 0; ++t) {
                     for (int64_t first = 0; first < nact; first += kEvalChunk) {
                         int64_t cnt = nact - first < kEvalChunk ? nact - first : kEvalChunk;
-                        k_candidates<<<nb(cnt, 256), 256, 0, st>>>(g, D, l, nodes, B.pend, act, B.ms, t, first, cnt,
+                        k_candidates<<<nb(cnt, 256), 256, 0, st>>>(g, D, l, kd, nodes, B.pend, act, B.ms, t, first, cnt,
                                                                    B.xyz, B.cvalid);
                         note_launch();
                         // the last step's gradients are never used: value only
@@ -1217,7 +1252,7 @@ gpr_status octree_lcp(gpr_model *M, const gpr_grid *grid, double theta, int D, c
                     }
                 }
                 if (nact > 0) {
-                    k_large_bound<<<nb(nact, 128), 128, 0, st>>>(g, D, l, nodes, B.pend, act, nact, B.ms, opts->alpha,
+                    k_large_bound<<<nb(nact, 128), 128, 0, st>>>(g, D, l, kd, nodes, B.pend, act, nact, B.ms, opts->alpha,
                                                                  B.decision, B.sides, B.bound, nullptr);
                     note_launch();
                 }
@@ -1240,7 +1275,7 @@ gpr_status octree_lcp(gpr_model *M, const gpr_grid *grid, double theta, int D, c
             if (!status) return GPR_ERR_CUDA;
             {
                 ProfScope ps("oct_local", st, (double)nlocal);
-                k_local_nodes<<<(unsigned)((nw + 3) / 4), 128, 0, st>>>(g, D, l, nodes, B.llist, nlocal, Mo, opts->beta,
+                k_local_nodes<<<(unsigned)((nw + 3) / 4), 128, 0, st>>>(g, D, l, kd, nodes, B.llist, nlocal, Mo, opts->beta,
                                                                         theta, opts->alpha, T, B.sides, B.decision,
                                                                         B.bound, dws, iws, c, status);
             }
@@ -1249,7 +1284,7 @@ gpr_status octree_lcp(gpr_model *M, const gpr_grid *grid, double theta, int D, c
             GPR_CUDA_TRY(cudaFreeAsync(lws, st));
         }
         GPR_CUDA_TRY(cudaMemsetAsync(B.counters, 0, 2 * sizeof(unsigned long long), st));
-        k_children<<<nb(count, 256), 256, 0, st>>>(g, D, l, nodes, count, B.decision, B.front[1 - cur], B.counters,
+        k_children<<<nb(count, 256), 256, 0, st>>>(g, D, l, kd, nodes, count, B.decision, B.front[1 - cur], B.counters,
                                                    B.leaf, B.counters + 1);
         note_launch();
         GPR_CUDA_TRY(cudaGetLastError());
@@ -1316,7 +1351,8 @@ extern "C" gpr_status gpr_octree_trace(gpr_model *M, const gpr_grid *grid, doubl
                                        double *bound, int64_t capacity, int64_t *count, void *stream)
 {
     if (!M || !grid_valid(grid) || !opts_valid(opts) || !nodes || !decision || !bound || !count) return GPR_ERR_ARG;
-    if (max_depth < 0 || max_depth > 20 || level < 0 || level > max_depth) return GPR_ERR_ARG;
+    if (max_depth < 0 || max_depth > 20 || level < 0 || level > (opts->tree == GPR_TREE_KD ? 3 : 1) * max_depth)
+        return GPR_ERR_ARG;
     OctTrace tr{level, nodes, decision, bound, capacity, 0, nullptr};
     gpr_status s = octree_lcp(M, grid, isovalue, max_depth, opts, nullptr, nullptr, (cudaStream_t)stream, &tr);
     *count = tr.count;

@@ -169,7 +169,8 @@ def test_local_model_levels_match_oracle(torch, g, kind):
     for l in (2, 3):
         a = g.gpr_octree_trace(M, grid, th, D, g.lcp_options(beta=50.0), l)
         b = g.gpr_octree_trace(M, grid, th, D, g.lcp_options(), l)
-        np.testing.assert_array_equal(a[0], b[0]); np.testing.assert_array_equal(a[1], b[1])
+        ia, ib = np.argsort(a[0]), np.argsort(b[0])  # the frontier order is not deterministic
+        np.testing.assert_array_equal(a[0][ia], b[0][ib]); np.testing.assert_array_equal(a[1][ia], b[1][ib])
 
 
 def test_local_model_adaptive_field(torch, g):
@@ -186,6 +187,42 @@ def test_local_model_adaptive_field(torch, g):
     g.gpr_lcp_dense(M, grid, th, opts, d)
     g.gpr_sync()
     nodes, dec, _ = g.gpr_octree_trace(M, grid, th, D, opts, D)
+    leaf = nodes[dec > 0]
+    lin = (leaf & 0x1FFFFF) + (n - 1) * (((leaf >> 21) & 0x1FFFFF) + (n - 1) * ((leaf >> 42) & 0x1FFFFF))
+    inS = np.zeros((n - 1) ** 3, bool); inS[lin] = True
+    av, dv = a.cpu().numpy(), d.cpu().numpy()
+    assert st["leaf_cells"] == inS.sum() and 0 < inS.sum() < inS.size
+    assert np.array_equal(av[inS], dv[inS]) and np.all(av[~inS] == 0)
+
+
+def test_kd_tree_levels_match_oracle_and_field(torch, g):
+    """The K-D tree (Sec. 9) on the device: every level against the oracle's K-D levels (p-test
+    exact, bound decisions within a factor 3 of alpha), and the adaptive field equal to the dense
+    field on its S (the paper-scale field on a 33^3 grid)."""
+    w = workloads.config2()
+    M = model_of(w)
+    om = oracle.Model.from_workload(w)
+    n, D, th = 33, 5, w.isovalues[1]
+    grid = g.make_grid(n)
+    opts = g.lcp_options(tree=g.GPR_TREE_KD)
+    seen = 0
+    for l in range(3 * D + 1):
+        nodes, dec, bnd = g.gpr_octree_trace(M, grid, th, D, opts, l)
+        if len(nodes) == 0:
+            break
+        odec, obnd, _ = om.octree_level(n, D, l, th, nodes, kd=True)
+        assert np.array_equal(odec == 1, dec == 1), l
+        bad = (odec > 0) != (dec > 0)
+        near = (obnd >= 1e-3 / 3) & (obnd <= 3e-3)
+        assert np.all(near[bad]), (l, obnd[bad & ~near][:8], bnd[bad & ~near][:8])
+        seen += len(nodes)
+    assert seen > 1000
+    a = torch.zeros((n - 1) ** 3, dtype=torch.float32, device="cuda")
+    d = torch.zeros_like(a)
+    st = g.gpr_lcp_adaptive(M, grid, th, D, opts, a)
+    g.gpr_lcp_dense(M, grid, th, opts, d)
+    g.gpr_sync()
+    nodes, dec, _ = g.gpr_octree_trace(M, grid, th, D, opts, 3 * D)
     leaf = nodes[dec > 0]
     lin = (leaf & 0x1FFFFF) + (n - 1) * (((leaf >> 21) & 0x1FFFFF) + (n - 1) * ((leaf >> 42) & 0x1FFFFF))
     inS = np.zeros((n - 1) ** 3, bool); inS[lin] = True

@@ -681,6 +681,41 @@ def test_local_model_bound_sec52():
         pytest.fail("no empty node")
 
 
+def test_kd_tree_levels():
+    """The K-D tree of Sec. 9 halves x, y, z in turn: its level 3L nodes are exactly the octree's
+    level-L nodes, so for the same node codes both give the same decisions and bounds; in between, a
+    node at level 3L + a spans half of its parent along axis a - 1 (checked through the p-test of a
+    node whose half holds no observation).  With alpha -> 0 it keeps every cell of non-zero LCP and
+    the adaptive field equals the dense one on S."""
+    w = workloads.config2()
+    M = oracle.Model.from_workload(w)
+    th = w.isovalues[1]
+    n, D = 17, 4
+    for L in (1, 2, 3):
+        s = 1 << L
+        nodes = np.array([i | (j << 21) | (k << 42) for k in range(s) for j in range(s) for i in range(s)], np.int64)
+        a = M.octree_level(n, D, L, th, nodes)
+        b = M.octree_level(n, D, 3 * L, th, nodes, kd=True)
+        for u, v in zip(a, b):
+            np.testing.assert_array_equal(u, v)
+    # level 1: two x-halves; level 2: (x, y) quarters at full z; level 5: (1/4, 1/4, 1/2)
+    for l, node, lo, hi in ((1, 1, (0.5, 0, 0), (1, 1, 1)), (2, 1 | (1 << 21), (0.5, 0.5, 0), (1, 1, 1)),
+                            (5, 3 | (2 << 21) | (1 << 42), (0.75, 0.5, 0.5), (1, 0.75, 1))):
+        _, _, blo, bhi = M.node_min(n, D, l, node, th, 1, kd=True)
+        np.testing.assert_allclose(blo, lo, atol=1e-15); np.testing.assert_allclose(bhi, hi, atol=1e-15)
+    w2 = workloads.small(2, 30, 9, ell=(0.3, 0.3, 0.3))
+    M2 = oracle.Model.from_workload(w2)
+    th2 = w2.isovalues[0]
+    Dd = workloads.depth_for(9)
+    dense = M2.lcp_dense(9, th2)
+    field, leaves, levels = M2.lcp_adaptive(9, Dd, th2, alpha=1e-300, kd=True)
+    assert len(levels) == 3 * Dd + 1
+    assert np.all(field[dense > 1e-12] == dense[dense > 1e-12])
+    field3, leaves3, _ = M2.lcp_adaptive(9, Dd, th2, kd=True)
+    lin = (leaves3 & 0x1FFFFF) + 8 * (((leaves3 >> 21) & 0x1FFFFF) + 8 * ((leaves3 >> 42) & 0x1FFFFF))
+    np.testing.assert_array_equal(field3[lin], dense[lin])
+
+
 def test_octree_alpha_zero_keeps_nonzero_cells_and_adaptive_equals_dense():
     """Algorithm 1 with alpha -> 0 keeps every cell whose dense LCP is non-zero, and the adaptive
     field equals the dense field on S and is 0 elsewhere (Sec. 5.3, last paragraph)."""
