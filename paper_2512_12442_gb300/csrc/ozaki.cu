@@ -374,6 +374,210 @@ __global__ void __launch_bounds__(G_NTHR, 1) k_oz_gemm(const __grid_constant__ C
     oz_teardown(P.tmem, ok, prm.status);
 }
 
+// A digits generated in the kernel (no HBM staging): 8 consecutive k of one row, all S slices,
+// written in the layout the 64-byte-swizzled 3-D TMA box would give ([slice][row][k], 64-byte rows,
+// 16-byte chunk c of row r at chunk c ^ ((r >> 1) & 3)).  Same digits as k_oz_adig.
+template <int S>
+__device__ __forceinline__ void gen_a_chunk(const OzParams &prm, unsigned char *a_stage, int r, int c, int kb,
+                                            const int *gx, const int *gy, const int *gz, const bool *rv)
+{
+    const int64_t j0 = (int64_t)kb * BKE + c * 8;
+    const float2 *px = prm.Tu + (int64_t)gx[r] * prm.mp, *py = prm.Tu + prm.off1 + (int64_t)gy[r] * prm.mp,
+                 *pz = prm.Tu + prm.off2 + (int64_t)gz[r] * prm.mp;
+    float2 tx[8], ty[8], tz[8];
+#pragma unroll
+    for (int e = 0; e < 8; e += 2) {
+        const float4 a = *(const float4 *)(px + j0 + e), b = *(const float4 *)(py + j0 + e),
+                     d = *(const float4 *)(pz + j0 + e);
+        tx[e] = make_float2(a.x, a.y); tx[e + 1] = make_float2(a.z, a.w);
+        ty[e] = make_float2(b.x, b.y); ty[e + 1] = make_float2(b.z, b.w);
+        tz[e] = make_float2(d.x, d.y); tz[e + 1] = make_float2(d.z, d.w);
+    }
+    float dig[S][8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        FF a = ff_mul(ff_mul(FF{tx[e].x, tx[e].y}, FF{ty[e].x, ty[e].y}), FF{tz[e].x, tz[e].y});
+        if (!rv[r] || j0 + e >= prm.m) a = FF{0.f, 0.f};
+        float rr = a.h;
+#pragma unroll
+        for (int d = 0; d < S; ++d) {
+            if (d == 3) rr += a.l;
+            const float i = rintf(ldexpf(rr, BETA * (d + 1)));
+            dig[d][e] = i;
+            rr = fmaf(-i, ldexpf(1.0f, -BETA * (d + 1)), rr);
+        }
+    }
+    const int pc = c ^ ((r >> 1) & 3);
+#pragma unroll
+    for (int d = 0; d < S; ++d) {
+        uint32_t wd[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const uint32_t lo = __bfloat16_as_ushort(__float2bfloat16_rn(dig[d][2 * q]));
+            const uint32_t hi = __bfloat16_as_ushort(__float2bfloat16_rn(dig[d][2 * q + 1]));
+            wd[q] = lo | (hi << 16);
+        }
+        *(uint4 *)(a_stage + d * A_SLICE + r * 64 + pc * 16) = make_uint4(wd[0], wd[1], wd[2], wd[3]);
+    }
+}
+
+// W rows with the kernel-row digits generated in shared memory by warps 2-9, which also drain the
+// accumulators: they fill each stage's A slices (after the MMAs of two blocks earlier freed it),
+// and at the end of each K chunk wait for its MMAs, drain and release TMEM.  Warp 0 loads only the
+// B slices by TMA; warp 1 issues the MMAs once both halves of a stage are in.
+template <int S>
+__global__ void __launch_bounds__(G_NTHR, 1) k_oz_gemm_gen(const __grid_constant__ CUtensorMap mapB, OzParams prm)
+{
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __shared__ uint32_t tmem_slot;
+    __shared__ int gx[TM], gy[TM], gz[TM];
+    __shared__ bool rv[TM];
+    __shared__ __align__(8) uint64_t fullA[2];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int64_t row0 = (int64_t)blockIdx.y * TM;
+    for (int r = tid; r < TM; r += G_NTHR) {
+        const int64_t row = row0 + r;
+        bool ok = row < prm.count;
+        int64_t p = ok ? (prm.pts ? prm.pts[row] : prm.pt_base + row) : 0;
+        const int64_t nx = prm.g.n[0], ny = prm.g.n[1];
+        if (p < 0 || p >= nx * ny * (int64_t)prm.g.n[2]) { ok = false; p = 0; }
+        gx[r] = (int)(p % nx);
+        gy[r] = (int)((p / nx) % ny);
+        gz[r] = (int)(p / (nx * ny));
+        rv[r] = ok;
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 256;" ::"r"(su32(&fullA[0])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 256;" ::"r"(su32(&fullA[1])));
+    }
+    const OzPipe<S> P = oz_setup<S>(smem_raw, &tmem_slot);  // its __syncthreads publishes the above
+    const int n0 = blockIdx.x * TN;
+    const int64_t m = prm.m;
+    const int64_t kend = (int64_t)n0 + TN < m ? (int64_t)n0 + TN : m;
+    const int nkb = (int)((kend + BKE - 1) / BKE);
+    const int nch = (nkb + KCH - 1) / KCH;
+    bool ok = true;
+    const uint32_t fa0 = su32(&fullA[0]);
+
+    if (warp == 0 && lane == 0) {
+        for (int kb = 0; kb < nkb; ++kb) {
+            const int s = kb & 1;
+            unsigned char *st = P.smem + s * OzPipe<S>::STAGE;
+            if (kb >= 2 && !wait_bar(P.empty0 + 8 * s, ((kb >> 1) - 1) & 1)) ok = false;
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(P.full0 + 8 * s),
+                         "r"((uint32_t)OzPipe<S>::B_ST)
+                         : "memory");
+            asm volatile(
+                "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
+                "%4}], [%5];" ::"r"(su32(st + OzPipe<S>::A_ST)),
+                "l"((uint64_t)&mapB), "r"(kb * BKE), "r"(n0), "r"(0), "r"(P.full0 + 8 * s)
+                : "memory");
+        }
+    } else if (warp == 1 && lane == 0) {
+        for (int kb = 0; kb < nkb; ++kb) {
+            const int s = kb & 1;
+            unsigned char *st = P.smem + s * OzPipe<S>::STAGE;
+            if (!wait_bar(P.full0 + 8 * s, (kb >> 1) & 1)) ok = false;
+            if (!wait_bar(fa0 + 8 * s, (kb >> 1) & 1)) ok = false;
+            if (kb % KCH == 0 && kb > 0 && !wait_bar(P.drained, ((kb / KCH) - 1) & 1)) ok = false;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t ab = su32(st), bb = su32(st + OzPipe<S>::A_ST);
+#pragma unroll
+            for (int kk = 0; kk < 2; ++kk)
+#pragma unroll
+                for (int sa = 0; sa < S; ++sa) {
+                    const int nrow = (S - sa) * TN;
+#pragma unroll
+                    for (int p0 = 0; p0 < nrow; p0 += 256) {
+                        const int nn = nrow - p0 < 256 ? nrow - p0 : 256;
+                        const uint32_t acc = (kb % KCH == 0 && kk == 0 && sa == 0) ? 0u : 1u;
+                        asm volatile(
+                            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+                                P.tmem + (uint32_t)(sa * TN + p0)),
+                            "l"(desc_sw64(ab + sa * A_SLICE + kk * 32)), "l"(desc_sw64(bb + p0 * 64 + kk * 32)),
+                            "r"(idesc_n(nn)), "r"(acc));
+                    }
+                }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(P.empty0 + 8 * s)
+                         : "memory");
+            if (kb == nkb - 1 || kb % KCH == KCH - 1)
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(P.done)
+                             : "memory");
+        }
+    } else if (warp >= 2) {
+        const int at = tid - 64;  // 0 .. 255
+        const int lq = warp & 3, half = (warp - 2) >> 2;
+        FF acc[32];
+#pragma unroll
+        for (int c = 0; c < 32; ++c) acc[c] = FF{0.f, 0.f};
+        for (int ch = 0; ch < nch; ++ch) {
+            const int kb1 = (ch + 1) * KCH < nkb ? (ch + 1) * KCH : nkb;
+            for (int kb = ch * KCH; kb < kb1; ++kb) {
+                const int s = kb & 1;
+                unsigned char *st = P.smem + s * OzPipe<S>::STAGE;
+                if (kb >= 2 && !wait_bar(P.empty0 + 8 * s, ((kb >> 1) - 1) & 1)) ok = false;
+                for (int q = at; q < TM * 4; q += 256) gen_a_chunk<S>(prm, st, q >> 2, q & 3, kb, gx, gy, gz, rv);
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> tensor-core reads
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(fa0 + 8 * s) : "memory");
+            }
+            // drain this chunk's level accumulators (smallest first) into float-float
+            if (!wait_bar(P.done, (uint32_t)(ch & 1))) ok = false;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+            for (int lvl = S - 1; lvl >= 0; --lvl) {
+                uint32_t rr[32];
+                const uint32_t taddr = P.tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(lvl * TN + half * 32);
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+                    "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                    : "=r"(rr[0]), "=r"(rr[1]), "=r"(rr[2]), "=r"(rr[3]), "=r"(rr[4]), "=r"(rr[5]), "=r"(rr[6]),
+                      "=r"(rr[7]), "=r"(rr[8]), "=r"(rr[9]), "=r"(rr[10]), "=r"(rr[11]), "=r"(rr[12]), "=r"(rr[13]),
+                      "=r"(rr[14]), "=r"(rr[15]), "=r"(rr[16]), "=r"(rr[17]), "=r"(rr[18]), "=r"(rr[19]), "=r"(rr[20]),
+                      "=r"(rr[21]), "=r"(rr[22]), "=r"(rr[23]), "=r"(rr[24]), "=r"(rr[25]), "=r"(rr[26]), "=r"(rr[27]),
+                      "=r"(rr[28]), "=r"(rr[29]), "=r"(rr[30]), "=r"(rr[31])
+                    : "r"(taddr));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                const float wgt = ldexpf(1.0f, -BETA * (lvl + 2));
+#pragma unroll
+                for (int c = 0; c < 32; ++c) acc[c] = ff_add_f(acc[c], __uint_as_float(rr[c]) * wgt);
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (ch < nch - 1 && lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(P.drained) : "memory");
+        }
+        // the MMAs are complete: stage the tile through shared memory and store whole row pieces
+        asm volatile("bar.sync 1, 256;" ::: "memory");  // every drain warp is past its last stage read
+        float4 *tile = (float4 *)P.smem;
+        const int r = lq * 32 + lane;
+#pragma unroll
+        for (int c = 0; c < 32; c += 2) {
+            const int64_t j = n0 + half * 32 + c;
+            FF v[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const float cs = (j + h < prm.mp) ? prm.colscale[j + h] : 0.f;
+                v[h] = FF{acc[c + h].h * cs, acc[c + h].l * cs};
+                if (prm.sf2 != 1.0f) v[h] = ff_mul(v[h], FF{prm.sf2, 0.f});
+            }
+            const int k = (half * 32 + c) >> 1;
+            tile[r * 32 + (k ^ (r & 31))] = make_float4(v[0].h, v[0].l, v[1].h, v[1].l);
+        }
+        asm volatile("bar.sync 1, 256;" ::: "memory");
+        const int64_t npts = (int64_t)prm.g.n[0] * prm.g.n[1] * (int64_t)prm.g.n[2];
+        for (int rr2 = 0; rr2 < 16; ++rr2) {
+            const int rt = (warp - 2) * 16 + rr2;
+            const int64_t row = row0 + rt;
+            if (row >= prm.count) break;
+            const int64_t p = prm.pts ? prm.pts[row] : prm.pt_base + row;
+            if (p < 0 || p >= npts) continue;
+            const int64_t orow = prm.out_by_point ? p % prm.row_mod : prm.out_off + row;
+            if (n0 + 2 * lane < prm.mp)
+                *(float4 *)(prm.W + orow * prm.mp + n0 + 2 * lane) = tile[rt * 32 + (lane ^ (rt & 31))];
+        }
+    }
+    oz_teardown(P.tmem, ok, prm.status);
+}
+
 // (double)f * 2^sc built from the bit pattern (no FP64 instructions): exact for normal f while
 // the result stays normal; zero and subnormal f give 0, a result outside the normal range its
 // FP64 evaluation.
@@ -948,11 +1152,11 @@ void adig_release(AdigBuf *b, cudaStream_t st)
     b->busy = false;
 }
 
-// Float-float W rows of the listed points on the tensor cores: row r of the list goes to row r
-// of W (count x mp float2), or to row p % row_mod for point p when out_by_point.  Rows are taken
-// in chunks whose A digits (S x rows x mpt BF16) fit 1.5 GB.
-gpr_status launch_oz_w(const gpr_model *M, const GridDev &g, const float2 *Tu, const int64_t *pts, int64_t pt_base,
-                       int64_t count, float2 *W, cudaStream_t st, bool out_by_point, int64_t row_mod)
+// The W rows with the A digits staged in HBM by k_oz_adig first, in row chunks whose digits
+// (S x rows x mpt BF16) fit 1.5 GB, and loaded by TMA in k_oz_gemm.
+static gpr_status oz_w_staged(const gpr_model *M, const GridDev &g, const float2 *Tu, const int64_t *pts,
+                              int64_t pt_base, int64_t count, float2 *W, cudaStream_t st, bool out_by_point,
+                              int64_t row_mod)
 {
     if (count <= 0) return GPR_OK;
     const OzOperands *O = M->oz;
@@ -1017,6 +1221,66 @@ gpr_status launch_oz_w(const gpr_model *M, const GridDev &g, const float2 *Tu, c
     }
     adig_release(buf, st);
     return rs;
+}
+
+// The same rows with the A digits generated inside the GEMM (k_oz_gemm_gen): nothing is staged in
+// HBM; launches of <= 65535 row tiles.
+static gpr_status oz_w_fused(const gpr_model *M, const GridDev &g, const float2 *Tu, const int64_t *pts,
+                             int64_t pt_base, int64_t count, float2 *W, cudaStream_t st, bool out_by_point,
+                             int64_t row_mod)
+{
+    const OzOperands *O = M->oz;
+    constexpr int S = 7;
+    OzParams prm;
+    prm.Tu = Tu;
+    prm.off1 = (int64_t)g.n[0] * M->mp;
+    prm.off2 = prm.off1 + (int64_t)g.n[1] * M->mp;
+    prm.mp = M->mp;
+    prm.mpt = O->mpt;
+    prm.m = M->m;
+    prm.g = g;
+    prm.colscale = O->colscale;
+    prm.sf2 = (float)M->kp.sf2;
+    prm.W = W;
+    prm.out_by_point = out_by_point ? 1 : 0;
+    prm.row_mod = row_mod > 0 ? row_mod : g.npts();
+    prm.status = gpr_status_word();
+    if (!prm.status) return GPR_ERR_CUDA;
+    size_t smem = 2 * (size_t)(S * A_SLICE + S * B_SLICE) + 64 + 1024;
+    GPR_CUDA_TRY(cudaFuncSetAttribute(k_oz_gemm_gen<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int64_t chunk = (int64_t)65535 * TM;
+    for (int64_t c0 = 0; c0 < count; c0 += chunk) {
+        const int64_t cnt = count - c0 < chunk ? count - c0 : chunk;
+        prm.pts = pts ? pts + c0 : nullptr;
+        prm.pt_base = pt_base + c0;
+        prm.count = cnt;
+        prm.out_off = c0;
+        dim3 grid((unsigned)(M->mp / TN), (unsigned)((cnt + TM - 1) / TM));
+        {
+            ProfScope ps("oz_w", st, (double)cnt);
+            k_oz_gemm_gen<S><<<grid, G_NTHR, smem, st>>>(O->map, prm);
+        }
+        note_launch();
+        GPR_CUDA_TRY(cudaGetLastError());
+    }
+    return GPR_OK;
+}
+
+// Float-float W rows of the listed points on the tensor cores: row r of the list goes to row r
+// of W (count x mp float2), or to row p % row_mod for point p when out_by_point.  Two kernels with
+// the same digits and the same MMA order (so the same bits): A digits generated in the GEMM, or
+// staged in HBM by k_oz_adig; the autotuner keeps the faster per size bucket.
+gpr_status launch_oz_w(const gpr_model *M, const GridDev &g, const float2 *Tu, const int64_t *pts, int64_t pt_base,
+                       int64_t count, float2 *W, cudaStream_t st, bool out_by_point, int64_t row_mod)
+{
+    if (count <= 0) return GPR_OK;
+    if (!M->oz) return GPR_ERR_ARG;
+    if (!encoder()) return GPR_ERR_UNSUPPORTED;
+    auto run = [&](int c) -> gpr_status {
+        return c == 0 ? oz_w_fused(M, g, Tu, pts, pt_base, count, W, st, out_by_point, row_mod)
+                      : oz_w_staged(M, g, Tu, pts, pt_base, count, W, st, out_by_point, row_mod);
+    };
+    return tune_run("oz_w_kernel", tune_bucket(count), 2, run, st);
 }
 
 gpr_status launch_stats_ff(const gpr_model *M, const GridDev &g, const int64_t *pts, int64_t count, const int32_t *slot,

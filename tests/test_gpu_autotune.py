@@ -48,6 +48,32 @@ def test_tile_widths_give_same_bits(torch, g, prec, name):
     assert all(np.array_equal(out[0], o) for o in out[1:])
 
 
+@pytest.mark.parametrize("case", ["ragged", "paper"])
+def test_digit_generation_in_the_gemm_gives_same_bits(torch, g, case):
+    """The FP64-class rows with the kernel-row digits generated inside the GEMM (choice 0) and staged in
+    HBM first (choice 1) are the same bits (same digits, same MMA order): the statistics of a point list
+    with rows beyond a 128-row tile and out-of-list neighbours, and of the paper-scale field's points."""
+    if case == "ragged":
+        w = workloads.small(33, 300, 19, ell=(0.15, 0.2, 0.25)); n = 19
+    else:
+        w = workloads.config2(); n = 64
+    M = model_of(w)
+    grid = g.make_grid(n)
+    rng = np.random.default_rng(7)
+    pts = np.unique(rng.integers(0, n ** 3, 3000 if case == "paper" else 777))
+    t_pts = torch.tensor(pts, dtype=torch.int64, device="cuda")
+    out = []
+    for c in (0, 1):
+        _force(g, "oz_w_kernel", c)
+        st = torch.zeros(len(pts), 15, dtype=torch.float64, device="cuda")
+        g.gpr_stats_points_split(M, grid, t_pts, st)
+        g.gpr_sync()
+        out.append(st.cpu().numpy())
+    _force(g, "oz_w_kernel", -1)
+    assert np.array_equal(out[0], out[1], equal_nan=True)
+    assert np.isfinite(out[0][:, :2]).all()
+
+
 def test_estimator_shapes_give_same_bits_and_table(torch, g):
     w = workloads.small(32, 120, 25)
     M = model_of(w)
