@@ -189,7 +189,9 @@ int64_t gpr_model_m(const gpr_model *model);
  *   other precisions:   mean/var/cov13 are float*; the O(m^2) part runs in that
  *   precision, while the mean k_x . Kt^-1 y (O(m) per point, but a sum of terms
  *   ~1e3 times larger than the result) is summed in float-float arithmetic.
- *   cov13 may be NULL; if given, slot e holds cov(p, p + OFF[e]) (see top).
+ *   cov13 may be NULL; if given, slot e holds cov(p, p + OFF[e]) (see top); for the
+ *   tensor-core precisions the whitened rows of that precision are then written to HBM
+ *   in z-slabs and reduced by the FP32 statistics kernel (for precision studies).
  *   The call may grow the model's workspace (cudaMalloc) on first use of a
  *   larger grid.
  */

@@ -128,8 +128,39 @@ extern "C" gpr_status gpr_reconstruct_dense(gpr_model *M, const gpr_grid *grid, 
     cudaStream_t st = (cudaStream_t)stream;
     GridDev g = make_grid(grid);
     size_t te = table_elems(M, g);
+    if (tc_precision(prec) && cov13) {
+        // covariances of this precision: the tensor-core rows themselves (written by the plain
+        // kernel) and the FP32 statistics kernel over them, in z-slabs with one halo plane
+        GPR_TRY(tc_prepare(M, st));
+        size_t rows = slab_rows(g, M->mp, sizeof(float), kWBudget);
+        size_t np = tc_partial_elems(prec, M, (int64_t)rows);
+        size_t bytes = Carver::round(te * sizeof(float)) + Carver::round(te * sizeof(float2)) +
+                       Carver::round(te * sizeof(double)) + Carver::round(np * sizeof(float)) +
+                       Carver::round(rows * M->mp * sizeof(float)) + 1024;
+        GPR_TRY(ws_reserve(M, 0, bytes, st));
+        Carver cv{(char *)ws_ptr(M, 0)};
+        float *T32 = cv.take<float>(te);
+        float2 *Tff = cv.take<float2>(te);
+        double *T64 = cv.take<double>(te);
+        float *part = cv.take<float>(np);
+        float *W = cv.take<float>(rows * M->mp);
+        GPR_TRY(build_tables(M, g, T64, T32, st, Tff));
+        int64_t nxy = (int64_t)g.n[0] * g.n[1], nz = g.n[2];
+        int64_t zs = (int64_t)(rows / nxy) - 2;
+        if (zs < 1) return GPR_ERR_OOM;
+        for (int64_t z0 = 0; z0 < nz; z0 += zs) {
+            int64_t z1 = z0 + zs < nz ? z0 + zs : nz;
+            int64_t za = z0 > 0 ? z0 - 1 : 0, zb = z1 < nz ? z1 + 1 : nz;
+            int64_t base = za * nxy, o = z0 * nxy;
+            GPR_TRY(launch_tc_var(M, g, prec, T32, nullptr, base, (zb - za) * nxy, part, (float *)var + base, st, W));
+            launch_stats_from_w32(M, g, nullptr, o, (z1 - z0) * nxy, nullptr, base, W, (float *)mean + o,
+                                  (float *)var + o, (float *)cov13 + o * 13, st);
+        }
+        launch_mean_compensated(M, g, Tff, T64, nullptr, 0, g.npts(), (float *)mean, st);
+        GPR_CUDA_TRY(cudaGetLastError());
+        return GPR_OK;
+    }
     if (tc_precision(prec)) {
-        if (cov13) return GPR_ERR_UNSUPPORTED;  // the tensor-core pass reduces W to |w|^2 on chip
         size_t np = tc_partial_elems(prec, M, g.npts());
         size_t bytes = Carver::round(te * sizeof(float)) + Carver::round(te * sizeof(float2)) +
                        Carver::round(te * sizeof(double)) + Carver::round(np * sizeof(float)) + 1024;

@@ -203,8 +203,10 @@ bool tc_precision(gpr_precision p);
 gpr_status tc_prepare(gpr_model *M, cudaStream_t st);
 void tc_release(gpr_model *M);
 size_t tc_partial_elems(gpr_precision p, const gpr_model *M, int64_t count);
+// W (nullable, count x mp): also write the whitened rows of this precision (plain kernel).
 gpr_status launch_tc_var(const gpr_model *M, const GridDev &g, gpr_precision prec, const float *T32,
-                         const int64_t *pts, int64_t pt_base, int64_t count, float *partial, float *var, cudaStream_t st);
+                         const int64_t *pts, int64_t pt_base, int64_t count, float *partial, float *var, cudaStream_t st,
+                         float *W = nullptr);
 // FP32-class mean/variance of a point list in any non-FP64 precision (SIMT FP32 or tensor cores);
 // the mean is always the compensated k . alpha.  `partial` needs tc_partial_elems floats (TC only).
 gpr_status fast_meanvar(gpr_model *M, const GridDev &g, gpr_precision prec, const float *T32, const float2 *Tff,

@@ -1268,8 +1268,9 @@ static gpr_status oz_w_fused(const gpr_model *M, const GridDev &g, const float2 
 
 // Float-float W rows of the listed points on the tensor cores: row r of the list goes to row r
 // of W (count x mp float2), or to row p % row_mod for point p when out_by_point.  Two kernels with
-// the same digits and the same MMA order (so the same bits): A digits generated in the GEMM, or
-// staged in HBM by k_oz_adig; the autotuner keeps the faster per size bucket.
+// the same digits and the same MMA order (so the same bits): A digits generated in the GEMM (no
+// HBM traffic but the kernel rows' digits, but regenerated by every 64-column tile), or staged in
+// HBM once by k_oz_adig; the autotuner keeps the faster per (row count, column tiles) bucket.
 gpr_status launch_oz_w(const gpr_model *M, const GridDev &g, const float2 *Tu, const int64_t *pts, int64_t pt_base,
                        int64_t count, float2 *W, cudaStream_t st, bool out_by_point, int64_t row_mod)
 {
@@ -1280,7 +1281,9 @@ gpr_status launch_oz_w(const gpr_model *M, const GridDev &g, const float2 *Tu, c
         return c == 0 ? oz_w_fused(M, g, Tu, pts, pt_base, count, W, st, out_by_point, row_mod)
                       : oz_w_staged(M, g, Tu, pts, pt_base, count, W, st, out_by_point, row_mod);
     };
-    return tune_run("oz_w_kernel", tune_bucket(count), 2, run, st);
+    // key: the row count's bucket and the number of 64-column tiles (the fused kernel regenerates a
+    // row block's digits once per tile, so its cost relative to staging grows with the model size)
+    return tune_run("oz_w_kernel", tune_bucket(count) * 256 + M->mp / TN, 2, run, st);
 }
 
 gpr_status launch_stats_ff(const gpr_model *M, const GridDev &g, const int64_t *pts, int64_t count, const int32_t *slot,

@@ -153,6 +153,7 @@ struct TcParams {
     const int64_t *pts;
     int64_t pt_base, count;
     float *partial;  // count x nN partial sums of w^2, one per 64 columns
+    float *W;        // nullable: the whitened rows themselves (count x mp), plain kernel only
     int64_t plen;    // floats in `partial` (bounds self-check)
     int64_t tlen;    // floats in T32 (bounds self-check)
     int nN;
@@ -349,6 +350,13 @@ __global__ void __launch_bounds__(NTHR, 1) k_tc_sumsq(const __grid_constant__ CU
             sum = fmaf(w, w, sum);
         }
         red[(half * (N / 2) + c0) / 32][lq * 32 + lane] = sum;
+        if (prm.W) {  // the rows themselves, for the covariances of this precision
+            const int64_t row = row0 + lq * 32 + lane;
+            const int64_t col0 = n0 + half * (N / 2) + c0;
+            if (row < prm.count)
+                for (int i = 0; i < 32; ++i)
+                    if (col0 + i < prm.mp) prm.W[row * prm.mp + col0 + i] = __uint_as_float(rr[i]);
+        }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -698,7 +706,8 @@ size_t tc_partial_elems(gpr_precision p, const gpr_model *M, int64_t count)
 
 // var of the listed points by the tensor-core contraction; `partial` holds tc_partial_elems floats.
 gpr_status launch_tc_var(const gpr_model *M, const GridDev &g, gpr_precision prec, const float *T32,
-                         const int64_t *pts, int64_t pt_base, int64_t count, float *partial, float *var, cudaStream_t st)
+                         const int64_t *pts, int64_t pt_base, int64_t count, float *partial, float *var, cudaStream_t st,
+                         float *W)
 {
     if (count <= 0) return GPR_OK;
     if (!M->tc) return GPR_ERR_ARG;
@@ -715,6 +724,7 @@ gpr_status launch_tc_var(const gpr_model *M, const GridDev &g, gpr_precision pre
     prm.pt_base = pt_base;
     prm.count = count;
     prm.partial = partial;
+    prm.W = W;
     prm.nN = (int)(M->tc->mpt / 64);
     prm.plen = count * prm.nN;
     prm.tlen = prm.off2 + (int64_t)g.n[2] * M->mp;
@@ -751,7 +761,8 @@ gpr_status launch_tc_var(const gpr_model *M, const GridDev &g, gpr_precision pre
     // key: model size and the order of magnitude of the point count
     int lg = 0;
     while (((int64_t)1 << lg) < count && lg < 62) ++lg;
-    GPR_TRY(tune_run(names[(int)prec], (tune_bucket(M->mp) << 6) | lg, 4, run, st));
+    if (W) GPR_TRY(run(1));  // rows out: the plain kernel (only it writes them), wide tiles
+    else GPR_TRY(tune_run(names[(int)prec], (tune_bucket(M->mp) << 6) | lg, 4, run, st));
     k_tc_finalize<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(partial, prm.nN, count, M->kp.sf2, var);
     note_launch();
     GPR_CUDA_TRY(cudaGetLastError());

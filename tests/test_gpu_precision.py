@@ -1,10 +1,15 @@
 """The precision study (m=2000 Matern-5/2, l=0.1, noise 1e-6): mean and variance of every
 precision against the FP64 oracle on the 64^3 sub-block [96, 160)^3 of the 256^3 grid (computed
-on that sub-block as a 64^3 grid with the same spacing), sampled at 3000 points.
+on that sub-block as a 64^3 grid with the same spacing), sampled at 20,000 points; and the cell LCP
+computed from each precision's own 15 statistics (for the tensor-core precisions, their whitened
+rows are written out and reduced to covariances) on a 16^3-cell block of it, against the oracle.
 
-Asserted: the FP64 path (1e-8 of the field scale) and the FP32 path (1e-4).  The tensor-core
-variants are reported (printed) rather than asserted, as the study asks; their single-pass forms
-are known to lose the variance on ill-conditioned models.
+Asserted: the FP64 path (1e-8 of the field scale; LCP 1e-4) and the FP32 path's mean and variance
+(1e-4).  The tensor-core variants and the FP32-class LCP are reported (printed) rather than
+asserted, as the study asks; single-pass tensor-core forms lose the variance on ill-conditioned
+models, and FP32-class covariances cannot feed the cell LCP (the 8x8 corner covariance spans nine
+decades, so its small eigenvalues are lost), which is why the library computes the LCP cells'
+statistics in FP64-class arithmetic whatever the pre-pass precision.
 """
 import numpy as np
 import pytest
@@ -28,7 +33,7 @@ def test_precision_study_subblock_vs_oracle():
     grid = g.make_grid(n, (lo, lo, lo), (hi, hi, hi))
     M = model_of(w)
     rng = np.random.default_rng(12)
-    idx = np.unique(np.concatenate([rng.integers(0, n ** 3, 3000), [0, n ** 3 - 1]]))
+    idx = np.unique(np.concatenate([rng.integers(0, n ** 3, 20000), [0, n ** 3 - 1]]))
     P = lo + np.stack([idx % n, (idx // n) % n, idx // (n * n)], 1) * ((hi - lo) / (n - 1))
     mu, vr = oracle.Model.from_workload(w).posterior(P)
     ys = np.abs(w.y).max()
@@ -42,7 +47,7 @@ def test_precision_study_subblock_vs_oracle():
         v_ = var.cpu().numpy().astype(np.float64)[idx]
         report[name] = (np.abs(m_ - mu).max() / ys, np.abs(m_ - mu).mean() / ys,
                         np.abs(v_ - vr).max() / w.sf2, np.abs(v_ - vr).mean() / w.sf2)
-    print("\nprecision study, m=2000 Matern-5/2, 64^3 sub-block, 3000 points:"
+    print("\nprecision study, m=2000 Matern-5/2, 64^3 sub-block, 20,000 points:"
           " max/mean |dmu|/max|y|, max/mean |dvar|/sf2")
     for k, v in report.items():
         print(f"  {k:7s} " + "  ".join(f"{x:.2e}" for x in v))
@@ -50,3 +55,28 @@ def test_precision_study_subblock_vs_oracle():
     assert report["FP32"][0] <= 1e-4 and report["FP32"][2] <= 1e-4, report["FP32"]
     for k in ("TF32", "TF32X3", "BF16", "BF16X3"):
         assert np.all(np.isfinite(report[k]))
+    # cell LCP from each precision's own statistics, on the 16^3 cells of [96, 112]^3
+    nl = 17
+    lo2, hi2 = lo_i * h, (lo_i + nl - 1) * h
+    g2 = g.make_grid(nl, (lo2, lo2, lo2), (hi2, hi2, hi2))
+    th = w.isovalues[0]
+    ref = oracle.Model.from_workload(w).lcp_block(nl, th, lo=(lo2, lo2, lo2), hi=(hi2, hi2, hi2))
+    lcp_err = {}
+    for name in ("FP64", "FP32", "TF32", "TF32X3", "BF16", "BF16X3"):
+        dt = torch.float64 if name == "FP64" else torch.float32
+        mean = torch.zeros(nl ** 3, dtype=dt, device="cuda")
+        var = torch.zeros_like(mean)
+        cov = torch.zeros(nl ** 3, 13, dtype=dt, device="cuda")
+        g.gpr_reconstruct_dense(M, g2, getattr(g, "GPR_P_" + name), mean, var, cov)
+        st15 = torch.cat([mean[:, None], var[:, None], cov], 1).double().contiguous()
+        out = torch.zeros((nl - 1) ** 3, dtype=torch.float32, device="cuda")
+        g.gpr_cell_lcp_from_stats(g2, st15, th, g.lcp_options(), None, out)
+        g.gpr_sync()
+        d = np.abs(out.cpu().numpy().astype(np.float64) - ref)
+        lcp_err[name] = (float(d.max()), float(d.mean()))
+    print(f"  cell LCP from the precision's own statistics, 16^3 cells, cells with LCP > 1e-3: "
+          f"{int((ref > 1e-3).sum())}; max / mean |dLCP|:")
+    for k, v in lcp_err.items():
+        print(f"  {k:7s} {v[0]:.2e} {v[1]:.2e}")
+    assert (ref > 1e-3).sum() > 50
+    assert lcp_err["FP64"][0] <= 1e-4, lcp_err
