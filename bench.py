@@ -38,7 +38,7 @@ METRIC = "LCP grid points/s"
 # 1600), profiles/sov_estimator_m500_grid64.txt.  The estimator is issue-bound: its roofline is the
 # issue rate, 4 warp instructions per clock on each of 152 SMs at 2.07 GHz; achieved =
 # orthant-samples counted on the device x this figure / launch time.
-SOV_WARP_INST_PER_ORTHANT_SAMPLE = 14.22
+SOV_WARP_INST_PER_ORTHANT_SAMPLE = 12.89
 ISSUE_PEAK_GINST = 152 * 4 * 2.07
 # Dense tensor peaks relative to BF16 (nominal dense rates: TF32 1.1, BF16 2.25 PFLOP/s)
 TF32_OVER_BF16 = 1.1 / 2.25

@@ -212,7 +212,12 @@ gpr_status gpr_stats_points(gpr_model *model, const gpr_grid *grid, const int64_
  * theta) - P(all 8 corners > theta) for the listed cells, from FP64 stats15 of
  * a full grid (device, n x 15 double).  Sigma_8 gets jitter*max(diag) on its
  * diagonal; if sum_c P(Y_c > theta) or sum_c P(Y_c < theta) is below skip_eps
- * the LCP is 0 (Boole's inequality); otherwise the estimator of opts->est runs:
+ * the LCP is 0 (Boole's inequality); a cell with a corner variance that is not
+ * positive after the jitter describes no Gaussian and gets NaN; otherwise the
+ * Cholesky pivots of Sigma_8 are floored at 1e-3 * jitter * max variance (harmless
+ * for rounding-level indefiniteness; statistics far from any covariance, such as
+ * single-pass TF32/BF16 ones, may still give NaN) and the estimator of opts->est
+ * runs:
  *   SOV-QMC: Genz's sequential conditioning over corners 0..7 in index order,
  *            n_samples points of the rank-1 lattice with generators frac(sqrt p)
  *            (p = 2,3,5,...,17) as 32-bit fractions, shifted per cell by the

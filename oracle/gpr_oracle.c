@@ -541,7 +541,8 @@ double or_bvn_lower(double a, double b, double r)
  * Readings (paper silent): Sigma += tau * max diag * I; pivot floor
  * 1e-3 * tau * max diag; if sum_c P(Y_c > theta) or sum_c P(Y_c < theta) is below
  * skip_eps, Boole's inequality bounds the LCP by it and the result is 0; a
- * cell whose largest variance is below 1e-30 is deterministic.
+ * cell whose largest variance is below 1e-30 is deterministic; a cell with a
+ * variance that is not positive after the jitter is no Gaussian and gets NaN.
  * est = EST_SOV: shifts of cell `cell` are SplitMix64 outputs 8*cell+i+1, top
  * 32 bits.  est = EST_MC: Philox-4x32-10 with key (seed lo, seed hi) and counter
  * (sample, cell lo, cell hi, r), r = 0,1 giving 8 normals by Box-Muller.
@@ -565,6 +566,8 @@ double or_cell_lcp(int d, const double *mu, const double *S, double theta, int e
     double jit = tau * maxdiag;
     for (int i = 0; i < d * d; ++i) Sj[i] = S[i];
     for (int i = 0; i < d; ++i) Sj[i * d + i] += jit;
+    for (int i = 0; i < d; ++i)
+        if (!(Sj[i * d + i] > 0.0)) return NAN;
     double s_above = 0.0, s_below = 0.0;
     for (int i = 0; i < d; ++i) {
         double sd = sqrt(Sj[i * d + i]);
@@ -1236,6 +1239,8 @@ double or_cell_lcp_adj(int d, const double *mu, const double *S, double theta, i
     double jit = tau * maxdiag;
     for (int i = 0; i < d * d; ++i) Sj[i] = S[i];
     for (int i = 0; i < d; ++i) Sj[i * d + i] += jit;
+    for (int i = 0; i < d; ++i)
+        if (!(Sj[i * d + i] > 0.0)) return NAN;
     double s_above = 0.0, s_below = 0.0;
     for (int i = 0; i < d; ++i) {
         double sd = sqrt(Sj[i * d + i]);

@@ -6,9 +6,9 @@ iteratively reweighted least squares) against SciPy's double-precision log_ndtr 
   CDF, x = -a <= 0:  Phi(-a) = exp(-a^2/2) * G(t),  t = 1 / (1 + 0.35 a),
                      G a degree-7 polynomial in u = 2t - 1 (a in [0, 13.2]).
   Quantile, p in (0, 1):  z = sqrt(2) (2p - 1) E,  w = -log(4 p (1 - p)),
-                     E a polynomial in a scaled variable on three pieces (degree 8 on the
-                     central piece, 9 on the two tail pieces):
-                     w in [0, 5];  s = sqrt(w) in [sqrt(5), 4];  s in [4, 9.3].
+                     E a polynomial in a scaled variable on two pieces (degree 7 on the
+                     central piece, 12 on the tail piece):
+                     w in [0, 5];  s = sqrt(w) in [sqrt(5), 9.3].
 The variable w is the one of M. Giles, "Approximating the erfinv function" (GPU Computing
 Gems, 2011), written in p so that the tails keep full relative precision; the
 coefficients are this script's own fit.  Run it to regenerate the header.
@@ -21,9 +21,9 @@ from scipy.special import log_ndtr, ndtri
 HERE = os.path.dirname(os.path.abspath(__file__))
 CDF_C0 = 0.35
 CDF_DEG = 7
-PPF_DEG_MID = 8
-PPF_DEG_TAIL = 9
-PPF_PIECES = (("w", 0.0, 5.0), ("s", float(np.sqrt(5.0)), 4.0), ("s", 4.0, 9.3))
+PPF_DEG_MID = 7
+PPF_DEG_TAIL = 12
+PPF_PIECES = (("w", 0.0, 5.0), ("s", float(np.sqrt(5.0)), 9.3))
 
 
 def fit(u, f, deg, iters=60):
@@ -68,31 +68,27 @@ def fmt(v):
     return f"{np.float32(v)!r}f".replace("np.float32(", "").replace(")", "")
 
 
-def horner(coeffs, var, sel=None):
-    """C expression: Horner chain in `var`; with `sel`, coefficients (a if sel else b)."""
-    def c(k):
-        if sel is None:
-            return fmt(coeffs[k])
-        return f"({sel} ? {fmt(coeffs[1][k])} : {fmt(coeffs[0][k])})"
-    n = len(coeffs if sel is None else coeffs[0])
-    expr = c(n - 1)
+def horner(coeffs, var):
+    """C expression: Horner chain in `var`."""
+    n = len(coeffs)
+    expr = fmt(coeffs[n - 1])
     for k in range(n - 2, -1, -1):
-        expr = f"fmaf({expr}, {var}, {c(k)})"
+        expr = f"fmaf({expr}, {var}, {fmt(coeffs[k])})"
     return expr
 
 
 def main():
     c = cdf_coeffs()
-    (m0, h0, p0), (m1, h1, p1), (m2, h2, p2) = ppf_coeffs()
+    (m0, h0, p0), (m1, h1, p1) = ppf_coeffs()
     r2 = np.sqrt(2.0)
-    p0, p1, p2 = p0 * r2, p1 * r2, p2 * r2  # sqrt(2) folded into the quantile polynomials
+    p0, p1 = p0 * r2, p1 * r2  # sqrt(2) folded into the quantile polynomials
     ln2 = np.log(2.0)
     # central piece from lg = log2(4p(1-p)):  v = (w - mid) / half = lg * (-ln2 / half) - mid / half
     lines = [
         "// Generated by fit_normal.py (minimax-relative-error fits against SciPy); do not edit.",
         f"// Standard normal CDF:  Phi(-a) = exp(-a^2/2) G(u),  u = 2/(1 + {CDF_C0} a) - 1.",
         "// Quantile:  z = (2p - 1) sqrt(2) E,  w = -log(4p(1-p)) = -ln2 lg; sqrt(2) E a polynomial in",
-        "//   (w - mid)/half for w < 5, else in (sqrt(w) - mid)/half on [sqrt 5, 4] or [4, 9.3].",
+        "//   (w - mid)/half for w < 5, else in (sqrt(w) - mid)/half on [sqrt 5, 9.3].",
         "#pragma once",
         f"#define NRM_CDF_C0 {fmt(CDF_C0)}",
         f"#define NRM_PPF_LG_SPLIT {fmt(-5.0 / ln2)}",
@@ -100,9 +96,8 @@ def main():
         f"static __device__ __forceinline__ float nrm_ppf_mid_lg(float lg) {{ const float v = fmaf(lg, {fmt(-ln2 * h0)}, "
         f"{fmt(-m0 * h0)}); return " + horner(p0, "v") + "; }",
         "static __device__ __forceinline__ float nrm_ppf_tail(float s) {",
-        "    const bool hi = s >= 4.0f;",
-        f"    const float v = fmaf(s, hi ? {fmt(h2)} : {fmt(h1)}, hi ? {fmt(-m2 * h2)} : {fmt(-m1 * h1)});",
-        "    return " + horner((p1, p2), "v", sel="hi") + ";",
+        f"    const float v = fmaf(s, {fmt(h1)}, {fmt(-m1 * h1)});",
+        "    return " + horner(p1, "v") + ";",
         "}",
     ]
     with open(os.path.join(HERE, "normal_approx.h"), "w") as f:

@@ -153,7 +153,11 @@ __global__ void k_cell_prep(GridDev g, const double *stats, const int32_t *slot,
             result = (lo || hi) ? 0.0f : 1.0f;
         } else {
             double jit = tau * maxd;
-            for (int c = 0; c < 8; ++c) S[c][c] += jit;
+            bool indef = false;
+            for (int c = 0; c < 8; ++c) {
+                S[c][c] += jit;
+                indef = indef || !(S[c][c] > 0.0);
+            }
             // P(Y_c > theta), P(Y_c < theta) in FP32 (relative error ~1e-5 down to 1e-30): a test
             // passes only with a 1% margin, so no cell or orthant the FP64 values would keep is dropped
             float sa = 0.f, sb = 0.f, pa[8], pb[8];
@@ -165,7 +169,11 @@ __global__ void k_cell_prep(GridDev g, const double *stats, const int32_t *slot,
                 sb += pb[c];
             }
             const float lim = (float)(0.99 * skip_eps);
-            if (CF == 1 && !(sa < lim || sb < lim)) {
+            if (indef) {
+                // a corner variance that stays non-positive after the jitter describes no
+                // Gaussian: the cell's LCP is undefined and reported as NaN
+                result = nanf("");
+            } else if (CF == 1 && !(sa < lim || sb < lim)) {
                 // corners taken as independent: 1 - prod P(Y_c < theta) - prod P(Y_c > theta)
                 float plo = 1.f, phi = 1.f;
                 for (int c = 0; c < 8; ++c) {

@@ -13,6 +13,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <unordered_map>
 #include <vector>
 
 #include "internal.h"
@@ -669,11 +670,19 @@ __device__ __forceinline__ bool in_local_box(const Geom &G, const double *x, dou
     return true;
 }
 
+__device__ __forceinline__ uint64_t mix64(uint64_t z)
+{
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
 // Pending nodes whose local set is a strict subset of M: flag them (decision 5 keeps the full-model
-// kernels off them) and track the largest local set.
+// kernels off them), track the largest local set, and record each set's size and an
+// order-independent hash of its members (nodes with equal sets share one factorisation).
 __global__ void k_local_flag(GridDev g, int D, int l, int kd, const int64_t *nodes, int64_t count, int8_t *decision,
                              const double *X, int64_t m, double beta, KernParams kp, uint8_t *flag,
-                             unsigned long long *cmax)
+                             unsigned long long *cmax, uint64_t *sig, int32_t *cnt)
 {
     int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (q >= count) return;
@@ -681,11 +690,27 @@ __global__ void k_local_flag(GridDev g, int D, int l, int kd, const int64_t *nod
     if (decision[q] != 0) return;
     Geom G = node_geom(g, D, l, kd, nodes[q]);
     int64_t c = 0;
-    for (int64_t i = 0; i < m; ++i) c += in_local_box(G, X + 3 * i, beta, kp) ? 1 : 0;
+    uint64_t h = 0;
+    for (int64_t i = 0; i < m; ++i)
+        if (in_local_box(G, X + 3 * i, beta, kp)) {
+            ++c;
+            h += mix64((uint64_t)i * 0x9E3779B97F4A7C15ULL + 1);
+        }
     if (c == m) return;
     flag[q] = 1;
     decision[q] = 5;
+    sig[q] = h;
+    cnt[q] = (int32_t)c;
     atomicMax(cmax, (unsigned long long)c);
+}
+
+__global__ void k_gather_local(const int64_t *list, int64_t nl, const uint64_t *sig, const int32_t *cnt,
+                               uint64_t *osig, int32_t *ocnt)
+{
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= nl) return;
+    osig[t] = sig[list[t]];
+    ocnt[t] = cnt[list[t]];
 }
 
 __device__ __forceinline__ double kval64(const KernParams &kp, const double *a, const double *b)
@@ -974,6 +999,242 @@ __global__ void k_local_nodes(GridDev g, int D, int l, int kd, const int64_t *no
     }
 }
 
+// ---- Grouped local models (plain GPR): nodes with equal local sets share one factorisation.
+// Group record g: grp[4g] = frontier position of a representative node, [4g+1] = |M'| = c,
+// [4g+2] = offset of its FP32 data (L'^-1 column-major c x c, then v' = L'^-1 y', alpha'), [4g+3] =
+// offset of its c member indices.
+
+// Left-looking Cholesky of the column-major c x c matrix L in place (warp-cooperative, FP64).
+__device__ void chol_warp(double *L, double *t, int64_t c, int lane, int *status)
+{
+    for (int64_t j = 0; j < c; ++j) {
+        for (int64_t r = j + lane; r < c; r += 32) {
+            double a = L[r + j * c];
+            for (int64_t k = 0; k < j; ++k) a -= L[r + k * c] * L[j + k * c];
+            t[r] = a;
+        }
+        __syncwarp();
+        double piv = t[j];
+        if (!(piv > 0.0)) {
+            if (lane == 0) atomicCAS(status, 0, (int)GPR_ERR_NOT_PD);
+            piv = 1e-300;
+        }
+        const double d = sqrt(piv);
+        for (int64_t r = j + lane; r < c; r += 32) L[r + j * c] = r == j ? d : t[r] / d;
+        __syncwarp();
+    }
+}
+
+// One warp per group: gather M' of the representative node, factor K' in FP64, and store L'^-1,
+// v' and alpha' in FP32 for the evaluations.
+__global__ void k_local_factor(GridDev g, int D, int l, int kd, const int64_t *nodes, const int64_t *grp, int64_t ng,
+                               LocalModel Mo, double beta, float *F, int32_t *I, double *ws, int64_t cmax, int *status)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    double *L = ws + warp * (cmax * cmax + 3 * cmax);
+    double *t = L + cmax * cmax, *x = t + cmax, *v = x + cmax;
+    for (int64_t gi = warp; gi < ng; gi += nwarps) {
+        const int64_t q = grp[4 * gi], c = grp[4 * gi + 1];
+        float *Fg = F + grp[4 * gi + 2];
+        int32_t *idx = I + grp[4 * gi + 3];
+        const Geom G = node_geom(g, D, l, kd, nodes[q]);
+        int64_t cc = 0;
+        for (int64_t base = 0; base < Mo.m; base += 32) {
+            const int64_t i = base + lane;
+            const bool in = i < Mo.m && in_local_box(G, Mo.X + 3 * i, beta, Mo.kp);
+            const unsigned msk = __ballot_sync(0xffffffffu, in);
+            if (in && cc + __popc(msk & ((1u << lane) - 1)) < c) idx[cc + __popc(msk & ((1u << lane) - 1))] = (int32_t)i;
+            cc += __popc(msk);
+        }
+        __syncwarp();
+        if (cc != c && lane == 0) atomicCAS(status, 0, (int)GPR_ERR_ARG);  // self-check: equal sets
+        for (int64_t s2 = 0; s2 < c; ++s2)
+            for (int64_t r = s2 + lane; r < c; r += 32)
+                L[r + s2 * c] = kval64(Mo.kp, Mo.X + 3 * idx[r], Mo.X + 3 * idx[s2]) + (r == s2 ? Mo.diag : 0.0);
+        __syncwarp();
+        chol_warp(L, t, c, lane, status);
+        for (int64_t r = lane; r < c; r += 32) v[r] = Mo.y[idx[r]];
+        __syncwarp();
+        fwd_solve(L, c, v, lane);
+        bwd_solve(L, c, v, t, lane);
+        for (int64_t r = lane; r < c; r += 32) {
+            Fg[c * c + r] = (float)v[r];
+            Fg[c * c + c + r] = (float)t[r];
+        }
+        // L'^-1 column by column: column j solves L' x = e_j (rows >= j)
+        for (int64_t j = 0; j < c; ++j) {
+            for (int64_t r = lane; r < c; r += 32) x[r] = r == j ? 1.0 : 0.0;
+            __syncwarp();
+            for (int64_t jj = j; jj < c; ++jj) {
+                const double xj = x[jj] / L[jj + jj * c];
+                __syncwarp();
+                if (lane == 0) x[jj] = xj;
+                for (int64_t r = jj + 1 + lane; r < c; r += 32) x[r] -= L[r + jj * c] * xj;
+                __syncwarp();
+            }
+            for (int64_t r = lane; r < c; r += 32) Fg[r + j * c] = r >= j ? (float)x[r] : 0.f;
+            __syncwarp();
+        }
+    }
+}
+
+// g = (theta - mu) / sigma on a group's local model in FP32 (w = L'^-1 k as a triangular mat-vec).
+__device__ float local_eval32(const KernParams &kp, const double *X, const int32_t *idx, const float *Fg, int64_t c,
+                              const double *x, double theta, bool want_grad, float grad[3], float *wk, int lane)
+{
+    float *kv = wk, *dk = wk + c, *w = wk + 4 * c;
+    const float ix = (float)(1.0 / kp.ell[0]), iy = (float)(1.0 / kp.ell[1]), iz = (float)(1.0 / kp.ell[2]);
+    for (int64_t r = lane; r < c; r += 32) {
+        const double *b = X + 3 * idx[r];
+        const float dx = (float)(x[0] - b[0]), dy = (float)(x[1] - b[1]), dz = (float)(x[2] - b[2]);
+        const float a = dx * ix, bb = dy * iy, cz = dz * iz, r2 = a * a + bb * bb + cz * cz;
+        float kvl, gcoef;
+        if (kp.kind == GPR_K_SE) {
+            kvl = (float)kp.sf2 * expf(-0.5f * r2);
+            gcoef = -kvl;
+        } else {
+            const float rr = sqrtf(r2), s5r = 2.23606797749979f * rr, e = expf(-s5r);
+            kvl = (float)kp.sf2 * (1.0f + s5r + (5.0f / 3.0f) * r2) * e;
+            gcoef = -(5.0f / 3.0f) * (float)kp.sf2 * (1.0f + s5r) * e;
+        }
+        kv[r] = kvl;
+        dk[3 * r] = gcoef * dx * ix * ix;
+        dk[3 * r + 1] = gcoef * dy * iy * iy;
+        dk[3 * r + 2] = gcoef * dz * iz * iz;
+    }
+    __syncwarp();
+    float mu = 0.f, ww = 0.f;
+    for (int64_t r = lane; r < c; r += 32) {
+        float a = 0.f;
+        for (int64_t j = 0; j <= r; ++j) a = fmaf(Fg[r + j * c], kv[j], a);
+        w[r] = a;
+        mu = fmaf(a, Fg[c * c + r], mu);
+        ww = fmaf(a, a, ww);
+    }
+    __syncwarp();
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        mu += __shfl_xor_sync(0xffffffffu, mu, o);
+        ww += __shfl_xor_sync(0xffffffffu, ww, o);
+    }
+    float var = (float)kp.sf2 - ww;
+    const float fl = (float)(1e-12 * kp.sf2);
+    if (!(var > fl)) var = fl;
+    const float sd = sqrtf(var), gl = (float)((theta - (double)mu) / (double)sd);
+    if (!want_grad) return gl;
+    // P_j = sum_{r >= j} L'^-1_rj w_r; d mu = dk . alpha', d var = -2 dk . P
+    float gm[3] = {0.f, 0.f, 0.f}, gv[3] = {0.f, 0.f, 0.f};
+    for (int64_t j = 0; j < c; ++j) {
+        float p = 0.f;
+        for (int64_t r = j + lane; r < c; r += 32) p = fmaf(Fg[r + j * c], w[r], p);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) p += __shfl_xor_sync(0xffffffffu, p, o);
+        if ((j & 31) == lane) {
+            const float al = Fg[c * c + c + j];
+            for (int d = 0; d < 3; ++d) {
+                gm[d] = fmaf(dk[3 * j + d], al, gm[d]);
+                gv[d] = fmaf(-2.f * dk[3 * j + d], p, gv[d]);
+            }
+        }
+    }
+    for (int d = 0; d < 3; ++d) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            gm[d] += __shfl_xor_sync(0xffffffffu, gm[d], o);
+            gv[d] += __shfl_xor_sync(0xffffffffu, gv[d], o);
+        }
+        grad[d] = -gm[d] / sd - gl * gv[d] / (2.f * var);
+    }
+    __syncwarp();
+    return gl;
+}
+
+// One warp per local node of a grouped (plain GPR) level: the minimiser of k_local_nodes on its
+// group's FP32 factor.
+__global__ void k_local_eval(GridDev g, int D, int l, int kd, const int64_t *nodes, const int64_t *list,
+                             const int32_t *node_group, int64_t nl, const int64_t *grp, KernParams kp, const double *X,
+                             double theta, double alpha, int T, const int8_t *sides, int8_t *decision, double *bound,
+                             const float *F, const int32_t *I, float *ws, int64_t cmax)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    float *wk = ws + warp * 5 * cmax;
+    for (int64_t t = warp; t < nl; t += nwarps) {
+        const int64_t q = list[t], gi = node_group[t];
+        const int64_t c = grp[4 * gi + 1];
+        const float *Fg = F + grp[4 * gi + 2];
+        const int32_t *idx = I + grp[4 * gi + 3];
+        const Geom G = node_geom(g, D, l, kd, nodes[q]);
+        const int sd = sides[q];
+        double gmin[2] = {INFINITY, INFINITY};
+        float gr[3];
+        const bool small = G.p1[0] - G.p0[0] <= 2 && G.p1[1] - G.p0[1] <= 2 && G.p1[2] - G.p0[2] <= 2;
+        const double dcount =
+            (double)((G.p1[0] - G.p0[0] + 1) * (G.p1[1] - G.p0[1] + 1) * (G.p1[2] - G.p0[2] + 1));
+        if (small) {
+            for (int64_t cz = G.p0[2]; cz <= G.p1[2]; ++cz)
+                for (int64_t cy = G.p0[1]; cy <= G.p1[1]; ++cy)
+                    for (int64_t cx = G.p0[0]; cx <= G.p1[0]; ++cx) {
+                        const double x[3] = {g.lo[0] + (double)cx * g.h[0], g.lo[1] + (double)cy * g.h[1],
+                                             g.lo[2] + (double)cz * g.h[2]};
+                        const double v = local_eval32(kp, X, idx, Fg, c, x, theta, false, gr, wk, lane);
+                        gmin[0] = fmin(gmin[0], v);
+                        gmin[1] = fmin(gmin[1], -v);
+                    }
+        } else {
+            double bx[2][3], bg[2][3];
+            for (int t27 = 0; t27 < 27; ++t27) {
+                const int id[3] = {t27 % 3, (t27 / 3) % 3, t27 / 9};
+                double x[3];
+                for (int d = 0; d < 3; ++d) x[d] = G.blo[d] + 0.5 * (double)id[d] * (G.bhi[d] - G.blo[d]);
+                const double v = local_eval32(kp, X, idx, Fg, c, x, theta, true, gr, wk, lane);
+                for (int s2 = 0; s2 < 2; ++s2) {
+                    const double sg = s2 == 0 ? 1.0 : -1.0;
+                    if (sg * v < gmin[s2]) {
+                        gmin[s2] = sg * v;
+                        for (int d = 0; d < 3; ++d) { bx[s2][d] = x[d]; bg[s2][d] = sg * gr[d]; }
+                    }
+                }
+            }
+            if (!(bound_of(sd, dcount, gmin[0], gmin[1]) > alpha)) {
+                for (int s2 = 0; s2 < 2; ++s2) {
+                    if (!(sd & (1 << s2))) continue;
+                    const double sg = s2 == 0 ? 1.0 : -1.0;
+                    for (int stp = 0; stp < T; ++stp) {
+                        double wv[3], u[3], un = 0.0;
+                        for (int d = 0; d < 3; ++d) {
+                            wv[d] = G.bhi[d] - G.blo[d];
+                            u[d] = -bg[s2][d] * wv[d];
+                            un = fmax(un, fabs(u[d]));
+                        }
+                        if (!(un > 0.0)) break;
+                        const double eta = 0.25 * ldexp(1.0, -stp);
+                        double xc[3];
+                        for (int d = 0; d < 3; ++d) {
+                            const double xn = bx[s2][d] + eta * wv[d] * u[d] / un;
+                            xc[d] = xn < G.blo[d] ? G.blo[d] : (xn > G.bhi[d] ? G.bhi[d] : xn);
+                        }
+                        const double v = sg * local_eval32(kp, X, idx, Fg, c, xc, theta, true, gr, wk, lane);
+                        if (v < gmin[s2]) {
+                            gmin[s2] = v;
+                            for (int d = 0; d < 3; ++d) { bx[s2][d] = xc[d]; bg[s2][d] = sg * gr[d]; }
+                        }
+                    }
+                }
+            }
+        }
+        if (lane == 0) {
+            const double bnd = bound_of(sd, dcount, gmin[0], gmin[1]);
+            bound[q] = bnd;
+            decision[q] = bnd > alpha ? 2 : 0;
+        }
+        __syncwarp();
+    }
+}
+
 struct OctBuffers {
     int64_t *front[2];
     int8_t *decision, *sides;
@@ -990,6 +1251,8 @@ struct OctBuffers {
     int64_t *ulist;
     uint8_t *lflag2;  // nodes on the local model (beta >= 0)
     int64_t *llist;
+    uint64_t *lsig;   // per node: hash and size of its local set
+    int32_t *lcnt;
     uint8_t *cvalid;
     MinState *ms;
     unsigned long long *counters;  // [0] nnext, [1] nsub
@@ -1031,6 +1294,170 @@ static gpr_status run_eval(const gpr_model *M, const EvalModel &E, OctBuffers &B
     return GPR_OK;
 }
 
+// Local models of the listed nodes (device list), one warp per node, FP64 throughout (gather,
+// factor, minimise); work space per warp, bounded to ~2 GB.
+static gpr_status local_per_node(gpr_model *M, const GridDev &g, int D, int l, int kd, const int64_t *nodes,
+                                 const OctBuffers &B, const int64_t *list, int64_t nlist, int64_t cmax, double theta,
+                                 const gpr_lcp_options *opts, int T, cudaStream_t st)
+{
+    const int64_t c = cmax > 0 ? cmax : 1;
+    const size_t dper = (size_t)c * c * (M->sgpr ? 2 : 1) + 12 * (size_t)c;
+    const size_t per = sizeof(double) * dper + sizeof(int32_t) * (size_t)c;
+    int64_t nw = nlist < 4 * (int64_t)num_sms() ? nlist : 4 * (int64_t)num_sms();
+    const int64_t cap = (int64_t)(((size_t)2 << 30) / per);
+    if (nw > cap) nw = cap > 0 ? cap : 1;
+    void *lws = nullptr;
+    GPR_CUDA_TRY(cudaMallocAsync(&lws, per * (size_t)nw + 256, st));
+    double *dws = (double *)lws;
+    int32_t *iws = (int32_t *)((char *)lws + sizeof(double) * dper * nw);
+    LocalModel Mo{M->X, M->y, M->sgpr ? M->A_M : nullptr, M->m, M->kp, M->sgpr ? M->kmm_jitter : M->sn2};
+    int *status = gpr_status_word();
+    if (!status) return GPR_ERR_CUDA;
+    {
+        ProfScope ps("oct_local", st, (double)nlist);
+        k_local_nodes<<<(unsigned)((nw + 3) / 4), 128, 0, st>>>(g, D, l, kd, nodes, list, nlist, Mo, opts->beta, theta,
+                                                                opts->alpha, T, B.sides, B.decision, B.bound, dws, iws,
+                                                                c, status);
+    }
+    note_launch();
+    GPR_CUDA_TRY(cudaGetLastError());
+    GPR_CUDA_TRY(cudaFreeAsync(lws, st));
+    return GPR_OK;
+}
+
+// Local models of a level's listed nodes for a plain GPR model: nodes are grouped by their local
+// set (hash and size, gathered from the device), one factorisation per group (FP64, stored as
+// FP32 L'^-1), then every node is bounded on its group's factor in FP32.  Groups are processed in
+// batches whose FP32 data stays within ~2 GB.
+static gpr_status local_grouped(gpr_model *M, const GridDev &g, int D, int l, int kd, const int64_t *nodes,
+                                const OctBuffers &B, int64_t nl, int64_t cmax, double theta,
+                                const gpr_lcp_options *opts, int T, cudaStream_t st)
+{
+    std::vector<uint64_t> hs((size_t)nl);
+    std::vector<int32_t> hc((size_t)nl);
+    std::vector<int64_t> hl((size_t)nl);
+    {
+        void *tmp = nullptr;
+        GPR_CUDA_TRY(cudaMallocAsync(&tmp, (size_t)nl * 12 + 256, st));
+        uint64_t *ds = (uint64_t *)tmp;
+        int32_t *dc = (int32_t *)((char *)tmp + (size_t)nl * 8);
+        k_gather_local<<<nb(nl, 256), 256, 0, st>>>(B.llist, nl, B.lsig, B.lcnt, ds, dc);
+        note_launch();
+        GPR_CUDA_TRY(cudaMemcpyAsync(hs.data(), ds, (size_t)nl * 8, cudaMemcpyDeviceToHost, st));
+        GPR_CUDA_TRY(cudaMemcpyAsync(hc.data(), dc, (size_t)nl * 4, cudaMemcpyDeviceToHost, st));
+        GPR_CUDA_TRY(cudaMemcpyAsync(hl.data(), B.llist, (size_t)nl * 8, cudaMemcpyDeviceToHost, st));
+        GPR_CUDA_TRY(cudaFreeAsync(tmp, st));
+        GPR_CUDA_TRY(cudaStreamSynchronize(st));
+    }
+    // groups in order of first appearance
+    std::unordered_map<uint64_t, int32_t> key_to_group;
+    std::vector<int32_t> node_group((size_t)nl);
+    std::vector<int64_t> rep, gc;
+    for (int64_t t = 0; t < nl; ++t) {
+        const uint64_t key = hs[t] ^ ((uint64_t)hc[t] * 0xD6E8FEB86659FD93ULL);
+        auto it = key_to_group.find(key);
+        if (it == key_to_group.end()) {
+            it = key_to_group.emplace(key, (int32_t)rep.size()).first;
+            rep.push_back(hl[t]);
+            gc.push_back(hc[t]);
+        }
+        node_group[t] = it->second;
+    }
+    // a set that only one node has is cheaper to factor and solve per node in FP64 than to invert
+    std::vector<int64_t> members(rep.size(), 0);
+    for (int64_t t = 0; t < nl; ++t) ++members[node_group[t]];
+    std::vector<int32_t> remap(rep.size(), -1);
+    std::vector<int64_t> rep2, gc2, singles;
+    for (size_t gi = 0; gi < rep.size(); ++gi)
+        if (members[gi] > 1) {
+            remap[gi] = (int32_t)rep2.size();
+            rep2.push_back(rep[gi]);
+            gc2.push_back(gc[gi]);
+        }
+    for (int64_t t = 0; t < nl; ++t) {
+        if (remap[node_group[t]] < 0) singles.push_back(hl[t]);
+        node_group[t] = remap[node_group[t]];
+    }
+    rep.swap(rep2);
+    gc.swap(gc2);
+    if (!singles.empty()) {
+        int64_t *dl = nullptr;
+        GPR_CUDA_TRY(cudaMallocAsync((void **)&dl, singles.size() * 8, st));
+        GPR_CUDA_TRY(cudaMemcpyAsync(dl, singles.data(), singles.size() * 8, cudaMemcpyHostToDevice, st));
+        GPR_TRY(local_per_node(M, g, D, l, kd, nodes, B, dl, (int64_t)singles.size(), cmax, theta, opts, T, st));
+        GPR_CUDA_TRY(cudaFreeAsync(dl, st));
+        GPR_CUDA_TRY(cudaStreamSynchronize(st));
+    }
+    const int64_t ng = (int64_t)rep.size();
+    const size_t budget = (size_t)2 << 30;
+    LocalModel Mo{M->X, M->y, nullptr, M->m, M->kp, M->sn2};
+    int *status = gpr_status_word();
+    if (!status) return GPR_ERR_CUDA;
+    int64_t g0 = 0;
+    while (g0 < ng) {
+        // a batch of groups [g0, g1) and the nodes that belong to it
+        size_t fbytes = 0, ibytes = 0;
+        int64_t g1 = g0;
+        std::vector<int64_t> tab;
+        while (g1 < ng) {
+            const size_t c = (size_t)gc[g1];
+            const size_t fb = Carver::round((c * c + 2 * c) * sizeof(float)), ib = Carver::round(c * sizeof(int32_t));
+            if (g1 > g0 && fbytes + ib + ibytes + fb > budget) break;
+            tab.insert(tab.end(), {rep[g1], (int64_t)c, (int64_t)(fbytes / sizeof(float)), (int64_t)(ibytes / sizeof(int32_t))});
+            fbytes += fb;
+            ibytes += ib;
+            ++g1;
+        }
+        std::vector<int64_t> blist;
+        std::vector<int32_t> bgroup;
+        for (int64_t t = 0; t < nl; ++t)
+            if (node_group[t] >= 0 && node_group[t] >= g0 && node_group[t] < g1) {
+                blist.push_back(hl[t]);
+                bgroup.push_back(node_group[t] - (int32_t)g0);
+            }
+        const int64_t bg = g1 - g0, bn = (int64_t)blist.size();
+        const int64_t nwf = bg < 4 * (int64_t)num_sms() ? bg : 4 * (int64_t)num_sms();
+        const int64_t nwe = bn < 16 * (int64_t)num_sms() ? bn : 16 * (int64_t)num_sms();
+        const size_t wsf = Carver::round((size_t)nwf * (cmax * cmax + 3 * cmax) * sizeof(double));
+        const size_t wse = Carver::round((size_t)nwe * 5 * cmax * sizeof(float));
+        const size_t total = Carver::round(fbytes) + Carver::round(ibytes) + wsf + wse +
+                             Carver::round(tab.size() * 8) + Carver::round(blist.size() * 8) +
+                             Carver::round(bgroup.size() * 4) + 1024;
+        void *buf = nullptr;
+        GPR_CUDA_TRY(cudaMallocAsync(&buf, total, st));
+        Carver cv{(char *)buf};
+        float *F = cv.take<float>(fbytes / sizeof(float));
+        int32_t *I = cv.take<int32_t>(ibytes / sizeof(int32_t));
+        double *wf = cv.take<double>((size_t)nwf * (cmax * cmax + 3 * cmax));
+        float *we = cv.take<float>((size_t)nwe * 5 * cmax);
+        int64_t *dtab = cv.take<int64_t>(tab.size());
+        int64_t *dlist = cv.take<int64_t>(blist.size());
+        int32_t *dgroup = cv.take<int32_t>(bgroup.size());
+        GPR_CUDA_TRY(cudaMemcpyAsync(dtab, tab.data(), tab.size() * 8, cudaMemcpyHostToDevice, st));
+        GPR_CUDA_TRY(cudaMemcpyAsync(dlist, blist.data(), blist.size() * 8, cudaMemcpyHostToDevice, st));
+        GPR_CUDA_TRY(cudaMemcpyAsync(dgroup, bgroup.data(), bgroup.size() * 4, cudaMemcpyHostToDevice, st));
+        {
+            ProfScope ps("oct_local_factor", st, (double)bg);
+            k_local_factor<<<(unsigned)((nwf + 3) / 4), 128, 0, st>>>(g, D, l, kd, nodes, dtab, bg, Mo, opts->beta, F, I,
+                                                                      wf, cmax, status);
+        }
+        note_launch();
+        {
+            ProfScope ps("oct_local", st, (double)bn);
+            k_local_eval<<<(unsigned)((nwe + 3) / 4), 128, 0, st>>>(g, D, l, kd, nodes, dlist, dgroup, bn, dtab, M->kp,
+                                                                    M->X, theta, opts->alpha, T, B.sides, B.decision,
+                                                                    B.bound, F, I, we, cmax);
+        }
+        note_launch();
+        GPR_CUDA_TRY(cudaGetLastError());
+        GPR_CUDA_TRY(cudaFreeAsync(buf, st));
+        // the host vectors are released at return; the copies above were queued before the free
+        GPR_CUDA_TRY(cudaStreamSynchronize(st));
+        g0 = g1;
+    }
+    return GPR_OK;
+}
+
 gpr_status octree_lcp(gpr_model *M, const gpr_grid *grid, double theta, int D, const gpr_lcp_options *opts,
                       float *lcp, gpr_adaptive_stats *stats, cudaStream_t st, OctTrace *trace)
 {
@@ -1055,7 +1482,8 @@ gpr_status octree_lcp(gpr_model *M, const gpr_grid *grid, double theta, int D, c
                    Carver::round((size_t)nc * sizeof(MinState)) + Carver::round((size_t)max_large * 27 * 16) + 512 +
                    csb + Carver::round(tc_partial_elems(GPR_P_BF16X3, M, n) * 4) + Carver::round((size_t)max_large * 2) +
                    Carver::round((size_t)max_large * 16) + 8192 + Carver::round((size_t)nc * 4) + 2 * Carver::round((size_t)nc) +
-                   Carver::round((size_t)nc) + Carver::round((size_t)nc * 8) + 256 * 24;
+                   Carver::round((size_t)nc) + Carver::round((size_t)nc * 8) + Carver::round((size_t)nc * 8) +
+                   Carver::round((size_t)nc * 4) + 256 * 26;
     gpr_precision pp = opts->prec == GPR_P_FP64 ? GPR_P_FP32 : opts->prec;
     GridCache *C = nullptr;
     GPR_TRY(grid_cache(M, grid, g, pp, &C, st));
@@ -1106,6 +1534,8 @@ gpr_status octree_lcp(gpr_model *M, const gpr_grid *grid, double theta, int D, c
     B.ulist = cv.take<int64_t>((size_t)max_large * 2);
     B.lflag2 = cv.take<uint8_t>((size_t)nc);
     B.llist = cv.take<int64_t>((size_t)nc);
+    B.lsig = cv.take<uint64_t>((size_t)nc);
+    B.lcnt = cv.take<int32_t>((size_t)nc);
     const bool local = opts->beta >= 0.0 && isfinite(opts->beta);
     int32_t *slot = (int32_t *)B.tmp_mean;  // reused by the leaf phase (n int32 fits in n floats)
     int64_t *clist = B.pend;                 // reused by the leaf phase (nc int64)
@@ -1156,7 +1586,7 @@ gpr_status octree_lcp(gpr_model *M, const gpr_grid *grid, double theta, int D, c
         if (local) {
             GPR_CUDA_TRY(cudaMemsetAsync(B.counters + 2, 0, sizeof(unsigned long long), st));
             k_local_flag<<<nb(count, 128), 128, 0, st>>>(g, D, l, kd, nodes, count, B.decision, M->X, m, opts->beta, M->kp,
-                                                         B.lflag2, B.counters + 2);
+                                                         B.lflag2, B.counters + 2, B.lsig, B.lcnt);
             note_launch();
             GPR_TRY(compact_flags(B.lflag2, count, B.llist, nullptr, &nlocal, B.cscr, B.csb, st));
             if (nlocal > 0)
@@ -1258,30 +1688,10 @@ gpr_status octree_lcp(gpr_model *M, const gpr_grid *grid, double theta, int D, c
                 }
             }
         }
-        if (nlocal > 0) {
-            // one warp per local node; FP64 work space per warp, bounded to ~2 GB
-            const int64_t c = cmax > 0 ? (int64_t)cmax : 1;
-            const size_t per = sizeof(double) * ((size_t)c * c * (M->sgpr ? 2 : 1) + 12 * (size_t)c) +
-                               sizeof(int32_t) * (size_t)c;
-            int64_t nw = nlocal < 4 * (int64_t)num_sms() ? nlocal : 4 * (int64_t)num_sms();
-            const int64_t cap = (int64_t)(((size_t)2 << 30) / per);
-            if (nw > cap) nw = cap > 0 ? cap : 1;
-            void *lws = nullptr;
-            GPR_CUDA_TRY(cudaMallocAsync(&lws, per * (size_t)nw + 256, st));
-            double *dws = (double *)lws;
-            int32_t *iws = (int32_t *)((char *)lws + sizeof(double) * ((size_t)c * c * (M->sgpr ? 2 : 1) + 12 * (size_t)c) * nw);
-            LocalModel Mo{M->X, M->y, M->sgpr ? M->A_M : nullptr, m, M->kp, M->sgpr ? M->kmm_jitter : M->sn2};
-            int *status = gpr_status_word();
-            if (!status) return GPR_ERR_CUDA;
-            {
-                ProfScope ps("oct_local", st, (double)nlocal);
-                k_local_nodes<<<(unsigned)((nw + 3) / 4), 128, 0, st>>>(g, D, l, kd, nodes, B.llist, nlocal, Mo, opts->beta,
-                                                                        theta, opts->alpha, T, B.sides, B.decision,
-                                                                        B.bound, dws, iws, c, status);
-            }
-            note_launch();
-            GPR_CUDA_TRY(cudaGetLastError());
-            GPR_CUDA_TRY(cudaFreeAsync(lws, st));
+        if (nlocal > 0 && !M->sgpr) {
+            GPR_TRY(local_grouped(M, g, D, l, kd, nodes, B, nlocal, (int64_t)cmax, theta, opts, T, st));
+        } else if (nlocal > 0) {
+            GPR_TRY(local_per_node(M, g, D, l, kd, nodes, B, B.llist, nlocal, (int64_t)cmax, theta, opts, T, st));
         }
         GPR_CUDA_TRY(cudaMemsetAsync(B.counters, 0, 2 * sizeof(unsigned long long), st));
         k_children<<<nb(count, 256), 256, 0, st>>>(g, D, l, kd, nodes, count, B.decision, B.front[1 - cur], B.counters,

@@ -140,9 +140,14 @@ def test_adaptive_argument_checks(torch, g):
 @pytest.mark.parametrize("kind", ["gpr", "sgpr"])
 def test_local_model_levels_match_oracle(torch, g, kind):
     """Sec. 5.2's local model (beta >= 0): nodes whose enlarged box (beta * l_d per axis) leaves some
-    observations out are bounded on the model of the rest, in FP64 on the device (one warp per node).
-    Level by level against the oracle: p-test decisions equal, bound decisions equal except within a
-    factor 3 of alpha, and the bounds of nodes both sides minimised fully agree to 1e-6 relative."""
+    observations out are bounded on the model of the rest.  Plain GPR: nodes with equal local sets
+    share one FP64 factorisation and are evaluated in FP32 (as the full model's bound is); SGPR: FP64
+    per node.  Level by level against the oracle's FP64 local model: p-test decisions equal, bound
+    decisions equal except within a factor 3 of alpha, and the bounds of nodes both sides minimised
+    fully agree to 1e-6 relative (SGPR, FP64), or to 5e-2 where they are >= alpha / 10 (plain, FP32
+    evaluations: the whitened FP32 variance carries ~6e-6 of sf2 against node variances of ~2e-4
+    of sf2, a few per cent in the Phi tails the bound sits in; far smaller bounds differ more in
+    relative terms and decide nothing)."""
     w = workloads.config2() if kind == "gpr" else workloads.sgpr(n=33)
     beta = 1.0
     M = model_of(w)
@@ -161,8 +166,11 @@ def test_local_model_levels_match_oracle(torch, g, kind):
         near = (obnd >= 1e-3 / 3) & (obnd <= 3e-3)
         assert np.all(near[bad]), (l, obnd[bad & ~near][:8], bnd[bad & ~near][:8])
         both0 = (odec == 0) & (dec == 0)
-        if both0.any():
+        if kind == "sgpr" and both0.any():
             np.testing.assert_allclose(bnd[both0], obnd[both0], rtol=1e-6, atol=1e-300)
+        near_a = both0 & (obnd >= 1e-4)  # FP32 evaluations: compare the bounds that decide
+        if kind == "gpr" and near_a.any():
+            np.testing.assert_allclose(bnd[near_a], obnd[near_a], rtol=5e-2, atol=1e-300)
         seen += len(nodes)
     assert seen > 100
     # a beta whose boxes cover the domain gives the full model's decisions exactly

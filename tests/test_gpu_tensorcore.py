@@ -91,14 +91,27 @@ def test_tc_prepass_lcp_equals_fp64(torch, g):
     assert np.array_equal(out[g.GPR_P_FP64], out[g.GPR_P_BF16X3])
 
 
-def test_tc_cov13_not_served(torch, g):
+@pytest.mark.parametrize("prec", ["TF32", "TF32X3", "BF16", "BF16X3"])
+def test_tc_cov13_against_oracle(torch, g, prec):
+    """The 13 forward covariances in the tensor-core precisions (their whitened rows written out
+    and reduced, cov = k(a, b) - w_a . w_b): NaN exactly where the neighbour is off the grid, and
+    within the precision's own error of the oracle elsewhere (split forms 1e-4 sf2, single-pass
+    forms 5e-2 sf2, the size of their variance errors at this conditioning)."""
     w = workloads.small(3, 20, 5)
     M = model_of(w)
-    t = torch.zeros(125, dtype=torch.float32, device="cuda")
-    c = torch.zeros(125, 13, dtype=torch.float32, device="cuda")
-    with pytest.raises(g.GPRError) as e:
-        g.gpr_reconstruct_dense(M, g.make_grid(5), g.GPR_P_TF32X3, t, t.clone(), c)
-    assert e.value.status == g.GPR_ERR_UNSUPPORTED
+    n = 5
+    mean = torch.zeros(n ** 3, dtype=torch.float32, device="cuda")
+    var = torch.zeros_like(mean)
+    cov = torch.zeros(n ** 3, 13, dtype=torch.float32, device="cuda")
+    g.gpr_reconstruct_dense(M, g.make_grid(n), getattr(g, "GPR_P_" + prec), mean, var, cov)
+    g.gpr_sync()
+    ref = oracle.Model.from_workload(w).stats15(n)
+    c = cov.cpu().numpy().astype(np.float64)
+    assert np.array_equal(np.isnan(c), np.isnan(ref[:, 2:]))
+    ok = ~np.isnan(c)
+    tol = (1e-4 if prec.endswith("X3") else 5e-2) * w.sf2
+    np.testing.assert_allclose(c[ok], ref[:, 2:][ok], rtol=0, atol=tol)
+    np.testing.assert_allclose(var.cpu().numpy().astype(np.float64), ref[:, 1], rtol=0, atol=tol)
 
 
 @pytest.mark.parametrize("case", ["config2", "small_m97"])

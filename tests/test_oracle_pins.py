@@ -374,6 +374,10 @@ def test_lcp_skip_and_range():
         A = rng.normal(size=(8, 8)); S = A @ A.T * rng.uniform(0.001, 1)
         v = oracle.cell_lcp(rng.normal(0, 1, 8), S, 0.0)
         assert 0.0 <= v <= 1.0
+    # a corner variance that is negative even after the jitter: no Gaussian, so no LCP
+    Sn = S.copy(); Sn[3, 3] = -0.5 * Sn.diagonal().max()
+    for est in (oracle.EST_SOV, oracle.EST_MC, oracle.EST_INDEP, oracle.EST_EDGE):
+        assert np.isnan(oracle.cell_lcp(np.zeros(8), Sn, 0.0, est=est))
 
 
 def test_lcp_field_brute_force_mc_small():
