@@ -232,6 +232,31 @@ __device__ __forceinline__ void gen_a_chunk(const TcParams &prm, unsigned char *
     }
 }
 
+// The MMAs of one 128-byte K block, in the order every variant uses (so all give the same bits):
+// TF32 K blocks are issued as two 16-element halves, each product over its two K steps in turn
+// (the order of the 64-byte-row variant below); BF16 blocks product by product over four K steps.
+template <int P, int N>
+__device__ __forceinline__ void issue_block128(uint32_t tmem, uint32_t abase0, uint32_t bbase0, bool first)
+{
+    using C = Cfg<P>;
+    constexpr int A_TILE = TM * 128, B_TILE = N * 128;
+    constexpr uint32_t ID = idesc<C::BF>(TM, N);
+    constexpr int H = C::BF ? 1 : 2;  // halves of the block
+#pragma unroll
+    for (int h = 0; h < H; ++h)
+        for (int t = 0; t < C::NPROD; ++t) {
+            int ia, ib;
+            prod_pair(P, t, ia, ib);
+            const uint32_t abase = abase0 + ia * A_TILE, bbase = bbase0 + ib * B_TILE;
+#pragma unroll
+            for (int k2 = 0; k2 < 4 / H; ++k2) {
+                const int kk = h * (4 / H) + k2;
+                const uint32_t acc = (!first || h > 0 || t > 0 || k2 > 0) ? 1u : 0u;
+                mma<C::BF>(tmem, desc_sw128(abase + kk * 32), desc_sw128(bbase + kk * 32), ID, acc);
+            }
+        }
+}
+
 // N: output columns per tile (64, 128 or 256; chosen per model size by the autotuner).  The
 // squares are summed per 32-column chunk and paired into 64-column partials, the same grouping
 // for every N, so all tile widths give the same bits.
@@ -291,7 +316,6 @@ __global__ void __launch_bounds__(NTHR, 1) k_tc_sumsq(const __grid_constant__ CU
     const uint32_t tmem = tmem_slot;
     bool ok_all = true;
     const CUtensorMap *maps[3] = {&mapB0, &mapB1, &mapB2};
-    constexpr uint32_t ID = idesc<C::BF>(TM, N);
 
     for (int kb = 0; kb < nkb; ++kb) {
         const int s = kb & 1, use = kb >> 1;
@@ -311,16 +335,7 @@ __global__ void __launch_bounds__(NTHR, 1) k_tc_sumsq(const __grid_constant__ CU
         if (tid == 0) {
             if (!mbar_wait(bar_full0 + 8 * s, use & 1)) ok_all = false;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            for (int t = 0; t < C::NPROD; ++t) {
-                int ia, ib;
-                prod_pair(P, t, ia, ib);
-                const uint32_t abase = smem_u32(st + ia * A_TILE), bbase = smem_u32(st + C::NA * A_TILE + ib * B_TILE);
-#pragma unroll
-                for (int kk = 0; kk < 4; ++kk) {
-                    uint32_t acc = (kb > 0 || t > 0 || kk > 0) ? 1u : 0u;
-                    mma<C::BF>(tmem, desc_sw128(abase + kk * 32), desc_sw128(bbase + kk * 32), ID, acc);
-                }
-            }
+            issue_block128<P, N>(tmem, smem_u32(st), smem_u32(st + C::NA * A_TILE), kb == 0);
             mma_commit(bar_free0 + 8 * s);
             if (kb == nkb - 1) mma_commit(bar_done);
         }
@@ -438,7 +453,6 @@ __global__ void __launch_bounds__(WS_NTHR, 1) k_tc_sumsq_ws(const __grid_constan
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_slot;
     bool ok_all = true;
-    constexpr uint32_t ID = idesc<C::BF>(TM, N);
 
     if (warp == 0 && lane == 0) {
         const CUtensorMap *maps[3] = {&mapB0, &mapB1, &mapB2};
@@ -457,14 +471,209 @@ __global__ void __launch_bounds__(WS_NTHR, 1) k_tc_sumsq_ws(const __grid_constan
             if (!mbar_wait(fullB0 + 8 * s, use & 1)) ok_all = false;
             if (!mbar_wait(fullA0 + 8 * s, use & 1)) ok_all = false;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            issue_block128<P, N>(tmem, smem_u32(st), smem_u32(st + C::NA * A_TILE), kb == 0);
+            mma_commit(empty0 + 8 * s);
+            if (kb == nkb - 1) mma_commit(bar_done);
+        }
+    } else if (warp >= 2) {
+        const int at = tid - 64;  // 0 .. 255
+        for (int kb = 0; kb < nkb; ++kb) {
+            const int s = kb & 1, use = kb >> 1;
+            unsigned char *st = smem + s * STAGE;
+            if (kb >= 2 && !mbar_wait(empty0 + 8 * s, (use - 1) & 1)) ok_all = false;
+            for (int q = at; q < TM * 8; q += 256) gen_a_chunk<P>(prm, st, q >> 3, q & 7, kb, gx, gy, gz, rvalid);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> tensor-core reads
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(fullA0 + 8 * s) : "memory");
+        }
+        // epilogue: warp w reads TMEM lanes 32 (w % 4), column half (w - 2) / 4
+        if (!mbar_wait(bar_done, 0)) ok_all = false;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const int lq = warp & 3, half = (warp - 2) >> 2;
+#pragma unroll
+        for (int c0 = 0; c0 < N / 2; c0 += 32) {
+            uint32_t rr[32];
+            const uint32_t taddr = tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(half * (N / 2) + c0);
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,"
+                "%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                : "=r"(rr[0]), "=r"(rr[1]), "=r"(rr[2]), "=r"(rr[3]), "=r"(rr[4]), "=r"(rr[5]), "=r"(rr[6]), "=r"(rr[7]),
+                  "=r"(rr[8]), "=r"(rr[9]), "=r"(rr[10]), "=r"(rr[11]), "=r"(rr[12]), "=r"(rr[13]), "=r"(rr[14]),
+                  "=r"(rr[15]), "=r"(rr[16]), "=r"(rr[17]), "=r"(rr[18]), "=r"(rr[19]), "=r"(rr[20]), "=r"(rr[21]),
+                  "=r"(rr[22]), "=r"(rr[23]), "=r"(rr[24]), "=r"(rr[25]), "=r"(rr[26]), "=r"(rr[27]), "=r"(rr[28]),
+                  "=r"(rr[29]), "=r"(rr[30]), "=r"(rr[31])
+                : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            float sum = 0.f;
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+                float w = __uint_as_float(rr[i]);
+                sum = fmaf(w, w, sum);
+            }
+            red[(half * (N / 2) + c0) / 32][lq * 32 + lane] = sum;
+        }
+        asm volatile("bar.sync 1, 256;" ::: "memory");  // the epilogue warps only
+        if (at < TM && row0 + at < prm.count) {
+            const int64_t row = row0 + at;
+#pragma unroll
+            for (int q = 0; q < N / 64; ++q) {
+                const int64_t idx = row * prm.nN + n0 / 64 + q;
+                if (idx < prm.plen) prm.partial[idx] = red[2 * q][at] + red[2 * q + 1][at];
+                else atomicCAS(prm.status, 0, (int)GPR_ERR_ARG);  // self-check: never expected
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (!ok_all) atomicCAS(prm.status, 0, (int)GPR_ERR_TIMEOUT);
+    if (warp == 0) {
+        __syncwarp();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)N));
+    }
+}
+
+// K-major, 64-byte swizzle (8-row groups 512 B apart).
+__device__ __forceinline__ uint64_t desc_sw64(uint32_t addr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(512 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)4 << 61;  // 64-byte swizzle
+    return d;
+}
+
+// One 16-byte chunk c (of 4) of row r of a 64-byte-row A tile (16 TF32 elements per K block),
+// hi and lo slices, in the 64-byte-swizzled K-major layout (chunk c of row r at c ^ ((r >> 1) & 3)).
+template <int P>
+__device__ __forceinline__ void gen_a_chunk64(const TcParams &prm, unsigned char *st, int r, int c, int kb,
+                                              const int *gx, const int *gy, const int *gz, const bool *rvalid)
+{
+    using C = Cfg<P>;
+    constexpr int A_TILE = TM * 64;
+    const int64_t m = prm.m;
+    const int64_t k0 = (int64_t)kb * 16 + c * 4;
+    float v[4] = {0.f, 0.f, 0.f, 0.f};
+    if (rvalid[r]) {
+        const float *tx = prm.T32 + (int64_t)gx[r] * prm.mp, *ty = prm.T32 + prm.off1 + (int64_t)gy[r] * prm.mp,
+                    *tz = prm.T32 + prm.off2 + (int64_t)gz[r] * prm.mp;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            int64_t j = k0 + e;
+            if (j < m && prm.off2 + (int64_t)gz[r] * prm.mp + j >= prm.tlen) {
+                atomicCAS(prm.status, 0, (int)GPR_ERR_ARG);  // self-check: never expected
+            } else if (j < m) {
+                float a = tx[j], b = ty[j], cc = tz[j];
+                if (prm.kind == GPR_K_SE) {
+                    v[e] = a * b * cc;
+                } else {
+                    float r2 = a + b + cc, rr = sqrtf(r2), s5r = 2.23606797749979f * rr;
+                    v[e] = prm.sf2 * (1.0f + s5r + (5.0f / 3.0f) * r2) * __expf(-s5r);
+                }
+            }
+        }
+    }
+    const int off = r * 64 + ((c ^ ((r >> 1) & 3)) << 4);
+    float4 hi, lo;
+    float *h = &hi.x, *l = &lo.x;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        h[e] = tf32_round(v[e]);
+        l[e] = tf32_round(v[e] - h[e]);
+    }
+    *(float4 *)(st + off) = hi;
+    if (C::NA > 1) *(float4 *)(st + A_TILE + off) = lo;
+}
+
+// TF32 / TF32x3 variant with 64-byte rows (16-element K blocks): two 48 KB stages, so two CTAs
+// share an SM (2 x 256 TMEM columns) and one CTA's prologue, generation and drain overlap the
+// other's MMAs.  Warp roles as in k_tc_sumsq_ws; the MMA order (per 16-element block: product by
+// product over two K steps) and the epilogue grouping equal the other variants', so the bits do.
+template <int P>
+__global__ void __launch_bounds__(WS_NTHR, 2) k_tc_sumsq_2c(const __grid_constant__ CUtensorMap mapB0,
+                                                           const __grid_constant__ CUtensorMap mapB1, TcParams prm)
+{
+    using C = Cfg<P>;
+    static_assert(!C::BF, "64-byte rows: TF32 operands only");
+    constexpr int N = 256;
+    constexpr int A_TILE = TM * 64;
+    constexpr int B_TILE = N * 64;
+    constexpr int STAGE = C::NA * A_TILE + C::NB * B_TILE;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t *bars = (uint64_t *)(smem + 2 * STAGE);  // fullB[2], fullA[2], empty[2], done
+    __shared__ uint32_t tmem_slot;
+    __shared__ int gx[TM], gy[TM], gz[TM];
+    __shared__ bool rvalid[TM];
+    __shared__ float red[N / 32][TM];
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int64_t row0 = (int64_t)blockIdx.x * TM;
+    const int n0 = blockIdx.y * N;
+    const int64_t m = prm.m;
+    const int64_t kend = (int64_t)n0 + N < m ? (int64_t)n0 + N : m;
+    const int nkb = (int)((kend + 15) / 16);
+    const uint32_t fullB0 = smem_u32(&bars[0]), fullA0 = smem_u32(&bars[2]), empty0 = smem_u32(&bars[4]),
+                   bar_done = smem_u32(&bars[6]);
+    if (tid == 0) {
+        mbar_init(fullB0, 1);
+        mbar_init(fullB0 + 8, 1);
+        mbar_init(fullA0, 256);
+        mbar_init(fullA0 + 8, 256);
+        mbar_init(empty0, 1);
+        mbar_init(empty0 + 8, 1);
+        mbar_init(bar_done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                     "r"((uint32_t)N));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    for (int r = tid; r < TM; r += WS_NTHR) {
+        int64_t row = row0 + r;
+        bool ok = row < prm.count;
+        int64_t p = ok ? (prm.pts ? prm.pts[row] : prm.pt_base + row) : 0;
+        int64_t nx = prm.g.n[0], ny = prm.g.n[1];
+        if (p < 0 || p >= nx * ny * (int64_t)prm.g.n[2]) { ok = false; p = 0; }
+        gx[r] = (int)(p % nx);
+        gy[r] = (int)((p / nx) % ny);
+        gz[r] = (int)(p / (nx * ny));
+        rvalid[r] = ok;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_slot;
+    bool ok_all = true;
+    constexpr uint32_t ID = idesc<false>(TM, N);
+
+    if (warp == 0 && lane == 0) {
+        const CUtensorMap *maps[2] = {&mapB0, &mapB1};
+        for (int kb = 0; kb < nkb; ++kb) {
+            const int s = kb & 1, use = kb >> 1;
+            unsigned char *st = smem + s * STAGE;
+            if (kb >= 2 && !mbar_wait(empty0 + 8 * s, (use - 1) & 1)) ok_all = false;
+            mbar_expect_tx(fullB0 + 8 * s, (uint32_t)(C::NB * B_TILE));
+            for (int b = 0; b < C::NB; ++b)
+                tma_load_2d(smem_u32(st + C::NA * A_TILE + b * B_TILE), maps[b], kb * 16, n0, fullB0 + 8 * s);
+        }
+    } else if (warp == 1 && lane == 0) {
+        for (int kb = 0; kb < nkb; ++kb) {
+            const int s = kb & 1, use = kb >> 1;
+            unsigned char *st = smem + s * STAGE;
+            if (!mbar_wait(fullB0 + 8 * s, use & 1)) ok_all = false;
+            if (!mbar_wait(fullA0 + 8 * s, use & 1)) ok_all = false;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             for (int t = 0; t < C::NPROD; ++t) {
                 int ia, ib;
                 prod_pair(P, t, ia, ib);
                 const uint32_t abase = smem_u32(st + ia * A_TILE), bbase = smem_u32(st + C::NA * A_TILE + ib * B_TILE);
 #pragma unroll
-                for (int kk = 0; kk < 4; ++kk) {
-                    uint32_t acc = (kb > 0 || t > 0 || kk > 0) ? 1u : 0u;
-                    mma<C::BF>(tmem, desc_sw128(abase + kk * 32), desc_sw128(bbase + kk * 32), ID, acc);
+                for (int k2 = 0; k2 < 2; ++k2) {
+                    uint32_t acc = (kb > 0 || t > 0 || k2 > 0) ? 1u : 0u;
+                    mma<false>(tmem, desc_sw64(abase + k2 * 32), desc_sw64(bbase + k2 * 32), ID, acc);
                 }
             }
             mma_commit(empty0 + 8 * s);
@@ -476,7 +685,7 @@ __global__ void __launch_bounds__(WS_NTHR, 1) k_tc_sumsq_ws(const __grid_constan
             const int s = kb & 1, use = kb >> 1;
             unsigned char *st = smem + s * STAGE;
             if (kb >= 2 && !mbar_wait(empty0 + 8 * s, (use - 1) & 1)) ok_all = false;
-            for (int q = at; q < TM * 8; q += 256) gen_a_chunk<P>(prm, st, q >> 3, q & 7, kb, gx, gy, gz, rvalid);
+            for (int q = at; q < TM * 4; q += 256) gen_a_chunk64<P>(prm, st, q >> 2, q & 3, kb, gx, gy, gz, rvalid);
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> tensor-core reads
             asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(fullA0 + 8 * s) : "memory");
         }
@@ -584,6 +793,37 @@ bool make_map(CUtensorMap *map, void *base, int64_t mpt, bool bf, int N)
                      box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
+}
+
+bool make_map64(CUtensorMap *map, void *base, int64_t mpt)
+{
+    auto enc = get_encode();
+    if (!enc) return false;
+    cuuint64_t gdim[2] = {(cuuint64_t)mpt, (cuuint64_t)mpt};
+    cuuint64_t gstride[1] = {(cuuint64_t)mpt * 4};
+    cuuint32_t box[2] = {16, 256};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, gdim, gstride, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+template <int P>
+gpr_status launch_tc2c(const gpr_model *M, const TcParams &prm, cudaStream_t st)
+{
+    using C = Cfg<P>;
+    CUtensorMap maps[2];
+    const TcOperands &B = *M->tc;
+    if (!make_map64(&maps[0], B.thi, B.mpt) || !make_map64(&maps[1], B.tlo, B.mpt)) return GPR_ERR_UNSUPPORTED;
+    const size_t smem = 2 * ((size_t)C::NA * TM * 64 + (size_t)C::NB * 256 * 64) + 64 + 1024;
+    dim3 grid((unsigned)((prm.count + TM - 1) / TM), (unsigned)(B.mpt / 256));
+    GPR_CUDA_TRY(cudaFuncSetAttribute(k_tc_sumsq_2c<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    ProfScope ps("tc_sumsq", st, (double)prm.count);
+    k_tc_sumsq_2c<P><<<grid, WS_NTHR, smem, st>>>(maps[0], maps[1], prm);
+    note_launch();
+    GPR_CUDA_TRY(cudaGetLastError());
+    return GPR_OK;
 }
 
 template <int P, int N>
@@ -734,6 +974,7 @@ gpr_status launch_tc_var(const gpr_model *M, const GridDev &g, gpr_precision pre
     // alternatives (same bits): tile width N and the plain or warp-specialised kernel
     auto run = [&](int c) -> gpr_status {
         const bool wide = c & 1, ws = c >> 1;
+        if (c == 4) return prec == GPR_P_TF32 ? launch_tc2c<GPR_P_TF32>(M, prm, st) : launch_tc2c<GPR_P_TF32X3>(M, prm, st);
         switch (prec) {
         case GPR_P_TF32:
             return ws ? (wide ? launch_tc<GPR_P_TF32, 256, true>(M, prm, st) : launch_tc<GPR_P_TF32, 128, true>(M, prm, st))
@@ -762,7 +1003,9 @@ gpr_status launch_tc_var(const gpr_model *M, const GridDev &g, gpr_precision pre
     int lg = 0;
     while (((int64_t)1 << lg) < count && lg < 62) ++lg;
     if (W) GPR_TRY(run(1));  // rows out: the plain kernel (only it writes them), wide tiles
-    else GPR_TRY(tune_run(names[(int)prec], (tune_bucket(M->mp) << 6) | lg, 4, run, st));
+    else  // TF32 operands also have the two-CTAs-per-SM variant
+        GPR_TRY(tune_run(names[(int)prec], (tune_bucket(M->mp) << 6) | lg,
+                         prec == GPR_P_TF32 || prec == GPR_P_TF32X3 ? 5 : 4, run, st));
     k_tc_finalize<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(partial, prm.nN, count, M->kp.sf2, var);
     note_launch();
     GPR_CUDA_TRY(cudaGetLastError());

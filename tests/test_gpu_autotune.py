@@ -37,7 +37,8 @@ def test_tile_widths_give_same_bits(torch, g, prec, name):
     M = model_of(w)
     grid = g.make_grid(w.n)
     out = []
-    for c in (0, 1, 2, 3):  # tile widths x (plain, warp-specialised)
+    # tile widths x (plain, warp-specialised), and for TF32 operands the two-CTAs-per-SM variant
+    for c in ((0, 1, 2, 3, 4) if prec.startswith("TF32") else (0, 1, 2, 3)):
         _force(g, name, c)
         mean = torch.zeros(w.n ** 3, dtype=torch.float32, device="cuda")
         var = torch.zeros_like(mean)
