@@ -91,7 +91,6 @@ struct gpr_model {
     float *BT32 = nullptr;     // mp x mp FP32 copy
     float *vy32 = nullptr;     // mp
     float2 *alpha_ff = nullptr; // mp: alpha as float-float (hi, lo)
-    float *Linv32 = nullptr;   // mp x mp FP32 copy of L^-1 (lower), zero padded
     float *X32 = nullptr;      // m x 3 FP32 observation sites
     float *alpha32 = nullptr;  // mp FP32 alpha
     TcOperands *tc = nullptr;  // built on first tensor-core use
@@ -203,6 +202,12 @@ bool tc_precision(gpr_precision p);
 gpr_status tc_prepare(gpr_model *M, cudaStream_t st);
 void tc_release(gpr_model *M);
 size_t tc_partial_elems(gpr_precision p, const gpr_model *M, int64_t count);
+// TF32x3 whitened rows at arbitrary points (count x 3 FP64 coordinates), reduced to partial sums
+// of |w|^2 and, with grad, of w . L^-1 d_k k per coordinate: partial[(point * T + type) * nN + g],
+// T = 4 with grad (else 1), nN = (mp rounded up to 256) / 64 groups of 64 columns.
+size_t tc_eval_partial_elems(const gpr_model *M, int64_t count);
+gpr_status launch_tc_eval(gpr_model *M, const double *xyz, int64_t count, bool grad, float *partial,
+                          size_t partial_elems, cudaStream_t st);
 // W (nullable, count x mp): also write the whitened rows of this precision (plain kernel).
 gpr_status launch_tc_var(const gpr_model *M, const GridDev &g, gpr_precision prec, const float *T32,
                          const int64_t *pts, int64_t pt_base, int64_t count, float *partial, float *var, cudaStream_t st,

@@ -20,11 +20,10 @@
 
 namespace {
 
-constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
 constexpr int64_t kEvalChunk = 131072;  // evaluation points per pipeline pass
 
 struct EvalModel {
-    const float *X32, *BT32, *Linv32, *alpha32;
+    const float *X32, *alpha32;
     int64_t m, mp;
     int kind;
     float ell[3];
@@ -32,129 +31,20 @@ struct EvalModel {
     float sf2;
 };
 
-__device__ __forceinline__ float kdirect(const EvalModel &E, float x, float y, float z, int64_t j)
-{
-    float a = (x - E.X32[3 * j]) * E.iell[0], b = (y - E.X32[3 * j + 1]) * E.iell[1],
-          c = (z - E.X32[3 * j + 2]) * E.iell[2];
-    float r2 = a * a + b * b + c * c;
-    if (E.kind == GPR_K_SE) return E.sf2 * __expf(-0.5f * r2);
-    float r = sqrtf(r2), s5r = 2.23606797749979f * r;
-    return E.sf2 * (1.0f + s5r + (5.0f / 3.0f) * r2) * __expf(-s5r);
-}
-
-// W rows (FP32) of arbitrary evaluation points: W = K(x, X) L^-T.
-__global__ void __launch_bounds__(NT) k_eval_w(EvalModel E, const double *xyz, int64_t count, float *W)
-{
-    __shared__ float As[BK][BM + 4], Bs[BK][BN + 4];
-    __shared__ float px[BM], py[BM], pz[BM];
-    __shared__ bool valid[BM];
-    int64_t row0 = (int64_t)blockIdx.y * BM, j0 = (int64_t)blockIdx.x * BN;
-    for (int r = threadIdx.x; r < BM; r += NT) {
-        int64_t row = row0 + r;
-        bool ok = row < count;
-        valid[r] = ok;
-        px[r] = ok ? (float)xyz[3 * row] : 0.f;
-        py[r] = ok ? (float)xyz[3 * row + 1] : 0.f;
-        pz[r] = ok ? (float)xyz[3 * row + 2] : 0.f;
-    }
-    __syncthreads();
-    int t = threadIdx.x, tx = t % 16, ty = t / 16;
-    float acc[4][4] = {};
-    int64_t kend = j0 + BN < E.m ? j0 + BN : E.m;
-    for (int64_t k0 = 0; k0 < kend; k0 += BK) {
-#pragma unroll
-        for (int e = 0; e < (BM * BK) / NT; ++e) {
-            int idx = t + NT * e, r = idx % BM, kk = idx / BM;
-            int64_t j = k0 + kk;
-            As[kk][r] = (j < E.m && valid[r]) ? kdirect(E, px[r], py[r], pz[r], j) : 0.f;
-        }
-#pragma unroll
-        for (int e = 0; e < (BK * BN) / NT; ++e) {
-            int idx = t + NT * e, kk = idx / BN, c = idx % BN;
-            Bs[kk][c] = E.BT32[(k0 + kk) * E.mp + j0 + c];
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < BK; ++kk) {
-            float a[4], b[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
-#pragma unroll
-            for (int c = 0; c < 4; ++c) b[c] = Bs[kk][tx * 4 + c];
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int c = 0; c < 4; ++c) acc[i][c] = fmaf(a[i], b[c], acc[i][c]);
-        }
-        __syncthreads();
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        int64_t row = row0 + ty * 4 + i;
-        if (row >= count) continue;
-#pragma unroll
-        for (int c = 0; c < 4; ++c) W[row * E.mp + j0 + tx * 4 + c] = acc[i][c];
-    }
-}
-
-// P rows = W L^-1, i.e. P = Kt^-1 k (P_i = sum_{j >= i} w_j [L^-1]_{ji}); feeds grad sigma^2.
-__global__ void __launch_bounds__(NT) k_eval_p(EvalModel E, const float *W, int64_t count, float *P)
-{
-    __shared__ float As[BK][BM + 4], Bs[BK][BN + 4];
-    int64_t row0 = (int64_t)blockIdx.y * BM, i0 = (int64_t)blockIdx.x * BN;
-    int t = threadIdx.x, tx = t % 16, ty = t / 16;
-    float acc[4][4] = {};
-    for (int64_t k0 = i0; k0 < E.m; k0 += BK) {
-#pragma unroll
-        for (int e = 0; e < (BM * BK) / NT; ++e) {
-            int idx = t + NT * e, r = idx % BM, kk = idx / BM;
-            int64_t row = row0 + r;
-            As[kk][r] = row < count ? W[row * E.mp + k0 + kk] : 0.f;
-        }
-#pragma unroll
-        for (int e = 0; e < (BK * BN) / NT; ++e) {
-            int idx = t + NT * e, kk = idx / BN, c = idx % BN;
-            Bs[kk][c] = E.Linv32[(k0 + kk) * E.mp + i0 + c];
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < BK; ++kk) {
-            float a[4], b[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
-#pragma unroll
-            for (int c = 0; c < 4; ++c) b[c] = Bs[kk][tx * 4 + c];
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int c = 0; c < 4; ++c) acc[i][c] = fmaf(a[i], b[c], acc[i][c]);
-        }
-        __syncthreads();
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        int64_t row = row0 + ty * 4 + i;
-        if (row >= count) continue;
-#pragma unroll
-        for (int c = 0; c < 4; ++c) P[row * E.mp + i0 + tx * 4 + c] = acc[i][c];
-    }
-}
-
-// g = (theta - mu)/sigma and grad g at each evaluation point (warp per point).
-// grad mu = sum_j dk_j alpha_j, grad sigma^2 = -2 sum_j dk_j P_j.
-__global__ void k_eval_reduce(EvalModel E, const double *xyz, const float *W, const float *P, int64_t count,
+// g = (theta - mu)/sigma and grad g at each evaluation point (warp per point).  mu and grad mu =
+// sum_j dk_j alpha_j here (compensated mu); |w|^2 and, with grad, w . L^-1 d_k k come as partial
+// sums over 64-column groups from the tensor-core evaluation: var = sf2 - |w|^2,
+// grad var = -2 w . L^-1 d_k k.
+__global__ void k_eval_reduce(EvalModel E, const double *xyz, const float *partial, int nN, bool grad, int64_t count,
                               double theta, float4 *out)
 {
     int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     int64_t q = blockIdx.x * (int64_t)(blockDim.x / 32) + warp;
     if (q >= count) return;
     float x = (float)xyz[3 * q], y = (float)xyz[3 * q + 1], z = (float)xyz[3 * q + 2];
-    float wsq = 0.f, mu_h = 0.f, mu_l = 0.f, gm[3] = {0, 0, 0}, gv[3] = {0, 0, 0};
-    const float *wr = W + q * E.mp, *pr = P ? P + q * E.mp : nullptr;  // no P: value only (gradient of mu)
+    float mu_h = 0.f, mu_l = 0.f, gm[3] = {0, 0, 0};
     float il2[3] = {1.f / (E.ell[0] * E.ell[0]), 1.f / (E.ell[1] * E.ell[1]), 1.f / (E.ell[2] * E.ell[2])};
     for (int64_t j = lane; j < E.m; j += 32) {
-        float w = wr[j];
-        wsq = fmaf(w, w, wsq);
         float d0 = x - E.X32[3 * j], d1 = y - E.X32[3 * j + 1], d2 = z - E.X32[3 * j + 2];
         float r2 = d0 * d0 * il2[0] + d1 * d1 * il2[1] + d2 * d2 * il2[2];
         float k, c;
@@ -166,31 +56,31 @@ __global__ void k_eval_reduce(EvalModel E, const double *xyz, const float *W, co
             k = E.sf2 * (1.0f + s5r + (5.0f / 3.0f) * r2) * e;
             c = -(5.0f / 3.0f) * E.sf2 * (1.0f + s5r) * e;
         }
-        float a = E.alpha32[j], pj = pr ? pr[j] : 0.f;
+        float a = E.alpha32[j];
         // compensated accumulation of mu (terms k*alpha reach ~1e3 for an O(1) result)
         float term = k * a, s = mu_h + term, bv = s - mu_h;
         mu_l += (mu_h - (s - bv)) + (term - bv);
         mu_h = s;
         float dd[3] = {d0, d1, d2};
 #pragma unroll
-        for (int dI = 0; dI < 3; ++dI) {
-            float dk = c * dd[dI] * il2[dI];
-            gm[dI] = fmaf(dk, a, gm[dI]);
-            gv[dI] = fmaf(-2.f * dk, pj, gv[dI]);
-        }
+        for (int dI = 0; dI < 3; ++dI) gm[dI] = fmaf(c * dd[dI] * il2[dI], a, gm[dI]);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        wsq += __shfl_xor_sync(0xffffffffu, wsq, o);
         mu_h += __shfl_xor_sync(0xffffffffu, mu_h, o);
         mu_l += __shfl_xor_sync(0xffffffffu, mu_l, o);
 #pragma unroll
-        for (int dI = 0; dI < 3; ++dI) {
-            gm[dI] += __shfl_xor_sync(0xffffffffu, gm[dI], o);
-            gv[dI] += __shfl_xor_sync(0xffffffffu, gv[dI], o);
-        }
+        for (int dI = 0; dI < 3; ++dI) gm[dI] += __shfl_xor_sync(0xffffffffu, gm[dI], o);
     }
     if (lane == 0) {
+        const int T = grad ? 4 : 1;
+        float wsq = 0.f, gv[3] = {0.f, 0.f, 0.f};
+        for (int g2 = 0; g2 < nN; ++g2) {
+            wsq += partial[(q * T) * nN + g2];
+            if (grad)
+                for (int dI = 0; dI < 3; ++dI) gv[dI] += partial[(q * T + 1 + dI) * nN + g2];
+        }
+        for (int dI = 0; dI < 3; ++dI) gv[dI] *= -2.f;
         float var = E.sf2 - wsq;
         float fl = 1e-12f * E.sf2;
         if (!(var > fl)) var = fl;
@@ -1244,7 +1134,8 @@ struct OctBuffers {
     int64_t *plist, *pend;
     float *tmp_mean, *tmp_var;
     double *xyz;
-    float *W, *P;
+    float *W;     // partial sums of the tensor-core evaluations
+    size_t wlen;  // floats in W
     float4 *ev, *lat;
     float *part;
     uint8_t *unal;
@@ -1275,20 +1166,15 @@ struct OctTrace {
     uint8_t *leaf_out;
 };
 
-static gpr_status run_eval(const gpr_model *M, const EvalModel &E, OctBuffers &B, int64_t cnt, double theta,
+static gpr_status run_eval(gpr_model *M, const EvalModel &E, OctBuffers &B, int64_t cnt, double theta,
                            cudaStream_t st, bool grad = true)
 {
-    dim3 grid((unsigned)(M->mp / BN), nb(cnt, BM));
     {
         ProfScope ps("oct_eval_w", st);
-        k_eval_w<<<grid, NT, 0, st>>>(E, B.xyz, cnt, B.W);
+        GPR_TRY(launch_tc_eval(M, B.xyz, cnt, grad, B.W, B.wlen, st));
     }
-    note_launch();
-    if (grad) {
-        k_eval_p<<<grid, NT, 0, st>>>(E, B.W, cnt, B.P);
-        note_launch();
-    }
-    k_eval_reduce<<<nb(cnt, 8), 256, 0, st>>>(E, B.xyz, B.W, grad ? B.P : nullptr, cnt, theta, B.ev);
+    const int nN = (int)(((M->mp + 255) / 256 * 256) / 64);
+    k_eval_reduce<<<nb(cnt, 8), 256, 0, st>>>(E, B.xyz, B.W, nN, grad, cnt, theta, B.ev);
     note_launch();
     GPR_CUDA_TRY(cudaGetLastError());
     return GPR_OK;
@@ -1477,7 +1363,7 @@ gpr_status octree_lcp(gpr_model *M, const gpr_grid *grid, double theta, int D, c
                    Carver::round((size_t)nc * 8) + Carver::round((size_t)m) + 3 * Carver::round((size_t)n) +
                    Carver::round((size_t)nc) + Carver::round((size_t)nc) + Carver::round((size_t)n * 16) +
                    Carver::round((size_t)nc * 8) + 2 * Carver::round((size_t)n * 4) +
-                   Carver::round((size_t)kEvalChunk * 24) + 2 * Carver::round((size_t)kEvalChunk * M->mp * 4) +
+                   Carver::round((size_t)kEvalChunk * 24) + Carver::round(tc_eval_partial_elems(M, kEvalChunk) * 4) +
                    Carver::round((size_t)kEvalChunk * 16) + Carver::round((size_t)kEvalChunk) +
                    Carver::round((size_t)nc * sizeof(MinState)) + Carver::round((size_t)max_large * 27 * 16) + 512 +
                    csb + Carver::round(tc_partial_elems(GPR_P_BF16X3, M, n) * 4) + Carver::round((size_t)max_large * 2) +
@@ -1520,8 +1406,8 @@ gpr_status octree_lcp(gpr_model *M, const gpr_grid *grid, double theta, int D, c
     B.tmp_mean = cv.take<float>((size_t)n);
     B.tmp_var = cv.take<float>((size_t)n);
     B.xyz = cv.take<double>((size_t)kEvalChunk * 3);
-    B.W = cv.take<float>((size_t)kEvalChunk * M->mp);
-    B.P = cv.take<float>((size_t)kEvalChunk * M->mp);
+    B.wlen = tc_eval_partial_elems(M, kEvalChunk);
+    B.W = cv.take<float>(B.wlen);
     B.ev = cv.take<float4>((size_t)kEvalChunk);
     B.lat = cv.take<float4>((size_t)max_large * 27);
     B.cvalid = cv.take<uint8_t>((size_t)kEvalChunk);
@@ -1541,7 +1427,7 @@ gpr_status octree_lcp(gpr_model *M, const gpr_grid *grid, double theta, int D, c
     int64_t *clist = B.pend;                 // reused by the leaf phase (nc int64)
 
     EvalModel E;
-    E.X32 = M->X32; E.BT32 = M->BT32; E.Linv32 = M->Linv32; E.alpha32 = M->alpha32;
+    E.X32 = M->X32; E.alpha32 = M->alpha32;
     E.m = M->m; E.mp = M->mp; E.kind = M->kp.kind; E.sf2 = (float)M->kp.sf2;
     for (int d = 0; d < 3; ++d) {
         E.ell[d] = (float)M->kp.ell[d];

@@ -213,7 +213,7 @@ __global__ void k_alpha_obs(const double *Linv, int64_t mb, const double *vy, co
 
 // BT[i][j] = Linv[j][i] for i <= j < m, else 0  (mp x mp), FP64 and FP32.
 __global__ void k_operands(const double *Linv, int64_t mb, int64_t m, int64_t mp, double *BT64, float *BT32,
-                           const double *vy, float *vy32, const double *alpha, float2 *alpha_ff, float *Linv32,
+                           const double *vy, float *vy32, const double *alpha, float2 *alpha_ff,
                            const double *X, float *X32, float *alpha32)
 {
     int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -230,7 +230,6 @@ __global__ void k_operands(const double *Linv, int64_t mb, int64_t m, int64_t mp
     double v = (i < m && j < m && i <= j) ? Linv[j * mb + i] : 0.0;
     BT64[idx] = v;
     BT32[idx] = (float)v;
-    Linv32[idx] = (i < m && j < m && j <= i) ? (float)Linv[i * mb + j] : 0.0f;
 }
 
 // Compact the padded mb x mb factor into m x m.
@@ -330,7 +329,6 @@ extern "C" gpr_status gpr_model_create(const double *obs_xyz, const double *y, i
     ALLOC(M->BT32, sizeof(float) * mp * mp);
     ALLOC(M->vy32, sizeof(float) * mp);
     ALLOC(M->alpha_ff, sizeof(float2) * mp);
-    ALLOC(M->Linv32, sizeof(float) * mp * mp);
     ALLOC(M->X32, sizeof(float) * 3 * m);
     ALLOC(M->alpha32, sizeof(float) * mp);
     ALLOC(A, sizeof(double) * mb * mb);
@@ -349,7 +347,7 @@ extern "C" gpr_status gpr_model_create(const double *obs_xyz, const double *y, i
     k_alpha_obs<<<nblk(m, 128), 128, 0, st>>>(M->Linv, mb, M->vy, M->y, m, noise_var, signal_var, M->alpha,
                                                M->mu_obs, M->var_obs);
     note_launch();
-    k_operands<<<nblk(mp * mp, 256), 256, 0, st>>>(M->Linv, mb, m, mp, M->BT64, M->BT32, M->vy, M->vy32, M->alpha, M->alpha_ff, M->Linv32, M->X, M->X32, M->alpha32);
+    k_operands<<<nblk(mp * mp, 256), 256, 0, st>>>(M->Linv, mb, m, mp, M->BT64, M->BT32, M->vy, M->vy32, M->alpha, M->alpha_ff, M->X, M->X32, M->alpha32);
     note_launch();
     k_unpad<<<nblk(m * m, 256), 256, 0, st>>>(A, mb, m, M->L);
     note_launch();
@@ -529,7 +527,6 @@ extern "C" gpr_status gpr_model_create_sgpr(const double *inducing_xyz, const do
     ALLOC(M->BT32, sizeof(float) * mp * mp);
     ALLOC(M->vy32, sizeof(float) * mp);
     ALLOC(M->alpha_ff, sizeof(float2) * mp);
-    ALLOC(M->Linv32, sizeof(float) * mp * mp);
     ALLOC(M->X32, sizeof(float) * 3 * m);
     ALLOC(M->alpha32, sizeof(float) * mp);
     ALLOC(A, sq);
@@ -582,7 +579,7 @@ extern "C" gpr_status gpr_model_create_sgpr(const double *inducing_xyz, const do
     k_sgpr_obs<<<nblk(m, 128), 128, 0, st>>>(M->y, AMd, m, mb, signal_var, M->mu_obs, M->var_obs);
     note_launch();
     k_operands<<<nblk(mp * mp, 256), 256, 0, st>>>(M->Linv, mb, m, mp, M->BT64, M->BT32, M->vy, M->vy32, M->alpha,
-                                                   M->alpha_ff, M->Linv32, M->X, M->X32, M->alpha32);
+                                                   M->alpha_ff, M->X, M->X32, M->alpha32);
     note_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) { gpr_internal_note_cuda_error(e, "sgpr setup launch", __LINE__); return fail(GPR_ERR_CUDA); }
@@ -605,7 +602,7 @@ extern "C" gpr_status gpr_model_destroy(gpr_model *M)
     if (!M) return GPR_ERR_ARG;
     cudaDeviceSynchronize();
     cudaFree(M->X); cudaFree(M->y); cudaFree(M->L); cudaFree(M->Linv); cudaFree(M->vy); cudaFree(M->alpha);
-    cudaFree(M->mu_obs); cudaFree(M->var_obs); cudaFree(M->A_M); cudaFree(M->BT64); cudaFree(M->BT32); cudaFree(M->vy32); cudaFree(M->alpha_ff); cudaFree(M->Linv32); cudaFree(M->X32); cudaFree(M->alpha32);
+    cudaFree(M->mu_obs); cudaFree(M->var_obs); cudaFree(M->A_M); cudaFree(M->BT64); cudaFree(M->BT32); cudaFree(M->vy32); cudaFree(M->alpha_ff); cudaFree(M->X32); cudaFree(M->alpha32);
     for (int w = 0; w < 2; ++w)
         if (M->own_ws.ptr[w]) cudaFree(M->own_ws.ptr[w]);
     tc_release(M);

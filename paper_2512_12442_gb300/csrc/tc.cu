@@ -736,6 +736,234 @@ __global__ void __launch_bounds__(WS_NTHR, 2) k_tc_sumsq_2c(const __grid_constan
     }
 }
 
+// ---- Evaluations at arbitrary points (the octree bound's minimiser): TF32x3 whitened rows of
+// the kernel vector and, with GRAD, of its three coordinate derivatives, reduced on the fly to
+// |w|^2 and w . (L^-1 d_k k): var = sf2 - |w|^2, grad var_d = -2 w . (L^-1 d_k k).
+
+struct TcEvalParams {
+    const double *xyz;  // count x 3 evaluation points
+    int64_t count;
+    const float *X32;   // m x 3 observation sites
+    int64_t m, mp;
+    int kind;
+    float sf2;
+    float iell[3], il2[3];
+    float *partial;     // (count x T) x nN partial sums, T = 4 with GRAD (|w|^2, w . dw_x, dw_y, dw_z), else 1
+    int nN;
+    int64_t plen;
+    int *status;
+};
+
+// Chunk c (4 elements) of row r: with GRAD, rows 32t .. 32t + 31 hold row type t (0: k(x, X_j),
+// 1..3: d k / d x_{t-1}) of the CTA's 32 points; without, row r is point r's kernel row.
+template <bool GRAD>
+__device__ __forceinline__ void gen_eval_chunk64(const TcEvalParams &prm, unsigned char *st, int r, int c, int kb,
+                                                 const float *px, const float *py, const float *pz, const bool *rvalid)
+{
+    constexpr int A_TILE = TM * 64;
+    const int type = GRAD ? r >> 5 : 0, pr = GRAD ? (r & 31) : r;
+    const int64_t k0 = (int64_t)kb * 16 + c * 4;
+    float v[4] = {0.f, 0.f, 0.f, 0.f};
+    if (rvalid[pr]) {
+        const float x = px[pr], y = py[pr], z = pz[pr];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int64_t j = k0 + e;
+            if (j >= prm.m) continue;
+            const float d0 = x - prm.X32[3 * j], d1 = y - prm.X32[3 * j + 1], d2 = z - prm.X32[3 * j + 2];
+            const float a = d0 * prm.iell[0], b = d1 * prm.iell[1], cc = d2 * prm.iell[2];
+            const float r2 = a * a + b * b + cc * cc;
+            float k, cf;
+            if (prm.kind == GPR_K_SE) {
+                k = prm.sf2 * __expf(-0.5f * r2);
+                cf = -k;
+            } else {
+                const float rr = sqrtf(r2), s5r = 2.23606797749979f * rr, ex = __expf(-s5r);
+                k = prm.sf2 * (1.0f + s5r + (5.0f / 3.0f) * r2) * ex;
+                cf = -(5.0f / 3.0f) * prm.sf2 * (1.0f + s5r) * ex;
+            }
+            if (type == 0) v[e] = k;
+            else {
+                const float dd = type == 1 ? d0 : (type == 2 ? d1 : d2);
+                const float il = type == 1 ? prm.il2[0] : (type == 2 ? prm.il2[1] : prm.il2[2]);
+                v[e] = cf * dd * il;
+            }
+        }
+    }
+    const int off = r * 64 + ((c ^ ((r >> 1) & 3)) << 4);
+    float4 hi, lo;
+    float *h = &hi.x, *l = &lo.x;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        h[e] = tf32_round(v[e]);
+        l[e] = tf32_round(v[e] - h[e]);
+    }
+    *(float4 *)(st + off) = hi;
+    *(float4 *)(st + A_TILE + off) = lo;
+}
+
+// The pipeline of k_tc_sumsq_2c (TMA warp, MMA warp, 8 generating and draining warps; two CTAs
+// per SM) on the evaluation rows.  GRAD: the drain pairs each derivative row with its point's
+// kernel row through shared memory, chunk by chunk.
+template <bool GRAD>
+__global__ void __launch_bounds__(WS_NTHR, 2) k_tc_eval(const __grid_constant__ CUtensorMap mapB0,
+                                                       const __grid_constant__ CUtensorMap mapB1, TcEvalParams prm)
+{
+    constexpr int P = GPR_P_TF32X3;
+    using C = Cfg<P>;
+    constexpr int N = 256;
+    constexpr int A_TILE = TM * 64;
+    constexpr int B_TILE = N * 64;
+    constexpr int STAGE = C::NA * A_TILE + C::NB * B_TILE;
+    constexpr int PTS = GRAD ? 32 : TM;  // points per CTA
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t *bars = (uint64_t *)(smem + 2 * STAGE);  // fullB[2], fullA[2], empty[2], done
+    __shared__ uint32_t tmem_slot;
+    __shared__ float px[PTS], py[PTS], pz[PTS];
+    __shared__ bool rvalid[PTS];
+    __shared__ float red[N / 32][TM];
+    __shared__ float wbuf[GRAD ? 2 : 1][32][32];  // [column half][column][point]: kernel-row chunk
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int64_t pt0 = (int64_t)blockIdx.x * PTS;
+    const int n0 = blockIdx.y * N;
+    const int64_t m = prm.m;
+    const int64_t kend = (int64_t)n0 + N < m ? (int64_t)n0 + N : m;
+    const int nkb = (int)((kend + 15) / 16);
+    const uint32_t fullB0 = smem_u32(&bars[0]), fullA0 = smem_u32(&bars[2]), empty0 = smem_u32(&bars[4]),
+                   bar_done = smem_u32(&bars[6]);
+    if (tid == 0) {
+        mbar_init(fullB0, 1);
+        mbar_init(fullB0 + 8, 1);
+        mbar_init(fullA0, 256);
+        mbar_init(fullA0 + 8, 256);
+        mbar_init(empty0, 1);
+        mbar_init(empty0 + 8, 1);
+        mbar_init(bar_done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                     "r"((uint32_t)N));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    for (int r = tid; r < PTS; r += WS_NTHR) {
+        const int64_t q = pt0 + r;
+        const bool ok = q < prm.count;
+        rvalid[r] = ok;
+        px[r] = ok ? (float)prm.xyz[3 * q] : 0.f;
+        py[r] = ok ? (float)prm.xyz[3 * q + 1] : 0.f;
+        pz[r] = ok ? (float)prm.xyz[3 * q + 2] : 0.f;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_slot;
+    bool ok_all = true;
+    constexpr uint32_t ID = idesc<false>(TM, N);
+
+    if (warp == 0 && lane == 0) {
+        const CUtensorMap *maps[2] = {&mapB0, &mapB1};
+        for (int kb = 0; kb < nkb; ++kb) {
+            const int s = kb & 1, use = kb >> 1;
+            unsigned char *st = smem + s * STAGE;
+            if (kb >= 2 && !mbar_wait(empty0 + 8 * s, (use - 1) & 1)) ok_all = false;
+            mbar_expect_tx(fullB0 + 8 * s, (uint32_t)(C::NB * B_TILE));
+            for (int b = 0; b < C::NB; ++b)
+                tma_load_2d(smem_u32(st + C::NA * A_TILE + b * B_TILE), maps[b], kb * 16, n0, fullB0 + 8 * s);
+        }
+    } else if (warp == 1 && lane == 0) {
+        for (int kb = 0; kb < nkb; ++kb) {
+            const int s = kb & 1, use = kb >> 1;
+            unsigned char *st = smem + s * STAGE;
+            if (!mbar_wait(fullB0 + 8 * s, use & 1)) ok_all = false;
+            if (!mbar_wait(fullA0 + 8 * s, use & 1)) ok_all = false;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            for (int t = 0; t < C::NPROD; ++t) {
+                int ia, ib;
+                prod_pair(P, t, ia, ib);
+                const uint32_t abase = smem_u32(st + ia * A_TILE), bbase = smem_u32(st + C::NA * A_TILE + ib * B_TILE);
+#pragma unroll
+                for (int k2 = 0; k2 < 2; ++k2) {
+                    uint32_t acc = (kb > 0 || t > 0 || k2 > 0) ? 1u : 0u;
+                    mma<false>(tmem, desc_sw64(abase + k2 * 32), desc_sw64(bbase + k2 * 32), ID, acc);
+                }
+            }
+            mma_commit(empty0 + 8 * s);
+            if (kb == nkb - 1) mma_commit(bar_done);
+        }
+    } else if (warp >= 2) {
+        const int at = tid - 64;  // 0 .. 255
+        for (int kb = 0; kb < nkb; ++kb) {
+            const int s = kb & 1, use = kb >> 1;
+            unsigned char *st = smem + s * STAGE;
+            if (kb >= 2 && !mbar_wait(empty0 + 8 * s, (use - 1) & 1)) ok_all = false;
+            for (int q = at; q < TM * 4; q += 256) gen_eval_chunk64<GRAD>(prm, st, q >> 2, q & 3, kb, px, py, pz, rvalid);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> tensor-core reads
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(fullA0 + 8 * s) : "memory");
+        }
+        if (!mbar_wait(bar_done, 0)) ok_all = false;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const int lq = warp & 3, half = (warp - 2) >> 2;
+#pragma unroll
+        for (int c0 = 0; c0 < N / 2; c0 += 32) {
+            uint32_t rr[32];
+            const uint32_t taddr = tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(half * (N / 2) + c0);
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,"
+                "%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                : "=r"(rr[0]), "=r"(rr[1]), "=r"(rr[2]), "=r"(rr[3]), "=r"(rr[4]), "=r"(rr[5]), "=r"(rr[6]), "=r"(rr[7]),
+                  "=r"(rr[8]), "=r"(rr[9]), "=r"(rr[10]), "=r"(rr[11]), "=r"(rr[12]), "=r"(rr[13]), "=r"(rr[14]),
+                  "=r"(rr[15]), "=r"(rr[16]), "=r"(rr[17]), "=r"(rr[18]), "=r"(rr[19]), "=r"(rr[20]), "=r"(rr[21]),
+                  "=r"(rr[22]), "=r"(rr[23]), "=r"(rr[24]), "=r"(rr[25]), "=r"(rr[26]), "=r"(rr[27]), "=r"(rr[28]),
+                  "=r"(rr[29]), "=r"(rr[30]), "=r"(rr[31])
+                : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            float sum = 0.f;
+            if (!GRAD || lq == 0) {
+#pragma unroll
+                for (int i = 0; i < 32; ++i) {
+                    const float w = __uint_as_float(rr[i]);
+                    sum = fmaf(w, w, sum);
+                }
+            }
+            if (GRAD) {
+                if (lq == 0)
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) wbuf[GRAD ? half : 0][i][lane] = __uint_as_float(rr[i]);
+                asm volatile("bar.sync 1, 256;" ::: "memory");
+                if (lq != 0)
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) sum = fmaf(__uint_as_float(rr[i]), wbuf[GRAD ? half : 0][i][lane], sum);
+                asm volatile("bar.sync 1, 256;" ::: "memory");
+            }
+            red[(half * (N / 2) + c0) / 32][lq * 32 + lane] = sum;
+        }
+        asm volatile("bar.sync 1, 256;" ::: "memory");  // the epilogue warps only
+        if (at < TM) {
+            const int type = GRAD ? at >> 5 : 0, pr = GRAD ? (at & 31) : at;
+            const int64_t q = pt0 + pr;
+            if (q < prm.count) {
+#pragma unroll
+                for (int g2 = 0; g2 < N / 64; ++g2) {
+                    const int64_t idx = (q * (GRAD ? 4 : 1) + type) * prm.nN + n0 / 64 + g2;
+                    if (idx < prm.plen) prm.partial[idx] = red[2 * g2][at] + red[2 * g2 + 1][at];
+                    else atomicCAS(prm.status, 0, (int)GPR_ERR_ARG);  // self-check: never expected
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (!ok_all) atomicCAS(prm.status, 0, (int)GPR_ERR_TIMEOUT);
+    if (warp == 0) {
+        __syncwarp();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)N));
+    }
+}
+
 __global__ void k_tc_finalize(const float *partial, int nN, int64_t count, double sf2, float *var)
 {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -945,6 +1173,54 @@ size_t tc_partial_elems(gpr_precision p, const gpr_model *M, int64_t count)
 }
 
 // var of the listed points by the tensor-core contraction; `partial` holds tc_partial_elems floats.
+size_t tc_eval_partial_elems(const gpr_model *M, int64_t count)
+{
+    const int64_t mpt = (M->mp + 255) / 256 * 256;
+    return (size_t)count * 4 * (size_t)(mpt / 64);
+}
+
+gpr_status launch_tc_eval(gpr_model *M, const double *xyz, int64_t count, bool grad, float *partial,
+                          size_t partial_elems, cudaStream_t st)
+{
+    if (count <= 0) return GPR_OK;
+    GPR_TRY(tc_prepare(M, st));
+    const TcOperands &B = *M->tc;
+    CUtensorMap maps[2];
+    if (!make_map64(&maps[0], B.thi, B.mpt) || !make_map64(&maps[1], B.tlo, B.mpt)) return GPR_ERR_UNSUPPORTED;
+    TcEvalParams prm;
+    prm.xyz = xyz;
+    prm.count = count;
+    prm.X32 = M->X32;
+    prm.m = M->m;
+    prm.mp = M->mp;
+    prm.kind = M->kp.kind;
+    prm.sf2 = (float)M->kp.sf2;
+    for (int d = 0; d < 3; ++d) {
+        prm.iell[d] = (float)(1.0 / M->kp.ell[d]);
+        prm.il2[d] = (float)(1.0 / (M->kp.ell[d] * M->kp.ell[d]));
+    }
+    prm.partial = partial;
+    prm.nN = (int)(B.mpt / 64);
+    prm.plen = (int64_t)partial_elems;
+    if ((size_t)count * (grad ? 4 : 1) * (size_t)prm.nN > partial_elems) return GPR_ERR_ARG;
+    prm.status = gpr_status_word();
+    if (!prm.status) return GPR_ERR_CUDA;
+    using C = Cfg<GPR_P_TF32X3>;
+    const size_t smem = 2 * ((size_t)C::NA * TM * 64 + (size_t)C::NB * 256 * 64) + 64 + 1024;
+    const int pts = grad ? 32 : TM;
+    dim3 grid((unsigned)((count + pts - 1) / pts), (unsigned)(B.mpt / 256));
+    if (grad) {
+        GPR_CUDA_TRY(cudaFuncSetAttribute(k_tc_eval<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_tc_eval<true><<<grid, WS_NTHR, smem, st>>>(maps[0], maps[1], prm);
+    } else {
+        GPR_CUDA_TRY(cudaFuncSetAttribute(k_tc_eval<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_tc_eval<false><<<grid, WS_NTHR, smem, st>>>(maps[0], maps[1], prm);
+    }
+    note_launch();
+    GPR_CUDA_TRY(cudaGetLastError());
+    return GPR_OK;
+}
+
 gpr_status launch_tc_var(const gpr_model *M, const GridDev &g, gpr_precision prec, const float *T32,
                          const int64_t *pts, int64_t pt_base, int64_t count, float *partial, float *var, cudaStream_t st,
                          float *W)
