@@ -34,7 +34,7 @@ import workloads  # noqa: E402
 METRIC = "LCP grid points/s"
 # Warp instructions k_sov issues per orthant-sample (one lattice point of one orthant,
 # P(all < theta) or P(all > theta)): ncu's smsp__inst_executed.sum of the tuned launch shape on the
-# 64^3 case (3,152,591,626) over the orthant-samples the device counted for it (138,575 orthants x
+# 64^3 case (2,857,493,008) over the orthant-samples the device counted for it (138,569 orthants x
 # 1600), profiles/sov_estimator_m500_grid64.txt.  The estimator is issue-bound: its roofline is the
 # issue rate, 4 warp instructions per clock on each of 152 SMs at 2.07 GHz; achieved =
 # orthant-samples counted on the device x this figure / launch time.
@@ -68,8 +68,9 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-side-by-side", action="store_true", help="skip the dense / FP32-SIMT comparison runs")
     p.add_argument("--cpu-sample", type=int, default=64, help="cells per axis of the oracle sample")
-    p.add_argument("--case", default="full", choices=["full", "small"],
+    p.add_argument("--case", default="full", choices=["full", "small", "small_adaptive"],
                    help="small: one dense LCP field of the same field on a 64^3 grid (for ncu captures); "
+                        "small_adaptive: one adaptive field (max depth 6) on that grid; "
                         "with --mode backward, the backward step on a 64^3 grid")
     return p.parse_args()
 
@@ -408,13 +409,16 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl")
     w = workloads.config2()
-    if args.case == "small" and args.mode != "backward":
+    if args.case in ("small", "small_adaptive") and args.mode != "backward":
         n = 64
         grid = g.make_grid(n)
         out = torch.zeros((n - 1) ** 3, dtype=torch.float32, device="cuda")
         M = g.gpr_model_create(w.X, w.y, w.kernel, w.ell, w.sf2, w.sn2)
         g.gpr_profile_reset(); g.gpr_profile_enable(True)
-        st = g.gpr_lcp_dense(M, grid, w.isovalues[1], g.lcp_options(prec=g.GPR_P_TF32X3), out)
+        if args.case == "small":
+            st = g.gpr_lcp_dense(M, grid, w.isovalues[1], g.lcp_options(prec=g.GPR_P_TF32X3), out)
+        else:
+            st = g.gpr_lcp_adaptive(M, grid, w.isovalues[1], 6, g.lcp_options(prec=g.GPR_P_TF32X3), out)
         g.gpr_sync()
         g.gpr_profile_enable(False)
         print(json.dumps({"case": "small", "grid": n, "m": w.m,

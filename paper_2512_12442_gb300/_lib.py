@@ -74,6 +74,7 @@ SIGNATURES = {
     "gpr_oz_mul_tn_test": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_int64, C.c_int32, C.c_void_p,
                                      C.c_void_p]),
     "gpr_oz_mul_linv_test": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
+    "gpr_eval_points": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_void_p]),
     "gpr_octree_trace": (C.c_int, [C.c_void_p, C.POINTER(GridC), C.c_double, C.c_int32, C.POINTER(LcpOptionsC),
                                    C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
                                    C.POINTER(C.c_int64), C.c_void_p]),

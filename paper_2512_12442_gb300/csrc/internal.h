@@ -91,7 +91,7 @@ struct gpr_model {
     float *BT32 = nullptr;     // mp x mp FP32 copy
     float *vy32 = nullptr;     // mp
     float2 *alpha_ff = nullptr; // mp: alpha as float-float (hi, lo)
-    float *X32 = nullptr;      // m x 3 FP32 observation sites
+    float *X32 = nullptr;      // m x 3 FP32 observation sites (float-float: hi, then lo at + 3 mp), zero-padded to mp x 3
     float *alpha32 = nullptr;  // mp FP32 alpha
     TcOperands *tc = nullptr;  // built on first tensor-core use
     OzOperands *oz = nullptr;  // built on first FP64-class tensor-core use

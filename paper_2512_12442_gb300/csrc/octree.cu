@@ -31,21 +31,36 @@ struct EvalModel {
     float sf2;
 };
 
+// (h, l) += the (h, l) of the lane `o` apart, h by Knuth's error-free two-sum.
+__device__ __forceinline__ void two_sum_shfl(float &h, float &l, int o)
+{
+    const float h2 = __shfl_xor_sync(0xffffffffu, h, o), l2 = __shfl_xor_sync(0xffffffffu, l, o);
+    const float s = h + h2, bv = s - h;
+    l += l2 + ((h - (s - bv)) + (h2 - bv));
+    h = s;
+}
+
 // g = (theta - mu)/sigma and grad g at each evaluation point (warp per point).  mu and grad mu =
 // sum_j dk_j alpha_j here (compensated mu); |w|^2 and, with grad, w . L^-1 d_k k come as partial
 // sums over 64-column groups from the tensor-core evaluation: var = sf2 - |w|^2,
 // grad var = -2 w . L^-1 d_k k.
 __global__ void k_eval_reduce(EvalModel E, const double *xyz, const float *partial, int nN, bool grad, int64_t count,
-                              double theta, float4 *out)
+                              double theta, float4 *out, float *moments)
 {
     int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     int64_t q = blockIdx.x * (int64_t)(blockDim.x / 32) + warp;
     if (q >= count) return;
-    float x = (float)xyz[3 * q], y = (float)xyz[3 * q + 1], z = (float)xyz[3 * q + 2];
-    float mu_h = 0.f, mu_l = 0.f, gm[3] = {0, 0, 0};
+    // coordinates and sites in float-float, so that differences of near points keep their digits
+    // (a sparse model's alpha is large: its grad mu needs them)
+    const float x = (float)xyz[3 * q], y = (float)xyz[3 * q + 1], z = (float)xyz[3 * q + 2];
+    const float xl = (float)(xyz[3 * q] - (double)x), yl = (float)(xyz[3 * q + 1] - (double)y),
+                zl = (float)(xyz[3 * q + 2] - (double)z);
+    const float *Xlo = E.X32 + 3 * E.mp;
+    float mu_h = 0.f, mu_l = 0.f, gm[3] = {0, 0, 0}, gml[3] = {0, 0, 0};
     float il2[3] = {1.f / (E.ell[0] * E.ell[0]), 1.f / (E.ell[1] * E.ell[1]), 1.f / (E.ell[2] * E.ell[2])};
     for (int64_t j = lane; j < E.m; j += 32) {
-        float d0 = x - E.X32[3 * j], d1 = y - E.X32[3 * j + 1], d2 = z - E.X32[3 * j + 2];
+        float d0 = (x - E.X32[3 * j]) + (xl - Xlo[3 * j]), d1 = (y - E.X32[3 * j + 1]) + (yl - Xlo[3 * j + 1]),
+              d2 = (z - E.X32[3 * j + 2]) + (zl - Xlo[3 * j + 2]);
         float r2 = d0 * d0 * il2[0] + d1 * d1 * il2[1] + d2 * d2 * il2[2];
         float k, c;
         if (E.kind == GPR_K_SE) {
@@ -61,17 +76,24 @@ __global__ void k_eval_reduce(EvalModel E, const double *xyz, const float *parti
         float term = k * a, s = mu_h + term, bv = s - mu_h;
         mu_l += (mu_h - (s - bv)) + (term - bv);
         mu_h = s;
+        // grad mu compensated the same way (sparse models' alpha = K_MM^-1 mu_M reaches ~1e5)
         float dd[3] = {d0, d1, d2};
 #pragma unroll
-        for (int dI = 0; dI < 3; ++dI) gm[dI] = fmaf(c * dd[dI] * il2[dI], a, gm[dI]);
+        for (int dI = 0; dI < 3; ++dI) {
+            const float tg = c * dd[dI] * il2[dI] * a, sg = gm[dI] + tg, bg = sg - gm[dI];
+            gml[dI] += (gm[dI] - (sg - bg)) + (tg - bg);
+            gm[dI] = sg;
+        }
     }
+    // lanes combined with the same error-free sums (the lanes' partial sums are large too)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        mu_h += __shfl_xor_sync(0xffffffffu, mu_h, o);
-        mu_l += __shfl_xor_sync(0xffffffffu, mu_l, o);
+        two_sum_shfl(mu_h, mu_l, o);
 #pragma unroll
-        for (int dI = 0; dI < 3; ++dI) gm[dI] += __shfl_xor_sync(0xffffffffu, gm[dI], o);
+        for (int dI = 0; dI < 3; ++dI) two_sum_shfl(gm[dI], gml[dI], o);
     }
+#pragma unroll
+    for (int dI = 0; dI < 3; ++dI) gm[dI] += gml[dI];
     if (lane == 0) {
         const int T = grad ? 4 : 1;
         float wsq = 0.f, gv[3] = {0.f, 0.f, 0.f};
@@ -92,6 +114,15 @@ __global__ void k_eval_reduce(EvalModel E, const double *xyz, const float *parti
         o.z = -gm[1] / sd - gg * gv[1] / (2.f * var);
         o.w = -gm[2] / sd - gg * gv[2] / (2.f * var);
         out[q] = o;
+        if (moments) {  // test hook: mu, var (unfloored), grad mu, grad var
+            float *mo = moments + 8 * q;
+            mo[0] = mu;
+            mo[1] = E.sf2 - wsq;
+            for (int dI = 0; dI < 3; ++dI) {
+                mo[2 + dI] = gm[dI];
+                mo[5 + dI] = gv[dI];
+            }
+        }
     }
 }
 
@@ -1174,7 +1205,7 @@ static gpr_status run_eval(gpr_model *M, const EvalModel &E, OctBuffers &B, int6
         GPR_TRY(launch_tc_eval(M, B.xyz, cnt, grad, B.W, B.wlen, st));
     }
     const int nN = (int)(((M->mp + 255) / 256 * 256) / 64);
-    k_eval_reduce<<<nb(cnt, 8), 256, 0, st>>>(E, B.xyz, B.W, nN, grad, cnt, theta, B.ev);
+    k_eval_reduce<<<nb(cnt, 8), 256, 0, st>>>(E, B.xyz, B.W, nN, grad, cnt, theta, B.ev, nullptr);
     note_launch();
     GPR_CUDA_TRY(cudaGetLastError());
     return GPR_OK;
@@ -1639,6 +1670,39 @@ gpr_status octree_leaf_mask(gpr_model *M, const gpr_grid *grid, double theta, in
 {
     OctTrace tr{-1, nullptr, nullptr, nullptr, 0, 0, leaf};
     return octree_lcp(M, grid, theta, D, opts, nullptr, nullptr, st, &tr);
+}
+
+// Test hook (not in the public header): the evaluation path of the bound's minimiser (tensor-core
+// rows and the warp reduction) at count points (device, count x 3 FP64); out: device float, 8 per
+// point: mu, var, grad mu (3), grad var (3) (the gradients 0 without grad).
+extern "C" gpr_status gpr_eval_points(gpr_model *M, const double *xyz, int64_t count, int32_t grad, float *out,
+                                      void *stream)
+{
+    if (!M || !xyz || !out || count < 0 || count > kEvalChunk) return GPR_ERR_ARG;
+    if (count == 0) return GPR_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    EvalModel E;
+    E.X32 = M->X32; E.alpha32 = M->alpha32;
+    E.m = M->m; E.mp = M->mp; E.kind = M->kp.kind; E.sf2 = (float)M->kp.sf2;
+    for (int d = 0; d < 3; ++d) {
+        E.ell[d] = (float)M->kp.ell[d];
+        E.iell[d] = (float)(1.0 / M->kp.ell[d]);
+    }
+    const size_t pe = tc_eval_partial_elems(M, count);
+    float *part = nullptr;
+    float4 *g4 = nullptr;
+    const size_t pe4 = (pe + 3) / 4 * 4;  // the g / grad g records after the partials, 16-byte aligned
+    GPR_CUDA_TRY(cudaMallocAsync((void **)&part, pe4 * sizeof(float) + (size_t)count * sizeof(float4), st));
+    g4 = (float4 *)(part + pe4);
+    gpr_status rc = launch_tc_eval(M, xyz, count, grad != 0, part, pe, st);
+    if (rc == GPR_OK) {
+        const int nN = (int)(((M->mp + 255) / 256 * 256) / 64);
+        k_eval_reduce<<<nb(count, 8), 256, 0, st>>>(E, xyz, part, nN, grad != 0, count, 0.0, g4, out);
+        note_launch();
+        if (cudaGetLastError() != cudaSuccess) rc = GPR_ERR_CUDA;
+    }
+    cudaFreeAsync(part, st);
+    return rc;
 }
 
 // Test hook (not in the public header): the frontier, decisions and bounds of one level.

@@ -224,7 +224,11 @@ __global__ void k_operands(const double *Linv, int64_t mb, int64_t m, int64_t mp
         alpha_ff[idx] = make_float2(h, (float)(a - (double)h));
         alpha32[idx] = h;
     }
-    if (idx < 3 * m) X32[idx] = (float)X[idx];
+    if (idx < 3 * mp) {  // hi parts, then lo parts (X = hi + lo to ~1e-15), each zero-padded to 3 mp
+        const float h = idx < 3 * m ? (float)X[idx] : 0.0f;
+        X32[idx] = h;
+        X32[3 * mp + idx] = idx < 3 * m ? (float)(X[idx] - (double)h) : 0.0f;
+    }
     if (idx >= mp * mp) return;
     int64_t i = idx / mp, j = idx % mp;
     double v = (i < m && j < m && i <= j) ? Linv[j * mb + i] : 0.0;
@@ -329,7 +333,7 @@ extern "C" gpr_status gpr_model_create(const double *obs_xyz, const double *y, i
     ALLOC(M->BT32, sizeof(float) * mp * mp);
     ALLOC(M->vy32, sizeof(float) * mp);
     ALLOC(M->alpha_ff, sizeof(float2) * mp);
-    ALLOC(M->X32, sizeof(float) * 3 * m);
+    ALLOC(M->X32, sizeof(float) * 6 * mp);
     ALLOC(M->alpha32, sizeof(float) * mp);
     ALLOC(A, sizeof(double) * mb * mb);
 #undef ALLOC
@@ -527,7 +531,7 @@ extern "C" gpr_status gpr_model_create_sgpr(const double *inducing_xyz, const do
     ALLOC(M->BT32, sizeof(float) * mp * mp);
     ALLOC(M->vy32, sizeof(float) * mp);
     ALLOC(M->alpha_ff, sizeof(float2) * mp);
-    ALLOC(M->X32, sizeof(float) * 3 * m);
+    ALLOC(M->X32, sizeof(float) * 6 * mp);
     ALLOC(M->alpha32, sizeof(float) * mp);
     ALLOC(A, sq);
     ALLOC(P, sq);

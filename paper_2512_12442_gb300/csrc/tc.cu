@@ -555,20 +555,23 @@ __device__ __forceinline__ void gen_a_chunk64(const TcParams &prm, unsigned char
     const int64_t m = prm.m;
     const int64_t k0 = (int64_t)kb * 16 + c * 4;
     float v[4] = {0.f, 0.f, 0.f, 0.f};
-    if (rvalid[r]) {
+    if (rvalid[r] && k0 < m) {
         const float *tx = prm.T32 + (int64_t)gx[r] * prm.mp, *ty = prm.T32 + prm.off1 + (int64_t)gy[r] * prm.mp,
                     *tz = prm.T32 + prm.off2 + (int64_t)gz[r] * prm.mp;
+        if (prm.off2 + (int64_t)gz[r] * prm.mp + k0 + 3 >= prm.tlen) {
+            atomicCAS(prm.status, 0, (int)GPR_ERR_ARG);  // self-check: never expected
+        } else {
+            // table rows are mp (a multiple of 64) floats long and k0 a multiple of 4: 16-byte loads;
+            // entries j >= m of a table row are masked below
+            const float4 a = *(const float4 *)(tx + k0), b = *(const float4 *)(ty + k0), cc = *(const float4 *)(tz + k0);
+            const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w}, cv[4] = {cc.x, cc.y, cc.z, cc.w};
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            int64_t j = k0 + e;
-            if (j < m && prm.off2 + (int64_t)gz[r] * prm.mp + j >= prm.tlen) {
-                atomicCAS(prm.status, 0, (int)GPR_ERR_ARG);  // self-check: never expected
-            } else if (j < m) {
-                float a = tx[j], b = ty[j], cc = tz[j];
+            for (int e = 0; e < 4; ++e) {
+                if (k0 + e >= m) continue;
                 if (prm.kind == GPR_K_SE) {
-                    v[e] = a * b * cc;
+                    v[e] = av[e] * bv[e] * cv[e];
                 } else {
-                    float r2 = a + b + cc, rr = sqrtf(r2), s5r = 2.23606797749979f * rr;
+                    const float r2 = av[e] + bv[e] + cv[e], rr = sqrtf(r2), s5r = 2.23606797749979f * rr;
                     v[e] = prm.sf2 * (1.0f + s5r + (5.0f / 3.0f) * r2) * __expf(-s5r);
                 }
             }
@@ -743,7 +746,7 @@ __global__ void __launch_bounds__(WS_NTHR, 2) k_tc_sumsq_2c(const __grid_constan
 struct TcEvalParams {
     const double *xyz;  // count x 3 evaluation points
     int64_t count;
-    const float *X32;   // m x 3 observation sites
+    const float *X32;   // m x 3 observation sites, float-float: hi, then lo at + 3 mp
     int64_t m, mp;
     int kind;
     float sf2;
@@ -754,23 +757,40 @@ struct TcEvalParams {
     int *status;
 };
 
-// Chunk c (4 elements) of row r: with GRAD, rows 32t .. 32t + 31 hold row type t (0: k(x, X_j),
-// 1..3: d k / d x_{t-1}) of the CTA's 32 points; without, row r is point r's kernel row.
+// Chunk c (4 elements) of rows r0 and r0 + 64 (r0 < 64): with GRAD, rows 32t .. 32t + 31 hold row
+// type t (0: k(x, X_j), 1..3: d k / d x_{t-1}) of the CTA's 32 points, so both rows belong to point
+// r0 mod 32 (types t0 and t0 + 2) and share one kernel evaluation; without, they are points r0 and
+// r0 + 64.  The sites X_j of the chunk come in three 16-byte loads.
 template <bool GRAD>
-__device__ __forceinline__ void gen_eval_chunk64(const TcEvalParams &prm, unsigned char *st, int r, int c, int kb,
-                                                 const float *px, const float *py, const float *pz, const bool *rvalid)
+__device__ __forceinline__ void gen_eval_chunk64(const TcEvalParams &prm, unsigned char *st, int r0, int c, int kb,
+                                                 const float (*pc)[GRAD ? 32 : TM], const bool *rvalid)
 {
     constexpr int A_TILE = TM * 64;
-    const int type = GRAD ? r >> 5 : 0, pr = GRAD ? (r & 31) : r;
     const int64_t k0 = (int64_t)kb * 16 + c * 4;
-    float v[4] = {0.f, 0.f, 0.f, 0.f};
-    if (rvalid[pr]) {
-        const float x = px[pr], y = py[pr], z = pz[pr];
+    float xs[12], xsl[12];
+#pragma unroll
+    for (int i = 0; i < 12; ++i) xs[i] = xsl[i] = 0.f;
+    if (k0 < prm.m) {  // X32 holds 2 x 3 mp floats (zero beyond m) and k0 + 3 < mp
+        const float4 *xp = (const float4 *)(prm.X32 + 3 * k0), *xq = (const float4 *)(prm.X32 + 3 * prm.mp + 3 * k0);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const float4 a = xp[i], b = xq[i];
+            xs[4 * i] = a.x; xs[4 * i + 1] = a.y; xs[4 * i + 2] = a.z; xs[4 * i + 3] = a.w;
+            xsl[4 * i] = b.x; xsl[4 * i + 1] = b.y; xsl[4 * i + 2] = b.z; xsl[4 * i + 3] = b.w;
+        }
+    }
+    float v[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+#pragma unroll
+    for (int h = 0; h < (GRAD ? 1 : 2); ++h) {
+        const int pr = GRAD ? (r0 & 31) : r0 + 64 * h;
+        if (!rvalid[pr] || k0 >= prm.m) continue;
+        const float x = pc[0][pr], y = pc[1][pr], z = pc[2][pr], xl = pc[3][pr], yl = pc[4][pr], zl = pc[5][pr];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-            const int64_t j = k0 + e;
-            if (j >= prm.m) continue;
-            const float d0 = x - prm.X32[3 * j], d1 = y - prm.X32[3 * j + 1], d2 = z - prm.X32[3 * j + 2];
+            if (k0 + e >= prm.m) continue;
+            // float-float differences: near points keep their digits
+            const float d0 = (x - xs[3 * e]) + (xl - xsl[3 * e]), d1 = (y - xs[3 * e + 1]) + (yl - xsl[3 * e + 1]),
+                        d2 = (z - xs[3 * e + 2]) + (zl - xsl[3 * e + 2]);
             const float a = d0 * prm.iell[0], b = d1 * prm.iell[1], cc = d2 * prm.iell[2];
             const float r2 = a * a + b * b + cc * cc;
             float k, cf;
@@ -782,24 +802,29 @@ __device__ __forceinline__ void gen_eval_chunk64(const TcEvalParams &prm, unsign
                 k = prm.sf2 * (1.0f + s5r + (5.0f / 3.0f) * r2) * ex;
                 cf = -(5.0f / 3.0f) * prm.sf2 * (1.0f + s5r) * ex;
             }
-            if (type == 0) v[e] = k;
-            else {
-                const float dd = type == 1 ? d0 : (type == 2 ? d1 : d2);
-                const float il = type == 1 ? prm.il2[0] : (type == 2 ? prm.il2[1] : prm.il2[2]);
-                v[e] = cf * dd * il;
+            if (GRAD) {
+                // row r0: type r0 / 32 (0: k, 1: d/dx); row r0 + 64: type 2 or 3 (d/dy, d/dz)
+                v[0][e] = (r0 >> 5) == 0 ? k : cf * d0 * prm.il2[0];
+                v[1][e] = (r0 >> 5) == 0 ? cf * d1 * prm.il2[1] : cf * d2 * prm.il2[2];
+            } else {
+                v[h][e] = k;
             }
         }
     }
-    const int off = r * 64 + ((c ^ ((r >> 1) & 3)) << 4);
-    float4 hi, lo;
-    float *h = &hi.x, *l = &lo.x;
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
-        h[e] = tf32_round(v[e]);
-        l[e] = tf32_round(v[e] - h[e]);
+    for (int h = 0; h < 2; ++h) {
+        const int r = r0 + 64 * h;
+        const int off = r * 64 + ((c ^ ((r >> 1) & 3)) << 4);
+        float4 hi, lo;
+        float *hh = &hi.x, *l = &lo.x;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            hh[e] = tf32_round(v[h][e]);
+            l[e] = tf32_round(v[h][e] - hh[e]);
+        }
+        *(float4 *)(st + off) = hi;
+        *(float4 *)(st + A_TILE + off) = lo;
     }
-    *(float4 *)(st + off) = hi;
-    *(float4 *)(st + A_TILE + off) = lo;
 }
 
 // The pipeline of k_tc_sumsq_2c (TMA warp, MMA warp, 8 generating and draining warps; two CTAs
@@ -820,7 +845,7 @@ __global__ void __launch_bounds__(WS_NTHR, 2) k_tc_eval(const __grid_constant__ 
     unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t *bars = (uint64_t *)(smem + 2 * STAGE);  // fullB[2], fullA[2], empty[2], done
     __shared__ uint32_t tmem_slot;
-    __shared__ float px[PTS], py[PTS], pz[PTS];
+    __shared__ float pc[6][PTS];  // point coordinates x, y, z (hi), then their lo parts
     __shared__ bool rvalid[PTS];
     __shared__ float red[N / 32][TM];
     __shared__ float wbuf[GRAD ? 2 : 1][32][32];  // [column half][column][point]: kernel-row chunk
@@ -852,9 +877,12 @@ __global__ void __launch_bounds__(WS_NTHR, 2) k_tc_eval(const __grid_constant__ 
         const int64_t q = pt0 + r;
         const bool ok = q < prm.count;
         rvalid[r] = ok;
-        px[r] = ok ? (float)prm.xyz[3 * q] : 0.f;
-        py[r] = ok ? (float)prm.xyz[3 * q + 1] : 0.f;
-        pz[r] = ok ? (float)prm.xyz[3 * q + 2] : 0.f;
+        for (int d = 0; d < 3; ++d) {
+            const double v = ok ? prm.xyz[3 * q + d] : 0.0;
+            const float h = (float)v;
+            pc[d][r] = h;
+            pc[3 + d][r] = (float)(v - (double)h);
+        }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -899,7 +927,7 @@ __global__ void __launch_bounds__(WS_NTHR, 2) k_tc_eval(const __grid_constant__ 
             const int s = kb & 1, use = kb >> 1;
             unsigned char *st = smem + s * STAGE;
             if (kb >= 2 && !mbar_wait(empty0 + 8 * s, (use - 1) & 1)) ok_all = false;
-            for (int q = at; q < TM * 4; q += 256) gen_eval_chunk64<GRAD>(prm, st, q >> 2, q & 3, kb, px, py, pz, rvalid);
+            gen_eval_chunk64<GRAD>(prm, st, at >> 2, at & 3, kb, pc, rvalid);  // rows at/4 and at/4 + 64
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> tensor-core reads
             asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(fullA0 + 8 * s) : "memory");
         }

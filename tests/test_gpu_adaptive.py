@@ -27,7 +27,10 @@ def g():
     return g
 
 
-def _compare_level(om, n, D, l, th, nodes, dec, bnd, alpha=1e-3, sample=None, seed=0):
+def _compare_level(om, n, D, l, th, nodes, dec, bnd, alpha=1e-3, sample=None, seed=0, bound_tol=None):
+    """Decisions of one level against the oracle; with bound_tol = (max, median) also the bounds
+    of nodes both sides minimised in full, as |log(bound / oracle bound)| (where the bound can
+    decide, >= alpha / 10; None skips that statistic)."""
     idx = np.arange(len(nodes))
     if sample is not None and len(idx) > sample:
         idx = np.sort(np.random.default_rng(seed).choice(len(idx), sample, replace=False))
@@ -40,6 +43,13 @@ def _compare_level(om, n, D, l, th, nodes, dec, bnd, alpha=1e-3, sample=None, se
     mism = keep_o != keep_g
     near = (obnd >= alpha / 3) & (obnd <= 3 * alpha)
     assert np.all(near[mism]), (l, obnd[mism & ~near][:10], bnd[idx][mism & ~near][:10])
+    both0 = (odec == 0) & (gd == 0) & (obnd >= alpha / 10)
+    if bound_tol is not None and both0.any():
+        lr = np.abs(np.log(bnd[idx][both0] / obnd[both0]))
+        if bound_tol[0] is not None:
+            assert lr.max() <= bound_tol[0], (l, lr.max())
+        if bound_tol[1] is not None:
+            assert np.median(lr) <= bound_tol[1], (l, np.median(lr))
     return int(mism.sum()), len(idx)
 
 
@@ -60,7 +70,9 @@ def test_octree_levels_match_oracle(torch, g, case, prec):
         nodes, dec, bnd = g.gpr_octree_trace(M, grid, th, D, g.lcp_options(prec=p), l)
         if len(nodes) == 0:
             break
-        mm, cnt = _compare_level(om, n, D, l, th, nodes, dec, bnd)
+        # well-conditioned models: the FP32-class evaluations follow the oracle's minimiser path,
+        # so the bounds agree to 1% (measured: < 0.05%)
+        mm, cnt = _compare_level(om, n, D, l, th, nodes, dec, bnd, bound_tol=(1e-2, None))
         total_mism += mm
     assert total_mism <= 0.01 * (n - 1) ** 3 + 2
 
@@ -109,8 +121,12 @@ def test_adaptive_config2_full_size_sampled_nodes(torch, g):
     for l in (2, 4, 5, 6, 7):
         nodes, dec, bnd = g.gpr_octree_trace(M, grid, th, w.max_depth, g.lcp_options(prec=g.GPR_P_TF32X3), l)
         assert len(nodes) > 0
+        # ill-conditioned model (var down to 4e-5 sf2): the FP32-class evaluations (|dvar| ~4e-5 sf2,
+        # |dmu| ~1e-4 max|y|) move g by up to a few per cent, a few times that in the Phi tails the
+        # bound sits in, and can send the local minimiser to another point: the median bound agrees
+        # within 10 % (measured: 2-6 %), single nodes by less (one node of 93 by a factor 12)
         mm, cnt = _compare_level(om, w.n, w.max_depth, l, th, nodes, dec, bnd, sample=150 if l >= 5 else None,
-                                 seed=l)
+                                 seed=l, bound_tol=(None, 0.1))
         assert mm <= max(3, 0.03 * cnt)
 
 
@@ -238,3 +254,59 @@ def test_kd_tree_levels_match_oracle_and_field(torch, g):
     assert st["leaf_cells"] == inS.sum() and 0 < inS.sum() < inS.size
     assert np.array_equal(av[inS], dv[inS]) and np.all(av[~inS] == 0)
 
+
+
+def _eval_points(g, torch, M, P):
+    """mu, var, grad mu, grad var at the points P by the bound minimiser's evaluation path."""
+    import ctypes as C
+    from paper_2512_12442_gb300._lib import load
+    xyz = torch.tensor(np.ascontiguousarray(P), dtype=torch.float64, device="cuda")
+    out = torch.zeros(len(P), 8, dtype=torch.float32, device="cuda")
+    rc = load().gpr_eval_points(C.c_void_p(M.handle), C.c_void_p(xyz.data_ptr()), len(P), 1,
+                                C.c_void_p(out.data_ptr()), None)
+    assert rc == 0
+    g.gpr_sync()
+    o = out.cpu().numpy().astype(np.float64)
+    return o[:, 0], o[:, 1], o[:, 2:5], o[:, 5:8]
+
+
+def _oracle_moments(om, P, t1, t2):
+    """The same four from the oracle's FP64 g = (t - mu) / sigma and grad g at two isovalues."""
+    g1, gr1 = om.eval_g(P, t1, 1)
+    g2, gr2 = om.eval_g(P, t2, 1)
+    sd = (t2 - t1) / (g2 - g1)
+    mu = t1 - g1 * sd
+    gvar = -2.0 * sd[:, None] ** 3 * (gr2 - gr1) / (t2 - t1)
+    gmu = -sd[:, None] * (gr1 + g1[:, None] * gvar / (2.0 * sd[:, None] ** 2))
+    return mu, sd ** 2, gmu, gvar
+
+
+@pytest.mark.parametrize("kind", ["gpr", "sgpr"])
+def test_bound_evaluations_vs_oracle(torch, g, kind):
+    """The bound minimiser's evaluations (TF32x3 tensor-core rows of k and of d k / d x_d, reduced to
+    |w|^2 and w . L^-1 d_k k; mean and its gradient by compensated k . alpha) at 2,000 random points
+    and 200 points next to observations, against the oracle's FP64 values (recovered from its g and
+    grad g at two isovalues).  Tolerances (FP32-class whitened arithmetic, the tolerance of the FP32
+    paths): |dmu| <= 1e-4 max|y|, |dvar| <= 1e-4 sf2, |d grad mu| <= 1e-4 max|y| / l_min,
+    |d grad var| <= 1e-4 sf2 / l_min for the plain model; 5e-4 for the sparse one, whose
+    K_MM + 1e-6 I (condition ~5e7, against ~4e5) amplifies the FP32 rounding of the kernel entries
+    more."""
+    w = workloads.config2() if kind == "gpr" else workloads.sgpr(n=33)
+    M = model_of(w)
+    om = oracle.Model.from_workload(w)
+    rng = np.random.default_rng(21)
+    X = np.asarray(w.X)
+    P = np.concatenate([rng.random((2000, 3)),
+                        np.clip(X[rng.integers(0, len(X), 200)] + rng.normal(0, 0.01, (200, 3)), 0, 1)])
+    mu, var, gmu, gvar = _eval_points(g, torch, M, P)
+    omu, ovar, ogmu, ogvar = _oracle_moments(om, P, float(w.isovalues[1]), float(w.isovalues[1]) + 1.0)
+    ys = np.abs(np.asarray(w.y)).max()  # observations, or the inducing means mu_M of the sparse model
+    lmin = float(np.min(w.ell))
+    err = (np.abs(mu - omu).max() / ys, np.abs(var - ovar).max() / w.sf2,
+           np.abs(gmu - ogmu).max() * lmin / ys, np.abs(gvar - ogvar).max() * lmin / w.sf2)
+    print(f"\n{kind}: max |dmu|/max|y| {err[0]:.2e}, |dvar|/sf2 {err[1]:.2e}, "
+          f"|d grad mu| l/max|y| {err[2]:.2e}, |d grad var| l/sf2 {err[3]:.2e}; "
+          f"var range {ovar.min():.2e}..{ovar.max():.2e}, |grad mu| l/max|y| up to "
+          f"{np.abs(ogmu).max() * lmin / ys:.2e}, |grad var| l/sf2 up to {np.abs(ogvar).max() * lmin / w.sf2:.2e}")
+    tol = 1e-4 if kind == "gpr" else 5e-4
+    assert max(err) <= tol, err
