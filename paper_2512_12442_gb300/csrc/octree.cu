@@ -313,16 +313,19 @@ __global__ void k_small_bound(GridDev g, int D, int l, int kd, const int64_t *no
     if (q >= count || decision[q] != 0) return;
     Geom G = node_geom(g, D, l, kd, nodes[q]);
     if (!is_small(G)) return;
-    double glo = INFINITY, ghi = INFINITY;
+    // g per point in FP32 (the table holds FP32-class values; FP64 division and square roots per
+    // point cost the FP64 pipe more than the rest of the kernel); the bound itself in FP64
+    const float thf = (float)theta, fl = (float)(1e-12 * sf2);
+    float gmin = INFINITY, gmax = -INFINITY;
     for (int64_t c = G.p0[2]; c <= G.p1[2]; ++c)
         for (int64_t b = G.p0[1]; b <= G.p1[1]; ++b)
             for (int64_t a = G.p0[0]; a <= G.p1[0]; ++a) {
-                float2 v = mv[a + (int64_t)g.n[0] * (b + (int64_t)g.n[1] * c)];
-                double var = fmax((double)v.y, 1e-12 * sf2);
-                double gg = (theta - (double)v.x) / sqrt(var);
-                glo = fmin(glo, gg);
-                ghi = fmin(ghi, -gg);
+                const float2 v = mv[a + (int64_t)g.n[0] * (b + (int64_t)g.n[1] * c)];
+                const float gg = (thf - v.x) * rsqrtf(fmaxf(v.y, fl));
+                gmin = fminf(gmin, gg);
+                gmax = fmaxf(gmax, gg);
             }
+    const double glo = (double)gmin, ghi = -(double)gmax;
     double dcount = (double)((G.p1[0] - G.p0[0] + 1) * (G.p1[1] - G.p0[1] + 1) * (G.p1[2] - G.p0[2] + 1));
     double bnd = bound_of(sides[q], dcount, glo, ghi);
     bound[q] = bnd;
