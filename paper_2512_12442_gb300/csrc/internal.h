@@ -204,7 +204,8 @@ void tc_release(gpr_model *M);
 size_t tc_partial_elems(gpr_precision p, const gpr_model *M, int64_t count);
 // TF32x3 whitened rows at arbitrary points (count x 3 FP64 coordinates), reduced to partial sums
 // of |w|^2 and, with grad, of w . L^-1 d_k k per coordinate: partial[(point * T + type) * nN + g],
-// T = 4 with grad (else 1), nN = (mp rounded up to 256) / 64 groups of 64 columns.
+// T = 4 with grad (else 1), nN = (mp rounded up to 256) / 64 groups of 64 columns; after the
+// count * 4 * nN partial sums, 8 floats per point: mu and (grad) grad mu as float-float pairs.
 size_t tc_eval_partial_elems(const gpr_model *M, int64_t count);
 gpr_status launch_tc_eval(gpr_model *M, const double *xyz, int64_t count, bool grad, float *partial,
                           size_t partial_elems, cudaStream_t st);

@@ -31,97 +31,46 @@ struct EvalModel {
     float sf2;
 };
 
-// (h, l) += the (h, l) of the lane `o` apart, h by Knuth's error-free two-sum.
-__device__ __forceinline__ void two_sum_shfl(float &h, float &l, int o)
+// g = (theta - mu)/sigma and grad g at each evaluation point (thread per point) from the tensor-core
+// evaluation's sums: |w|^2 and (grad) w . L^-1 d_k k per 64-column group, var = sf2 - |w|^2,
+// grad var = -2 w . L^-1 d_k k; mu and grad mu = sum_j dk_j alpha_j as float-float pairs (summed
+// error-free in the generating warps).  Without grad the gradient is 0.
+__global__ void k_eval_reduce(EvalModel E, const float *partial, int nN, bool grad, int64_t count, double theta,
+                              float4 *out, float *moments)
 {
-    const float h2 = __shfl_xor_sync(0xffffffffu, h, o), l2 = __shfl_xor_sync(0xffffffffu, l, o);
-    const float s = h + h2, bv = s - h;
-    l += l2 + ((h - (s - bv)) + (h2 - bv));
-    h = s;
-}
-
-// g = (theta - mu)/sigma and grad g at each evaluation point (warp per point).  mu and grad mu =
-// sum_j dk_j alpha_j here (compensated mu); |w|^2 and, with grad, w . L^-1 d_k k come as partial
-// sums over 64-column groups from the tensor-core evaluation: var = sf2 - |w|^2,
-// grad var = -2 w . L^-1 d_k k.
-__global__ void k_eval_reduce(EvalModel E, const double *xyz, const float *partial, int nN, bool grad, int64_t count,
-                              double theta, float4 *out, float *moments)
-{
-    int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    int64_t q = blockIdx.x * (int64_t)(blockDim.x / 32) + warp;
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (q >= count) return;
-    // coordinates and sites in float-float, so that differences of near points keep their digits
-    // (a sparse model's alpha is large: its grad mu needs them)
-    const float x = (float)xyz[3 * q], y = (float)xyz[3 * q + 1], z = (float)xyz[3 * q + 2];
-    const float xl = (float)(xyz[3 * q] - (double)x), yl = (float)(xyz[3 * q + 1] - (double)y),
-                zl = (float)(xyz[3 * q + 2] - (double)z);
-    const float *Xlo = E.X32 + 3 * E.mp;
-    float mu_h = 0.f, mu_l = 0.f, gm[3] = {0, 0, 0}, gml[3] = {0, 0, 0};
-    float il2[3] = {1.f / (E.ell[0] * E.ell[0]), 1.f / (E.ell[1] * E.ell[1]), 1.f / (E.ell[2] * E.ell[2])};
-    for (int64_t j = lane; j < E.m; j += 32) {
-        float d0 = (x - E.X32[3 * j]) + (xl - Xlo[3 * j]), d1 = (y - E.X32[3 * j + 1]) + (yl - Xlo[3 * j + 1]),
-              d2 = (z - E.X32[3 * j + 2]) + (zl - Xlo[3 * j + 2]);
-        float r2 = d0 * d0 * il2[0] + d1 * d1 * il2[1] + d2 * d2 * il2[2];
-        float k, c;
-        if (E.kind == GPR_K_SE) {
-            k = E.sf2 * __expf(-0.5f * r2);
-            c = -k;
-        } else {
-            float r = sqrtf(r2), s5r = 2.23606797749979f * r, e = __expf(-s5r);
-            k = E.sf2 * (1.0f + s5r + (5.0f / 3.0f) * r2) * e;
-            c = -(5.0f / 3.0f) * E.sf2 * (1.0f + s5r) * e;
-        }
-        float a = E.alpha32[j];
-        // compensated accumulation of mu (terms k*alpha reach ~1e3 for an O(1) result)
-        float term = k * a, s = mu_h + term, bv = s - mu_h;
-        mu_l += (mu_h - (s - bv)) + (term - bv);
-        mu_h = s;
-        // grad mu compensated the same way (sparse models' alpha = K_MM^-1 mu_M reaches ~1e5)
-        float dd[3] = {d0, d1, d2};
-#pragma unroll
+    const float *mo = partial + count * 4 * nN + 8 * q;
+    const int T = grad ? 4 : 1;
+    float wsq = 0.f, gv[3] = {0.f, 0.f, 0.f}, gm[3] = {0.f, 0.f, 0.f};
+    for (int g2 = 0; g2 < nN; ++g2) {
+        wsq += partial[(q * T) * nN + g2];
+        if (grad)
+            for (int dI = 0; dI < 3; ++dI) gv[dI] += partial[(q * T + 1 + dI) * nN + g2];
+    }
+    for (int dI = 0; dI < 3; ++dI) {
+        gv[dI] *= -2.f;
+        if (grad) gm[dI] = mo[2 + 2 * dI] + mo[3 + 2 * dI];
+    }
+    const float mu = mo[0] + mo[1];
+    float var = E.sf2 - wsq;
+    const float fl = 1e-12f * E.sf2;
+    if (!(var > fl)) var = fl;
+    const float sd = sqrtf(var);
+    const float gg = (float)(theta - (double)mu) / sd;
+    float4 o;
+    o.x = gg;
+    o.y = -gm[0] / sd - gg * gv[0] / (2.f * var);
+    o.z = -gm[1] / sd - gg * gv[1] / (2.f * var);
+    o.w = -gm[2] / sd - gg * gv[2] / (2.f * var);
+    out[q] = o;
+    if (moments) {  // test hook: mu, var (unfloored), grad mu, grad var
+        float *m8 = moments + 8 * q;
+        m8[0] = mu;
+        m8[1] = E.sf2 - wsq;
         for (int dI = 0; dI < 3; ++dI) {
-            const float tg = c * dd[dI] * il2[dI] * a, sg = gm[dI] + tg, bg = sg - gm[dI];
-            gml[dI] += (gm[dI] - (sg - bg)) + (tg - bg);
-            gm[dI] = sg;
-        }
-    }
-    // lanes combined with the same error-free sums (the lanes' partial sums are large too)
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        two_sum_shfl(mu_h, mu_l, o);
-#pragma unroll
-        for (int dI = 0; dI < 3; ++dI) two_sum_shfl(gm[dI], gml[dI], o);
-    }
-#pragma unroll
-    for (int dI = 0; dI < 3; ++dI) gm[dI] += gml[dI];
-    if (lane == 0) {
-        const int T = grad ? 4 : 1;
-        float wsq = 0.f, gv[3] = {0.f, 0.f, 0.f};
-        for (int g2 = 0; g2 < nN; ++g2) {
-            wsq += partial[(q * T) * nN + g2];
-            if (grad)
-                for (int dI = 0; dI < 3; ++dI) gv[dI] += partial[(q * T + 1 + dI) * nN + g2];
-        }
-        for (int dI = 0; dI < 3; ++dI) gv[dI] *= -2.f;
-        float var = E.sf2 - wsq;
-        float fl = 1e-12f * E.sf2;
-        if (!(var > fl)) var = fl;
-        float sd = sqrtf(var), mu = mu_h + mu_l;
-        float gg = (float)(theta - (double)mu) / sd;
-        float4 o;
-        o.x = gg;
-        o.y = -gm[0] / sd - gg * gv[0] / (2.f * var);
-        o.z = -gm[1] / sd - gg * gv[1] / (2.f * var);
-        o.w = -gm[2] / sd - gg * gv[2] / (2.f * var);
-        out[q] = o;
-        if (moments) {  // test hook: mu, var (unfloored), grad mu, grad var
-            float *mo = moments + 8 * q;
-            mo[0] = mu;
-            mo[1] = E.sf2 - wsq;
-            for (int dI = 0; dI < 3; ++dI) {
-                mo[2 + dI] = gm[dI];
-                mo[5 + dI] = gv[dI];
-            }
+            m8[2 + dI] = gm[dI];
+            m8[5 + dI] = gv[dI];
         }
     }
 }
@@ -1208,7 +1157,7 @@ static gpr_status run_eval(gpr_model *M, const EvalModel &E, OctBuffers &B, int6
         GPR_TRY(launch_tc_eval(M, B.xyz, cnt, grad, B.W, B.wlen, st));
     }
     const int nN = (int)(((M->mp + 255) / 256 * 256) / 64);
-    k_eval_reduce<<<nb(cnt, 8), 256, 0, st>>>(E, B.xyz, B.W, nN, grad, cnt, theta, B.ev, nullptr);
+    k_eval_reduce<<<nb(cnt, 256), 256, 0, st>>>(E, B.W, nN, grad, cnt, theta, B.ev, nullptr);
     note_launch();
     GPR_CUDA_TRY(cudaGetLastError());
     return GPR_OK;
@@ -1700,7 +1649,7 @@ extern "C" gpr_status gpr_eval_points(gpr_model *M, const double *xyz, int64_t c
     gpr_status rc = launch_tc_eval(M, xyz, count, grad != 0, part, pe, st);
     if (rc == GPR_OK) {
         const int nN = (int)(((M->mp + 255) / 256 * 256) / 64);
-        k_eval_reduce<<<nb(count, 8), 256, 0, st>>>(E, xyz, part, nN, grad != 0, count, 0.0, g4, out);
+        k_eval_reduce<<<nb(count, 256), 256, 0, st>>>(E, part, nN, grad != 0, count, 0.0, g4, out);
         note_launch();
         if (cudaGetLastError() != cudaSuccess) rc = GPR_ERR_CUDA;
     }

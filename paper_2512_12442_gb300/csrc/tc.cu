@@ -752,6 +752,8 @@ struct TcEvalParams {
     float sf2;
     float iell[3], il2[3];
     float *partial;     // (count x T) x nN partial sums, T = 4 with GRAD (|w|^2, w . dw_x, dw_y, dw_z), else 1
+    float *mom;         // count x 8: mu and (GRAD) grad mu as float-float pairs (hi, lo), by the last column tile
+    const float *alpha32;  // mp FP32 alpha (zero beyond m)
     int nN;
     int64_t plen;
     int *status;
@@ -761,9 +763,22 @@ struct TcEvalParams {
 // type t (0: k(x, X_j), 1..3: d k / d x_{t-1}) of the CTA's 32 points, so both rows belong to point
 // r0 mod 32 (types t0 and t0 + 2) and share one kernel evaluation; without, they are points r0 and
 // r0 + 64.  The sites X_j of the chunk come in three 16-byte loads.
+// (h, l) += t with Knuth's error-free two-sum (the rounding error goes to l).
+__device__ __forceinline__ void acc2(float &h, float &l, float t)
+{
+    const float s = h + t, bv = s - h;
+    l += (h - (s - bv)) + (t - bv);
+    h = s;
+}
+
+// The generating thread also sums, for the last column tile (whose K range is every site), the
+// mean k . alpha and with GRAD its gradient sum_j dk_j alpha_j of its point(s) over its chunks,
+// error-free (alpha reaches ~1e3 for plain and ~1e5 for sparse models): acc[h] = (mu hi, lo, then
+// grad hi, lo per axis) of point r0 + 64 h (GRAD: of point r0 mod 32, rows r0 < 32 only).
 template <bool GRAD>
 __device__ __forceinline__ void gen_eval_chunk64(const TcEvalParams &prm, unsigned char *st, int r0, int c, int kb,
-                                                 const float (*pc)[GRAD ? 32 : TM], const bool *rvalid)
+                                                 const float (*pc)[GRAD ? 32 : TM], const bool *rvalid, bool accum,
+                                                 float (&acc)[2][8])
 {
     constexpr int A_TILE = TM * 64;
     const int64_t k0 = (int64_t)kb * 16 + c * 4;
@@ -779,6 +794,12 @@ __device__ __forceinline__ void gen_eval_chunk64(const TcEvalParams &prm, unsign
             xsl[4 * i] = b.x; xsl[4 * i + 1] = b.y; xsl[4 * i + 2] = b.z; xsl[4 * i + 3] = b.w;
         }
     }
+    float al[4] = {0.f, 0.f, 0.f, 0.f};
+    if (accum && k0 < prm.m) {
+        const float4 a4 = *(const float4 *)(prm.alpha32 + k0);
+        al[0] = a4.x; al[1] = a4.y; al[2] = a4.z; al[3] = a4.w;
+    }
+    const bool acc_here = accum && (!GRAD || r0 < 32);
     float v[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
 #pragma unroll
     for (int h = 0; h < (GRAD ? 1 : 2); ++h) {
@@ -802,12 +823,21 @@ __device__ __forceinline__ void gen_eval_chunk64(const TcEvalParams &prm, unsign
                 k = prm.sf2 * (1.0f + s5r + (5.0f / 3.0f) * r2) * ex;
                 cf = -(5.0f / 3.0f) * prm.sf2 * (1.0f + s5r) * ex;
             }
+            const float g0 = cf * d0 * prm.il2[0], g1 = cf * d1 * prm.il2[1], g2 = cf * d2 * prm.il2[2];
             if (GRAD) {
                 // row r0: type r0 / 32 (0: k, 1: d/dx); row r0 + 64: type 2 or 3 (d/dy, d/dz)
-                v[0][e] = (r0 >> 5) == 0 ? k : cf * d0 * prm.il2[0];
-                v[1][e] = (r0 >> 5) == 0 ? cf * d1 * prm.il2[1] : cf * d2 * prm.il2[2];
+                v[0][e] = (r0 >> 5) == 0 ? k : g0;
+                v[1][e] = (r0 >> 5) == 0 ? g1 : g2;
             } else {
                 v[h][e] = k;
+            }
+            if (acc_here) {
+                acc2(acc[h][0], acc[h][1], k * al[e]);
+                if (GRAD) {
+                    acc2(acc[h][2], acc[h][3], g0 * al[e]);
+                    acc2(acc[h][4], acc[h][5], g1 * al[e]);
+                    acc2(acc[h][6], acc[h][7], g2 * al[e]);
+                }
             }
         }
     }
@@ -923,13 +953,46 @@ __global__ void __launch_bounds__(WS_NTHR, 2) k_tc_eval(const __grid_constant__ 
         }
     } else if (warp >= 2) {
         const int at = tid - 64;  // 0 .. 255
+        const bool accum = blockIdx.y == gridDim.y - 1;  // the last column tile sees every site
+        float acc[2][8];
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int i = 0; i < 8; ++i) acc[h][i] = 0.f;
         for (int kb = 0; kb < nkb; ++kb) {
             const int s = kb & 1, use = kb >> 1;
             unsigned char *st = smem + s * STAGE;
             if (kb >= 2 && !mbar_wait(empty0 + 8 * s, (use - 1) & 1)) ok_all = false;
-            gen_eval_chunk64<GRAD>(prm, st, at >> 2, at & 3, kb, pc, rvalid);  // rows at/4 and at/4 + 64
+            gen_eval_chunk64<GRAD>(prm, st, at >> 2, at & 3, kb, pc, rvalid, accum, acc);  // rows at/4 and at/4 + 64
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> tensor-core reads
             asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(fullA0 + 8 * s) : "memory");
+        }
+        if (accum) {
+            // the four chunk threads of a point are lanes 4q .. 4q + 3: combine them error-free
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+#pragma unroll
+                for (int i = 0; i < 8; i += 2)
+#pragma unroll
+                    for (int o = 1; o <= 2; o <<= 1) {
+                        const float h2 = __shfl_xor_sync(0xffffffffu, acc[h][i], o);
+                        const float l2 = __shfl_xor_sync(0xffffffffu, acc[h][i + 1], o);
+                        acc2(acc[h][i], acc[h][i + 1], h2);
+                        acc[h][i + 1] += l2;
+                    }
+            const int r0 = at >> 2;
+            if ((at & 3) == 0 && (!GRAD || r0 < 32)) {
+#pragma unroll
+                for (int h = 0; h < (GRAD ? 1 : 2); ++h) {
+                    const int pr = GRAD ? r0 : r0 + 64 * h;
+                    const int64_t q = pt0 + pr;
+                    if (q < prm.count) {
+                        float *mo = prm.mom + 8 * q;
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) mo[i] = acc[h][i];
+                    }
+                }
+            }
         }
         if (!mbar_wait(bar_done, 0)) ok_all = false;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -1204,7 +1267,7 @@ size_t tc_partial_elems(gpr_precision p, const gpr_model *M, int64_t count)
 size_t tc_eval_partial_elems(const gpr_model *M, int64_t count)
 {
     const int64_t mpt = (M->mp + 255) / 256 * 256;
-    return (size_t)count * 4 * (size_t)(mpt / 64);
+    return (size_t)count * (4 * (size_t)(mpt / 64) + 8);
 }
 
 gpr_status launch_tc_eval(gpr_model *M, const double *xyz, int64_t count, bool grad, float *partial,
@@ -1229,8 +1292,10 @@ gpr_status launch_tc_eval(gpr_model *M, const double *xyz, int64_t count, bool g
     }
     prm.partial = partial;
     prm.nN = (int)(B.mpt / 64);
-    prm.plen = (int64_t)partial_elems;
-    if ((size_t)count * (grad ? 4 : 1) * (size_t)prm.nN > partial_elems) return GPR_ERR_ARG;
+    prm.plen = (int64_t)count * 4 * prm.nN;  // the moments follow the partial sums
+    prm.mom = partial + prm.plen;
+    prm.alpha32 = M->alpha32;
+    if ((size_t)count * (4 * (size_t)prm.nN + 8) > partial_elems) return GPR_ERR_ARG;
     prm.status = gpr_status_word();
     if (!prm.status) return GPR_ERR_CUDA;
     using C = Cfg<GPR_P_TF32X3>;
