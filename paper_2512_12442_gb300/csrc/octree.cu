@@ -22,20 +22,11 @@ namespace {
 
 constexpr int64_t kEvalChunk = 131072;  // evaluation points per pipeline pass
 
-struct EvalModel {
-    const float *X32, *alpha32;
-    int64_t m, mp;
-    int kind;
-    float ell[3];
-    float iell[3];  // 1 / ell
-    float sf2;
-};
-
 // g = (theta - mu)/sigma and grad g at each evaluation point (thread per point) from the tensor-core
 // evaluation's sums: |w|^2 and (grad) w . L^-1 d_k k per 64-column group, var = sf2 - |w|^2,
 // grad var = -2 w . L^-1 d_k k; mu and grad mu = sum_j dk_j alpha_j as float-float pairs (summed
 // error-free in the generating warps).  Without grad the gradient is 0.
-__global__ void k_eval_reduce(EvalModel E, const float *partial, int nN, bool grad, int64_t count, double theta,
+__global__ void k_eval_reduce(float sf2, const float *partial, int nN, bool grad, int64_t count, double theta,
                               float4 *out, float *moments)
 {
     const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -53,8 +44,8 @@ __global__ void k_eval_reduce(EvalModel E, const float *partial, int nN, bool gr
         if (grad) gm[dI] = mo[2 + 2 * dI] + mo[3 + 2 * dI];
     }
     const float mu = mo[0] + mo[1];
-    float var = E.sf2 - wsq;
-    const float fl = 1e-12f * E.sf2;
+    float var = sf2 - wsq;
+    const float fl = 1e-12f * sf2;
     if (!(var > fl)) var = fl;
     const float sd = sqrtf(var);
     const float gg = (float)(theta - (double)mu) / sd;
@@ -67,7 +58,7 @@ __global__ void k_eval_reduce(EvalModel E, const float *partial, int nN, bool gr
     if (moments) {  // test hook: mu, var (unfloored), grad mu, grad var
         float *m8 = moments + 8 * q;
         m8[0] = mu;
-        m8[1] = E.sf2 - wsq;
+        m8[1] = sf2 - wsq;
         for (int dI = 0; dI < 3; ++dI) {
             m8[2 + dI] = gm[dI];
             m8[5 + dI] = gv[dI];
@@ -1149,7 +1140,7 @@ struct OctTrace {
     uint8_t *leaf_out;
 };
 
-static gpr_status run_eval(gpr_model *M, const EvalModel &E, OctBuffers &B, int64_t cnt, double theta,
+static gpr_status run_eval(gpr_model *M, OctBuffers &B, int64_t cnt, double theta,
                            cudaStream_t st, bool grad = true)
 {
     {
@@ -1157,7 +1148,7 @@ static gpr_status run_eval(gpr_model *M, const EvalModel &E, OctBuffers &B, int6
         GPR_TRY(launch_tc_eval(M, B.xyz, cnt, grad, B.W, B.wlen, st));
     }
     const int nN = (int)(((M->mp + 255) / 256 * 256) / 64);
-    k_eval_reduce<<<nb(cnt, 256), 256, 0, st>>>(E, B.W, nN, grad, cnt, theta, B.ev, nullptr);
+    k_eval_reduce<<<nb(cnt, 256), 256, 0, st>>>((float)M->kp.sf2, B.W, nN, grad, cnt, theta, B.ev, nullptr);
     note_launch();
     GPR_CUDA_TRY(cudaGetLastError());
     return GPR_OK;
@@ -1409,13 +1400,6 @@ gpr_status octree_lcp(gpr_model *M, const gpr_grid *grid, double theta, int D, c
     int32_t *slot = (int32_t *)B.tmp_mean;  // reused by the leaf phase (n int32 fits in n floats)
     int64_t *clist = B.pend;                 // reused by the leaf phase (nc int64)
 
-    EvalModel E;
-    E.X32 = M->X32; E.alpha32 = M->alpha32;
-    E.m = M->m; E.mp = M->mp; E.kind = M->kp.kind; E.sf2 = (float)M->kp.sf2;
-    for (int d = 0; d < 3; ++d) {
-        E.ell[d] = (float)M->kp.ell[d];
-        E.iell[d] = (float)(1.0 / M->kp.ell[d]);
-    }
 
     GPR_CUDA_TRY(cudaMemsetAsync(B.leaf, 0, (size_t)nc, st));
     k_obs_flags<<<nb(m, 128), 128, 0, st>>>(M->mu_obs, M->var_obs, m, theta, opts->alpha, B.obs_flags);
@@ -1513,7 +1497,7 @@ gpr_status octree_lcp(gpr_model *M, const gpr_grid *grid, double theta, int D, c
                     k_lattice_points<<<nb(cnt, 256), 256, 0, st>>>(g, D, l, kd, nodes, B.pend, B.ulist, first, cnt, B.xyz);
                     note_launch();
                     // lattice values only: the start points' gradients are evaluated afresh below
-                    GPR_TRY(run_eval(M, E, B, cnt, theta, st, false));
+                    GPR_TRY(run_eval(M, B, cnt, theta, st, false));
                     k_scatter_lattice<<<nb(cnt, 256), 256, 0, st>>>(B.ev, B.ulist, first, cnt, B.lat);
                     note_launch();
                 }
@@ -1534,7 +1518,7 @@ gpr_status octree_lcp(gpr_model *M, const gpr_grid *grid, double theta, int D, c
                     int64_t cnt = nact - first < kEvalChunk ? nact - first : kEvalChunk;
                     k_start_points<<<nb(cnt, 256), 256, 0, st>>>(B.ms, act, first, cnt, B.xyz);
                     note_launch();
-                    GPR_TRY(run_eval(M, E, B, cnt, theta, st));
+                    GPR_TRY(run_eval(M, B, cnt, theta, st));
                     k_start_grad<<<nb(cnt, 256), 256, 0, st>>>(B.ev, act, first, cnt, B.ms);
                     note_launch();
                 }
@@ -1545,7 +1529,7 @@ gpr_status octree_lcp(gpr_model *M, const gpr_grid *grid, double theta, int D, c
                                                                    B.xyz, B.cvalid);
                         note_launch();
                         // the last step's gradients are never used: value only
-                        GPR_TRY(run_eval(M, E, B, cnt, theta, st, t < T - 1));
+                        GPR_TRY(run_eval(M, B, cnt, theta, st, t < T - 1));
                         k_accept<<<nb(cnt, 256), 256, 0, st>>>(B.xyz, B.cvalid, B.ev, act, first, cnt, B.ms);
                         note_launch();
                     }
@@ -1633,13 +1617,6 @@ extern "C" gpr_status gpr_eval_points(gpr_model *M, const double *xyz, int64_t c
     if (!M || !xyz || !out || count < 0 || count > kEvalChunk) return GPR_ERR_ARG;
     if (count == 0) return GPR_OK;
     cudaStream_t st = (cudaStream_t)stream;
-    EvalModel E;
-    E.X32 = M->X32; E.alpha32 = M->alpha32;
-    E.m = M->m; E.mp = M->mp; E.kind = M->kp.kind; E.sf2 = (float)M->kp.sf2;
-    for (int d = 0; d < 3; ++d) {
-        E.ell[d] = (float)M->kp.ell[d];
-        E.iell[d] = (float)(1.0 / M->kp.ell[d]);
-    }
     const size_t pe = tc_eval_partial_elems(M, count);
     float *part = nullptr;
     float4 *g4 = nullptr;
@@ -1649,7 +1626,7 @@ extern "C" gpr_status gpr_eval_points(gpr_model *M, const double *xyz, int64_t c
     gpr_status rc = launch_tc_eval(M, xyz, count, grad != 0, part, pe, st);
     if (rc == GPR_OK) {
         const int nN = (int)(((M->mp + 255) / 256 * 256) / 64);
-        k_eval_reduce<<<nb(count, 256), 256, 0, st>>>(E, part, nN, grad != 0, count, 0.0, g4, out);
+        k_eval_reduce<<<nb(count, 256), 256, 0, st>>>((float)M->kp.sf2, part, nN, grad != 0, count, 0.0, g4, out);
         note_launch();
         if (cudaGetLastError() != cudaSuccess) rc = GPR_ERR_CUDA;
     }
