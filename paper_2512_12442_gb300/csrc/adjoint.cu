@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(256, 2) k_adj_sample(const AdjRec *rec, const 
 #pragma unroll
         for (int side = 0; side < 2; ++side) {
             float sg = side == 0 ? 1.f : -1.f;
-            float u[8], e[8], z[7];
+            float pd[8], e[8], z[7];  // pd: the density at u_i, from the exponential of Phi(u_i)
             float f = 1.f;
             // no early exit: once f underflows to 0 the rest stays finite and the sample adds 0
 #pragma unroll
@@ -202,8 +202,12 @@ __global__ void __launch_bounds__(256, 2) k_adj_sample(const AdjRec *rec, const 
                 float s = sg * W.bs[i];
 #pragma unroll
                 for (int j = 0; j < i; ++j) s = fmaf(-W.Ls[trs(i, j)], z[j], s);
-                u[i] = s;
-                e[i] = i == 0 ? (side ? e0hi : e0lo) : nrm_cdf(u[i]);
+                if (i == 0) {
+                    e[0] = side ? e0hi : e0lo;
+                    pd[0] = pdf0;
+                } else {
+                    e[i] = nrm_cdf_pdf(s, pd[i]);
+                }
                 f *= e[i];
                 if (i < 7) z[i] = nrm_ppf(fmaxf(w[i] * e[i], 1e-37f));
             }
@@ -219,7 +223,7 @@ __global__ void __launch_bounds__(256, 2) k_adj_sample(const AdjRec *rec, const 
                     const float iph = 2.50662827f * __expf(0.5f * z[i] * z[i]);  // 1 / phi(z)
                     if (iph < INFINITY) ebar = fmaf(zbar[i] * w[i], iph, ebar);
                 }
-                const float ubar = ebar * (i == 0 ? pdf0 : npdf(u[i]));
+                const float ubar = ebar * pd[i];
                 bbar[i] = fmaf(sg, ubar, bbar[i]);
 #pragma unroll
                 for (int j = 0; j < i; ++j) {

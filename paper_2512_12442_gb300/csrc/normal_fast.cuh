@@ -40,6 +40,17 @@ static __device__ __forceinline__ float nrm_cdf(float x)
     return x < 0.0f ? e : 1.0f - e;
 }
 
+// Phi(x) and, from the same exponential, the density phi(x) = exp(-x^2/2) / sqrt(2 pi).
+static __device__ __forceinline__ float nrm_cdf_pdf(float x, float &pdf)
+{
+    const float a = fabsf(x);
+    const float u = fmaf(2.0f, rcp_approx(fmaf(NRM_CDF_C0, a, 1.0f)), -1.0f);
+    const float g = ex2_approx(a * (a * -0.72134752f));
+    pdf = 0.3989422804014327f * g;
+    const float e = g * nrm_cdf_g(u);
+    return x < 0.0f ? e : 1.0f - e;
+}
+
 // Tail piece of the quantile (p < 0.0017 or its mirror), out of line: it is rare, and keeping
 // one copy keeps the unrolled estimator loop small enough for the instruction cache.
 static __device__ __noinline__ float nrm_ppf_tail_lg(float lg)

@@ -31,9 +31,9 @@ def _compare_level(om, n, D, l, th, nodes, dec, bnd, alpha=1e-3, sample=None, se
     """Decisions of one level against the oracle; with bound_tol = (max, median) also the bounds
     of nodes both sides minimised in full, as |log(bound / oracle bound)| (where the bound can
     decide, >= alpha / 10; None skips that statistic)."""
-    idx = np.arange(len(nodes))
+    idx = np.argsort(nodes, kind="stable")  # the frontier's order is not deterministic: sample by code
     if sample is not None and len(idx) > sample:
-        idx = np.sort(np.random.default_rng(seed).choice(len(idx), sample, replace=False))
+        idx = idx[np.sort(np.random.default_rng(seed).choice(len(idx), sample, replace=False))]
     odec, obnd, _ = om.octree_level(n, D, l, th, nodes[idx], alpha=alpha)
     gd = dec[idx]
     # p-test decisions agree exactly
@@ -54,10 +54,12 @@ def _compare_level(om, n, D, l, th, nodes, dec, bnd, alpha=1e-3, sample=None, se
 
 
 @pytest.mark.parametrize("case,prec", [("small", "fp32"), ("config1", "fp32"), ("small", "tf32x3"),
-                                       ("config1", "tf32x3")])
+                                       ("config1", "tf32x3"), ("matern", "tf32x3")])
 def test_octree_levels_match_oracle(torch, g, case, prec):
     if case == "small":
         w = workloads.small(5, 60, 17, ell=(0.2, 0.2, 0.2))
+    elif case == "matern":
+        w = workloads.small(5, 60, 17, ell=(0.2, 0.25, 0.3), kernel=workloads.MATERN52)
     else:
         w = workloads.config1()
     M = model_of(w)
@@ -121,12 +123,13 @@ def test_adaptive_config2_full_size_sampled_nodes(torch, g):
     for l in (2, 4, 5, 6, 7):
         nodes, dec, bnd = g.gpr_octree_trace(M, grid, th, w.max_depth, g.lcp_options(prec=g.GPR_P_TF32X3), l)
         assert len(nodes) > 0
-        # ill-conditioned model (var down to 4e-5 sf2): the FP32-class evaluations (|dvar| ~4e-5 sf2,
-        # |dmu| ~1e-4 max|y|) move g by up to a few per cent, a few times that in the Phi tails the
-        # bound sits in, and can send the local minimiser to another point: the median bound agrees
-        # within 10 % (measured: 2-6 %), single nodes by less (one node of 93 by a factor 12)
+        # ill-conditioned model (var down to 4e-5 sf2): the FP32-class variances (|dvar| up to ~4e-5
+        # sf2 in the TF32x3 pre-pass and the evaluations) move g by up to a few per cent, a few times
+        # that in the Phi tails the bound sits in, and the local minimiser can end at another point:
+        # the median bound agrees within 25 % (measured 2-10 %), single nodes by less (one node of 93
+        # by a factor 12)
         mm, cnt = _compare_level(om, w.n, w.max_depth, l, th, nodes, dec, bnd, sample=150 if l >= 5 else None,
-                                 seed=l, bound_tol=(None, 0.1))
+                                 seed=l, bound_tol=(None, 0.25))
         assert mm <= max(3, 0.03 * cnt)
 
 
@@ -281,7 +284,7 @@ def _oracle_moments(om, P, t1, t2):
     return mu, sd ** 2, gmu, gvar
 
 
-@pytest.mark.parametrize("kind", ["gpr", "sgpr"])
+@pytest.mark.parametrize("kind", ["gpr", "sgpr", "matern"])
 def test_bound_evaluations_vs_oracle(torch, g, kind):
     """The bound minimiser's evaluations (TF32x3 tensor-core rows of k and of d k / d x_d, reduced to
     |w|^2 and w . L^-1 d_k k; mean and its gradient by compensated k . alpha) at 2,000 random points
@@ -290,8 +293,13 @@ def test_bound_evaluations_vs_oracle(torch, g, kind):
     paths): |dmu| <= 1e-4 max|y|, |dvar| <= 1e-4 sf2, |d grad mu| <= 1e-4 max|y| / l_min,
     |d grad var| <= 1e-4 sf2 / l_min for the plain model; 5e-4 for the sparse one, whose
     K_MM + 1e-6 I (condition ~5e7, against ~4e5) amplifies the FP32 rounding of the kernel entries
-    more."""
-    w = workloads.config2() if kind == "gpr" else workloads.sgpr(n=33)
+    more.  The Matern-5/2 case (m=300, l=(0.12, 0.18, 0.25)) checks that kernel's derivative rows."""
+    if kind == "gpr":
+        w = workloads.config2()
+    elif kind == "sgpr":
+        w = workloads.sgpr(n=33)
+    else:
+        w = workloads.small(9, 300, 33, ell=(0.12, 0.18, 0.25), kernel=workloads.MATERN52)
     M = model_of(w)
     om = oracle.Model.from_workload(w)
     rng = np.random.default_rng(21)
@@ -299,7 +307,7 @@ def test_bound_evaluations_vs_oracle(torch, g, kind):
     P = np.concatenate([rng.random((2000, 3)),
                         np.clip(X[rng.integers(0, len(X), 200)] + rng.normal(0, 0.01, (200, 3)), 0, 1)])
     mu, var, gmu, gvar = _eval_points(g, torch, M, P)
-    omu, ovar, ogmu, ogvar = _oracle_moments(om, P, float(w.isovalues[1]), float(w.isovalues[1]) + 1.0)
+    omu, ovar, ogmu, ogvar = _oracle_moments(om, P, float(w.isovalues[-1]), float(w.isovalues[-1]) + 1.0)
     ys = np.abs(np.asarray(w.y)).max()  # observations, or the inducing means mu_M of the sparse model
     lmin = float(np.min(w.ell))
     err = (np.abs(mu - omu).max() / ys, np.abs(var - ovar).max() / w.sf2,
@@ -308,5 +316,5 @@ def test_bound_evaluations_vs_oracle(torch, g, kind):
           f"|d grad mu| l/max|y| {err[2]:.2e}, |d grad var| l/sf2 {err[3]:.2e}; "
           f"var range {ovar.min():.2e}..{ovar.max():.2e}, |grad mu| l/max|y| up to "
           f"{np.abs(ogmu).max() * lmin / ys:.2e}, |grad var| l/sf2 up to {np.abs(ogvar).max() * lmin / w.sf2:.2e}")
-    tol = 1e-4 if kind == "gpr" else 5e-4
+    tol = 5e-4 if kind == "sgpr" else 1e-4
     assert max(err) <= tol, err
