@@ -35,8 +35,8 @@ static __device__ __forceinline__ float rsqrt_approx(float x)
 static __device__ __forceinline__ float nrm_cdf(float x)
 {
     const float a = fabsf(x);
-    const float u = fmaf(2.0f, rcp_approx(fmaf(NRM_CDF_C0, a, 1.0f)), -1.0f);
-    const float e = ex2_approx(a * (a * -0.72134752f)) * nrm_cdf_g(u);
+    const float t = rcp_approx(fmaf(NRM_CDF_C0, a, 1.0f));
+    const float e = ex2_approx(a * (a * -0.72134752f)) * nrm_cdf_g(t);
     return x < 0.0f ? e : 1.0f - e;
 }
 
@@ -44,10 +44,10 @@ static __device__ __forceinline__ float nrm_cdf(float x)
 static __device__ __forceinline__ float nrm_cdf_pdf(float x, float &pdf)
 {
     const float a = fabsf(x);
-    const float u = fmaf(2.0f, rcp_approx(fmaf(NRM_CDF_C0, a, 1.0f)), -1.0f);
+    const float t = rcp_approx(fmaf(NRM_CDF_C0, a, 1.0f));
     const float g = ex2_approx(a * (a * -0.72134752f));
     pdf = 0.3989422804014327f * g;
-    const float e = g * nrm_cdf_g(u);
+    const float e = g * nrm_cdf_g(t);
     return x < 0.0f ? e : 1.0f - e;
 }
 
