@@ -33,12 +33,13 @@ import workloads  # noqa: E402
 
 METRIC = "LCP grid points/s"
 # Warp instructions k_sov issues per orthant-sample (one lattice point of one orthant,
-# P(all < theta) or P(all > theta)): ncu's smsp__inst_executed.sum of the tuned launch shape on the
-# 64^3 case (2,711,838,586) over the orthant-samples the device counted for it (138,569 orthants x
-# 1600), profiles/sov_estimator_m500_grid64.txt.  The estimator is issue-bound: its roofline is the
+# P(all < theta) or P(all > theta)): ncu's smsp__inst_executed.sum of the estimator launch of the
+# default workload (50,103,618,421; one pass, the launch shapes of a shared tuning table) over the
+# orthant-samples the device counted for it (4,051,083,200), profiles/sov_estimator_m500_grid64.txt
+# (12.23 on the 64^3 case).  The estimator is issue-bound: its roofline is the
 # issue rate, 4 warp instructions per clock on each of 152 SMs at 2.07 GHz; achieved =
 # orthant-samples counted on the device x this figure / launch time.
-SOV_WARP_INST_PER_ORTHANT_SAMPLE = 12.23
+SOV_WARP_INST_PER_ORTHANT_SAMPLE = 12.37
 ISSUE_PEAK_GINST = 152 * 4 * 2.07
 # Dense tensor peaks relative to BF16 (nominal dense rates: TF32 1.1, BF16 2.25 PFLOP/s)
 TF32_OVER_BF16 = 1.1 / 2.25
