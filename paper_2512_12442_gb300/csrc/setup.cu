@@ -115,8 +115,10 @@ __global__ void k_potrf_diag(double *A, int64_t mb, int kb, int *status)
 __global__ void k_trsm_panel(double *A, int64_t mb, int kb)
 {
     __shared__ double Lk[NB][NB + 1];
+    __shared__ double rd[NB];  // 1 / L_cc: one division per column instead of one per row and column
     int64_t r0 = (int64_t)kb * NB;
     for (int t = threadIdx.x; t < NB * NB; t += blockDim.x) Lk[t / NB][t % NB] = A[(r0 + t / NB) * mb + r0 + t % NB];
+    if (threadIdx.x < NB) rd[threadIdx.x] = 1.0 / A[(r0 + threadIdx.x) * mb + r0 + threadIdx.x];
     __syncthreads();
     int64_t row = r0 + NB + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (row >= mb) return;
@@ -128,7 +130,7 @@ __global__ void k_trsm_panel(double *A, int64_t mb, int kb)
         double s = x[c];
 #pragma unroll
         for (int k = 0; k < c; ++k) s -= x[k] * Lk[c][k];
-        x[c] = s / Lk[c][c];
+        x[c] = s * rd[c];
     }
 #pragma unroll
     for (int c = 0; c < NB; ++c) A[row * mb + r0 + c] = x[c];
@@ -156,24 +158,35 @@ __global__ void k_syrk_update(double *A, int64_t mb, int kb)
     }
 }
 
-// L^-1 column by column (warp per column j): x = L^-1 e_j by forward substitution.
+// L^-1 column by column (warp per column j): x = L^-1 e_j by forward substitution in blocks of
+// 32 rows.  Lane r owns row i = 32 b + r of block b: it first sums L_ik x_k over the finished rows
+// k in [j, 32 b) on its own, then the block is solved in 32 steps, each broadcasting one new x_t
+// by a shuffle (x_i = -(sum_k L_ik x_k) / L_ii, x_j = 1 / L_jj, x_i = 0 above j).  The sequential
+// chain is 32 short steps per block instead of one warp reduction per row.  mb is a multiple of 32.
 __global__ void k_trtri_cols(const double *L, int64_t mb, double *Linv)
 {
     extern __shared__ double xs[];
-    int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    int64_t j = blockIdx.x * (int64_t)(blockDim.x / 32) + warp;
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int64_t j = blockIdx.x * (int64_t)(blockDim.x / 32) + warp;
     if (j >= mb) return;
     double *x = xs + (int64_t)warp * mb;
-    for (int64_t i = lane; i < mb; i += 32) x[i] = 0.0;
-    __syncwarp();
-    if (lane == 0) x[j] = 1.0 / L[j * mb + j];
-    __syncwarp();
-    for (int64_t i = j + 1; i < mb; ++i) {
-        double s = 0.0;
-        for (int64_t k = j + lane; k < i; k += 32) s += L[i * mb + k] * x[k];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) x[i] = -s / L[i * mb + i];
+    const int64_t b0 = j / 32, nb32 = mb / 32;
+    for (int64_t i = lane; i < 32 * b0; i += 32) x[i] = 0.0;
+    for (int64_t b = b0; b < nb32; ++b) {
+        const int64_t i = 32 * b + lane;
+        const double *Li = L + i * mb;
+        const double ri = 1.0 / Li[i];  // each lane's own row: one division per row
+        double p = 0.0;
+        for (int64_t k = j; k < 32 * b; ++k) p = fma(Li[k], x[k], p);
+        double xi = 0.0;
+        for (int t = 0; t < 32; ++t) {
+            const int64_t it = 32 * b + t;
+            double xt = it < j ? 0.0 : (it == j ? ri : -p * ri);  // lane t's value counts
+            xt = __shfl_sync(0xffffffffu, xt, t);
+            if (lane == t) xi = xt;
+            if (lane > t && it >= j) p = fma(Li[it], xt, p);
+        }
+        x[i] = xi;
         __syncwarp();
     }
     for (int64_t i = lane; i < mb; i += 32) Linv[i * mb + j] = x[i];
