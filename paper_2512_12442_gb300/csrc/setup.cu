@@ -97,10 +97,11 @@ __global__ void k_potrf_diag(double *A, int64_t mb, int kb, int *status)
             if (lane == 0) atomicCAS(status, 0, (int)GPR_ERR_NOT_PD);
             piv = 1.0;  // keep going with finite numbers; the status word reports the failure
         }
-        double ljj = sqrt(piv);
+        const double inv = rsqrt(piv);  // one reciprocal square root for the pivot and the column
+        const double ljj = piv * inv;
         __syncwarp();
         if (lane == j) S[j][j] = ljj;
-        if (lane > j) S[lane][j] /= ljj;
+        if (lane > j) S[lane][j] *= inv;
         __syncwarp();
         if (lane > j) {
             double lij = S[lane][j];
