@@ -242,6 +242,10 @@ def test_kd_tree_levels_match_oracle_and_field(torch, g):
         bad = (odec > 0) != (dec > 0)
         near = (obnd >= 1e-3 / 3) & (obnd <= 3e-3)
         assert np.all(near[bad]), (l, obnd[bad & ~near][:8], bnd[bad & ~near][:8])
+        # bounds both sides computed in full: median within 25% (FP32-class evaluations, as for the octree)
+        both0 = (odec == 0) & (dec == 0) & (obnd >= 1e-4)
+        if both0.sum() >= 5:
+            assert np.median(np.abs(np.log(bnd[both0] / obnd[both0]))) <= 0.25, l
         seen += len(nodes)
     assert seen > 1000
     a = torch.zeros((n - 1) ** 3, dtype=torch.float32, device="cuda")
