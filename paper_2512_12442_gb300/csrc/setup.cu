@@ -211,14 +211,22 @@ __global__ void k_vy(const double *Linv, int64_t mb, const double *y, int64_t m,
 __global__ void k_alpha_obs(const double *Linv, int64_t mb, const double *vy, const double *y, int64_t m,
                             double sn2, double sf2, double *alpha, double *mu_obs, double *var_obs)
 {
-    int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    // warp per column j, lanes over the rows i >= j (the loads of one lane are independent)
+    const int lane = threadIdx.x & 31;
+    const int64_t j = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     if (j >= m) return;
     double a = 0.0, q = 0.0;
-    for (int64_t i = j; i < m; ++i) {
+    for (int64_t i = j + lane; i < m; i += 32) {
         double l = Linv[i * mb + j];
         a += l * vy[i];
         q += l * l;
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        q += __shfl_xor_sync(0xffffffffu, q, o);
+    }
+    if (lane != 0) return;
     alpha[j] = a;
     mu_obs[j] = y[j] - sn2 * a;
     double v = sn2 - sn2 * sn2 * q, fl = 1e-12 * sf2;
@@ -271,7 +279,7 @@ static void chol_blocked(double *A, int64_t mb, int *status, cudaStream_t st)
         note_launch();
         int64_t rows = mb - (int64_t)(kb + 1) * NB;
         if (rows > 0) {
-            k_trsm_panel<<<nblk(rows, 128), 128, 0, st>>>(A, mb, kb);
+            k_trsm_panel<<<nblk(rows, 32), 32, 0, st>>>(A, mb, kb);  // a warp per CTA: more SMs share the FP64 work
             note_launch();
             unsigned T = (unsigned)(nbk - kb - 1);
             k_syrk_update<<<dim3(T, T), 256, 0, st>>>(A, mb, kb);
@@ -362,7 +370,7 @@ extern "C" gpr_status gpr_model_create(const double *obs_xyz, const double *y, i
     trtri(A, mb, M->Linv, st);
     k_vy<<<nblk(mp, 8), 256, 0, st>>>(M->Linv, mb, M->y, m, M->vy, mp);
     note_launch();
-    k_alpha_obs<<<nblk(m, 128), 128, 0, st>>>(M->Linv, mb, M->vy, M->y, m, noise_var, signal_var, M->alpha,
+    k_alpha_obs<<<nblk(m * 32, 256), 256, 0, st>>>(M->Linv, mb, M->vy, M->y, m, noise_var, signal_var, M->alpha,
                                                M->mu_obs, M->var_obs);
     note_launch();
     k_operands<<<nblk(mp * mp, 256), 256, 0, st>>>(M->Linv, mb, m, mp, M->BT64, M->BT32, M->vy, M->vy32, M->alpha, M->alpha_ff, M->X, M->X32, M->alpha32);
