@@ -115,6 +115,26 @@ __device__ __forceinline__ double bound_of(int sides, double dcount, double glo,
     return -expm1(dcount * lBhi);
 }
 
+// The same in FP32, for bounds from FP32-class values of g (the per-point table and the tensor-core
+// evaluations): FP64 erfc, log and expm1 per node cost the FP64 pipe more than the rest of those
+// kernels, and add no accuracy to FP32 inputs.  Below Phi = 1e-37 the leading asymptotic term.
+__device__ __forceinline__ float log_norm_cdf32(float gg)
+{
+    if (gg >= 0.0f) return log1pf(-0.5f * erfcf(gg * 0.70710678f));
+    const float c = 0.5f * erfcf(-gg * 0.70710678f);
+    if (c > 1e-37f) return logf(c);
+    return -0.5f * gg * gg - logf(-gg * 2.5066283f);
+}
+
+__device__ __forceinline__ float bound_of32(int sides, float dcount, float glo, float ghi)
+{
+    const float lBlo = (sides & 1) ? log_norm_cdf32(glo) : -INFINITY;
+    const float lBhi = (sides & 2) ? log_norm_cdf32(ghi) : -INFINITY;
+    if (sides == 3) return -expm1f(dcount * lBlo) - expf(dcount * lBhi);
+    if (sides == 1) return -expm1f(dcount * lBlo);
+    return -expm1f(dcount * lBhi);
+}
+
 // Observation flags for the p-test: bit0 = P(Y_i < theta) > alpha, bit1 = P(Y_i > theta) > alpha.
 __global__ void k_obs_flags(const double *mu_obs, const double *var_obs, int64_t m, double theta, double alpha,
                             uint8_t *flags)
@@ -265,9 +285,8 @@ __global__ void k_small_bound(GridDev g, int D, int l, int kd, const int64_t *no
                 gmin = fminf(gmin, gg);
                 gmax = fmaxf(gmax, gg);
             }
-    const double glo = (double)gmin, ghi = -(double)gmax;
-    double dcount = (double)((G.p1[0] - G.p0[0] + 1) * (G.p1[1] - G.p0[1] + 1) * (G.p1[2] - G.p0[2] + 1));
-    double bnd = bound_of(sides[q], dcount, glo, ghi);
+    const float dcount = (float)((G.p1[0] - G.p0[0] + 1) * (G.p1[1] - G.p0[1] + 1) * (G.p1[2] - G.p0[2] + 1));
+    const double bnd = (double)bound_of32(sides[q], dcount, gmin, -gmax);
     bound[q] = bnd;
     decision[q] = bnd > alpha ? 2 : 0;
 }
@@ -472,14 +491,14 @@ __global__ void k_large_bound(GridDev g, int D, int l, int kd, const int64_t *no
     const int64_t q = act ? act[t] / 2 : t;
     int64_t node = pend[q];
     Geom G = node_geom(g, D, l, kd, nodes[node]);
-    double dcount = (double)((G.p1[0] - G.p0[0] + 1) * (G.p1[1] - G.p0[1] + 1) * (G.p1[2] - G.p0[2] + 1));
-    double bnd = bound_of(sides[node], dcount, (double)ms[q].g[0], (double)ms[q].g[1]);
+    const float dcount = (float)((G.p1[0] - G.p0[0] + 1) * (G.p1[1] - G.p0[1] + 1) * (G.p1[2] - G.p0[2] + 1));
+    const double bnd = (double)bound_of32(sides[node], dcount, ms[q].g[0], ms[q].g[1]);
     bound[node] = bnd;
     decision[node] = bnd > alpha ? 2 : 0;
     if (active) {
         for (int sd = 0; sd < 2; ++sd) {
             const bool need = bnd <= alpha && (sides[node] & (1 << sd)) &&
-                              dcount * log_norm_cdf((double)ms[q].g[sd]) > -69.0;  // B^d > 1e-30
+                              dcount * log_norm_cdf32(ms[q].g[sd]) > -69.0f;  // B^d > 1e-30
             active[2 * q + sd] = need ? 1 : 0;
         }
     }
