@@ -445,12 +445,23 @@ __global__ void k_mean_ff(const float2 *Tff, int64_t off1, int64_t off2, int64_t
     if (p < 0 || p >= nx * ny * (int64_t)g.n[2]) return;
     int64_t gx = p % nx, gy = (p / nx) % ny, gz = p / (nx * ny);
     const float2 *tx = Tff + gx * mp, *ty = Tff + off1 + gy * mp, *tz = Tff + off2 + gz * mp;
-    FF acc = {0.f, 0.f};
-    for (int64_t j = lane; j < m; j += 32) {
-        float2 a = tx[j], b = ty[j], c = tz[j], al = aff[j];
-        FF k = ff_mul(ff_mul(FF{a.x, a.y}, FF{b.x, b.y}), FF{c.x, c.y});
+    // two independent accumulation chains (more loads and float-float products in flight)
+    FF acc = {0.f, 0.f}, acc2 = {0.f, 0.f};
+    int64_t j = lane;
+    for (; j + 32 < m; j += 64) {
+        const float2 a = tx[j], b = ty[j], c = tz[j], al = aff[j];
+        const float2 a2 = tx[j + 32], b2 = ty[j + 32], c2 = tz[j + 32], al2 = aff[j + 32];
+        const FF k = ff_mul(ff_mul(FF{a.x, a.y}, FF{b.x, b.y}), FF{c.x, c.y});
+        const FF k2 = ff_mul(ff_mul(FF{a2.x, a2.y}, FF{b2.x, b2.y}), FF{c2.x, c2.y});
+        acc = ff_add(acc, ff_mul(k, FF{al.x, al.y}));
+        acc2 = ff_add(acc2, ff_mul(k2, FF{al2.x, al2.y}));
+    }
+    if (j < m) {
+        const float2 a = tx[j], b = ty[j], c = tz[j], al = aff[j];
+        const FF k = ff_mul(ff_mul(FF{a.x, a.y}, FF{b.x, b.y}), FF{c.x, c.y});
         acc = ff_add(acc, ff_mul(k, FF{al.x, al.y}));
     }
+    acc = ff_add(acc, acc2);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         FF t = {__shfl_xor_sync(0xffffffffu, acc.h, o), __shfl_xor_sync(0xffffffffu, acc.l, o)};
