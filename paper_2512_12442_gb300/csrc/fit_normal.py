@@ -79,7 +79,8 @@ def horner(coeffs, var):
     return expr
 
 
-def main():
+def main(path=None):
+    """Writes the header (to `path`, default normal_approx.h beside this script)."""
     c = cdf_coeffs()
     (_, _, p0), (m1, h1, p1) = ppf_coeffs()
     r2 = np.sqrt(2.0)
@@ -100,7 +101,7 @@ def main():
         "    return " + horner(p1, "v") + ";",
         "}",
     ]
-    with open(os.path.join(HERE, "normal_approx.h"), "w") as f:
+    with open(path or os.path.join(HERE, "normal_approx.h"), "w") as f:
         f.write("\n".join(lines) + "\n")
 
 
