@@ -112,6 +112,27 @@ def test_adaptive_field_vs_dense_and_oracle(torch, g, case):
     assert np.sqrt(np.mean((a - d) ** 2)) < 2e-3
 
 
+@pytest.mark.parametrize("m,n", [(1, 2), (1, 5), (3, 3), (3, 9)])
+def test_adaptive_degenerate_models_and_grids(torch, g, m, n):
+    """One or three observations, grids of 1, 8, 64 and 512 cells (max depth 0 .. 3): the adaptive
+    field equals the dense field on the GPU's S and 0 elsewhere, and the oracle's adaptive field
+    within 1e-4 where both keep the cell (the evaluations and the bound run on padded 64-column
+    operands with m = 1)."""
+    w = workloads.small(50 + m, m, n, ell=(0.4, 0.5, 0.6))
+    M = model_of(w)
+    om = oracle.Model.from_workload(w)
+    th = float(np.median(w.y)) if m > 1 else float(w.y[0]) + 0.05
+    D = w.max_depth
+    a, d, sa, _ = _fields(g, torch, M, n, D, th)
+    keep = a != 0
+    assert np.array_equal(a[keep], d[keep])
+    of, _, _ = om.lcp_adaptive(n, D, th)
+    both = keep & (of != 0)
+    if both.any():
+        assert np.abs(a[both] - of[both]).max() <= 1e-4
+    assert sa["leaf_cells"] <= (n - 1) ** 3
+
+
 def test_adaptive_config2_full_size_sampled_nodes(torch, g):
     """Paper-scale field (m=500, 128^3, D=7): sampled nodes of the deepest four levels against the
     oracle's per-node decision (each node's decision depends only on the node)."""
