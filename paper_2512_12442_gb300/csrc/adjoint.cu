@@ -998,6 +998,7 @@ extern "C" gpr_status gpr_lcp_backward(gpr_model *M, const gpr_grid *grid, doubl
                                        const gpr_lcp_options *opts, const float *dL_dlcp, double *dL_dy,
                                        double *dL_dloglen, void *stream)
 {
+    TraceRange trace_("gpr_lcp_backward");
     if (!M || !grid_valid(grid) || !opts_valid(opts) || !dL_dlcp || !dL_dy || !dL_dloglen || !isfinite(isovalue))
         return GPR_ERR_ARG;
     if (opts->est != GPR_EST_SOV_QMC) return GPR_ERR_UNSUPPORTED;  // the indicator MC has no useful gradient
@@ -1009,6 +1010,7 @@ extern "C" gpr_status gpr_lcp_backward_adaptive(gpr_model *M, const gpr_grid *gr
                                                 int32_t max_depth, const gpr_lcp_options *opts, const float *dL_dlcp,
                                                 double *dL_dy, double *dL_dloglen, void *stream)
 {
+    TraceRange trace_("gpr_lcp_backward_adaptive");
     if (!M || !grid_valid(grid) || !opts_valid(opts) || !dL_dlcp || !dL_dy || !dL_dloglen || !isfinite(isovalue))
         return GPR_ERR_ARG;
     if (max_depth < 0 || max_depth > 20) return GPR_ERR_ARG;

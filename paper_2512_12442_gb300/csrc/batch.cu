@@ -59,6 +59,7 @@ extern "C" gpr_status gpr_lcp_adaptive_batched(gpr_model *const *models, const g
                                                const gpr_lcp_options *opts, float *const *lcps,
                                                gpr_adaptive_stats *stats, void *stream)
 {
+    TraceRange trace_("gpr_lcp_adaptive_batched");
     if (count < 0 || !opts_valid(opts)) return GPR_ERR_ARG;
     if (count == 0) return GPR_OK;
     if (!models || !grids || !isovalues || !max_depths || !lcps) return GPR_ERR_ARG;
@@ -191,7 +192,10 @@ extern "C" gpr_status gpr_lcp_adaptive_batched(gpr_model *const *models, const g
     // one persistent estimator launch over every field's records
     int64_t nres = reserved.load();
     if (nres > cap) nres = cap;
-    if (nres > 0) launch_estimator(P.recs, P.nrec, nres, lcp_opts(opts, 0.0), st);
+    if (nres > 0) {
+        TraceRange est("batched_estimator");
+        launch_estimator(P.recs, P.nrec, nres, lcp_opts(opts, 0.0), st);
+    }
     GPR_CUDA_TRY(cudaGetLastError());
     if (!P.done) GPR_CUDA_TRY(cudaEventCreateWithFlags(&P.done, cudaEventDisableTiming));
     GPR_CUDA_TRY(cudaEventRecord(P.done, st));

@@ -123,6 +123,7 @@ static const size_t kWBudget = (size_t)4 << 30;  // bytes of W rows held at once
 extern "C" gpr_status gpr_reconstruct_dense(gpr_model *M, const gpr_grid *grid, gpr_precision prec, void *mean,
                                             void *var, void *cov13, void *stream)
 {
+    TraceRange trace_("gpr_reconstruct_dense");
     if (!M || !grid_valid(grid) || !mean || !var) return GPR_ERR_ARG;
     if (prec < GPR_P_FP64 || prec > GPR_P_BF16X3) return GPR_ERR_ARG;
     cudaStream_t st = (cudaStream_t)stream;
@@ -245,6 +246,7 @@ __global__ void k_fill_slot(const int64_t *idx, int64_t count, int64_t npts, int
 extern "C" gpr_status gpr_stats_points(gpr_model *M, const gpr_grid *grid, const int64_t *point_idx, int64_t count,
                                        double *stats, void *stream)
 {
+    TraceRange trace_("gpr_stats_points");
     if (!M || !grid_valid(grid) || count < 0 || (count > 0 && (!point_idx || !stats))) return GPR_ERR_ARG;
     if (count == 0) return GPR_OK;
     cudaStream_t st = (cudaStream_t)stream;
@@ -304,6 +306,7 @@ extern "C" gpr_status gpr_cell_lcp_from_stats(const gpr_grid *grid, const double
                                               const gpr_lcp_options *opts, const int64_t *cell_idx, int64_t count,
                                               float *lcp, void *stream)
 {
+    TraceRange trace_("gpr_cell_lcp_from_stats");
     if (!grid_valid(grid) || !stats15 || !lcp || !opts_valid(opts) || !isfinite(isovalue)) return GPR_ERR_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     GridDev g = make_grid(grid);
@@ -330,6 +333,7 @@ void prepass_margins(const gpr_model *M, double &mv, double &mm)
 extern "C" gpr_status gpr_lcp_dense(gpr_model *M, const gpr_grid *grid, double isovalue, const gpr_lcp_options *opts,
                                     float *lcp, gpr_adaptive_stats *stats, void *stream)
 {
+    TraceRange trace_("gpr_lcp_dense");
     if (!M || !grid_valid(grid) || !lcp || !opts_valid(opts) || !isfinite(isovalue)) return GPR_ERR_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     GridDev g = make_grid(grid);

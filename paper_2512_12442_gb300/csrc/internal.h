@@ -350,8 +350,19 @@ gpr_status lcp_from_kept_cells(gpr_model *M, const GridDev &g, const double *T64
 
 // ---- tracing (profile.cu)
 void note_launch(int n = 1);
+// RAII host range on the NVTX timeline (a no-op unless a tool such as ncu or nsys is attached):
+// one per C-ABI call and per phase, so a capture can be filtered by phase.  end() closes it early.
+struct TraceRange {
+    bool open;
+    explicit TraceRange(const char *name);
+    ~TraceRange() { end(); }
+    void end();
+    TraceRange(const TraceRange &) = delete;
+    TraceRange &operator=(const TraceRange &) = delete;
+};
 // RAII scope: records CUDA events around the enclosed launches when profiling is on, and adds
-// `units` (rows, points: the work the launches process) to the scope's total.
+// `units` (rows, points: the work the launches process) to the scope's total.  It also opens an
+// NVTX range of the same name.
 struct ProfScope {
     const char *name;
     cudaStream_t st;

@@ -1443,6 +1443,7 @@ gpr_status octree_lcp(gpr_model *M, const gpr_grid *grid, double theta, int D, c
     int64_t count = 1;
     int cur = 0;
     if (stats) memset(stats, 0, sizeof *stats);
+    TraceRange levels("algorithm1_levels");
     for (int l = 0; l <= last && count > 0; ++l) {
         const int64_t *nodes = B.front[cur];
         const int64_t s = axis_extent(D, l, kd, 2);  // the node's largest extent
@@ -1587,6 +1588,7 @@ gpr_status octree_lcp(gpr_model *M, const gpr_grid *grid, double theta, int D, c
         count = (int64_t)hc[0];
         cur = 1 - cur;
     }
+    levels.end();
     if (trace) {
         if (trace->leaf_out)
             GPR_CUDA_TRY(cudaMemcpyAsync(trace->leaf_out, B.leaf, (size_t)nc, cudaMemcpyDeviceToDevice, st));
@@ -1595,6 +1597,7 @@ gpr_status octree_lcp(gpr_model *M, const gpr_grid *grid, double theta, int D, c
     int64_t leaf_cells = 0, rp = 0, est = 0;
     gpr_adaptive_stats tmp;
     memset(&tmp, 0, sizeof tmp);
+    TraceRange leaf("leaf_lcp");
     GPR_TRY(lcp_from_kept_cells(M, g, T64, B.leaf, pflag, B.plist, slot, clist, B.cscr, B.csb, lcp_opts(opts, theta),
                                 lcp, &tmp, st));
     leaf_cells = tmp.leaf_cells;
@@ -1612,6 +1615,7 @@ extern "C" gpr_status gpr_lcp_adaptive(gpr_model *M, const gpr_grid *grid, doubl
                                        const gpr_lcp_options *opts, float *lcp, gpr_adaptive_stats *stats,
                                        void *stream)
 {
+    TraceRange trace_("gpr_lcp_adaptive");
     if (!M || !grid_valid(grid) || !lcp || !opts_valid(opts) || !isfinite(isovalue)) return GPR_ERR_ARG;
     if (max_depth < 0 || max_depth > 20) return GPR_ERR_ARG;
     for (int d = 0; d < 3; ++d)
@@ -1633,6 +1637,7 @@ gpr_status octree_leaf_mask(gpr_model *M, const gpr_grid *grid, double theta, in
 extern "C" gpr_status gpr_eval_points(gpr_model *M, const double *xyz, int64_t count, int32_t grad, float *out,
                                       void *stream)
 {
+    TraceRange trace_("gpr_eval_points");
     if (!M || !xyz || !out || count < 0 || count > kEvalChunk) return GPR_ERR_ARG;
     if (count == 0) return GPR_OK;
     cudaStream_t st = (cudaStream_t)stream;
@@ -1658,6 +1663,7 @@ extern "C" gpr_status gpr_octree_trace(gpr_model *M, const gpr_grid *grid, doubl
                                        const gpr_lcp_options *opts, int32_t level, int64_t *nodes, int8_t *decision,
                                        double *bound, int64_t capacity, int64_t *count, void *stream)
 {
+    TraceRange trace_("gpr_octree_trace");
     if (!M || !grid_valid(grid) || !opts_valid(opts) || !nodes || !decision || !bound || !count) return GPR_ERR_ARG;
     if (max_depth < 0 || max_depth > 20 || level < 0 || level > (opts->tree == GPR_TREE_KD ? 3 : 1) * max_depth)
         return GPR_ERR_ARG;

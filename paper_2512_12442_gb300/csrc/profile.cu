@@ -1,7 +1,10 @@
 // Phase timing and launch counting (tracing support): when enabled, CUDA events are
 // recorded on the launching stream around each instrumented kernel, and launches of the
-// library's own kernels are counted.
+// library's own kernels are counted.  Every instrumented scope and every C-ABI call also opens
+// an NVTX range (header-only NVTX v3: without an attached tool each call is a branch).
 #include <string.h>
+
+#include <nvtx3/nvToolsExt.h>
 
 #include <map>
 #include <mutex>
@@ -86,9 +89,18 @@ void note_launch(int n)
     launches += n;
 }
 
+TraceRange::TraceRange(const char *name) : open(true) { nvtxRangePushA(name); }
+
+void TraceRange::end()
+{
+    if (open) nvtxRangePop();
+    open = false;
+}
+
 ProfScope::ProfScope(const char *name_, cudaStream_t st_, double units_)
     : name(name_), st(st_), active(false), units(units_)
 {
+    nvtxRangePushA(name_);
     std::lock_guard<std::mutex> g(mu);
     if (!enabled) return;
     active = true;
@@ -99,6 +111,7 @@ ProfScope::ProfScope(const char *name_, cudaStream_t st_, double units_)
 
 ProfScope::~ProfScope()
 {
+    nvtxRangePop();
     if (!active) return;
     std::lock_guard<std::mutex> g(mu);
     cudaEventRecord((cudaEvent_t)b, st);

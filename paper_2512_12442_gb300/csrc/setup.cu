@@ -302,6 +302,7 @@ extern "C" gpr_status gpr_model_create(const double *obs_xyz, const double *y, i
                                        const double length_scales[3], double signal_var, double noise_var,
                                        void *stream, gpr_model **out)
 {
+    TraceRange trace_("gpr_model_create");
     if (!out) return GPR_ERR_ARG;
     *out = nullptr;
     if (!obs_xyz || !y || !length_scales || m < 1 || m > 8192) return GPR_ERR_ARG;
@@ -489,6 +490,7 @@ extern "C" gpr_status gpr_model_create_sgpr(const double *inducing_xyz, const do
                                             int64_t m, gpr_kernel kernel, const double length_scales[3],
                                             double signal_var, double kmm_jitter, void *stream, gpr_model **out)
 {
+    TraceRange trace_("gpr_model_create_sgpr");
     if (!out) return GPR_ERR_ARG;
     *out = nullptr;
     if (!inducing_xyz || !mu_M || !A_M || !length_scales || m < 1 || m > 8192) return GPR_ERR_ARG;
