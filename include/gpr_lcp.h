@@ -367,7 +367,10 @@ gpr_status gpr_sync(void *stream);
 /* ---- Tracing (no counterpart in the paper; the paper reports per-phase wall time,
  * Sec. 6.2).  When enabled, the library records CUDA events on the launching stream
  * around its main kernels, grouped by name ("w64", "meanvar32", "stats_from_w64",
- * "cell_prep", "sov", "mc", "classify", ...). */
+ * "cell_prep", "sov", "mc", "classify", ...).  Independently of this switch, every call
+ * below that computes opens an NVTX range named after itself, with nested ranges for its
+ * phases ("algorithm1_levels", "leaf_lcp", "batched_estimator" and the group names above),
+ * for a profiler attached through NVTX (a no-op otherwise). */
 void gpr_profile_enable(int on);
 /* Clears the accumulated times and the launch counter. */
 void gpr_profile_reset(void);
