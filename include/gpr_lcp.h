@@ -71,8 +71,21 @@ typedef enum {
  *                     1 - prod_c P(Y_c < theta) - prod_c P(Y_c > theta)
  *   GPR_EST_EDGE_MAX  Pothkow et al.'s approximation: the largest edge-crossing probability
  *                     1 - P(Y_i < theta, Y_j < theta) - P(Y_i > theta, Y_j > theta) over the 12
- *                     cell edges, bivariate normal probabilities by Owen's T function */
-typedef enum { GPR_EST_SOV_QMC = 0, GPR_EST_MC = 1, GPR_EST_INDEP = 2, GPR_EST_EDGE_MAX = 3 } gpr_estimator;
+ *                     cell edges, bivariate normal probabilities by Owen's T function
+ *   GPR_EST_SOV_ORDERED  GPR_EST_SOV_QMC with each orthant's corners taken in ascending order
+ *                     of their standardised thresholds s (theta - mu_c) / sigma_c (s = +1 for
+ *                     all-below, -1 for all-above; ties by corner index; the order is decided
+ *                     in FP64), so each orthant has its own Cholesky factor.  Same lattice, same
+ *                     cost per sample; on strongly correlated corners far more accurate at the
+ *                     same sample count.  Forward only: the backward calls, and the
+ *                     allocation-free entry point, return GPR_ERR_UNSUPPORTED for it. */
+typedef enum {
+    GPR_EST_SOV_QMC = 0,
+    GPR_EST_MC = 1,
+    GPR_EST_INDEP = 2,
+    GPR_EST_EDGE_MAX = 3,
+    GPR_EST_SOV_ORDERED = 4
+} gpr_estimator;
 
 /* Arithmetic of the FP64-class reconstruction of the LCP cells' corners.
  * GPR_EXACT_AUTO: BF16 tensor cores with an error-free split of both operands into

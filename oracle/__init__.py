@@ -24,6 +24,7 @@ EST_SOV = 0
 EST_MC = 1
 EST_INDEP = 2
 EST_EDGE = 3
+EST_SOV_ORD = 4
 
 _lib = None
 _dp = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")

@@ -493,6 +493,36 @@ static void chol_floor(const double *S, int d, double floor_, double *L)
 #define EST_MC 1
 #define EST_INDEP 2
 #define EST_EDGE 3
+#define EST_SOV_ORD 4
+
+/* One orthant, P(s (theta - Y_c) > 0 for every corner c) with s = +1 (all below) or -1 (all
+ * above), by the lattice rule of or_sov_orthant with the variables taken in ascending order of
+ * their standardised thresholds s (theta - mu_c) / sigma_c (ties: lower index first), the
+ * ordering Genz and Bretz recommend without its conditional updates.  The corner most likely to
+ * leave the orthant comes first, so its factor, exact and independent of the sample, carries
+ * most of the probability of strongly correlated corners and the lattice sees a flat integrand.
+ * Sj: jittered covariance; floor_: the Cholesky pivot floor. */
+static double sov_orthant_ordered(int d, const double *Sj, const double *mu, double theta, double s, double floor_,
+                                  int64_t N, const uint32_t *sh)
+{
+    int perm[16];
+    double key[16], Sp[256], Lp[256], bp[16];
+    for (int i = 0; i < d; ++i) {
+        key[i] = (s * (theta - mu[i])) / sqrt(Sj[i * d + i]);
+        perm[i] = i;
+    }
+    for (int i = 1; i < d; ++i) { /* insertion sort, stable */
+        int v = perm[i], j = i;
+        while (j > 0 && key[v] < key[perm[j - 1]]) { perm[j] = perm[j - 1]; --j; }
+        perm[j] = v;
+    }
+    for (int a = 0; a < d; ++a) {
+        bp[a] = s * (theta - mu[perm[a]]);
+        for (int b = 0; b < d; ++b) Sp[a * d + b] = Sj[perm[a] * d + perm[b]];
+    }
+    chol_floor(Sp, d, floor_, Lp);
+    return or_sov_orthant(d, Lp, bp, N, sh);
+}
 
 /* P(X1 < a, X2 < b) for a standard bivariate normal with correlation r (|r| < 1): the
  * integral over x1 < a of phi(x1) P(X2 < b | X1 = x1) = phi(x1) Phi((b - r x1) / sqrt(1 - r^2)),
@@ -551,7 +581,9 @@ double or_bvn_lower(double a, double b, double r)
  * 1 - prod_c P(Y_c < theta) - prod_c P(Y_c > theta).
  * est = EST_EDGE: Pothkow et al.'s approximation (Sec. 2.2, Sec. 9): the largest
  * crossing probability 1 - P(Y_i < theta, Y_j < theta) - P(Y_i > theta, Y_j > theta)
- * over the cell's edges (corner pairs i, j = i ^ 2^a; 12 for d = 8). */
+ * over the cell's edges (corner pairs i, j = i ^ 2^a; 12 for d = 8).
+ * est = EST_SOV_ORD: EST_SOV with each orthant's variables reordered
+ * (sov_orthant_ordered); the same lattice shifts. */
 double or_cell_lcp(int d, const double *mu, const double *S, double theta, int est, int64_t N,
                    uint64_t seed, uint64_t cell, double tau, double skip_eps)
 {
@@ -597,6 +629,13 @@ double or_cell_lcp(int d, const double *mu, const double *S, double theta, int e
                 if (pe > best) best = pe;
             }
         return best;
+    }
+    if (est == EST_SOV_ORD) {
+        uint32_t sh[16];
+        for (int i = 0; i < d - 1; ++i) sh[i] = (uint32_t)(or_splitmix64(seed, (uint64_t)cell * 8 + i + 1) >> 32);
+        double v = 1.0 - sov_orthant_ordered(d, Sj, mu, theta, 1.0, 1e-3 * jit, N, sh) -
+                   sov_orthant_ordered(d, Sj, mu, theta, -1.0, 1e-3 * jit, N, sh);
+        return v < 0.0 ? 0.0 : (v > 1.0 ? 1.0 : v);
     }
     chol_floor(Sj, d, 1e-3 * jit, L);
     double p_lo, p_hi;

@@ -12,7 +12,7 @@ from ._lib import AdaptiveStatsC, GridC, LcpOptionsC, load
 
 GPR_K_SE, GPR_K_MATERN52 = 0, 1
 GPR_P_FP64, GPR_P_FP32, GPR_P_TF32, GPR_P_TF32X3, GPR_P_BF16, GPR_P_BF16X3 = range(6)
-GPR_EST_SOV_QMC, GPR_EST_MC, GPR_EST_INDEP, GPR_EST_EDGE_MAX = 0, 1, 2, 3
+GPR_EST_SOV_QMC, GPR_EST_MC, GPR_EST_INDEP, GPR_EST_EDGE_MAX, GPR_EST_SOV_ORDERED = 0, 1, 2, 3, 4
 GPR_EXACT_AUTO, GPR_EXACT_FP64 = 0, 1
 GPR_TREE_OCTREE, GPR_TREE_KD = 0, 1
 GPR_OK, GPR_ERR_ARG, GPR_ERR_NOT_PD, GPR_ERR_CUDA, GPR_ERR_OOM, GPR_ERR_TIMEOUT, GPR_ERR_UNSUPPORTED = range(7)

@@ -119,14 +119,17 @@ extern "C" gpr_status gpr_lcp_adaptive_batched(gpr_model *const *models, const g
     const int W = worker_count((int)jobs.size());
     if ((int)P.arenas.size() < W) P.arenas.resize(W);
 
-    // the shared record buffer (records of fields that do not fit estimate on their own stream)
+    // the shared record buffer (records of fields that do not fit estimate on their own stream);
+    // the ordered estimator keeps a second factor per cell, in a parallel array after the first
+    const bool two = opts->est == GPR_EST_SOV_ORDERED;
+    const size_t rb = record_bytes() * (two ? 2 : 1);
     int64_t cap = total_cells;
-    if ((size_t)cap * record_bytes() > kRecordBudget) cap = (int64_t)(kRecordBudget / record_bytes());
+    if ((size_t)cap * rb > kRecordBudget) cap = (int64_t)(kRecordBudget / rb);
     if (const char *e = getenv("GPR_BATCH_RECORD_CAP")) {  // tests of the per-field fallback
         int64_t v = atoll(e);
         if (v >= 0 && v < cap) cap = v;
     }
-    const size_t want = (size_t)cap * record_bytes();
+    const size_t want = (size_t)cap * rb;
     // the previous call's estimator (maybe on another stream) still reads the buffer
     if (P.done) GPR_CUDA_TRY(cudaStreamWaitEvent(st, P.done, 0));
     if (P.rec_bytes < want) {
@@ -139,7 +142,8 @@ extern "C" gpr_status gpr_lcp_adaptive_batched(gpr_model *const *models, const g
     }
     if (!P.nrec) GPR_CUDA_TRY(cudaMalloc(&P.nrec, 2 * sizeof(unsigned long long)));  // count, estimator ticket
     std::atomic<int64_t> reserved{0};
-    RecordSink sink{P.recs, P.nrec, cap, &reserved};
+    void *recs2 = two ? (void *)((char *)P.recs + (size_t)cap * record_bytes()) : nullptr;
+    RecordSink sink{P.recs, P.nrec, cap, &reserved, recs2};
 
     GPR_CUDA_TRY(cudaMemsetAsync(P.nrec, 0, sizeof(unsigned long long), st));
     cudaEvent_t fork;
@@ -194,7 +198,7 @@ extern "C" gpr_status gpr_lcp_adaptive_batched(gpr_model *const *models, const g
     if (nres > cap) nres = cap;
     if (nres > 0) {
         TraceRange est("batched_estimator");
-        launch_estimator(P.recs, P.nrec, nres, lcp_opts(opts, 0.0), st);
+        launch_estimator(P.recs, recs2, P.nrec, nres, lcp_opts(opts, 0.0), st);
     }
     GPR_CUDA_TRY(cudaGetLastError());
     if (!P.done) GPR_CUDA_TRY(cudaEventCreateWithFlags(&P.done, cudaEventDisableTiming));

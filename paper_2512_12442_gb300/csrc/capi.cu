@@ -49,7 +49,8 @@ extern "C" gpr_status gpr_sync(void *stream)
 bool est_opts_valid(const gpr_lcp_options *o)
 {
     if (!o) return false;
-    if (o->est != GPR_EST_SOV_QMC && o->est != GPR_EST_MC && o->est != GPR_EST_INDEP && o->est != GPR_EST_EDGE_MAX)
+    if (o->est != GPR_EST_SOV_QMC && o->est != GPR_EST_MC && o->est != GPR_EST_INDEP && o->est != GPR_EST_EDGE_MAX &&
+        o->est != GPR_EST_SOV_ORDERED)
         return false;
     if (o->n_samples < 1 || o->n_samples > (1 << 24)) return false;
     if (!(o->jitter >= 0.0) || !(o->skip_eps >= 0.0) || !isfinite(o->jitter) || !isfinite(o->skip_eps)) return false;
@@ -313,7 +314,7 @@ extern "C" gpr_status gpr_cell_lcp_from_stats(const gpr_grid *grid, const double
     if (!cell_idx) count = g.ncells();
     if (count < 0 || count > g.ncells()) return GPR_ERR_ARG;
     if (count == 0) return GPR_OK;
-    size_t bytes = cell_lcp_scratch_bytes(count);
+    size_t bytes = cell_lcp_scratch_bytes(count, opts->est);
     GPR_TRY(scratch_reserve(bytes, st));
     return run_cell_lcp(g, stats15, nullptr, cell_idx, count, lcp_opts(opts, isovalue), lcp, cell_idx != nullptr,
                         g_scratch, g_scratch_bytes, nullptr, st);
@@ -345,17 +346,17 @@ extern "C" gpr_status gpr_lcp_dense(gpr_model *M, const gpr_grid *grid, double i
         // every point in FP64, every cell estimated (no pre-pass)
         size_t rows = slab_rows(g, M->mp, sizeof(double), kWBudget);
         size_t bytes = Carver::round(te * sizeof(double)) + Carver::round(rows * M->mp * sizeof(double)) +
-                       Carver::round((size_t)n * 15 * sizeof(double)) + cell_lcp_scratch_bytes(nc) + 2048;
+                       Carver::round((size_t)n * 15 * sizeof(double)) + cell_lcp_scratch_bytes(nc, lo.est) + 2048;
         GPR_TRY(ws_reserve(M, 0, bytes, st));
         Carver cv{(char *)ws_ptr(M, 0)};
         double *T64 = cv.take<double>(te);
         double *W = cv.take<double>(rows * M->mp);
         double *S15 = cv.take<double>((size_t)n * 15);
-        void *scr = cv.take<char>(cell_lcp_scratch_bytes(nc));
+        void *scr = cv.take<char>(cell_lcp_scratch_bytes(nc, lo.est));
         GPR_TRY(build_tables(M, g, T64, nullptr, st));
         GPR_TRY(dense_stats64(M, g, T64, W, rows, S15, nullptr, nullptr, nullptr, st));
         int64_t nest = 0;
-        GPR_TRY(run_cell_lcp(g, S15, nullptr, nullptr, nc, lo, lcp, false, scr, cell_lcp_scratch_bytes(nc),
+        GPR_TRY(run_cell_lcp(g, S15, nullptr, nullptr, nc, lo, lcp, false, scr, cell_lcp_scratch_bytes(nc, lo.est),
                              stats ? &nest : nullptr, st));
         if (stats) {
             stats->recon_points = n;
@@ -419,7 +420,7 @@ gpr_status lcp_from_kept_cells(gpr_model *M, const GridDev &g, const double *T64
         GridCache *C = M->cache;
         int64_t nrows = 0;
         GPR_TRY(cache_fill_stats(M, C, g, pflag, (uint8_t *)slot, plist, cscr, csb, &nrows, st));
-        GPR_TRY(ws_reserve(M, 1, cell_lcp_scratch_bytes(ncell) + 1024, st));
+        GPR_TRY(ws_reserve(M, 1, cell_lcp_scratch_bytes(ncell, lo.est) + 1024, st));
         if (stats) stats->recon_points = nrows;
         int64_t nest = 0;
         GPR_TRY(run_cell_lcp(g, C->S15, nullptr, clist, ncell, lo, lcp, false, ws_ptr(M, 1), ws_size(M, 1),
@@ -444,13 +445,13 @@ gpr_status lcp_from_kept_cells(gpr_model *M, const GridDev &g, const double *T64
         if (R < 3) return GPR_ERR_OOM;
         const int64_t zs = R - 2, ring = R * nxy;
         size_t b2 = Carver::round((size_t)ring * M->mp * 8) + Carver::round((size_t)n * 15 * 8) +
-                    cell_lcp_scratch_bytes(ncell) + Carver::round(te * sizeof(float2)) + 2 * Carver::round((size_t)n) +
+                    cell_lcp_scratch_bytes(ncell, lo.est) + Carver::round(te * sizeof(float2)) + 2 * Carver::round((size_t)n) +
                     2048;
         GPR_TRY(ws_reserve(M, 1, b2, st));
         Carver cv2{(char *)ws_ptr(M, 1)};
         float2 *W = cv2.take<float2>((size_t)ring * M->mp);
         double *S15 = cv2.take<double>((size_t)n * 15);
-        void *scr = cv2.take<char>(cell_lcp_scratch_bytes(ncell));
+        void *scr = cv2.take<char>(cell_lcp_scratch_bytes(ncell, lo.est));
         float2 *Tu = cv2.take<float2>(te);
         uint8_t *zflag = cv2.take<uint8_t>((size_t)n);
         uint8_t *bflag = cv2.take<uint8_t>((size_t)n);
@@ -471,18 +472,18 @@ gpr_status lcp_from_kept_cells(gpr_model *M, const GridDev &g, const double *T64
             if (cnt > 0) GPR_TRY(launch_stats_ff(M, g, plist, cnt, nullptr, W, S15, st, true, ring));
         }
         int64_t nest = 0;
-        GPR_TRY(run_cell_lcp(g, S15, nullptr, clist, ncell, lo, lcp, false, scr, cell_lcp_scratch_bytes(ncell),
+        GPR_TRY(run_cell_lcp(g, S15, nullptr, clist, ncell, lo, lcp, false, scr, cell_lcp_scratch_bytes(ncell, lo.est),
                              stats ? &nest : nullptr, st));
         if (stats) stats->cells_estimated = nest;
         return GPR_OK;
     }
     size_t b2 = Carver::round((size_t)npts * M->mp * sizeof(double)) + Carver::round((size_t)npts * 15 * sizeof(double)) +
-                cell_lcp_scratch_bytes(ncell) + Carver::round(te * sizeof(float2)) + 2048;
+                cell_lcp_scratch_bytes(ncell, lo.est) + Carver::round(te * sizeof(float2)) + 2048;
     GPR_TRY(ws_reserve(M, 1, b2, st));
     Carver cv2{(char *)ws_ptr(M, 1)};
     double *W = cv2.take<double>((size_t)npts * M->mp);
     double *S15 = cv2.take<double>((size_t)npts * 15);
-    void *scr = cv2.take<char>(cell_lcp_scratch_bytes(ncell));
+    void *scr = cv2.take<char>(cell_lcp_scratch_bytes(ncell, lo.est));
     float2 *Tu = cv2.take<float2>(te);
     if (use_oz) {
         GPR_TRY(oz_prepare(M, st));
@@ -495,7 +496,7 @@ gpr_status lcp_from_kept_cells(gpr_model *M, const GridDev &g, const double *T64
     }
     GPR_CUDA_TRY(cudaGetLastError());
     int64_t nest = 0;
-    GPR_TRY(run_cell_lcp(g, S15, slot, clist, ncell, lo, lcp, false, scr, cell_lcp_scratch_bytes(ncell),
+    GPR_TRY(run_cell_lcp(g, S15, slot, clist, ncell, lo, lcp, false, scr, cell_lcp_scratch_bytes(ncell, lo.est),
                          stats ? &nest : nullptr, st));
     if (stats) stats->cells_estimated = nest;
     return GPR_OK;

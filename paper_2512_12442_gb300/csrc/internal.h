@@ -297,16 +297,18 @@ struct RecordSink {
     unsigned long long *nrec;  // device counter of appended records (and the estimator's ticket after it)
     int64_t capacity;
     std::atomic<int64_t> *reserved;
+    void *recs2;  // GPR_EST_SOV_ORDERED: the all-above orthants' records, parallel to recs (else null)
 };
 void set_record_sink(RecordSink *sink);  // for the calling thread; nullptr to clear
 size_t record_bytes();
-// nrec[0]: the device record count; nrec[1]: scratch for the estimator's work ticket.
-void launch_estimator(const void *recs, unsigned long long *nrec, int64_t max_records, const LcpOpts &o,
-                      cudaStream_t st);
+// nrec[0]: the device record count; nrec[1]: scratch for the estimator's work ticket.  recs2:
+// the all-above orthants' records of GPR_EST_SOV_ORDERED, index for index with recs (else null).
+void launch_estimator(const void *recs, const void *recs2, unsigned long long *nrec, int64_t max_records,
+                      const LcpOpts &o, cudaStream_t st);
 gpr_status run_cell_lcp(const GridDev &g, const double *stats, const int32_t *slot, const int64_t *cells,
                         int64_t count, const LcpOpts &o, float *lcp, bool out_by_position, void *scratch,
                         size_t scratch_bytes, int64_t *n_estimated, cudaStream_t st);
-size_t cell_lcp_scratch_bytes(int64_t count);
+size_t cell_lcp_scratch_bytes(int64_t count, int est);  // est: gpr_estimator
 size_t cell_rec_bytes();
 gpr_status run_cell_lcp_on_scratch(const GridDev &g, const double *stats, const int64_t *cells, int64_t count,
                                    const LcpOpts &o, float *lcp, bool by_pos, void *scratch, int64_t max_records,

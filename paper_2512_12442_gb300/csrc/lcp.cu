@@ -101,19 +101,61 @@ __device__ float bvn_lower(double h, double k, double r)
     return 0.5f * nrm_cdf((float)h) + 0.5f * nrm_cdf((float)k) - t1 - t2 - beta;
 }
 
+// Cholesky factor (pivots floored at fl) of the cell's covariance with its corners taken in
+// ascending order of the standardised threshold s (theta - mu_c) / sigma_c (ties: lower corner
+// first), and the thresholds s (theta - mu) in that order: the all-below (s = +1) or all-above
+// (s = -1) orthant of the ordered estimator.  The order is decided in FP64.
+__device__ void ordered_factor(const double (&S)[8][8], const double (&mu)[8], double theta, double s, double fl,
+                               CellRec &r)
+{
+    int perm[8];
+    double key[8];
+    for (int c = 0; c < 8; ++c) {
+        key[c] = (s * (theta - mu[c])) / sqrt(S[c][c]);
+        perm[c] = c;
+    }
+    for (int i = 1; i < 8; ++i) {  // insertion sort, stable
+        const int v = perm[i];
+        int j = i;
+        while (j > 0 && key[v] < key[perm[j - 1]]) {
+            perm[j] = perm[j - 1];
+            --j;
+        }
+        perm[j] = v;
+    }
+    double Lm[8][8];
+    for (int a = 0; a < 8; ++a) {
+        for (int b = 0; b <= a; ++b) {
+            double t = S[perm[a]][perm[b]];
+            for (int q = 0; q < b; ++q) t -= Lm[a][q] * Lm[b][q];
+            if (a == b) {
+                if (!(t > fl)) t = fl;
+                Lm[a][a] = sqrt(t);
+            } else {
+                Lm[a][b] = t / Lm[b][b];
+            }
+        }
+    }
+    for (int a = 0; a < 8; ++a) {
+        r.b[a] = (float)(s * (theta - mu[perm[a]]));
+        for (int b = 0; b <= a; ++b) r.L[tri(a, b)] = (float)Lm[a][b];
+    }
+}
+
 // CF: 0 = queue records for the sampling estimators, 1 = independent-corner closed form,
-// 2 = edge-max closed form (results written in place, no records).
+// 2 = edge-max closed form (results written in place, no records), 3 = queue records of the
+// ordered SOV estimator (the all-below factor in recs, the all-above one in recs2, same index).
 template <int CF>
 __global__ void k_cell_prep(GridDev g, const double *stats, const int32_t *slot, const int64_t *cells,
                             int64_t count, double theta, double tau, double skip_eps, PairTable pt, float *lcp,
                             bool by_pos, CellRec *recs, unsigned long long *nrec, unsigned long long *nown,
-                            int *status, unsigned long long *orth_ctr)
+                            int *status, unsigned long long *orth_ctr, CellRec *recs2)
 {
     bool closed = false;  // a closed-form estimator evaluated this cell (counted as estimated)
     int64_t pos = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     bool active = pos < count;
     bool need = false;
-    CellRec r;
+    CellRec r, r2;
     int64_t outi = 0;
     if (active) {
         int64_t cidx = cells ? cells[pos] : pos;
@@ -204,6 +246,9 @@ __global__ void k_cell_prep(GridDev g, const double *stats, const int32_t *slot,
                     }
                 result = fminf(fmaxf(best, 0.f), 1.f);
                 closed = true;
+            } else if (CF == 3 && !(sa < lim || sb < lim)) {
+                ordered_factor(S, mu, theta, 1.0, 1e-3 * jit, r);
+                ordered_factor(S, mu, theta, -1.0, 1e-3 * jit, r2);
             } else if (CF == 0 && !(sa < lim || sb < lim)) {
                 double Lm[8][8];
                 double fl = 1e-3 * jit;
@@ -223,6 +268,8 @@ __global__ void k_cell_prep(GridDev g, const double *stats, const int32_t *slot,
                     r.b[a] = (float)(theta - mu[a]);
                     for (int b = 0; b <= a; ++b) r.L[tri(a, b)] = (float)Lm[a][b];
                 }
+            }
+            if ((CF == 0 || CF == 3) && !indef && !(sa < lim || sb < lim)) {
                 // Frechet bound: P(all < theta) <= min_c P(Y_c < theta) (and likewise above).  An
                 // orthant bounded below 1e-7 is taken as 0: the LCP moves by less than 1e-7.
                 float mlo = 1.f, mhi = 1.f;
@@ -238,7 +285,7 @@ __global__ void k_cell_prep(GridDev g, const double *stats, const int32_t *slot,
         }
         if (!need) lcp[outi] = result;
     }
-    if (CF != 0) {  // closed-form estimators: count the cells they evaluated (no records)
+    if (CF == 1 || CF == 2) {  // closed-form estimators: count the cells they evaluated (no records)
         const unsigned cmask = __ballot_sync(0xffffffffu, closed);
         if (cmask && (threadIdx.x & 31) == __ffs(cmask) - 1) atomicAdd(nrec, (unsigned long long)__popc(cmask));
         return;
@@ -258,7 +305,15 @@ __global__ void k_cell_prep(GridDev g, const double *stats, const int32_t *slot,
         if (nown) atomicAdd(nown, (unsigned long long)__popc(mask));
     }
     base = __shfl_sync(0xffffffffu, base, leader);
-    if (need) recs[base + __popc(mask & ((1u << lane) - 1))] = r;
+    if (need) {
+        const unsigned long long at = base + __popc(mask & ((1u << lane) - 1));
+        recs[at] = r;
+        if (CF == 3) {
+            r2.cell = r.cell;
+            r2.out = r.out;
+            recs2[at] = r2;
+        }
+    }
 }
 
 __device__ __forceinline__ uint64_t splitmix64(uint64_t seed, uint64_t k)
@@ -384,6 +439,69 @@ __global__ void __launch_bounds__(256, MINB) k_sov(const CellRec *recs, const un
     }
 }
 
+// The ordered SOV estimator: the same lattice and recursion as k_sov, but each orthant has its own
+// factor and signed thresholds (all-below from recs, all-above from recs2, same index), so the
+// two orthants run one after the other with the lattice coordinates recomputed for each.
+template <int MINB>
+__global__ void __launch_bounds__(256, MINB) k_sov_ord(const CellRec *recs, const CellRec *recs2,
+                                                      const unsigned long long *nrec, unsigned long long *ticket,
+                                                      int N, uint64_t seed, Lattice lat)
+{
+    int lane = threadIdx.x & 31;
+    int64_t n = (int64_t)*nrec;
+    for (;;) {
+        unsigned long long t = 0;
+        if (lane == 0) t = atomicAdd(ticket, 1ull);
+        const int64_t q = (int64_t)__shfl_sync(0xffffffffu, t, 0);
+        if (q >= n) break;
+        const uint64_t cellid = (uint64_t)recs[q].cell & ((1ull << 56) - 1);
+        const int skip = (int)((uint64_t)recs[q].cell >> 56);
+        uint32_t D = 0;
+        if (lane < 7) D = (uint32_t)(splitmix64(seed, cellid * 8 + lane + 1) >> 32);
+        uint32_t Ds[7];
+#pragma unroll
+        for (int i = 0; i < 7; ++i) Ds[i] = __shfl_sync(0xffffffffu, D, i);
+        float acc_lo = 0.f, acc_hi = 0.f;
+#pragma unroll 1
+        for (int side = 0; side < 2; ++side) {
+            if (skip & (1 << side)) continue;
+            const CellRec &r = side ? recs2[q] : recs[q];
+            float Ls[28], cb[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const float inv = 1.0f / r.L[tri(i, i)];
+                cb[i] = r.b[i] * inv;
+#pragma unroll
+                for (int j = 0; j < i; ++j) Ls[i * (i - 1) / 2 + j] = r.L[tri(i, j)] * inv;
+            }
+            const float e_first = nrm_cdf(cb[0]);
+            float a = 0.f;
+            for (int k = lane; k < N; k += 64) {
+                const bool two = k + 32 < N;
+                float w0[7], w1[7];
+#pragma unroll
+                for (int i = 0; i < 7; ++i) {
+                    w0[i] = lattice_w((uint32_t)k * lat.G[i] + Ds[i]);
+                    w1[i] = lattice_w((uint32_t)(k + 32) * lat.G[i] + Ds[i]);
+                }
+                float f0, f1;
+                sov_pair(Ls, cb, 1.0f, e_first, w0, w1, f0, f1);
+                a += two ? f0 + f1 : f0;
+            }
+            if (side) acc_hi = a; else acc_lo = a;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            acc_lo += __shfl_xor_sync(0xffffffffu, acc_lo, o);
+            acc_hi += __shfl_xor_sync(0xffffffffu, acc_hi, o);
+        }
+        if (lane == 0) {
+            double v = 1.0 - (double)acc_lo / N - (double)acc_hi / N;
+            *recs[q].out = (float)(v < 0.0 ? 0.0 : (v > 1.0 ? 1.0 : v));
+        }
+    }
+}
+
 // Philox-4x32-10 (Salmon et al., SC'11).
 __device__ __forceinline__ void philox(uint32_t c[4], uint32_t k0, uint32_t k1)
 {
@@ -460,7 +578,11 @@ Lattice make_lattice()
 
 }  // namespace
 
-size_t cell_lcp_scratch_bytes(int64_t count) { return Carver::round(sizeof(CellRec) * (size_t)count) + 256; }
+// records and, for the ordered estimator, the parallel all-above records
+size_t cell_lcp_scratch_bytes(int64_t count, int est)
+{
+    return (est == GPR_EST_SOV_ORDERED ? 2 : 1) * Carver::round(sizeof(CellRec) * (size_t)count) + 256;
+}
 
 namespace {
 thread_local RecordSink *tl_sink = nullptr;
@@ -469,8 +591,8 @@ thread_local RecordSink *tl_sink = nullptr;
 void set_record_sink(RecordSink *sink) { tl_sink = sink; }
 size_t record_bytes() { return sizeof(CellRec); }
 
-void launch_estimator(const void *recs, unsigned long long *nrec, int64_t max_records, const LcpOpts &o,
-                      cudaStream_t st)
+void launch_estimator(const void *recs, const void *recs2, unsigned long long *nrec, int64_t max_records,
+                      const LcpOpts &o, cudaStream_t st)
 {
     // one warp per record, persistent over the device count (nrec[0]; nrec[1] is the work ticket);
     // the register variant and the CTAs per SM are chosen by the autotuner
@@ -479,7 +601,17 @@ void launch_estimator(const void *recs, unsigned long long *nrec, int64_t max_re
         int64_t blocks = (max_records + 7) / 8;
         if (blocks > (int64_t)num_sms() * per_sm[c]) blocks = (int64_t)num_sms() * per_sm[c];
         if (blocks < 1) blocks = 1;
-        if (o.est == GPR_EST_SOV_QMC) {
+        if (o.est == GPR_EST_SOV_ORDERED) {
+            static Lattice lat = make_lattice();
+            GPR_CUDA_TRY(cudaMemsetAsync(nrec + 1, 0, sizeof(unsigned long long), st));
+            ProfScope _ps("sov_ordered", st);
+            if (c < 2)
+                k_sov_ord<2><<<(unsigned)blocks, 256, 0, st>>>((const CellRec *)recs, (const CellRec *)recs2, nrec,
+                                                               nrec + 1, o.n_samples, o.seed, lat);
+            else
+                k_sov_ord<3><<<(unsigned)blocks, 256, 0, st>>>((const CellRec *)recs, (const CellRec *)recs2, nrec,
+                                                               nrec + 1, o.n_samples, o.seed, lat);
+        } else if (o.est == GPR_EST_SOV_QMC) {
             static Lattice lat = make_lattice();
             GPR_CUDA_TRY(cudaMemsetAsync(nrec + 1, 0, sizeof(unsigned long long), st));
             ProfScope _ps("sov", st);
@@ -497,8 +629,9 @@ void launch_estimator(const void *recs, unsigned long long *nrec, int64_t max_re
         GPR_CUDA_TRY(cudaGetLastError());
         return GPR_OK;
     };
-    tune_run(o.est == GPR_EST_SOV_QMC ? "sov_shape" : "mc_ctas_per_sm", tune_bucket(max_records),
-             o.est == GPR_EST_SOV_QMC ? 4 : 3, run, st);
+    const bool sov = o.est == GPR_EST_SOV_QMC || o.est == GPR_EST_SOV_ORDERED;
+    tune_run(o.est == GPR_EST_SOV_QMC ? "sov_shape" : (sov ? "sov_ordered_shape" : "mc_ctas_per_sm"),
+             tune_bucket(max_records), sov ? 4 : 3, run, st);
 }
 
 gpr_status run_cell_lcp(const GridDev &g, const double *stats, const int32_t *slot, const int64_t *cells,
@@ -509,15 +642,17 @@ gpr_status run_cell_lcp(const GridDev &g, const double *stats, const int32_t *sl
         if (n_estimated) *n_estimated = 0;
         return GPR_OK;
     }
-    if (scratch_bytes < cell_lcp_scratch_bytes(count)) return GPR_ERR_ARG;
+    if (scratch_bytes < cell_lcp_scratch_bytes(count, o.est)) return GPR_ERR_ARG;
     Carver cv{(char *)scratch};
     unsigned long long *nrec = cv.take<unsigned long long>(2);  // record count, estimator ticket
     CellRec *recs = cv.take<CellRec>((size_t)count);
+    const bool ordered = o.est == GPR_EST_SOV_ORDERED;
+    CellRec *recs2 = ordered ? cv.take<CellRec>((size_t)count) : nullptr;  // all-above records
     // a batch sink with room takes the records; its owner runs one estimator launch for all
     RecordSink *sink = tl_sink;
     bool to_sink = false;
     const bool closed = o.est == GPR_EST_INDEP || o.est == GPR_EST_EDGE_MAX;  // no records, no estimator
-    if (sink && !closed) {
+    if (sink && !closed && (!ordered || sink->recs2)) {
         int64_t cur = sink->reserved->load();
         while (cur + count <= sink->capacity && !sink->reserved->compare_exchange_weak(cur, cur + count)) {
         }
@@ -532,19 +667,24 @@ gpr_status run_cell_lcp(const GridDev &g, const double *stats, const int32_t *sl
         const unsigned nb = (unsigned)((count + 127) / 128);
         if (o.est == GPR_EST_INDEP)
             k_cell_prep<1><<<nb, 128, 0, st>>>(g, stats, slot, cells, count, o.theta, o.tau, o.skip_eps, pt, lcp,
-                                               by_pos, recs, nrec, nullptr, status, nullptr);
+                                               by_pos, recs, nrec, nullptr, status, nullptr, nullptr);
         else if (o.est == GPR_EST_EDGE_MAX)
             k_cell_prep<2><<<nb, 128, 0, st>>>(g, stats, slot, cells, count, o.theta, o.tau, o.skip_eps, pt, lcp,
-                                               by_pos, recs, nrec, nullptr, status, nullptr);
+                                               by_pos, recs, nrec, nullptr, status, nullptr, nullptr);
+        else if (ordered)
+            k_cell_prep<3><<<nb, 128, 0, st>>>(
+                g, stats, slot, cells, count, o.theta, o.tau, o.skip_eps, pt, lcp, by_pos,
+                to_sink ? (CellRec *)sink->recs : recs, to_sink ? sink->nrec : nrec, to_sink ? nrec : nullptr,
+                status, prof_counter(PROF_CTR_ORTHANTS), to_sink ? (CellRec *)sink->recs2 : recs2);
         else
             k_cell_prep<0><<<nb, 128, 0, st>>>(
                 g, stats, slot, cells, count, o.theta, o.tau, o.skip_eps, pt, lcp, by_pos,
                 to_sink ? (CellRec *)sink->recs : recs, to_sink ? sink->nrec : nrec, to_sink ? nrec : nullptr,
-                status, prof_counter(PROF_CTR_ORTHANTS));
+                status, prof_counter(PROF_CTR_ORTHANTS), nullptr);
     }
     note_launch();
     GPR_CUDA_TRY(cudaGetLastError());
-    if (!to_sink && !closed) launch_estimator(recs, nrec, count, o, st);
+    if (!to_sink && !closed) launch_estimator(recs, recs2, nrec, count, o, st);
     GPR_CUDA_TRY(cudaGetLastError());
     if (n_estimated) {
         unsigned long long h = 0;
@@ -820,6 +960,7 @@ gpr_status run_cell_lcp_on_scratch(const GridDev &g, const double *stats, const 
                                    const LcpOpts &o, float *lcp, bool by_pos, void *scratch, int64_t max_records,
                                    int *status, cudaStream_t st)
 {
+    if (o.est == GPR_EST_SOV_ORDERED) return GPR_ERR_UNSUPPORTED;  // one record per cell only
     if (count <= 0) return GPR_OK;
     if (count > max_records) return GPR_ERR_ARG;
     unsigned long long *nrec = (unsigned long long *)scratch;  // record count, estimator ticket
@@ -829,13 +970,13 @@ gpr_status run_cell_lcp_on_scratch(const GridDev &g, const double *stats, const 
     const unsigned nb = (unsigned)((count + 127) / 128);
     if (o.est == GPR_EST_INDEP)
         k_cell_prep<1><<<nb, 128, 0, st>>>(g, stats, nullptr, cells, count, o.theta, o.tau, o.skip_eps, pt, lcp,
-                                           by_pos, recs, nrec, nullptr, status, nullptr);
+                                           by_pos, recs, nrec, nullptr, status, nullptr, nullptr);
     else if (o.est == GPR_EST_EDGE_MAX)
         k_cell_prep<2><<<nb, 128, 0, st>>>(g, stats, nullptr, cells, count, o.theta, o.tau, o.skip_eps, pt, lcp,
-                                           by_pos, recs, nrec, nullptr, status, nullptr);
+                                           by_pos, recs, nrec, nullptr, status, nullptr, nullptr);
     else
         k_cell_prep<0><<<nb, 128, 0, st>>>(g, stats, nullptr, cells, count, o.theta, o.tau, o.skip_eps, pt, lcp,
-                                           by_pos, recs, nrec, nullptr, status, nullptr);
+                                           by_pos, recs, nrec, nullptr, status, nullptr, nullptr);
     note_launch();
     GPR_CUDA_TRY(cudaGetLastError());
     if (o.est == GPR_EST_INDEP || o.est == GPR_EST_EDGE_MAX) return GPR_OK;  // evaluated in place

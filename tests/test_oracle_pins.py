@@ -250,6 +250,7 @@ def test_lcp_independent_corners_closed_form():
     lcp = oracle.cell_lcp(mu, S, th, tau=0.0, n_samples=64)
     ref = 1 - np.prod(ndtr((th - mu) / sd)) - np.prod(ndtr((mu - th) / sd))
     assert lcp == pytest.approx(ref, abs=1e-13)
+    assert oracle.cell_lcp(mu, S, th, est=oracle.EST_SOV_ORD, tau=0.0, n_samples=64) == pytest.approx(ref, abs=1e-13)
 
 
 def test_lcp_equicorrelated_quadrature():
@@ -336,6 +337,43 @@ def test_sov_general_cells_against_genz_mvn_cdf():
         assert big == pytest.approx(ref, abs=6e-5), (big, ref)
         paper_n = oracle.cell_lcp(mu, S, th, tau=0.0, n_samples=1600)
         assert abs(paper_n - ref) <= 0.2 * math.sqrt(ref * (1 - ref) / 1600), (paper_n, ref)
+        # the ordered variant integrates the same orthants in another variable order
+        big = oracle.cell_lcp(mu, S, th, est=oracle.EST_SOV_ORD, tau=0.0, n_samples=1 << 20)
+        assert big == pytest.approx(ref, abs=6e-5), (big, ref)
+
+
+def test_ordered_sov_perfectly_correlated_corners_closed_form():
+    """Corners that share one normal variable, Y_c = mu_c + sigma Z with distinct means:
+    P(all < theta) = Phi(min_c z_c), P(all > theta) = Phi(-max_c z_c), z_c = (theta - mu_c) / sigma,
+    so LCP = Phi(z_max) - Phi(z_min) (Sec. 4's definition).  The ordered estimator takes the corner
+    with the smallest standardised threshold first for the all-below orthant (the largest for the
+    all-above one): its first factor is the exact answer and every later factor is 1 up to the
+    jitter, whatever the lattice.  A reversed or unsorted order misses by up to ~1e-3 (the index
+    order's error here), so the order itself is pinned."""
+    rng = np.random.default_rng(3)
+    sd = 0.2
+    S = np.full((8, 8), sd * sd)
+    for trial in range(4):
+        mu = rng.normal(0.0, 0.1, 8)
+        th = float(np.median(mu)) + 0.01 * trial
+        z = (th - mu) / sd
+        exact = ndtr(z.max()) - ndtr(z.min())
+        got = oracle.cell_lcp(mu, S, th, est=oracle.EST_SOV_ORD, tau=1e-10, n_samples=1600)
+        assert got == pytest.approx(exact, abs=1e-8), (got, exact)
+
+
+def test_ordered_sov_relabelling_invariance():
+    """The ordered estimator sorts the corners by their standardised thresholds, so relabelling the
+    corners (permuting mu and Sigma together) leaves its factors, and its value, unchanged to the
+    last bit; the index-order estimator has no such property."""
+    rng = np.random.default_rng(11)
+    A = rng.normal(size=(8, 8)); S = A @ A.T / 8 + 0.1 * np.eye(8)
+    mu = rng.normal(0.0, 0.4, 8); th = 0.05
+    a = oracle.cell_lcp(mu, S, th, est=oracle.EST_SOV_ORD, n_samples=1600, cell=5)
+    for seed in range(3):
+        p = np.random.default_rng(100 + seed).permutation(8)
+        b = oracle.cell_lcp(mu[p], S[np.ix_(p, p)], th, est=oracle.EST_SOV_ORD, n_samples=1600, cell=5)
+        assert a == b, (a, b)
 
 
 def test_bivariate_normal_against_library_and_closed_form():
