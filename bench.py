@@ -513,17 +513,29 @@ def main():
     g.gpr_sync(stream)
 
     # the same field by the other paths, side by side at the same accuracy (same FP64-class leaf
-    # statistics and estimator): dense with the TF32x3 pre-pass, dense with the plain FP32 SIMT pre-pass
+    # statistics and estimator): dense with the TF32x3 pre-pass, dense with the plain FP32 SIMT
+    # pre-pass; and the adaptive path with the ordered SOV estimator (its own, more accurate
+    # estimate: the largest and mean per-cell difference from the default fields are reported)
     side = {}
     if args.mode == "adaptive" and not args.no_side_by_side:
-        for label, mode, pr in (("dense_tf32x3", "dense", "tf32x3"), ("dense_fp32_simt", "dense", "fp32")):
-            o2 = g.lcp_options(prec=precs[pr])
+        ordered = None
+        for label, mode, pr, est in (("dense_tf32x3", "dense", "tf32x3", g.GPR_EST_SOV_QMC),
+                                     ("dense_fp32_simt", "dense", "fp32", g.GPR_EST_SOV_QMC),
+                                     ("adaptive_ordered_sov", "adaptive", args.prec, g.GPR_EST_SOV_ORDERED)):
+            o2 = g.lcp_options(prec=precs[pr], est=est)
             step(mode=mode, o=o2).close()
             k2 = max(1, min(args.steps, 3))
             t2 = max_over_ranks(timed(k2, mode=mode, o=o2), world)
             side[label] = {"ms_per_step": t2, "value": world * pts_per_step / (t2 / 1e3), "steps": k2}
+            if est == g.GPR_EST_SOV_ORDERED:
+                ordered = [f.clone() for f in fields]
         step().close()  # the default path's fields again, for the accuracy check below
         g.gpr_sync(stream)
+        if ordered is not None:
+            d = [(a - b).abs() for a, b in zip(ordered, fields)]
+            side["adaptive_ordered_sov"]["max_abs_diff_vs_default"] = max(float(x.max()) for x in d)
+            side["adaptive_ordered_sov"]["mean_abs_diff_vs_default_on_nonzero"] = float(
+                sum(float(x[f != 0].sum()) for x, f in zip(d, fields)) / max(1, sum(int((f != 0).sum()) for f in fields)))
 
     if rank != 0:
         if world > 1:
