@@ -69,6 +69,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-side-by-side", action="store_true", help="skip the dense / FP32-SIMT comparison runs")
     p.add_argument("--cpu-sample", type=int, default=64, help="cells per axis of the oracle sample")
+    p.add_argument("--est", default="sov", choices=["sov", "ordered"],
+                   help="small cases only: the cell estimator (index-order or ordered SOV)")
     p.add_argument("--case", default="full", choices=["full", "small", "small_adaptive"],
                    help="small: one dense LCP field of the same field on a 64^3 grid (for ncu captures); "
                         "small_adaptive: one adaptive field (max depth 6) on that grid; "
@@ -415,16 +417,18 @@ def main():
         out = torch.zeros((n - 1) ** 3, dtype=torch.float32, device="cuda")
         M = g.gpr_model_create(w.X, w.y, w.kernel, w.ell, w.sf2, w.sn2)
         g.gpr_profile_reset(); g.gpr_profile_enable(True)
+        est = g.GPR_EST_SOV_ORDERED if args.est == "ordered" else g.GPR_EST_SOV_QMC
+        o = g.lcp_options(prec=g.GPR_P_TF32X3, est=est)
         if args.case == "small":
-            st = g.gpr_lcp_dense(M, grid, w.isovalues[1], g.lcp_options(prec=g.GPR_P_TF32X3), out)
+            st = g.gpr_lcp_dense(M, grid, w.isovalues[1], o, out)
         else:
-            st = g.gpr_lcp_adaptive(M, grid, w.isovalues[1], 6, g.lcp_options(prec=g.GPR_P_TF32X3), out)
+            st = g.gpr_lcp_adaptive(M, grid, w.isovalues[1], 6, o, out)
         g.gpr_sync()
         g.gpr_profile_enable(False)
-        print(json.dumps({"case": "small", "grid": n, "m": w.m,
+        print(json.dumps({"case": "small", "grid": n, "m": w.m, "est": args.est,
                           **{k: st[k] for k in ("recon_points", "leaf_cells", "cells_estimated")},
                           "sov_orthants": g.gpr_profile_units("sov_orthants"),
-                          "sov_launches": g.gpr_profile_read("sov")[1]}))
+                          "sov_launches": g.gpr_profile_read("sov" if args.est == "sov" else "sov_ordered")[1]}))
         return
     if args.mode == "backward":
         run_backward(args, g, torch, rank, world, local)
