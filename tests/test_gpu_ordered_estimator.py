@@ -47,17 +47,21 @@ def test_ordered_dense_config1_every_cell(torch, g):
     assert st["cells_estimated"] > 100
 
 
-def test_ordered_paper_scale_block(torch, g):
-    """Paper-scale field (m=500, 128^3) at the median isovalue, launched as the bench launches the
-    dense path: a 12^3-cell block across the surface against the oracle cell by cell."""
+@pytest.mark.parametrize("iso,c0", [(0, (50, 60, 40)), (1, (68, 44, 44))])
+def test_ordered_paper_scale_block(torch, g, iso, c0):
+    """Paper-scale field (m=500, 128^3), launched as the bench launches the dense path: a 12^3-cell
+    block across the surface against the oracle cell by cell (185 cells with LCP in (0.01, 0.99)
+    at the first isovalue, 1300 at the median one)."""
     w = workloads.config2()
     M = model_of(w)
     n = w.n
-    th = w.isovalues[1]
+    th = w.isovalues[iso]
     gpu, _ = _dense(g, torch, M, n, th, prec=g.GPR_P_FP32)
     f = gpu.reshape(n - 1, n - 1, n - 1)
-    ref = oracle.Model.from_workload(w).lcp_block(n, th, (50, 60, 40), (62, 72, 52), est=oracle.EST_SOV_ORD)
-    d = np.abs(f[40:52, 60:72, 50:62] - ref.reshape(12, 12, 12))
+    ref = oracle.Model.from_workload(w).lcp_block(n, th, c0, tuple(v + 12 for v in c0),
+                                                 est=oracle.EST_SOV_ORD).reshape(12, 12, 12)
+    assert np.sum((ref > 0.01) & (ref < 0.99)) >= 150
+    d = np.abs(f[c0[2]:c0[2] + 12, c0[1]:c0[1] + 12, c0[0]:c0[0] + 12] - ref)
     assert d.max() <= 1e-4, d.max()
     assert 0.0 <= gpu.min() and gpu.max() <= 1.0
 
@@ -129,3 +133,4 @@ def test_ordered_estimator_unsupported_where_documented(torch, g):
     with pytest.raises(g.GPRError) as e:
         g.gpr_cell_lcp_from_stats_noalloc(grid, s15, 0.0, opts, None, out)
     assert e.value.status == g.GPR_ERR_UNSUPPORTED
+
