@@ -81,6 +81,8 @@ def lib():
         L.or_cell_lcp_adj.restype = C.c_double
         L.or_cell_lcp_adj.argtypes = [C.c_int, _dp, _dp, C.c_double, C.c_int64, C.c_uint64, C.c_uint64, C.c_double,
                                       C.c_double, C.c_double, _dp, _dp]
+        L.or_cell_lcp_adj_ordered.restype = C.c_double
+        L.or_cell_lcp_adj_ordered.argtypes = L.or_cell_lcp_adj.argtypes
         L.or_lcp_grad_block.restype = C.c_double
         L.or_lcp_grad_block.argtypes = [C.c_void_p, C.POINTER(_Grid), C.c_double, C.c_int64, C.c_uint64, C.c_double,
                                         C.c_double, _dp, _i64p, _i64p, _dp, _dp]
@@ -325,14 +327,16 @@ class Model:
         return g, gr
 
 
-def cell_lcp_adj(mu, S, theta, wbar=1.0, n_samples=1600, seed=0, cell=0, tau=1e-10, skip_eps=1e-9):
-    """Adjoint of the SOV cell rule: (LCP, dLCP/dmu * wbar, dLCP/dSigma * wbar)."""
+def cell_lcp_adj(mu, S, theta, wbar=1.0, n_samples=1600, seed=0, cell=0, tau=1e-10, skip_eps=1e-9, est=EST_SOV):
+    """Adjoint of the SOV cell rule (est EST_SOV, or EST_SOV_ORD for the ordered rule):
+    (LCP, dLCP/dmu * wbar, dLCP/dSigma * wbar)."""
     mu = np.ascontiguousarray(mu, np.float64)
     S = np.ascontiguousarray(S, np.float64)
     d = mu.shape[0]
     mb = np.zeros(d); Sb = np.zeros(d * d)
-    v = lib().or_cell_lcp_adj(d, mu, S.reshape(-1), float(theta), int(n_samples), C.c_uint64(seed), C.c_uint64(cell),
-                              float(tau), float(skip_eps), float(wbar), mb, Sb)
+    fn = lib().or_cell_lcp_adj_ordered if est == EST_SOV_ORD else lib().or_cell_lcp_adj
+    v = fn(d, mu, S.reshape(-1), float(theta), int(n_samples), C.c_uint64(seed), C.c_uint64(cell),
+           float(tau), float(skip_eps), float(wbar), mb, Sb)
     return v, mb, Sb.reshape(d, d)
 
 

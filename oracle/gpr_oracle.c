@@ -1310,6 +1310,62 @@ double or_cell_lcp_adj(int d, const double *mu, const double *S, double theta, i
     return v;
 }
 
+/* Adjoint of the ordered rule (EST_SOV_ORD): each orthant's reverse sweep runs on its own
+ * permuted factor, its Sigma adjoint is taken through that factor's Cholesky and permuted back;
+ * the order itself is piecewise constant, so away from ties it contributes nothing.  Same
+ * outputs and conventions as or_cell_lcp_adj. */
+double or_cell_lcp_adj_ordered(int d, const double *mu, const double *S, double theta, int64_t N, uint64_t seed,
+                               uint64_t cell, double tau, double skip_eps, double wbar, double *mubar, double *Sbar)
+{
+    for (int i = 0; i < d; ++i) mubar[i] = 0.0;
+    for (int i = 0; i < d * d; ++i) Sbar[i] = 0.0;
+    double Sj[256];
+    double maxdiag = 0.0;
+    int amax = 0;
+    for (int i = 0; i < d; ++i) if (S[i * d + i] > maxdiag) { maxdiag = S[i * d + i]; amax = i; }
+    if (!(maxdiag > 1e-30)) return or_cell_lcp(d, mu, S, theta, EST_SOV_ORD, N, seed, cell, tau, skip_eps);
+    double jit = tau * maxdiag;
+    for (int i = 0; i < d * d; ++i) Sj[i] = S[i];
+    for (int i = 0; i < d; ++i) Sj[i * d + i] += jit;
+    for (int i = 0; i < d; ++i)
+        if (!(Sj[i * d + i] > 0.0)) return NAN;
+    double v = or_cell_lcp(d, mu, S, theta, EST_SOV_ORD, N, seed, cell, tau, skip_eps);
+    if (!(v > 0.0) || !(v < 1.0)) return v; /* skipped, clamped or deterministic: constant */
+    uint32_t sh[16];
+    for (int i = 0; i < d - 1; ++i) sh[i] = (uint32_t)(or_splitmix64(seed, (uint64_t)cell * 8 + i + 1) >> 32);
+    for (int side = 0; side < 2; ++side) {
+        const double s = side ? -1.0 : 1.0;
+        int perm[16];
+        double key[16], Sp[256], Lp[256], bp[16], bbar[16], Lbar[256], Sbp[256];
+        for (int i = 0; i < d; ++i) {
+            key[i] = (s * (theta - mu[i])) / sqrt(Sj[i * d + i]);
+            perm[i] = i;
+        }
+        for (int i = 1; i < d; ++i) {
+            int t = perm[i], j = i;
+            while (j > 0 && key[t] < key[perm[j - 1]]) { perm[j] = perm[j - 1]; --j; }
+            perm[j] = t;
+        }
+        for (int a = 0; a < d; ++a) {
+            bp[a] = s * (theta - mu[perm[a]]);
+            bbar[a] = 0.0;
+            for (int b = 0; b < d; ++b) Sp[a * d + b] = Sj[perm[a] * d + perm[b]];
+        }
+        chol_floor(Sp, d, 1e-3 * jit, Lp);
+        for (int i = 0; i < d * d; ++i) Lbar[i] = 0.0;
+        sov_orthant_adj(d, Lp, bp, N, sh, -wbar, bbar, Lbar);
+        chol_adj(d, Lp, Lbar, Sbp);
+        for (int a = 0; a < d; ++a) {
+            mubar[perm[a]] += -s * bbar[a]; /* b = s (theta - mu) */
+            for (int b = 0; b < d; ++b) Sbar[perm[a] * d + perm[b]] += Sbp[a * d + b];
+        }
+    }
+    double tr = 0.0;
+    for (int i = 0; i < d; ++i) tr += Sbar[i * d + i];
+    Sbar[amax * d + amax] += tau * tr;
+    return v;
+}
+
 /* d k(a, b) / d log l_d for the kernel (a, b fixed). */
 static double kernel_dlogl(int kernel, const double *ell, double sf2, const double *a, const double *b, int dd)
 {

@@ -835,6 +835,36 @@ def test_cell_adjoint_matches_finite_differences():
         assert an == pytest.approx(fd, rel=1e-5, abs=1e-9)
 
 
+def test_ordered_cell_adjoint_matches_finite_differences():
+    """The ordered rule's reverse sweep (each orthant on its own permuted factor, adjoints permuted
+    back): dLCP/dmu and dLCP/dSigma against central differences of the same estimator at a point
+    whose corner order does not change within the step (the order is piecewise constant)."""
+    rng = np.random.default_rng(3)
+    A = rng.normal(size=(8, 8)); S = A @ A.T / 8 + 0.05 * np.ones((8, 8)) + 0.02 * np.eye(8)
+    mu = rng.normal(0, 0.2, 8)
+    th = 0.05
+    z = (th - mu) / np.sqrt(np.diag(S))
+    assert np.min(np.diff(np.sort(z))) > 1e-3  # no near-ties: a 1e-5 step keeps both orders
+    est = oracle.EST_SOV_ORD
+    v, mb, Sb = oracle.cell_lcp_adj(mu, S, th, est=est)
+    assert v == pytest.approx(oracle.cell_lcp(mu, S, th, est=est), abs=1e-15)
+    h = 1e-5
+    for i in range(8):
+        e = np.zeros(8); e[i] = h
+        fd = (oracle.cell_lcp(mu + e, S, th, est=est) - oracle.cell_lcp(mu - e, S, th, est=est)) / (2 * h)
+        assert mb[i] == pytest.approx(fd, rel=1e-6, abs=1e-10)
+    for (i, j) in ((0, 0), (2, 5), (7, 7), (1, 6), (3, 4)):
+        E = np.zeros((8, 8)); E[i, j] += h
+        if i != j:
+            E[j, i] += h
+        fd = (oracle.cell_lcp(mu, S + E, th, est=est) - oracle.cell_lcp(mu, S - E, th, est=est)) / (2 * h)
+        an = Sb[i, j] + (Sb[j, i] if i != j else 0.0)
+        assert an == pytest.approx(fd, rel=1e-5, abs=1e-9)
+    # the two rules estimate the same LCP, so their gradients agree to the estimators' accuracy
+    _, mb0, _ = oracle.cell_lcp_adj(mu, S, th)
+    assert np.abs(mb - mb0).max() <= 0.05 * np.abs(mb0).max()
+
+
 @pytest.mark.parametrize("kernel", [workloads.SE, workloads.MATERN52])
 def test_field_gradient_matches_finite_differences(kernel):
     """loss = sum_c w_c LCP_c on a small field: dloss/dy_i and dloss/dlog l_d (analytic, chain rule
