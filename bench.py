@@ -195,7 +195,9 @@ def run_reference(args):
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": w.name + " x3 isovalues", "sample": f"{k}^3 cells at the median isovalue"},
+           "config": {"workload": f"{w.name}, 3 isovalues (P25/P50/P75 of y), SOV-QMC 1600, {args.mode}",
+                      "m": w.m, "grid": w.n, "mode": args.mode,
+                      "sample": f"{k}^3 cells at the median isovalue (every cell of the block, oracle)"},
            "cpu_baseline": {"value": v, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
                             "sample": f"{k}^3-cell block per step, model set-up included"},
            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
