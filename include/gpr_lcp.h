@@ -75,9 +75,9 @@ typedef enum {
  *   GPR_EST_SOV_ORDERED  GPR_EST_SOV_QMC with each orthant's corners taken in ascending order
  *                     of their standardised thresholds s (theta - mu_c) / sigma_c (s = +1 for
  *                     all-below, -1 for all-above; ties by corner index; the order is decided
- *                     in FP64), so each orthant has its own Cholesky factor.  Same lattice, same
- *                     cost per sample; on strongly correlated corners far more accurate at the
- *                     same sample count.  Forward only: the backward calls, and the
+ *                     in FP64), so each orthant has its own Cholesky factor.  Same lattice and
+ *                     no more work per sample; on strongly correlated corners far more accurate
+ *                     at the same sample count.  Forward only: the backward calls, and the
  *                     allocation-free entry point, return GPR_ERR_UNSUPPORTED for it. */
 typedef enum {
     GPR_EST_SOV_QMC = 0,
